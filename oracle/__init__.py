@@ -1,0 +1,227 @@
+"""Plain scalar CPU oracle for PAC stochastic aggregation (SIMD-PAC-DB).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product path (``paper_2603_15023_gb300``) never imports it, and the two share
+no code: this wrapper marshals numpy arrays into the C oracle in
+``pac_oracle.c`` and nothing else.
+
+Every function cites the passage of the paper it follows; the readings taken
+where the paper is silent are listed at the top of ``pac_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pac_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+COUNT, SUM, AVG, MIN, MAX = 0, 1, 2, 3, 4
+I64, F32, F64 = 0, 1, 2
+EXACT, APPROX = 0, 1
+BALANCED, RAW = 0, 1
+ADAPTIVE, INDEPENDENT = 0, 1
+F_NULL, F_DIVERSITY, F_ZEROVAR = 1, 2, 4
+APX_CHUNK = 4096
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc into ``oracle/liboracle.so``."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "pac_oracle.h"))
+    ):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u64, i64, u32, i32, sz, vp, dbl = (
+            ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int,
+            ctypes.c_size_t, ctypes.c_void_p, ctypes.c_double,
+        )
+        sig = {
+            "orc_fmix64": (u64, [u64]),
+            "orc_fmix64_inverse": (u64, [u64]),
+            "orc_query_key": (u64, [u64]),
+            "orc_pac_hash": (u64, [i64, u64, i32]),
+            "orc_hash_keys": (None, [vp, sz, u64, i32, vp]),
+            "orc_rng_u64": (u64, [u64, u64, u64]),
+            "orc_u01": (dbl, [u64]),
+            "orc_u01_open0": (dbl, [u64]),
+            "orc_box_muller": (dbl, [u64, u64]),
+            "orc_aggregate_direct": (i32, [vp, vp, i32, vp, i32, sz, u32, i32, vp, vp, vp]),
+            "orc_aggregate_brute": (i32, [vp, u64, i32, vp, i32, vp, i32, sz, u32, i32, vp]),
+            "orc_approx_sum_i64": (i32, [vp, vp, vp, i32, sz, u32, vp]),
+            "orc_approx_avg_i64": (i32, [vp, vp, vp, i32, sz, u32, vp]),
+            "orc_approx_sum_f32state": (i32, [vp, vp, i32, vp, i32, sz, u32, vp]),
+            "orc_release_scale": (dbl, [i32, i32]),
+            "orc_finalize": (None, [vp, vp, u32, u32, vp, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _vtype(values: Optional[np.ndarray]) -> int:
+    if values is None or values.dtype == np.int64:
+        return I64
+    if values.dtype == np.float32:
+        return F32
+    if values.dtype == np.float64:
+        return F64
+    raise TypeError(values.dtype)
+
+
+def _out_dtype(kind: int, vtype: int):
+    if kind == COUNT:
+        return np.uint64
+    if kind == AVG:
+        return np.float64
+    return np.int64 if vtype == I64 else np.float64
+
+
+# -- hashing (Sec. 2 "SIMD-PAC-DB", Sec. 4.2 "PAC Hash") -----------------------
+
+def fmix64(k: int) -> int:
+    return lib().orc_fmix64(k)
+
+
+def fmix64_inverse(h: int) -> int:
+    return lib().orc_fmix64_inverse(h)
+
+
+def query_key(seed: int) -> int:
+    return lib().orc_query_key(seed)
+
+
+def pac_hash(key: int, qkey: int, mode: int = BALANCED) -> int:
+    return lib().orc_pac_hash(key, qkey, mode)
+
+
+def hash_keys(keys: np.ndarray, qkey: int, mode: int = BALANCED) -> np.ndarray:
+    keys = np.ascontiguousarray(keys, dtype=np.int64)
+    out = np.empty(keys.shape[0], dtype=np.uint64)
+    lib().orc_hash_keys(_p(keys), keys.shape[0], qkey, mode, _p(out))
+    return out
+
+
+def rng_u64(seed: int, stream: int, counter: int) -> int:
+    return lib().orc_rng_u64(seed, stream, counter)
+
+
+# -- aggregation (Sec. 4.2 "PAC Aggregation") -------------------------------
+
+def _gid_args(gids: Optional[np.ndarray]):
+    if gids is None:
+        return None, 0
+    gids = np.ascontiguousarray(gids)
+    return gids, gids.dtype.itemsize
+
+
+def aggregate(masks: np.ndarray, values: Optional[np.ndarray], gids: Optional[np.ndarray],
+              n_groups: int, kind: int):
+    """Exact definition, row by row.  Returns (out[n_groups,64], n_g, or_g, status)."""
+    masks = np.ascontiguousarray(masks, dtype=np.uint64)
+    values = None if values is None else np.ascontiguousarray(values)
+    vt = _vtype(values)
+    g, gb = _gid_args(gids)
+    out = np.zeros((n_groups, 64), dtype=_out_dtype(kind, vt))
+    mn = np.zeros(n_groups, dtype=np.uint64)
+    mo = np.zeros(n_groups, dtype=np.uint64)
+    st = lib().orc_aggregate_direct(_p(masks), _p(values), vt, _p(g), gb, masks.shape[0],
+                                    n_groups, kind, _p(out), _p(mn), _p(mo))
+    return out, mn, mo, st
+
+
+def aggregate_brute(keys: np.ndarray, qkey: int, mode: int, values: Optional[np.ndarray],
+                    gids: Optional[np.ndarray], n_groups: int, kind: int):
+    """Same definition over 64 materialised subsamples.  Returns (out, status)."""
+    keys = np.ascontiguousarray(keys, dtype=np.int64)
+    values = None if values is None else np.ascontiguousarray(values)
+    vt = _vtype(values)
+    g, gb = _gid_args(gids)
+    out = np.zeros((n_groups, 64), dtype=_out_dtype(kind, vt))
+    st = lib().orc_aggregate_brute(_p(keys), qkey, mode, _p(values), vt, _p(g), gb,
+                                   keys.shape[0], n_groups, kind, _p(out))
+    return out, st
+
+
+def approx_sum_i64(masks, values, gids, n_groups):
+    """Two-sided 25-level approximate integer SUM (Sec. 5 "Approximation")."""
+    masks = np.ascontiguousarray(masks, dtype=np.uint64)
+    values = np.ascontiguousarray(values, dtype=np.int64)
+    g, gb = _gid_args(gids)
+    out = np.zeros((n_groups, 64), dtype=np.int64)
+    st = lib().orc_approx_sum_i64(_p(masks), _p(values), _p(g), gb, masks.shape[0], n_groups, _p(out))
+    return out, st
+
+
+def approx_avg_i64(masks, values, gids, n_groups):
+    masks = np.ascontiguousarray(masks, dtype=np.uint64)
+    values = np.ascontiguousarray(values, dtype=np.int64)
+    g, gb = _gid_args(gids)
+    out = np.zeros((n_groups, 64), dtype=np.float64)
+    st = lib().orc_approx_avg_i64(_p(masks), _p(values), _p(g), gb, masks.shape[0], n_groups, _p(out))
+    return out, st
+
+
+def approx_sum_f32state(masks, values, gids, n_groups):
+    masks = np.ascontiguousarray(masks, dtype=np.uint64)
+    values = np.ascontiguousarray(values)
+    vt = _vtype(values)
+    g, gb = _gid_args(gids)
+    out = np.zeros((n_groups, 64), dtype=np.float64)
+    st = lib().orc_approx_sum_f32state(_p(masks), _p(values), vt, _p(g), gb, masks.shape[0],
+                                       n_groups, _p(out))
+    return out, st
+
+
+# -- finalize (Sec. 4.1 noise function; Sec. 2; Sec. 3.2 "NULLs") --------------
+
+def release_scale(kind: int, variant: int = EXACT) -> float:
+    return lib().orc_release_scale(kind, variant)
+
+
+def finalize(y: np.ndarray, scales, meta_n: np.ndarray, meta_or: np.ndarray, seed: int,
+             budget: float, mode: int = ADAPTIVE):
+    """y: [n_groups, n_specs, 64] unscaled results.  Returns dict of outputs."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n_groups, n_specs = y.shape[0], y.shape[1]
+    scales = np.ascontiguousarray(np.asarray(scales, dtype=np.float64))
+    assert scales.shape == (n_specs,)
+    meta_n = np.ascontiguousarray(meta_n, dtype=np.uint64)
+    meta_or = np.ascontiguousarray(meta_or, dtype=np.uint64)
+    nc = n_groups * n_specs
+    noised = np.zeros(nc, dtype=np.float64)
+    is_null = np.zeros(nc, dtype=np.uint8)
+    flags = np.zeros(nc, dtype=np.uint32)
+    post = np.zeros(64, dtype=np.float64)
+    js = ctypes.c_int32(0)
+    lib().orc_finalize(_p(y), _p(scales), n_specs, n_groups, _p(meta_n), _p(meta_or), seed,
+                       budget, mode, _p(noised), _p(is_null), _p(flags), _p(post),
+                       ctypes.byref(js))
+    return {"noised": noised, "is_null": is_null, "flags": flags, "posterior": post,
+            "jstar": js.value}

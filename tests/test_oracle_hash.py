@@ -1,0 +1,126 @@
+"""Pins for the oracle's hashing and random-number layer.
+
+pac_hash (Sec. 2 "SIMD-PAC-DB", Sec. 4.2 "PAC Hash") turns a PU key into a
+64-bit word whose bit j says whether the PU lies in possible world j.  The
+paper prints no hash value, so the pins are properties the paper fixes (each
+PU in exactly m/2 worlds under the balanced construction of Sec. 4.1, each
+world a 50% sample) plus properties of the published building blocks
+(fmix64 is a bijection with fmix64(0) = 0; SplitMix64's published outputs).
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+M64 = (1 << 64) - 1
+GAMMA = 0x9E3779B97F4A7C15
+
+
+def _golden_u64(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [int(l) for l in f if l.strip() and not l.startswith("#")]
+
+
+def _py_splitmix64(state, count):
+    """Python SplitMix64, pinned to the published vector in the first test."""
+    out = []
+    for _ in range(count):
+        state = (state + GAMMA) & M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def test_splitmix64_published_vector():
+    assert _py_splitmix64(0, 3) == _golden_u64("splitmix64_seed0.txt")
+
+
+def test_rng_is_splitmix64_by_stream_and_counter(orc):
+    # draw(seed, stream, c) = output c of SplitMix64 started from output
+    # `stream` of SplitMix64(seed): compare with stepping the sequences.
+    for seed in (0, 1, 0xDEADBEEF, M64):
+        for stream in (0, 1, 2, 7):
+            stream_state = _py_splitmix64((seed + stream * GAMMA) & M64, 1)[0]
+            seq = _py_splitmix64(stream_state, 40)
+            got = [orc.rng_u64(seed, stream, c) for c in range(40)]
+            assert got == seq
+
+
+def test_fmix64_zero_and_inverse(orc):
+    assert orc.fmix64(0) == 0  # every step maps 0 to 0
+    rng = np.random.default_rng(1)
+    xs = [int(x) for x in rng.integers(0, 2**63, size=20000, dtype=np.int64)]
+    xs += [0, 1, 2, M64, 1 << 63, (1 << 63) - 1]
+    for x in xs:
+        assert orc.fmix64_inverse(orc.fmix64(x)) == x
+        assert orc.fmix64(orc.fmix64_inverse(x)) == x
+
+
+def test_fmix64_avalanche(orc):
+    # a one-bit change of the input flips about half of the output bits
+    rng = np.random.default_rng(2)
+    flips = []
+    for x in rng.integers(0, 2**63, size=400, dtype=np.int64):
+        x = int(x)
+        h = orc.fmix64(x)
+        for b in range(0, 64, 7):
+            flips.append(bin(h ^ orc.fmix64(x ^ (1 << b))).count("1"))
+    assert abs(np.mean(flips) - 32.0) < 0.5
+
+
+def test_balanced_masks_exactly_half(orc):
+    rng = np.random.default_rng(3)
+    keys = rng.integers(-(2**62), 2**62, size=50000, dtype=np.int64)
+    for seed in (0, 5):
+        masks = orc.hash_keys(keys, orc.query_key(seed), orc.BALANCED)
+        lo = masks & np.uint64(0xFFFFFFFF)
+        hi = masks >> np.uint64(32)
+        assert np.all(hi == (~lo & np.uint64(0xFFFFFFFF)))
+        pc = np.array([bin(int(m)).count("1") for m in masks[:5000]])
+        assert np.all(pc == 32)
+
+
+def test_raw_masks_binomial(orc):
+    keys = np.arange(200000, dtype=np.int64)
+    masks = orc.hash_keys(keys, orc.query_key(11), orc.RAW)
+    pc = np.unpackbits(masks.view(np.uint8)).reshape(-1, 64).sum(1)
+    assert abs(pc.mean() - 32.0) < 5 * 4 / np.sqrt(len(pc))
+    assert abs(pc.var() - 16.0) < 0.5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_each_world_is_a_half_sample(orc, mode):
+    # every bit is set for ~50% of the distinct PUs (each world is a 50%
+    # subsample of the PU table, Sec. 2 "PAC-DB Example")
+    n = 100000
+    keys = np.arange(n, dtype=np.int64) * 7919 + 3
+    masks = orc.hash_keys(keys, orc.query_key(42), mode)
+    bits = np.unpackbits(masks.view(np.uint8), bitorder="little").reshape(-1, 64)
+    frac = bits.mean(0)
+    assert np.all(np.abs(frac - 0.5) < 5 * 0.5 / np.sqrt(n))
+
+
+def test_rehash_per_query_reshuffles_worlds(orc):
+    # two query keys give (nearly) independent world memberships
+    keys = np.arange(50000, dtype=np.int64)
+    a = orc.hash_keys(keys, orc.query_key(1), orc.RAW)
+    b = orc.hash_keys(keys, orc.query_key(2), orc.RAW)
+    ba = np.unpackbits(a.view(np.uint8)).reshape(-1, 64)
+    bb = np.unpackbits(b.view(np.uint8)).reshape(-1, 64)
+    agree = (ba == bb).mean()
+    assert abs(agree - 0.5) < 0.01
+    assert orc.query_key(1) != orc.query_key(2)
+
+
+def test_uniform_draws(orc):
+    assert orc.lib().orc_u01(0) == 0.0
+    assert orc.lib().orc_u01(M64) < 1.0
+    assert orc.lib().orc_u01_open0(0) > 0.0
+    assert orc.lib().orc_u01_open0(M64) == 1.0
+    z = np.array([orc.lib().orc_box_muller(orc.rng_u64(9, 2, 2 * i), orc.rng_u64(9, 2, 2 * i + 1))
+                  for i in range(20000)])
+    assert stats.kstest(z, "norm").pvalue > 1e-3
