@@ -1,0 +1,235 @@
+/*
+ * pac.h -- C ABI of the GB300 (sm_103a) PAC stochastic-aggregation library
+ * (SIMD-PAC-DB, arXiv 2603.15023).
+ *
+ * The library computes the data-parallel hot path of SIMD-PAC-DB on one GPU:
+ *   1. pac_hash_keys      PU key -> 64-bit world mask (Sec. 2 "SIMD-PAC-DB",
+ *                         Sec. 4.2 "PAC Hash");
+ *   2. pac_aggregate[_multi]
+ *                         per-group, per-world COUNT/SUM/AVG/MIN/MAX over the
+ *                         set bits of the mask (Sec. 4.2 "PAC Aggregation"),
+ *                         exactly or in the approximate variants of Sec. 5
+ *                         "Approximation";
+ *   3. pac_finalize       variance of each cell's 64 world results under the
+ *                         posterior and the PAC noise derived from it (Sec. 2
+ *                         "PAC Privacy", Sec. 4.1 noise function steps 1-4,
+ *                         Sec. 3.2 "NULLs", Sec. 5 "Diversity Check").
+ *
+ * Conventions shared by every entry point
+ *   - m = 64 worlds: world j <-> bit j of the mask, 0 <= j < 64 (Sec. 5).
+ *   - Per-world results are row-major [n_groups][64].
+ *   - Unless stated otherwise, data pointers are DEVICE pointers owned by the
+ *     caller; the library never frees them and never keeps them after the
+ *     call returns.  Calls are asynchronous on the given stream (a
+ *     cudaStream_t; NULL = legacy default stream).
+ *   - Argument errors are found on the host before any launch and return
+ *     PAC_E_INVALID or PAC_E_UNSUPPORTED with nothing enqueued.  Conditions
+ *     only the device can see (an exact integer SUM that does not fit int64,
+ *     an approximate cascade past its last level, a device wait that timed
+ *     out) are recorded in the context's device status word and returned by
+ *     the next pac_sync_status().
+ *   - No C++ exception crosses this boundary.  A context is used by one host
+ *     thread at a time.
+ */
+#ifndef PAC_H
+#define PAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pac_stream; /* same type as cudaStream_t */
+typedef struct pac_ctx pac_ctx;
+
+typedef enum {
+    PAC_OK = 0,
+    PAC_E_INVALID = 1,     /* bad argument: null pointer, size, enum value */
+    PAC_E_NOMEM = 2,       /* device or host allocation failed */
+    PAC_E_CUDA = 3,        /* a CUDA runtime call failed (see pac_last_error) */
+    PAC_E_OVERFLOW = 4,    /* a result did not fit its output type */
+    PAC_E_TIMEOUT = 5,     /* a bounded device wait gave up */
+    PAC_E_UNSUPPORTED = 6  /* valid request this build does not serve */
+} pac_status;
+
+/* Aggregates of Sec. 4.2 "PAC Aggregation": agg in {sum,count,avg,min,max}. */
+typedef enum { PAC_COUNT = 0, PAC_SUM = 1, PAC_AVG = 2, PAC_MIN = 3, PAC_MAX = 4 } pac_kind;
+
+/* Value column types. */
+typedef enum { PAC_I64 = 0, PAC_F32 = 1, PAC_F64 = 2 } pac_dtype;
+
+/* PAC_EXACT: r_j = agg{e(t) : pu[j] = 1} exactly (integers bit-exact; float
+ * SUM in FP32 with compensated two-sum partials, within 1e-6 relative of the
+ * FP64 sum).  PAC_APPROX: the paper's approximate variants (Sec. 5
+ * "Approximation"): integer SUM/AVG through 25 levels of 16-bit counters
+ * cascading every 4 bits, two-sided; float SUM with plain FLOAT state. */
+typedef enum { PAC_EXACT = 0, PAC_APPROX = 1 } pac_variant;
+
+/* PAC_HASH_BALANCED: every PU lies in exactly 32 worlds (Sec. 2: a hash with
+ * guaranteed 32 one-bits); worlds j and j+32 are complements.
+ * PAC_HASH_RAW: the 64 bits of the keyed hash (binomial popcount). */
+typedef enum { PAC_HASH_BALANCED = 0, PAC_HASH_RAW = 1 } pac_hash_mode;
+
+/* PAC_FIN_ADAPTIVE: the posterior over the secret world is updated after
+ * every release (Sec. 2, adaptive composition; Sec. 4.1 step 4).
+ * PAC_FIN_INDEPENDENT: every cell is noised under the uniform prior (not the
+ * paper's composition; offered for independent releases). */
+typedef enum { PAC_FIN_ADAPTIVE = 0, PAC_FIN_INDEPENDENT = 1 } pac_fin_mode;
+
+/* Input selector for pac_aggregate*: the first column holds PU keys (int64,
+ * hashed inside the aggregation with query_key and hash_mode) or already
+ * computed world masks (uint64, e.g. from pac_hash_keys). */
+#define PAC_IN_KEYS 0u
+#define PAC_IN_MASKS 1u
+
+/* Per-cell flags written by pac_finalize. */
+#define PAC_F_NULL 1u      /* released NULL (Sec. 3.2 "NULLs") */
+#define PAC_F_DIVERSITY 2u /* >= 64 rows but <= 40 worlds ever updated (Sec. 5) */
+#define PAC_F_ZEROVAR 4u   /* variance under the posterior was exactly 0 */
+
+/* ---------------------------------------------------------------------------
+ * Context.  Owns device workspace (grown on demand, freed by pac_destroy),
+ * a device status word and the last error message.  `device` is the CUDA
+ * ordinal the context's launches use; it is made current in every call.
+ * ------------------------------------------------------------------------ */
+pac_status pac_create(pac_ctx **ctx, int device);
+void pac_destroy(pac_ctx *ctx);
+const char *pac_last_error(const pac_ctx *ctx);
+const char *pac_status_string(pac_status s);
+
+/* Synchronises `stream`, returns (and clears) the device status word:
+ * PAC_OK, PAC_E_OVERFLOW or PAC_E_TIMEOUT. */
+pac_status pac_sync_status(pac_ctx *ctx, pac_stream stream);
+
+/* Host-only: the per-query hash key K (Sec. 4.2: drawn independently per
+ * query) for a query seed: the first SplitMix64 output of seed XOR the
+ * ASCII tag "PAC_KEY!". */
+uint64_t pac_query_key(uint64_t seed);
+
+/* ---------------------------------------------------------------------------
+ * 1. pac_hash_keys  (Sec. 2 "SIMD-PAC-DB"; Sec. 4.2 "PAC Hash")
+ *   keys  [n] int64 PU keys (device); masks [n] uint64 out (device).
+ *   mask = balance(fmix64(fmix64(key) XOR query_key)), fmix64 being
+ *   MurmurHash3's 64-bit finalizer; balance keeps the low 32 bits and puts
+ *   their complement in the high 32 (PAC_HASH_BALANCED) or is the identity
+ *   (PAC_HASH_RAW).  n = 0 is a no-op.  keys and masks may alias.
+ * ------------------------------------------------------------------------ */
+pac_status pac_hash_keys(pac_ctx *ctx, const int64_t *keys, uint64_t *masks, size_t n,
+                         uint64_t query_key, int32_t hash_mode, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * 2. pac_aggregate / pac_aggregate_multi  (Sec. 4.2 "PAC Aggregation";
+ *    Sec. 5 for the approximate variants; Sec. 3.2 "NULLs" for meta)
+ *
+ * Shared input of one query:
+ *   keys_or_masks [n] int64 keys (PAC_IN_KEYS) or uint64 masks (PAC_IN_MASKS)
+ *   group_ids     [n] unsigned group id of width gid_bytes (1, 2 or 4), each
+ *                 < n_groups; NULL means ungrouped (n_groups must be 1)
+ *   n             rows (0 allowed: every output is zero)
+ *   n_groups      >= 1
+ * One aggregate per spec:
+ *   values  [n] column of vtype (ignored, may be NULL, for PAC_COUNT)
+ *   out     [n_groups*64] results, type by kind:
+ *             COUNT                      -> uint64
+ *             SUM, MIN, MAX over PAC_I64 -> int64 (SUM exact; APPROX SUM is
+ *                                           the unscaled two-sided sum)
+ *             AVG (any), SUM/MIN/MAX over floats -> double
+ *           An empty world gives 0 for every kind (Sec. 3.2: unset worlds
+ *           count as zeros).
+ * meta (optional, may be NULL): [n_groups*2] uint64 {rows n_g, OR of the
+ *   masks of the group's rows}, the NULL accumulator of Sec. 3.2.
+ * Supported: every kind/vtype with PAC_EXACT; PAC_APPROX for SUM and AVG
+ * over PAC_I64 (25-level cascade) and SUM over floats (FLOAT state).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const void *keys_or_masks;
+    uint32_t in_flags;     /* PAC_IN_KEYS or PAC_IN_MASKS */
+    int32_t hash_mode;     /* pac_hash_mode, used with PAC_IN_KEYS */
+    uint64_t query_key;    /* K, used with PAC_IN_KEYS */
+    const void *group_ids; /* NULL = ungrouped */
+    int32_t gid_bytes;     /* 1, 2 or 4 (ignored when ungrouped) */
+    uint32_t n_groups;
+    size_t n;
+} pac_input;
+
+typedef struct {
+    int32_t kind;       /* pac_kind */
+    int32_t variant;    /* pac_variant */
+    int32_t vtype;      /* pac_dtype of values */
+    int32_t reserved;   /* must be 0 */
+    const void *values; /* device [n] */
+    void *out;          /* device [n_groups*64]; an input of pac_finalize */
+} pac_agg_spec;
+
+#define PAC_MAX_SPECS 16
+
+pac_status pac_aggregate(pac_ctx *ctx, const void *keys_or_masks, uint32_t in_flags,
+                         uint64_t query_key, int32_t hash_mode, const void *values,
+                         int32_t vtype, const void *group_ids, int32_t gid_bytes, size_t n,
+                         uint32_t n_groups, int32_t kind, int32_t variant, void *out,
+                         uint64_t *meta, pac_stream stream);
+
+/* Several aggregates over one pass of the shared key/group columns
+ * (n_specs <= PAC_MAX_SPECS; specs is a HOST array). */
+pac_status pac_aggregate_multi(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
+                               int32_t n_specs, uint64_t *meta, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * 3. pac_finalize  (Sec. 2 "PAC Privacy" and fused pac_noised_count;
+ *    Sec. 4.1 noise function steps 1-4; Sec. 3.2 "NULLs"; Sec. 5
+ *    "Diversity Check")
+ *
+ * Releases every cell of one query: cell c = g*n_specs + s, for group g and
+ * spec s (specs: the HOST array given to pac_aggregate_multi, whose `out`
+ * buffers hold the 64 world results).  meta: the device {n_g, or_g} array
+ * filled by the aggregation.  For each cell, in that order:
+ *   NULL with probability (64 - popcount(or_g))/64 (no posterior update);
+ *   y_j = scale * r_j for worlds in or_g, 0 for the others, scale 2 for
+ *   COUNT and SUM (count[j*]*2 of Sec. 2) and 1 otherwise;
+ *   s^2 = Var_{j~P}[y_j]; Delta = s^2/(2*budget);
+ *   release y_{j*} + sqrt(Delta)*z, z standard normal;
+ *   P <- P*W/sum(P*W), W_j = exp(-(release - y_j)^2/(2*Delta))
+ *   (PAC_FIN_ADAPTIVE only).
+ * The secret world j*, the NULL draws and z come from one counter-based
+ * SplitMix64 generator keyed by `seed` (draw i of stream t is output i of
+ * SplitMix64 started at output t of SplitMix64(seed); streams 0: j*,
+ * 1: NULL, 2: Box-Muller pairs).  budget > 0 is the per-cell MI budget B.
+ * Outputs (device): noised[n_cells] (0 for NULL cells), is_null[n_cells],
+ * flags[n_cells] (PAC_F_*), posterior[64] final P (may be NULL).
+ * ------------------------------------------------------------------------ */
+pac_status pac_finalize(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs,
+                        uint32_t n_groups, const uint64_t *meta, uint64_t seed, double budget,
+                        int32_t mode, double *noised, uint8_t *is_null, uint32_t *flags,
+                        double *posterior, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * End-to-end query from HOST memory: copies the columns named by `in` and
+ * `specs` (HOST pointers, ideally pinned) into context-owned device
+ * workspace, runs pac_aggregate_multi and pac_finalize there, and copies the
+ * released cells back into HOST noised/is_null/flags (n_groups*n_specs
+ * each).  The specs' `out` fields are ignored (results live in workspace).
+ * Synchronous: returns after the results are on the host, with the device
+ * status folded into the return value.
+ * ------------------------------------------------------------------------ */
+pac_status pac_query_host(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
+                          int32_t n_specs, uint64_t seed, double budget, int32_t mode,
+                          double *noised, uint8_t *is_null, uint32_t *flags, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Path selection and introspection (for benchmarks and tests).
+ *   pac_set_option(ctx, name, value): "agg_path" 0 = automatic (tensor-core
+ *   path where it applies), 1 = force the per-bit CUDA-core path, 2 = force
+ *   the tensor-core path (PAC_E_UNSUPPORTED where it cannot serve).
+ *   pac_get_info(ctx, name, &value): "last_path" (1 per-bit, 2 tensor core,
+ *   3 partitioned high-cardinality), "last_launches" kernels launched by the
+ *   last call.
+ * ------------------------------------------------------------------------ */
+pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value);
+pac_status pac_get_info(pac_ctx *ctx, const char *name, int64_t *value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAC_H */

@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
             "orc_u01_open0": (dbl, [u64]),
             "orc_box_muller": (dbl, [u64, u64]),
             "orc_aggregate_direct": (i32, [vp, vp, i32, vp, i32, sz, u32, i32, vp, vp, vp]),
+            "orc_aggregate_world": (i32, [vp, vp, i32, vp, i32, sz, u32, i32, i32, vp]),
             "orc_aggregate_brute": (i32, [vp, u64, i32, vp, i32, vp, i32, sz, u32, i32, vp]),
             "orc_approx_sum_i64": (i32, [vp, vp, vp, i32, sz, u32, vp]),
             "orc_approx_avg_i64": (i32, [vp, vp, vp, i32, sz, u32, vp]),
@@ -154,6 +155,19 @@ def aggregate(masks: np.ndarray, values: Optional[np.ndarray], gids: Optional[np
     st = lib().orc_aggregate_direct(_p(masks), _p(values), vt, _p(g), gb, masks.shape[0],
                                     n_groups, kind, _p(out), _p(mn), _p(mo))
     return out, mn, mo, st
+
+
+def aggregate_world(masks: np.ndarray, values: Optional[np.ndarray], gids: Optional[np.ndarray],
+                    n_groups: int, kind: int, world: int):
+    """r_j of one world for every group.  Returns (out[n_groups], status)."""
+    masks = np.ascontiguousarray(masks, dtype=np.uint64)
+    values = None if values is None else np.ascontiguousarray(values)
+    vt = _vtype(values)
+    g, gb = _gid_args(gids)
+    out = np.zeros(n_groups, dtype=_out_dtype(kind, vt))
+    st = lib().orc_aggregate_world(_p(masks), _p(values), vt, _p(g), gb, masks.shape[0], n_groups,
+                                   kind, world, _p(out))
+    return out, st
 
 
 def aggregate_brute(keys: np.ndarray, qkey: int, mode: int, values: Optional[np.ndarray],

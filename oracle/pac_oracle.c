@@ -270,6 +270,23 @@ int orc_aggregate_direct(const uint64_t *masks, const void *values, int vtype,
     return status;
 }
 
+/* One world only: r_j for a single j, every group (the same definition,
+ * restricted to one world so that large inputs can be sampled). */
+int orc_aggregate_world(const uint64_t *masks, const void *values, int vtype,
+                        const void *gids, int gid_bytes, size_t n,
+                        uint32_t n_groups, int kind, int world, void *out) {
+    int status = 0;
+    acc_t *acc = (acc_t *)malloc(sizeof(acc_t) * (size_t)n_groups);
+    if (!acc) return 2;
+    for (uint32_t g = 0; g < n_groups; g++) acc_init(&acc[g]);
+    for (size_t i = 0; i < n; i++)
+        if ((masks[i] >> world) & 1ULL)
+            acc_update(&acc[gid_at(gids, gid_bytes, i)], values, vtype, i);
+    for (uint32_t g = 0; g < n_groups; g++) acc_emit(&acc[g], vtype, kind, out, g, &status);
+    free(acc);
+    return status;
+}
+
 /* ====================================================================== */
 /* Brute force over materialised worlds (Sec. 4.1 steps (1)-(2); the       */
 /* subsets coincide with S_j = { u : pac_hash_K(u)[j] = 1 } as Theorem 2   */

@@ -64,6 +64,11 @@ int orc_aggregate_direct(const uint64_t *masks, const void *values, int vtype,
                          uint32_t n_groups, int kind, void *out,
                          uint64_t *meta_n, uint64_t *meta_or);
 
+/* r_j of one world j for every group: out[n_groups] (sampling large inputs). */
+int orc_aggregate_world(const uint64_t *masks, const void *values, int vtype,
+                        const void *gids, int gid_bytes, size_t n,
+                        uint32_t n_groups, int kind, int world, void *out);
+
 /* ---- the same definition, computed world by world on materialised
  *      subsamples (Sec. 4.1 compilation procedure steps (1)-(2), with the
  *      hash-coupled SamplePU of Theorem 2) ------------------------------- */

@@ -1,0 +1,194 @@
+"""Thin ctypes binding of the C ABI in ``include/pac.h`` (``libpac.so``).
+
+Function names are the C names; arguments are marshalled, nothing is
+computed here.  Device buffers are passed as integer addresses (for example
+``tensor.data_ptr()`` of a CUDA tensor) and streams as ``cudaStream_t``
+handles (``torch.cuda.current_stream().cuda_stream``).  Loading fails loudly
+when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpac.so")
+
+PAC_OK, PAC_E_INVALID, PAC_E_NOMEM, PAC_E_CUDA, PAC_E_OVERFLOW, PAC_E_TIMEOUT, PAC_E_UNSUPPORTED = range(7)
+PAC_COUNT, PAC_SUM, PAC_AVG, PAC_MIN, PAC_MAX = range(5)
+PAC_I64, PAC_F32, PAC_F64 = range(3)
+PAC_EXACT, PAC_APPROX = 0, 1
+PAC_HASH_BALANCED, PAC_HASH_RAW = 0, 1
+PAC_FIN_ADAPTIVE, PAC_FIN_INDEPENDENT = 0, 1
+PAC_IN_KEYS, PAC_IN_MASKS = 0, 1
+PAC_F_NULL, PAC_F_DIVERSITY, PAC_F_ZEROVAR = 1, 2, 4
+PAC_MAX_SPECS = 16
+
+# every symbol the header declares
+EXPORTED = (
+    "pac_create", "pac_destroy", "pac_last_error", "pac_status_string", "pac_sync_status",
+    "pac_query_key", "pac_hash_keys", "pac_aggregate", "pac_aggregate_multi", "pac_finalize",
+    "pac_query_host", "pac_set_option", "pac_get_info",
+)
+
+
+class PacInput(ctypes.Structure):
+    _fields_ = [
+        ("keys_or_masks", ctypes.c_void_p),
+        ("in_flags", ctypes.c_uint32),
+        ("hash_mode", ctypes.c_int32),
+        ("query_key", ctypes.c_uint64),
+        ("group_ids", ctypes.c_void_p),
+        ("gid_bytes", ctypes.c_int32),
+        ("n_groups", ctypes.c_uint32),
+        ("n", ctypes.c_size_t),
+    ]
+
+
+class PacAggSpec(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
+        ("vtype", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("values", ctypes.c_void_p),
+        ("out", ctypes.c_void_p),
+    ]
+
+
+class PacError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libpac.so (raises if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u32, i32, u64, i64, sz, dbl = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64,
+                                       ctypes.c_int64, ctypes.c_size_t, ctypes.c_double)
+    sigs = {
+        "pac_create": (i32, [ctypes.POINTER(vp), ctypes.c_int]),
+        "pac_destroy": (None, [vp]),
+        "pac_last_error": (ctypes.c_char_p, [vp]),
+        "pac_status_string": (ctypes.c_char_p, [i32]),
+        "pac_sync_status": (i32, [vp, vp]),
+        "pac_query_key": (u64, [u64]),
+        "pac_hash_keys": (i32, [vp, vp, vp, sz, u64, i32, vp]),
+        "pac_aggregate": (i32, [vp, vp, u32, u64, i32, vp, i32, vp, i32, sz, u32, i32, i32, vp, vp, vp]),
+        "pac_aggregate_multi": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacAggSpec), i32, vp, vp]),
+        "pac_finalize": (i32, [vp, ctypes.POINTER(PacAggSpec), i32, u32, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
+        "pac_query_host": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacAggSpec), i32, u64, dbl, i32,
+                                 vp, vp, vp, vp]),
+        "pac_set_option": (i32, [vp, ctypes.c_char_p, i64]),
+        "pac_get_info": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(i64)]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_name(st: int) -> str:
+    return lib().pac_status_string(st).decode()
+
+
+def _check(ctx, st: int):
+    if st != PAC_OK:
+        msg = lib().pac_last_error(ctx).decode() if ctx else ""
+        raise PacError(st, msg)
+
+
+# ---- the C entry points, same names ---------------------------------------
+
+def pac_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    st = lib().pac_create(ctypes.byref(h), device)
+    if st != PAC_OK:
+        raise PacError(st, f"pac_create(device={device})")
+    return h.value
+
+
+def pac_destroy(ctx: int) -> None:
+    lib().pac_destroy(ctx)
+
+
+def pac_last_error(ctx: int) -> str:
+    return lib().pac_last_error(ctx).decode()
+
+
+def pac_status_string(st: int) -> str:
+    return status_name(st)
+
+
+def pac_sync_status(ctx: int, stream: int = 0) -> int:
+    """Returns the status code (does not raise on OVERFLOW/TIMEOUT)."""
+    return lib().pac_sync_status(ctx, stream)
+
+
+def pac_query_key(seed: int) -> int:
+    return lib().pac_query_key(seed)
+
+
+def pac_hash_keys(ctx: int, keys: int, masks: int, n: int, query_key: int, hash_mode: int,
+                  stream: int = 0) -> None:
+    _check(ctx, lib().pac_hash_keys(ctx, keys, masks, n, query_key, hash_mode, stream))
+
+
+def pac_aggregate(ctx: int, keys_or_masks: int, in_flags: int, query_key: int, hash_mode: int,
+                  values: int, vtype: int, group_ids: int, gid_bytes: int, n: int, n_groups: int,
+                  kind: int, variant: int, out: int, meta: int, stream: int = 0) -> None:
+    _check(ctx, lib().pac_aggregate(ctx, keys_or_masks, in_flags, query_key, hash_mode, values, vtype,
+                                    group_ids, gid_bytes, n, n_groups, kind, variant, out, meta, stream))
+
+
+def make_input(keys_or_masks: int, n: int, *, in_flags: int = PAC_IN_KEYS, hash_mode: int = PAC_HASH_BALANCED,
+               query_key: int = 0, group_ids: int = 0, gid_bytes: int = 0, n_groups: int = 1) -> PacInput:
+    return PacInput(keys_or_masks, in_flags, hash_mode, query_key, group_ids or None, gid_bytes, n_groups, n)
+
+
+def make_specs(specs: Sequence[tuple]) -> ctypes.Array:
+    """specs: (kind, variant, vtype, values_ptr, out_ptr) tuples."""
+    arr = (PacAggSpec * max(len(specs), 1))()
+    for i, (kind, variant, vtype, values, out) in enumerate(specs):
+        arr[i] = PacAggSpec(kind, variant, vtype, 0, values or None, out)
+    return arr
+
+
+def pac_aggregate_multi(ctx: int, inp: PacInput, specs: ctypes.Array, n_specs: int, meta: int,
+                        stream: int = 0) -> None:
+    _check(ctx, lib().pac_aggregate_multi(ctx, ctypes.byref(inp), specs, n_specs, meta or None, stream))
+
+
+def pac_finalize(ctx: int, specs: ctypes.Array, n_specs: int, n_groups: int, meta: int, seed: int,
+                 budget: float, mode: int, noised: int, is_null: int, flags: int, posterior: int,
+                 stream: int = 0) -> None:
+    _check(ctx, lib().pac_finalize(ctx, specs, n_specs, n_groups, meta, seed, budget, mode, noised, is_null,
+                                   flags, posterior or None, stream))
+
+
+def pac_query_host(ctx: int, inp: PacInput, specs: ctypes.Array, n_specs: int, seed: int, budget: float,
+                   mode: int, noised: int, is_null: int, flags: int, stream: int = 0) -> None:
+    _check(ctx, lib().pac_query_host(ctx, ctypes.byref(inp), specs, n_specs, seed, budget, mode, noised,
+                                     is_null, flags, stream))
+
+
+def pac_set_option(ctx: int, name: str, value: int) -> None:
+    _check(ctx, lib().pac_set_option(ctx, name.encode(), value))
+
+
+def pac_get_info(ctx: int, name: str) -> int:
+    v = ctypes.c_int64(0)
+    _check(ctx, lib().pac_get_info(ctx, name.encode(), ctypes.byref(v)))
+    return v.value

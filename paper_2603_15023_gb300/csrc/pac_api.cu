@@ -1,0 +1,472 @@
+// pac_api.cu -- the C ABI (include/pac.h): argument checking, path choice,
+// context-owned workspace and the launches of the PAC kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pac_ctx.h"
+#include "pac_internal.cuh"
+#include "pac_kernels.h"
+#include "pac_mma.h"
+
+using namespace pacgpu;
+
+namespace {
+
+bool is_float(int32_t vtype) { return vtype == PAC_F32 || vtype == PAC_F64; }
+
+// Which per-world state a spec needs on the per-bit path (-1: none).
+int spec_op(const pac_agg_spec &s) {
+    switch (s.kind) {
+    case PAC_COUNT: return -1;
+    case PAC_SUM:
+    case PAC_AVG:
+        if (s.vtype == PAC_I64) return s.variant == PAC_APPROX ? -1 : OP_ISUM;
+        return s.variant == PAC_APPROX ? OP_FSUM_PLAIN : OP_FSUM_COMP;
+    case PAC_MIN: return is_float(s.vtype) ? OP_FMIN : OP_IMIN;
+    case PAC_MAX: return is_float(s.vtype) ? OP_FMAX : OP_IMAX;
+    }
+    return -1;
+}
+
+bool spec_is_cascade(const pac_agg_spec &s) {
+    return (s.kind == PAC_SUM || s.kind == PAC_AVG) && s.vtype == PAC_I64 && s.variant == PAC_APPROX;
+}
+
+pac_status check_input(pac_ctx *ctx, const pac_input *in) {
+    if (!in) return fail(ctx, PAC_E_INVALID, "input is NULL");
+    if (in->n > 0 && !in->keys_or_masks) return fail(ctx, PAC_E_INVALID, "keys_or_masks is NULL");
+    if (in->in_flags != PAC_IN_KEYS && in->in_flags != PAC_IN_MASKS)
+        return fail(ctx, PAC_E_INVALID, "in_flags %u", in->in_flags);
+    if (in->hash_mode != PAC_HASH_BALANCED && in->hash_mode != PAC_HASH_RAW)
+        return fail(ctx, PAC_E_INVALID, "hash_mode %d", in->hash_mode);
+    if (in->n_groups == 0) return fail(ctx, PAC_E_INVALID, "n_groups must be >= 1");
+    if (!in->group_ids && in->n_groups != 1)
+        return fail(ctx, PAC_E_INVALID, "ungrouped input needs n_groups == 1");
+    if (in->group_ids && in->gid_bytes != 1 && in->gid_bytes != 2 && in->gid_bytes != 4)
+        return fail(ctx, PAC_E_INVALID, "gid_bytes %d", in->gid_bytes);
+    if (in->group_ids && in->gid_bytes == 1 && in->n_groups > 256)
+        return fail(ctx, PAC_E_INVALID, "n_groups %u exceeds 8-bit group ids", in->n_groups);
+    if (in->group_ids && in->gid_bytes == 2 && in->n_groups > 65536)
+        return fail(ctx, PAC_E_INVALID, "n_groups %u exceeds 16-bit group ids", in->n_groups);
+    return PAC_OK;
+}
+
+pac_status check_specs(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs) {
+    if (n_specs < 0 || n_specs > PAC_MAX_SPECS) return fail(ctx, PAC_E_INVALID, "n_specs %d", n_specs);
+    if (n_specs > 0 && !specs) return fail(ctx, PAC_E_INVALID, "specs is NULL");
+    for (int i = 0; i < n_specs; i++) {
+        const pac_agg_spec &s = specs[i];
+        if (s.kind < PAC_COUNT || s.kind > PAC_MAX) return fail(ctx, PAC_E_INVALID, "spec %d: kind %d", i, s.kind);
+        if (s.variant != PAC_EXACT && s.variant != PAC_APPROX)
+            return fail(ctx, PAC_E_INVALID, "spec %d: variant %d", i, s.variant);
+        if (s.kind != PAC_COUNT && (s.vtype < PAC_I64 || s.vtype > PAC_F64))
+            return fail(ctx, PAC_E_INVALID, "spec %d: vtype %d", i, s.vtype);
+        if (s.reserved != 0) return fail(ctx, PAC_E_INVALID, "spec %d: reserved must be 0", i);
+        if (!s.out) return fail(ctx, PAC_E_INVALID, "spec %d: out is NULL", i);
+        if (s.kind != PAC_COUNT && in->n > 0 && !s.values)
+            return fail(ctx, PAC_E_INVALID, "spec %d: values is NULL", i);
+        if (spec_is_cascade(s) && in->n_groups > static_cast<uint32_t>(apx_max_groups()))
+            return fail(ctx, PAC_E_UNSUPPORTED, "spec %d: approximate integer SUM/AVG serves at most %d groups",
+                        i, apx_max_groups());
+    }
+    return PAC_OK;
+}
+
+InputDev make_input(const pac_input *in) {
+    InputDev d;
+    d.km = in->keys_or_masks;
+    d.gids = in->group_ids;
+    d.qkey = in->query_key;
+    d.n = in->n;
+    d.in_flags = in->in_flags;
+    d.hash_mode = in->hash_mode;
+    d.gid_bytes = in->group_ids ? in->gid_bytes : 0;
+    d.n_groups = in->n_groups;
+    return d;
+}
+
+pac_status run_bitloop(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                       uint64_t *meta, cudaStream_t stream, int *launches) {
+    BitloopParams p{};
+    p.in = make_input(in);
+    p.meta = meta;
+    p.status = ctx->d_status;
+    // one state slot per distinct (op, column)
+    int slot_of[PAC_MAX_SPECS];
+    for (int i = 0; i < n_specs; i++) {
+        slot_of[i] = -1;
+        const int op = spec_op(specs[i]);
+        if (op < 0) continue;
+        for (int k = 0; k < p.n_slots; k++)
+            if (p.slot[k].op == op && p.slot[k].values == specs[i].values && p.slot[k].vtype == specs[i].vtype)
+                slot_of[i] = k;
+        if (slot_of[i] < 0) {
+            p.slot[p.n_slots].op = op;
+            p.slot[p.n_slots].vtype = specs[i].vtype;
+            p.slot[p.n_slots].values = specs[i].values;
+            slot_of[i] = p.n_slots++;
+        }
+    }
+    for (int i = 0; i < n_specs; i++) {
+        if (spec_is_cascade(specs[i])) continue;
+        p.outs[p.n_out].kind = specs[i].kind;
+        p.outs[p.n_out].slot = slot_of[i];
+        p.outs[p.n_out].out = specs[i].out;
+        p.n_out++;
+    }
+    const uint32_t G = in->n_groups;
+    const int ns = bitloop_pick_ns(p.n_slots);
+    int n_warps = 8;
+    while (n_warps > 1 && bitloop_smem_bytes(n_warps, p.n_slots, G, ns) > 200 * 1024) n_warps /= 2;
+    const bool lowcard = bitloop_smem_bytes(n_warps, p.n_slots, G, ns) <= 200 * 1024;
+    const size_t per_part = static_cast<size_t>(1 + p.n_slots) * G * kWorlds * 8;
+    if (lowcard) {
+        const int ctas_per_sm = n_warps >= 8 ? 2 : 4;
+        uint64_t n_ctas = static_cast<uint64_t>(ctx->n_sms) * ctas_per_sm;
+        const uint64_t min_rows = 4096;
+        if (in->n / min_rows < n_ctas) n_ctas = in->n / min_rows;
+        if (n_ctas < 1) n_ctas = 1;
+        p.rows_per_cta = (in->n + n_ctas - 1) / n_ctas;
+        p.rows_per_cta = align_up(p.rows_per_cta, 32);
+        if (p.rows_per_cta == 0) p.rows_per_cta = 32;
+        n_ctas = (in->n + p.rows_per_cta - 1) / p.rows_per_cta;
+        if (n_ctas < 1) n_ctas = 1;
+        const size_t need = n_ctas * per_part + 256 + n_ctas * G * 8 + 256;
+        pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, need);
+        if (st != PAC_OK) return st;
+        Carver cv(ctx->ws);
+        p.partials = cv.take(n_ctas * per_part);
+        p.ng_partials = static_cast<uint64_t *>(cv.take(n_ctas * G * 8));
+        PAC_CUDA(ctx, launch_bitloop_lowcard(p, static_cast<int>(n_ctas), n_warps, stream));
+        PAC_CUDA(ctx, launch_bitloop_merge(p, static_cast<int>(n_ctas), false, stream));
+        *launches += 2;
+    } else {
+        const size_t need = per_part + 256 + G * 8 + 256;
+        pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, need);
+        if (st != PAC_OK) return st;
+        Carver cv(ctx->ws);
+        p.partials = cv.take(per_part);
+        p.ng_partials = static_cast<uint64_t *>(cv.take(G * 8));
+        int n_ctas = ctx->n_sms * 8;
+        PAC_CUDA(ctx, launch_bitloop_atomic(p, n_ctas, stream));
+        PAC_CUDA(ctx, launch_bitloop_merge(p, 1, true, stream));
+        *launches += 3;
+    }
+    ctx->last_path = 1;
+    return PAC_OK;
+}
+
+pac_status run_cascades(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                        cudaStream_t stream, int *launches) {
+    for (int i = 0; i < n_specs; i++) {
+        if (!spec_is_cascade(specs[i])) continue;
+        // one cascade per distinct column serves its SUM and AVG specs
+        bool seen = false;
+        for (int k = 0; k < i; k++)
+            if (spec_is_cascade(specs[k]) && specs[k].values == specs[i].values) seen = true;
+        if (seen) continue;
+        int first_sum = -1, first_avg = -1;
+        for (int k = i; k < n_specs; k++) {
+            if (!spec_is_cascade(specs[k]) || specs[k].values != specs[i].values) continue;
+            if (specs[k].kind == PAC_SUM && first_sum < 0) first_sum = k;
+            if (specs[k].kind == PAC_AVG && first_avg < 0) first_avg = k;
+        }
+        ApxParams p{};
+        p.in = make_input(in);
+        p.values = static_cast<const int64_t *>(specs[i].values);
+        p.status = ctx->d_status;
+        const size_t states = apx_scratch_bytes(in->n, in->n_groups);
+        pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, states + 1024);
+        if (st != PAC_OK) return st;
+        Carver cv(ctx->ws);
+        p.ng = static_cast<uint64_t *>(cv.take(in->n_groups * sizeof(uint64_t)));
+        p.states = static_cast<ApxState *>(cv.take(states));
+        PAC_CUDA(ctx, launch_approx(p, first_sum >= 0 ? specs[first_sum].out : nullptr,
+                                    first_avg >= 0 ? specs[first_avg].out : nullptr, stream, launches));
+        // further output buffers for the same (column, kind) get a copy
+        for (int k = i; k < n_specs; k++) {
+            if (!spec_is_cascade(specs[k]) || specs[k].values != specs[i].values) continue;
+            if (k == first_sum || k == first_avg) continue;
+            const void *src = specs[specs[k].kind == PAC_SUM ? first_sum : first_avg].out;
+            PAC_CUDA(ctx, cudaMemcpyAsync(specs[k].out, src, static_cast<size_t>(in->n_groups) * kWorlds * 8,
+                                          cudaMemcpyDeviceToDevice, stream));
+        }
+    }
+    return PAC_OK;
+}
+
+pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                          uint64_t *meta, cudaStream_t stream) {
+    int launches = 0;
+    pac_status st;
+    ctx->last_launches = 0;
+    // The tensor-core path serves COUNT and exact int64 SUM/AVG.
+    const int want = static_cast<int>(ctx->opt_agg_path);
+    bool mma_ok = want != 1 && mma_supported(in, specs, n_specs);
+    if (want == 2 && !mma_ok) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path cannot serve this query");
+    if (mma_ok) {
+        st = run_mma(ctx, in, specs, n_specs, meta, stream, &launches);
+        if (st != PAC_OK) return st;
+        ctx->last_path = 2;
+    } else {
+        st = run_bitloop(ctx, in, specs, n_specs, meta, stream, &launches);
+        if (st != PAC_OK) return st;
+    }
+    st = run_cascades(ctx, in, specs, n_specs, stream, &launches);
+    if (st != PAC_OK) return st;
+    ctx->last_launches = launches;
+    return PAC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported entry points
+// ===========================================================================
+extern "C" {
+
+pac_status pac_create(pac_ctx **out, int device) {
+    if (!out) return PAC_E_INVALID;
+    *out = nullptr;
+    pac_ctx *ctx = new (std::nothrow) pac_ctx();
+    if (!ctx) return PAC_E_NOMEM;
+    ctx->device = device;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device < 0 || device >= count) {
+        delete ctx;
+        cudaGetLastError();
+        return e != cudaSuccess ? PAC_E_CUDA : PAC_E_INVALID;
+    }
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        delete ctx;
+        return PAC_E_CUDA;
+    }
+    *out = ctx;
+    return PAC_OK;
+}
+
+void pac_destroy(pac_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->qws) cudaFree(ctx->qws);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+const char *pac_last_error(const pac_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+const char *pac_status_string(pac_status s) {
+    switch (s) {
+    case PAC_OK: return "PAC_OK";
+    case PAC_E_INVALID: return "PAC_E_INVALID";
+    case PAC_E_NOMEM: return "PAC_E_NOMEM";
+    case PAC_E_CUDA: return "PAC_E_CUDA";
+    case PAC_E_OVERFLOW: return "PAC_E_OVERFLOW";
+    case PAC_E_TIMEOUT: return "PAC_E_TIMEOUT";
+    case PAC_E_UNSUPPORTED: return "PAC_E_UNSUPPORTED";
+    }
+    return "unknown";
+}
+
+pac_status pac_sync_status(pac_ctx *ctx, pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    pac_status st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    uint32_t h = 0;
+    PAC_CUDA(ctx, cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    PAC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), stream));
+    PAC_CUDA(ctx, cudaStreamSynchronize(stream));
+    if (h & kStatusTimeout) return fail(ctx, PAC_E_TIMEOUT, "a bounded device wait gave up");
+    if (h & kStatusOverflow) return fail(ctx, PAC_E_OVERFLOW, "a result did not fit its output type");
+    return PAC_OK;
+}
+
+uint64_t pac_query_key(uint64_t seed) {
+    return splitmix_mix((seed ^ 0x5041435f4b455921ull) + kGolden);
+}
+
+pac_status pac_hash_keys(pac_ctx *ctx, const int64_t *keys, uint64_t *masks, size_t n, uint64_t query_key,
+                         int32_t hash_mode, pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    if (n > 0 && (!keys || !masks)) return fail(ctx, PAC_E_INVALID, "keys/masks is NULL");
+    if (hash_mode != PAC_HASH_BALANCED && hash_mode != PAC_HASH_RAW)
+        return fail(ctx, PAC_E_INVALID, "hash_mode %d", hash_mode);
+    pac_status st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    PAC_CUDA(ctx, launch_hash(keys, masks, n, query_key, hash_mode, ctx->n_sms, stream));
+    ctx->last_launches = n ? 1 : 0;
+    return PAC_OK;
+}
+
+pac_status pac_aggregate_multi(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                               uint64_t *meta, pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    pac_status st = check_input(ctx, in);
+    if (st != PAC_OK) return st;
+    st = check_specs(ctx, in, specs, n_specs);
+    if (st != PAC_OK) return st;
+    if (n_specs == 0 && !meta) return fail(ctx, PAC_E_INVALID, "nothing to compute");
+    st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    return aggregate_impl(ctx, in, specs, n_specs, meta, stream);
+}
+
+pac_status pac_aggregate(pac_ctx *ctx, const void *keys_or_masks, uint32_t in_flags, uint64_t query_key,
+                         int32_t hash_mode, const void *values, int32_t vtype, const void *group_ids,
+                         int32_t gid_bytes, size_t n, uint32_t n_groups, int32_t kind, int32_t variant, void *out,
+                         uint64_t *meta, pac_stream stream) {
+    pac_input in;
+    in.keys_or_masks = keys_or_masks;
+    in.in_flags = in_flags;
+    in.hash_mode = hash_mode;
+    in.query_key = query_key;
+    in.group_ids = group_ids;
+    in.gid_bytes = gid_bytes;
+    in.n_groups = n_groups;
+    in.n = n;
+    pac_agg_spec s;
+    s.kind = kind;
+    s.variant = variant;
+    s.vtype = kind == PAC_COUNT ? PAC_I64 : vtype;
+    s.reserved = 0;
+    s.values = values;
+    s.out = out;
+    return pac_aggregate_multi(ctx, &in, &s, 1, meta, stream);
+}
+
+pac_status pac_finalize(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs, uint32_t n_groups,
+                        const uint64_t *meta, uint64_t seed, double budget, int32_t mode, double *noised,
+                        uint8_t *is_null, uint32_t *flags, double *posterior, pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    if (n_specs < 1 || n_specs > PAC_MAX_SPECS || !specs) return fail(ctx, PAC_E_INVALID, "n_specs %d", n_specs);
+    if (n_groups < 1) return fail(ctx, PAC_E_INVALID, "n_groups must be >= 1");
+    if (!meta || !noised || !is_null || !flags) return fail(ctx, PAC_E_INVALID, "NULL output or meta");
+    if (!(budget > 0.0)) return fail(ctx, PAC_E_INVALID, "budget must be > 0");
+    if (mode != PAC_FIN_ADAPTIVE && mode != PAC_FIN_INDEPENDENT) return fail(ctx, PAC_E_INVALID, "mode %d", mode);
+    FinParams p{};
+    for (int i = 0; i < n_specs; i++) {
+        if (specs[i].kind < PAC_COUNT || specs[i].kind > PAC_MAX || !specs[i].out)
+            return fail(ctx, PAC_E_INVALID, "spec %d", i);
+        p.spec[i].kind = specs[i].kind;
+        p.spec[i].vtype = specs[i].kind == PAC_COUNT ? PAC_I64 : specs[i].vtype;
+        p.spec[i].variant = specs[i].variant;
+        p.spec[i].out = specs[i].out;
+    }
+    p.n_specs = n_specs;
+    p.n_groups = n_groups;
+    p.meta = meta;
+    p.seed = seed;
+    p.budget = budget;
+    p.mode = mode;
+    p.noised = noised;
+    p.is_null = is_null;
+    p.flags = flags;
+    p.posterior = posterior;
+    pac_status st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    PAC_CUDA(ctx, launch_finalize(p, stream));
+    ctx->last_launches = 1;
+    return PAC_OK;
+}
+
+pac_status pac_query_host(pac_ctx *ctx, const pac_input *in_h, const pac_agg_spec *specs_h, int32_t n_specs,
+                          uint64_t seed, double budget, int32_t mode, double *noised, uint8_t *is_null,
+                          uint32_t *flags, pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    pac_status st = check_input(ctx, in_h);
+    if (st != PAC_OK) return st;
+    if (n_specs < 1 || n_specs > PAC_MAX_SPECS || !specs_h) return fail(ctx, PAC_E_INVALID, "n_specs %d", n_specs);
+    if (!noised || !is_null || !flags) return fail(ctx, PAC_E_INVALID, "NULL host output");
+    st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    const size_t n = in_h->n;
+    const uint32_t G = in_h->n_groups;
+    const size_t n_cells = static_cast<size_t>(G) * n_specs;
+    const size_t gbytes = in_h->group_ids ? n * in_h->gid_bytes : 0;
+    // staging layout: keys | gids | value columns | outs | meta | released cells
+    size_t need = align_up(n * 8, 256) + align_up(gbytes, 256) + 4096;
+    for (int i = 0; i < n_specs; i++) {
+        if (specs_h[i].kind != PAC_COUNT) need += align_up(n * (specs_h[i].vtype == PAC_F32 ? 4 : 8), 256);
+        need += align_up(static_cast<size_t>(G) * kWorlds * 8, 256);
+    }
+    need += align_up(static_cast<size_t>(G) * 16, 256) + 3 * align_up(n_cells * 8, 256);
+    st = ensure_buffer(ctx, &ctx->qws, &ctx->qws_bytes, need);
+    if (st != PAC_OK) return st;
+    Carver cv(ctx->qws);
+    pac_input in = *in_h;
+    void *d_keys = cv.take(n * 8);
+    if (n) PAC_CUDA(ctx, cudaMemcpyAsync(d_keys, in_h->keys_or_masks, n * 8, cudaMemcpyHostToDevice, stream));
+    in.keys_or_masks = d_keys;
+    if (in_h->group_ids) {
+        void *d_g = cv.take(gbytes);
+        if (n) PAC_CUDA(ctx, cudaMemcpyAsync(d_g, in_h->group_ids, gbytes, cudaMemcpyHostToDevice, stream));
+        in.group_ids = d_g;
+    }
+    pac_agg_spec specs[PAC_MAX_SPECS];
+    for (int i = 0; i < n_specs; i++) {
+        specs[i] = specs_h[i];
+        if (specs[i].kind != PAC_COUNT) {
+            const size_t vb = n * (specs[i].vtype == PAC_F32 ? 4 : 8);
+            // a column shared by several specs is copied once
+            const void *dv = nullptr;
+            for (int k = 0; k < i; k++)
+                if (specs_h[k].kind != PAC_COUNT && specs_h[k].values == specs_h[i].values) dv = specs[k].values;
+            if (!dv) {
+                void *d = cv.take(vb);
+                if (n) PAC_CUDA(ctx, cudaMemcpyAsync(d, specs_h[i].values, vb, cudaMemcpyHostToDevice, stream));
+                dv = d;
+            }
+            specs[i].values = dv;
+        }
+        specs[i].out = cv.take(static_cast<size_t>(G) * kWorlds * 8);
+    }
+    uint64_t *d_meta = static_cast<uint64_t *>(cv.take(static_cast<size_t>(G) * 16));
+    double *d_noised = static_cast<double *>(cv.take(n_cells * 8));
+    uint8_t *d_null = static_cast<uint8_t *>(cv.take(n_cells));
+    uint32_t *d_flags = static_cast<uint32_t *>(cv.take(n_cells * 4));
+    st = pac_aggregate_multi(ctx, &in, specs, n_specs, d_meta, stream);
+    if (st != PAC_OK) return st;
+    const int64_t agg_launches = ctx->last_launches;
+    st = pac_finalize(ctx, specs, n_specs, G, d_meta, seed, budget, mode, d_noised, d_null, d_flags, nullptr, stream);
+    if (st != PAC_OK) return st;
+    ctx->last_launches += agg_launches;
+    PAC_CUDA(ctx, cudaMemcpyAsync(noised, d_noised, n_cells * 8, cudaMemcpyDeviceToHost, stream));
+    PAC_CUDA(ctx, cudaMemcpyAsync(is_null, d_null, n_cells, cudaMemcpyDeviceToHost, stream));
+    PAC_CUDA(ctx, cudaMemcpyAsync(flags, d_flags, n_cells * 4, cudaMemcpyDeviceToHost, stream));
+    return pac_sync_status(ctx, stream);
+}
+
+pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value) {
+    if (!ctx || !name) return PAC_E_INVALID;
+    if (strcmp(name, "agg_path") == 0) {
+        if (value < 0 || value > 2) return fail(ctx, PAC_E_INVALID, "agg_path %lld", static_cast<long long>(value));
+        ctx->opt_agg_path = value;
+        return PAC_OK;
+    }
+    return fail(ctx, PAC_E_INVALID, "unknown option %s", name);
+}
+
+pac_status pac_get_info(pac_ctx *ctx, const char *name, int64_t *value) {
+    if (!ctx || !name || !value) return PAC_E_INVALID;
+    if (strcmp(name, "last_path") == 0) {
+        *value = ctx->last_path;
+        return PAC_OK;
+    }
+    if (strcmp(name, "last_launches") == 0) {
+        *value = ctx->last_launches;
+        return PAC_OK;
+    }
+    return fail(ctx, PAC_E_INVALID, "unknown info %s", name);
+}
+
+}  // extern "C"

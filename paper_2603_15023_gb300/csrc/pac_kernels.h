@@ -1,0 +1,101 @@
+// pac_kernels.h -- launch parameters and launchers of the PAC kernels.
+#pragma once
+
+#include "pac_internal.cuh"
+
+namespace pacgpu {
+
+// Per-world state operations of the per-bit path.
+enum SlotOp : int32_t {
+    OP_ISUM = 0,       // exact int64 sum (wrapping partials, int128 merge)
+    OP_FSUM_COMP = 1,  // FP32 sum + compensation (two-sum), exact variant
+    OP_FSUM_PLAIN = 2, // FP32 state only (the paper's approximate float SUM)
+    OP_IMIN = 3,
+    OP_IMAX = 4,
+    OP_FMIN = 5,
+    OP_FMAX = 6,
+};
+
+struct SlotDev {
+    int32_t op, vtype;
+    const void *values;
+};
+
+struct OutDev {
+    int32_t kind, slot;  // slot: index into SlotDev[] (unused for COUNT)
+    void *out;
+};
+
+struct BitloopParams {
+    InputDev in;
+    int32_t n_slots, n_out;
+    SlotDev slot[kMaxSpecs];
+    OutDev outs[kMaxSpecs];
+    uint64_t rows_per_cta;
+    void *partials;         // lowcard: [ctas][1+n_slots][G][64]; atomic: [1+n_slots][G][64]
+    uint64_t *ng_partials;  // lowcard: [ctas][G]; atomic: [G]
+    uint64_t *meta;         // [G][2] or nullptr
+    uint32_t *status;
+};
+
+int bitloop_pick_ns(int n_slots);
+size_t bitloop_smem_bytes(int n_warps, int n_slots, uint32_t G, int ns);
+cudaError_t launch_bitloop_lowcard(const BitloopParams &p, int n_ctas, int n_warps, cudaStream_t s);
+cudaError_t launch_bitloop_atomic(const BitloopParams &p, int n_ctas, cudaStream_t s);
+cudaError_t launch_bitloop_merge(const BitloopParams &p, int n_parts, bool atomic, cudaStream_t s);
+
+// ---- hash --------------------------------------------------------------
+cudaError_t launch_hash(const int64_t *keys, uint64_t *masks, size_t n, uint64_t qkey, int mode,
+                        int n_sms, cudaStream_t s);
+
+// ---- approximate integer SUM / AVG (Sec. 5 "Approximation") -------------
+constexpr int kApxLevels = 25;
+constexpr int kApxChunk = 4096;
+// One (chunk-block, group) state: per side 25 levels x 32 packed words
+// (world l in the low 16 bits, world l+32 in the high 16 bits) and 25
+// level totals.
+struct ApxSide {
+    uint32_t w[kApxLevels][32];
+    uint32_t t[kApxLevels];
+};
+struct ApxState {
+    ApxSide side[2];
+};
+
+struct ApxParams {
+    InputDev in;
+    const int64_t *values;
+    ApxState *states;   // [n_blocks][G]
+    uint64_t *ng;       // [G] row counts (zeroed by the launcher)
+    uint32_t *status;
+    uint64_t n_chunks;
+    uint32_t chunks_per_block;
+};
+
+int apx_max_groups();
+size_t apx_scratch_bytes(uint64_t n, uint32_t G);
+// Fills out ([G][64] int64 for SUM, double for AVG).
+cudaError_t launch_approx(const ApxParams &p, void *out_sum, void *out_avg, cudaStream_t s,
+                          int *launches);
+
+// ---- finalize -------------------------------------------------------------
+struct FinSpec {
+    int32_t kind, vtype, variant, pad;
+    const void *out;
+};
+struct FinParams {
+    FinSpec spec[kMaxSpecs];
+    int32_t n_specs;
+    uint32_t n_groups;
+    const uint64_t *meta;
+    uint64_t seed;
+    double budget;
+    int32_t mode;
+    double *noised;
+    uint8_t *is_null;
+    uint32_t *flags;
+    double *posterior;
+};
+cudaError_t launch_finalize(const FinParams &p, cudaStream_t s);
+
+}  // namespace pacgpu

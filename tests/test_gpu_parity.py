@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars: masks, counts, integer sums, MIN/MAX, the approximate integer cascade
+and the NULL/j*/flag decisions bit-exact; exact float sums within 1e-6 of the
+FP64 oracle relative to the world's sum of |v|; the paper's FLOAT-state SUM
+within the FP32 bound gamma_n * sum|v|; noised releases within 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2603_15023_gb300 import binding as B
+from paper_2603_15023_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+KINDS = [B.PAC_COUNT, B.PAC_SUM, B.PAC_AVG, B.PAC_MIN, B.PAC_MAX]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from pac_gpu_util import Ctx
+    c = Ctx(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("mode", [B.PAC_HASH_BALANCED, B.PAC_HASH_RAW])
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 4095, 100_003])
+def test_hash_keys_bit_exact(ctx, mode, n):
+    keys = inputs.uniform_i64(n, 0, n, -(2**62), 2**62)
+    qk = B.pac_query_key(n)
+    assert qk == orc.query_key(n)
+    got = ctx.hash_keys(keys, qk, mode)
+    np.testing.assert_array_equal(got, orc.hash_keys(keys, qk, mode))
+    if n:
+        np.testing.assert_array_equal(ctx.hash_keys(keys, qk, mode, inplace=True), got)
+
+
+def _oracle_all(masks, gids, G, kind, vals):
+    out, mn, mo, st = orc.aggregate(masks, vals, gids, G, kind)
+    return out, mn, mo, st
+
+
+def _check_exact(got, ref, kind, vals, masks, gids, G):
+    if vals is not None and vals.dtype != np.int64 and kind in (B.PAC_SUM, B.PAC_AVG):
+        absw, *_ = orc.aggregate(masks, np.abs(vals).astype(np.float64), gids, G, B.PAC_SUM)
+        if kind == B.PAC_AVG:
+            cnt, *_ = orc.aggregate(masks, None, gids, G, B.PAC_COUNT)
+            absw = absw / np.maximum(cnt.astype(np.float64), 1)
+        err = np.abs(got - ref)
+        assert np.all(err <= 1e-6 * absw + 1e-300), float(np.max(err / np.maximum(absw, 1e-300)))
+    else:
+        np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("G,gdt", [(1, None), (3, np.uint8), (17, np.uint16), (5000, np.int32)])
+@pytest.mark.parametrize("vdtype", [np.int64, np.float32, np.float64])
+@pytest.mark.parametrize("n", [0, 1, 33, 10_000, 250_007])
+def test_exact_aggregates(ctx, G, gdt, vdtype, n):
+    w = inputs.small(n + G, n, G, max(n // 7, 1), vdtype=vdtype, vlo=-10**6, vhi=10**6)
+    gids = None if G == 1 else w.gids.astype(gdt)
+    qk = orc.query_key(n)
+    masks = orc.hash_keys(w.keys, qk, orc.BALANCED)
+    specs = [(k, B.PAC_EXACT, None if k == B.PAC_COUNT else w.values[0]) for k in KINDS]
+    got, meta, st = ctx.aggregate(w.keys, gids, G, specs, qkey=qk)
+    assert st == B.PAC_OK
+    for (kind, _, vals), g_out in zip(specs, got):
+        ref, mn, mo, rst = _oracle_all(masks, gids, G, kind, vals)
+        assert rst == 0
+        _check_exact(g_out, ref, kind, vals, masks, gids, G)
+    np.testing.assert_array_equal(meta[:, 0], mn)
+    np.testing.assert_array_equal(meta[:, 1], mo)
+
+
+@pytest.mark.parametrize("in_flags", [B.PAC_IN_KEYS, B.PAC_IN_MASKS])
+@pytest.mark.parametrize("hash_mode", [B.PAC_HASH_BALANCED, B.PAC_HASH_RAW])
+def test_masks_input_and_raw_hash(ctx, in_flags, hash_mode):
+    w = inputs.small(5, 70_001, 4, 9000, vlo=-(2**40), vhi=2**40)
+    qk = orc.query_key(77)
+    masks = orc.hash_keys(w.keys, qk, hash_mode)
+    first = masks if in_flags == B.PAC_IN_MASKS else w.keys
+    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, w.values[0]), (B.PAC_MAX, 0, w.values[0])]
+    got, meta, st = ctx.aggregate(first, w.gids.astype(np.uint8), 4, specs, in_flags=in_flags,
+                                  hash_mode=hash_mode, qkey=qk)
+    assert st == B.PAC_OK
+    for (kind, _, vals), g_out in zip(specs, got):
+        ref, *_ = orc.aggregate(masks, vals, w.gids.astype(np.uint8), 4, kind)
+        np.testing.assert_array_equal(g_out, ref)
+
+
+@pytest.mark.parametrize("G", [1, 4, 32])
+@pytest.mark.parametrize("n", [0, 5, 4096, 4097, 100_000, 1_000_003])
+def test_approx_int_cascade_bit_exact(ctx, G, n):
+    w = inputs.small(n * 3 + G, n, G, max(n // 5, 1), vlo=-(10**9), vhi=10**9)
+    gids = None if G == 1 else w.gids.astype(np.uint8)
+    qk = orc.query_key(3)
+    masks = orc.hash_keys(w.keys, qk, orc.BALANCED)
+    specs = [(B.PAC_SUM, B.PAC_APPROX, w.values[0]), (B.PAC_AVG, B.PAC_APPROX, w.values[0])]
+    got, meta, st = ctx.aggregate(w.keys, gids, G, specs, qkey=qk)
+    assert st == B.PAC_OK
+    rs, s1 = orc.approx_sum_i64(masks, w.values[0], gids, G)
+    ra, s2 = orc.approx_avg_i64(masks, w.values[0], gids, G)
+    np.testing.assert_array_equal(got[0], rs)
+    np.testing.assert_array_equal(got[1], ra)
+
+
+def test_approx_cascade_many_flushes(ctx):
+    # large positive values in few groups: deep cascades inside chunks and in the tree
+    n = 600_000
+    r = np.random.default_rng(9)
+    vals = r.integers(2**40, 2**41, n).astype(np.int64)
+    keys = r.integers(0, 50, n).astype(np.int64)
+    gids = r.integers(0, 2, n).astype(np.uint8)
+    qk = orc.query_key(9)
+    masks = orc.hash_keys(keys, qk, orc.RAW)
+    got, _, st = ctx.aggregate(keys, gids, 2, [(B.PAC_SUM, B.PAC_APPROX, vals)], qkey=qk,
+                               hash_mode=B.PAC_HASH_RAW)
+    ref, _ = orc.approx_sum_i64(masks, vals, gids, 2)
+    assert st == B.PAC_OK
+    np.testing.assert_array_equal(got[0], ref)
+
+
+@pytest.mark.parametrize("vdtype", [np.float32, np.float64])
+def test_approx_float_state_bound(ctx, vdtype):
+    n = 300_000
+    r = np.random.default_rng(4)
+    vals = r.lognormal(0, 1.5, n).astype(vdtype)
+    keys = r.integers(0, 30000, n).astype(np.int64)
+    gids = r.integers(0, 3, n).astype(np.uint8)
+    qk = orc.query_key(4)
+    masks = orc.hash_keys(keys, qk, orc.BALANCED)
+    got, _, st = ctx.aggregate(keys, gids, 3, [(B.PAC_SUM, B.PAC_APPROX, vals)], qkey=qk)
+    ref, *_ = orc.aggregate(masks, vals, gids, 3, B.PAC_SUM)
+    absw, *_ = orc.aggregate(masks, np.abs(vals).astype(np.float64), gids, 3, B.PAC_SUM)
+    u = 2.0**-24
+    gam = (n + 1) * u / (1 - (n + 1) * u)
+    assert st == B.PAC_OK
+    assert np.all(np.abs(got[0] - ref) <= gam * absw)
+
+
+def test_int64_sum_overflow_reported(ctx):
+    n = 64
+    vals = np.full(n, 2**62, dtype=np.int64)
+    keys = np.arange(n, dtype=np.int64)
+    got, _, st = ctx.aggregate(keys, None, 1, [(B.PAC_SUM, B.PAC_EXACT, vals)], qkey=1)
+    assert st == B.PAC_E_OVERFLOW
+
+
+def test_argument_errors(ctx):
+    import ctypes
+    inp = B.make_input(0, 10, n_groups=1)
+    sp = B.make_specs([(B.PAC_COUNT, 0, B.PAC_I64, 0, 1234)])
+    with pytest.raises(B.PacError) as e:
+        B.pac_aggregate_multi(ctx.h, inp, sp, 1, 0)
+    assert e.value.status == B.PAC_E_INVALID
+    inp = B.make_input(1234, 10, n_groups=3)  # ungrouped with 3 groups
+    with pytest.raises(B.PacError):
+        B.pac_aggregate_multi(ctx.h, inp, sp, 1, 0)
+    bad = B.make_specs([(9, 0, B.PAC_I64, 0, 1234)])
+    with pytest.raises(B.PacError):
+        B.pac_aggregate_multi(ctx.h, B.make_input(1234, 10), bad, 1, 0)
+    with pytest.raises(B.PacError):
+        B.pac_set_option(ctx.h, "agg_path", 7)
+    assert ctypes.c_int(B.lib().pac_hash_keys(ctx.h, None, None, 5, 0, 0, None)).value == B.PAC_E_INVALID
+
+
+@pytest.mark.parametrize("mode", [B.PAC_FIN_ADAPTIVE, B.PAC_FIN_INDEPENDENT])
+@pytest.mark.parametrize("G", [1, 7, 300])
+def test_finalize_matches_oracle(ctx, mode, G):
+    r = np.random.default_rng(G)
+    kv = [(B.PAC_COUNT, 0, B.PAC_I64), (B.PAC_SUM, 0, B.PAC_I64), (B.PAC_AVG, 0, B.PAC_I64),
+          (B.PAC_SUM, 0, B.PAC_F64), (B.PAC_MIN, 0, B.PAC_I64)]
+    outs = [r.integers(0, 5000, (G, 64)).astype(np.uint64),
+            r.integers(-10**9, 10**9, (G, 64)).astype(np.int64),
+            r.normal(50, 9, (G, 64)),
+            r.lognormal(3, 1, (G, 64)),
+            r.integers(-100, 100, (G, 64)).astype(np.int64)]
+    meta = np.zeros((G, 2), dtype=np.uint64)
+    meta[:, 0] = r.integers(0, 200, G)
+    meta[:, 1] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    meta[::3, 1] = np.uint64(0x0000FFFF0000FFFF)       # sparse groups: NULL draws
+    meta[::5, 1] = np.uint64(0x00000000FFFFFFFF)       # single PU: diversity flag
+    outs[0][2 % G, :] = 5                              # one constant cell (zero variance)
+    seed, budget = 1234 + G, 1.0 / 128
+    got = ctx.finalize(outs, kv, meta, seed, budget, mode)
+    y = np.stack([o.astype(np.float64) for o in outs], axis=1)   # [G, S, 64]
+    scales = [orc.release_scale(k) for k, _, _ in kv]
+    ref = orc.finalize(y, scales, meta[:, 0], meta[:, 1], seed, budget, mode)
+    np.testing.assert_array_equal(got["is_null"], ref["is_null"])
+    np.testing.assert_array_equal(got["flags"], ref["flags"])
+    live = ref["is_null"] == 0
+    np.testing.assert_allclose(got["noised"][live], ref["noised"][live], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(got["posterior"], ref["posterior"], rtol=1e-6, atol=1e-12)
+
+
+def test_lowcard_60m_full_size_sampled(ctx):
+    """The 60M-row, 4-group, 4-column workload at full size, in the launch
+    configuration the benchmark times: sampled worlds against the oracle,
+    every world against the balanced invariants."""
+    w = inputs.lowcard_60m(seed=0)
+    qk = orc.query_key(0)
+    specs = [(B.PAC_COUNT, 0, None)] + [(B.PAC_SUM, 0, v) for v in w.values] + \
+            [(B.PAC_AVG, 0, v) for v in w.values]
+    got, meta, st = ctx.aggregate(w.keys, w.gids, 4, specs, qkey=qk)
+    assert st == B.PAC_OK
+    masks = orc.hash_keys(w.keys, qk, orc.BALANCED)
+    for j in (0, 21, 42, 63):
+        c, _ = orc.aggregate_world(masks, None, w.gids, 4, B.PAC_COUNT, j)
+        np.testing.assert_array_equal(got[0][:, j], c)
+        for k, v in enumerate(w.values):
+            s, _ = orc.aggregate_world(masks, v, w.gids, 4, B.PAC_SUM, j)
+            np.testing.assert_array_equal(got[1 + k][:, j], s)
+            a, _ = orc.aggregate_world(masks, v, w.gids, 4, B.PAC_AVG, j)
+            np.testing.assert_array_equal(got[5 + k][:, j], a)
+    ng = np.bincount(w.gids, minlength=4).astype(np.uint64)
+    cnt = got[0].astype(np.int64)
+    np.testing.assert_array_equal(meta[:, 0], ng)
+    assert np.all(cnt[:, :32] + cnt[:, 32:] == ng.astype(np.int64)[:, None])
+    for k, v in enumerate(w.values):
+        tot = np.array([v[w.gids == g].sum() for g in range(4)])
+        assert np.all(got[1 + k][:, :32] + got[1 + k][:, 32:] == tot[:, None])

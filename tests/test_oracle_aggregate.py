@@ -157,3 +157,16 @@ def test_sum_overflow_is_reported(orc):
     masks = np.full(8, np.uint64(1))
     s, _, _, st = orc.aggregate(masks, v, None, 1, orc.SUM)
     assert st == 4 and s[0, 0] == np.iinfo(np.int64).max
+
+
+def test_single_world_matches_all_worlds(orc):
+    w = inputs.small(9, 30000, 4, 2000, vlo=-10**6, vhi=10**6)
+    masks = orc.hash_keys(w.keys, orc.query_key(9), orc.RAW)
+    for kname in KINDS:
+        kind = _kind(orc, kname)
+        v = None if kind == orc.COUNT else w.values[0]
+        full, *_ = orc.aggregate(masks, v, w.gids, 4, kind)
+        for j in (0, 31, 32, 63):
+            one, st = orc.aggregate_world(masks, v, w.gids, 4, kind, j)
+            assert st == 0
+            np.testing.assert_array_equal(one, full[:, j])
