@@ -100,7 +100,8 @@ const char *pac_last_error(const pac_ctx *ctx);
 const char *pac_status_string(pac_status s);
 
 /* Synchronises `stream`, returns (and clears) the device status word:
- * PAC_OK, PAC_E_OVERFLOW or PAC_E_TIMEOUT. */
+ * PAC_OK, PAC_E_OVERFLOW, PAC_E_TIMEOUT, or PAC_E_INVALID when a group id
+ * was >= n_groups (such rows are skipped, never written out of bounds). */
 pac_status pac_sync_status(pac_ctx *ctx, pac_stream stream);
 
 /* Host-only: the per-query hash key K (Sec. 4.2: drawn independently per
@@ -126,7 +127,8 @@ pac_status pac_hash_keys(pac_ctx *ctx, const int64_t *keys, uint64_t *masks, siz
  * Shared input of one query:
  *   keys_or_masks [n] int64 keys (PAC_IN_KEYS) or uint64 masks (PAC_IN_MASKS)
  *   group_ids     [n] unsigned group id of width gid_bytes (1, 2 or 4), each
- *                 < n_groups; NULL means ungrouped (n_groups must be 1)
+ *                 < n_groups; NULL means ungrouped (n_groups must be 1 unless
+ *                 n = 0)
  *   n             rows (0 allowed: every output is zero)
  *   n_groups      >= 1
  * One aggregate per spec:

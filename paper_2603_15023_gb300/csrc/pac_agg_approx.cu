@@ -130,6 +130,7 @@ __global__ void k_apx_chunks(const __grid_constant__ ApxParams p) {
             uint64_t mask = 0;
             if (valid) {
                 gid = row_gid(p.in, row);
+                if (gid >= G && g == 0) raise_status(p.status, kStatusBadGroup);
                 if (gid == g) {
                     v = row_i64(p.values, row);
                     mask = row_mask(p.in, row);

@@ -149,12 +149,18 @@ __global__ void __launch_bounds__(256) k_bitloop_lowcard(const __grid_constant__
     for (uint64_t base = begin + static_cast<uint64_t>(warp) * 32; base < end;
          base += static_cast<uint64_t>(n_warps) * 32) {
         const uint64_t row = base + lane;
-        const bool valid = row < end;
+        bool valid = row < end;
         uint64_t mask = 0, vals[NS];
         uint32_t gid = 0;
         if (valid) {
-            mask = row_mask(p.in, row);
             gid = row_gid(p.in, row);
+            if (gid >= G) {  // out-of-range group id: skip the row, report it
+                raise_status(p.status, kStatusBadGroup);
+                valid = false;
+                gid = 0;
+            } else {
+                mask = row_mask(p.in, row);
+            }
         }
 #pragma unroll
         for (int s = 0; s < NS; s++) {
@@ -307,13 +313,19 @@ __global__ void __launch_bounds__(256) k_bitloop_atomic(const __grid_constant__ 
     unsigned long long my_max = 0;
     for (uint64_t base = warp_global * 32; base < p.in.n; base += n_warps_total * 32) {
         const uint64_t row = base + lane;
-        const bool valid = row < p.in.n;
+        bool valid = row < p.in.n;
         uint64_t mask = 0;
         uint32_t gid = 0;
         uint64_t vals[kMaxSpecs];
         if (valid) {
-            mask = row_mask(p.in, row);
             gid = row_gid(p.in, row);
+            if (gid >= G) {  // out-of-range group id: skip the row, report it
+                raise_status(p.status, kStatusBadGroup);
+                valid = false;
+                gid = 0;
+            } else {
+                mask = row_mask(p.in, row);
+            }
         }
         for (int s = 0; s < p.n_slots; s++) {
             vals[s] = valid ? load_slot_value(p.slot[s], row) : 0ull;

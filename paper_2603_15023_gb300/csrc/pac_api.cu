@@ -43,7 +43,7 @@ pac_status check_input(pac_ctx *ctx, const pac_input *in) {
     if (in->hash_mode != PAC_HASH_BALANCED && in->hash_mode != PAC_HASH_RAW)
         return fail(ctx, PAC_E_INVALID, "hash_mode %d", in->hash_mode);
     if (in->n_groups == 0) return fail(ctx, PAC_E_INVALID, "n_groups must be >= 1");
-    if (!in->group_ids && in->n_groups != 1)
+    if (!in->group_ids && in->n_groups != 1 && in->n > 0)
         return fail(ctx, PAC_E_INVALID, "ungrouped input needs n_groups == 1");
     if (in->group_ids && in->gid_bytes != 1 && in->gid_bytes != 2 && in->gid_bytes != 4)
         return fail(ctx, PAC_E_INVALID, "gid_bytes %d", in->gid_bytes);
@@ -287,6 +287,7 @@ pac_status pac_sync_status(pac_ctx *ctx, pac_stream stream) {
     PAC_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), stream));
     PAC_CUDA(ctx, cudaStreamSynchronize(stream));
     if (h & kStatusTimeout) return fail(ctx, PAC_E_TIMEOUT, "a bounded device wait gave up");
+    if (h & kStatusBadGroup) return fail(ctx, PAC_E_INVALID, "a group id was >= n_groups (rows skipped)");
     if (h & kStatusOverflow) return fail(ctx, PAC_E_OVERFLOW, "a result did not fit its output type");
     return PAC_OK;
 }

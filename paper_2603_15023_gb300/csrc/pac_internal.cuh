@@ -15,6 +15,7 @@ namespace pacgpu {
 // Device status word bits (read back by pac_sync_status).
 constexpr uint32_t kStatusOverflow = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
+constexpr uint32_t kStatusBadGroup = 4u;  // a row's group id was >= n_groups (row skipped)
 
 constexpr int kWorlds = 64;   // m = 64 possible worlds (Sec. 2 "SIMD-PAC-DB")
 constexpr int kMaxSpecs = PAC_MAX_SPECS;

@@ -1,13 +1,619 @@
-// pac_mma.cu -- the tensor-core (tcgen05) aggregation path.
+// pac_mma.cu -- tensor-core (tcgen05) stochastic COUNT and exact int64
+// SUM/AVG (Sec. 4.2 "PAC Aggregation").
+//
+// For one group g the 64 world sums of a value column are a contraction over
+// rows:  S[j] = sum_i v_i * bit_j(mask_i).  Splitting every value into 4-bit
+// digits, S[j] = sum_q 16^q * sum_i d_q(v_i) * bit_j(mask_i), so the per-group
+// state is the small matrix product  D_g = Bits_g^T * Digits_g  (64 worlds x
+// features) accumulated on the tensor cores:
+//   A operand  (M = 64 worlds x K rows): bit j of row i as an E4M3 byte,
+//              0x00 or 0x01;
+//   B operand  (N features x K rows): a constant 1 (COUNT) and the digits of
+//              each value column as E4M3 bytes 0x00..0x0F;
+//   D          FP32 in tensor memory.
+// E4M3 bytes 0..15 encode exactly n * 2^-9 (subnormal and first binade share
+// the scale), so every product is an integer times 2^-18 and the FP32
+// accumulation stays exact while a column's digit total is below 2^24: a CTA
+// handles at most 2^20 rows.  Digit totals are recombined with exact 128-bit
+// integer arithmetic, so SUM is bit-exact and overflow is detected exactly.
+//
+// A value column's digits are chosen per 512-row tile: L = the number of
+// digits the tile's largest magnitude needs (rounded up to 2, 4, 6, 8, 12
+// or 16).  Tiles without negative values use unsigned digits; tiles with
+// negatives use two's-complement digits whose top digit is signed (-8..7,
+// sign-magnitude E4M3).  Features are ordered digit-major, so a tile with
+// fewer digits touches a prefix of the accumulator columns.
+//
+// Rows of a tile are sorted by group in shared memory (each group's run is
+// padded with zero rows to the 32-row MMA step) and each group's run is
+// multiplied into its own accumulator.  Operands use the MN-major,
+// no-swizzle canonical layout: a 128-byte core matrix is 8 rows (K) x 16
+// bytes (M or N); LBO is the stride between 8-row blocks, SBO = 128 the
+// stride between 16-byte column blocks.
+#include <climits>
+
+#include "pac_internal.cuh"
+#include "pac_kernels.h"
 #include "pac_mma.h"
 
 namespace pacgpu {
 
-bool mma_supported(const pac_input *, const pac_agg_spec *, int) { return false; }
+namespace {
 
-pac_status run_mma(pac_ctx *ctx, const pac_input *, const pac_agg_spec *, int, uint64_t *, cudaStream_t,
-                   int *) {
-    return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path not built");
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = 256;
+constexpr int kRowsPerThread = 2;
+constexpr int kTileRows = kThreads * kRowsPerThread;  // 512
+constexpr int kStages = 2;
+constexpr int kMmaK = 32;               // rows per tcgen05.mma of 8-bit operands
+constexpr int kMaxGroups = 8;
+constexpr int kMaxCols = 4;
+constexpr uint32_t kMaxRowsPerCta = 1u << 20;  // keeps FP32 digit totals below 2^24
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+// Accumulator / feature columns per group for C value columns.
+__host__ __device__ constexpr int feat_alloc(int C) { return C == 1 ? 32 : 80; }
+__host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
+
+struct MmaParams {
+    InputDev in;
+    const long long *col[kMaxCols];
+    int32_t n_cols;
+    int32_t n_alloc;
+    uint32_t rows_per_cta;
+    uint32_t k_cap;          // row slots per stage (multiple of 32)
+    uint32_t a_bytes;        // per stage
+    uint32_t b_bytes;        // per stage
+    unsigned long long *acc; // [G][64][n_alloc] int64 digit totals (zeroed)
+    unsigned long long *ng;  // [G] rows per group (zeroed)
+    uint32_t *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait on an mbarrier phase; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f8f6f4, A = B = E4M3, D = F32, A and B MN-major, M = 64.
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+    return (1u << 4) | (1u << 15) | (1u << 16) | (static_cast<uint32_t>(n >> 3) << 17) | (4u << 24);
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc));
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// 4 mask bits -> 4 bytes 0x00/0x01
+__device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
+
+// 16 bits -> 16 bytes of 0x00/0x01 (one 16-world column block of A)
+__device__ __forceinline__ void write_bits16(uint32_t addr, uint32_t x) {
+    sts128(addr, spread4(x & 0xF), spread4((x >> 4) & 0xF), spread4((x >> 8) & 0xF), spread4((x >> 12) & 0xF));
+}
+
+// Digit bytes of one row.  C4 = 1: one column, feature 4+q = digit q.
+// C4 = 4: up to four columns, feature 4 + 4q + c = digit q of column c.
+// Word 0 holds the COUNT feature (byte 1) and three zero pad features.
+template <int C4, int L>
+struct Features {
+    static constexpr int kN = round16(4 + L * C4);
+    static constexpr int kWords = kN / 4;
+    __device__ __forceinline__ static void build(const long long *v, bool sgn, uint32_t *w) {
+        w[0] = 1u;
+#pragma unroll
+        for (int k = 1; k < kWords; k++) w[k] = 0u;
+        if (C4 == 1) {
+            const unsigned long long u = static_cast<unsigned long long>(v[0]);
+#pragma unroll
+            for (int k = 0; k < (L + 3) / 4; k++) {
+                uint32_t x = static_cast<uint32_t>(u >> (16 * k)) & 0xFFFFu;
+                x = (x | (x << 8)) & 0x00FF00FFu;
+                x = (x | (x << 4)) & 0x0F0F0F0Fu;
+                w[1 + k] = x;
+            }
+            if (L % 4) w[1 + (L - 1) / 4] &= (1u << (8 * (L % 4))) - 1u;  // keep digits < L only
+            if (sgn) {
+                const long long d = v[0] >> (4 * (L - 1));
+                const uint32_t b = d < 0 ? (0x80u | static_cast<uint32_t>(-d)) : static_cast<uint32_t>(d);
+                const int wi = 1 + (L - 1) / 4, sh = 8 * ((L - 1) % 4);
+                w[wi] = (w[wi] & ~(0xFFu << sh)) | (b << sh);
+            }
+        } else {
+            // two digits per byte p of the 64-bit values
+#pragma unroll
+            for (int p = 0; p < L / 2; p++) {
+                const int h = p / 4, b = p % 4;
+                const uint32_t a0 = static_cast<uint32_t>(static_cast<unsigned long long>(v[0]) >> (32 * h));
+                const uint32_t a1 = static_cast<uint32_t>(static_cast<unsigned long long>(v[1]) >> (32 * h));
+                const uint32_t a2 = static_cast<uint32_t>(static_cast<unsigned long long>(v[2]) >> (32 * h));
+                const uint32_t a3 = static_cast<uint32_t>(static_cast<unsigned long long>(v[3]) >> (32 * h));
+                const uint32_t sel = static_cast<uint32_t>(b | ((4 + b) << 4));
+                const uint32_t t01 = __byte_perm(a0, a1, sel);
+                const uint32_t t23 = __byte_perm(a2, a3, sel);
+                const uint32_t word = __byte_perm(t01, t23, 0x5410);
+                w[1 + 2 * p] = word & 0x0F0F0F0Fu;
+                w[2 + 2 * p] = (word >> 4) & 0x0F0F0F0Fu;
+            }
+            if (sgn) {
+                uint32_t top = 0;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const long long d = v[c] >> (4 * (L - 1));
+                    const uint32_t b = d < 0 ? (0x80u | static_cast<uint32_t>(-d)) : static_cast<uint32_t>(d);
+                    top |= b << (8 * c);
+                }
+                w[L] = top;
+            }
+        }
+    }
+};
+
+template <int C4, int L>
+__device__ __forceinline__ void write_features(uint32_t b_stage, uint32_t slot, const long long *v, bool sgn) {
+    using F = Features<C4, L>;
+    uint32_t w[F::kWords];
+    F::build(v, sgn, w);
+    const uint32_t lbo = (F::kN / 16) * 128;
+    const uint32_t base = b_stage + (slot >> 3) * lbo + (slot & 7) * 16;
+#pragma unroll
+    for (int h = 0; h < F::kN / 16; h++) sts128(base + h * 128, w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3]);
+}
+
+template <int C4>
+__device__ __forceinline__ void write_features_l(int L, uint32_t b_stage, uint32_t slot, const long long *v, bool sgn) {
+    switch (L) {
+    case 2: write_features<C4, 2>(b_stage, slot, v, sgn); break;
+    case 4: write_features<C4, 4>(b_stage, slot, v, sgn); break;
+    case 6: write_features<C4, 6>(b_stage, slot, v, sgn); break;
+    case 8: write_features<C4, 8>(b_stage, slot, v, sgn); break;
+    case 12: write_features<C4, 12>(b_stage, slot, v, sgn); break;
+    default: write_features<C4, 16>(b_stage, slot, v, sgn); break;
+    }
+}
+
+__device__ __forceinline__ int digit_class(int need) {
+    if (need <= 2) return 2;
+    if (need <= 4) return 4;
+    if (need <= 6) return 6;
+    if (need <= 8) return 8;
+    if (need <= 12) return 12;
+    return 16;
+}
+
+template <int C4>
+__global__ void __launch_bounds__(kThreads, 1) k_agg_mma(const __grid_constant__ MmaParams p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mma_bar[kStages];
+    __shared__ uint32_t tmem_slot;
+    __shared__ uint32_t warp_cnt[kThreads / 32][kMaxGroups];
+    __shared__ uint32_t warp_bits[kThreads / 32];
+    __shared__ uint32_t warp_neg[kThreads / 32];
+    __shared__ uint32_t woff[kThreads / 32][kMaxGroups];
+    __shared__ uint32_t grp_lo[kMaxGroups], grp_cnt[kMaxGroups], grp_len[kMaxGroups];
+    __shared__ int tile_L, tile_N, tile_sgn;
+    __shared__ unsigned long long ng_acc[kMaxGroups];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t G = p.in.n_groups;
+    const int C = p.n_cols;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; s++) mbar_init(&mma_bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        abort_flag = 0;
+    }
+    if (tid < kMaxGroups) ng_acc[tid] = 0;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t used_cols = G * static_cast<uint32_t>(p.n_alloc);
+    // zero the accumulators (warps 0-3 own TMEM lane quadrants 0-3)
+    if (warp < 4) {
+        const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+        for (uint32_t c0 = 0; c0 < used_cols; c0 += 16) {
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+                    tmem + lane_base + c0),
+                "r"(0u));
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+    const uint64_t begin = static_cast<uint64_t>(blockIdx.x) * p.rows_per_cta;
+    const uint64_t end = min(p.in.n, begin + p.rows_per_cta);
+    const uint32_t n_tiles = static_cast<uint32_t>((end - begin + kTileRows - 1) / kTileRows);
+    const uint32_t smem_base = smem_u32(smem);
+    const bool balanced_keys = !(p.in.in_flags & PAC_IN_MASKS) && p.in.hash_mode == PAC_HASH_BALANCED;
+
+    for (uint32_t it = 0; it < n_tiles; it++) {
+        const int s = it % kStages;
+        const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
+        const uint32_t b_stage = a_stage + p.a_bytes;
+        const uint64_t row0 = begin + static_cast<uint64_t>(it) * kTileRows;
+
+        // (1) rows into registers
+        uint64_t mask[kRowsPerThread];
+        uint32_t gid[kRowsPerThread];
+        long long v[kRowsPerThread][4];
+        bool valid[kRowsPerThread];
+        uint32_t bits = 0, neg = 0;
+#pragma unroll
+        for (int r = 0; r < kRowsPerThread; r++) {
+            const uint64_t row = row0 + r * kThreads + tid;
+            valid[r] = row < end;
+            mask[r] = 0;
+            gid[r] = 0xFFFFFFFFu;
+#pragma unroll
+            for (int c = 0; c < 4; c++) v[r][c] = 0;
+            if (valid[r]) {
+                gid[r] = row_gid(p.in, row);
+                if (gid[r] >= G) {  // out-of-range group id: skip the row, report it
+                    raise_status(p.status, kStatusBadGroup);
+                    valid[r] = false;
+                    gid[r] = 0xFFFFFFFFu;
+                    continue;
+                }
+                mask[r] = row_mask(p.in, row);
+#pragma unroll
+                for (int c = 0; c < C4; c++) {
+                    if (c < C) {
+                        const long long x = __ldg(p.col[c] + row);
+                        v[r][c] = x;
+                        const unsigned long long m = x < 0 ? ~static_cast<unsigned long long>(x) : static_cast<unsigned long long>(x);
+                        const uint32_t bl = m ? 64u - __clzll(static_cast<long long>(m)) : 0u;
+                        bits = bl > bits ? bl : bits;
+                        neg |= x < 0 ? 1u : 0u;
+                    }
+                }
+            }
+        }
+        // (2) warp statistics: group counts, magnitude, signs
+        uint32_t b0[kMaxGroups], b1[kMaxGroups];
+#pragma unroll
+        for (int g = 0; g < kMaxGroups; g++) {
+            b0[g] = __ballot_sync(kFull, gid[0] == static_cast<uint32_t>(g));
+            b1[g] = __ballot_sync(kFull, gid[1] == static_cast<uint32_t>(g));
+        }
+        bits = __reduce_max_sync(kFull, bits);
+        neg = __reduce_or_sync(kFull, neg);
+        if (lane == 0) {
+#pragma unroll
+            for (int g = 0; g < kMaxGroups; g++) warp_cnt[warp][g] = __popc(b0[g]) + __popc(b1[g]);
+            warp_bits[warp] = bits;
+            warp_neg[warp] = neg;
+        }
+        // (3) the stage's previous MMAs must have finished reading it
+        if (tid == 0 && it >= kStages) {
+            if (!mbar_wait(&mma_bar[s], ((it / kStages) - 1) & 1)) abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        // (4) tile layout: group runs, digit count
+        if (warp == 0) {
+            uint32_t cnt = 0;
+            if (lane < static_cast<int>(G))
+                for (int w = 0; w < kThreads / 32; w++) cnt += warp_cnt[w][lane];
+            const uint32_t len = (cnt + kMmaK - 1) & ~static_cast<uint32_t>(kMmaK - 1);
+            uint32_t incl = len;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane < static_cast<int>(G)) {
+                const uint32_t lo = incl - len;
+                grp_lo[lane] = lo;
+                grp_cnt[lane] = cnt;
+                grp_len[lane] = len;
+                ng_acc[lane] += cnt;
+                uint32_t run = lo;
+                for (int w = 0; w < kThreads / 32; w++) {
+                    woff[w][lane] = run;
+                    run += warp_cnt[w][lane];
+                }
+            }
+            uint32_t mb = lane < kThreads / 32 ? warp_bits[lane] : 0u;
+            uint32_t ng = lane < kThreads / 32 ? warp_neg[lane] : 0u;
+            mb = __reduce_max_sync(kFull, mb);
+            ng = __reduce_or_sync(kFull, ng);
+            if (lane == 0) {
+                const int need = ng ? static_cast<int>((mb + 1 + 3) / 4) : static_cast<int>((mb + 3) / 4);
+                const int L = digit_class(need);
+                tile_L = L;
+                tile_sgn = ng ? 1 : 0;
+                tile_N = C4 == 1 ? round16(4 + L) : round16(4 + L * 4);
+            }
+        }
+        __syncthreads();
+        // (5) operands into the stage, rows sorted by group
+        const int L = tile_L;
+        const bool sgn = tile_sgn != 0;
+#pragma unroll
+        for (int r = 0; r < kRowsPerThread; r++) {
+            if (!valid[r]) continue;
+            uint32_t rank = 0, base = 0;
+#pragma unroll
+            for (int g = 0; g < kMaxGroups; g++) {
+                if (gid[r] == static_cast<uint32_t>(g)) {
+                    rank = r == 0 ? __popc(b0[g] & lt) : __popc(b0[g]) + __popc(b1[g] & lt);
+                    base = woff[warp][g];
+                }
+            }
+            const uint32_t slot = base + rank;
+            const uint32_t a_row = a_stage + (slot >> 3) * 512 + (slot & 7) * 16;
+            const uint32_t lo = static_cast<uint32_t>(mask[r]);
+            write_bits16(a_row, lo & 0xFFFFu);
+            write_bits16(a_row + 128, lo >> 16);
+            if (balanced_keys) {
+                // worlds 32..63 are the complement of worlds 0..31
+                const uint32_t hi = ~lo;
+                write_bits16(a_row + 256, hi & 0xFFFFu);
+                write_bits16(a_row + 384, hi >> 16);
+            } else {
+                const uint32_t hi = static_cast<uint32_t>(mask[r] >> 32);
+                write_bits16(a_row + 256, hi & 0xFFFFu);
+                write_bits16(a_row + 384, hi >> 16);
+            }
+            write_features_l<C4>(L, b_stage, slot, v[r], sgn);
+        }
+        // zero rows that pad each group's run to the MMA step (warp g: group g)
+        if (warp < static_cast<int>(G)) {
+            const uint32_t pad = grp_len[warp] - grp_cnt[warp];
+            if (static_cast<uint32_t>(lane) < pad) {
+                const uint32_t slot = grp_lo[warp] + grp_cnt[warp] + lane;
+                const uint32_t a_row = a_stage + (slot >> 3) * 512 + (slot & 7) * 16;
+                for (int h = 0; h < 4; h++) sts128(a_row + h * 128, 0, 0, 0, 0);
+                const int N = tile_N;
+                const uint32_t b_row = b_stage + (slot >> 3) * ((N / 16) * 128) + (slot & 7) * 16;
+                for (int h = 0; h < N / 16; h++) sts128(b_row + h * 128, 0, 0, 0, 0);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // (6) one thread issues the MMAs of the tile and commits them
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int N = tile_N;
+            const uint32_t idesc = instr_desc(N);
+            const uint32_t lbo_b = (N / 16) * 128;
+            for (uint32_t g = 0; g < G; g++) {
+                const uint32_t d = tmem + g * static_cast<uint32_t>(p.n_alloc);
+                for (uint32_t k0 = grp_lo[g]; k0 < grp_lo[g] + grp_len[g]; k0 += kMmaK) {
+                    const uint64_t da = smem_desc(a_stage + (k0 >> 3) * 512, 512, 128);
+                    const uint64_t db = smem_desc(b_stage + (k0 >> 3) * lbo_b, lbo_b, 128);
+                    mma_f8(d, da, db, idesc);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mma_bar[s])));
+        }
+    }
+    // drain: the last commit covers every MMA issued before it
+    if (tid == 0 && n_tiles > 0 && !abort_flag) {
+        const uint32_t last = n_tiles - 1;
+        if (!mbar_wait(&mma_bar[last % kStages], (last / kStages) & 1)) abort_flag = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (abort_flag) {
+        if (tid == 0) raise_status(p.status, kStatusTimeout);
+    } else if (warp < 4) {
+        // read back: TMEM lane 32w + l (l < 16) holds world 16w + l
+        const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+        const int world = 16 * warp + lane;
+        for (uint32_t g = 0; g < G; g++) {
+            for (int c0 = 0; c0 < p.n_alloc; c0 += 16) {
+                uint32_t r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(tmem + lane_base + g * static_cast<uint32_t>(p.n_alloc) + c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (lane < 16) {
+                    unsigned long long *dst = p.acc + (static_cast<size_t>(g) * kWorlds + world) * p.n_alloc + c0;
+#pragma unroll
+                    for (int k = 0; k < 16; k++) {
+                        const int x = __float2int_rn(__uint_as_float(r[k]) * 262144.0f);  // units of 2^-18
+                        if (x) atomicAdd(dst + k, static_cast<unsigned long long>(static_cast<long long>(x)));
+                    }
+                }
+            }
+        }
+    }
+    if (tid < static_cast<int>(G) && ng_acc[tid]) atomicAdd(p.ng + tid, ng_acc[tid]);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+struct FinishParams {
+    const unsigned long long *acc;
+    const unsigned long long *ng;
+    uint32_t G;
+    int32_t n_cols, c4, n_alloc;
+    int32_t n_out;
+    int32_t out_kind[kMaxSpecs];
+    int32_t out_col[kMaxSpecs];
+    void *out[kMaxSpecs];
+    uint64_t *meta;
+    uint32_t *status;
+};
+
+// Digit totals -> COUNT / SUM / AVG per (group, world), metadata per group.
+__global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
+    const size_t cell = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    const bool live = cell < static_cast<size_t>(f.G) * kWorlds;
+    const uint32_t g = live ? static_cast<uint32_t>(cell / kWorlds) : 0;
+    const int j = static_cast<int>(cell % kWorlds);
+    const long long *a = reinterpret_cast<const long long *>(f.acc) + cell * f.n_alloc;
+    const unsigned long long cnt = live ? static_cast<unsigned long long>(a[0]) : 0ull;
+    const unsigned bal = __ballot_sync(kFull, live && cnt > 0);
+    if (f.meta && live) {
+        if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(f.meta + 2 * g + 1)[j >= 32 ? 1 : 0] = bal;
+        if (j == 0) f.meta[2 * g] = f.ng[g];
+    }
+    if (!live) return;
+    for (int s = 0; s < f.n_out; s++) {
+        if (f.out_kind[s] == PAC_COUNT) {
+            static_cast<unsigned long long *>(f.out[s])[cell] = cnt;
+            continue;
+        }
+        const int c = f.out_col[s];
+        __int128 tot = 0;
+        for (int q = 15; q >= 0; q--) {
+            const int feat = f.c4 == 1 ? 4 + q : 4 + q * f.c4 + c;
+            const long long dq = feat < f.n_alloc ? a[feat] : 0;
+            tot = tot * 16 + dq;
+        }
+        const bool fits = tot >= static_cast<__int128>(LLONG_MIN) && tot <= static_cast<__int128>(LLONG_MAX);
+        if (!fits) raise_status(f.status, kStatusOverflow);
+        const long long val = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
+        if (f.out_kind[s] == PAC_SUM) static_cast<long long *>(f.out[s])[cell] = val;
+        else static_cast<double *>(f.out[s])[cell] = cnt ? static_cast<double>(val) / static_cast<double>(cnt) : 0.0;
+    }
+}
+
+int mma_c4(int C) { return C == 1 ? 1 : 4; }
+
+// Distinct value columns of the specs (or -1 when a spec is not served).
+int mma_columns(const pac_agg_spec *specs, int n_specs, const void **cols) {
+    int C = 0;
+    for (int i = 0; i < n_specs; i++) {
+        const pac_agg_spec &s = specs[i];
+        if (s.kind == PAC_COUNT) continue;
+        if (!((s.kind == PAC_SUM || s.kind == PAC_AVG) && s.vtype == PAC_I64 && s.variant == PAC_EXACT)) return -1;
+        int k = 0;
+        while (k < C && cols[k] != s.values) k++;
+        if (k == C) {
+            if (C == kMaxCols) return -1;
+            cols[C++] = s.values;
+        }
+    }
+    return C;
+}
+
+}  // namespace
+
+bool mma_supported(const pac_input *in, const pac_agg_spec *specs, int n_specs) {
+    const void *cols[kMaxCols];
+    const int C = mma_columns(specs, n_specs, cols);
+    if (C < 0 || in->n == 0) return false;
+    if (in->n_groups > static_cast<uint32_t>(kMaxGroups)) return false;
+    const int n_alloc = feat_alloc(C == 0 ? 1 : C);
+    return in->n_groups * static_cast<uint32_t>(n_alloc) <= kTmemCols;
+}
+
+pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
+                   cudaStream_t stream, int *launches) {
+    MmaParams p{};
+    const void *cols[kMaxCols];
+    int C = mma_columns(specs, n_specs, cols);
+    if (C < 0) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path: unsupported spec");
+    const int Ceff = C == 0 ? 1 : C;  // COUNT only: one zero column
+    const int c4 = mma_c4(Ceff);
+    p.in.km = in->keys_or_masks;
+    p.in.gids = in->group_ids;
+    p.in.qkey = in->query_key;
+    p.in.n = in->n;
+    p.in.in_flags = in->in_flags;
+    p.in.hash_mode = in->hash_mode;
+    p.in.gid_bytes = in->group_ids ? in->gid_bytes : 0;
+    p.in.n_groups = in->n_groups;
+    for (int c = 0; c < C; c++) p.col[c] = static_cast<const long long *>(cols[c]);
+    p.n_cols = C;
+    p.n_alloc = feat_alloc(Ceff);
+    p.status = ctx->d_status;
+    const uint32_t G = in->n_groups;
+    uint64_t per = (in->n + ctx->n_sms - 1) / ctx->n_sms;
+    per = (per + kTileRows - 1) / kTileRows * kTileRows;
+    if (per > kMaxRowsPerCta) per = kMaxRowsPerCta;
+    p.rows_per_cta = static_cast<uint32_t>(per);
+    const uint64_t n_ctas = (in->n + per - 1) / per;
+    p.k_cap = (kTileRows + (kMmaK - 1) * G + kMmaK - 1) / kMmaK * kMmaK;
+    p.a_bytes = p.k_cap * 64;
+    p.b_bytes = p.k_cap * p.n_alloc;
+    const size_t smem = static_cast<size_t>(kStages) * (p.a_bytes + p.b_bytes);
+    if (smem > 220 * 1024) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path: tile does not fit shared memory");
+    const size_t acc_bytes = static_cast<size_t>(G) * kWorlds * p.n_alloc * 8;
+    pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, acc_bytes + G * 8 + 1024);
+    if (st != PAC_OK) return st;
+    Carver cv(ctx->ws);
+    p.acc = static_cast<unsigned long long *>(cv.take(acc_bytes));
+    p.ng = static_cast<unsigned long long *>(cv.take(G * 8));
+    PAC_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, cv.off, stream));
+    if (c4 == 1) {
+        PAC_CUDA(ctx, cudaFuncSetAttribute(k_agg_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k_agg_mma<1><<<static_cast<unsigned>(n_ctas), kThreads, smem, stream>>>(p);
+    } else {
+        PAC_CUDA(ctx, cudaFuncSetAttribute(k_agg_mma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        k_agg_mma<4><<<static_cast<unsigned>(n_ctas), kThreads, smem, stream>>>(p);
+    }
+    PAC_CUDA(ctx, cudaGetLastError());
+    FinishParams f{};
+    f.acc = p.acc;
+    f.ng = p.ng;
+    f.G = G;
+    f.n_cols = C;
+    f.c4 = c4;
+    f.n_alloc = p.n_alloc;
+    f.meta = meta;
+    f.status = ctx->d_status;
+    for (int i = 0; i < n_specs; i++) {
+        f.out_kind[f.n_out] = specs[i].kind;
+        int c = 0;
+        while (c < C && cols[c] != specs[i].values) c++;
+        f.out_col[f.n_out] = c;
+        f.out[f.n_out] = specs[i].out;
+        f.n_out++;
+    }
+    const size_t cells = static_cast<size_t>(G) * kWorlds;
+    k_mma_finish<<<static_cast<unsigned>((cells + 255) / 256), 256, 0, stream>>>(f);
+    PAC_CUDA(ctx, cudaGetLastError());
+    *launches += 3;  // memset + aggregation + finish
+    return PAC_OK;
 }
 
 }  // namespace pacgpu

@@ -52,10 +52,12 @@ class Ctx:
         return dm.cpu().numpy().view(np.uint64)
 
     def aggregate(self, first: np.ndarray, gids, n_groups: int, specs, *, in_flags=B.PAC_IN_KEYS,
-                  hash_mode=B.PAC_HASH_BALANCED, qkey=0, want_meta=True, keep=None):
-        """specs: list of (kind, variant, values ndarray or None).  Returns
-        (outs list of ndarrays [G,64], meta [G,2] uint64 or None, status)."""
+                  hash_mode=B.PAC_HASH_BALANCED, qkey=0, want_meta=True, keep=None, path=0):
+        """specs: list of (kind, variant, values ndarray or None).  path: 0 auto,
+        1 per-bit, 2 tensor core.  Returns (outs list of ndarrays [G,64],
+        meta [G,2] uint64 or None, status)."""
         T = torch()
+        B.pac_set_option(self.h, "agg_path", path)
         n = first.shape[0]
         dfirst = dev(first.view(np.int64) if first.dtype == np.uint64 else first.astype(np.int64))
         dg = dev(gids) if gids is not None else None
@@ -84,6 +86,8 @@ class Ctx:
         B.pac_aggregate_multi(self.h, inp, sp, len(spec_t), meta.data_ptr() if meta is not None else 0,
                               self.stream())
         st = B.pac_sync_status(self.h, self.stream())
+        self.last_path = B.pac_get_info(self.h, "last_path")
+        B.pac_set_option(self.h, "agg_path", 0)
         res = [o.cpu().numpy().view(od) for o, od in outs]
         m = meta.cpu().numpy().view(np.uint64) if meta is not None else None
         if keep is not None:
