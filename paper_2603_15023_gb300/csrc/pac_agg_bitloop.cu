@@ -130,21 +130,22 @@ __global__ void __launch_bounds__(256) k_bitloop_lowcard(const __grid_constant__
     uint64_t *st = reinterpret_cast<uint64_t *>(smem_raw) + warp * per_warp;
     uint64_t *ng_all = reinterpret_cast<uint64_t *>(smem_raw) + n_warps * per_warp;  // [warps][G]
     uint64_t *ng = ng_all + warp * G;
-    unsigned long long *maxabs = reinterpret_cast<unsigned long long *>(ng_all + n_warps * G);  // [NS]
+    // per warp, per slot: saturating sum of |v| (an exact int64 SUM needs every
+    // CTA partial to fit; |partial| <= sum |v| < 2^63 guarantees it)
+    unsigned long long *abssum = reinterpret_cast<unsigned long long *>(ng_all + n_warps * G);  // [warps][NS]
 
     for (size_t k = lane; k < per_warp; k += 32) {
         const int q = static_cast<int>(k / (static_cast<size_t>(G) * kWorlds));
         st[k] = q == 0 ? 0ull : op_identity(p.slot[q - 1].op);
     }
     for (uint32_t g = lane; g < G; g += 32) ng[g] = 0;
-    if (threadIdx.x < NS) maxabs[threadIdx.x] = 0;
     __syncthreads();
 
     const uint64_t begin = static_cast<uint64_t>(blockIdx.x) * p.rows_per_cta;
     const uint64_t end = min(p.in.n, begin + p.rows_per_cta);
-    uint64_t my_maxabs[NS];
+    uint64_t my_abs[NS];
 #pragma unroll
-    for (int s = 0; s < NS; s++) my_maxabs[s] = 0;
+    for (int s = 0; s < NS; s++) my_abs[s] = 0;
 
     for (uint64_t base = begin + static_cast<uint64_t>(warp) * 32; base < end;
          base += static_cast<uint64_t>(n_warps) * 32) {
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(256) k_bitloop_lowcard(const __grid_constant__
                 if (p.slot[s].op == OP_ISUM) {
                     const long long v = static_cast<long long>(vals[s]);
                     const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
-                    my_maxabs[s] = a > my_maxabs[s] ? a : my_maxabs[s];
+                    const uint64_t t = my_abs[s] + a;
+                    my_abs[s] = t < a ? ~0ull : t;
                 }
             }
         }
@@ -220,14 +222,13 @@ __global__ void __launch_bounds__(256) k_bitloop_lowcard(const __grid_constant__
     }
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        if (s < p.n_slots && p.slot[s].op == OP_ISUM) {
-            uint64_t m = my_maxabs[s];
-            for (int o = 16; o; o >>= 1) {
-                const uint64_t t = __shfl_xor_sync(kFull, m, o);
-                m = t > m ? t : m;
-            }
-            if (lane == 0) atomicMax(&maxabs[s], static_cast<unsigned long long>(m));
+        uint64_t m = my_abs[s];
+        for (int o = 16; o; o >>= 1) {
+            const uint64_t t = __shfl_xor_sync(kFull, m, o);
+            const uint64_t u = m + t;
+            m = u < t ? ~0ull : u;
         }
+        if (lane == 0) abssum[warp * NS + s] = m;
     }
     __syncthreads();
 
@@ -251,8 +252,12 @@ __global__ void __launch_bounds__(256) k_bitloop_lowcard(const __grid_constant__
         ng_out[g] = a;
     }
     if (threadIdx.x < NS && threadIdx.x < p.n_slots && p.slot[threadIdx.x].op == OP_ISUM) {
-        const double bound = static_cast<double>(maxabs[threadIdx.x]) * static_cast<double>(end > begin ? end - begin : 0);
-        if (bound >= 9.2e18) raise_status(p.status, kStatusOverflow);
+        uint64_t tot = 0;
+        for (int w = 0; w < n_warps; w++) {
+            const uint64_t t = tot + abssum[w * NS + threadIdx.x];
+            tot = t < tot ? ~0ull : t;
+        }
+        if (tot >= (1ull << 63)) raise_status(p.status, kStatusOverflow);
     }
 }
 
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(256) k_bitloop_atomic(const __grid_constant__ 
     uint64_t *st = static_cast<uint64_t *>(p.partials);
     const uint64_t warp_global = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps_total = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-    unsigned long long my_max = 0;
+    unsigned long long my_abs = 0;
     for (uint64_t base = warp_global * 32; base < p.in.n; base += n_warps_total * 32) {
         const uint64_t row = base + lane;
         bool valid = row < p.in.n;
@@ -332,7 +337,8 @@ __global__ void __launch_bounds__(256) k_bitloop_atomic(const __grid_constant__ 
             if (p.slot[s].op == OP_ISUM) {
                 const long long v = static_cast<long long>(vals[s]);
                 const unsigned long long a = v < 0 ? 0ull - static_cast<unsigned long long>(v) : static_cast<unsigned long long>(v);
-                my_max = a > my_max ? a : my_max;
+                const unsigned long long t = my_abs + a;
+                my_abs = t < a ? ~0ull : t;
             }
         }
         const uint32_t mlo = static_cast<uint32_t>(mask), mhi = static_cast<uint32_t>(mask >> 32);
@@ -354,13 +360,17 @@ __global__ void __launch_bounds__(256) k_bitloop_atomic(const __grid_constant__ 
             if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(p.ng_partials + g), 1ull);
         }
     }
-    // conservative int64 overflow guard: every group's rows bounded by n
+    // int64 SUM guard: the wrapping atomics are exact while every world's sum
+    // fits; the total of |v| over all rows bounds every world's sum
     for (int o = 16; o; o >>= 1) {
-        const unsigned long long t = __shfl_xor_sync(kFull, my_max, o);
-        my_max = t > my_max ? t : my_max;
+        const unsigned long long t = __shfl_xor_sync(kFull, my_abs, o);
+        const unsigned long long u = my_abs + t;
+        my_abs = u < t ? ~0ull : u;
     }
-    if (lane == 0 && static_cast<double>(my_max) * static_cast<double>(p.in.n) >= 9.2e18)
-        raise_status(p.status, kStatusOverflow);
+    if (lane == 0 && my_abs) {
+        const unsigned long long prev = atomicAdd(p.abs_total, my_abs);
+        if (prev + my_abs < prev || prev + my_abs >= (1ull << 63)) raise_status(p.status, kStatusOverflow);
+    }
 }
 
 }  // namespace
@@ -443,7 +453,7 @@ int bitloop_pick_ns(int n_slots) { return n_slots <= 1 ? 1 : (n_slots <= 4 ? 4 :
 
 size_t bitloop_smem_bytes(int n_warps, int n_slots, uint32_t G, int ns) {
     return static_cast<size_t>(n_warps) * (1 + n_slots) * G * kWorlds * 8 +
-           static_cast<size_t>(n_warps) * G * 8 + static_cast<size_t>(ns) * 8;
+           static_cast<size_t>(n_warps) * G * 8 + static_cast<size_t>(n_warps) * ns * 8;
 }
 
 cudaError_t launch_bitloop_lowcard(const BitloopParams &p, int n_ctas, int n_warps, cudaStream_t s) {

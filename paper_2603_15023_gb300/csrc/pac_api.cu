@@ -144,12 +144,14 @@ pac_status run_bitloop(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *sp
         PAC_CUDA(ctx, launch_bitloop_merge(p, static_cast<int>(n_ctas), false, stream));
         *launches += 2;
     } else {
-        const size_t need = per_part + 256 + G * 8 + 256;
+        const size_t need = per_part + 256 + G * 8 + 256 + 256;
         pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, need);
         if (st != PAC_OK) return st;
         Carver cv(ctx->ws);
         p.partials = cv.take(per_part);
         p.ng_partials = static_cast<uint64_t *>(cv.take(G * 8));
+        p.abs_total = static_cast<unsigned long long *>(cv.take(8));
+        PAC_CUDA(ctx, cudaMemsetAsync(p.abs_total, 0, 8, stream));
         int n_ctas = ctx->n_sms * 8;
         PAC_CUDA(ctx, launch_bitloop_atomic(p, n_ctas, stream));
         PAC_CUDA(ctx, launch_bitloop_merge(p, 1, true, stream));

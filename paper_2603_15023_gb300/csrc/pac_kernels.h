@@ -36,6 +36,7 @@ struct BitloopParams {
     uint64_t *ng_partials;  // lowcard: [ctas][G]; atomic: [G]
     uint64_t *meta;         // [G][2] or nullptr
     uint32_t *status;
+    unsigned long long *abs_total;  // atomic path: running sum of |v| (zeroed)
 };
 
 int bitloop_pick_ns(int n_slots);

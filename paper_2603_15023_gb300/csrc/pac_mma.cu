@@ -41,16 +41,15 @@ namespace pacgpu {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 256;
-constexpr int kRowsPerThread = 2;
-constexpr int kTileRows = kThreads * kRowsPerThread;  // 512
+constexpr int kThreads = 512;
+constexpr int kTileRows = kThreads;  // one row per thread per tile
 constexpr int kStages = 2;
 constexpr int kMmaK = 32;               // rows per tcgen05.mma of 8-bit operands
 constexpr int kMaxGroups = 8;
 constexpr int kMaxCols = 4;
 constexpr uint32_t kMaxRowsPerCta = 1u << 20;  // keeps FP32 digit totals below 2^24
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint32_t kWaitLimit = 1u << 24;  // with <= 256 ns sleeps: a few seconds
 
 // Accumulator / feature columns per group for C value columns.
 __host__ __device__ constexpr int feat_alloc(int C) { return C == 1 ? 32 : 80; }
@@ -78,9 +77,12 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait on an mbarrier phase; false when the limit ran out.
+// Bounded wait on an mbarrier phase; false when the limit ran out.  Polls
+// back off with __nanosleep so a waiting warp does not take issue slots from
+// the warps it is waiting for.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     uint32_t done = 0;
+    uint32_t ns = 32;
     for (uint32_t it = 0; it < kWaitLimit; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -88,6 +90,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
     }
     return false;
 }
@@ -128,12 +132,16 @@ template <int C4, int L>
 struct Features {
     static constexpr int kN = round16(4 + L * C4);
     static constexpr int kWords = kN / 4;
-    __device__ __forceinline__ static void build(const long long *v, bool sgn, uint32_t *w) {
+    __device__ __forceinline__ static uint32_t sm_byte(long long d) {
+        return d < 0 ? (0x80u | static_cast<uint32_t>(-d)) : static_cast<uint32_t>(d);
+    }
+    __device__ __forceinline__ static void build(long long v0, long long v1, long long v2, long long v3, bool sgn,
+                                                 uint32_t *w) {
         w[0] = 1u;
 #pragma unroll
         for (int k = 1; k < kWords; k++) w[k] = 0u;
         if (C4 == 1) {
-            const unsigned long long u = static_cast<unsigned long long>(v[0]);
+            const unsigned long long u = static_cast<unsigned long long>(v0);
 #pragma unroll
             for (int k = 0; k < (L + 3) / 4; k++) {
                 uint32_t x = static_cast<uint32_t>(u >> (16 * k)) & 0xFFFFu;
@@ -141,48 +149,40 @@ struct Features {
                 x = (x | (x << 4)) & 0x0F0F0F0Fu;
                 w[1 + k] = x;
             }
-            if (L % 4) w[1 + (L - 1) / 4] &= (1u << (8 * (L % 4))) - 1u;  // keep digits < L only
+            if (L % 4) w[1 + (L - 1) / 4] &= (1u << (8 * (L % 4))) - 1u;  // digits < L only
             if (sgn) {
-                const long long d = v[0] >> (4 * (L - 1));
-                const uint32_t b = d < 0 ? (0x80u | static_cast<uint32_t>(-d)) : static_cast<uint32_t>(d);
                 const int wi = 1 + (L - 1) / 4, sh = 8 * ((L - 1) % 4);
-                w[wi] = (w[wi] & ~(0xFFu << sh)) | (b << sh);
+                w[wi] = (w[wi] & ~(0xFFu << sh)) | (sm_byte(v0 >> (4 * (L - 1))) << sh);
             }
         } else {
-            // two digits per byte p of the 64-bit values
+            // byte p of the four values holds digits 2p and 2p+1
 #pragma unroll
             for (int p = 0; p < L / 2; p++) {
                 const int h = p / 4, b = p % 4;
-                const uint32_t a0 = static_cast<uint32_t>(static_cast<unsigned long long>(v[0]) >> (32 * h));
-                const uint32_t a1 = static_cast<uint32_t>(static_cast<unsigned long long>(v[1]) >> (32 * h));
-                const uint32_t a2 = static_cast<uint32_t>(static_cast<unsigned long long>(v[2]) >> (32 * h));
-                const uint32_t a3 = static_cast<uint32_t>(static_cast<unsigned long long>(v[3]) >> (32 * h));
+                const uint32_t a0 = static_cast<uint32_t>(static_cast<unsigned long long>(v0) >> (32 * h));
+                const uint32_t a1 = static_cast<uint32_t>(static_cast<unsigned long long>(v1) >> (32 * h));
+                const uint32_t a2 = static_cast<uint32_t>(static_cast<unsigned long long>(v2) >> (32 * h));
+                const uint32_t a3 = static_cast<uint32_t>(static_cast<unsigned long long>(v3) >> (32 * h));
                 const uint32_t sel = static_cast<uint32_t>(b | ((4 + b) << 4));
-                const uint32_t t01 = __byte_perm(a0, a1, sel);
-                const uint32_t t23 = __byte_perm(a2, a3, sel);
-                const uint32_t word = __byte_perm(t01, t23, 0x5410);
+                const uint32_t word = __byte_perm(__byte_perm(a0, a1, sel), __byte_perm(a2, a3, sel), 0x5410);
                 w[1 + 2 * p] = word & 0x0F0F0F0Fu;
                 w[2 + 2 * p] = (word >> 4) & 0x0F0F0F0Fu;
             }
             if (sgn) {
-                uint32_t top = 0;
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const long long d = v[c] >> (4 * (L - 1));
-                    const uint32_t b = d < 0 ? (0x80u | static_cast<uint32_t>(-d)) : static_cast<uint32_t>(d);
-                    top |= b << (8 * c);
-                }
-                w[L] = top;
+                const int sh = 4 * (L - 1);
+                w[L] = sm_byte(v0 >> sh) | (sm_byte(v1 >> sh) << 8) | (sm_byte(v2 >> sh) << 16) |
+                       (sm_byte(v3 >> sh) << 24);
             }
         }
     }
 };
 
 template <int C4, int L>
-__device__ __forceinline__ void write_features(uint32_t b_stage, uint32_t slot, const long long *v, bool sgn) {
+__device__ __forceinline__ void write_features(uint32_t b_stage, uint32_t slot, long long v0, long long v1,
+                                               long long v2, long long v3, bool sgn) {
     using F = Features<C4, L>;
     uint32_t w[F::kWords];
-    F::build(v, sgn, w);
+    F::build(v0, v1, v2, v3, sgn, w);
     const uint32_t lbo = (F::kN / 16) * 128;
     const uint32_t base = b_stage + (slot >> 3) * lbo + (slot & 7) * 16;
 #pragma unroll
@@ -190,14 +190,15 @@ __device__ __forceinline__ void write_features(uint32_t b_stage, uint32_t slot, 
 }
 
 template <int C4>
-__device__ __forceinline__ void write_features_l(int L, uint32_t b_stage, uint32_t slot, const long long *v, bool sgn) {
+__device__ __forceinline__ void write_features_l(int L, uint32_t b_stage, uint32_t slot, long long v0, long long v1,
+                                                 long long v2, long long v3, bool sgn) {
     switch (L) {
-    case 2: write_features<C4, 2>(b_stage, slot, v, sgn); break;
-    case 4: write_features<C4, 4>(b_stage, slot, v, sgn); break;
-    case 6: write_features<C4, 6>(b_stage, slot, v, sgn); break;
-    case 8: write_features<C4, 8>(b_stage, slot, v, sgn); break;
-    case 12: write_features<C4, 12>(b_stage, slot, v, sgn); break;
-    default: write_features<C4, 16>(b_stage, slot, v, sgn); break;
+    case 2: write_features<C4, 2>(b_stage, slot, v0, v1, v2, v3, sgn); break;
+    case 4: write_features<C4, 4>(b_stage, slot, v0, v1, v2, v3, sgn); break;
+    case 6: write_features<C4, 6>(b_stage, slot, v0, v1, v2, v3, sgn); break;
+    case 8: write_features<C4, 8>(b_stage, slot, v0, v1, v2, v3, sgn); break;
+    case 12: write_features<C4, 12>(b_stage, slot, v0, v1, v2, v3, sgn); break;
+    default: write_features<C4, 16>(b_stage, slot, v0, v1, v2, v3, sgn); break;
     }
 }
 
@@ -210,27 +211,65 @@ __device__ __forceinline__ int digit_class(int need) {
     return 16;
 }
 
+// Raw columns of one row, loaded two tiles ahead of their use.
+struct RawRow {
+    unsigned long long km;
+    uint32_t gid;
+    long long v0, v1, v2, v3;
+};
+
 template <int C4>
-__global__ void __launch_bounds__(kThreads, 1) k_agg_mma(const __grid_constant__ MmaParams p) {
+__device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin, uint32_t off, bool ok, RawRow &r) {
+    r.km = 0;
+    r.gid = 0xFFFFFFFFu;
+    r.v0 = r.v1 = r.v2 = r.v3 = 0;
+    if (!ok) return;
+    const uint64_t row = cta_begin + off;
+    r.km = __ldg(static_cast<const unsigned long long *>(p.in.km) + row);
+    r.gid = row_gid(p.in, row);
+    if (p.n_cols > 0) r.v0 = __ldg(p.col[0] + row);
+    if (C4 == 4) {
+        if (p.n_cols > 1) r.v1 = __ldg(p.col[1] + row);
+        if (p.n_cols > 2) r.v2 = __ldg(p.col[2] + row);
+        if (p.n_cols > 3) r.v3 = __ldg(p.col[3] + row);
+    }
+}
+
+// Named barrier among the producer warps only.
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised CTA: warps 0..15 produce operands (one row per thread per
+// tile), warp 16 issues the tensor-core MMAs.  Producers agree on a tile's
+// layout through a producer-only named barrier; the stage ring is handed over
+// with mbarriers: full[s] (16 producer-warp arrivals) and empty[s] (arrived
+// by tcgen05.commit when the MMAs that read stage s are done).
+template <int C4>
+__global__ void __launch_bounds__(kThreads + 32, 1) k_agg_mma(const __grid_constant__ MmaParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mma_bar[kStages];
+    constexpr int kWarps = kThreads / 32;  // producer warps
+    __shared__ __align__(8) uint64_t full_bar[kStages];
+    __shared__ __align__(8) uint64_t empty_bar[kStages];
     __shared__ uint32_t tmem_slot;
-    __shared__ uint32_t warp_cnt[kThreads / 32][kMaxGroups];
-    __shared__ uint32_t warp_bits[kThreads / 32];
-    __shared__ uint32_t warp_neg[kThreads / 32];
-    __shared__ uint32_t woff[kThreads / 32][kMaxGroups];
-    __shared__ uint32_t grp_lo[kMaxGroups], grp_cnt[kMaxGroups], grp_len[kMaxGroups];
-    __shared__ int tile_L, tile_N, tile_sgn;
+    __shared__ uint32_t st_cnt[2][kWarps][kMaxGroups];  // by tile parity
+    __shared__ uint32_t st_mag[2][kWarps][2];
+    __shared__ uint32_t meta_lo[kStages][kMaxGroups], meta_len[kStages][kMaxGroups];
+    __shared__ int meta_n[kStages];
     __shared__ unsigned long long ng_acc[kMaxGroups];
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t G = p.in.n_groups;
-    const int C = p.n_cols;
     const uint32_t lt = (1u << lane) - 1u;
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; s++) mbar_init(&mma_bar[s], 1);
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&full_bar[s], kWarps);
+            mbar_init(&empty_bar[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag = 0;
     }
@@ -245,8 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_agg_mma(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
     const uint32_t used_cols = G * static_cast<uint32_t>(p.n_alloc);
-    // zero the accumulators (warps 0-3 own TMEM lane quadrants 0-3)
-    if (warp < 4) {
+    if (warp < 4) {  // zero the accumulators (warps 0-3 own TMEM lane quadrants 0-3)
         const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
         for (uint32_t c0 = 0; c0 < used_cols; c0 += 16) {
             asm volatile(
@@ -262,176 +300,171 @@ __global__ void __launch_bounds__(kThreads, 1) k_agg_mma(const __grid_constant__
 
     const uint64_t begin = static_cast<uint64_t>(blockIdx.x) * p.rows_per_cta;
     const uint64_t end = min(p.in.n, begin + p.rows_per_cta);
-    const uint32_t n_tiles = static_cast<uint32_t>((end - begin + kTileRows - 1) / kTileRows);
+    const uint32_t n_rows = static_cast<uint32_t>(end - begin);
+    const uint32_t n_tiles = (n_rows + kTileRows - 1) / kTileRows;
     const uint32_t smem_base = smem_u32(smem);
-    const bool balanced_keys = !(p.in.in_flags & PAC_IN_MASKS) && p.in.hash_mode == PAC_HASH_BALANCED;
 
-    for (uint32_t it = 0; it < n_tiles; it++) {
-        const int s = it % kStages;
-        const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
-        const uint32_t b_stage = a_stage + p.a_bytes;
-        const uint64_t row0 = begin + static_cast<uint64_t>(it) * kTileRows;
-
-        // (1) rows into registers
-        uint64_t mask[kRowsPerThread];
-        uint32_t gid[kRowsPerThread];
-        long long v[kRowsPerThread][4];
-        bool valid[kRowsPerThread];
-        uint32_t bits = 0, neg = 0;
-#pragma unroll
-        for (int r = 0; r < kRowsPerThread; r++) {
-            const uint64_t row = row0 + r * kThreads + tid;
-            valid[r] = row < end;
-            mask[r] = 0;
-            gid[r] = 0xFFFFFFFFu;
-#pragma unroll
-            for (int c = 0; c < 4; c++) v[r][c] = 0;
-            if (valid[r]) {
-                gid[r] = row_gid(p.in, row);
-                if (gid[r] >= G) {  // out-of-range group id: skip the row, report it
-                    raise_status(p.status, kStatusBadGroup);
-                    valid[r] = false;
-                    gid[r] = 0xFFFFFFFFu;
-                    continue;
-                }
-                mask[r] = row_mask(p.in, row);
-#pragma unroll
-                for (int c = 0; c < C4; c++) {
-                    if (c < C) {
-                        const long long x = __ldg(p.col[c] + row);
-                        v[r][c] = x;
-                        const unsigned long long m = x < 0 ? ~static_cast<unsigned long long>(x) : static_cast<unsigned long long>(x);
-                        const uint32_t bl = m ? 64u - __clzll(static_cast<long long>(m)) : 0u;
-                        bits = bl > bits ? bl : bits;
-                        neg |= x < 0 ? 1u : 0u;
+    if (warp == kWarps) {
+        // ---------------- MMA warp ----------------
+        for (uint32_t it = 0; it < n_tiles; it++) {
+            const int s = it % kStages;
+            if (lane == 0) {
+                if (!mbar_wait(&full_bar[s], (it / kStages) & 1)) abort_flag = 1;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
+                const uint32_t b_stage = a_stage + p.a_bytes;
+                const int N = meta_n[s];
+                const uint32_t idesc = instr_desc(N);
+                const uint32_t lbo_b = (N / 16) * 128;
+                for (uint32_t g = 0; g < G; g++) {
+                    const uint32_t d = tmem + g * static_cast<uint32_t>(p.n_alloc);
+                    const uint32_t k_lo = meta_lo[s][g], k_hi = k_lo + meta_len[s][g];
+                    for (uint32_t k0 = k_lo; k0 < k_hi; k0 += kMmaK) {
+                        const uint64_t da = smem_desc(a_stage + (k0 >> 3) * 512, 512, 128);
+                        const uint64_t db = smem_desc(b_stage + (k0 >> 3) * lbo_b, lbo_b, 128);
+                        mma_f8(d, da, db, idesc);
                     }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&empty_bar[s])));
             }
+            __syncwarp();
         }
-        // (2) warp statistics: group counts, magnitude, signs
-        uint32_t b0[kMaxGroups], b1[kMaxGroups];
-#pragma unroll
-        for (int g = 0; g < kMaxGroups; g++) {
-            b0[g] = __ballot_sync(kFull, gid[0] == static_cast<uint32_t>(g));
-            b1[g] = __ballot_sync(kFull, gid[1] == static_cast<uint32_t>(g));
+        // drain: the last commit covers every MMA issued before it
+        if (lane == 0 && n_tiles > 0) {
+            const uint32_t last = n_tiles - 1;
+            if (!mbar_wait(&empty_bar[last % kStages], (last / kStages) & 1)) abort_flag = 1;
         }
-        bits = __reduce_max_sync(kFull, bits);
-        neg = __reduce_or_sync(kFull, neg);
-        if (lane == 0) {
-#pragma unroll
-            for (int g = 0; g < kMaxGroups; g++) warp_cnt[warp][g] = __popc(b0[g]) + __popc(b1[g]);
-            warp_bits[warp] = bits;
-            warp_neg[warp] = neg;
-        }
-        // (3) the stage's previous MMAs must have finished reading it
-        if (tid == 0 && it >= kStages) {
-            if (!mbar_wait(&mma_bar[s], ((it / kStages) - 1) & 1)) abort_flag = 1;
-        }
-        __syncthreads();
-        if (abort_flag) break;
-        // (4) tile layout: group runs, digit count
-        if (warp == 0) {
-            uint32_t cnt = 0;
-            if (lane < static_cast<int>(G))
-                for (int w = 0; w < kThreads / 32; w++) cnt += warp_cnt[w][lane];
+        __syncwarp();
+    } else {
+        // ---------------- producer warps ----------------
+        const bool keys_in = !(p.in.in_flags & PAC_IN_MASKS);
+        const bool balanced_keys = keys_in && p.in.hash_mode == PAC_HASH_BALANCED;
+        RawRow nx0, nx1;  // tiles it and it+1
+        load_raw<C4>(p, begin, static_cast<uint32_t>(tid), static_cast<uint32_t>(tid) < n_rows, nx0);
+        load_raw<C4>(p, begin, kTileRows + tid, kTileRows + static_cast<uint32_t>(tid) < n_rows, nx1);
+        for (uint32_t it = 0; it < n_tiles; it++) {
+            const int s = it % kStages;
+            const int pb = it & 1;
+            const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
+            const uint32_t b_stage = a_stage + p.a_bytes;
+            const RawRow cur = nx0;
+            nx0 = nx1;
+            {
+                const uint32_t off = (it + 2) * kTileRows + tid;
+                load_raw<C4>(p, begin, off, it + 2 < n_tiles && off < n_rows, nx1);
+            }
+            // (1) this row: group, world mask, magnitude and sign statistics
+            uint32_t gid = cur.gid;
+            bool valid = gid != 0xFFFFFFFFu;
+            if (valid && gid >= G) {  // out-of-range group id: skip the row, report it
+                raise_status(p.status, kStatusBadGroup);
+                valid = false;
+                gid = 0xFFFFFFFFu;
+            }
+            uint32_t lo32 = 0, hi32 = 0;
+            if (valid) {
+                const uint64_t m = keys_in ? keyed_world_mask(static_cast<long long>(cur.km), p.in.qkey, p.in.hash_mode)
+                                           : cur.km;
+                lo32 = static_cast<uint32_t>(m);
+                hi32 = static_cast<uint32_t>(m >> 32);
+            }
+            // OR of |v| in one's complement (v, or ~v for v < 0) bounds every
+            // value's bit length; the sign bits say whether any is negative
+            unsigned long long mag = static_cast<unsigned long long>(cur.v0 ^ (cur.v0 >> 63));
+            unsigned long long sgnbits = static_cast<unsigned long long>(cur.v0);
+            if (C4 == 4) {
+                mag |= static_cast<unsigned long long>(cur.v1 ^ (cur.v1 >> 63));
+                mag |= static_cast<unsigned long long>(cur.v2 ^ (cur.v2 >> 63));
+                mag |= static_cast<unsigned long long>(cur.v3 ^ (cur.v3 >> 63));
+                sgnbits |= static_cast<unsigned long long>(cur.v1 | cur.v2 | cur.v3);
+            }
+            const uint32_t mag_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(mag >> 32));
+            const uint32_t mag_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(mag));
+            const uint32_t any_neg = __reduce_or_sync(kFull, static_cast<uint32_t>(sgnbits >> 63));
+            // (2) group rank inside the warp
+            const uint32_t peers = __match_any_sync(kFull, gid);
+            const uint32_t rank = __popc(peers & lt);
+            if (lane < kMaxGroups) st_cnt[pb][warp][lane] = 0;
+            __syncwarp();
+            if (valid && rank == 0) st_cnt[pb][warp][gid] = __popc(peers);
+            if (lane == 0) {
+                st_mag[pb][warp][0] = mag_hi | (any_neg << 31);  // bit 63 of a magnitude is never set
+                st_mag[pb][warp][1] = mag_lo;
+            }
+            producers_sync();
+            // (3) every warp derives the tile layout: group runs, its own offsets, digits
+            uint32_t cnt = 0, before = 0;
+            if (lane < static_cast<int>(G)) {
+                for (int w = 0; w < kWarps; w++) {
+                    const uint32_t c = st_cnt[pb][w][lane];
+                    cnt += c;
+                    before += w < warp ? c : 0u;
+                }
+            }
             const uint32_t len = (cnt + kMmaK - 1) & ~static_cast<uint32_t>(kMmaK - 1);
             uint32_t incl = len;
-            for (int o = 1; o < 32; o <<= 1) {
+            for (int o = 1; o < kMaxGroups; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(kFull, incl, o);
                 if (lane >= o) incl += t;
             }
-            if (lane < static_cast<int>(G)) {
-                const uint32_t lo = incl - len;
-                grp_lo[lane] = lo;
-                grp_cnt[lane] = cnt;
-                grp_len[lane] = len;
+            const uint32_t glo = incl - len;
+            const uint32_t my_off = glo + before;  // lane g: this warp's first slot in group g
+            const uint32_t oh = __reduce_or_sync(kFull, lane < kWarps ? st_mag[pb][lane][0] : 0u);
+            const uint32_t ol = __reduce_or_sync(kFull, lane < kWarps ? st_mag[pb][lane][1] : 0u);
+            const bool neg = (oh >> 31) != 0;
+            const uint32_t mh = oh & 0x7FFFFFFFu;
+            const int bits = mh ? 64 - __clz(static_cast<int>(mh)) : (ol ? 32 - __clz(static_cast<int>(ol)) : 0);
+            const int L = digit_class(neg ? (bits + 4) / 4 : (bits + 3) / 4);
+            const int N = C4 == 1 ? round16(4 + L) : round16(4 + L * 4);
+            const uint32_t slot = __shfl_sync(kFull, my_off, valid ? static_cast<int>(gid) : 0) + rank;
+            // (4) the stage must be free: the MMAs of tile it - kStages are done
+            if (it >= kStages) {
+                if (lane == 0 && !mbar_wait(&empty_bar[s], ((it / kStages) - 1) & 1)) abort_flag = 1;
+                __syncwarp();
+            }
+            if (warp == 0 && lane < static_cast<int>(G)) {
+                meta_lo[s][lane] = glo;
+                meta_len[s][lane] = len;
                 ng_acc[lane] += cnt;
-                uint32_t run = lo;
-                for (int w = 0; w < kThreads / 32; w++) {
-                    woff[w][lane] = run;
-                    run += warp_cnt[w][lane];
-                }
+                if (lane == 0) meta_n[s] = N;
             }
-            uint32_t mb = lane < kThreads / 32 ? warp_bits[lane] : 0u;
-            uint32_t ng = lane < kThreads / 32 ? warp_neg[lane] : 0u;
-            mb = __reduce_max_sync(kFull, mb);
-            ng = __reduce_or_sync(kFull, ng);
-            if (lane == 0) {
-                const int need = ng ? static_cast<int>((mb + 1 + 3) / 4) : static_cast<int>((mb + 3) / 4);
-                const int L = digit_class(need);
-                tile_L = L;
-                tile_sgn = ng ? 1 : 0;
-                tile_N = C4 == 1 ? round16(4 + L) : round16(4 + L * 4);
-            }
-        }
-        __syncthreads();
-        // (5) operands into the stage, rows sorted by group
-        const int L = tile_L;
-        const bool sgn = tile_sgn != 0;
-#pragma unroll
-        for (int r = 0; r < kRowsPerThread; r++) {
-            if (!valid[r]) continue;
-            uint32_t rank = 0, base = 0;
-#pragma unroll
-            for (int g = 0; g < kMaxGroups; g++) {
-                if (gid[r] == static_cast<uint32_t>(g)) {
-                    rank = r == 0 ? __popc(b0[g] & lt) : __popc(b0[g]) + __popc(b1[g] & lt);
-                    base = woff[warp][g];
-                }
-            }
-            const uint32_t slot = base + rank;
-            const uint32_t a_row = a_stage + (slot >> 3) * 512 + (slot & 7) * 16;
-            const uint32_t lo = static_cast<uint32_t>(mask[r]);
-            write_bits16(a_row, lo & 0xFFFFu);
-            write_bits16(a_row + 128, lo >> 16);
-            if (balanced_keys) {
-                // worlds 32..63 are the complement of worlds 0..31
-                const uint32_t hi = ~lo;
-                write_bits16(a_row + 256, hi & 0xFFFFu);
-                write_bits16(a_row + 384, hi >> 16);
-            } else {
-                const uint32_t hi = static_cast<uint32_t>(mask[r] >> 32);
-                write_bits16(a_row + 256, hi & 0xFFFFu);
-                write_bits16(a_row + 384, hi >> 16);
-            }
-            write_features_l<C4>(L, b_stage, slot, v[r], sgn);
-        }
-        // zero rows that pad each group's run to the MMA step (warp g: group g)
-        if (warp < static_cast<int>(G)) {
-            const uint32_t pad = grp_len[warp] - grp_cnt[warp];
-            if (static_cast<uint32_t>(lane) < pad) {
-                const uint32_t slot = grp_lo[warp] + grp_cnt[warp] + lane;
+            // (5) operands into the stage, rows sorted by group
+            if (valid) {
                 const uint32_t a_row = a_stage + (slot >> 3) * 512 + (slot & 7) * 16;
-                for (int h = 0; h < 4; h++) sts128(a_row + h * 128, 0, 0, 0, 0);
-                const int N = tile_N;
-                const uint32_t b_row = b_stage + (slot >> 3) * ((N / 16) * 128) + (slot & 7) * 16;
-                for (int h = 0; h < N / 16; h++) sts128(b_row + h * 128, 0, 0, 0, 0);
+                const uint32_t w0 = spread4(lo32 & 0xF), w1 = spread4((lo32 >> 4) & 0xF);
+                const uint32_t w2 = spread4((lo32 >> 8) & 0xF), w3 = spread4((lo32 >> 12) & 0xF);
+                const uint32_t w4 = spread4((lo32 >> 16) & 0xF), w5 = spread4((lo32 >> 20) & 0xF);
+                const uint32_t w6 = spread4((lo32 >> 24) & 0xF), w7 = spread4(lo32 >> 28);
+                sts128(a_row, w0, w1, w2, w3);
+                sts128(a_row + 128, w4, w5, w6, w7);
+                if (balanced_keys) {
+                    // worlds 32..63 are the complement of worlds 0..31
+                    constexpr uint32_t k1 = 0x01010101u;
+                    sts128(a_row + 256, w0 ^ k1, w1 ^ k1, w2 ^ k1, w3 ^ k1);
+                    sts128(a_row + 384, w4 ^ k1, w5 ^ k1, w6 ^ k1, w7 ^ k1);
+                } else {
+                    write_bits16(a_row + 256, hi32 & 0xFFFFu);
+                    write_bits16(a_row + 384, hi32 >> 16);
+                }
+                write_features_l<C4>(L, b_stage, slot, cur.v0, cur.v1, cur.v2, cur.v3, neg);
             }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // (6) one thread issues the MMAs of the tile and commits them
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const int N = tile_N;
-            const uint32_t idesc = instr_desc(N);
-            const uint32_t lbo_b = (N / 16) * 128;
-            for (uint32_t g = 0; g < G; g++) {
-                const uint32_t d = tmem + g * static_cast<uint32_t>(p.n_alloc);
-                for (uint32_t k0 = grp_lo[g]; k0 < grp_lo[g] + grp_len[g]; k0 += kMmaK) {
-                    const uint64_t da = smem_desc(a_stage + (k0 >> 3) * 512, 512, 128);
-                    const uint64_t db = smem_desc(b_stage + (k0 >> 3) * lbo_b, lbo_b, 128);
-                    mma_f8(d, da, db, idesc);
+            // zero the rows that pad each group's run to the MMA step (warp g: group g)
+            if (warp < static_cast<int>(G)) {
+                const uint32_t gcnt = __shfl_sync(kFull, cnt, warp), glen = __shfl_sync(kFull, len, warp);
+                const uint32_t gl = __shfl_sync(kFull, glo, warp);
+                if (static_cast<uint32_t>(lane) < glen - gcnt) {
+                    const uint32_t ps = gl + gcnt + lane;
+                    const uint32_t a_row = a_stage + (ps >> 3) * 512 + (ps & 7) * 16;
+                    for (int h = 0; h < 4; h++) sts128(a_row + h * 128, 0, 0, 0, 0);
+                    const uint32_t b_row = b_stage + (ps >> 3) * ((N / 16) * 128) + (ps & 7) * 16;
+                    for (int h = 0; h < N / 16; h++) sts128(b_row + h * 128, 0, 0, 0, 0);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mma_bar[s])));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_bar[s]);
         }
-    }
-    // drain: the last commit covers every MMA issued before it
-    if (tid == 0 && n_tiles > 0 && !abort_flag) {
-        const uint32_t last = n_tiles - 1;
-        if (!mbar_wait(&mma_bar[last % kStages], (last / kStages) & 1)) abort_flag = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -575,8 +608,10 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
     p.k_cap = (kTileRows + (kMmaK - 1) * G + kMmaK - 1) / kMmaK * kMmaK;
     p.a_bytes = p.k_cap * 64;
     p.b_bytes = p.k_cap * p.n_alloc;
-    const size_t smem = static_cast<size_t>(kStages) * (p.a_bytes + p.b_bytes);
+    size_t smem = static_cast<size_t>(kStages) * (p.a_bytes + p.b_bytes);
     if (smem > 220 * 1024) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path: tile does not fit shared memory");
+    // one CTA per SM: the CTA owns all 512 tensor-memory columns
+    if (smem < 120 * 1024) smem = 120 * 1024;
     const size_t acc_bytes = static_cast<size_t>(G) * kWorlds * p.n_alloc * 8;
     pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, acc_bytes + G * 8 + 1024);
     if (st != PAC_OK) return st;
@@ -586,10 +621,10 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
     PAC_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, cv.off, stream));
     if (c4 == 1) {
         PAC_CUDA(ctx, cudaFuncSetAttribute(k_agg_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k_agg_mma<1><<<static_cast<unsigned>(n_ctas), kThreads, smem, stream>>>(p);
+        k_agg_mma<1><<<static_cast<unsigned>(n_ctas), kThreads + 32, smem, stream>>>(p);
     } else {
         PAC_CUDA(ctx, cudaFuncSetAttribute(k_agg_mma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k_agg_mma<4><<<static_cast<unsigned>(n_ctas), kThreads, smem, stream>>>(p);
+        k_agg_mma<4><<<static_cast<unsigned>(n_ctas), kThreads + 32, smem, stream>>>(p);
     }
     PAC_CUDA(ctx, cudaGetLastError());
     FinishParams f{};
