@@ -41,9 +41,12 @@ namespace pacgpu {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 512;
-constexpr int kTileRows = kThreads;  // one row per thread per tile
-constexpr int kStages = 2;
+constexpr int kThreads = 512;        // producer threads
+constexpr int kMmaWarps = 4;         // warps issuing tcgen05.mma
+constexpr int kMaxSlots = 16;        // accumulator slots (one group each)
+constexpr int kRows = 2;             // rows per producer thread per tile
+constexpr int kTileRows = kThreads * kRows;
+constexpr int kStages = 1;
 constexpr int kMmaK = 32;               // rows per tcgen05.mma of 8-bit operands
 constexpr int kMaxGroups = 8;
 constexpr int kMaxCols = 4;
@@ -82,7 +85,7 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 // the warps it is waiting for.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     uint32_t done = 0;
-    uint32_t ns = 32;
+    uint32_t ns = 16;
     for (uint32_t it = 0; it < kWaitLimit; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -90,8 +93,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
-        __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (it >= 32) {
+            __nanosleep(ns);
+            if (ns < 128) ns <<= 1;
+        }
     }
     return false;
 }
@@ -189,25 +194,27 @@ __device__ __forceinline__ void write_features(uint32_t b_stage, uint32_t slot, 
     for (int h = 0; h < F::kN / 16; h++) sts128(base + h * 128, w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3]);
 }
 
+// Digit classes: C4 = 4 uses 4, 6, 8 or 16 digits; C4 = 1 uses 12 or 16.
 template <int C4>
 __device__ __forceinline__ void write_features_l(int L, uint32_t b_stage, uint32_t slot, long long v0, long long v1,
                                                  long long v2, long long v3, bool sgn) {
-    switch (L) {
-    case 2: write_features<C4, 2>(b_stage, slot, v0, v1, v2, v3, sgn); break;
-    case 4: write_features<C4, 4>(b_stage, slot, v0, v1, v2, v3, sgn); break;
-    case 6: write_features<C4, 6>(b_stage, slot, v0, v1, v2, v3, sgn); break;
-    case 8: write_features<C4, 8>(b_stage, slot, v0, v1, v2, v3, sgn); break;
-    case 12: write_features<C4, 12>(b_stage, slot, v0, v1, v2, v3, sgn); break;
-    default: write_features<C4, 16>(b_stage, slot, v0, v1, v2, v3, sgn); break;
+    if (C4 == 1) {
+        if (L <= 12) write_features<C4, 12>(b_stage, slot, v0, v1, v2, v3, sgn);
+        else write_features<C4, 16>(b_stage, slot, v0, v1, v2, v3, sgn);
+    } else {
+        if (L <= 4) write_features<C4, 4>(b_stage, slot, v0, v1, v2, v3, sgn);
+        else if (L <= 6) write_features<C4, 6>(b_stage, slot, v0, v1, v2, v3, sgn);
+        else if (L <= 8) write_features<C4, 8>(b_stage, slot, v0, v1, v2, v3, sgn);
+        else write_features<C4, 16>(b_stage, slot, v0, v1, v2, v3, sgn);
     }
 }
 
+template <int C4>
 __device__ __forceinline__ int digit_class(int need) {
-    if (need <= 2) return 2;
+    if (C4 == 1) return need <= 12 ? 12 : 16;
     if (need <= 4) return 4;
     if (need <= 6) return 6;
     if (need <= 8) return 8;
-    if (need <= 12) return 12;
     return 16;
 }
 
@@ -218,7 +225,15 @@ struct RawRow {
     long long v0, v1, v2, v3;
 };
 
-template <int C4>
+template <int GB>
+__device__ __forceinline__ uint32_t gid_load(const void *gids, uint64_t row) {
+    if (GB == 1) return __ldg(static_cast<const unsigned char *>(gids) + row);
+    if (GB == 2) return __ldg(static_cast<const unsigned short *>(gids) + row);
+    if (GB == 4) return __ldg(static_cast<const unsigned int *>(gids) + row);
+    return 0;
+}
+
+template <int C4, int GB>
 __device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin, uint32_t off, bool ok, RawRow &r) {
     r.km = 0;
     r.gid = 0xFFFFFFFFu;
@@ -226,7 +241,7 @@ __device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin,
     if (!ok) return;
     const uint64_t row = cta_begin + off;
     r.km = __ldg(static_cast<const unsigned long long *>(p.in.km) + row);
-    r.gid = row_gid(p.in, row);
+    r.gid = gid_load<GB>(p.in.gids, row);
     if (p.n_cols > 0) r.v0 = __ldg(p.col[0] + row);
     if (C4 == 4) {
         if (p.n_cols > 1) r.v1 = __ldg(p.col[1] + row);
@@ -242,48 +257,263 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Warp-specialised CTA: warps 0..15 produce operands (one row per thread per
-// tile), warp 16 issues the tensor-core MMAs.  Producers agree on a tile's
-// layout through a producer-only named barrier; the stage ring is handed over
-// with mbarriers: full[s] (16 producer-warp arrivals) and empty[s] (arrived
-// by tcgen05.commit when the MMAs that read stage s are done).
-template <int C4>
-__global__ void __launch_bounds__(kThreads + 32, 1) k_agg_mma(const __grid_constant__ MmaParams p) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    constexpr int kWarps = kThreads / 32;  // producer warps
-    __shared__ __align__(8) uint64_t full_bar[kStages];
-    __shared__ __align__(8) uint64_t empty_bar[kStages];
-    __shared__ uint32_t tmem_slot;
-    __shared__ uint32_t st_cnt[2][kWarps][kMaxGroups];  // by tile parity
-    __shared__ uint32_t st_mag[2][kWarps][2];
-    __shared__ uint32_t meta_lo[kStages][kMaxGroups], meta_len[kStages][kMaxGroups];
-    __shared__ int meta_n[kStages];
-    __shared__ unsigned long long ng_acc[kMaxGroups];
-    __shared__ int abort_flag;
+// Shared state of one CTA of the tensor-core aggregation.
+struct MmaShared {
+    uint64_t full_bar;   // producers -> MMA warps: the stage holds a tile
+    uint64_t empty_bar;  // MMA warps (tcgen05.commit) -> producers: the stage is free
+    uint32_t tmem_slot;
+    int abort_flag;
+    uint32_t st_cnt[2][kThreads / 32][kMaxGroups];  // per producer warp, by tile parity
+    uint32_t st_mag[2][kThreads / 32][2];
+    uint32_t meta_lo[kMaxGroups], meta_len[kMaxGroups];
+    int meta_n;
+    unsigned long long ng_acc[kMaxGroups];
+    // accumulator slots: slot s holds group sl_group[s], is fed by MMA warp
+    // sl_warp[s] and takes the group's 32-row blocks with index = sl_idx[s]
+    // modulo grp_nslot[g]
+    int n_slots;
+    uint8_t sl_group[kMaxSlots], sl_warp[kMaxSlots], sl_idx[kMaxSlots], grp_nslot[kMaxGroups];
+};
 
+// Slot plan from the first tile's group counts: one slot per group, spare
+// slots to the groups with most rows per slot, slots dealt to the MMA warps
+// heaviest first.  One thread.
+__device__ void plan_slots(MmaShared &sh, uint32_t G, uint32_t max_slots, const uint32_t *cnt) {
+    uint32_t ns[kMaxGroups];
+    for (uint32_t g = 0; g < kMaxGroups; g++) ns[g] = g < G ? 1u : 0u;
+    for (uint32_t e = G; e < max_slots; e++) {
+        uint32_t best = 0;
+        for (uint32_t g = 1; g < G; g++)
+            if (static_cast<unsigned long long>(cnt[g] + 1) * ns[best] >
+                static_cast<unsigned long long>(cnt[best] + 1) * ns[g])
+                best = g;
+        ns[best]++;
+    }
+    int sl = 0;
+    for (uint32_t g = 0; g < G; g++) {
+        sh.grp_nslot[g] = static_cast<uint8_t>(ns[g]);
+        for (uint32_t k = 0; k < ns[g]; k++, sl++) {
+            sh.sl_group[sl] = static_cast<uint8_t>(g);
+            sh.sl_idx[sl] = static_cast<uint8_t>(k);
+        }
+    }
+    sh.n_slots = sl;
+    uint32_t load[kMmaWarps] = {0, 0, 0, 0};
+    int held[kMmaWarps] = {0, 0, 0, 0};
+    bool dealt[kMaxSlots] = {};
+    for (int r = 0; r < sl; r++) {
+        int pick = -1;
+        uint32_t wmax = 0;
+        for (int t = 0; t < sl; t++) {
+            const uint32_t w = (cnt[sh.sl_group[t]] + 1) / ns[sh.sl_group[t]];
+            if (!dealt[t] && (pick < 0 || w > wmax)) {
+                pick = t;
+                wmax = w;
+            }
+        }
+        // lightest warp that still has room (a warp keeps at most
+        // kMaxSlots / kMmaWarps slots in registers)
+        int lw = -1;
+        for (int q = 0; q < kMmaWarps; q++)
+            if (held[q] < kMaxSlots / kMmaWarps && (lw < 0 || load[q] < load[lw])) lw = q;
+        dealt[pick] = true;
+        sh.sl_warp[pick] = static_cast<uint8_t>(lw);
+        load[lw] += wmax;
+        held[lw]++;
+    }
+}
+
+// One tile of the producer warps: statistics, layout, operands.
+template <int C4>
+__device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, uint32_t it, uint32_t max_slots,
+                                             const RawRow &r0, const RawRow &r1, uint32_t a_stage, uint32_t b_stage,
+                                             bool keys_in, bool balanced_keys) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kThreads / 32;
     const uint32_t G = p.in.n_groups;
     const uint32_t lt = (1u << lane) - 1u;
+    const int pb = it & 1;
+
+    // (1) group, world mask, magnitude and sign statistics of the rows
+    uint32_t gid[kRows], lo32[kRows], hi32[kRows];
+    bool valid[kRows];
+    unsigned long long mag = 0, sgnbits = 0;
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+        const RawRow &c = r == 0 ? r0 : r1;
+        gid[r] = c.gid;
+        valid[r] = gid[r] != 0xFFFFFFFFu;
+        if (valid[r] && gid[r] >= G) {  // out-of-range group id: skip the row, report it
+            raise_status(p.status, kStatusBadGroup);
+            valid[r] = false;
+            gid[r] = 0xFFFFFFFFu;
+        }
+        lo32[r] = 0;
+        hi32[r] = 0;
+        if (valid[r]) {
+            const uint64_t m = keys_in ? keyed_world_mask(static_cast<long long>(c.km), p.in.qkey, p.in.hash_mode) : c.km;
+            lo32[r] = static_cast<uint32_t>(m);
+            hi32[r] = static_cast<uint32_t>(m >> 32);
+        }
+        // OR of |v| in one's complement (v, or ~v for v < 0) bounds every
+        // value's bit length; the sign bits say whether any is negative
+        mag |= static_cast<unsigned long long>(c.v0 ^ (c.v0 >> 63));
+        sgnbits |= static_cast<unsigned long long>(c.v0);
+        if (C4 == 4) {
+            mag |= static_cast<unsigned long long>(c.v1 ^ (c.v1 >> 63));
+            mag |= static_cast<unsigned long long>(c.v2 ^ (c.v2 >> 63));
+            mag |= static_cast<unsigned long long>(c.v3 ^ (c.v3 >> 63));
+            sgnbits |= static_cast<unsigned long long>(c.v1 | c.v2 | c.v3);
+        }
+    }
+    // (2) per-group ballots of the warp's rows: counts and ranks
+    uint32_t rank[kRows] = {0, 0};
+    uint32_t my_cnt = 0;  // lane g: this warp's rows of group g
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; g++) {
+        if (g < static_cast<int>(G)) {
+            const uint32_t b0 = __ballot_sync(kFull, gid[0] == static_cast<uint32_t>(g));
+            const uint32_t b1 = __ballot_sync(kFull, gid[1] == static_cast<uint32_t>(g));
+            const uint32_t c0 = __popc(b0);
+            if (gid[0] == static_cast<uint32_t>(g)) rank[0] = __popc(b0 & lt);
+            if (gid[1] == static_cast<uint32_t>(g)) rank[1] = c0 + __popc(b1 & lt);
+            if (lane == g) my_cnt = c0 + __popc(b1);
+        }
+    }
+    if (lane < kMaxGroups) sh.st_cnt[pb][warp][lane] = my_cnt;
+    const uint32_t mag_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(mag >> 32));
+    const uint32_t mag_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(mag));
+    const uint32_t any_neg = __reduce_or_sync(kFull, static_cast<uint32_t>(sgnbits >> 63));
+    if (lane == 0) {
+        sh.st_mag[pb][warp][0] = mag_hi | (any_neg << 31);  // bit 63 of a magnitude is never set
+        sh.st_mag[pb][warp][1] = mag_lo;
+    }
+    producers_sync();
+    // (3) every warp derives the tile layout: group runs, its own offsets, digits
+    uint32_t cnt = 0, before = 0;
+    if (lane < kMaxGroups) {
+        uint32_t c[kWarps];
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) c[w] = sh.st_cnt[pb][w][lane];
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) {
+            cnt += c[w];
+            before += w < warp ? c[w] : 0u;
+        }
+    }
+    uint32_t oh = lane < kWarps ? sh.st_mag[pb][lane][0] : 0u;
+    uint32_t ol = lane < kWarps ? sh.st_mag[pb][lane][1] : 0u;
+    oh = __reduce_or_sync(kFull, oh);
+    ol = __reduce_or_sync(kFull, ol);
+    const uint32_t len = (cnt + kMmaK - 1) & ~static_cast<uint32_t>(kMmaK - 1);
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < kMaxGroups; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t glo = incl - len;
+    const bool neg = (oh >> 31) != 0;
+    const uint32_t mh = oh & 0x7FFFFFFFu;
+    const int bits = mh ? 64 - __clz(static_cast<int>(mh)) : (ol ? 32 - __clz(static_cast<int>(ol)) : 0);
+    const int L = digit_class<C4>(neg ? (bits + 4) / 4 : (bits + 3) / 4);
+    const int N = C4 == 1 ? round16(4 + L) : round16(4 + L * 4);
+    const uint32_t base = glo + before;  // lane g: this warp's first slot in group g
+    uint32_t slot[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; r++) slot[r] = __shfl_sync(kFull, base, valid[r] ? static_cast<int>(gid[r]) : 0) + rank[r];
+    // (4) the stage must be free: the MMAs of the previous tile are done
+    if (it > 0) {
+        if (lane == 0 && !mbar_wait(&sh.empty_bar, (it - 1) & 1)) sh.abort_flag = 1;
+        __syncwarp();
+    }
+    if (warp == 0) {
+        if (lane < static_cast<int>(G)) {
+            sh.meta_lo[lane] = glo;
+            sh.meta_len[lane] = len;
+            sh.ng_acc[lane] += cnt;
+        }
+        if (lane == 0) sh.meta_n = N;
+        if (it == 0) {
+            uint32_t cg[kMaxGroups];
+#pragma unroll
+            for (int g = 0; g < kMaxGroups; g++) cg[g] = __shfl_sync(kFull, cnt, g);
+            if (lane == 0) plan_slots(sh, G, max_slots, cg);
+        }
+    }
+    // (5) operands into the stage, rows sorted by group
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+        if (!valid[r]) continue;
+        const RawRow &c = r == 0 ? r0 : r1;
+        const uint32_t x = lo32[r];
+        const uint32_t a_row = a_stage + (slot[r] >> 3) * 512 + (slot[r] & 7) * 16;
+        const uint32_t w0 = spread4(x & 0xF), w1 = spread4((x >> 4) & 0xF);
+        const uint32_t w2 = spread4((x >> 8) & 0xF), w3 = spread4((x >> 12) & 0xF);
+        const uint32_t w4 = spread4((x >> 16) & 0xF), w5 = spread4((x >> 20) & 0xF);
+        const uint32_t w6 = spread4((x >> 24) & 0xF), w7 = spread4(x >> 28);
+        sts128(a_row, w0, w1, w2, w3);
+        sts128(a_row + 128, w4, w5, w6, w7);
+        if (balanced_keys) {
+            // worlds 32..63 are the complement of worlds 0..31
+            constexpr uint32_t k1 = 0x01010101u;
+            sts128(a_row + 256, w0 ^ k1, w1 ^ k1, w2 ^ k1, w3 ^ k1);
+            sts128(a_row + 384, w4 ^ k1, w5 ^ k1, w6 ^ k1, w7 ^ k1);
+        } else {
+            write_bits16(a_row + 256, hi32[r] & 0xFFFFu);
+            write_bits16(a_row + 384, hi32[r] >> 16);
+        }
+        write_features_l<C4>(L, b_stage, slot[r], c.v0, c.v1, c.v2, c.v3, neg);
+    }
+    // zero the rows that pad each group's run to the MMA step (warp g: group g)
+    if (warp < static_cast<int>(G)) {
+        const uint32_t gcnt = __shfl_sync(kFull, cnt, warp), glen = __shfl_sync(kFull, len, warp);
+        const uint32_t gl = __shfl_sync(kFull, glo, warp);
+        if (static_cast<uint32_t>(lane) < glen - gcnt) {
+            const uint32_t ps = gl + gcnt + lane;
+            const uint32_t a_row = a_stage + (ps >> 3) * 512 + (ps & 7) * 16;
+            for (int h = 0; h < 4; h++) sts128(a_row + h * 128, 0, 0, 0, 0);
+            const uint32_t b_row = b_stage + (ps >> 3) * ((N / 16) * 128) + (ps & 7) * 16;
+            for (int h = 0; h < N / 16; h++) sts128(b_row + h * 128, 0, 0, 0, 0);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sh.full_bar);
+}
+
+// Warp-specialised CTA: warps 0..15 produce operands (two rows per thread per
+// tile), warps 16..19 issue the tensor-core MMAs, each into its own
+// accumulator slots.  Producers agree on a tile's layout through a
+// producer-only named barrier; the single operand stage is handed over with
+// two mbarriers (full: 16 producer-warp arrivals; empty: one tcgen05.commit
+// per MMA warp).
+template <int C4, int GB>
+__global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const __grid_constant__ MmaParams p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ MmaShared sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kThreads / 32;
+    const uint32_t G = p.in.n_groups;
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; s++) {
-            mbar_init(&full_bar[s], kWarps);
-            mbar_init(&empty_bar[s], 1);
-        }
+        mbar_init(&sh.full_bar, kWarps);
+        mbar_init(&sh.empty_bar, kMmaWarps);
         asm volatile("fence.mbarrier_init.release.cluster;");
-        abort_flag = 0;
+        sh.abort_flag = 0;
     }
-    if (tid < kMaxGroups) ng_acc[tid] = 0;
+    if (tid < kMaxGroups) sh.ng_acc[tid] = 0;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = tmem_slot;
-    const uint32_t used_cols = G * static_cast<uint32_t>(p.n_alloc);
+    const uint32_t tmem = sh.tmem_slot;
+    const uint32_t max_slots = min(static_cast<uint32_t>(kMaxSlots), kTmemCols / static_cast<uint32_t>(p.n_alloc));
+    const uint32_t used_cols = max_slots * static_cast<uint32_t>(p.n_alloc);
     if (warp < 4) {  // zero the accumulators (warps 0-3 own TMEM lane quadrants 0-3)
         const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
         for (uint32_t c0 = 0; c0 < used_cols; c0 += 16) {
@@ -302,180 +532,122 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_agg_mma(const __grid_const
     const uint64_t end = min(p.in.n, begin + p.rows_per_cta);
     const uint32_t n_rows = static_cast<uint32_t>(end - begin);
     const uint32_t n_tiles = (n_rows + kTileRows - 1) / kTileRows;
-    const uint32_t smem_base = smem_u32(smem);
+    const uint32_t a_stage = smem_u32(smem);
+    const uint32_t b_stage = a_stage + p.a_bytes;
 
-    if (warp == kWarps) {
-        // ---------------- MMA warp ----------------
+    if (warp >= kWarps) {
+        // ---------------- MMA warps ----------------
+        const int mw = warp - kWarps;
+        // this warp's slots (known after the first tile): up to 4 cached in registers
+        int my_n = 0;
+        uint32_t my_sl[kMaxSlots / kMmaWarps], my_g[kMaxSlots / kMmaWarps], my_idx[kMaxSlots / kMmaWarps],
+            my_share[kMaxSlots / kMmaWarps];
         for (uint32_t it = 0; it < n_tiles; it++) {
-            const int s = it % kStages;
             if (lane == 0) {
-                if (!mbar_wait(&full_bar[s], (it / kStages) & 1)) abort_flag = 1;
+                if (!mbar_wait(&sh.full_bar, it & 1)) sh.abort_flag = 1;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
-                const uint32_t b_stage = a_stage + p.a_bytes;
-                const int N = meta_n[s];
+                if (it == 0) {
+                    // the k-th slot dealt to this warp goes to register set k
+                    // (compile-time indices keep the sets in registers)
+#pragma unroll
+                    for (int k = 0; k < kMaxSlots / kMmaWarps; k++) my_sl[k] = my_g[k] = my_idx[k] = my_share[k] = 0;
+                    int found = 0;
+#pragma unroll
+                    for (int sl = 0; sl < kMaxSlots; sl++) {
+                        const bool mine = sl < sh.n_slots && sh.sl_warp[sl] == mw;
+#pragma unroll
+                        for (int k = 0; k < kMaxSlots / kMmaWarps; k++) {
+                            if (mine && found == k) {
+                                my_sl[k] = static_cast<uint32_t>(sl);
+                                my_g[k] = sh.sl_group[sl];
+                                my_idx[k] = sh.sl_idx[sl];
+                                my_share[k] = sh.grp_nslot[sh.sl_group[sl]];
+                            }
+                        }
+                        found += mine ? 1 : 0;
+                    }
+                    my_n = found < kMaxSlots / kMmaWarps ? found : kMaxSlots / kMmaWarps;
+                }
+                const int N = sh.meta_n;
                 const uint32_t idesc = instr_desc(N);
                 const uint32_t lbo_b = (N / 16) * 128;
-                for (uint32_t g = 0; g < G; g++) {
-                    const uint32_t d = tmem + g * static_cast<uint32_t>(p.n_alloc);
-                    const uint32_t k_lo = meta_lo[s][g], k_hi = k_lo + meta_len[s][g];
-                    for (uint32_t k0 = k_lo; k0 < k_hi; k0 += kMmaK) {
-                        const uint64_t da = smem_desc(a_stage + (k0 >> 3) * 512, 512, 128);
-                        const uint64_t db = smem_desc(b_stage + (k0 >> 3) * lbo_b, lbo_b, 128);
+                // descriptors of slot 0; one 32-row block moves the start address
+                // (in 16-byte units) by 4*512/16 for A and 4*lbo_b/16 for B
+                const uint64_t da0 = smem_desc(a_stage, 512, 128);
+                const uint64_t db0 = smem_desc(b_stage, lbo_b, 128);
+                const uint32_t step_b = lbo_b >> 2;
+                uint32_t lo[kMaxSlots / kMmaWarps], nb[kMaxSlots / kMmaWarps];
+#pragma unroll
+                for (int k = 0; k < kMaxSlots / kMmaWarps; k++) {
+                    if (k < my_n) {
+                        lo[k] = sh.meta_lo[my_g[k]];
+                        nb[k] = sh.meta_len[my_g[k]] / kMmaK;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kMaxSlots / kMmaWarps; k++) {
+                    if (k >= my_n) continue;
+                    const uint32_t d = tmem + my_sl[k] * static_cast<uint32_t>(p.n_alloc);
+                    const uint32_t blk0 = (lo[k] >> 5) + my_idx[k];
+                    const uint32_t blk_end = (lo[k] >> 5) + nb[k];
+                    uint64_t da = da0 + blk0 * 128u;
+                    uint64_t db = db0 + blk0 * step_b;
+                    const uint64_t sa = 128ull * my_share[k], sb = static_cast<uint64_t>(step_b) * my_share[k];
+                    for (uint32_t blk = blk0; blk < blk_end; blk += my_share[k]) {
                         mma_f8(d, da, db, idesc);
+                        da += sa;
+                        db += sb;
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&empty_bar[s])));
+                    smem_u32(&sh.empty_bar)));
             }
             __syncwarp();
         }
-        // drain: the last commit covers every MMA issued before it
+        // drain: every MMA warp's last commit has arrived once the last phase completes
         if (lane == 0 && n_tiles > 0) {
-            const uint32_t last = n_tiles - 1;
-            if (!mbar_wait(&empty_bar[last % kStages], (last / kStages) & 1)) abort_flag = 1;
+            if (!mbar_wait(&sh.empty_bar, (n_tiles - 1) & 1)) sh.abort_flag = 1;
         }
         __syncwarp();
     } else {
         // ---------------- producer warps ----------------
+        // two register sets of raw rows, each reloaded right after its tile
+        // is produced, so a load has a whole tile of work to arrive in
         const bool keys_in = !(p.in.in_flags & PAC_IN_MASKS);
         const bool balanced_keys = keys_in && p.in.hash_mode == PAC_HASH_BALANCED;
-        RawRow nx0, nx1;  // tiles it and it+1
-        load_raw<C4>(p, begin, static_cast<uint32_t>(tid), static_cast<uint32_t>(tid) < n_rows, nx0);
-        load_raw<C4>(p, begin, kTileRows + tid, kTileRows + static_cast<uint32_t>(tid) < n_rows, nx1);
-        for (uint32_t it = 0; it < n_tiles; it++) {
-            const int s = it % kStages;
-            const int pb = it & 1;
-            const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
-            const uint32_t b_stage = a_stage + p.a_bytes;
-            const RawRow cur = nx0;
-            nx0 = nx1;
+        RawRow a0, a1, b0, b1;
+        const uint32_t t = static_cast<uint32_t>(tid);
+        load_raw<C4, GB>(p, begin, t, t < n_rows, a0);
+        load_raw<C4, GB>(p, begin, kThreads + t, kThreads + t < n_rows, a1);
+        load_raw<C4, GB>(p, begin, kTileRows + t, kTileRows + t < n_rows, b0);
+        load_raw<C4, GB>(p, begin, kTileRows + kThreads + t, kTileRows + kThreads + t < n_rows, b1);
+        for (uint32_t it = 0; it < n_tiles; it += 2) {
+            produce_tile<C4>(p, sh, it, max_slots, a0, a1, a_stage, b_stage, keys_in, balanced_keys);
             {
-                const uint32_t off = (it + 2) * kTileRows + tid;
-                load_raw<C4>(p, begin, off, it + 2 < n_tiles && off < n_rows, nx1);
+                const uint32_t off = (it + 2) * kTileRows + t;
+                load_raw<C4, GB>(p, begin, off, off < n_rows, a0);
+                load_raw<C4, GB>(p, begin, off + kThreads, off + kThreads < n_rows, a1);
             }
-            // (1) this row: group, world mask, magnitude and sign statistics
-            uint32_t gid = cur.gid;
-            bool valid = gid != 0xFFFFFFFFu;
-            if (valid && gid >= G) {  // out-of-range group id: skip the row, report it
-                raise_status(p.status, kStatusBadGroup);
-                valid = false;
-                gid = 0xFFFFFFFFu;
+            if (it + 1 < n_tiles) {
+                produce_tile<C4>(p, sh, it + 1, max_slots, b0, b1, a_stage, b_stage, keys_in, balanced_keys);
+                const uint32_t off = (it + 3) * kTileRows + t;
+                load_raw<C4, GB>(p, begin, off, off < n_rows, b0);
+                load_raw<C4, GB>(p, begin, off + kThreads, off + kThreads < n_rows, b1);
             }
-            uint32_t lo32 = 0, hi32 = 0;
-            if (valid) {
-                const uint64_t m = keys_in ? keyed_world_mask(static_cast<long long>(cur.km), p.in.qkey, p.in.hash_mode)
-                                           : cur.km;
-                lo32 = static_cast<uint32_t>(m);
-                hi32 = static_cast<uint32_t>(m >> 32);
-            }
-            // OR of |v| in one's complement (v, or ~v for v < 0) bounds every
-            // value's bit length; the sign bits say whether any is negative
-            unsigned long long mag = static_cast<unsigned long long>(cur.v0 ^ (cur.v0 >> 63));
-            unsigned long long sgnbits = static_cast<unsigned long long>(cur.v0);
-            if (C4 == 4) {
-                mag |= static_cast<unsigned long long>(cur.v1 ^ (cur.v1 >> 63));
-                mag |= static_cast<unsigned long long>(cur.v2 ^ (cur.v2 >> 63));
-                mag |= static_cast<unsigned long long>(cur.v3 ^ (cur.v3 >> 63));
-                sgnbits |= static_cast<unsigned long long>(cur.v1 | cur.v2 | cur.v3);
-            }
-            const uint32_t mag_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(mag >> 32));
-            const uint32_t mag_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(mag));
-            const uint32_t any_neg = __reduce_or_sync(kFull, static_cast<uint32_t>(sgnbits >> 63));
-            // (2) group rank inside the warp
-            const uint32_t peers = __match_any_sync(kFull, gid);
-            const uint32_t rank = __popc(peers & lt);
-            if (lane < kMaxGroups) st_cnt[pb][warp][lane] = 0;
-            __syncwarp();
-            if (valid && rank == 0) st_cnt[pb][warp][gid] = __popc(peers);
-            if (lane == 0) {
-                st_mag[pb][warp][0] = mag_hi | (any_neg << 31);  // bit 63 of a magnitude is never set
-                st_mag[pb][warp][1] = mag_lo;
-            }
-            producers_sync();
-            // (3) every warp derives the tile layout: group runs, its own offsets, digits
-            uint32_t cnt = 0, before = 0;
-            if (lane < static_cast<int>(G)) {
-                for (int w = 0; w < kWarps; w++) {
-                    const uint32_t c = st_cnt[pb][w][lane];
-                    cnt += c;
-                    before += w < warp ? c : 0u;
-                }
-            }
-            const uint32_t len = (cnt + kMmaK - 1) & ~static_cast<uint32_t>(kMmaK - 1);
-            uint32_t incl = len;
-            for (int o = 1; o < kMaxGroups; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const uint32_t glo = incl - len;
-            const uint32_t my_off = glo + before;  // lane g: this warp's first slot in group g
-            const uint32_t oh = __reduce_or_sync(kFull, lane < kWarps ? st_mag[pb][lane][0] : 0u);
-            const uint32_t ol = __reduce_or_sync(kFull, lane < kWarps ? st_mag[pb][lane][1] : 0u);
-            const bool neg = (oh >> 31) != 0;
-            const uint32_t mh = oh & 0x7FFFFFFFu;
-            const int bits = mh ? 64 - __clz(static_cast<int>(mh)) : (ol ? 32 - __clz(static_cast<int>(ol)) : 0);
-            const int L = digit_class(neg ? (bits + 4) / 4 : (bits + 3) / 4);
-            const int N = C4 == 1 ? round16(4 + L) : round16(4 + L * 4);
-            const uint32_t slot = __shfl_sync(kFull, my_off, valid ? static_cast<int>(gid) : 0) + rank;
-            // (4) the stage must be free: the MMAs of tile it - kStages are done
-            if (it >= kStages) {
-                if (lane == 0 && !mbar_wait(&empty_bar[s], ((it / kStages) - 1) & 1)) abort_flag = 1;
-                __syncwarp();
-            }
-            if (warp == 0 && lane < static_cast<int>(G)) {
-                meta_lo[s][lane] = glo;
-                meta_len[s][lane] = len;
-                ng_acc[lane] += cnt;
-                if (lane == 0) meta_n[s] = N;
-            }
-            // (5) operands into the stage, rows sorted by group
-            if (valid) {
-                const uint32_t a_row = a_stage + (slot >> 3) * 512 + (slot & 7) * 16;
-                const uint32_t w0 = spread4(lo32 & 0xF), w1 = spread4((lo32 >> 4) & 0xF);
-                const uint32_t w2 = spread4((lo32 >> 8) & 0xF), w3 = spread4((lo32 >> 12) & 0xF);
-                const uint32_t w4 = spread4((lo32 >> 16) & 0xF), w5 = spread4((lo32 >> 20) & 0xF);
-                const uint32_t w6 = spread4((lo32 >> 24) & 0xF), w7 = spread4(lo32 >> 28);
-                sts128(a_row, w0, w1, w2, w3);
-                sts128(a_row + 128, w4, w5, w6, w7);
-                if (balanced_keys) {
-                    // worlds 32..63 are the complement of worlds 0..31
-                    constexpr uint32_t k1 = 0x01010101u;
-                    sts128(a_row + 256, w0 ^ k1, w1 ^ k1, w2 ^ k1, w3 ^ k1);
-                    sts128(a_row + 384, w4 ^ k1, w5 ^ k1, w6 ^ k1, w7 ^ k1);
-                } else {
-                    write_bits16(a_row + 256, hi32 & 0xFFFFu);
-                    write_bits16(a_row + 384, hi32 >> 16);
-                }
-                write_features_l<C4>(L, b_stage, slot, cur.v0, cur.v1, cur.v2, cur.v3, neg);
-            }
-            // zero the rows that pad each group's run to the MMA step (warp g: group g)
-            if (warp < static_cast<int>(G)) {
-                const uint32_t gcnt = __shfl_sync(kFull, cnt, warp), glen = __shfl_sync(kFull, len, warp);
-                const uint32_t gl = __shfl_sync(kFull, glo, warp);
-                if (static_cast<uint32_t>(lane) < glen - gcnt) {
-                    const uint32_t ps = gl + gcnt + lane;
-                    const uint32_t a_row = a_stage + (ps >> 3) * 512 + (ps & 7) * 16;
-                    for (int h = 0; h < 4; h++) sts128(a_row + h * 128, 0, 0, 0, 0);
-                    const uint32_t b_row = b_stage + (ps >> 3) * ((N / 16) * 128) + (ps & 7) * 16;
-                    for (int h = 0; h < N / 16; h++) sts128(b_row + h * 128, 0, 0, 0, 0);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&full_bar[s]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (abort_flag) {
+    if (sh.abort_flag) {
         if (tid == 0) raise_status(p.status, kStatusTimeout);
     } else if (warp < 4) {
-        // read back: TMEM lane 32w + l (l < 16) holds world 16w + l
+        // read back: TMEM lane 32w + l (l < 16) holds world 16w + l; the slots
+        // of a group add into the same totals
         const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
         const int world = 16 * warp + lane;
-        for (uint32_t g = 0; g < G; g++) {
+        for (int sl = 0; sl < sh.n_slots; sl++) {
+            const uint32_t g = sh.sl_group[sl];
             for (int c0 = 0; c0 < p.n_alloc; c0 += 16) {
                 uint32_t r[16];
                 asm volatile(
@@ -483,7 +655,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_agg_mma(const __grid_const
                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                       "=r"(r[15])
-                    : "r"(tmem + lane_base + g * static_cast<uint32_t>(p.n_alloc) + c0));
+                    : "r"(tmem + lane_base + static_cast<uint32_t>(sl) * static_cast<uint32_t>(p.n_alloc) + c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 if (lane < 16) {
                     unsigned long long *dst = p.acc + (static_cast<size_t>(g) * kWorlds + world) * p.n_alloc + c0;
@@ -496,7 +668,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_agg_mma(const __grid_const
             }
         }
     }
-    if (tid < static_cast<int>(G) && ng_acc[tid]) atomicAdd(p.ng + tid, ng_acc[tid]);
+    if (tid < static_cast<int>(G) && sh.ng_acc[tid]) atomicAdd(p.ng + tid, sh.ng_acc[tid]);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
@@ -619,13 +791,31 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
     p.acc = static_cast<unsigned long long *>(cv.take(acc_bytes));
     p.ng = static_cast<unsigned long long *>(cv.take(G * 8));
     PAC_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, cv.off, stream));
+    const int gb = in->group_ids ? in->gid_bytes : 0;
+    cudaError_t e = cudaSuccess;
+#define PAC_MMA_LAUNCH(C4_, GB_)                                                                              \
+    do {                                                                                                      \
+        e = cudaFuncSetAttribute(k_agg_mma<C4_, GB_>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                 static_cast<int>(smem));                                                    \
+        if (e == cudaSuccess) k_agg_mma<C4_, GB_><<<static_cast<unsigned>(n_ctas), kThreads + 32 * kMmaWarps, smem, stream>>>(p); \
+    } while (0)
     if (c4 == 1) {
-        PAC_CUDA(ctx, cudaFuncSetAttribute(k_agg_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k_agg_mma<1><<<static_cast<unsigned>(n_ctas), kThreads + 32, smem, stream>>>(p);
+        switch (gb) {
+        case 1: PAC_MMA_LAUNCH(1, 1); break;
+        case 2: PAC_MMA_LAUNCH(1, 2); break;
+        case 4: PAC_MMA_LAUNCH(1, 4); break;
+        default: PAC_MMA_LAUNCH(1, 0); break;
+        }
     } else {
-        PAC_CUDA(ctx, cudaFuncSetAttribute(k_agg_mma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        k_agg_mma<4><<<static_cast<unsigned>(n_ctas), kThreads + 32, smem, stream>>>(p);
+        switch (gb) {
+        case 1: PAC_MMA_LAUNCH(4, 1); break;
+        case 2: PAC_MMA_LAUNCH(4, 2); break;
+        case 4: PAC_MMA_LAUNCH(4, 4); break;
+        default: PAC_MMA_LAUNCH(4, 0); break;
+        }
     }
+#undef PAC_MMA_LAUNCH
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");
     PAC_CUDA(ctx, cudaGetLastError());
     FinishParams f{};
     f.acc = p.acc;

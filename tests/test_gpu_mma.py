@@ -81,6 +81,19 @@ def test_mma_shapes(ctx, G, C, n):
     _check(ctx, keys, gids, G, _specs(vals), masks, qkey=qk)
 
 
+@pytest.mark.parametrize("C", [0, 1])
+def test_mma_eight_groups_skewed(ctx, C):
+    # eight groups with a heavy head: uneven accumulator slots across MMA warps
+    n = 250_003
+    r = np.random.default_rng(77 + C)
+    keys = r.integers(0, 20_000, n).astype(np.int64)
+    gids = np.minimum(r.geometric(0.45, n) - 1, 7).astype(np.uint8)
+    vals = [r.integers(0, 10**9, n).astype(np.int64) for _ in range(C)]
+    qk = orc.query_key(77)
+    masks = orc.hash_keys(keys, qk, orc.BALANCED)
+    _check(ctx, keys, gids, 8, _specs(vals), masks, qkey=qk)
+
+
 @pytest.mark.parametrize("dist", ["small", "cents", "big", "mixed", "wide", "zeros"])
 @pytest.mark.parametrize("C", [1, 4])
 def test_mma_value_ranges(ctx, dist, C):
