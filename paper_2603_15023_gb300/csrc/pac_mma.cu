@@ -751,14 +751,18 @@ bool mma_supported(const pac_input *in, const pac_agg_spec *specs, int n_specs) 
     return in->n_groups * static_cast<uint32_t>(n_alloc) <= kTmemCols;
 }
 
-pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
-                   cudaStream_t stream, int *launches) {
-    MmaParams p{};
-    const void *cols[kMaxCols];
-    int C = mma_columns(specs, n_specs, cols);
-    if (C < 0) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path: unsupported spec");
+// Builds the launch of the tensor-core path.  scratch: the accumulators
+// (mma_scratch_bytes bytes, cleared here); status: the device status word.
+static pac_status mma_plan(const pac_input *in, const pac_agg_spec *specs, int n_specs, int n_sms, MmaParams &p,
+                           size_t &smem, int &c4, const void **cols, int &C, const char **why) {
+    p = MmaParams{};
+    C = mma_columns(specs, n_specs, cols);
+    if (C < 0) {
+        *why = "tensor-core path: unsupported spec";
+        return PAC_E_UNSUPPORTED;
+    }
     const int Ceff = C == 0 ? 1 : C;  // COUNT only: one zero column
-    const int c4 = mma_c4(Ceff);
+    c4 = mma_c4(Ceff);
     p.in.km = in->keys_or_masks;
     p.in.gids = in->group_ids;
     p.in.qkey = in->query_key;
@@ -770,34 +774,59 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
     for (int c = 0; c < C; c++) p.col[c] = static_cast<const long long *>(cols[c]);
     p.n_cols = C;
     p.n_alloc = feat_alloc(Ceff);
-    p.status = ctx->d_status;
     const uint32_t G = in->n_groups;
-    uint64_t per = (in->n + ctx->n_sms - 1) / ctx->n_sms;
+    uint64_t per = (in->n + n_sms - 1) / n_sms;
     per = (per + kTileRows - 1) / kTileRows * kTileRows;
     if (per > kMaxRowsPerCta) per = kMaxRowsPerCta;
+    if (per == 0) per = kTileRows;
     p.rows_per_cta = static_cast<uint32_t>(per);
-    const uint64_t n_ctas = (in->n + per - 1) / per;
     p.k_cap = (kTileRows + (kMmaK - 1) * G + kMmaK - 1) / kMmaK * kMmaK;
     p.a_bytes = p.k_cap * 64;
     p.b_bytes = p.k_cap * p.n_alloc;
-    size_t smem = static_cast<size_t>(kStages) * (p.a_bytes + p.b_bytes);
-    if (smem > 220 * 1024) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path: tile does not fit shared memory");
+    smem = static_cast<size_t>(kStages) * (p.a_bytes + p.b_bytes);
+    if (smem > 220 * 1024) {
+        *why = "tensor-core path: tile does not fit shared memory";
+        return PAC_E_UNSUPPORTED;
+    }
     // one CTA per SM: the CTA owns all 512 tensor-memory columns
     if (smem < 120 * 1024) smem = 120 * 1024;
-    const size_t acc_bytes = static_cast<size_t>(G) * kWorlds * p.n_alloc * 8;
-    pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, acc_bytes + G * 8 + 1024);
+    return PAC_OK;
+}
+
+size_t mma_scratch_bytes(const pac_input *in, const pac_agg_spec *specs, int n_specs) {
+    const void *cols[kMaxCols];
+    const int C = mma_columns(specs, n_specs, cols);
+    const int Ceff = C <= 0 ? 1 : C;
+    return static_cast<size_t>(in->n_groups) * kWorlds * feat_alloc(Ceff) * 8 + 256 + in->n_groups * 8;
+}
+
+pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
+                      cudaStream_t stream, void *scratch, uint32_t *status, int n_sms, int *launches,
+                      const char **why) {
+    MmaParams p;
+    size_t smem;
+    int c4, C;
+    const void *cols[kMaxCols];
+    pac_status st = mma_plan(in, specs, n_specs, n_sms, p, smem, c4, cols, C, why);
     if (st != PAC_OK) return st;
-    Carver cv(ctx->ws);
-    p.acc = static_cast<unsigned long long *>(cv.take(acc_bytes));
-    p.ng = static_cast<unsigned long long *>(cv.take(G * 8));
-    PAC_CUDA(ctx, cudaMemsetAsync(ctx->ws, 0, cv.off, stream));
+    const uint32_t G = in->n_groups;
+    const uint64_t n_ctas = (in->n + p.rows_per_cta - 1) / p.rows_per_cta;
+    const size_t acc_bytes = static_cast<size_t>(G) * kWorlds * p.n_alloc * 8;
+    p.acc = static_cast<unsigned long long *>(scratch);
+    p.ng = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + ((acc_bytes + 255) / 256) * 256);
+    p.status = status;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, ((acc_bytes + 255) / 256) * 256 + G * 8, stream);
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return PAC_E_CUDA;
+    }
     const int gb = in->group_ids ? in->gid_bytes : 0;
-    cudaError_t e = cudaSuccess;
 #define PAC_MMA_LAUNCH(C4_, GB_)                                                                              \
     do {                                                                                                      \
         e = cudaFuncSetAttribute(k_agg_mma<C4_, GB_>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                  static_cast<int>(smem));                                                    \
-        if (e == cudaSuccess) k_agg_mma<C4_, GB_><<<static_cast<unsigned>(n_ctas), kThreads + 32 * kMmaWarps, smem, stream>>>(p); \
+        if (e == cudaSuccess)                                                                                 \
+            k_agg_mma<C4_, GB_><<<static_cast<unsigned>(n_ctas), kThreads + 32 * kMmaWarps, smem, stream>>>(p); \
     } while (0)
     if (c4 == 1) {
         switch (gb) {
@@ -815,8 +844,11 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
         }
     }
 #undef PAC_MMA_LAUNCH
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core aggregation launch");
-    PAC_CUDA(ctx, cudaGetLastError());
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return PAC_E_CUDA;
+    }
     FinishParams f{};
     f.acc = p.acc;
     f.ng = p.ng;
@@ -825,7 +857,7 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
     f.c4 = c4;
     f.n_alloc = p.n_alloc;
     f.meta = meta;
-    f.status = ctx->d_status;
+    f.status = status;
     for (int i = 0; i < n_specs; i++) {
         f.out_kind[f.n_out] = specs[i].kind;
         int c = 0;
@@ -836,8 +868,22 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
     }
     const size_t cells = static_cast<size_t>(G) * kWorlds;
     k_mma_finish<<<static_cast<unsigned>((cells + 255) / 256), 256, 0, stream>>>(f);
-    PAC_CUDA(ctx, cudaGetLastError());
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *why = cudaGetErrorString(e);
+        return PAC_E_CUDA;
+    }
     *launches += 3;  // memset + aggregation + finish
+    return PAC_OK;
+}
+
+pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
+                   cudaStream_t stream, int *launches) {
+    pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, mma_scratch_bytes(in, specs, n_specs) + 1024);
+    if (st != PAC_OK) return st;
+    const char *why = "";
+    st = mma_launch(in, specs, n_specs, meta, stream, ctx->ws, ctx->d_status, ctx->n_sms, launches, &why);
+    if (st != PAC_OK) return fail(ctx, st, "%s", why);
     return PAC_OK;
 }
 
