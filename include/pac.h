@@ -220,6 +220,39 @@ pac_status pac_query_host(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
                           double *noised, uint8_t *is_null, uint32_t *flags, pac_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * pac_aggregate_noalloc -- the paper has no counterpart: this is a service
+ * of the library for callers that cannot allocate device memory.
+ *
+ * Some callers cannot call cudaMalloc: code that runs under a memory pool
+ * owning all device memory (a database engine's buffer manager, a
+ * framework's caching allocator) and code with a device-memory budget fixed
+ * before it starts, where an allocation could fail or stall the device at
+ * the wrong time.  This entry point computes what pac_aggregate_multi
+ * computes for COUNT and exact int64 SUM/AVG specs (the tensor-core path:
+ * at most 4 distinct value columns and 8 groups) without any allocation:
+ * it never calls cudaMalloc, cudaFree or an allocating library routine and
+ * needs no pac_ctx.  Its scratch is a fixed 263,168-byte __device__ array
+ * (plus a 4-byte status word) that every GPU which loads the library holds
+ * until the process exits.
+ *   in, specs, n_specs, meta: as pac_aggregate_multi (HOST structs, DEVICE
+ *       buffers owned by the caller).
+ *   stream: work is enqueued on it; the call synchronises it before
+ *       returning, then returns the device status (PAC_E_OVERFLOW for an
+ *       int64 overflow, PAC_E_INVALID for a group id >= n_groups).
+ *   err, err_len: optional HOST buffer for a message (may be NULL).
+ * Returns PAC_E_UNSUPPORTED for specs the tensor-core path does not serve
+ * and PAC_E_INVALID when a query would need more than the static scratch.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and its contents persist between
+ * calls (each call clears what must start at zero): calls whose work
+ * overlaps on the same GPU (other host threads, other streams) race and must
+ * be serialised by the caller.
+ * ------------------------------------------------------------------------ */
+pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                                 uint64_t *meta, pac_stream stream, char *err, size_t err_len);
+
+/* ---------------------------------------------------------------------------
  * Path selection and introspection (for benchmarks and tests).
  *   pac_set_option(ctx, name, value): "agg_path" 0 = automatic (tensor-core
  *   path where it applies), 1 = force the per-bit CUDA-core path, 2 = force

@@ -29,7 +29,7 @@ PAC_MAX_SPECS = 16
 EXPORTED = (
     "pac_create", "pac_destroy", "pac_last_error", "pac_status_string", "pac_sync_status",
     "pac_query_key", "pac_hash_keys", "pac_aggregate", "pac_aggregate_multi", "pac_finalize",
-    "pac_query_host", "pac_set_option", "pac_get_info",
+    "pac_query_host", "pac_set_option", "pac_get_info", "pac_aggregate_noalloc",
 )
 
 
@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
                                  vp, vp, vp, vp]),
         "pac_set_option": (i32, [vp, ctypes.c_char_p, i64]),
         "pac_get_info": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(i64)]),
+        "pac_aggregate_noalloc": (i32, [ctypes.POINTER(PacInput), ctypes.POINTER(PacAggSpec), i32, vp, vp,
+                                        ctypes.c_char_p, sz]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -192,3 +194,11 @@ def pac_get_info(ctx: int, name: str) -> int:
     v = ctypes.c_int64(0)
     _check(ctx, lib().pac_get_info(ctx, name.encode(), ctypes.byref(v)))
     return v.value
+
+
+def pac_aggregate_noalloc(inp: PacInput, specs: ctypes.Array, n_specs: int, meta: int, stream: int = 0) -> None:
+    """The allocation-free aggregation (see include/pac.h); raises PacError."""
+    buf = ctypes.create_string_buffer(512)
+    st = lib().pac_aggregate_noalloc(ctypes.byref(inp), specs, n_specs, meta or None, stream, buf, len(buf))
+    if st != PAC_OK:
+        raise PacError(st, buf.value.decode())
