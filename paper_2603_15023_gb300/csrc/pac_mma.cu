@@ -41,12 +41,13 @@ namespace pacgpu {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 512;        // producer threads
+constexpr int kThreads = 512;        // producer threads: two groups of 8 warps
+constexpr int kGroupThreads = 256;   // one producer group
 constexpr int kMmaWarps = 4;         // warps issuing tcgen05.mma
 constexpr int kMaxSlots = 16;        // accumulator slots (one group each)
 constexpr int kRows = 2;             // rows per producer thread per tile
-constexpr int kTileRows = kThreads * kRows;
-constexpr int kStages = 1;
+constexpr int kTileRows = kGroupThreads * kRows;  // a producer group fills one stage per tile
+constexpr int kStages = 2;                        // one per producer group
 constexpr int kMmaK = 32;               // rows per tcgen05.mma of 8-bit operands
 constexpr int kMaxGroups = 8;
 constexpr int kMaxCols = 4;
@@ -233,41 +234,73 @@ __device__ __forceinline__ uint32_t gid_load(const void *gids, uint64_t row) {
     return 0;
 }
 
+// Loads row `off` of the CTA's range.  Rows past the end load the last row
+// instead (always in bounds) and come back with the invalid group id; value
+// columns beyond n_cols load column 0 and are zeroed.  No branches.
 template <int C4, int GB>
-__device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin, uint32_t off, bool ok, RawRow &r) {
-    r.km = 0;
-    r.gid = 0xFFFFFFFFu;
-    r.v0 = r.v1 = r.v2 = r.v3 = 0;
-    if (!ok) return;
-    const uint64_t row = cta_begin + off;
+__device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin, uint32_t off, uint32_t n_rows,
+                                         RawRow &r) {
+    const bool ok = off < n_rows;
+    const uint64_t row = cta_begin + (ok ? off : n_rows - 1);
     r.km = __ldg(static_cast<const unsigned long long *>(p.in.km) + row);
-    r.gid = gid_load<GB>(p.in.gids, row);
-    if (p.n_cols > 0) r.v0 = __ldg(p.col[0] + row);
+    const uint32_t g = gid_load<GB>(p.in.gids, row);
+    r.gid = ok ? g : 0xFFFFFFFFu;
+    const long long x0 = __ldg(p.col[0] + row);
+    r.v0 = p.n_cols > 0 ? x0 : 0;
     if (C4 == 4) {
-        if (p.n_cols > 1) r.v1 = __ldg(p.col[1] + row);
-        if (p.n_cols > 2) r.v2 = __ldg(p.col[2] + row);
-        if (p.n_cols > 3) r.v3 = __ldg(p.col[3] + row);
+        const long long x1 = __ldg(p.col[1] + row);
+        const long long x2 = __ldg(p.col[2] + row);
+        const long long x3 = __ldg(p.col[3] + row);
+        r.v1 = p.n_cols > 1 ? x1 : 0;
+        r.v2 = p.n_cols > 2 ? x2 : 0;
+        r.v3 = p.n_cols > 3 ? x3 : 0;
+    } else {
+        r.v1 = r.v2 = r.v3 = 0;
     }
 }
 
-// Named barrier among the producer warps only.
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+// Both rows of a thread under one dispatch on the tile's digit class.
+template <int C4>
+__device__ __forceinline__ void write_features_2rows(int L, uint32_t b_stage, uint32_t s0, uint32_t s1,
+                                                     const RawRow &r0, const RawRow &r1, bool sgn) {
+#define PAC_FEAT2(LL)                                                                        \
+    do {                                                                                     \
+        write_features<C4, LL>(b_stage, s0, r0.v0, r0.v1, r0.v2, r0.v3, sgn);                 \
+        write_features<C4, LL>(b_stage, s1, r1.v0, r1.v1, r1.v2, r1.v3, sgn);                 \
+    } while (0)
+    if (C4 == 1) {
+        if (L <= 12) PAC_FEAT2(12);
+        else PAC_FEAT2(16);
+    } else {
+        if (L <= 4) PAC_FEAT2(4);
+        else if (L <= 6) PAC_FEAT2(6);
+        else if (L <= 8) PAC_FEAT2(8);
+        else PAC_FEAT2(16);
+    }
+#undef PAC_FEAT2
+}
+
+// Named barrier among the warps of one producer group (ids 1 and 2).
+__device__ __forceinline__ void producers_sync(int pg) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + pg), "n"(kGroupThreads) : "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Shared state of one CTA of the tensor-core aggregation.
+// Shared state of one CTA of the tensor-core aggregation.  Producer group g
+// (warps 8g..8g+7) fills stage g with the tiles it = g, g+2, g+4, ...
 struct MmaShared {
-    uint64_t full_bar;   // producers -> MMA warps: the stage holds a tile
-    uint64_t empty_bar;  // MMA warps (tcgen05.commit) -> producers: the stage is free
+    uint64_t full_bar[kStages];   // producers -> MMA warps: the stage holds a tile
+    uint64_t empty_bar[kStages];  // MMA warps (tcgen05.commit) -> producers: the stage is free
     uint32_t tmem_slot;
     int abort_flag;
-    uint32_t st_cnt[2][kThreads / 32][kMaxGroups];  // per producer warp, by tile parity
-    uint32_t st_mag[2][kThreads / 32][2];
-    uint32_t meta_lo[kMaxGroups], meta_len[kMaxGroups];
-    int meta_n;
-    unsigned long long ng_acc[kMaxGroups];
+    uint32_t st_cnt[kStages][2][kGroupThreads / 32][kMaxGroups];  // per group, tile parity, warp
+    uint32_t st_mag[kStages][2][kGroupThreads / 32][2];
+    uint32_t meta_lo[kStages][kMaxGroups], meta_len[kStages][kMaxGroups];
+    int meta_n[kStages];
+    unsigned long long ng_acc[kStages][kMaxGroups];
     // accumulator slots: slot s holds group sl_group[s], is fed by MMA warp
     // sl_warp[s] and takes the group's 32-row blocks with index = sl_idx[s]
     // modulo grp_nslot[g]
@@ -328,32 +361,34 @@ template <int C4>
 __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, uint32_t it, uint32_t max_slots,
                                              const RawRow &r0, const RawRow &r1, uint32_t a_stage, uint32_t b_stage,
                                              bool keys_in, bool balanced_keys) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kWarps = kThreads / 32;
+    const int lane = threadIdx.x & 31;
+    constexpr int kWarps = kGroupThreads / 32;
+    const int pg = static_cast<int>(it & 1);                 // producer group = stage
+    const int warp = (threadIdx.x >> 5) - pg * kWarps;       // warp within the group
     const uint32_t G = p.in.n_groups;
     const uint32_t lt = (1u << lane) - 1u;
-    const int pb = it & 1;
+    const int pb = (it >> 1) & 1;                            // the group's tile parity
 
     // (1) group, world mask, magnitude and sign statistics of the rows
     uint32_t gid[kRows], lo32[kRows], hi32[kRows];
     bool valid[kRows];
+    bool any_bad = false;
+    const bool raw_hash = p.in.hash_mode == PAC_HASH_RAW;
     unsigned long long mag = 0, sgnbits = 0;
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
         const RawRow &c = r == 0 ? r0 : r1;
         gid[r] = c.gid;
+        const bool bad = gid[r] != 0xFFFFFFFFu && gid[r] >= G;  // out-of-range group id: skip, report
+        any_bad |= bad;
+        gid[r] = bad ? 0xFFFFFFFFu : gid[r];
         valid[r] = gid[r] != 0xFFFFFFFFu;
-        if (valid[r] && gid[r] >= G) {  // out-of-range group id: skip the row, report it
-            raise_status(p.status, kStatusBadGroup);
-            valid[r] = false;
-            gid[r] = 0xFFFFFFFFu;
-        }
-        lo32[r] = 0;
-        hi32[r] = 0;
-        if (valid[r]) {
-            const uint64_t m = keys_in ? keyed_world_mask(static_cast<long long>(c.km), p.in.qkey, p.in.hash_mode) : c.km;
-            lo32[r] = static_cast<uint32_t>(m);
-            hi32[r] = static_cast<uint32_t>(m >> 32);
+        {
+            const uint64_t h = mm3_fmix64(mm3_fmix64(c.km) ^ p.in.qkey);
+            const uint32_t hl = static_cast<uint32_t>(h);
+            const uint32_t hh = raw_hash ? static_cast<uint32_t>(h >> 32) : ~hl;  // balanced: complement
+            lo32[r] = keys_in ? hl : static_cast<uint32_t>(c.km);
+            hi32[r] = keys_in ? hh : static_cast<uint32_t>(c.km >> 32);
         }
         // OR of |v| in one's complement (v, or ~v for v < 0) bounds every
         // value's bit length; the sign bits say whether any is negative
@@ -366,43 +401,47 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
             sgnbits |= static_cast<unsigned long long>(c.v1 | c.v2 | c.v3);
         }
     }
-    // (2) per-group ballots of the warp's rows: counts and ranks
-    uint32_t rank[kRows] = {0, 0};
-    uint32_t my_cnt = 0;  // lane g: this warp's rows of group g
-#pragma unroll
-    for (int g = 0; g < kMaxGroups; g++) {
-        if (g < static_cast<int>(G)) {
-            const uint32_t b0 = __ballot_sync(kFull, gid[0] == static_cast<uint32_t>(g));
-            const uint32_t b1 = __ballot_sync(kFull, gid[1] == static_cast<uint32_t>(g));
-            const uint32_t c0 = __popc(b0);
-            if (gid[0] == static_cast<uint32_t>(g)) rank[0] = __popc(b0 & lt);
-            if (gid[1] == static_cast<uint32_t>(g)) rank[1] = c0 + __popc(b1 & lt);
-            if (lane == g) my_cnt = c0 + __popc(b1);
-        }
+    // (2) ranks inside the warp: rows of one group get consecutive ranks,
+    // pass-0 rows first; leaders publish the warp's count per group
+    if (__any_sync(kFull, any_bad) && lane == 0) raise_status(p.status, kStatusBadGroup);
+    uint32_t rank[kRows];
+    {
+        uint32_t *cnt_row = sh.st_cnt[pg][pb][warp];
+        if (lane < kMaxGroups) cnt_row[lane] = 0;
+        __syncwarp();
+        const uint32_t peers0 = __match_any_sync(kFull, gid[0]);
+        rank[0] = __popc(peers0 & lt);
+        if (valid[0] && rank[0] == 0) cnt_row[gid[0]] = __popc(peers0);
+        __syncwarp();
+        const uint32_t peers1 = __match_any_sync(kFull, gid[1]);
+        const uint32_t r1 = __popc(peers1 & lt);
+        const uint32_t before1 = valid[1] ? cnt_row[gid[1]] : 0u;
+        rank[1] = before1 + r1;
+        __syncwarp();
+        if (valid[1] && r1 == 0) cnt_row[gid[1]] = before1 + __popc(peers1);
     }
-    if (lane < kMaxGroups) sh.st_cnt[pb][warp][lane] = my_cnt;
     const uint32_t mag_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(mag >> 32));
     const uint32_t mag_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(mag));
     const uint32_t any_neg = __reduce_or_sync(kFull, static_cast<uint32_t>(sgnbits >> 63));
     if (lane == 0) {
-        sh.st_mag[pb][warp][0] = mag_hi | (any_neg << 31);  // bit 63 of a magnitude is never set
-        sh.st_mag[pb][warp][1] = mag_lo;
+        sh.st_mag[pg][pb][warp][0] = mag_hi | (any_neg << 31);  // bit 63 of a magnitude is never set
+        sh.st_mag[pg][pb][warp][1] = mag_lo;
     }
-    producers_sync();
+    producers_sync(pg);
     // (3) every warp derives the tile layout: group runs, its own offsets, digits
     uint32_t cnt = 0, before = 0;
     if (lane < kMaxGroups) {
         uint32_t c[kWarps];
 #pragma unroll
-        for (int w = 0; w < kWarps; w++) c[w] = sh.st_cnt[pb][w][lane];
+        for (int w = 0; w < kWarps; w++) c[w] = sh.st_cnt[pg][pb][w][lane];
 #pragma unroll
         for (int w = 0; w < kWarps; w++) {
             cnt += c[w];
             before += w < warp ? c[w] : 0u;
         }
     }
-    uint32_t oh = lane < kWarps ? sh.st_mag[pb][lane][0] : 0u;
-    uint32_t ol = lane < kWarps ? sh.st_mag[pb][lane][1] : 0u;
+    uint32_t oh = lane < kWarps ? sh.st_mag[pg][pb][lane][0] : 0u;
+    uint32_t ol = lane < kWarps ? sh.st_mag[pg][pb][lane][1] : 0u;
     oh = __reduce_or_sync(kFull, oh);
     ol = __reduce_or_sync(kFull, ol);
     const uint32_t len = (cnt + kMmaK - 1) & ~static_cast<uint32_t>(kMmaK - 1);
@@ -419,21 +458,25 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
     const int L = digit_class<C4>(neg ? (bits + 4) / 4 : (bits + 3) / 4);
     const int N = C4 == 1 ? round16(4 + L) : round16(4 + L * 4);
     const uint32_t base = glo + before;  // lane g: this warp's first slot in group g
+    // invalid rows (past the end of the range) go to a trash slot past k_cap
     uint32_t slot[kRows];
 #pragma unroll
-    for (int r = 0; r < kRows; r++) slot[r] = __shfl_sync(kFull, base, valid[r] ? static_cast<int>(gid[r]) : 0) + rank[r];
-    // (4) the stage must be free: the MMAs of the previous tile are done
-    if (it > 0) {
-        if (lane == 0 && !mbar_wait(&sh.empty_bar, (it - 1) & 1)) sh.abort_flag = 1;
+    for (int r = 0; r < kRows; r++) {
+        const uint32_t sv = __shfl_sync(kFull, base, valid[r] ? static_cast<int>(gid[r]) : 0) + rank[r];
+        slot[r] = valid[r] ? sv : p.k_cap;
+    }
+    // (4) the stage must be free: the MMAs of the group's previous tile are done
+    if (it >= kStages) {
+        if (lane == 0 && !mbar_wait(&sh.empty_bar[pg], ((it >> 1) - 1) & 1)) sh.abort_flag = 1;
         __syncwarp();
     }
     if (warp == 0) {
         if (lane < static_cast<int>(G)) {
-            sh.meta_lo[lane] = glo;
-            sh.meta_len[lane] = len;
-            sh.ng_acc[lane] += cnt;
+            sh.meta_lo[pg][lane] = glo;
+            sh.meta_len[pg][lane] = len;
+            sh.ng_acc[pg][lane] += cnt;
         }
-        if (lane == 0) sh.meta_n = N;
+        if (lane == 0) sh.meta_n[pg] = N;
         if (it == 0) {
             uint32_t cg[kMaxGroups];
 #pragma unroll
@@ -444,9 +487,7 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
     // (5) operands into the stage, rows sorted by group
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
-        if (!valid[r]) continue;
-        const RawRow &c = r == 0 ? r0 : r1;
-        const uint32_t x = lo32[r];
+        const uint32_t x = lo32[r], y = hi32[r];
         const uint32_t a_row = a_stage + (slot[r] >> 3) * 512 + (slot[r] & 7) * 16;
         const uint32_t w0 = spread4(x & 0xF), w1 = spread4((x >> 4) & 0xF);
         const uint32_t w2 = spread4((x >> 8) & 0xF), w3 = spread4((x >> 12) & 0xF);
@@ -460,11 +501,11 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
             sts128(a_row + 256, w0 ^ k1, w1 ^ k1, w2 ^ k1, w3 ^ k1);
             sts128(a_row + 384, w4 ^ k1, w5 ^ k1, w6 ^ k1, w7 ^ k1);
         } else {
-            write_bits16(a_row + 256, hi32[r] & 0xFFFFu);
-            write_bits16(a_row + 384, hi32[r] >> 16);
+            write_bits16(a_row + 256, y & 0xFFFFu);
+            write_bits16(a_row + 384, y >> 16);
         }
-        write_features_l<C4>(L, b_stage, slot[r], c.v0, c.v1, c.v2, c.v3, neg);
     }
+    write_features_2rows<C4>(L, b_stage, slot[0], slot[1], r0, r1, neg);
     // zero the rows that pad each group's run to the MMA step (warp g: group g)
     if (warp < static_cast<int>(G)) {
         const uint32_t gcnt = __shfl_sync(kFull, cnt, warp), glen = __shfl_sync(kFull, len, warp);
@@ -479,7 +520,7 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    if (lane == 0) mbar_arrive(&sh.full_bar);
+    if (lane == 0) mbar_arrive(&sh.full_bar[pg]);
 }
 
 // Warp-specialised CTA: warps 0..15 produce operands (two rows per thread per
@@ -497,12 +538,14 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
     const uint32_t G = p.in.n_groups;
 
     if (tid == 0) {
-        mbar_init(&sh.full_bar, kWarps);
-        mbar_init(&sh.empty_bar, kMmaWarps);
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&sh.full_bar[s], kGroupThreads / 32);
+            mbar_init(&sh.empty_bar[s], kMmaWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         sh.abort_flag = 0;
     }
-    if (tid < kMaxGroups) sh.ng_acc[tid] = 0;
+    if (tid < kStages * kMaxGroups) (&sh.ng_acc[0][0])[tid] = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_slot)),
                      "r"(kTmemCols));
@@ -532,8 +575,7 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
     const uint64_t end = min(p.in.n, begin + p.rows_per_cta);
     const uint32_t n_rows = static_cast<uint32_t>(end - begin);
     const uint32_t n_tiles = (n_rows + kTileRows - 1) / kTileRows;
-    const uint32_t a_stage = smem_u32(smem);
-    const uint32_t b_stage = a_stage + p.a_bytes;
+    const uint32_t smem_base = smem_u32(smem);
 
     if (warp >= kWarps) {
         // ---------------- MMA warps ----------------
@@ -544,7 +586,10 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
             my_share[kMaxSlots / kMmaWarps];
         for (uint32_t it = 0; it < n_tiles; it++) {
             if (lane == 0) {
-                if (!mbar_wait(&sh.full_bar, it & 1)) sh.abort_flag = 1;
+                const int s = static_cast<int>(it & 1);
+                const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
+                const uint32_t b_stage = a_stage + p.a_bytes;
+                if (!mbar_wait(&sh.full_bar[s], (it >> 1) & 1)) sh.abort_flag = 1;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 if (it == 0) {
                     // the k-th slot dealt to this warp goes to register set k
@@ -568,7 +613,7 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
                     }
                     my_n = found < kMaxSlots / kMmaWarps ? found : kMaxSlots / kMmaWarps;
                 }
-                const int N = sh.meta_n;
+                const int N = sh.meta_n[s];
                 const uint32_t idesc = instr_desc(N);
                 const uint32_t lbo_b = (N / 16) * 128;
                 // descriptors of slot 0; one 32-row block moves the start address
@@ -580,8 +625,8 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
 #pragma unroll
                 for (int k = 0; k < kMaxSlots / kMmaWarps; k++) {
                     if (k < my_n) {
-                        lo[k] = sh.meta_lo[my_g[k]];
-                        nb[k] = sh.meta_len[my_g[k]] / kMmaK;
+                        lo[k] = sh.meta_lo[s][my_g[k]];
+                        nb[k] = sh.meta_len[s][my_g[k]] / kMmaK;
                     }
                 }
 #pragma unroll
@@ -600,39 +645,47 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&sh.empty_bar)));
+                    smem_u32(&sh.empty_bar[s])));
             }
             __syncwarp();
         }
-        // drain: every MMA warp's last commit has arrived once the last phase completes
+        // drain: the last commit of each MMA warp covers every MMA it issued
         if (lane == 0 && n_tiles > 0) {
-            if (!mbar_wait(&sh.empty_bar, (n_tiles - 1) & 1)) sh.abort_flag = 1;
+            const uint32_t last = n_tiles - 1;
+            if (!mbar_wait(&sh.empty_bar[last & 1], (last >> 1) & 1)) sh.abort_flag = 1;
         }
         __syncwarp();
     } else {
         // ---------------- producer warps ----------------
-        // two register sets of raw rows, each reloaded right after its tile
-        // is produced, so a load has a whole tile of work to arrive in
+        // group pg produces the tiles it = pg, pg+2, ...; two register sets of
+        // raw rows, each reloaded right after its tile is produced, so a load
+        // has a whole tile of work to arrive in
+        const int pg = warp / (kGroupThreads / 32);
+        const uint32_t gt = static_cast<uint32_t>(tid - pg * kGroupThreads);  // thread within the group
+        const uint32_t a_stage = smem_base + pg * (p.a_bytes + p.b_bytes);
+        const uint32_t b_stage = a_stage + p.a_bytes;
         const bool keys_in = !(p.in.in_flags & PAC_IN_MASKS);
         const bool balanced_keys = keys_in && p.in.hash_mode == PAC_HASH_BALANCED;
         RawRow a0, a1, b0, b1;
-        const uint32_t t = static_cast<uint32_t>(tid);
-        load_raw<C4, GB>(p, begin, t, t < n_rows, a0);
-        load_raw<C4, GB>(p, begin, kThreads + t, kThreads + t < n_rows, a1);
-        load_raw<C4, GB>(p, begin, kTileRows + t, kTileRows + t < n_rows, b0);
-        load_raw<C4, GB>(p, begin, kTileRows + kThreads + t, kTileRows + kThreads + t < n_rows, b1);
-        for (uint32_t it = 0; it < n_tiles; it += 2) {
+        {
+            const uint32_t o0 = pg * kTileRows + gt, o1 = (pg + 2) * kTileRows + gt;
+            load_raw<C4, GB>(p, begin, o0, n_rows, a0);
+            load_raw<C4, GB>(p, begin, o0 + kGroupThreads, n_rows, a1);
+            load_raw<C4, GB>(p, begin, o1, n_rows, b0);
+            load_raw<C4, GB>(p, begin, o1 + kGroupThreads, n_rows, b1);
+        }
+        for (uint32_t it = pg; it < n_tiles; it += 4) {
             produce_tile<C4>(p, sh, it, max_slots, a0, a1, a_stage, b_stage, keys_in, balanced_keys);
             {
-                const uint32_t off = (it + 2) * kTileRows + t;
-                load_raw<C4, GB>(p, begin, off, off < n_rows, a0);
-                load_raw<C4, GB>(p, begin, off + kThreads, off + kThreads < n_rows, a1);
+                const uint32_t off = (it + 4) * kTileRows + gt;
+                load_raw<C4, GB>(p, begin, off, n_rows, a0);
+                load_raw<C4, GB>(p, begin, off + kGroupThreads, n_rows, a1);
             }
-            if (it + 1 < n_tiles) {
-                produce_tile<C4>(p, sh, it + 1, max_slots, b0, b1, a_stage, b_stage, keys_in, balanced_keys);
-                const uint32_t off = (it + 3) * kTileRows + t;
-                load_raw<C4, GB>(p, begin, off, off < n_rows, b0);
-                load_raw<C4, GB>(p, begin, off + kThreads, off + kThreads < n_rows, b1);
+            if (it + 2 < n_tiles) {
+                produce_tile<C4>(p, sh, it + 2, max_slots, b0, b1, a_stage, b_stage, keys_in, balanced_keys);
+                const uint32_t off = (it + 6) * kTileRows + gt;
+                load_raw<C4, GB>(p, begin, off, n_rows, b0);
+                load_raw<C4, GB>(p, begin, off + kGroupThreads, n_rows, b1);
             }
         }
     }
@@ -668,7 +721,10 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
             }
         }
     }
-    if (tid < static_cast<int>(G) && sh.ng_acc[tid]) atomicAdd(p.ng + tid, sh.ng_acc[tid]);
+    if (tid < static_cast<int>(G)) {
+        const unsigned long long rows_g = sh.ng_acc[0][tid] + sh.ng_acc[1][tid];
+        if (rows_g) atomicAdd(p.ng + tid, rows_g);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
@@ -772,6 +828,11 @@ static pac_status mma_plan(const pac_input *in, const pac_agg_spec *specs, int n
     p.in.gid_bytes = in->group_ids ? in->gid_bytes : 0;
     p.in.n_groups = in->n_groups;
     for (int c = 0; c < C; c++) p.col[c] = static_cast<const long long *>(cols[c]);
+    // The producers load every column slot without a branch: unused slots
+    // point at a live n-row 8-byte column (column 0, or the key/mask column
+    // of a COUNT-only query) and their values are zeroed after the load.
+    for (int c = C; c < kMaxCols; c++)
+        p.col[c] = C > 0 ? p.col[0] : static_cast<const long long *>(in->keys_or_masks);
     p.n_cols = C;
     p.n_alloc = feat_alloc(Ceff);
     const uint32_t G = in->n_groups;
@@ -781,8 +842,9 @@ static pac_status mma_plan(const pac_input *in, const pac_agg_spec *specs, int n
     if (per == 0) per = kTileRows;
     p.rows_per_cta = static_cast<uint32_t>(per);
     p.k_cap = (kTileRows + (kMmaK - 1) * G + kMmaK - 1) / kMmaK * kMmaK;
-    p.a_bytes = p.k_cap * 64;
-    p.b_bytes = p.k_cap * p.n_alloc;
+    // one more 8-row block past k_cap takes the writes of invalid rows
+    p.a_bytes = (p.k_cap + 8) * 64;
+    p.b_bytes = (p.k_cap + 8) * p.n_alloc;
     smem = static_cast<size_t>(kStages) * (p.a_bytes + p.b_bytes);
     if (smem > 220 * 1024) {
         *why = "tensor-core path: tile does not fit shared memory";
