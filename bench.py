@@ -1,10 +1,20 @@
 """Benchmark of the PAC stochastic-aggregation hot path on GB300.
 
-One step = one PAC query over the 60M-row, 4-group, 4-column low-cardinality
-workload: hash of the PU keys, per-group per-world COUNT + 4 exact SUMs + 4
-exact AVGs over the m = 64 worlds, and the adaptive finalize (variance under
-the posterior + PAC noise) of all 36 cells.  Inputs are resident in HBM and
-larger than L2 (2.46 GB), so no flush is needed between steps.
+One step = one PAC query over a synthetic workload resident in HBM: the hash
+of the PU keys (fused into the aggregation), the per-group per-world
+aggregates over the m = 64 worlds, and the release of every cell (variance
+under the posterior + PAC noise).  Workloads (``--workload``):
+
+* ``lowcard_60m`` (default, the headline): 60M rows, 4 groups (uint8),
+  COUNT + 4 exact SUMs + 4 exact AVGs of int64 cents, adaptive finalize of
+  the 36 cells.  Inputs 2.46 GB > L2, no flush needed.
+* ``ungrouped_1m``: 1M rows, no GROUP BY, COUNT + exact SUM, adaptive
+  finalize of 2 cells.  The 16 MB input fits in L2, so L2 is flushed
+  (a 512 MB write) before every step, outside the step's events.
+* ``highcard_100m``: 100M rows, Zipf(1.1) over 1M groups (int32), COUNT +
+  exact SUM.  The adaptive release of 2M cells is one sequential posterior
+  chain, so the step is the aggregation alone and the release of all cells in
+  the independent mode is timed once beside it (``finalize_ms``).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
@@ -12,8 +22,11 @@ a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -27,8 +40,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "PAC-aggregated rows/s at m=64 worlds, % of HBM roofline; p99 query latency"
-WORKLOAD = "lowcard_60m"
-BYTES_PER_ROW = 8 + 1 + 4 * 8   # int64 PU key + uint8 group id + four int64 value columns
+L2_BYTES = 129 * 1024 * 1024
+
+# per workload: group-id width, value columns used, specs, release mode,
+# algorithmic bytes per row (inputs read once), per-group output bytes
+WORKLOADS = {
+    "lowcard_60m": {"gid_bytes": 1, "n_cols": 4, "aggs": "count+sum+avg", "finalize": "adaptive",
+                    "in_bytes_per_row": 8 + 1 + 4 * 8, "flush_l2": False,
+                    "describe": "count + 4 sum + 4 avg, exact; adaptive finalize of 36 cells"},
+    "ungrouped_1m": {"gid_bytes": 0, "n_cols": 1, "aggs": "count+sum", "finalize": "adaptive",
+                     "in_bytes_per_row": 8 + 8, "flush_l2": True,
+                     "describe": "count + sum, exact; adaptive finalize of 2 cells"},
+    "highcard_100m": {"gid_bytes": 4, "n_cols": 1, "aggs": "count+sum", "finalize": "separate",
+                      "in_bytes_per_row": 8 + 4 + 8, "flush_l2": False,
+                      "describe": "count + sum, exact; release of the 2M cells timed separately"},
+}
 
 
 def _peaks():
@@ -39,6 +65,30 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _source_sha(path: str) -> str:
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def _traffic(workload: str, n: int):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summaries (a `bench-traffic:` line), scaled to n rows; None when no
+    capture exists or the kernel source changed since it was taken."""
+    pat = re.compile(r"bench-traffic:\s*workload=(\S+)\s+kernel_source=(\S+)\s+sha=(\S+)\s+bytes_per_row=([0-9.]+)")
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(f) as fh:
+            for line in fh:
+                m = pat.search(line)
+                if m and m.group(1) == workload:
+                    try:
+                        if _source_sha(m.group(2)) != m.group(3):
+                            return None
+                    except OSError:
+                        return None
+                    return float(m.group(4)) * n
+    return None
 
 
 class ClockSampler:
@@ -98,31 +148,50 @@ def _dist():
     return world, rank, local
 
 
-def _specs_for(w, B, outs):
+def _gen(workload: str, seed: int, rows):
+    from paper_2603_15023_gb300 import inputs
+    fn = inputs.WORKLOADS[workload]
+    return fn(seed=seed) if rows is None else fn(seed=seed, n=rows)
+
+
+def _spec_list(B, wcfg, vals, outs):
+    """(kind, variant, vtype, values, out) per spec: COUNT, SUM per column,
+    AVG per column (lowcard only)."""
+    C = wcfg["n_cols"]
     specs = [(B.PAC_COUNT, B.PAC_EXACT, B.PAC_I64, 0, outs[0])]
-    for k in range(4):
-        specs.append((B.PAC_SUM, B.PAC_EXACT, B.PAC_I64, w["vals"][k], outs[1 + k]))
-    for k in range(4):
-        specs.append((B.PAC_AVG, B.PAC_EXACT, B.PAC_I64, w["vals"][k], outs[5 + k]))
+    for k in range(C):
+        specs.append((B.PAC_SUM, B.PAC_EXACT, B.PAC_I64, vals[k], outs[1 + k]))
+    if "avg" in wcfg["aggs"]:
+        for k in range(C):
+            specs.append((B.PAC_AVG, B.PAC_EXACT, B.PAC_I64, vals[k], outs[1 + C + k]))
     return specs
 
 
-def cpu_oracle_sample(rows: int, seed: int = 0):
-    """Times the oracle (as it stands) on the first `rows` rows of the workload."""
+def _n_specs(wcfg):
+    C = wcfg["n_cols"]
+    return 1 + C + (C if "avg" in wcfg["aggs"] else 0)
+
+
+def cpu_oracle_sample(workload: str, rows: int, seed: int = 0):
+    """Times the oracle (as it stands) on the first `rows` rows of the
+    workload: hash, every aggregate of the step, and the release."""
     import oracle as orc
-    from paper_2603_15023_gb300 import inputs
-    wl = inputs.lowcard_60m(seed=seed, n=rows)
+    wcfg = WORKLOADS[workload]
+    wl = _gen(workload, seed, rows)
+    G = wl.n_groups
     qk = orc.query_key(seed)
     t0 = time.perf_counter()
     masks = orc.hash_keys(wl.keys, qk, orc.BALANCED)
-    res = [orc.aggregate(masks, None, wl.gids, 4, orc.COUNT)]
-    for v in wl.values:
-        res.append(orc.aggregate(masks, v, wl.gids, 4, orc.SUM))
-    for v in wl.values:
-        res.append(orc.aggregate(masks, v, wl.gids, 4, orc.AVG))
-    y = np.stack([r[0].astype(np.float64) for r in res], axis=1)
-    scales = [2.0] * 5 + [1.0] * 4
-    orc.finalize(y, scales, res[0][1], res[0][2], 99, 1.0 / 128, orc.ADAPTIVE)
+    res = [orc.aggregate(masks, None, wl.gids, G, orc.COUNT)]
+    for v in wl.values[:wcfg["n_cols"]]:
+        res.append(orc.aggregate(masks, v, wl.gids, G, orc.SUM))
+    if "avg" in wcfg["aggs"]:
+        for v in wl.values[:wcfg["n_cols"]]:
+            res.append(orc.aggregate(masks, v, wl.gids, G, orc.AVG))
+    if wcfg["finalize"] != "separate":
+        y = np.stack([r[0].astype(np.float64) for r in res], axis=1)
+        scales = [2.0] * (1 + wcfg["n_cols"]) + [1.0] * (len(res) - 1 - wcfg["n_cols"])
+        orc.finalize(y, scales, res[0][1], res[0][2], 99, 1.0 / 128, orc.ADAPTIVE)
     dt = time.perf_counter() - t0
     return rows / dt, dt
 
@@ -134,19 +203,19 @@ def run_reference(args):
     rows = args.ref_rows
     vals = []
     for i in range(args.warmup + args.steps):
-        v, dt = cpu_oracle_sample(rows)
+        v, dt = cpu_oracle_sample(args.workload, rows)
         if i >= args.warmup:
             vals.append((v, dt))
     value = statistics.median(v for v, _ in vals)
     ms = statistics.median(dt for _, dt in vals) * 1e3
+    wcfg = WORKLOADS[args.workload]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rows": rows, "groups": 4, "value_columns": 4,
-                   "aggregates": "count + 4 sum + 4 avg, exact", "worlds": 64},
+        "config": {"workload": args.workload, "rows": rows, "aggregates": wcfg["describe"], "worlds": 64},
         "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {rows} rows of {WORKLOAD}, one thread"},
+                         "sample": f"first {rows} rows of {args.workload}, one thread"},
         "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -156,7 +225,6 @@ def run_reference(args):
 def run_ours(args):
     import torch
     from paper_2603_15023_gb300 import binding as B
-    from paper_2603_15023_gb300 import inputs
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -167,44 +235,58 @@ def run_ours(args):
     if args.path:
         B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2}[args.path])
 
-    wl = inputs.lowcard_60m(seed=rank, n=args.rows)
+    wcfg = WORKLOADS[args.workload]
+    wl = _gen(args.workload, rank, args.rows)
     n, G = wl.n, wl.n_groups
+    C = wcfg["n_cols"]
+    n_specs = _n_specs(wcfg)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     d_keys = torch.from_numpy(wl.keys).cuda()
-    d_gids = torch.from_numpy(wl.gids).cuda()
-    d_vals = [torch.from_numpy(v).cuda() for v in wl.values]
-    outs = [torch.empty((G, 64), dtype=torch.int64 if i < 5 else torch.float64, device="cuda") for i in range(9)]
+    d_gids = torch.from_numpy(wl.gids).cuda() if wl.gids is not None else None
+    d_vals = [torch.from_numpy(v).cuda() for v in wl.values[:C]]
+    outs = [torch.empty((G, 64), dtype=torch.int64 if i < 1 + C else torch.float64, device="cuda")
+            for i in range(n_specs)]
     meta = torch.empty((G, 2), dtype=torch.int64, device="cuda")
-    n_cells = G * 9
+    n_cells = G * n_specs
     noised = torch.empty(n_cells, dtype=torch.float64, device="cuda")
     is_null = torch.empty(n_cells, dtype=torch.uint8, device="cuda")
     flags = torch.empty(n_cells, dtype=torch.int32, device="cuda")
     qk = B.pac_query_key(rank)
-    inp = B.make_input(d_keys.data_ptr(), n, query_key=qk, group_ids=d_gids.data_ptr(), gid_bytes=1, n_groups=G)
-    w = {"vals": [v.data_ptr() for v in d_vals]}
-    specs = B.make_specs(_specs_for(w, B, [o.data_ptr() for o in outs]))
+    inp = B.make_input(d_keys.data_ptr(), n, query_key=qk,
+                       group_ids=d_gids.data_ptr() if d_gids is not None else 0,
+                       gid_bytes=wcfg["gid_bytes"], n_groups=G)
+    specs = B.make_specs(_spec_list(B, wcfg, [v.data_ptr() for v in d_vals], [o.data_ptr() for o in outs]))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda") if wcfg["flush_l2"] else None
+    in_step_finalize = wcfg["finalize"] == "adaptive"
 
     def step(i, ev=None):
         if ev is not None:
             ev[0].record(stream)
-        B.pac_aggregate_multi(ctx, inp, specs, 9, meta.data_ptr(), sptr)
+        B.pac_aggregate_multi(ctx, inp, specs, n_specs, meta.data_ptr(), sptr)
+        k = B.pac_get_info(ctx, "last_launches")
         if ev is not None:
             ev[1].record(stream)
-        B.pac_finalize(ctx, specs, 9, G, meta.data_ptr(), 1000 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
-                       noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+        if in_step_finalize:
+            B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 1000 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
+                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+            k += B.pac_get_info(ctx, "last_launches")
+        if ev is not None:
+            ev[2].record(stream)
+        return k
 
     for i in range(args.warmup):
+        if flush is not None:
+            flush.fill_(i)
         step(i)
     torch.cuda.synchronize()
     st = B.pac_sync_status(ctx, sptr)
     if st != B.PAC_OK:
         raise RuntimeError(B.status_name(st))
-    agg_launches = B.pac_get_info(ctx, "last_path")
     path = B.pac_get_info(ctx, "last_path")
 
     clocks = ClockSampler(local)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         torch.distributed.barrier()
@@ -214,19 +296,18 @@ def run_ours(args):
     start.record(stream)
     launches = 0
     for i in range(args.steps):
-        step(args.warmup + i, evs[i])
-        launches += B.pac_get_info(ctx, "last_launches")  # finalize's launch
+        if flush is not None:
+            flush.fill_(i)  # L2 flush between steps, outside the step's events
+        launches += step(args.warmup + i, evs[i])
     end.record(stream)
     torch.cuda.synchronize()
     clocks.stop()
-    # aggregation launches per step (the finalize call overwrote last_launches)
-    B.pac_aggregate_multi(ctx, inp, specs, 9, meta.data_ptr(), sptr)
-    torch.cuda.synchronize()
-    agg_launches = B.pac_get_info(ctx, "last_launches")
-    launches += agg_launches * args.steps
-    total_ms = start.elapsed_time(end)
-    agg_ms = [a.elapsed_time(b) for a, b in evs]
-    ms_step = total_ms / args.steps
+    st = B.pac_sync_status(ctx, sptr)
+    if st != B.PAC_OK:
+        raise RuntimeError(B.status_name(st))
+    agg_ms = [a.elapsed_time(b) for a, b, _ in evs]
+    step_ms = [a.elapsed_time(c) for a, _, c in evs]
+    ms_step = start.elapsed_time(end) / args.steps if flush is None else statistics.mean(step_ms)
     t = torch.tensor([ms_step, statistics.mean(agg_ms)], dtype=torch.float64)
     if world > 1:
         import torch.distributed as dist
@@ -236,59 +317,77 @@ def run_ours(args):
     ms_step, agg_mean = float(t[0]), float(t[1])
     value = n * world / (ms_step / 1e3)
 
+    # the release of every cell, timed once beside the step when it is not in it
+    fin_ms = None
+    if not in_step_finalize:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 5, 1.0 / 128, B.PAC_FIN_INDEPENDENT,
+                       noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fin_ms = e0.elapsed_time(e1)
+
     # end to end through the C ABI from pinned host memory
     e2e = None
     if args.e2e_steps > 0:
         h_keys = torch.from_numpy(wl.keys).pin_memory()
-        h_gids = torch.from_numpy(wl.gids).pin_memory()
-        h_vals = [torch.from_numpy(v).pin_memory() for v in wl.values]
+        h_gids = torch.from_numpy(wl.gids).pin_memory() if wl.gids is not None else None
+        h_vals = [torch.from_numpy(v).pin_memory() for v in wl.values[:C]]
         h_noised = torch.empty(n_cells, dtype=torch.float64).pin_memory()
         h_null = torch.empty(n_cells, dtype=torch.uint8).pin_memory()
         h_flags = torch.empty(n_cells, dtype=torch.int32).pin_memory()
-        hin = B.make_input(h_keys.data_ptr(), n, query_key=qk, group_ids=h_gids.data_ptr(), gid_bytes=1,
-                           n_groups=G)
-        hw = {"vals": [v.data_ptr() for v in h_vals]}
-        hspecs = B.make_specs(_specs_for(hw, B, [1] * 9))
+        hin = B.make_input(h_keys.data_ptr(), n, query_key=qk,
+                           group_ids=h_gids.data_ptr() if h_gids is not None else 0,
+                           gid_bytes=wcfg["gid_bytes"], n_groups=G)
+        hspecs = B.make_specs(_spec_list(B, wcfg, [v.data_ptr() for v in h_vals], [1] * n_specs))
+        mode = B.PAC_FIN_ADAPTIVE if in_step_finalize else B.PAC_FIN_INDEPENDENT
         for i in range(2):
-            B.pac_query_host(ctx, hin, hspecs, 9, 7 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE, h_noised.data_ptr(),
+            B.pac_query_host(ctx, hin, hspecs, n_specs, 7 + i, 1.0 / 128, mode, h_noised.data_ptr(),
                              h_null.data_ptr(), h_flags.data_ptr(), sptr)
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
-            B.pac_query_host(ctx, hin, hspecs, 9, 100 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE, h_noised.data_ptr(),
+            B.pac_query_host(ctx, hin, hspecs, n_specs, 100 + i, 1.0 / 128, mode, h_noised.data_ptr(),
                              h_null.data_ptr(), h_flags.data_ptr(), sptr)
         dt = (time.perf_counter() - t0) / args.e2e_steps
-        h2d = n * BYTES_PER_ROW
+        h2d = n * wcfg["in_bytes_per_row"]
         d2h = n_cells * (8 + 1 + 4)
         e2e = {"value": n * world / dt, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": dt * 1e3}
 
     peak, peak_src = _peaks()
-    algo_bytes = n * BYTES_PER_ROW
+    out_bytes = G * 64 * 8 * n_specs + G * 16
+    algo_bytes = n * wcfg["in_bytes_per_row"] + out_bytes
     achieved = algo_bytes / (agg_mean / 1e3) / 1e9
-    line = None
+    kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
+              2: "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"}.get(path, str(path))
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, dt = cpu_oracle_sample(args.cpu_rows)
+            v, dt = cpu_oracle_sample(args.workload, args.cpu_rows)
             cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                   "sample": f"first {args.cpu_rows} rows of {WORKLOAD} (COUNT + 4 SUM + 4 AVG + finalize), "
+                   "sample": f"first {args.cpu_rows} rows of {args.workload} ({wcfg['describe']}), "
                              f"one thread, {dt:.1f} s"}
+        l2 = ("L2 flushed before every step (512 MB write), inputs 16 MB" if flush is not None else
+              f"inputs {n * wcfg['in_bytes_per_row'] / 1e9:.2f} GB > 129 MB L2 (no flush needed)")
         line = {
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rows": n, "groups": G, "value_columns": 4, "worlds": 64,
-                       "aggregates": "count + 4 sum + 4 avg, exact; adaptive finalize of 36 cells",
-                       "l2": "inputs 2.46 GB > 129 MB L2 (no flush needed)",
+            "config": {"workload": args.workload, "rows": n, "groups": G, "value_columns": C, "worlds": 64,
+                       "aggregates": wcfg["describe"], "l2": l2,
                        "agg_path": {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores"}.get(path, str(path))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "aggregation (main + merge)",
-                         "peak_source": peak_src, "agg_ms": agg_mean},
+                         "frac": achieved / peak, "traffic": _traffic(args.workload, n) if path == 2 else None,
+                         "kernel": kernel, "algorithmic_bytes": algo_bytes, "peak_source": peak_src,
+                         "agg_ms": agg_mean, "agg_ms_min": min(agg_ms)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
         }
+        if fin_ms is not None:
+            line["finalize_ms"] = fin_ms
         print(json.dumps(line))
     B.pac_destroy(ctx)
     if world > 1:
@@ -303,7 +402,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--rows", type=int, default=60_000_000)
+    ap.add_argument("--workload", default="lowcard_60m", choices=sorted(WORKLOADS))
+    ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
     ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=4_000_000)

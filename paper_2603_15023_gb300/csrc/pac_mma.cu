@@ -935,7 +935,7 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
         *why = cudaGetErrorString(e);
         return PAC_E_CUDA;
     }
-    *launches += 3;  // memset + aggregation + finish
+    *launches += 2;  // aggregation + finish kernels (the clearing memset is not a kernel)
     return PAC_OK;
 }
 
