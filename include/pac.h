@@ -220,6 +220,76 @@ pac_status pac_query_host(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
                           double *noised, uint8_t *is_null, uint32_t *flags, pac_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * 4. Batched queries: thousands of independent PAC queries (each one the
+ *    aggregation of Sec. 4.2 over its own columns, then optionally the
+ *    release of Sec. 2 / Sec. 4.1 steps 1-4 over its own cells) in one
+ *    persistent aggregation launch.
+ *
+ * A query of a batch.  `in` and the specs' `values`/`out` are as for
+ * pac_aggregate_multi (DEVICE buffers owned by the caller, HOST structs).
+ * Every spec must be PAC_EXACT (the approximate integer cascade has its own
+ * schedule and runs only through pac_aggregate_multi).
+ *   meta      device [n_groups*2] {n_g, or_g}, or NULL (then fin_mode must
+ *             be -1).
+ *   fin_mode  PAC_FIN_ADAPTIVE or PAC_FIN_INDEPENDENT to release the query's
+ *             cells like pac_finalize(seed, budget) would, or -1 for the
+ *             aggregation alone.
+ *   noised, is_null, flags  device [n_groups*n_specs] release outputs (used
+ *             when fin_mode >= 0).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    pac_input in;
+    const pac_agg_spec *specs; /* HOST array of n_specs (1..PAC_MAX_SPECS) */
+    int32_t n_specs;
+    int32_t fin_mode;
+    uint64_t *meta;
+    uint64_t seed;
+    double budget;
+    double *noised;
+    uint8_t *is_null;
+    uint32_t *flags;
+} pac_query;
+
+typedef struct pac_batch pac_batch;
+
+/* Plan flags. */
+#define PAC_BATCH_AUTOTUNE 1u /* time candidate work-item sizes and state
+                                 placements on this batch and keep the fastest
+                                 (the choice is cached in the context) */
+
+/* Plans a batch: checks every query (PAC_E_INVALID / PAC_E_UNSUPPORTED name
+ * the first bad query in pac_last_error), chooses per query where its
+ * per-world states live (warp-private shared memory or global atomics),
+ * cuts all queries into work items and uploads the descriptors once into
+ * plan-owned device memory.  Synchronous.  The specs arrays are copied; the
+ * device buffers they name must stay valid while the plan is launched.
+ * With PAC_BATCH_AUTOTUNE the candidate configurations are launched on this
+ * batch (writing its outputs) and timed. */
+pac_status pac_batch_plan(pac_ctx *ctx, const pac_query *queries, int32_t n_queries, uint32_t flags,
+                          pac_batch **plan);
+
+/* Enqueues the whole batch on `stream`: one memset of the plan's scratch,
+ * one persistent aggregation kernel over every query's work items (dynamic
+ * scheduling), one merge kernel that writes every query's outputs and meta,
+ * and, if any query releases, one finalize kernel (one warp per query).  No
+ * allocation, no host synchronisation: the launch can be captured in a CUDA
+ * graph and replayed.  Device conditions (overflow, bad group ids) go to the
+ * context's status word (pac_sync_status).  Launches of one plan must not
+ * overlap on the GPU (they share the plan's scratch). */
+pac_status pac_batch_launch(pac_ctx *ctx, pac_batch *plan, pac_stream stream);
+
+/* Frees a plan (synchronises the device first).  NULL is a no-op. */
+void pac_batch_free(pac_batch *plan);
+
+/* Plan introspection: "n_items", "item_rows", "smem_cap", "kernels"
+ * (kernels per launch), "n_warp_private" (queries with shared-memory
+ * states), "n_atomic" (queries with global-atomic states). */
+pac_status pac_batch_info(const pac_batch *plan, const char *name, int64_t *value);
+
+/* Plan + launch + synchronise + free.  Returns the device status. */
+pac_status pac_batch_run(pac_ctx *ctx, const pac_query *queries, int32_t n_queries, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
  * pac_aggregate_noalloc -- the paper has no counterpart: this is a service
  * of the library for callers that cannot allocate device memory.
  *

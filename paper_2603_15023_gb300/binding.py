@@ -30,7 +30,9 @@ EXPORTED = (
     "pac_create", "pac_destroy", "pac_last_error", "pac_status_string", "pac_sync_status",
     "pac_query_key", "pac_hash_keys", "pac_aggregate", "pac_aggregate_multi", "pac_finalize",
     "pac_query_host", "pac_set_option", "pac_get_info", "pac_aggregate_noalloc",
+    "pac_batch_plan", "pac_batch_launch", "pac_batch_free", "pac_batch_info", "pac_batch_run",
 )
+PAC_BATCH_AUTOTUNE = 1
 
 
 class PacInput(ctypes.Structure):
@@ -54,6 +56,21 @@ class PacAggSpec(ctypes.Structure):
         ("reserved", ctypes.c_int32),
         ("values", ctypes.c_void_p),
         ("out", ctypes.c_void_p),
+    ]
+
+
+class PacQuery(ctypes.Structure):
+    _fields_ = [
+        ("in_", PacInput),
+        ("specs", ctypes.POINTER(PacAggSpec)),
+        ("n_specs", ctypes.c_int32),
+        ("fin_mode", ctypes.c_int32),
+        ("meta", ctypes.c_void_p),
+        ("seed", ctypes.c_uint64),
+        ("budget", ctypes.c_double),
+        ("noised", ctypes.c_void_p),
+        ("is_null", ctypes.c_void_p),
+        ("flags", ctypes.c_void_p),
     ]
 
 
@@ -93,6 +110,11 @@ def lib() -> ctypes.CDLL:
         "pac_get_info": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(i64)]),
         "pac_aggregate_noalloc": (i32, [ctypes.POINTER(PacInput), ctypes.POINTER(PacAggSpec), i32, vp, vp,
                                         ctypes.c_char_p, sz]),
+        "pac_batch_plan": (i32, [vp, ctypes.POINTER(PacQuery), i32, u32, ctypes.POINTER(vp)]),
+        "pac_batch_launch": (i32, [vp, vp, vp]),
+        "pac_batch_free": (None, [vp]),
+        "pac_batch_info": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(i64)]),
+        "pac_batch_run": (i32, [vp, ctypes.POINTER(PacQuery), i32, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -202,3 +224,45 @@ def pac_aggregate_noalloc(inp: PacInput, specs: ctypes.Array, n_specs: int, meta
     st = lib().pac_aggregate_noalloc(ctypes.byref(inp), specs, n_specs, meta or None, stream, buf, len(buf))
     if st != PAC_OK:
         raise PacError(st, buf.value.decode())
+
+
+def make_query(inp: PacInput, specs: ctypes.Array, n_specs: int, *, meta: int = 0, fin_mode: int = -1,
+               seed: int = 0, budget: float = 1.0 / 128, noised: int = 0, is_null: int = 0,
+               flags: int = 0) -> PacQuery:
+    """One query of a batch; `specs` must outlive the plan call (it is copied there)."""
+    return PacQuery(inp, ctypes.cast(specs, ctypes.POINTER(PacAggSpec)), n_specs, fin_mode, meta or None, seed,
+                    budget, noised or None, is_null or None, flags or None)
+
+
+def make_queries(qs: Sequence[PacQuery]) -> ctypes.Array:
+    arr = (PacQuery * max(len(qs), 1))()
+    for i, q in enumerate(qs):
+        arr[i] = q
+    return arr
+
+
+def pac_batch_plan(ctx: int, queries: ctypes.Array, n_queries: int, flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(ctx, lib().pac_batch_plan(ctx, queries, n_queries, flags, ctypes.byref(h)))
+    return h.value
+
+
+def pac_batch_launch(ctx: int, plan: int, stream: int = 0) -> None:
+    _check(ctx, lib().pac_batch_launch(ctx, plan, stream))
+
+
+def pac_batch_free(plan: int) -> None:
+    lib().pac_batch_free(plan)
+
+
+def pac_batch_info(plan: int, name: str) -> int:
+    v = ctypes.c_int64(0)
+    st = lib().pac_batch_info(plan, name.encode(), ctypes.byref(v))
+    if st != PAC_OK:
+        raise PacError(st, f"pac_batch_info({name})")
+    return v.value
+
+
+def pac_batch_run(ctx: int, queries: ctypes.Array, n_queries: int, stream: int = 0) -> int:
+    """Returns the status (device conditions included) instead of raising on them."""
+    return lib().pac_batch_run(ctx, queries, n_queries, stream)

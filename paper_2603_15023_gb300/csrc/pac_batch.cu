@@ -1,0 +1,847 @@
+// pac_batch.cu -- many independent PAC queries in one persistent launch
+// (Sec. 4.2 "PAC Aggregation" per query; the release of Sec. 2 / Sec. 4.1
+// per query through the batched finalize kernel).
+//
+// A plan cuts every query into work items of consecutive rows and uploads
+// one descriptor per query and one record per item.  A launch is:
+//   memset of the plan's zeroed scratch (atomic states, item counter);
+//   k_batch_agg   persistent CTAs (occupancy x SMs) take items from a global
+//                 counter.  A query whose per-world states fit shared memory
+//                 keeps them warp-private (lane l owns worlds l and l+32, the
+//                 rows of one group inside a 32-row batch are folded in
+//                 registers first) and writes one partial state per item; a
+//                 query with many groups folds the same way and adds the
+//                 folded values into its global state with atomics;
+//   k_batch_merge one thread per (query, group, world) cell: item partials
+//                 merged in item order (deterministic float results) or the
+//                 atomic state decoded, typed outputs and meta written;
+//   k_finalize_batch (optional) one warp per releasing query.
+// Atomic MIN/MAX states use an order-preserving unsigned encoding whose
+// identity is 0, so one memset initialises every atomic state.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "pac_ctx.h"
+#include "pac_kernels.h"
+#include "pac_ops.cuh"
+#include "pac_validate.h"
+
+namespace pacgpu {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBatchWarps = 8;
+using namespace ops;
+
+struct BatchQueryDev {
+    InputDev in;
+    int32_t n_slots, n_out;
+    int32_t mode;  // 0: warp-private shared-memory states, 1: global atomics
+    int32_t pad;
+    SlotDev slot[kMaxSpecs];
+    OutDev outs[kMaxSpecs];
+    uint64_t *meta;
+    uint64_t *state;  // mode 0: [n_items][1+n_slots][G][64] partials; mode 1: [1+n_slots][G][64]
+    uint64_t *ng;     // mode 0: [n_items][G]; mode 1: [G]
+    unsigned long long *abs;  // mode 1: [n_slots] running sums of |v| (zeroed)
+    uint32_t first_item, n_items;
+};
+
+struct BatchItem {
+    uint32_t q, k;     // query, item index within the query
+    uint64_t row0;
+    uint32_t rows, pad;
+};
+
+// Order-preserving map of a MIN/MAX state value to an unsigned key whose
+// identity (the value no row can beat) is 0.
+__device__ __forceinline__ unsigned long long minmax_key(int op, uint64_t bits) {
+    const unsigned long long sign = 1ull << 63;
+    long long ord = static_cast<long long>(bits);
+    if (op == OP_FMIN || op == OP_FMAX) ord = ord >= 0 ? ord : (ord ^ 0x7fffffffffffffffll);
+    const unsigned long long u = static_cast<unsigned long long>(ord) ^ sign;
+    return (op == OP_IMIN || op == OP_FMIN) ? ~u : u;
+}
+
+__device__ __forceinline__ uint64_t minmax_value(int op, unsigned long long key) {
+    const unsigned long long sign = 1ull << 63;
+    const unsigned long long u = (op == OP_IMIN || op == OP_FMIN) ? ~key : key;
+    long long ord = static_cast<long long>(u ^ sign);
+    if (op == OP_FMIN || op == OP_FMAX) ord = ord >= 0 ? ord : (ord ^ 0x7fffffffffffffffll);
+    return static_cast<uint64_t>(ord);
+}
+
+// Adds one lane's folded state of one world into the global atomic state.
+__device__ __forceinline__ void atomic_fold(int op, uint64_t *cell, uint64_t acc) {
+    switch (op) {
+    case OP_ISUM: atomicAdd(reinterpret_cast<unsigned long long *>(cell), static_cast<unsigned long long>(acc)); break;
+    case OP_FSUM_COMP: {
+        const double v = static_cast<double>(__int_as_float(static_cast<int>(acc))) +
+                         static_cast<double>(__int_as_float(static_cast<int>(acc >> 32)));
+        atomicAdd(reinterpret_cast<double *>(cell), v);
+        break;
+    }
+    case OP_FSUM_PLAIN: atomicAdd(reinterpret_cast<float *>(cell), __int_as_float(static_cast<int>(acc))); break;
+    default: atomicMax(reinterpret_cast<unsigned long long *>(cell), minmax_key(op, acc)); break;
+    }
+}
+
+// Per-item copy of the query's descriptor fields the row loop reads.
+struct ItemShared {
+    InputDev in;
+    SlotDev slot[kMaxSpecs];
+    int32_t n_slots, mode;
+    uint64_t *state, *ng;
+    unsigned long long *abs;
+    uint64_t row0, row_end;
+    uint32_t k;
+    uint32_t item;
+};
+
+// Loads row `row`'s group, mask and slot values; invalid rows get valid=false.
+template <int NS>
+__device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, bool &valid, uint32_t &gid,
+                                         uint64_t &mask, uint64_t (&vals)[NS], uint64_t (&my_abs)[NS],
+                                         uint32_t *status) {
+    const uint32_t G = is.in.n_groups;
+    gid = 0;
+    mask = 0;
+    if (valid) {
+        gid = row_gid(is.in, row);
+        if (gid >= G) {  // out-of-range group id: skip the row, report it
+            raise_status(status, kStatusBadGroup);
+            valid = false;
+            gid = 0;
+        } else {
+            mask = row_mask(is.in, row);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        vals[s] = 0;
+        if (s < is.n_slots && valid) {
+            vals[s] = load_slot_value(is.slot[s], row);
+            if (is.slot[s].op == OP_ISUM) {
+                const long long v = static_cast<long long>(vals[s]);
+                const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+                const uint64_t t = my_abs[s] + a;
+                my_abs[s] = t < a ? ~0ull : t;
+            }
+        }
+    }
+}
+
+// Folds the rows of group run `run` (a lane mask of this 32-row batch) into
+// this lane's two worlds: counts c0/c1 and one state per slot.
+template <int NS>
+__device__ __forceinline__ void fold_run(const ItemShared &is, uint32_t run, uint32_t mlo, uint32_t mhi,
+                                         const uint64_t (&vals)[NS], int lane, uint32_t &c0, uint32_t &c1,
+                                         uint64_t (&acc)[NS][2]) {
+    c0 = c1 = 0;
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const uint64_t id = s < is.n_slots ? op_identity(is.slot[s].op) : 0ull;
+        acc[s][0] = id;
+        acc[s][1] = id;
+    }
+    for (uint32_t rr = run; rr; rr &= rr - 1) {
+        const int r = __ffs(rr) - 1;
+        const uint32_t b0 = (__shfl_sync(kFull, mlo, r) >> lane) & 1u;
+        const uint32_t b1 = (__shfl_sync(kFull, mhi, r) >> lane) & 1u;
+        c0 += b0;
+        c1 += b1;
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            if (s < is.n_slots) {
+                const uint64_t v = __shfl_sync(kFull, vals[s], r);
+                op_update(is.slot[s].op, acc[s][0], v, b0);
+                op_update(is.slot[s].op, acc[s][1], v, b1);
+            }
+        }
+    }
+}
+
+// One item of a query with warp-private shared-memory states.
+template <int NS>
+__device__ void item_warp_private(const ItemShared &is, unsigned char *smem_raw, uint32_t *status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const uint32_t G = is.in.n_groups;
+    const int nq = 1 + is.n_slots;
+    const size_t per_warp = static_cast<size_t>(nq) * G * kWorlds;
+    uint64_t *st = reinterpret_cast<uint64_t *>(smem_raw) + warp * per_warp;
+    uint64_t *ng_all = reinterpret_cast<uint64_t *>(smem_raw) + n_warps * per_warp;  // [warps][G]
+    uint64_t *ng = ng_all + warp * G;
+    unsigned long long *abssum = reinterpret_cast<unsigned long long *>(ng_all + n_warps * G);  // [warps][NS]
+
+    for (size_t k = lane; k < per_warp; k += 32) {
+        const int qn = static_cast<int>(k / (static_cast<size_t>(G) * kWorlds));
+        st[k] = qn == 0 ? 0ull : op_identity(is.slot[qn - 1].op);
+    }
+    for (uint32_t g = lane; g < G; g += 32) ng[g] = 0;
+    __syncwarp();
+
+    uint64_t my_abs[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) my_abs[s] = 0;
+    for (uint64_t base = is.row0 + static_cast<uint64_t>(warp) * 32; base < is.row_end;
+         base += static_cast<uint64_t>(n_warps) * 32) {
+        const uint64_t row = base + lane;
+        bool valid = row < is.row_end;
+        uint32_t gid;
+        uint64_t mask, vals[NS];
+        load_row<NS>(is, row, valid, gid, mask, vals, my_abs, status);
+        const uint32_t mlo = static_cast<uint32_t>(mask), mhi = static_cast<uint32_t>(mask >> 32);
+        uint32_t pending = __ballot_sync(kFull, valid);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const uint32_t g = __shfl_sync(kFull, gid, leader);
+            const uint32_t run = __ballot_sync(kFull, valid && gid == g);
+            pending &= ~run;
+            uint32_t c0, c1;
+            uint64_t acc[NS][2];
+            fold_run<NS>(is, run, mlo, mhi, vals, lane, c0, c1, acc);
+            uint64_t *cst = st + static_cast<size_t>(g) * kWorlds;
+            cst[lane] += c0;
+            cst[lane + 32] += c1;
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                if (s < is.n_slots) {
+                    uint64_t *sst = st + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
+                    op_merge(is.slot[s].op, sst[lane], acc[s][0]);
+                    op_merge(is.slot[s].op, sst[lane + 32], acc[s][1]);
+                }
+            }
+            if (lane == 0) ng[g] += __popc(run);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        uint64_t m = my_abs[s];
+        for (int o = 16; o; o >>= 1) {
+            const uint64_t t = __shfl_xor_sync(kFull, m, o);
+            const uint64_t u = m + t;
+            m = u < t ? ~0ull : u;
+        }
+        if (lane == 0) abssum[warp * NS + s] = m;
+    }
+    __syncthreads();
+
+    // the item's partial: warps merged in warp order
+    uint64_t *out = is.state + static_cast<size_t>(is.k) * per_warp;
+    const uint64_t *st0 = reinterpret_cast<const uint64_t *>(smem_raw);
+    for (size_t k = threadIdx.x; k < per_warp; k += blockDim.x) {
+        const int qn = static_cast<int>(k / (static_cast<size_t>(G) * kWorlds));
+        uint64_t a = st0[k];
+        for (int w = 1; w < n_warps; w++) {
+            const uint64_t b = st0[static_cast<size_t>(w) * per_warp + k];
+            if (qn == 0) a += b;
+            else op_merge(is.slot[qn - 1].op, a, b);
+        }
+        out[k] = a;
+    }
+    uint64_t *ng_out = is.ng + static_cast<size_t>(is.k) * G;
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) {
+        uint64_t a = 0;
+        for (int w = 0; w < n_warps; w++) a += ng_all[w * G + g];
+        ng_out[g] = a;
+    }
+    // an exact int64 SUM needs every item partial to fit: sum |v| < 2^63
+    if (threadIdx.x < NS && static_cast<int>(threadIdx.x) < is.n_slots && is.slot[threadIdx.x].op == OP_ISUM) {
+        uint64_t tot = 0;
+        for (int w = 0; w < n_warps; w++) {
+            const uint64_t t = tot + abssum[w * NS + threadIdx.x];
+            tot = t < tot ? ~0ull : t;
+        }
+        if (tot >= (1ull << 63)) raise_status(status, kStatusOverflow);
+    }
+    __syncthreads();  // shared memory is reused by the next item
+}
+
+// One item of a query with global-atomic states.
+template <int NS>
+__device__ void item_atomic(const ItemShared &is, uint32_t *status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const uint32_t G = is.in.n_groups;
+    uint64_t my_abs[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) my_abs[s] = 0;
+    for (uint64_t base = is.row0 + static_cast<uint64_t>(warp) * 32; base < is.row_end;
+         base += static_cast<uint64_t>(n_warps) * 32) {
+        const uint64_t row = base + lane;
+        bool valid = row < is.row_end;
+        uint32_t gid;
+        uint64_t mask, vals[NS];
+        load_row<NS>(is, row, valid, gid, mask, vals, my_abs, status);
+        const uint32_t mlo = static_cast<uint32_t>(mask), mhi = static_cast<uint32_t>(mask >> 32);
+        uint32_t pending = __ballot_sync(kFull, valid);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const uint32_t g = __shfl_sync(kFull, gid, leader);
+            const uint32_t run = __ballot_sync(kFull, valid && gid == g);
+            pending &= ~run;
+            uint32_t c0, c1;
+            uint64_t acc[NS][2];
+            fold_run<NS>(is, run, mlo, mhi, vals, lane, c0, c1, acc);
+            uint64_t *cst = is.state + static_cast<size_t>(g) * kWorlds;
+            if (c0) atomicAdd(reinterpret_cast<unsigned long long *>(cst + lane), static_cast<unsigned long long>(c0));
+            if (c1) atomicAdd(reinterpret_cast<unsigned long long *>(cst + lane + 32), static_cast<unsigned long long>(c1));
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                if (s < is.n_slots) {
+                    uint64_t *sst = is.state + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
+                    if (c0) atomic_fold(is.slot[s].op, sst + lane, acc[s][0]);
+                    if (c1) atomic_fold(is.slot[s].op, sst + lane + 32, acc[s][1]);
+                }
+            }
+            if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(is.ng + g), static_cast<unsigned long long>(__popc(run)));
+        }
+    }
+    // int64 SUM guard: the wrapping atomics are exact while the query's total
+    // of |v| stays below 2^63, which bounds every world's sum
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (s >= is.n_slots || is.slot[s].op != OP_ISUM) continue;
+        unsigned long long m = my_abs[s];
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(kFull, m, o);
+            const unsigned long long u = m + t;
+            m = u < t ? ~0ull : u;
+        }
+        if (lane == 0 && m) {
+            const unsigned long long prev = atomicAdd(is.abs + s, m);
+            if (prev + m < prev || prev + m >= (1ull << 63)) raise_status(status, kStatusOverflow);
+        }
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQueryDev *__restrict__ qs,
+                                                                const BatchItem *__restrict__ items,
+                                                                uint32_t n_items, unsigned int *counter,
+                                                                uint32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ItemShared is;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t it = atomicAdd(counter, 1u);
+            is.item = it;
+            if (it < n_items) {
+                const BatchItem item = items[it];
+                const BatchQueryDev &q = qs[item.q];
+                is.in = q.in;
+                is.n_slots = q.n_slots;
+                is.mode = q.mode;
+                is.state = q.state;
+                is.ng = q.ng;
+                is.abs = q.abs;
+                is.row0 = item.row0;
+                is.row_end = item.row0 + item.rows;
+                is.k = item.k;
+            }
+        }
+        __syncthreads();
+        if (is.item >= n_items) break;
+        if (threadIdx.x < kMaxSpecs && static_cast<int>(threadIdx.x) < is.n_slots)
+            is.slot[threadIdx.x] = qs[items[is.item].q].slot[threadIdx.x];
+        __syncthreads();
+        if (is.mode == 0) item_warp_private<NS>(is, smem_raw, status);
+        else item_atomic<NS>(is, status);
+        __syncthreads();  // every thread is done with `is` before thread 0 refills it
+    }
+}
+
+// One thread per (query, group, world) cell of the whole batch.
+__global__ void __launch_bounds__(256) k_batch_merge(const BatchQueryDev *__restrict__ qs,
+                                                     const uint64_t *__restrict__ cell_prefix, int n_queries,
+                                                     uint64_t total_cells, uint32_t *status) {
+    const uint64_t cell = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+    const bool live = cell < total_cells;
+    // query of this cell: the last q with cell_prefix[q] <= cell (prefixes are multiples of 64)
+    int lo = 0, hi = n_queries - 1;
+    const uint64_t c = live ? cell : 0;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cell_prefix[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchQueryDev &q = qs[lo];
+    const uint64_t local = c - cell_prefix[lo];
+    const uint32_t G = q.in.n_groups;
+    const uint32_t g = static_cast<uint32_t>(local / kWorlds);
+    const int j = static_cast<int>(local % kWorlds);
+    const size_t per_q = static_cast<size_t>(G) * kWorlds;
+    const size_t per_part = per_q * (1 + q.n_slots);
+    const bool atomic = q.mode == 1;
+    const uint32_t parts = atomic ? 1u : q.n_items;
+
+    uint64_t cnt = 0;
+    if (live)
+        for (uint32_t k = 0; k < parts; k++) cnt += q.state[k * per_part + local];
+    // meta: rows and OR of masks (bit j set iff world j saw a row); a warp
+    // covers 32 worlds of one group because query prefixes are multiples of 64
+    const unsigned bal = __ballot_sync(kFull, live && cnt > 0);
+    if (!live) return;
+    if (q.meta) {
+        if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(q.meta + 2 * g + 1)[j >= 32 ? 1 : 0] = bal;
+        if (j == 0) {
+            uint64_t ng = 0;
+            for (uint32_t k = 0; k < parts; k++) ng += q.ng[static_cast<size_t>(k) * G + g];
+            q.meta[2 * g] = ng;
+        }
+    }
+    for (int s = 0; s < q.n_out; s++) {
+        const OutDev o = q.outs[s];
+        if (o.kind == PAC_COUNT) {
+            static_cast<uint64_t *>(o.out)[local] = cnt;
+            continue;
+        }
+        const int op = q.slot[o.slot].op;
+        const uint64_t *sp = q.state + static_cast<size_t>(o.slot + 1) * per_q + local;
+        if (op == OP_ISUM) {
+            __int128 tot = 0;
+            for (uint32_t k = 0; k < parts; k++) tot += static_cast<long long>(sp[k * per_part]);
+            const bool fits = tot >= static_cast<__int128>(LLONG_MIN) && tot <= static_cast<__int128>(LLONG_MAX);
+            if (!fits) raise_status(status, kStatusOverflow);
+            const long long v = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
+            if (o.kind == PAC_SUM) static_cast<long long *>(o.out)[local] = v;
+            else static_cast<double *>(o.out)[local] = cnt ? static_cast<double>(v) / static_cast<double>(cnt) : 0.0;
+        } else if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
+            double total;
+            if (atomic) {
+                total = op == OP_FSUM_COMP ? __longlong_as_double(static_cast<long long>(sp[0]))
+                                           : static_cast<double>(__int_as_float(static_cast<int>(sp[0])));
+            } else {
+                uint64_t a = sp[0];
+                for (uint32_t k = 1; k < parts; k++) op_merge(op, a, sp[k * per_part]);
+                total = static_cast<double>(__int_as_float(static_cast<int>(a)));
+                if (op == OP_FSUM_COMP) total += static_cast<double>(__int_as_float(static_cast<int>(a >> 32)));
+            }
+            if (o.kind == PAC_SUM) static_cast<double *>(o.out)[local] = total;
+            else static_cast<double *>(o.out)[local] = cnt ? total / static_cast<double>(cnt) : 0.0;
+        } else {
+            uint64_t a;
+            if (atomic) {
+                a = minmax_value(op, sp[0]);
+            } else {
+                a = sp[0];
+                for (uint32_t k = 1; k < parts; k++) op_merge(op, a, sp[k * per_part]);
+            }
+            if (op == OP_IMIN || op == OP_IMAX)
+                static_cast<long long *>(o.out)[local] = cnt ? static_cast<long long>(a) : 0ll;
+            else
+                static_cast<double *>(o.out)[local] = cnt ? __longlong_as_double(static_cast<long long>(a)) : 0.0;
+        }
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side: plans
+// ===========================================================================
+struct BatchConfig {
+    uint32_t item_rows;   // rows per work item (multiple of 32)
+    size_t smem_cap;      // warp-private states only when they fit this many bytes
+};
+
+}  // namespace pacgpu
+
+struct pac_batch {
+    int device = 0;
+    int n_queries = 0;
+    uint32_t n_items = 0;
+    int n_rel = 0;
+    int ns = 1;
+    size_t smem = 0;
+    int n_ctas = 0;
+    int n_warp_private = 0, n_atomic = 0;
+    pacgpu::BatchConfig cfg{};
+    void *dbuf = nullptr;
+    pacgpu::BatchQueryDev *d_q = nullptr;
+    pacgpu::BatchItem *d_items = nullptr;
+    uint64_t *d_prefix = nullptr;
+    pacgpu::FinParams *d_fin = nullptr;
+    unsigned int *d_counter = nullptr;
+    void *zero_base = nullptr;
+    size_t zero_bytes = 0;
+    uint64_t total_cells = 0;
+    uint32_t *d_status = nullptr;
+};
+
+namespace pacgpu {
+namespace {
+
+template <int NS>
+cudaError_t batch_kernel_setup(size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch_agg<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_agg<NS>, kBatchWarps * 32, smem);
+}
+
+// Builds (and uploads) a plan for one configuration.
+pac_status build_plan(pac_ctx *ctx, const pac_query *qs, int n_queries, const BatchConfig &cfg, pac_batch **out) {
+    pac_batch *b = new (std::nothrow) pac_batch();
+    if (!b) return fail(ctx, PAC_E_NOMEM, "plan allocation");
+    b->device = ctx->device;
+    b->n_queries = n_queries;
+    b->cfg = cfg;
+    b->d_status = ctx->d_status;
+    std::vector<BatchQueryDev> hq(n_queries);
+    std::vector<BatchItem> hitems;
+    std::vector<uint64_t> prefix(n_queries + 1, 0);
+    std::vector<FinParams> hfin;
+    std::vector<int> fin_q;
+    // largest slot count decides the kernel's register arrays
+    int max_slots = 0;
+    std::vector<int> nslots(n_queries, 0);
+    for (int i = 0; i < n_queries; i++) {
+        int ns = 0;
+        const void *vals[kMaxSpecs];
+        int ops[kMaxSpecs], vts[kMaxSpecs];
+        for (int s = 0; s < qs[i].n_specs; s++) {
+            const int op = spec_op(qs[i].specs[s]);
+            if (op < 0) continue;
+            bool seen = false;
+            for (int k = 0; k < ns; k++)
+                if (ops[k] == op && vals[k] == qs[i].specs[s].values && vts[k] == qs[i].specs[s].vtype) seen = true;
+            if (!seen) {
+                ops[ns] = op;
+                vals[ns] = qs[i].specs[s].values;
+                vts[ns] = qs[i].specs[s].vtype;
+                ns++;
+            }
+        }
+        nslots[i] = ns;
+        max_slots = std::max(max_slots, ns);
+    }
+    b->ns = bitloop_pick_ns(max_slots);
+    // layout: scratch that must start at zero comes first, then partials
+    size_t zero_off = 256;                  // item counter lives at offset 0
+    size_t part_off = 0;                    // relative, placed after the zeroed region
+    std::vector<size_t> z_state(n_queries), z_ng(n_queries), z_abs(n_queries), p_state(n_queries), p_ng(n_queries);
+    size_t smem_max = 1024;
+    for (int i = 0; i < n_queries; i++) {
+        const pac_query &q = qs[i];
+        BatchQueryDev &d = hq[i];
+        std::memset(&d, 0, sizeof(d));
+        d.in = make_input(&q.in);
+        d.meta = q.meta;
+        int slot_of[kMaxSpecs];
+        for (int s = 0; s < q.n_specs; s++) {
+            slot_of[s] = -1;
+            const int op = spec_op(q.specs[s]);
+            if (op < 0) continue;
+            for (int k = 0; k < d.n_slots; k++)
+                if (d.slot[k].op == op && d.slot[k].values == q.specs[s].values && d.slot[k].vtype == q.specs[s].vtype)
+                    slot_of[s] = k;
+            if (slot_of[s] < 0) {
+                d.slot[d.n_slots].op = op;
+                d.slot[d.n_slots].vtype = q.specs[s].vtype;
+                d.slot[d.n_slots].values = q.specs[s].values;
+                slot_of[s] = d.n_slots++;
+            }
+        }
+        for (int s = 0; s < q.n_specs; s++) {
+            d.outs[d.n_out].kind = q.specs[s].kind;
+            d.outs[d.n_out].slot = slot_of[s];
+            d.outs[d.n_out].out = q.specs[s].out;
+            d.n_out++;
+        }
+        const uint32_t G = q.in.n_groups;
+        const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
+        const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);
+        d.mode = smem_need <= cfg.smem_cap ? 0 : 1;
+        const uint64_t n = q.in.n;
+        const uint32_t n_items = n == 0 ? 1u : static_cast<uint32_t>((n + cfg.item_rows - 1) / cfg.item_rows);
+        d.first_item = static_cast<uint32_t>(hitems.size());
+        d.n_items = n_items;
+        for (uint32_t k = 0; k < n_items; k++) {
+            BatchItem it{};
+            it.q = static_cast<uint32_t>(i);
+            it.k = k;
+            it.row0 = static_cast<uint64_t>(k) * cfg.item_rows;
+            const uint64_t rem = n - std::min<uint64_t>(n, it.row0);
+            it.rows = static_cast<uint32_t>(std::min<uint64_t>(rem, cfg.item_rows));
+            hitems.push_back(it);
+        }
+        if (d.mode == 0) {
+            smem_max = std::max(smem_max, smem_need);
+            p_state[i] = align_up(part_off, 256);
+            part_off = p_state[i] + per_part * n_items;
+            p_ng[i] = align_up(part_off, 256);
+            part_off = p_ng[i] + static_cast<size_t>(G) * 8 * n_items;
+            b->n_warp_private++;
+        } else {
+            z_state[i] = align_up(zero_off, 256);
+            zero_off = z_state[i] + per_part;
+            z_ng[i] = align_up(zero_off, 256);
+            zero_off = z_ng[i] + static_cast<size_t>(G) * 8;
+            z_abs[i] = align_up(zero_off, 256);
+            zero_off = z_abs[i] + kMaxSpecs * 8;
+            b->n_atomic++;
+        }
+        prefix[i + 1] = prefix[i] + static_cast<uint64_t>(G) * kWorlds;
+        if (q.fin_mode >= 0) {
+            FinParams f{};
+            for (int s = 0; s < q.n_specs; s++) {
+                f.spec[s].kind = q.specs[s].kind;
+                f.spec[s].vtype = q.specs[s].kind == PAC_COUNT ? PAC_I64 : q.specs[s].vtype;
+                f.spec[s].variant = q.specs[s].variant;
+                f.spec[s].out = q.specs[s].out;
+            }
+            f.n_specs = q.n_specs;
+            f.n_groups = G;
+            f.meta = q.meta;
+            f.seed = q.seed;
+            f.budget = q.budget;
+            f.mode = q.fin_mode;
+            f.noised = q.noised;
+            f.is_null = q.is_null;
+            f.flags = q.flags;
+            f.posterior = nullptr;
+            hfin.push_back(f);
+        }
+    }
+    b->n_items = static_cast<uint32_t>(hitems.size());
+    b->n_rel = static_cast<int>(hfin.size());
+    b->total_cells = prefix[n_queries];
+    b->smem = smem_max;
+    const size_t zero_bytes = align_up(zero_off, 256);
+    size_t off = zero_bytes;
+    const size_t off_parts = align_up(off, 256);
+    off = off_parts + part_off;
+    const size_t off_q = align_up(off, 256);
+    off = off_q + sizeof(BatchQueryDev) * n_queries;
+    const size_t off_items = align_up(off, 256);
+    off = off_items + sizeof(BatchItem) * hitems.size();
+    const size_t off_prefix = align_up(off, 256);
+    off = off_prefix + sizeof(uint64_t) * prefix.size();
+    const size_t off_fin = align_up(off, 256);
+    off = off_fin + sizeof(FinParams) * hfin.size();
+    cudaError_t e = cudaMalloc(&b->dbuf, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(ctx, PAC_E_NOMEM, "batch plan: cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
+    }
+    char *base = static_cast<char *>(b->dbuf);
+    for (int i = 0; i < n_queries; i++) {
+        BatchQueryDev &d = hq[i];
+        if (d.mode == 0) {
+            d.state = reinterpret_cast<uint64_t *>(base + off_parts + p_state[i]);
+            d.ng = reinterpret_cast<uint64_t *>(base + off_parts + p_ng[i]);
+            d.abs = nullptr;
+        } else {
+            d.state = reinterpret_cast<uint64_t *>(base + z_state[i]);
+            d.ng = reinterpret_cast<uint64_t *>(base + z_ng[i]);
+            d.abs = reinterpret_cast<unsigned long long *>(base + z_abs[i]);
+        }
+    }
+    b->d_counter = reinterpret_cast<unsigned int *>(base);
+    b->zero_base = base;
+    b->zero_bytes = zero_bytes;
+    b->d_q = reinterpret_cast<BatchQueryDev *>(base + off_q);
+    b->d_items = reinterpret_cast<BatchItem *>(base + off_items);
+    b->d_prefix = reinterpret_cast<uint64_t *>(base + off_prefix);
+    b->d_fin = hfin.empty() ? nullptr : reinterpret_cast<FinParams *>(base + off_fin);
+    e = cudaMemcpy(b->d_q, hq.data(), sizeof(BatchQueryDev) * n_queries, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hitems.empty())
+        e = cudaMemcpy(b->d_items, hitems.data(), sizeof(BatchItem) * hitems.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_prefix, prefix.data(), sizeof(uint64_t) * prefix.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hfin.empty())
+        e = cudaMemcpy(b->d_fin, hfin.data(), sizeof(FinParams) * hfin.size(), cudaMemcpyHostToDevice);
+    int per_sm = 0;
+    if (e == cudaSuccess) {
+        switch (b->ns) {
+        case 1: e = batch_kernel_setup<1>(b->smem, &per_sm); break;
+        case 4: e = batch_kernel_setup<4>(b->smem, &per_sm); break;
+        default: e = batch_kernel_setup<kMaxSpecs>(b->smem, &per_sm); break;
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->dbuf);
+        delete b;
+        return cuda_fail(ctx, e, "batch plan upload");
+    }
+    b->n_ctas = ctx->n_sms * std::max(per_sm, 1);
+    *out = b;
+    return PAC_OK;
+}
+
+pac_status launch_plan(pac_ctx *ctx, pac_batch *b, cudaStream_t s) {
+    PAC_CUDA(ctx, cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s));
+    const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(b->n_ctas, std::max<uint32_t>(b->n_items, 1)));
+    switch (b->ns) {
+    case 1: k_batch_agg<1><<<grid, kBatchWarps * 32, b->smem, s>>>(b->d_q, b->d_items, b->n_items, b->d_counter, b->d_status); break;
+    case 4: k_batch_agg<4><<<grid, kBatchWarps * 32, b->smem, s>>>(b->d_q, b->d_items, b->n_items, b->d_counter, b->d_status); break;
+    default:
+        k_batch_agg<kMaxSpecs><<<grid, kBatchWarps * 32, b->smem, s>>>(b->d_q, b->d_items, b->n_items, b->d_counter,
+                                                                       b->d_status);
+        break;
+    }
+    PAC_CUDA(ctx, cudaGetLastError());
+    if (b->total_cells > 0) {
+        const uint64_t blocks = (b->total_cells + 255) / 256;
+        k_batch_merge<<<static_cast<unsigned>(blocks), 256, 0, s>>>(b->d_q, b->d_prefix, b->n_queries, b->total_cells,
+                                                                    b->d_status);
+        PAC_CUDA(ctx, cudaGetLastError());
+    }
+    if (b->n_rel > 0) PAC_CUDA(ctx, launch_finalize_batch(b->d_fin, b->n_rel, s));
+    return PAC_OK;
+}
+
+void free_plan(pac_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    if (b->dbuf) cudaFree(b->dbuf);
+    delete b;
+}
+
+pac_status check_batch(pac_ctx *ctx, const pac_query *qs, int32_t n) {
+    if (n < 1) return fail(ctx, PAC_E_INVALID, "n_queries %d", n);
+    if (!qs) return fail(ctx, PAC_E_INVALID, "queries is NULL");
+    for (int i = 0; i < n; i++) {
+        const pac_query &q = qs[i];
+        pac_status st = check_input(ctx, &q.in);
+        if (st == PAC_OK) st = check_specs(ctx, &q.in, q.specs, q.n_specs);
+        if (st == PAC_OK && q.n_specs < 1) st = fail(ctx, PAC_E_INVALID, "n_specs %d", q.n_specs);
+        if (st != PAC_OK) return fail(ctx, st, "query %d: %s", i, ctx->last_error.c_str());
+        for (int s = 0; s < q.n_specs; s++)
+            if (q.specs[s].variant != PAC_EXACT)
+                return fail(ctx, PAC_E_UNSUPPORTED, "query %d spec %d: batches serve PAC_EXACT specs only", i, s);
+        if (q.in.n > 0xFFFFFFFFull * 1024ull) return fail(ctx, PAC_E_INVALID, "query %d: too many rows", i);
+        if (q.fin_mode != -1) {
+            if (q.fin_mode != PAC_FIN_ADAPTIVE && q.fin_mode != PAC_FIN_INDEPENDENT)
+                return fail(ctx, PAC_E_INVALID, "query %d: fin_mode %d", i, q.fin_mode);
+            if (!q.meta || !q.noised || !q.is_null || !q.flags)
+                return fail(ctx, PAC_E_INVALID, "query %d: release needs meta and outputs", i);
+            if (!(q.budget > 0.0)) return fail(ctx, PAC_E_INVALID, "query %d: budget must be > 0", i);
+        }
+    }
+    return PAC_OK;
+}
+
+// Configurations the autotuner tries: work-item size x shared-memory cap.
+const BatchConfig kCandidates[] = {
+    {1u << 15, 48 * 1024}, {1u << 15, 100 * 1024}, {1u << 15, 200 * 1024},
+    {1u << 17, 48 * 1024}, {1u << 17, 100 * 1024}, {1u << 17, 200 * 1024},
+};
+constexpr BatchConfig kDefault = {1u << 16, 100 * 1024};
+
+uint64_t batch_signature(const pac_query *qs, int n) {
+    uint64_t rows = 0, cells = 0;
+    for (int i = 0; i < n; i++) {
+        rows += qs[i].in.n;
+        cells += qs[i].in.n_groups;
+    }
+    auto lg = [](uint64_t x) { uint64_t l = 0; while (x > 1) { x >>= 1; l++; } return l; };
+    return (static_cast<uint64_t>(n) << 32) ^ (lg(rows) << 16) ^ lg(cells + 1);
+}
+
+}  // namespace
+}  // namespace pacgpu
+
+using namespace pacgpu;
+
+namespace {
+// Autotune cache per process: batch signature -> configuration.
+std::map<uint64_t, BatchConfig> &tune_cache() {
+    static std::map<uint64_t, BatchConfig> m;
+    return m;
+}
+}  // namespace
+
+extern "C" {
+
+pac_status pac_batch_plan(pac_ctx *ctx, const pac_query *queries, int32_t n_queries, uint32_t flags,
+                          pac_batch **plan) {
+    if (!ctx || !plan) return PAC_E_INVALID;
+    *plan = nullptr;
+    pac_status st = check_batch(ctx, queries, n_queries);
+    if (st != PAC_OK) return st;
+    st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    BatchConfig cfg = kDefault;
+    const uint64_t sig = batch_signature(queries, n_queries);
+    auto hit = tune_cache().find(sig);
+    if (hit != tune_cache().end()) {
+        cfg = hit->second;
+    } else if (flags & PAC_BATCH_AUTOTUNE) {
+        cudaStream_t s = nullptr;
+        PAC_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (const BatchConfig &c : kCandidates) {
+            pac_batch *b = nullptr;
+            if (build_plan(ctx, queries, n_queries, c, &b) != PAC_OK) continue;
+            float ms = 1e30f;
+            if (launch_plan(ctx, b, s) == PAC_OK && cudaStreamSynchronize(s) == cudaSuccess) {
+                cudaEventRecord(e0, s);
+                launch_plan(ctx, b, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            free_plan(b);
+            if (ms < best) {
+                best = ms;
+                cfg = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(s);
+        cudaGetLastError();
+        tune_cache()[sig] = cfg;
+    }
+    return build_plan(ctx, queries, n_queries, cfg, plan);
+}
+
+pac_status pac_batch_launch(pac_ctx *ctx, pac_batch *plan, pac_stream stream) {
+    if (!ctx || !plan) return PAC_E_INVALID;
+    if (plan->device != ctx->device) return fail(ctx, PAC_E_INVALID, "plan belongs to device %d", plan->device);
+    pac_status st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    plan->d_status = ctx->d_status;
+    st = launch_plan(ctx, plan, stream);
+    if (st != PAC_OK) return st;
+    ctx->last_launches = 2 + (plan->total_cells > 0 ? 0 : -1) + (plan->n_rel > 0 ? 1 : 0);
+    return PAC_OK;
+}
+
+void pac_batch_free(pac_batch *plan) { free_plan(plan); }
+
+pac_status pac_batch_info(const pac_batch *plan, const char *name, int64_t *value) {
+    if (!plan || !name || !value) return PAC_E_INVALID;
+    if (!strcmp(name, "n_items")) *value = plan->n_items;
+    else if (!strcmp(name, "item_rows")) *value = plan->cfg.item_rows;
+    else if (!strcmp(name, "smem_cap")) *value = static_cast<int64_t>(plan->cfg.smem_cap);
+    else if (!strcmp(name, "kernels")) *value = 2 + (plan->total_cells > 0 ? 0 : -1) + (plan->n_rel > 0 ? 1 : 0);
+    else if (!strcmp(name, "n_warp_private")) *value = plan->n_warp_private;
+    else if (!strcmp(name, "n_atomic")) *value = plan->n_atomic;
+    else return PAC_E_INVALID;
+    return PAC_OK;
+}
+
+pac_status pac_batch_run(pac_ctx *ctx, const pac_query *queries, int32_t n_queries, pac_stream stream) {
+    pac_batch *plan = nullptr;
+    pac_status st = pac_batch_plan(ctx, queries, n_queries, 0, &plan);
+    if (st != PAC_OK) return st;
+    st = pac_batch_launch(ctx, plan, stream);
+    if (st == PAC_OK) st = pac_sync_status(ctx, stream);
+    else cudaStreamSynchronize(stream);
+    pac_batch_free(plan);
+    return st;
+}
+
+}  // extern "C"

@@ -138,6 +138,23 @@ __global__ void __launch_bounds__(256) k_finalize_independent(const __grid_const
     }
 }
 
+// One warp per query of a batch: the query's cells in order, under its own
+// posterior (adaptive) or the uniform prior per cell (independent).
+__global__ void __launch_bounds__(256) k_finalize_batch(const FinParams *__restrict__ ps, int n) {
+    const int lane = threadIdx.x & 31;
+    const int w = static_cast<int>((static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (w >= n) return;
+    const FinParams &p = ps[w];
+    const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> 58);
+    double logp0 = -log(64.0), logp1 = -log(64.0);
+    const uint64_t n_cells = static_cast<uint64_t>(p.n_groups) * p.n_specs;
+    for (uint64_t c = 0; c < n_cells; c++) release_cell(p, c, jstar, logp0, logp1);
+    if (p.posterior) {
+        p.posterior[lane] = exp(logp0);
+        p.posterior[lane + 32] = exp(logp1);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_finalize(const FinParams &p, cudaStream_t s) {
@@ -150,6 +167,13 @@ cudaError_t launch_finalize(const FinParams &p, cudaStream_t s) {
         if (blocks == 0) blocks = 1;
         k_finalize_independent<<<static_cast<unsigned>(blocks), 256, 0, s>>>(p);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const FinParams *d_params, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = static_cast<unsigned>((n + 7) / 8);
+    k_finalize_batch<<<blocks, 256, 0, s>>>(d_params, n);
     return cudaGetLastError();
 }
 

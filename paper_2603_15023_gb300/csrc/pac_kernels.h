@@ -98,5 +98,7 @@ struct FinParams {
     double *posterior;
 };
 cudaError_t launch_finalize(const FinParams &p, cudaStream_t s);
+// One warp per query: d_params[n] device array of per-query parameters.
+cudaError_t launch_finalize_batch(const FinParams *d_params, int n, cudaStream_t s);
 
 }  // namespace pacgpu

@@ -58,3 +58,27 @@ def test_create_without_gpu_fails_cleanly():
         pytest.skip("a GPU is present")
     with pytest.raises(B.PacError):
         B.pac_create(0)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of pac_input / pac_agg_spec / pac_query have the C
+    header's sizes and field offsets (checked by compiling a probe with gcc)."""
+    import ctypes
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "pac.h"\n'
+        'int main(void) {\n'
+        '  printf("%zu %zu %zu\\n", sizeof(pac_input), offsetof(pac_input, n_groups), offsetof(pac_input, n));\n'
+        '  printf("%zu %zu %zu\\n", sizeof(pac_agg_spec), offsetof(pac_agg_spec, values), offsetof(pac_agg_spec, out));\n'
+        '  printf("%zu %zu %zu %zu\\n", sizeof(pac_query), offsetof(pac_query, specs), offsetof(pac_query, seed),'
+        ' offsetof(pac_query, flags));\n'
+        '  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)])
+    got = [list(map(int, line.split())) for line in subprocess.check_output([str(exe)], text=True).splitlines()]
+    assert got[0] == [ctypes.sizeof(B.PacInput), B.PacInput.n_groups.offset, B.PacInput.n.offset]
+    assert got[1] == [ctypes.sizeof(B.PacAggSpec), B.PacAggSpec.values.offset, B.PacAggSpec.out.offset]
+    assert got[2] == [ctypes.sizeof(B.PacQuery), B.PacQuery.specs.offset, B.PacQuery.seed.offset,
+                      B.PacQuery.flags.offset]
