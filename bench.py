@@ -15,6 +15,9 @@ under the posterior + PAC noise).  Workloads (``--workload``):
   exact SUM.  The adaptive release of 2M cells is one sequential posterior
   chain, so the step is the aggregation alone and the release of all cells in
   the independent mode is timed once beside it (``finalize_ms``).
+* ``batch_4096``: 4096 independent queries (4.26G rows, 102 GB generated in
+  HBM), COUNT + exact int64 SUM + exact float32 SUM each; a step is one
+  replay of the CUDA graph holding the autotuned plan's launch.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
@@ -54,6 +57,10 @@ WORKLOADS = {
     "highcard_100m": {"gid_bytes": 4, "n_cols": 1, "aggs": "count+sum", "finalize": "separate",
                       "in_bytes_per_row": 8 + 4 + 8, "flush_l2": False,
                       "describe": "count + sum, exact; release of the 2M cells timed separately"},
+    "batch_4096": {"gid_bytes": 4, "n_cols": 2, "aggs": "count+sum+fsum", "finalize": "none",
+                   "in_bytes_per_row": 8 + 4 + 8 + 4, "flush_l2": False,
+                   "describe": "4096 independent queries (rows log-uniform 1e3..1e7, groups 1..1e4): count + "
+                               "exact int64 sum + exact float32 sum, one plan launch in a CUDA graph"},
 }
 
 
@@ -196,6 +203,29 @@ def cpu_oracle_sample(workload: str, rows: int, seed: int = 0):
     return rows / dt, dt
 
 
+def cpu_oracle_batch_sample(rows_budget: int, seed: int = 0):
+    """Times the oracle on the first queries of the batched workload (whole
+    queries, in order, until `rows_budget` rows): hash, COUNT, SUM, float SUM."""
+    import oracle as orc
+    from paper_2603_15023_gb300 import inputs
+    spec = inputs.batch_4096(seed=seed)
+    cols, rows = [], 0
+    for q in range(spec.n_queries):
+        if rows + int(spec.rows[q]) > rows_budget and cols:
+            break
+        cols.append((q, spec.columns(q)))
+        rows += int(spec.rows[q])
+    t0 = time.perf_counter()
+    for q, (keys, gids, v, f) in cols:
+        G = int(spec.groups[q])
+        masks = orc.hash_keys(keys, orc.query_key(1_000_000 + q), orc.BALANCED)
+        orc.aggregate(masks, None, gids, G, orc.COUNT)
+        orc.aggregate(masks, v, gids, G, orc.SUM)
+        orc.aggregate(masks, f, gids, G, orc.SUM)
+    dt = time.perf_counter() - t0
+    return rows / dt, dt, len(cols), rows
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -203,7 +233,10 @@ def run_reference(args):
     rows = args.ref_rows
     vals = []
     for i in range(args.warmup + args.steps):
-        v, dt = cpu_oracle_sample(args.workload, rows)
+        if args.workload == "batch_4096":
+            v, dt, _, _ = cpu_oracle_batch_sample(rows)
+        else:
+            v, dt = cpu_oracle_sample(args.workload, rows)
         if i >= args.warmup:
             vals.append((v, dt))
     value = statistics.median(v for v, _ in vals)
@@ -222,10 +255,114 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """The batched workload: every query's columns generated in HBM, one
+    autotuned plan, its launch captured in a CUDA graph; a step is one replay
+    (the aggregation of all queries)."""
+    import torch
+    from paper_2603_15023_gb300 import batch_inputs, inputs
+    from paper_2603_15023_gb300 import binding as B
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    ctx = B.pac_create(local)
+    spec = inputs.batch_4096(seed=rank, n_queries=args.queries)
+    s = torch.cuda.Stream()
+    db = batch_inputs.DeviceBatch(spec, stream=s.cuda_stream)
+    s.synchronize()
+    t0 = time.perf_counter()
+    plan = B.pac_batch_plan(ctx, db.queries, db.n_queries, 0 if args.no_autotune else B.PAC_BATCH_AUTOTUNE)
+    plan_s = time.perf_counter() - t0
+    info = {k: B.pac_batch_info(plan, k) for k in ("n_items", "item_rows", "smem_cap", "kernels",
+                                                    "n_warp_private", "n_atomic")}
+    with torch.cuda.stream(s):
+        B.pac_batch_launch(ctx, plan, s.cuda_stream)
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        B.pac_batch_launch(ctx, plan, s.cuda_stream)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            graph.replay()
+    s.synchronize()
+    st = B.pac_sync_status(ctx, s.cuda_stream)
+    if st != B.PAC_OK:
+        raise RuntimeError(B.status_name(st))
+    clocks = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(s):
+        start.record(s)
+        for i in range(args.steps):
+            evs[i][0].record(s)
+            graph.replay()
+            evs[i][1].record(s)
+        end.record(s)
+    torch.cuda.synchronize()
+    clocks.stop()
+    st = B.pac_sync_status(ctx, s.cuda_stream)
+    if st != B.PAC_OK:
+        raise RuntimeError(B.status_name(st))
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = start.elapsed_time(end) / args.steps
+    t = torch.tensor([ms_step], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t = t.cpu()
+    ms_step = float(t[0])
+    value = db.total_rows * world / (ms_step / 1e3)
+    peak, peak_src = _peaks()
+    algo = db.algorithmic_bytes()
+    achieved = algo / (statistics.mean(step_ms) / 1e3) / 1e9
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, dt, nq, rows = cpu_oracle_batch_sample(args.cpu_rows)
+            cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                   "sample": f"the first {nq} queries of batch_4096 ({rows} rows; hash, count, sum, float sum), "
+                             f"one thread, {dt:.1f} s"}
+        wcfg = WORKLOADS["batch_4096"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64+f32", "data": "synthetic (generated in HBM)",
+            "config": {"workload": "batch_4096", "queries": db.n_queries, "rows": db.total_rows,
+                       "groups_total": db.total_groups, "worlds": 64, "aggregates": wcfg["describe"],
+                       "l2": f"inputs {db.total_rows * wcfg['in_bytes_per_row'] / 1e9:.1f} GB > 129 MB L2",
+                       "plan": info, "plan_seconds_incl_autotune": plan_s},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_batch_agg + k_batch_merge (one graph replay)",
+                         "algorithmic_bytes": algo, "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "e2e": None,
+            "gpu_launches": info["kernels"] * args.steps,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+    B.pac_batch_free(plan)
+    B.pac_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2603_15023_gb300 import binding as B
 
+    if args.workload == "batch_4096":
+        return run_batch(args)
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     if world > 1:
@@ -409,6 +546,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=4_000_000)
     ap.add_argument("--ref-rows", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--queries", type=int, default=4096, help="batch_4096: number of queries")
+    ap.add_argument("--no-autotune", action="store_true", help="batch_4096: default plan configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -290,6 +290,57 @@ pac_status pac_batch_info(const pac_batch *plan, const char *name, int64_t *valu
 pac_status pac_batch_run(pac_ctx *ctx, const pac_query *queries, int32_t n_queries, pac_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * 5. Serving: continuous batching of incoming PAC queries (each one a
+ *    pac_query as above: aggregation of Sec. 4.2, release of Sec. 2 /
+ *    Sec. 4.1 when fin_mode >= 0).
+ *
+ * A server owns a worker thread, a device-memory arena of cfg.mem_budget
+ * bytes for the plans of admitted queries (their per-world states, partials
+ * and descriptors), a pinned staging area and cfg.n_streams CUDA streams.
+ * Submitted queries wait in arrival order; the worker admits as many as the
+ * arena's free space, cfg.max_inflight and cfg.max_batch allow, plans them
+ * as one batch inside the arena, and enqueues it on the next stream, so
+ * batches admitted while others run overlap on the device.  Completion is
+ * stamped on the host by a stream callback; the ticket's latency is from
+ * pac_serve_submit to that stamp.  The query's column buffers must stay
+ * valid and unmodified, and its output buffers untouched, until the ticket
+ * is done.  All entry points are thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    size_t mem_budget;    /* arena bytes for admitted plans (> 0) */
+    int32_t max_inflight; /* admitted, unfinished queries at most (>= 1) */
+    int32_t max_batch;    /* queries per launch at most (>= 1) */
+    int32_t n_streams;    /* streams carrying launches (1..8) */
+    int32_t reserved;     /* must be 0 */
+} pac_serve_config;
+
+typedef struct pac_server pac_server;
+
+/* Creates a server on ctx's device (the server keeps its own context). */
+pac_status pac_serve_create(pac_ctx *ctx, const pac_serve_config *cfg, pac_server **srv);
+
+/* Queues a copy of *q (its specs array is copied too) and returns its
+ * ticket.  PAC_E_INVALID / PAC_E_UNSUPPORTED as pac_batch_plan for a bad
+ * query; PAC_E_NOMEM when the query alone needs more than the arena. */
+pac_status pac_serve_submit(pac_server *srv, const pac_query *q, uint64_t *ticket);
+
+/* Non-blocking: *done = 1 once the ticket's results are in its output
+ * buffers (then *latency_ms, if not NULL, is its latency and the ticket is
+ * forgotten), else 0.  Returns the ticket's device status once done. */
+pac_status pac_serve_poll(pac_server *srv, uint64_t ticket, int32_t *done, double *latency_ms);
+
+/* Blocks until the ticket is done; as pac_serve_poll otherwise. */
+pac_status pac_serve_wait(pac_server *srv, uint64_t ticket, double *latency_ms);
+
+/* Server statistics over completed tickets: "completed", "batches",
+ * "mean_batch" (queries per launch), "p50_ms", "p99_ms", "max_ms",
+ * "max_inflight_seen", "arena_high_water" (bytes). */
+pac_status pac_serve_stats(pac_server *srv, const char *name, double *value);
+
+/* Finishes every queued and running query, then frees the server. */
+void pac_serve_destroy(pac_server *srv);
+
+/* ---------------------------------------------------------------------------
  * pac_aggregate_noalloc -- the paper has no counterpart: this is a service
  * of the library for callers that cannot allocate device memory.
  *

@@ -31,6 +31,8 @@ EXPORTED = (
     "pac_query_key", "pac_hash_keys", "pac_aggregate", "pac_aggregate_multi", "pac_finalize",
     "pac_query_host", "pac_set_option", "pac_get_info", "pac_aggregate_noalloc",
     "pac_batch_plan", "pac_batch_launch", "pac_batch_free", "pac_batch_info", "pac_batch_run",
+    "pac_serve_create", "pac_serve_submit", "pac_serve_poll", "pac_serve_wait", "pac_serve_stats",
+    "pac_serve_destroy",
 )
 PAC_BATCH_AUTOTUNE = 1
 
@@ -71,6 +73,16 @@ class PacQuery(ctypes.Structure):
         ("noised", ctypes.c_void_p),
         ("is_null", ctypes.c_void_p),
         ("flags", ctypes.c_void_p),
+    ]
+
+
+class PacServeConfig(ctypes.Structure):
+    _fields_ = [
+        ("mem_budget", ctypes.c_size_t),
+        ("max_inflight", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32),
+        ("n_streams", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -115,6 +127,12 @@ def lib() -> ctypes.CDLL:
         "pac_batch_free": (None, [vp]),
         "pac_batch_info": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(i64)]),
         "pac_batch_run": (i32, [vp, ctypes.POINTER(PacQuery), i32, vp]),
+        "pac_serve_create": (i32, [vp, ctypes.POINTER(PacServeConfig), ctypes.POINTER(vp)]),
+        "pac_serve_submit": (i32, [vp, ctypes.POINTER(PacQuery), ctypes.POINTER(u64)]),
+        "pac_serve_poll": (i32, [vp, u64, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+        "pac_serve_wait": (i32, [vp, u64, ctypes.POINTER(dbl)]),
+        "pac_serve_stats": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(dbl)]),
+        "pac_serve_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -266,3 +284,48 @@ def pac_batch_info(plan: int, name: str) -> int:
 def pac_batch_run(ctx: int, queries: ctypes.Array, n_queries: int, stream: int = 0) -> int:
     """Returns the status (device conditions included) instead of raising on them."""
     return lib().pac_batch_run(ctx, queries, n_queries, stream)
+
+
+# ---- serving -------------------------------------------------------------
+
+def pac_serve_create(ctx: int, mem_budget: int, max_inflight: int = 256, max_batch: int = 64,
+                     n_streams: int = 2) -> int:
+    h = ctypes.c_void_p()
+    cfg = PacServeConfig(mem_budget, max_inflight, max_batch, n_streams, 0)
+    _check(ctx, lib().pac_serve_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def pac_serve_submit(srv: int, query: PacQuery) -> int:
+    """Returns the ticket; raises PacError for a rejected query."""
+    t = ctypes.c_uint64(0)
+    st = lib().pac_serve_submit(srv, ctypes.byref(query), ctypes.byref(t))
+    if st != PAC_OK:
+        raise PacError(st, "pac_serve_submit")
+    return t.value
+
+
+def pac_serve_poll(srv: int, ticket: int):
+    """(done, latency_ms, status) without blocking."""
+    d, lat = ctypes.c_int32(0), ctypes.c_double(0.0)
+    st = lib().pac_serve_poll(srv, ticket, ctypes.byref(d), ctypes.byref(lat))
+    return bool(d.value), lat.value, st
+
+
+def pac_serve_wait(srv: int, ticket: int):
+    """(latency_ms, status); blocks until the ticket is done."""
+    lat = ctypes.c_double(0.0)
+    st = lib().pac_serve_wait(srv, ticket, ctypes.byref(lat))
+    return lat.value, st
+
+
+def pac_serve_stats(srv: int, name: str) -> float:
+    v = ctypes.c_double(0.0)
+    st = lib().pac_serve_stats(srv, name.encode(), ctypes.byref(v))
+    if st != PAC_OK:
+        raise PacError(st, f"pac_serve_stats({name})")
+    return v.value
+
+
+def pac_serve_destroy(srv: int) -> None:
+    lib().pac_serve_destroy(srv)

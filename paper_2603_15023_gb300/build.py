@@ -20,6 +20,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpac.so")
+# synthetic-input generator for benchmarks and tests: a library of its own,
+# so the method's library holds nothing but the method
+GEN_SRC = os.path.join(CSRC, "gen")
+GEN_LIB = os.path.join(HERE, "libpacgen.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -50,16 +54,18 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compiles and links libpac.so if any source changed; returns its path."""
+    """Compiles and links libpac.so and libpacgen.so if any source changed;
+    returns the path of libpac.so."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     headers = _headers()
     srcs = _sources()
-    objs = []
+    gen_srcs = sorted(glob.glob(os.path.join(GEN_SRC, "*.cu")))
+    objs, gen_objs = [], []
     jobs = []
-    for src in srcs:
+    for src in srcs + gen_srcs:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
+        (gen_objs if src in gen_srcs else objs).append(obj)
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
             jobs.append(cmd)
@@ -77,10 +83,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
+    for lib, lib_objs in ((LIB, objs), (GEN_LIB, gen_objs)):
+        if lib_objs and (force or jobs or _stale(lib, lib_objs)):
+            tmp = lib + f".tmp{os.getpid()}"
+            run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *lib_objs])
+            os.replace(tmp, lib)
     return LIB
 
 

@@ -29,34 +29,14 @@
 #include "pac_kernels.h"
 #include "pac_ops.cuh"
 #include "pac_validate.h"
+#include "pac_batch.h"
 
 namespace pacgpu {
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBatchWarps = 8;
 using namespace ops;
-
-struct BatchQueryDev {
-    InputDev in;
-    int32_t n_slots, n_out;
-    int32_t mode;  // 0: warp-private shared-memory states, 1: global atomics
-    int32_t pad;
-    SlotDev slot[kMaxSpecs];
-    OutDev outs[kMaxSpecs];
-    uint64_t *meta;
-    uint64_t *state;  // mode 0: [n_items][1+n_slots][G][64] partials; mode 1: [1+n_slots][G][64]
-    uint64_t *ng;     // mode 0: [n_items][G]; mode 1: [G]
-    unsigned long long *abs;  // mode 1: [n_slots] running sums of |v| (zeroed)
-    uint32_t first_item, n_items;
-};
-
-struct BatchItem {
-    uint32_t q, k;     // query, item index within the query
-    uint64_t row0;
-    uint32_t rows, pad;
-};
 
 // Order-preserving map of a MIN/MAX state value to an unsigned key whose
 // identity (the value no row can beat) is 0.
@@ -441,39 +421,10 @@ __global__ void __launch_bounds__(256) k_batch_merge(const BatchQueryDev *__rest
 
 }  // namespace
 
+
 // ===========================================================================
 // host side: plans
 // ===========================================================================
-struct BatchConfig {
-    uint32_t item_rows;   // rows per work item (multiple of 32)
-    size_t smem_cap;      // warp-private states only when they fit this many bytes
-};
-
-}  // namespace pacgpu
-
-struct pac_batch {
-    int device = 0;
-    int n_queries = 0;
-    uint32_t n_items = 0;
-    int n_rel = 0;
-    int ns = 1;
-    size_t smem = 0;
-    int n_ctas = 0;
-    int n_warp_private = 0, n_atomic = 0;
-    pacgpu::BatchConfig cfg{};
-    void *dbuf = nullptr;
-    pacgpu::BatchQueryDev *d_q = nullptr;
-    pacgpu::BatchItem *d_items = nullptr;
-    uint64_t *d_prefix = nullptr;
-    pacgpu::FinParams *d_fin = nullptr;
-    unsigned int *d_counter = nullptr;
-    void *zero_base = nullptr;
-    size_t zero_bytes = 0;
-    uint64_t total_cells = 0;
-    uint32_t *d_status = nullptr;
-};
-
-namespace pacgpu {
 namespace {
 
 template <int NS>
@@ -484,54 +435,32 @@ cudaError_t batch_kernel_setup(size_t smem, int *blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_agg<NS>, kBatchWarps * 32, smem);
 }
 
-// Builds (and uploads) a plan for one configuration.
-pac_status build_plan(pac_ctx *ctx, const pac_query *qs, int n_queries, const BatchConfig &cfg, pac_batch **out) {
+template <typename T>
+T *img_at(pac_batch *b, size_t off) {
+    return reinterpret_cast<T *>(b->image.data() + off);
+}
+
+}  // namespace
+
+pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const BatchConfig &cfg, pac_batch **out) {
     pac_batch *b = new (std::nothrow) pac_batch();
     if (!b) return fail(ctx, PAC_E_NOMEM, "plan allocation");
     b->device = ctx->device;
     b->n_queries = n_queries;
     b->cfg = cfg;
-    b->d_status = ctx->d_status;
     std::vector<BatchQueryDev> hq(n_queries);
     std::vector<BatchItem> hitems;
     std::vector<uint64_t> prefix(n_queries + 1, 0);
     std::vector<FinParams> hfin;
-    std::vector<int> fin_q;
-    // largest slot count decides the kernel's register arrays
+    b->rel_state.assign(n_queries, 0);
+    b->rel_ng.assign(n_queries, 0);
+    b->rel_abs.assign(n_queries, 0);
+    // the largest distinct-slot count decides the kernel's register arrays
     int max_slots = 0;
-    std::vector<int> nslots(n_queries, 0);
     for (int i = 0; i < n_queries; i++) {
-        int ns = 0;
-        const void *vals[kMaxSpecs];
-        int ops[kMaxSpecs], vts[kMaxSpecs];
-        for (int s = 0; s < qs[i].n_specs; s++) {
-            const int op = spec_op(qs[i].specs[s]);
-            if (op < 0) continue;
-            bool seen = false;
-            for (int k = 0; k < ns; k++)
-                if (ops[k] == op && vals[k] == qs[i].specs[s].values && vts[k] == qs[i].specs[s].vtype) seen = true;
-            if (!seen) {
-                ops[ns] = op;
-                vals[ns] = qs[i].specs[s].values;
-                vts[ns] = qs[i].specs[s].vtype;
-                ns++;
-            }
-        }
-        nslots[i] = ns;
-        max_slots = std::max(max_slots, ns);
-    }
-    b->ns = bitloop_pick_ns(max_slots);
-    // layout: scratch that must start at zero comes first, then partials
-    size_t zero_off = 256;                  // item counter lives at offset 0
-    size_t part_off = 0;                    // relative, placed after the zeroed region
-    std::vector<size_t> z_state(n_queries), z_ng(n_queries), z_abs(n_queries), p_state(n_queries), p_ng(n_queries);
-    size_t smem_max = 1024;
-    for (int i = 0; i < n_queries; i++) {
-        const pac_query &q = qs[i];
         BatchQueryDev &d = hq[i];
         std::memset(&d, 0, sizeof(d));
-        d.in = make_input(&q.in);
-        d.meta = q.meta;
+        const pac_query &q = qs[i];
         int slot_of[kMaxSpecs];
         for (int s = 0; s < q.n_specs; s++) {
             slot_of[s] = -1;
@@ -553,6 +482,19 @@ pac_status build_plan(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             d.outs[d.n_out].out = q.specs[s].out;
             d.n_out++;
         }
+        max_slots = std::max(max_slots, static_cast<int>(d.n_slots));
+    }
+    b->ns = bitloop_pick_ns(max_slots);
+    // device block: [zeroed scratch | partials | image]; offsets relative to it
+    size_t zero_off = 256;  // the item counter lives at offset 0
+    size_t part_off = 0;    // relative to the start of the partials region
+    std::vector<size_t> p_state(n_queries, 0), p_ng(n_queries, 0);
+    size_t smem_max = 1024;
+    for (int i = 0; i < n_queries; i++) {
+        const pac_query &q = qs[i];
+        BatchQueryDev &d = hq[i];
+        d.in = make_input(&q.in);
+        d.meta = q.meta;
         const uint32_t G = q.in.n_groups;
         const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
         const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);
@@ -578,12 +520,12 @@ pac_status build_plan(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             part_off = p_ng[i] + static_cast<size_t>(G) * 8 * n_items;
             b->n_warp_private++;
         } else {
-            z_state[i] = align_up(zero_off, 256);
-            zero_off = z_state[i] + per_part;
-            z_ng[i] = align_up(zero_off, 256);
-            zero_off = z_ng[i] + static_cast<size_t>(G) * 8;
-            z_abs[i] = align_up(zero_off, 256);
-            zero_off = z_abs[i] + kMaxSpecs * 8;
+            b->rel_state[i] = align_up(zero_off, 256);
+            zero_off = b->rel_state[i] + per_part;
+            b->rel_ng[i] = align_up(zero_off, 256);
+            zero_off = b->rel_ng[i] + static_cast<size_t>(G) * 8;
+            b->rel_abs[i] = align_up(zero_off, 256);
+            zero_off = b->rel_abs[i] + kMaxSpecs * 8;
             b->n_atomic++;
         }
         prefix[i + 1] = prefix[i] + static_cast<uint64_t>(G) * kWorlds;
@@ -612,120 +554,136 @@ pac_status build_plan(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
     b->n_rel = static_cast<int>(hfin.size());
     b->total_cells = prefix[n_queries];
     b->smem = smem_max;
-    const size_t zero_bytes = align_up(zero_off, 256);
-    size_t off = zero_bytes;
-    const size_t off_parts = align_up(off, 256);
-    off = off_parts + part_off;
-    const size_t off_q = align_up(off, 256);
-    off = off_q + sizeof(BatchQueryDev) * n_queries;
-    const size_t off_items = align_up(off, 256);
-    off = off_items + sizeof(BatchItem) * hitems.size();
-    const size_t off_prefix = align_up(off, 256);
-    off = off_prefix + sizeof(uint64_t) * prefix.size();
-    const size_t off_fin = align_up(off, 256);
-    off = off_fin + sizeof(FinParams) * hfin.size();
-    cudaError_t e = cudaMalloc(&b->dbuf, off);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        delete b;
-        return fail(ctx, PAC_E_NOMEM, "batch plan: cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
-    }
-    char *base = static_cast<char *>(b->dbuf);
+    b->zero_bytes = align_up(zero_off, 256);
+    const size_t parts_base = b->zero_bytes;
     for (int i = 0; i < n_queries; i++) {
-        BatchQueryDev &d = hq[i];
-        if (d.mode == 0) {
-            d.state = reinterpret_cast<uint64_t *>(base + off_parts + p_state[i]);
-            d.ng = reinterpret_cast<uint64_t *>(base + off_parts + p_ng[i]);
-            d.abs = nullptr;
-        } else {
-            d.state = reinterpret_cast<uint64_t *>(base + z_state[i]);
-            d.ng = reinterpret_cast<uint64_t *>(base + z_ng[i]);
-            d.abs = reinterpret_cast<unsigned long long *>(base + z_abs[i]);
+        if (hq[i].mode == 0) {
+            b->rel_state[i] = parts_base + p_state[i];
+            b->rel_ng[i] = parts_base + p_ng[i];
+            b->rel_abs[i] = SIZE_MAX;
         }
     }
-    b->d_counter = reinterpret_cast<unsigned int *>(base);
-    b->zero_base = base;
-    b->zero_bytes = zero_bytes;
-    b->d_q = reinterpret_cast<BatchQueryDev *>(base + off_q);
-    b->d_items = reinterpret_cast<BatchItem *>(base + off_items);
-    b->d_prefix = reinterpret_cast<uint64_t *>(base + off_prefix);
-    b->d_fin = hfin.empty() ? nullptr : reinterpret_cast<FinParams *>(base + off_fin);
-    e = cudaMemcpy(b->d_q, hq.data(), sizeof(BatchQueryDev) * n_queries, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !hitems.empty())
-        e = cudaMemcpy(b->d_items, hitems.data(), sizeof(BatchItem) * hitems.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_prefix, prefix.data(), sizeof(uint64_t) * prefix.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !hfin.empty())
-        e = cudaMemcpy(b->d_fin, hfin.data(), sizeof(FinParams) * hfin.size(), cudaMemcpyHostToDevice);
-    int per_sm = 0;
-    if (e == cudaSuccess) {
-        switch (b->ns) {
-        case 1: e = batch_kernel_setup<1>(b->smem, &per_sm); break;
-        case 4: e = batch_kernel_setup<4>(b->smem, &per_sm); break;
-        default: e = batch_kernel_setup<kMaxSpecs>(b->smem, &per_sm); break;
-        }
-    }
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(b->dbuf);
-        delete b;
-        return cuda_fail(ctx, e, "batch plan upload");
-    }
-    b->n_ctas = ctx->n_sms * std::max(per_sm, 1);
+    b->image_off = align_up(parts_base + part_off, 256);
+    // the image
+    size_t off = 0;
+    b->img_q = off;
+    off = align_up(off + sizeof(BatchQueryDev) * n_queries, 256);
+    b->img_items = off;
+    off = align_up(off + sizeof(BatchItem) * hitems.size(), 256);
+    b->img_prefix = off;
+    off = align_up(off + sizeof(uint64_t) * prefix.size(), 256);
+    b->img_fin = off;
+    off = align_up(off + sizeof(FinParams) * hfin.size(), 256);
+    b->image.assign(off, 0);
+    std::memcpy(b->image.data() + b->img_q, hq.data(), sizeof(BatchQueryDev) * n_queries);
+    if (!hitems.empty()) std::memcpy(b->image.data() + b->img_items, hitems.data(), sizeof(BatchItem) * hitems.size());
+    std::memcpy(b->image.data() + b->img_prefix, prefix.data(), sizeof(uint64_t) * prefix.size());
+    if (!hfin.empty()) std::memcpy(b->image.data() + b->img_fin, hfin.data(), sizeof(FinParams) * hfin.size());
+    b->device_bytes = b->image_off + b->image.size();
     *out = b;
     return PAC_OK;
 }
 
-pac_status launch_plan(pac_ctx *ctx, pac_batch *b, cudaStream_t s) {
-    PAC_CUDA(ctx, cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s));
+void plan_bind(pac_batch *b, void *dbuf) {
+    b->dbuf = dbuf;
+    char *base = static_cast<char *>(dbuf);
+    BatchQueryDev *q = img_at<BatchQueryDev>(b, b->img_q);
+    for (int i = 0; i < b->n_queries; i++) {
+        q[i].state = reinterpret_cast<uint64_t *>(base + b->rel_state[i]);
+        q[i].ng = reinterpret_cast<uint64_t *>(base + b->rel_ng[i]);
+        q[i].abs = b->rel_abs[i] == SIZE_MAX ? nullptr : reinterpret_cast<unsigned long long *>(base + b->rel_abs[i]);
+    }
+}
+
+pac_status plan_setup_kernel(pac_ctx *ctx, pac_batch *b) {
+    int per_sm = 0;
+    cudaError_t e;
+    switch (b->ns) {
+    case 1: e = batch_kernel_setup<1>(b->smem, &per_sm); break;
+    case 4: e = batch_kernel_setup<4>(b->smem, &per_sm); break;
+    default: e = batch_kernel_setup<kMaxSpecs>(b->smem, &per_sm); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch kernel setup");
+    b->n_ctas = ctx->n_sms * std::max(per_sm, 1);
+    return PAC_OK;
+}
+
+pac_status plan_enqueue(pac_ctx *ctx, pac_batch *b, cudaStream_t s, const void *image_src) {
+    char *base = static_cast<char *>(b->dbuf);
+    if (image_src)
+        PAC_CUDA(ctx, cudaMemcpyAsync(base + b->image_off, image_src, b->image.size(), cudaMemcpyHostToDevice, s));
+    PAC_CUDA(ctx, cudaMemsetAsync(base, 0, b->zero_bytes, s));
+    const BatchQueryDev *d_q = reinterpret_cast<const BatchQueryDev *>(base + b->image_off + b->img_q);
+    const BatchItem *d_items = reinterpret_cast<const BatchItem *>(base + b->image_off + b->img_items);
+    const uint64_t *d_prefix = reinterpret_cast<const uint64_t *>(base + b->image_off + b->img_prefix);
+    const FinParams *d_fin = reinterpret_cast<const FinParams *>(base + b->image_off + b->img_fin);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(base);
     const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(b->n_ctas, std::max<uint32_t>(b->n_items, 1)));
     switch (b->ns) {
-    case 1: k_batch_agg<1><<<grid, kBatchWarps * 32, b->smem, s>>>(b->d_q, b->d_items, b->n_items, b->d_counter, b->d_status); break;
-    case 4: k_batch_agg<4><<<grid, kBatchWarps * 32, b->smem, s>>>(b->d_q, b->d_items, b->n_items, b->d_counter, b->d_status); break;
+    case 1: k_batch_agg<1><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
+    case 4: k_batch_agg<4><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
     default:
-        k_batch_agg<kMaxSpecs><<<grid, kBatchWarps * 32, b->smem, s>>>(b->d_q, b->d_items, b->n_items, b->d_counter,
-                                                                       b->d_status);
+        k_batch_agg<kMaxSpecs><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status);
         break;
     }
     PAC_CUDA(ctx, cudaGetLastError());
     if (b->total_cells > 0) {
         const uint64_t blocks = (b->total_cells + 255) / 256;
-        k_batch_merge<<<static_cast<unsigned>(blocks), 256, 0, s>>>(b->d_q, b->d_prefix, b->n_queries, b->total_cells,
+        k_batch_merge<<<static_cast<unsigned>(blocks), 256, 0, s>>>(d_q, d_prefix, b->n_queries, b->total_cells,
                                                                     b->d_status);
         PAC_CUDA(ctx, cudaGetLastError());
     }
-    if (b->n_rel > 0) PAC_CUDA(ctx, launch_finalize_batch(b->d_fin, b->n_rel, s));
+    if (b->n_rel > 0) PAC_CUDA(ctx, launch_finalize_batch(d_fin, b->n_rel, s));
     return PAC_OK;
 }
 
-void free_plan(pac_batch *b) {
+void plan_destroy(pac_batch *b) {
     if (!b) return;
-    cudaSetDevice(b->device);
-    cudaDeviceSynchronize();
-    if (b->dbuf) cudaFree(b->dbuf);
+    if (b->owns_dbuf && b->dbuf) {
+        cudaSetDevice(b->device);
+        cudaDeviceSynchronize();
+        cudaFree(b->dbuf);
+    }
     delete b;
+}
+
+namespace {
+
+// A plan with its own device block, image uploaded synchronously.
+pac_status build_owned_plan(pac_ctx *ctx, const pac_query *qs, int n, const BatchConfig &cfg, pac_batch **out) {
+    pac_batch *b = nullptr;
+    pac_status st = plan_build(ctx, qs, n, cfg, &b);
+    if (st != PAC_OK) return st;
+    void *dbuf = nullptr;
+    cudaError_t e = cudaMalloc(&dbuf, b->device_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(ctx, PAC_E_NOMEM, "batch plan: cudaMalloc(%zu): %s", b->device_bytes, cudaGetErrorString(e));
+    }
+    b->owns_dbuf = true;
+    plan_bind(b, dbuf);
+    b->d_status = ctx->d_status;
+    e = cudaMemcpy(static_cast<char *>(dbuf) + b->image_off, b->image.data(), b->image.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        plan_destroy(b);
+        return cuda_fail(ctx, e, "batch plan upload");
+    }
+    st = plan_setup_kernel(ctx, b);
+    if (st != PAC_OK) {
+        plan_destroy(b);
+        return st;
+    }
+    *out = b;
+    return PAC_OK;
 }
 
 pac_status check_batch(pac_ctx *ctx, const pac_query *qs, int32_t n) {
     if (n < 1) return fail(ctx, PAC_E_INVALID, "n_queries %d", n);
     if (!qs) return fail(ctx, PAC_E_INVALID, "queries is NULL");
     for (int i = 0; i < n; i++) {
-        const pac_query &q = qs[i];
-        pac_status st = check_input(ctx, &q.in);
-        if (st == PAC_OK) st = check_specs(ctx, &q.in, q.specs, q.n_specs);
-        if (st == PAC_OK && q.n_specs < 1) st = fail(ctx, PAC_E_INVALID, "n_specs %d", q.n_specs);
+        pac_status st = check_query(ctx, &qs[i]);
         if (st != PAC_OK) return fail(ctx, st, "query %d: %s", i, ctx->last_error.c_str());
-        for (int s = 0; s < q.n_specs; s++)
-            if (q.specs[s].variant != PAC_EXACT)
-                return fail(ctx, PAC_E_UNSUPPORTED, "query %d spec %d: batches serve PAC_EXACT specs only", i, s);
-        if (q.in.n > 0xFFFFFFFFull * 1024ull) return fail(ctx, PAC_E_INVALID, "query %d: too many rows", i);
-        if (q.fin_mode != -1) {
-            if (q.fin_mode != PAC_FIN_ADAPTIVE && q.fin_mode != PAC_FIN_INDEPENDENT)
-                return fail(ctx, PAC_E_INVALID, "query %d: fin_mode %d", i, q.fin_mode);
-            if (!q.meta || !q.noised || !q.is_null || !q.flags)
-                return fail(ctx, PAC_E_INVALID, "query %d: release needs meta and outputs", i);
-            if (!(q.budget > 0.0)) return fail(ctx, PAC_E_INVALID, "query %d: budget must be > 0", i);
-        }
     }
     return PAC_OK;
 }
@@ -735,7 +693,6 @@ const BatchConfig kCandidates[] = {
     {1u << 15, 48 * 1024}, {1u << 15, 100 * 1024}, {1u << 15, 200 * 1024},
     {1u << 17, 48 * 1024}, {1u << 17, 100 * 1024}, {1u << 17, 200 * 1024},
 };
-constexpr BatchConfig kDefault = {1u << 16, 100 * 1024};
 
 uint64_t batch_signature(const pac_query *qs, int n) {
     uint64_t rows = 0, cells = 0;
@@ -743,22 +700,47 @@ uint64_t batch_signature(const pac_query *qs, int n) {
         rows += qs[i].in.n;
         cells += qs[i].in.n_groups;
     }
-    auto lg = [](uint64_t x) { uint64_t l = 0; while (x > 1) { x >>= 1; l++; } return l; };
+    auto lg = [](uint64_t x) {
+        uint64_t l = 0;
+        while (x > 1) {
+            x >>= 1;
+            l++;
+        }
+        return l;
+    };
     return (static_cast<uint64_t>(n) << 32) ^ (lg(rows) << 16) ^ lg(cells + 1);
 }
 
-}  // namespace
-}  // namespace pacgpu
-
-using namespace pacgpu;
-
-namespace {
 // Autotune cache per process: batch signature -> configuration.
 std::map<uint64_t, BatchConfig> &tune_cache() {
     static std::map<uint64_t, BatchConfig> m;
     return m;
 }
+
 }  // namespace
+
+pac_status check_query(pac_ctx *ctx, const pac_query *q) {
+    pac_status st = check_input(ctx, &q->in);
+    if (st == PAC_OK) st = check_specs(ctx, &q->in, q->specs, q->n_specs);
+    if (st == PAC_OK && q->n_specs < 1) st = fail(ctx, PAC_E_INVALID, "n_specs %d", q->n_specs);
+    if (st != PAC_OK) return st;
+    for (int s = 0; s < q->n_specs; s++)
+        if (q->specs[s].variant != PAC_EXACT)
+            return fail(ctx, PAC_E_UNSUPPORTED, "spec %d: batches serve PAC_EXACT specs only", s);
+    if (q->in.n > 0xFFFFFFFFull * 1024ull) return fail(ctx, PAC_E_INVALID, "too many rows");
+    if (q->fin_mode != -1) {
+        if (q->fin_mode != PAC_FIN_ADAPTIVE && q->fin_mode != PAC_FIN_INDEPENDENT)
+            return fail(ctx, PAC_E_INVALID, "fin_mode %d", q->fin_mode);
+        if (!q->meta || !q->noised || !q->is_null || !q->flags)
+            return fail(ctx, PAC_E_INVALID, "a release needs meta and its outputs");
+        if (!(q->budget > 0.0)) return fail(ctx, PAC_E_INVALID, "budget must be > 0");
+    }
+    return PAC_OK;
+}
+
+}  // namespace pacgpu
+
+using namespace pacgpu;
 
 extern "C" {
 
@@ -770,7 +752,7 @@ pac_status pac_batch_plan(pac_ctx *ctx, const pac_query *queries, int32_t n_quer
     if (st != PAC_OK) return st;
     st = bind_device(ctx);
     if (st != PAC_OK) return st;
-    BatchConfig cfg = kDefault;
+    BatchConfig cfg = kBatchDefault;
     const uint64_t sig = batch_signature(queries, n_queries);
     auto hit = tune_cache().find(sig);
     if (hit != tune_cache().end()) {
@@ -784,15 +766,15 @@ pac_status pac_batch_plan(pac_ctx *ctx, const pac_query *queries, int32_t n_quer
         float best = 1e30f;
         for (const BatchConfig &c : kCandidates) {
             pac_batch *b = nullptr;
-            if (build_plan(ctx, queries, n_queries, c, &b) != PAC_OK) continue;
+            if (build_owned_plan(ctx, queries, n_queries, c, &b) != PAC_OK) continue;
             float ms = 1e30f;
-            if (launch_plan(ctx, b, s) == PAC_OK && cudaStreamSynchronize(s) == cudaSuccess) {
+            if (plan_enqueue(ctx, b, s, nullptr) == PAC_OK && cudaStreamSynchronize(s) == cudaSuccess) {
                 cudaEventRecord(e0, s);
-                launch_plan(ctx, b, s);
+                plan_enqueue(ctx, b, s, nullptr);
                 cudaEventRecord(e1, s);
                 if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
             }
-            free_plan(b);
+            plan_destroy(b);
             if (ms < best) {
                 best = ms;
                 cfg = c;
@@ -804,7 +786,7 @@ pac_status pac_batch_plan(pac_ctx *ctx, const pac_query *queries, int32_t n_quer
         cudaGetLastError();
         tune_cache()[sig] = cfg;
     }
-    return build_plan(ctx, queries, n_queries, cfg, plan);
+    return build_owned_plan(ctx, queries, n_queries, cfg, plan);
 }
 
 pac_status pac_batch_launch(pac_ctx *ctx, pac_batch *plan, pac_stream stream) {
@@ -813,22 +795,23 @@ pac_status pac_batch_launch(pac_ctx *ctx, pac_batch *plan, pac_stream stream) {
     pac_status st = bind_device(ctx);
     if (st != PAC_OK) return st;
     plan->d_status = ctx->d_status;
-    st = launch_plan(ctx, plan, stream);
+    st = plan_enqueue(ctx, plan, stream, nullptr);
     if (st != PAC_OK) return st;
-    ctx->last_launches = 2 + (plan->total_cells > 0 ? 0 : -1) + (plan->n_rel > 0 ? 1 : 0);
+    ctx->last_launches = 2 + (plan->n_rel > 0 ? 1 : 0);
     return PAC_OK;
 }
 
-void pac_batch_free(pac_batch *plan) { free_plan(plan); }
+void pac_batch_free(pac_batch *plan) { plan_destroy(plan); }
 
 pac_status pac_batch_info(const pac_batch *plan, const char *name, int64_t *value) {
     if (!plan || !name || !value) return PAC_E_INVALID;
     if (!strcmp(name, "n_items")) *value = plan->n_items;
     else if (!strcmp(name, "item_rows")) *value = plan->cfg.item_rows;
     else if (!strcmp(name, "smem_cap")) *value = static_cast<int64_t>(plan->cfg.smem_cap);
-    else if (!strcmp(name, "kernels")) *value = 2 + (plan->total_cells > 0 ? 0 : -1) + (plan->n_rel > 0 ? 1 : 0);
+    else if (!strcmp(name, "kernels")) *value = 2 + (plan->n_rel > 0 ? 1 : 0);
     else if (!strcmp(name, "n_warp_private")) *value = plan->n_warp_private;
     else if (!strcmp(name, "n_atomic")) *value = plan->n_atomic;
+    else if (!strcmp(name, "device_bytes")) *value = static_cast<int64_t>(plan->device_bytes);
     else return PAC_E_INVALID;
     return PAC_OK;
 }

@@ -121,3 +121,79 @@ WORKLOADS = {
     "lowcard_60m": lowcard_60m,
     "highcard_100m": highcard_100m,
 }
+
+
+# ---------------------------------------------------------------------------
+# Counter-based columns (the host twin of the GPU generator in libpacgen.so):
+# draw `row` of `column` under `seed` is mix(mix(seed + (column+1) G) + (row+1) G)
+# with SplitMix64's output function `mix` and G its golden gamma.  Used for the
+# batched workload, whose 4.45G rows are generated on the device; any sampled
+# query can be regenerated here, bit for bit, for the oracle.
+# ---------------------------------------------------------------------------
+_G = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def counter_u64(seed: int, column: int, rows: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        start = _mix(np.asarray([np.uint64(seed) + (np.uint64(column) + np.uint64(1)) * _G], dtype=np.uint64))[0]
+        r = np.asarray(rows, dtype=np.uint64)
+        return _mix(start + (r + np.uint64(1)) * _G)
+
+
+def counter_i64(seed: int, column: int, n: int, lo: int, span: int, row0: int = 0) -> np.ndarray:
+    u = counter_u64(seed, column, np.arange(row0, row0 + n, dtype=np.uint64))
+    return (np.int64(lo) + (u % np.uint64(span)).astype(np.int64)).astype(np.int64)
+
+
+def counter_u32(seed: int, column: int, n: int, span: int, row0: int = 0) -> np.ndarray:
+    u = counter_u64(seed, column, np.arange(row0, row0 + n, dtype=np.uint64))
+    return (u % np.uint64(span)).astype(np.uint32)
+
+
+def counter_f32_1000(seed: int, column: int, n: int, row0: int = 0) -> np.ndarray:
+    u = counter_u64(seed, column, np.arange(row0, row0 + n, dtype=np.uint64))
+    return ((u >> np.uint64(40)).astype(np.float64) * (1000.0 / 16777216.0)).astype(np.float32)
+
+
+@dataclass
+class BatchSpec:
+    """Shapes of the batched workload: per query rows, groups and PU-key
+    domain; its columns come from the counter-based generator with column
+    ids 4*q + {0: key, 1: group id, 2: int64 value, 3: float32 value}."""
+    seed: int
+    rows: np.ndarray     # int64 [Q]
+    groups: np.ndarray   # int64 [Q]
+    keys: np.ndarray     # int64 [Q]
+
+    @property
+    def n_queries(self) -> int:
+        return int(self.rows.shape[0])
+
+    def columns(self, q: int):
+        """Host copy of query q's columns: keys int64, gids uint32, v int64, f float32."""
+        n, G, K = int(self.rows[q]), int(self.groups[q]), int(self.keys[q])
+        return (counter_i64(self.seed, 4 * q, n, 0, K), counter_u32(self.seed, 4 * q + 1, n, G),
+                counter_i64(self.seed, 4 * q + 2, n, 1, 100_000), counter_f32_1000(self.seed, 4 * q + 3, n))
+
+
+def _log_uniform(r: np.random.Generator, lo: float, hi: float, n: int) -> np.ndarray:
+    return np.exp(r.uniform(np.log(lo), np.log(hi), n))
+
+
+def batch_4096(seed: int = 0, n_queries: int = 4096, rows_lo: float = 1e3, rows_hi: float = 1e7,
+               groups_hi: float = 1e4, keys_lo: float = 1e3, keys_hi: float = 1e6) -> BatchSpec:
+    """4096 independent queries: rows log-uniform in [1e3, 1e7], groups
+    log-uniform integers in [1, 1e4], PU keys uniform over a domain whose size
+    is log-uniform in [1e3, 1e6]; int64 values uniform in [1, 1e5] and
+    float32 values uniform in [0, 1000)."""
+    r = _rng(seed, 1000)
+    rows = np.rint(_log_uniform(r, rows_lo, rows_hi, n_queries)).astype(np.int64)
+    groups = np.clip(np.rint(_log_uniform(r, 1.0, groups_hi, n_queries)), 1, groups_hi).astype(np.int64)
+    keys = np.rint(_log_uniform(r, keys_lo, keys_hi, n_queries)).astype(np.int64)
+    return BatchSpec(seed, rows, groups, keys)

@@ -261,3 +261,44 @@ def test_batch_rejects_bad_queries(ctx):
     q2 = B.make_query(q.query.in_, q.specs, 1, meta=0, fin_mode=B.PAC_FIN_ADAPTIVE)
     assert B.lib().pac_batch_plan(ctx, B.make_queries([q2]), 1, 0, ctypes.byref(h)) == B.PAC_E_INVALID
     assert B.lib().pac_batch_plan(ctx, arr, 0, 0, ctypes.byref(h)) == B.PAC_E_INVALID
+
+
+def test_batch_4096_full_size_sampled(ctx):
+    """The full batched workload (4096 queries, 4.26G rows generated in HBM)
+    in the launch configuration the benchmark times (autotuned plan): sampled
+    queries and worlds against the oracle on host-regenerated columns, every
+    world of those queries against the balanced invariants."""
+    T = _torch()
+    from paper_2603_15023_gb300 import batch_inputs
+    spec = inputs.batch_4096(seed=0)
+    s = T.cuda.Stream()
+    db = batch_inputs.DeviceBatch(spec, stream=s.cuda_stream)
+    s.synchronize()
+    plan = B.pac_batch_plan(ctx, db.queries, db.n_queries, B.PAC_BATCH_AUTOTUNE)
+    try:
+        B.pac_batch_launch(ctx, plan, s.cuda_stream)
+        s.synchronize()
+        assert B.pac_sync_status(ctx, s.cuda_stream) == B.PAC_OK
+    finally:
+        B.pac_batch_free(plan)
+    order = np.argsort(spec.rows)
+    picks = sorted({int(order[0]), int(order[1]), int(np.argmax(spec.groups)), int(np.argmax(spec.rows)),
+                    int(order[len(order) // 2]), 7, 4095})
+    for q in picks:
+        keys, gids, v, f = spec.columns(q)
+        G = int(spec.groups[q])
+        masks = orc.hash_keys(keys, db.query_key(q), orc.BALANCED)
+        cnt, sm, fs, meta = db.results(q)
+        for j in (0, 17, 40, 63):
+            c, _ = orc.aggregate_world(masks, None, gids, G, B.PAC_COUNT, j)
+            np.testing.assert_array_equal(cnt[:, j], c)
+            sj, _ = orc.aggregate_world(masks, v, gids, G, B.PAC_SUM, j)
+            np.testing.assert_array_equal(sm[:, j], sj)
+            fj, _ = orc.aggregate_world(masks, f, gids, G, B.PAC_SUM, j)
+            # float32 values are non-negative: sum |v| of the world = its sum
+            assert np.all(np.abs(fs[:, j] - fj) <= 1e-6 * np.abs(fj) + 1e-300)
+        ng = np.bincount(gids, minlength=G).astype(np.uint64)
+        np.testing.assert_array_equal(meta[:, 0], ng)
+        assert np.all(cnt[:, :32].astype(np.int64) + cnt[:, 32:].astype(np.int64) == ng.astype(np.int64)[:, None])
+        tot = np.bincount(gids, weights=v.astype(np.float64), minlength=G)
+        assert np.all(sm[:, :32] + sm[:, 32:] == np.rint(tot).astype(np.int64)[:, None])
