@@ -57,6 +57,10 @@ WORKLOADS = {
     "highcard_100m": {"gid_bytes": 4, "n_cols": 1, "aggs": "count+sum", "finalize": "separate",
                       "in_bytes_per_row": 8 + 4 + 8, "flush_l2": False,
                       "describe": "count + sum, exact; release of the 2M cells timed separately"},
+    "serving": {"gid_bytes": 4, "n_cols": 3, "aggs": "count+sum+fsum+dsum", "finalize": "adaptive",
+                "in_bytes_per_row": 8 + 4 + 8 + 4 + 8, "flush_l2": False,
+                "describe": "Poisson arrivals at 2000 queries/s, shapes of batch_4096, count + exact int64 sum + exact "
+                            "float32 sum + exact float64 lognormal(0,1.5) sum, adaptive release of every cell"},
     "batch_4096": {"gid_bytes": 4, "n_cols": 2, "aggs": "count+sum+fsum", "finalize": "none",
                    "in_bytes_per_row": 8 + 4 + 8 + 4, "flush_l2": False,
                    "describe": "4096 independent queries (rows log-uniform 1e3..1e7, groups 1..1e4): count + "
@@ -357,12 +361,130 @@ def run_batch(args):
     return 0
 
 
+def run_serving(args):
+    """Continuous batching under Poisson arrivals: a pool of query shapes drawn
+    from the batched workload's distribution lives in HBM (columns generated
+    on the device, plus a float64 lognormal(0, 1.5) column); every arrival
+    takes a pool shape, a seed and a slot of an output ring, and is submitted
+    to the server at its scheduled arrival time (or as soon as its ring slot
+    is free).  Latency = completion stamp - scheduled arrival."""
+    import torch
+    from paper_2603_15023_gb300 import binding as B
+    from paper_2603_15023_gb300 import gen, inputs
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    ctx = B.pac_create(local)
+    spec = inputs.batch_4096(seed=100 + rank, n_queries=args.pool)
+    P = spec.n_queries
+    s = torch.cuda.Stream()
+    cols = []
+    r = inputs._rng(100 + rank, 2000)
+    for q in range(P):
+        n, G, K = int(spec.rows[q]), int(spec.groups[q]), int(spec.keys[q])
+        k = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        g = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        v = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        f = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+        gen.fill_i64(k.data_ptr(), n, spec.seed, 4 * q, 0, K, stream=s.cuda_stream)
+        gen.fill_u32(g.data_ptr(), n, spec.seed, 4 * q + 1, G, stream=s.cuda_stream)
+        gen.fill_i64(v.data_ptr(), n, spec.seed, 4 * q + 2, 1, 100_000, stream=s.cuda_stream)
+        gen.fill_f32_1000(f.data_ptr(), n, spec.seed, 4 * q + 3, stream=s.cuda_stream)
+        d = torch.from_numpy(r.lognormal(0.0, 1.5, max(n, 1))).to("cuda")
+        cols.append((n, G, k, g, v, f, d))
+    s.synchronize()
+    max_g = int(spec.groups.max())
+    R = args.ring
+    ring = []
+    for _ in range(R):
+        outs = [torch.empty((max_g, 64), dtype=dt, device="cuda")
+                for dt in (torch.int64, torch.int64, torch.float64, torch.float64)]
+        meta = torch.empty((max_g, 2), dtype=torch.int64, device="cuda")
+        nz = torch.empty(max_g * 4, dtype=torch.float64, device="cuda")
+        nl = torch.empty(max_g * 4, dtype=torch.uint8, device="cuda")
+        fl = torch.empty(max_g * 4, dtype=torch.int32, device="cuda")
+        ring.append((outs, meta, nz, nl, fl))
+    srv = B.pac_serve_create(ctx, mem_budget=args.serve_mem_gb << 30, max_inflight=min(args.ring, 512),
+                             max_batch=64, n_streams=4)
+    lam = args.rate
+    n_req = int(lam * args.serve_seconds)
+    rr = inputs._rng(100 + rank, 3000)
+    arrivals = np.cumsum(rr.exponential(1.0 / lam, n_req))
+    shapes = rr.integers(0, P, n_req)
+    keep = []
+    tickets = [None] * n_req
+    t_sub = np.zeros(n_req)
+    busy = [None] * R
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        slot = i % R
+        if busy[slot] is not None:
+            j = busy[slot]
+            lat, st = B.pac_serve_wait(srv, tickets[j])
+            if st != B.PAC_OK:
+                raise RuntimeError(B.status_name(st))
+            tickets[j] = (t_sub[j] - arrivals[j] + lat / 1e3)
+        now = time.perf_counter() - t0
+        if now < arrivals[i]:
+            time.sleep(arrivals[i] - now)
+        n, G, k, g, v, f, d = cols[int(shapes[i])]
+        outs, meta, nz, nl, fl = ring[slot]
+        specs = B.make_specs([(B.PAC_COUNT, B.PAC_EXACT, B.PAC_I64, 0, outs[0].data_ptr()),
+                              (B.PAC_SUM, B.PAC_EXACT, B.PAC_I64, v.data_ptr(), outs[1].data_ptr()),
+                              (B.PAC_SUM, B.PAC_EXACT, B.PAC_F32, f.data_ptr(), outs[2].data_ptr()),
+                              (B.PAC_SUM, B.PAC_EXACT, B.PAC_F64, d.data_ptr(), outs[3].data_ptr())])
+        inp = B.make_input(k.data_ptr(), n, query_key=B.pac_query_key(7_000_000 + i), group_ids=g.data_ptr(),
+                           gid_bytes=4, n_groups=G)
+        qd = B.make_query(inp, specs, 4, meta=meta.data_ptr(), fin_mode=B.PAC_FIN_ADAPTIVE, seed=9_000 + i,
+                          budget=1.0 / 128, noised=nz.data_ptr(), is_null=nl.data_ptr(), flags=fl.data_ptr())
+        keep.append(specs)
+        t_sub[i] = time.perf_counter() - t0
+        tickets[i] = B.pac_serve_submit(srv, qd)
+        busy[slot] = i
+    for i in range(n_req):
+        if not isinstance(tickets[i], float):
+            lat, st = B.pac_serve_wait(srv, tickets[i])
+            if st != B.PAC_OK:
+                raise RuntimeError(B.status_name(st))
+            tickets[i] = (t_sub[i] - arrivals[i] + lat / 1e3)
+    wall = time.perf_counter() - t0
+    clocks.stop()
+    lat_ms = np.array(tickets, dtype=np.float64) * 1e3
+    rows = int(sum(cols[int(q)][0] for q in shapes))
+    stats = {k: B.pac_serve_stats(srv, k) for k in ("batches", "mean_batch", "max_inflight_seen",
+                                                     "arena_high_water")}
+    B.pac_serve_destroy(srv)
+    value = rows / wall
+    line = {
+        "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": n_req, "warmup": 0,
+        "ms_per_step": wall * 1e3 / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64+f32+f64", "data": "synthetic (generated in HBM)",
+        "config": {"workload": "serving", "arrival_rate_qps": lam, "requests": n_req, "pool_shapes": P,
+                   "offered_rows_per_s": rows / float(arrivals[-1]) if n_req else 0.0,
+                   "aggregates": WORKLOADS["serving"]["describe"], "server": stats,
+                   "output_ring_slots": R},
+        "latency": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                    "max_ms": float(lat_ms.max()), "definition": "completion stamp - scheduled Poisson arrival"},
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": int(stats["batches"]) * 3,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
+    B.pac_destroy(ctx)
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2603_15023_gb300 import binding as B
 
     if args.workload == "batch_4096":
         return run_batch(args)
+    if args.workload == "serving":
+        return run_serving(args)
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     if world > 1:
@@ -548,6 +670,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=4096, help="batch_4096: number of queries")
     ap.add_argument("--no-autotune", action="store_true", help="batch_4096: default plan configuration")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (queries/s)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--pool", type=int, default=64, help="serving: resident query shapes")
+    ap.add_argument("--ring", type=int, default=256, help="serving: output slots (outstanding requests)")
+    ap.add_argument("--serve-mem-gb", type=int, default=8, help="serving: server arena (GiB)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

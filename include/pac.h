@@ -376,11 +376,13 @@ pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_spec *specs,
 /* ---------------------------------------------------------------------------
  * Path selection and introspection (for benchmarks and tests).
  *   pac_set_option(ctx, name, value): "agg_path" 0 = automatic (tensor-core
- *   path where it applies), 1 = force the per-bit CUDA-core path, 2 = force
- *   the tensor-core path (PAC_E_UNSUPPORTED where it cannot serve).
- *   pac_get_info(ctx, name, &value): "last_path" (1 per-bit, 2 tensor core,
- *   3 partitioned high-cardinality), "last_launches" kernels launched by the
- *   last call.
+ *   path where it applies, else the per-bit engine), 1 = force the plain
+ *   per-bit CUDA-core kernels, 2 = force the tensor-core path
+ *   (PAC_E_UNSUPPORTED where it cannot serve), 3 = force the per-bit engine
+ *   (warp bit-transpose; the engine of the batched path).
+ *   pac_get_info(ctx, name, &value): "last_path" (1 plain per-bit, 2 tensor
+ *   core, 3 per-bit engine), "last_launches" kernels launched by the last
+ *   call.
  * ------------------------------------------------------------------------ */
 pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value);
 pac_status pac_get_info(pac_ctx *ctx, const char *name, int64_t *value);

@@ -11,6 +11,7 @@
 #include "pac_kernels.h"
 #include "pac_mma.h"
 #include "pac_validate.h"
+#include "pac_batch.h"
 
 using namespace pacgpu;
 
@@ -89,6 +90,62 @@ pac_status run_bitloop(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *sp
     return PAC_OK;
 }
 
+// The per-bit engine of the batched path (warp bit-transpose, warp-private
+// or atomic states) on one query: a one-query plan placed in the context's
+// workspace, its descriptors staged in pinned memory.
+pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                      uint64_t *meta, cudaStream_t stream, int *launches) {
+    pac_agg_spec kept[PAC_MAX_SPECS];
+    int k = 0;
+    for (int i = 0; i < n_specs; i++)
+        if (!spec_is_cascade(specs[i])) kept[k++] = specs[i];
+    if (k == 0 && !meta) return PAC_OK;
+    pac_query q{};
+    q.in = *in;
+    q.specs = kept;
+    q.n_specs = k;
+    q.fin_mode = -1;
+    q.meta = meta;
+    pac_batch *b = nullptr;
+    pac_status st = plan_build(ctx, &q, 1, kBatchDefault, &b);
+    if (st != PAC_OK) return st;
+    st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, b->device_bytes);
+    if (st == PAC_OK && ctx->pin_bytes < b->image.size()) {
+        if (ctx->pin) {
+            cudaEventSynchronize(ctx->pin_ev);
+            cudaFreeHost(ctx->pin);
+            ctx->pin = nullptr;
+        }
+        ctx->pin_bytes = 0;
+        const size_t want = b->image.size() * 2 + 4096;
+        if (cudaMallocHost(&ctx->pin, want) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(ctx, PAC_E_NOMEM, "pinned staging of %zu bytes", want);
+        } else {
+            ctx->pin_bytes = want;
+        }
+    }
+    if (st == PAC_OK && !ctx->pin_ev && cudaEventCreateWithFlags(&ctx->pin_ev, cudaEventDisableTiming) != cudaSuccess)
+        st = fail(ctx, PAC_E_CUDA, "event");
+    if (st != PAC_OK) {
+        plan_destroy(b);
+        return st;
+    }
+    cudaEventSynchronize(ctx->pin_ev);  // the previous copy out of the staging is done
+    plan_bind(b, ctx->ws);
+    b->d_status = ctx->d_status;
+    std::memcpy(ctx->pin, b->image.data(), b->image.size());
+    st = plan_setup_kernel(ctx, b);
+    if (st == PAC_OK) st = plan_enqueue(ctx, b, stream, ctx->pin);
+    if (st == PAC_OK && cudaEventRecord(ctx->pin_ev, stream) != cudaSuccess) st = fail(ctx, PAC_E_CUDA, "event record");
+    const bool b_atomic = b->n_atomic > 0;
+    plan_destroy(b);
+    if (st != PAC_OK) return st;
+    *launches += 2 + (b_atomic ? 3 : 0);
+    ctx->last_path = 3;
+    return PAC_OK;
+}
+
 pac_status run_cascades(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
                         cudaStream_t stream, int *launches) {
     for (int i = 0; i < n_specs; i++) {
@@ -133,16 +190,21 @@ pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
     int launches = 0;
     pac_status st;
     ctx->last_launches = 0;
-    // The tensor-core path serves COUNT and exact int64 SUM/AVG.
+    // The tensor-core path serves COUNT and exact int64 SUM/AVG over few
+    // groups; the per-bit engine serves everything else; agg_path 1 forces the
+    // plain per-bit kernels (the baseline the other paths are measured against).
     const int want = static_cast<int>(ctx->opt_agg_path);
-    bool mma_ok = want != 1 && mma_supported(in, specs, n_specs);
+    bool mma_ok = (want == 0 || want == 2) && mma_supported(in, specs, n_specs);
     if (want == 2 && !mma_ok) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path cannot serve this query");
     if (mma_ok) {
         st = run_mma(ctx, in, specs, n_specs, meta, stream, &launches);
         if (st != PAC_OK) return st;
         ctx->last_path = 2;
-    } else {
+    } else if (want == 1) {
         st = run_bitloop(ctx, in, specs, n_specs, meta, stream, &launches);
+        if (st != PAC_OK) return st;
+    } else {
+        st = run_engine(ctx, in, specs, n_specs, meta, stream, &launches);
         if (st != PAC_OK) return st;
     }
     st = run_cascades(ctx, in, specs, n_specs, stream, &launches);
@@ -189,6 +251,11 @@ void pac_destroy(pac_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->qws) cudaFree(ctx->qws);
+    if (ctx->pin_ev) {
+        cudaEventSynchronize(ctx->pin_ev);
+        cudaEventDestroy(ctx->pin_ev);
+    }
+    if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
 }
@@ -380,7 +447,7 @@ pac_status pac_query_host(pac_ctx *ctx, const pac_input *in_h, const pac_agg_spe
 pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value) {
     if (!ctx || !name) return PAC_E_INVALID;
     if (strcmp(name, "agg_path") == 0) {
-        if (value < 0 || value > 2) return fail(ctx, PAC_E_INVALID, "agg_path %lld", static_cast<long long>(value));
+        if (value < 0 || value > 3) return fail(ctx, PAC_E_INVALID, "agg_path %lld", static_cast<long long>(value));
         ctx->opt_agg_path = value;
         return PAC_OK;
     }

@@ -75,13 +75,49 @@ __device__ __forceinline__ void atomic_fold(int op, uint64_t *cell, uint64_t acc
 struct ItemShared {
     InputDev in;
     SlotDev slot[kMaxSpecs];
-    int32_t n_slots, mode;
+    int32_t n_slots, mode, bal;
     uint64_t *state, *ng;
     unsigned long long *abs;
     uint64_t row0, row_end;
     uint32_t k;
     uint32_t item;
+    // mode 1: rows read from the group-ordered copies
+    const uint64_t *smask;
+    const uint32_t *sgid;
+    const uint64_t *sval;
+    uint64_t n;
 };
+
+// ---------------------------------------------------------------------------
+// The per-bit engine on one 32-row batch of a warp.
+//
+// Lane r loads row r; the 32x32 bit matrix of world bits (row r, world j) is
+// transposed across the warp so that lane j holds T_j, the set of this
+// batch's rows in world j (a 32-bit row mask).  For every run R of rows of
+// one group, lane j then gets:
+//   count      popc(T_j & R);
+//   int64 SUM  sum_b 2^b popc(T_j & R & V_b), V_b = rows whose value has
+//              bit b (non-negative values of at most 32 bits, long runs), or
+//              a broadcast loop over the rows of R;
+//   float SUM  a broadcast loop over R in FP32, 8-row blocks folded into a
+//              compensated (two-sum) accumulator;
+//   MIN/MAX    a broadcast loop over R.
+// With balanced masks (world j+32 = complement of world j) COUNT and int64
+// SUM are kept for worlds 0..31 plus the run's total (exact integers, so
+// world j+32 = total - world j); float SUM and MIN/MAX keep both worlds,
+// since a float complement would cancel.  Without balance lane j also
+// holds T'_j for world j+32.  The run's contributions go to a sink: the warp's
+// private shared-memory state or the query's global state (atomics).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu : s == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t o = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~m) | ((o >> s) & m)) : ((x & m) | ((o << s) & ~m));
+    }
+    return x;
+}
 
 // Loads row `row`'s group, mask and slot values; invalid rows get valid=false.
 template <int NS>
@@ -91,6 +127,26 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
     const uint32_t G = is.in.n_groups;
     gid = 0;
     mask = 0;
+    if (is.smask) {  // group-ordered copy: ids already checked, masks already hashed
+        if (valid) {
+            gid = __ldg(is.sgid + row);
+            mask = __ldg(reinterpret_cast<const unsigned long long *>(is.smask) + row);
+        }
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            vals[s] = 0;
+            if (s < is.n_slots && valid) {
+                vals[s] = __ldg(reinterpret_cast<const unsigned long long *>(is.sval) + s * is.n + row);
+                if (is.slot[s].op == OP_ISUM) {
+                    const long long v = static_cast<long long>(vals[s]);
+                    const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+                    const uint64_t t = my_abs[s] + a;
+                    my_abs[s] = t < a ? ~0ull : t;
+                }
+            }
+        }
+        return;
+    }
     if (valid) {
         gid = row_gid(is.in, row);
         if (gid >= G) {  // out-of-range group id: skip the row, report it
@@ -116,35 +172,256 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
     }
 }
 
-// Folds the rows of group run `run` (a lane mask of this 32-row batch) into
-// this lane's two worlds: counts c0/c1 and one state per slot.
+// One run's contributions for this lane: worlds j (index 0) and j+32 (1).
 template <int NS>
-__device__ __forceinline__ void fold_run(const ItemShared &is, uint32_t run, uint32_t mlo, uint32_t mhi,
-                                         const uint64_t (&vals)[NS], int lane, uint32_t &c0, uint32_t &c1,
-                                         uint64_t (&acc)[NS][2]) {
-    c0 = c1 = 0;
+struct RunAcc {
+    uint32_t c0, c1;         // counts (c1 unused with bal)
+    uint32_t n;              // rows in the run (uniform)
+    uint64_t a0[NS], a1[NS]; // slot states of worlds j and j+32 (a1 unused for int64 SUM with bal)
+    uint64_t tot[NS];        // int64 SUM totals over the run (uniform)
+};
+
+__device__ __forceinline__ uint64_t pack_pair(float s, float c) {
+    return static_cast<uint32_t>(__float_as_int(s)) | (static_cast<uint64_t>(static_cast<uint32_t>(__float_as_int(c))) << 32);
+}
+
+// Folds one 8-row block sum into a compensated (sum, comp) pair.
+__device__ __forceinline__ void comp_add(float &s, float &c, float blk) {
+    float ns, e;
+    two_sum(s, blk, ns, e);
+    s = ns;
+    c += e;
+}
+
+// Fills `ra` for run R of this batch.  T0/T1: transposed world sets of
+// worlds j and j+32 (T1 ignored with bal).  slice[s]: bit count when slot s
+// may be bit-sliced (0: loop).
+template <int NS>
+__device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint32_t T0, uint32_t T1, bool bal,
+                                         const uint64_t (&vals)[NS], const int (&slice)[NS], int lane,
+                                         RunAcc<NS> &ra) {
+    const uint32_t M0 = T0 & R;
+    const uint32_t M1 = bal ? (R & ~T0) : (T1 & R);
+    ra.n = __popc(R);
+    ra.c0 = __popc(M0);
+    ra.c1 = __popc(M1);
+    bool any_loop = false;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        const uint64_t id = s < is.n_slots ? op_identity(is.slot[s].op) : 0ull;
-        acc[s][0] = id;
-        acc[s][1] = id;
+        if (s >= is.n_slots) continue;
+        const int op = is.slot[s].op;
+        ra.a0[s] = ra.a1[s] = op_identity(op);
+        ra.tot[s] = 0;
+        if (op == OP_ISUM && slice[s] > 0 && ra.n >= 8) {
+            uint64_t acc0 = 0, acc1 = 0, tot = 0;
+            for (int b = 0; b < slice[s]; b++) {
+                const uint32_t vb = __ballot_sync(kFull, (vals[s] >> b) & 1ull) & R;
+                acc0 += static_cast<uint64_t>(__popc(M0 & vb)) << b;
+                acc1 += static_cast<uint64_t>(__popc(M1 & vb)) << b;
+                tot += static_cast<uint64_t>(__popc(vb)) << b;
+            }
+            ra.a0[s] = acc0;
+            ra.a1[s] = acc1;
+            ra.tot[s] = tot;
+        } else {
+            any_loop = true;
+        }
     }
-    for (uint32_t rr = run; rr; rr &= rr - 1) {
+    if (!any_loop) return;
+    // broadcast loop over the rows of R for the remaining slots
+    float fs0[NS], fc0[NS], fb0[NS], fs1[NS], fc1[NS], fb1[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) fs0[s] = fc0[s] = fb0[s] = fs1[s] = fc1[s] = fb1[s] = 0.0f;
+    int blk = 0;
+    for (uint32_t rr = R; rr; rr &= rr - 1) {
         const int r = __ffs(rr) - 1;
-        const uint32_t b0 = (__shfl_sync(kFull, mlo, r) >> lane) & 1u;
-        const uint32_t b1 = (__shfl_sync(kFull, mhi, r) >> lane) & 1u;
-        c0 += b0;
-        c1 += b1;
+        const bool b0 = (M0 >> r) & 1u, b1 = (M1 >> r) & 1u;
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-            if (s < is.n_slots) {
-                const uint64_t v = __shfl_sync(kFull, vals[s], r);
-                op_update(is.slot[s].op, acc[s][0], v, b0);
-                op_update(is.slot[s].op, acc[s][1], v, b1);
+            if (s >= is.n_slots) continue;
+            const int op = is.slot[s].op;
+            if (op == OP_ISUM) {
+                if (slice[s] > 0 && ra.n >= 8) continue;
+                const uint64_t x = __shfl_sync(kFull, vals[s], r);
+                ra.a0[s] += b0 ? x : 0ull;
+                ra.a1[s] += b1 ? x : 0ull;
+                ra.tot[s] += x;
+            } else if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
+                const float x = __int_as_float(__shfl_sync(kFull, static_cast<int>(vals[s]), r));
+                fb0[s] += b0 ? x : 0.0f;
+                fb1[s] += b1 ? x : 0.0f;
+            } else {
+                const uint64_t x = __shfl_sync(kFull, vals[s], r);
+                op_update(op, ra.a0[s], x, b0 ? 1u : 0u);
+                op_update(op, ra.a1[s], x, b1 ? 1u : 0u);
+            }
+        }
+        if (++blk == 8) {
+            blk = 0;
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                comp_add(fs0[s], fc0[s], fb0[s]);
+                comp_add(fs1[s], fc1[s], fb1[s]);
+                fb0[s] = fb1[s] = 0.0f;
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (s >= is.n_slots) continue;
+        const int op = is.slot[s].op;
+        if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
+            comp_add(fs0[s], fc0[s], fb0[s]);
+            comp_add(fs1[s], fc1[s], fb1[s]);
+            if (op == OP_FSUM_COMP) {
+                ra.a0[s] = pack_pair(fs0[s], fc0[s]);
+                ra.a1[s] = pack_pair(fs1[s], fc1[s]);
+            } else {
+                ra.a0[s] = pack_pair(fs0[s] + fc0[s], 0.0f);
+                ra.a1[s] = pack_pair(fs1[s] + fc1[s], 0.0f);
             }
         }
     }
 }
+
+// States kept as worlds 0..31 + total with balanced masks (exact integers).
+__device__ __forceinline__ bool by_complement(int op, bool bal) { return bal && op == OP_ISUM; }
+
+// Processes rows [base, base+32) of the item: transposes, finds the runs and
+// hands every run to `sink(g, ra)`.
+template <int NS, typename Sink>
+__device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, uint64_t end, uint64_t (&my_abs)[NS],
+                                         uint32_t *status, Sink &sink) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t row = base + lane;
+    bool valid = row < end;
+    uint32_t gid;
+    uint64_t mask, vals[NS];
+    load_row<NS>(is, row, valid, gid, mask, vals, my_abs, status);
+    const bool bal = is.bal != 0;
+    const uint32_t T0 = warp_transpose32(valid ? static_cast<uint32_t>(mask) : 0u, lane);
+    const uint32_t T1 = bal ? 0u : warp_transpose32(valid ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
+    // bit-slicing is used for non-negative int64 values of at most 32 bits
+    int slice[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        slice[s] = 0;
+        if (s < is.n_slots && is.slot[s].op == OP_ISUM) {
+            const uint32_t hi = __reduce_or_sync(kFull, static_cast<uint32_t>(vals[s] >> 32));
+            const uint32_t lo = __reduce_or_sync(kFull, static_cast<uint32_t>(vals[s]));
+            slice[s] = hi ? 0 : 32 - __clz(static_cast<int>(lo));
+        }
+    }
+    uint32_t pending = __ballot_sync(kFull, valid);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const uint32_t g = __shfl_sync(kFull, gid, leader);
+        const uint32_t R = __ballot_sync(kFull, valid && gid == g);
+        pending &= ~R;
+        RunAcc<NS> ra;
+        run_fold<NS>(is, R, T0, T1, bal, vals, slice, lane, ra);
+        sink(g, ra, lane, bal);
+    }
+}
+
+// Sink into the warp's private shared-memory state.
+template <int NS>
+struct SmemSink {
+    const ItemShared &is;
+    uint64_t *st;    // this warp's [1+n_slots][G][64]
+    uint64_t *ng;    // this warp's [G]
+    uint32_t G;
+    __device__ __forceinline__ void operator()(uint32_t g, const RunAcc<NS> &ra, int lane, bool bal) {
+        uint64_t *cst = st + static_cast<size_t>(g) * kWorlds;
+        cst[lane] += ra.c0;
+        if (!bal) cst[lane + 32] += ra.c1;
+        else if (lane == 0) cst[32] += ra.n;
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            if (s >= is.n_slots) continue;
+            const int op = is.slot[s].op;
+            uint64_t *sst = st + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
+            op_merge(op, sst[lane], ra.a0[s]);
+            if (!by_complement(op, bal)) op_merge(op, sst[lane + 32], ra.a1[s]);
+            else if (lane == 0) op_merge(op, sst[32], ra.tot[s]);
+        }
+        if (lane == 0) ng[g] += ra.n;
+    }
+};
+
+// Sink into the query's global state with atomics.
+template <int NS>
+struct AtomicSink {
+    const ItemShared &is;
+    uint32_t G;
+    __device__ __forceinline__ void operator()(uint32_t g, const RunAcc<NS> &ra, int lane, bool bal) {
+        uint64_t *cst = is.state + static_cast<size_t>(g) * kWorlds;
+        if (ra.c0) atomicAdd(reinterpret_cast<unsigned long long *>(cst + lane), static_cast<unsigned long long>(ra.c0));
+        if (!bal) {
+            if (ra.c1) atomicAdd(reinterpret_cast<unsigned long long *>(cst + lane + 32), static_cast<unsigned long long>(ra.c1));
+        } else if (lane == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(cst + 32), static_cast<unsigned long long>(ra.n));
+        }
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            if (s >= is.n_slots) continue;
+            const int op = is.slot[s].op;
+            uint64_t *sst = is.state + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
+            if (ra.c0) atomic_fold(op, sst + lane, ra.a0[s]);
+            if (!by_complement(op, bal)) {
+                if (ra.c1) atomic_fold(op, sst + lane + 32, ra.a1[s]);
+            } else if (lane == 0) {
+                atomic_fold(op, sst + 32, ra.tot[s]);
+            }
+        }
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(is.ng + g), static_cast<unsigned long long>(ra.n));
+    }
+};
+
+// Adds run `b` into run accumulator `a` (same group).
+template <int NS>
+__device__ __forceinline__ void run_merge(const ItemShared &is, RunAcc<NS> &a, const RunAcc<NS> &b) {
+    a.c0 += b.c0;
+    a.c1 += b.c1;
+    a.n += b.n;
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (s >= is.n_slots) continue;
+        const int op = is.slot[s].op;
+        if (op == OP_ISUM) {
+            a.a0[s] += b.a0[s];
+            a.a1[s] += b.a1[s];
+            a.tot[s] += b.tot[s];
+        } else {
+            op_merge(op, a.a0[s], b.a0[s]);
+            op_merge(op, a.a1[s], b.a1[s]);
+        }
+    }
+}
+
+// Carries the current group's run across 32-row batches (rows in group
+// order) and flushes it to the global state with atomics when the group
+// changes and at the end of the item.
+template <int NS>
+struct CarrySink {
+    AtomicSink<NS> out;
+    const ItemShared &is;
+    RunAcc<NS> acc;
+    uint32_t g_cur = 0xFFFFFFFFu;
+    __device__ __forceinline__ void operator()(uint32_t g, const RunAcc<NS> &ra, int lane, bool bal) {
+        if (g == g_cur) {
+            run_merge<NS>(is, acc, ra);
+            return;
+        }
+        if (g_cur != 0xFFFFFFFFu) out(g_cur, acc, lane, bal);
+        acc = ra;
+        g_cur = g;
+    }
+    __device__ __forceinline__ void flush(int lane, bool bal) {
+        if (g_cur != 0xFFFFFFFFu) out(g_cur, acc, lane, bal);
+        g_cur = 0xFFFFFFFFu;
+    }
+};
 
 // One item of a query with warp-private shared-memory states.
 template <int NS>
@@ -168,37 +445,10 @@ __device__ void item_warp_private(const ItemShared &is, unsigned char *smem_raw,
     uint64_t my_abs[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) my_abs[s] = 0;
+    SmemSink<NS> sink{is, st, ng, G};
     for (uint64_t base = is.row0 + static_cast<uint64_t>(warp) * 32; base < is.row_end;
-         base += static_cast<uint64_t>(n_warps) * 32) {
-        const uint64_t row = base + lane;
-        bool valid = row < is.row_end;
-        uint32_t gid;
-        uint64_t mask, vals[NS];
-        load_row<NS>(is, row, valid, gid, mask, vals, my_abs, status);
-        const uint32_t mlo = static_cast<uint32_t>(mask), mhi = static_cast<uint32_t>(mask >> 32);
-        uint32_t pending = __ballot_sync(kFull, valid);
-        while (pending) {
-            const int leader = __ffs(pending) - 1;
-            const uint32_t g = __shfl_sync(kFull, gid, leader);
-            const uint32_t run = __ballot_sync(kFull, valid && gid == g);
-            pending &= ~run;
-            uint32_t c0, c1;
-            uint64_t acc[NS][2];
-            fold_run<NS>(is, run, mlo, mhi, vals, lane, c0, c1, acc);
-            uint64_t *cst = st + static_cast<size_t>(g) * kWorlds;
-            cst[lane] += c0;
-            cst[lane + 32] += c1;
-#pragma unroll
-            for (int s = 0; s < NS; s++) {
-                if (s < is.n_slots) {
-                    uint64_t *sst = st + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
-                    op_merge(is.slot[s].op, sst[lane], acc[s][0]);
-                    op_merge(is.slot[s].op, sst[lane + 32], acc[s][1]);
-                }
-            }
-            if (lane == 0) ng[g] += __popc(run);
-        }
-    }
+         base += static_cast<uint64_t>(n_warps) * 32)
+        batch32w<NS>(is, base, is.row_end, my_abs, status, sink);
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         uint64_t m = my_abs[s];
@@ -250,37 +500,16 @@ __device__ void item_atomic(const ItemShared &is, uint32_t *status) {
     uint64_t my_abs[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) my_abs[s] = 0;
-    for (uint64_t base = is.row0 + static_cast<uint64_t>(warp) * 32; base < is.row_end;
-         base += static_cast<uint64_t>(n_warps) * 32) {
-        const uint64_t row = base + lane;
-        bool valid = row < is.row_end;
-        uint32_t gid;
-        uint64_t mask, vals[NS];
-        load_row<NS>(is, row, valid, gid, mask, vals, my_abs, status);
-        const uint32_t mlo = static_cast<uint32_t>(mask), mhi = static_cast<uint32_t>(mask >> 32);
-        uint32_t pending = __ballot_sync(kFull, valid);
-        while (pending) {
-            const int leader = __ffs(pending) - 1;
-            const uint32_t g = __shfl_sync(kFull, gid, leader);
-            const uint32_t run = __ballot_sync(kFull, valid && gid == g);
-            pending &= ~run;
-            uint32_t c0, c1;
-            uint64_t acc[NS][2];
-            fold_run<NS>(is, run, mlo, mhi, vals, lane, c0, c1, acc);
-            uint64_t *cst = is.state + static_cast<size_t>(g) * kWorlds;
-            if (c0) atomicAdd(reinterpret_cast<unsigned long long *>(cst + lane), static_cast<unsigned long long>(c0));
-            if (c1) atomicAdd(reinterpret_cast<unsigned long long *>(cst + lane + 32), static_cast<unsigned long long>(c1));
-#pragma unroll
-            for (int s = 0; s < NS; s++) {
-                if (s < is.n_slots) {
-                    uint64_t *sst = is.state + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
-                    if (c0) atomic_fold(is.slot[s].op, sst + lane, acc[s][0]);
-                    if (c1) atomic_fold(is.slot[s].op, sst + lane + 32, acc[s][1]);
-                }
-            }
-            if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(is.ng + g), static_cast<unsigned long long>(__popc(run)));
-        }
-    }
+    CarrySink<NS> sink{AtomicSink<NS>{is, G}, is};
+    // each warp takes one contiguous stretch of the item, so group runs of
+    // the group-ordered rows stay long within a warp
+    const uint64_t span = is.row_end > is.row0 ? is.row_end - is.row0 : 0;
+    const uint64_t per_warp = ((span + n_warps - 1) / n_warps + 31) / 32 * 32;
+    const uint64_t w0 = is.row0 + static_cast<uint64_t>(warp) * per_warp;
+    const uint64_t w1 = min(is.row_end, w0 + per_warp);
+    ItemShared const &isr = is;
+    for (uint64_t base = w0; base < w1; base += 32) batch32w<NS>(isr, base, w1, my_abs, status, sink);
+    sink.flush(lane, is.bal != 0);
     // int64 SUM guard: the wrapping atomics are exact while the query's total
     // of |v| stays below 2^63, which bounds every world's sum
 #pragma unroll
@@ -316,12 +545,21 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQuery
                 is.in = q.in;
                 is.n_slots = q.n_slots;
                 is.mode = q.mode;
+                is.bal = q.bal;
                 is.state = q.state;
                 is.ng = q.ng;
                 is.abs = q.abs;
                 is.row0 = item.row0;
                 is.row_end = item.row0 + item.rows;
                 is.k = item.k;
+                is.smask = q.mode == 1 ? q.smask : nullptr;
+                is.sgid = q.sgid;
+                is.sval = q.sval;
+                is.n = q.in.n;
+                if (q.mode == 1) {
+                    const uint64_t kept = q.pcnt[q.in.n_groups];  // rows that survived the group-id check
+                    if (is.row_end > kept) is.row_end = kept;
+                }
             }
         }
         __syncthreads();
@@ -332,6 +570,108 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQuery
         if (is.mode == 0) item_warp_private<NS>(is, smem_raw, status);
         else item_atomic<NS>(is, status);
         __syncthreads();  // every thread is done with `is` before thread 0 refills it
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Partition of the many-group (mode 1) queries by group: a histogram of the
+// group ids, an exclusive scan per query, and a scatter of (mask, group id,
+// slot values) into group order.  Warps aggregate their atomics per group
+// (match_any): one atomic per distinct group of a 32-row batch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_part_hist(const BatchQueryDev *__restrict__ qs,
+                                                   const BatchItem *__restrict__ items, uint32_t n_items,
+                                                   uint32_t *status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem item = items[it];
+        const BatchQueryDev &q = qs[item.q];
+        if (q.mode != 1) continue;
+        const uint32_t G = q.in.n_groups;
+        const uint64_t end = item.row0 + item.rows;
+        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; base < end;
+             base += static_cast<uint64_t>(n_warps) * 32) {
+            const uint64_t r = base + lane;
+            bool valid = r < end;
+            uint32_t g = valid ? row_gid(q.in, r) : 0xFFFFFFFFu;
+            if (valid && g >= G) {  // out-of-range group id: the row is dropped, and reported
+                raise_status(status, kStatusBadGroup);
+                valid = false;
+                g = 0xFFFFFFFFu;
+            }
+            const uint32_t peers = __match_any_sync(kFull, g);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(q.pcnt + g, static_cast<uint32_t>(__popc(peers)));
+        }
+    }
+}
+
+// One CTA (1024 threads) per query: pcur = exclusive prefix of pcnt, and
+// pcnt[G] = the number of rows kept.
+__global__ void __launch_bounds__(1024) k_part_scan(const BatchQueryDev *__restrict__ qs) {
+    __shared__ uint32_t wsum[32];
+    const BatchQueryDev &q = qs[blockIdx.x];
+    if (q.mode != 1) return;
+    const uint32_t G = q.in.n_groups;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t chunk = (G + blockDim.x - 1) / blockDim.x;
+    const uint32_t g0 = min(G, t * chunk), g1 = min(G, g0 + chunk);
+    uint32_t local = 0;
+    for (uint32_t g = g0; g < g1; g++) local += q.pcnt[g];
+    uint32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < static_cast<int>(blockDim.x >> 5) ? wsum[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += v;
+        }
+        wsum[lane] = w;  // inclusive prefix over warps
+    }
+    __syncthreads();
+    uint32_t run = incl - local + (warp > 0 ? wsum[warp - 1] : 0u);
+    for (uint32_t g = g0; g < g1; g++) {
+        const uint32_t c = q.pcnt[g];
+        q.pcur[g] = run;
+        run += c;
+    }
+    if (t == static_cast<int>(blockDim.x) - 1) q.pcnt[G] = wsum[(blockDim.x >> 5) - 1];
+}
+
+__global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__restrict__ qs,
+                                                      const BatchItem *__restrict__ items, uint32_t n_items) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem item = items[it];
+        const BatchQueryDev &q = qs[item.q];
+        if (q.mode != 1) continue;
+        const uint32_t G = q.in.n_groups;
+        const uint64_t end = item.row0 + item.rows;
+        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; base < end;
+             base += static_cast<uint64_t>(n_warps) * 32) {
+            const uint64_t r = base + lane;
+            bool valid = r < end;
+            uint32_t g = valid ? row_gid(q.in, r) : 0xFFFFFFFFu;
+            if (valid && g >= G) {
+                valid = false;
+                g = 0xFFFFFFFFu;
+            }
+            const uint32_t peers = __match_any_sync(kFull, g);
+            const int leader = __ffs(peers) - 1;
+            uint32_t at = 0;
+            if (valid && lane == leader) at = atomicAdd(q.pcur + g, static_cast<uint32_t>(__popc(peers)));
+            at = __shfl_sync(kFull, at, leader);
+            if (!valid) continue;
+            const uint64_t d = at + __popc(peers & lt);
+            q.smask[d] = row_mask(q.in, r);
+            q.sgid[d] = g;
+            for (int s = 0; s < q.n_slots; s++) q.sval[static_cast<uint64_t>(s) * q.in.n + d] = load_slot_value(q.slot[s], r);
+        }
     }
 }
 
@@ -358,10 +698,20 @@ __global__ void __launch_bounds__(256) k_batch_merge(const BatchQueryDev *__rest
     const size_t per_part = per_q * (1 + q.n_slots);
     const bool atomic = q.mode == 1;
     const uint32_t parts = atomic ? 1u : q.n_items;
+    // balanced masks: COUNT / int64 SUM of world j >= 32 = group total - world j-32
+    const bool comp = q.bal != 0 && j >= 32;
+    const size_t src = comp ? local - 32 : local;        // world j-32
+    const size_t tot_at = local - j + 32;                 // the group's total
 
     uint64_t cnt = 0;
-    if (live)
-        for (uint32_t k = 0; k < parts; k++) cnt += q.state[k * per_part + local];
+    if (live) {
+        for (uint32_t k = 0; k < parts; k++) cnt += q.state[k * per_part + src];
+        if (comp) {
+            uint64_t tot = 0;
+            for (uint32_t k = 0; k < parts; k++) tot += q.state[k * per_part + tot_at];
+            cnt = tot - cnt;
+        }
+    }
     // meta: rows and OR of masks (bit j set iff world j saw a row); a warp
     // covers 32 worlds of one group because query prefixes are multiples of 64
     const unsigned bal = __ballot_sync(kFull, live && cnt > 0);
@@ -383,8 +733,14 @@ __global__ void __launch_bounds__(256) k_batch_merge(const BatchQueryDev *__rest
         const int op = q.slot[o.slot].op;
         const uint64_t *sp = q.state + static_cast<size_t>(o.slot + 1) * per_q + local;
         if (op == OP_ISUM) {
+            const uint64_t *sq = q.state + static_cast<size_t>(o.slot + 1) * per_q;
             __int128 tot = 0;
-            for (uint32_t k = 0; k < parts; k++) tot += static_cast<long long>(sp[k * per_part]);
+            for (uint32_t k = 0; k < parts; k++) tot += static_cast<long long>(sq[k * per_part + src]);
+            if (comp) {
+                __int128 all = 0;
+                for (uint32_t k = 0; k < parts; k++) all += static_cast<long long>(sq[k * per_part + tot_at]);
+                tot = all - tot;
+            }
             const bool fits = tot >= static_cast<__int128>(LLONG_MIN) && tot <= static_cast<__int128>(LLONG_MAX);
             if (!fits) raise_status(status, kStatusOverflow);
             const long long v = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
@@ -455,6 +811,11 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
     b->rel_state.assign(n_queries, 0);
     b->rel_ng.assign(n_queries, 0);
     b->rel_abs.assign(n_queries, 0);
+    b->rel_pcnt.assign(n_queries, SIZE_MAX);
+    b->rel_pcur.assign(n_queries, SIZE_MAX);
+    b->rel_smask.assign(n_queries, SIZE_MAX);
+    b->rel_sgid.assign(n_queries, SIZE_MAX);
+    b->rel_sval.assign(n_queries, SIZE_MAX);
     // the largest distinct-slot count decides the kernel's register arrays
     int max_slots = 0;
     for (int i = 0; i < n_queries; i++) {
@@ -484,17 +845,19 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         }
         max_slots = std::max(max_slots, static_cast<int>(d.n_slots));
     }
-    b->ns = bitloop_pick_ns(max_slots);
+    b->ns = max_slots <= 1 ? 1 : max_slots <= 2 ? 2 : max_slots <= 4 ? 4 : kMaxSpecs;
     // device block: [zeroed scratch | partials | image]; offsets relative to it
     size_t zero_off = 256;  // the item counter lives at offset 0
     size_t part_off = 0;    // relative to the start of the partials region
     std::vector<size_t> p_state(n_queries, 0), p_ng(n_queries, 0);
+    std::vector<size_t> p_pcur(n_queries, 0), p_smask(n_queries, 0), p_sgid(n_queries, 0), p_sval(n_queries, 0);
     size_t smem_max = 1024;
     for (int i = 0; i < n_queries; i++) {
         const pac_query &q = qs[i];
         BatchQueryDev &d = hq[i];
         d.in = make_input(&q.in);
         d.meta = q.meta;
+        d.bal = (q.in.in_flags == PAC_IN_KEYS && q.in.hash_mode == PAC_HASH_BALANCED) ? 1 : 0;
         const uint32_t G = q.in.n_groups;
         const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
         const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);
@@ -526,6 +889,17 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             zero_off = b->rel_ng[i] + static_cast<size_t>(G) * 8;
             b->rel_abs[i] = align_up(zero_off, 256);
             zero_off = b->rel_abs[i] + kMaxSpecs * 8;
+            b->rel_pcnt[i] = align_up(zero_off, 256);
+            zero_off = b->rel_pcnt[i] + (static_cast<size_t>(G) + 1) * 4;
+            // group-ordered copies (fully overwritten by the scatter)
+            p_pcur[i] = align_up(part_off, 256);
+            part_off = p_pcur[i] + static_cast<size_t>(G) * 4;
+            p_smask[i] = align_up(part_off, 256);
+            part_off = p_smask[i] + n * 8;
+            p_sgid[i] = align_up(part_off, 256);
+            part_off = p_sgid[i] + n * 4;
+            p_sval[i] = align_up(part_off, 256);
+            part_off = p_sval[i] + n * 8 * static_cast<size_t>(d.n_slots);
             b->n_atomic++;
         }
         prefix[i + 1] = prefix[i] + static_cast<uint64_t>(G) * kWorlds;
@@ -561,6 +935,11 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             b->rel_state[i] = parts_base + p_state[i];
             b->rel_ng[i] = parts_base + p_ng[i];
             b->rel_abs[i] = SIZE_MAX;
+        } else {
+            b->rel_pcur[i] = parts_base + p_pcur[i];
+            b->rel_smask[i] = parts_base + p_smask[i];
+            b->rel_sgid[i] = parts_base + p_sgid[i];
+            b->rel_sval[i] = parts_base + p_sval[i];
         }
     }
     b->image_off = align_up(parts_base + part_off, 256);
@@ -592,6 +971,12 @@ void plan_bind(pac_batch *b, void *dbuf) {
         q[i].state = reinterpret_cast<uint64_t *>(base + b->rel_state[i]);
         q[i].ng = reinterpret_cast<uint64_t *>(base + b->rel_ng[i]);
         q[i].abs = b->rel_abs[i] == SIZE_MAX ? nullptr : reinterpret_cast<unsigned long long *>(base + b->rel_abs[i]);
+        auto at = [&](size_t rel) { return rel == SIZE_MAX ? nullptr : base + rel; };
+        q[i].pcnt = reinterpret_cast<uint32_t *>(at(b->rel_pcnt[i]));
+        q[i].pcur = reinterpret_cast<uint32_t *>(at(b->rel_pcur[i]));
+        q[i].smask = reinterpret_cast<uint64_t *>(at(b->rel_smask[i]));
+        q[i].sgid = reinterpret_cast<uint32_t *>(at(b->rel_sgid[i]));
+        q[i].sval = reinterpret_cast<uint64_t *>(at(b->rel_sval[i]));
     }
 }
 
@@ -600,6 +985,7 @@ pac_status plan_setup_kernel(pac_ctx *ctx, pac_batch *b) {
     cudaError_t e;
     switch (b->ns) {
     case 1: e = batch_kernel_setup<1>(b->smem, &per_sm); break;
+    case 2: e = batch_kernel_setup<2>(b->smem, &per_sm); break;
     case 4: e = batch_kernel_setup<4>(b->smem, &per_sm); break;
     default: e = batch_kernel_setup<kMaxSpecs>(b->smem, &per_sm); break;
     }
@@ -619,8 +1005,17 @@ pac_status plan_enqueue(pac_ctx *ctx, pac_batch *b, cudaStream_t s, const void *
     const FinParams *d_fin = reinterpret_cast<const FinParams *>(base + b->image_off + b->img_fin);
     unsigned int *counter = reinterpret_cast<unsigned int *>(base);
     const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(b->n_ctas, std::max<uint32_t>(b->n_items, 1)));
+    if (b->n_atomic > 0) {
+        const unsigned pgrid = static_cast<unsigned>(std::min<uint64_t>(static_cast<uint64_t>(ctx->n_sms) * 8,
+                                                                        std::max<uint32_t>(b->n_items, 1)));
+        k_part_hist<<<pgrid, 256, 0, s>>>(d_q, d_items, b->n_items, b->d_status);
+        k_part_scan<<<static_cast<unsigned>(b->n_queries), 1024, 0, s>>>(d_q);
+        k_part_scatter<<<pgrid, 256, 0, s>>>(d_q, d_items, b->n_items);
+        PAC_CUDA(ctx, cudaGetLastError());
+    }
     switch (b->ns) {
     case 1: k_batch_agg<1><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
+    case 2: k_batch_agg<2><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
     case 4: k_batch_agg<4><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
     default:
         k_batch_agg<kMaxSpecs><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status);
@@ -797,7 +1192,7 @@ pac_status pac_batch_launch(pac_ctx *ctx, pac_batch *plan, pac_stream stream) {
     plan->d_status = ctx->d_status;
     st = plan_enqueue(ctx, plan, stream, nullptr);
     if (st != PAC_OK) return st;
-    ctx->last_launches = 2 + (plan->n_rel > 0 ? 1 : 0);
+    ctx->last_launches = 2 + (plan->n_rel > 0 ? 1 : 0) + (plan->n_atomic > 0 ? 3 : 0);
     return PAC_OK;
 }
 
@@ -808,7 +1203,7 @@ pac_status pac_batch_info(const pac_batch *plan, const char *name, int64_t *valu
     if (!strcmp(name, "n_items")) *value = plan->n_items;
     else if (!strcmp(name, "item_rows")) *value = plan->cfg.item_rows;
     else if (!strcmp(name, "smem_cap")) *value = static_cast<int64_t>(plan->cfg.smem_cap);
-    else if (!strcmp(name, "kernels")) *value = 2 + (plan->n_rel > 0 ? 1 : 0);
+    else if (!strcmp(name, "kernels")) *value = 2 + (plan->n_rel > 0 ? 1 : 0) + (plan->n_atomic > 0 ? 3 : 0);
     else if (!strcmp(name, "n_warp_private")) *value = plan->n_warp_private;
     else if (!strcmp(name, "n_atomic")) *value = plan->n_atomic;
     else if (!strcmp(name, "device_bytes")) *value = static_cast<int64_t>(plan->device_bytes);

@@ -15,14 +15,25 @@ struct BatchQueryDev {
     InputDev in;
     int32_t n_slots, n_out;
     int32_t mode;  // 0: warp-private shared-memory states, 1: global atomics
-    int32_t pad;
+    int32_t bal;   // balanced keyed masks: worlds 32..63 are the complements of 0..31
     SlotDev slot[kMaxSpecs];
     OutDev outs[kMaxSpecs];
     uint64_t *meta;
+    // per-world states [quantity][G][64], quantity 0 = COUNT, 1+s = slot s.
+    // With bal, COUNT and SUM states hold worlds 0..31 in entries 0..31 and
+    // the group's total in entry 32 (worlds 32..63 = total - world j-32);
+    // MIN/MAX states always hold all 64 worlds.
     uint64_t *state;  // mode 0: [n_items][1+n_slots][G][64] partials; mode 1: [1+n_slots][G][64]
     uint64_t *ng;     // mode 0: [n_items][G]; mode 1: [G]
     unsigned long long *abs;  // mode 1: [n_slots] running sums of |v| (zeroed)
     uint32_t first_item, n_items;
+    // mode 1: the rows partitioned by group before aggregation, so that runs
+    // of one group are long and atomics are paid once per run
+    uint32_t *pcnt;   // [G+1] rows per group (zeroed); [G] = rows kept after the scan
+    uint32_t *pcur;   // [G] scatter cursors
+    uint64_t *smask;  // [n] world masks in group order
+    uint32_t *sgid;   // [n] group ids in group order
+    uint64_t *sval;   // [n_slots][n] slot values (64-bit patterns) in group order
 };
 
 struct BatchItem {
@@ -58,6 +69,7 @@ struct pac_batch {
     std::vector<unsigned char> image;
     size_t img_q = 0, img_items = 0, img_prefix = 0, img_fin = 0;
     std::vector<size_t> rel_state, rel_ng, rel_abs;  // per query, relative to the device block
+    std::vector<size_t> rel_pcnt, rel_pcur, rel_smask, rel_sgid, rel_sval;  // mode-1 partition buffers
     size_t zero_bytes = 0, image_off = 0, device_bytes = 0;
     void *dbuf = nullptr;
     bool owns_dbuf = false;

@@ -16,6 +16,9 @@ struct pac_ctx {
     void *qws = nullptr;  // pac_query_host staging (inputs and outputs)
     size_t qws_bytes = 0;
     uint32_t *d_status = nullptr;
+    void *pin = nullptr;  // pinned staging of per-bit engine descriptors
+    size_t pin_bytes = 0;
+    cudaEvent_t pin_ev = nullptr;  // the last copy out of `pin`
     int64_t opt_agg_path = 0;
     int64_t last_path = 0;
     int64_t last_launches = 0;

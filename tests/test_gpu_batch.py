@@ -91,6 +91,15 @@ class Q:
     def release(self):
         return (self.noised.cpu().numpy(), self.is_null.cpu().numpy(), self.flags.cpu().numpy().view(np.uint32))
 
+    def abs_world(self, kind):
+        """Per (group, world) sum of |v| (divided by the count for AVG): the
+        scale of the float-sum tolerance."""
+        absw, *_ = orc.aggregate(self.masks, np.abs(self.vals).astype(np.float64), self.gids, self.G, B.PAC_SUM)
+        if kind == B.PAC_AVG:
+            cnt, *_ = orc.aggregate(self.masks, None, self.gids, self.G, B.PAC_COUNT)
+            absw = absw / np.maximum(cnt.astype(np.float64), 1)
+        return absw
+
     def check(self):
         got, meta = self.results()
         for kind, g_out in zip(self.kinds, got):
@@ -163,7 +172,7 @@ def test_mixed_batch_matches_oracle(ctx):
     qs = _mixed_batch()
     info = _run(ctx, qs)
     assert info["n_warp_private"] > 0 and info["n_atomic"] > 0, info
-    assert info["kernels"] == 3
+    assert info["kernels"] == 6   # partition (3) + aggregation + merge + release
     for q in qs:
         q.check()
 
@@ -224,7 +233,10 @@ def test_batch_in_cuda_graph(ctx):
                     if q.vt == B.PAC_I64 or kind in (B.PAC_COUNT, B.PAC_MIN, B.PAC_MAX):
                         np.testing.assert_array_equal(a, b)
                     else:
-                        np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-9)
+                        # float sums: rows of a group are summed in scatter order,
+                        # so replays agree within the bound, not bit for bit
+                        bound = q.abs_world(kind)
+                        assert np.all(np.abs(a - b) <= 2e-6 * bound + 1e-300)
                 np.testing.assert_array_equal(meta, r_meta)
         for q in qs:
             q.check()

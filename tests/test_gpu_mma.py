@@ -192,4 +192,4 @@ def test_auto_path_picks_tensor_cores(ctx):
     ctx.aggregate(w.keys, w.gids.astype(np.uint8), 4, [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, w.values[0])])
     assert ctx.last_path == 2
     ctx.aggregate(w.keys, w.gids.astype(np.uint8), 4, [(B.PAC_MAX, 0, w.values[0])])
-    assert ctx.last_path == 1
+    assert ctx.last_path == 3   # MAX: the per-bit engine

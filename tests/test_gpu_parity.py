@@ -220,3 +220,73 @@ def test_lowcard_60m_full_size_sampled(ctx):
     for k, v in enumerate(w.values):
         tot = np.array([v[w.gids == g].sum() for g in range(4)])
         assert np.all(got[1 + k][:, :32] + got[1 + k][:, 32:] == tot[:, None])
+
+
+@pytest.mark.parametrize("path", [1, 3])
+@pytest.mark.parametrize("mode", [B.PAC_HASH_BALANCED, B.PAC_HASH_RAW])
+@pytest.mark.parametrize("G,gdt", [(1, None), (17, np.uint16), (5000, np.int32)])
+@pytest.mark.parametrize("vdtype", [np.int64, np.float32, np.float64])
+def test_forced_per_bit_paths(ctx, path, mode, G, gdt, vdtype):
+    """The plain per-bit kernels (path 1) and the per-bit engine (path 3) on
+    every kind, both hash modes, few and many groups, against the oracle."""
+    n = 100_003
+    w = inputs.small(7 * G + n, n, G, 9_000, vdtype=vdtype, vlo=-10**6, vhi=10**6)
+    gids = None if G == 1 else w.gids.astype(gdt)
+    qk = orc.query_key(G)
+    masks = orc.hash_keys(w.keys, qk, mode)
+    specs = [(k, B.PAC_EXACT, None if k == B.PAC_COUNT else w.values[0]) for k in KINDS]
+    got, meta, st = ctx.aggregate(w.keys, gids, G, specs, qkey=qk, hash_mode=mode, path=path)
+    assert st == B.PAC_OK
+    assert ctx.last_path == path
+    for (kind, _, vals), g_out in zip(specs, got):
+        ref, mn, mo, rst = _oracle_all(masks, gids, G, kind, vals)
+        assert rst == 0
+        _check_exact(g_out, ref, kind, vals, masks, gids, G)
+    np.testing.assert_array_equal(meta[:, 0], mn)
+    np.testing.assert_array_equal(meta[:, 1], mo)
+
+
+@pytest.mark.parametrize("dist", ["narrow", "wide", "negative", "zeros"])
+def test_engine_int_sums_bit_sliced_and_looped(ctx, dist):
+    """Int64 SUM on the engine: narrow non-negative values take the bit-sliced
+    form, wide or negative ones the broadcast loop; both exact."""
+    n, G = 200_000, 3
+    r = np.random.default_rng(len(dist))
+    keys = r.integers(0, 50_000, n).astype(np.int64)
+    gids = np.sort(r.integers(0, G, n)).astype(np.uint8)   # long runs
+    vals = {"narrow": r.integers(0, 2**31, n), "wide": r.integers(0, 2**40, n),
+            "negative": r.integers(-10**9, 10**9, n), "zeros": np.zeros(n, dtype=np.int64)}[dist].astype(np.int64)
+    qk = orc.query_key(99)
+    masks = orc.hash_keys(keys, qk, orc.BALANCED)
+    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals), (B.PAC_AVG, 0, vals), (B.PAC_MIN, 0, vals)]
+    got, meta, st = ctx.aggregate(keys, gids, G, specs, qkey=qk, path=3)
+    assert st == B.PAC_OK and ctx.last_path == 3
+    for (kind, _, v), g_out in zip(specs, got):
+        ref, *_ = orc.aggregate(masks, v, gids, G, kind)
+        np.testing.assert_array_equal(g_out, ref)
+
+
+@pytest.mark.parametrize("G", [3, 3000])
+def test_engine_bad_group_ids_skipped_and_reported(ctx, G):
+    """Rows whose group id is >= n_groups are dropped (never written out of
+    bounds) and reported as PAC_E_INVALID; the other rows aggregate exactly,
+    on both state placements of the engine (few groups: shared memory; many
+    groups: partitioned rows with atomics)."""
+    n = 50_000
+    r = np.random.default_rng(G)
+    keys = r.integers(0, 9_000, n).astype(np.int64)
+    gids = r.integers(0, G, n).astype(np.int32)
+    bad = r.random(n) < 0.01
+    gids_bad = gids.copy()
+    gids_bad[bad] = G + 5
+    vals = r.integers(-1000, 1000, n).astype(np.int64)
+    qk = orc.query_key(5)
+    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals)]
+    got, meta, st = ctx.aggregate(keys, gids_bad, G, specs, qkey=qk, path=3)
+    assert st == B.PAC_E_INVALID
+    keep = ~bad
+    masks = orc.hash_keys(keys[keep], qk, orc.BALANCED)
+    for (kind, _, v), g_out in zip(specs, got):
+        ref, mn, mo, _ = orc.aggregate(masks, None if v is None else v[keep], gids[keep], G, kind)
+        np.testing.assert_array_equal(g_out, ref)
+    np.testing.assert_array_equal(meta[:, 0], mn)
