@@ -53,7 +53,8 @@ constexpr int kMaxGroups = 8;
 constexpr int kMaxCols = 4;
 constexpr uint32_t kMaxRowsPerCta = 1u << 20;  // keeps FP32 digit totals below 2^24
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kWaitLimit = 1u << 24;  // with <= 256 ns sleeps: a few seconds
+constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s of wall time
+constexpr uint32_t kSuspendHintNs = 20000;    // longest park of one try_wait
 
 // Accumulator / feature columns per group for C value columns.
 __host__ __device__ constexpr int feat_alloc(int C) { return C == 1 ? 32 : 80; }
@@ -81,25 +82,33 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait on an mbarrier phase; false when the limit ran out.  Polls
-// back off with __nanosleep so a waiting warp does not take issue slots from
-// the warps it is waiting for.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase; false once kWaitNs of wall time have
+// passed.  Each try_wait may park the warp until the phase completes
+// (suspend-time hint) and polls back off with __nanosleep, so a waiting warp
+// takes few issue slots from the warps it is waiting for.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     uint32_t done = 0;
     uint32_t ns = 16;
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
             : "memory");
         if (done) return true;
-        if (it >= 32) {
+        if (global_ns() - t0 > kWaitNs) return false;
+        if (it >= 8) {
             __nanosleep(ns);
             if (ns < 128) ns <<= 1;
         }
     }
-    return false;
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
