@@ -404,8 +404,8 @@ def run_serving(args):
         nl = torch.empty(max_g * 4, dtype=torch.uint8, device="cuda")
         fl = torch.empty(max_g * 4, dtype=torch.int32, device="cuda")
         ring.append((outs, meta, nz, nl, fl))
-    srv = B.pac_serve_create(ctx, mem_budget=args.serve_mem_gb << 30, max_inflight=min(args.ring, 512),
-                             max_batch=64, n_streams=4)
+    srv = B.pac_serve_create(ctx, mem_budget=args.serve_mem_gb << 30, max_inflight=args.ring,
+                             max_batch=256, n_streams=8)
     lam = args.rate
     n_req = int(lam * args.serve_seconds)
     rr = inputs._rng(100 + rank, 3000)
@@ -673,8 +673,8 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (queries/s)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--pool", type=int, default=64, help="serving: resident query shapes")
-    ap.add_argument("--ring", type=int, default=256, help="serving: output slots (outstanding requests)")
-    ap.add_argument("--serve-mem-gb", type=int, default=8, help="serving: server arena (GiB)")
+    ap.add_argument("--ring", type=int, default=512, help="serving: output slots (outstanding requests)")
+    ap.add_argument("--serve-mem-gb", type=int, default=32, help="serving: server arena (GiB)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

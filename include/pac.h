@@ -298,9 +298,10 @@ pac_status pac_batch_run(pac_ctx *ctx, const pac_query *queries, int32_t n_queri
  * bytes for the plans of admitted queries (their per-world states, partials
  * and descriptors), a pinned staging area and cfg.n_streams CUDA streams.
  * Submitted queries wait in arrival order; the worker admits as many as the
- * arena's free space, cfg.max_inflight and cfg.max_batch allow, plans them
- * as one batch inside the arena, and enqueues it on the next stream, so
- * batches admitted while others run overlap on the device.  Completion is
+ * arena's free space, cfg.max_inflight and cfg.max_batch allow as soon as
+ * one of its streams is idle, plans them as one batch inside the arena, and
+ * enqueues it on that stream, so batches admitted while others run overlap
+ * on the device and arrivals during busy periods are batched together.  Completion is
  * stamped on the host by a stream callback; the ticket's latency is from
  * pac_serve_submit to that stamp.  The query's column buffers must stay
  * valid and unmodified, and its output buffers untouched, until the ticket
@@ -310,7 +311,9 @@ typedef struct {
     size_t mem_budget;    /* arena bytes for admitted plans (> 0) */
     int32_t max_inflight; /* admitted, unfinished queries at most (>= 1) */
     int32_t max_batch;    /* queries per launch at most (>= 1) */
-    int32_t n_streams;    /* streams carrying launches (1..8) */
+    int32_t n_streams;    /* streams carrying launches (1..32); a batch is
+                             launched only when a stream is idle, with
+                             everything queued (up to max_batch) */
     int32_t reserved;     /* must be 0 */
 } pac_serve_config;
 

@@ -79,6 +79,7 @@ struct Ticket {
 };
 
 struct Flight {
+    int stream_idx = -1;
     pac_batch *plan = nullptr;
     size_t arena_off = 0, arena_bytes = 0;
     size_t stage_off = 0, stage_bytes = 0;
@@ -110,7 +111,7 @@ struct pac_server {
     size_t pinned_bytes = 0;
     RangeAlloc *arena_alloc = nullptr, *pin_alloc = nullptr;
     std::vector<cudaStream_t> streams;
-    int next_stream = 0;
+    std::vector<Flight *> stream_busy;  // the flight each stream is running (nullptr: idle)
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
@@ -153,6 +154,7 @@ void retire(pac_server *s) {
             s->lat.push_back(t.latency_ms);
         }
         s->inflight_q -= static_cast<int>(f->tickets.size());
+        if (f->stream_idx >= 0 && s->stream_busy[f->stream_idx] == f) s->stream_busy[f->stream_idx] = nullptr;
         if (f->arena_bytes) s->arena_alloc->release(f->arena_off, f->arena_bytes);
         if (f->stage_bytes) s->pin_alloc->release(f->stage_off, f->stage_bytes);
         s->arena_used -= f->arena_bytes;
@@ -166,7 +168,7 @@ void retire(pac_server *s) {
 
 // Plans, places and enqueues the queries `ids` (lock NOT held).  Returns
 // the flight, or nullptr when the arena or staging cannot hold the plan now.
-Flight *launch_batch(pac_server *s, const std::vector<uint64_t> &ids, std::unique_lock<std::mutex> &lk) {
+Flight *launch_batch(pac_server *s, const std::vector<uint64_t> &ids, int si, std::unique_lock<std::mutex> &lk) {
     std::vector<pac_query> qs;
     qs.reserve(ids.size());
     for (uint64_t id : ids) qs.push_back(s->tickets[id].q);
@@ -205,8 +207,9 @@ Flight *launch_batch(pac_server *s, const std::vector<uint64_t> &ids, std::uniqu
     f->tickets = ids;
     s->arena_used += b->device_bytes;
     s->arena_hw = std::max(s->arena_hw, s->arena_used);
-    const cudaStream_t stream = s->streams[s->next_stream];
-    s->next_stream = (s->next_stream + 1) % static_cast<int>(s->streams.size());
+    const cudaStream_t stream = s->streams[si];
+    f->stream_idx = si;
+    s->stream_busy[si] = f;
     lk.unlock();
     char *dev = static_cast<char *>(s->arena) + aoff;
     char *pin = s->pinned + poff;
@@ -239,7 +242,15 @@ void worker_main(pac_server *s) {
         if (s->stop && s->queue.empty() && s->flights.empty()) break;
         bool launched = false;
         const int room = std::min(s->cfg.max_batch, s->cfg.max_inflight - s->inflight_q);
-        if (!s->queue.empty() && room > 0) {
+        // launch only on an idle stream: while all streams are busy, arrivals
+        // queue up and go out together as one larger batch
+        int si = -1;
+        for (int k = 0; k < static_cast<int>(s->streams.size()); k++)
+            if (!s->stream_busy[k]) {
+                si = k;
+                break;
+            }
+        if (!s->queue.empty() && room > 0 && si >= 0) {
             std::vector<uint64_t> ids;
             size_t need = 0;
             for (size_t i = 0; i < s->queue.size() && static_cast<int>(ids.size()) < room; i++) {
@@ -249,7 +260,7 @@ void worker_main(pac_server *s) {
                 ids.push_back(s->queue[i]);
             }
             while (!ids.empty()) {
-                Flight *f = launch_batch(s, ids, lk);
+                Flight *f = launch_batch(s, ids, si, lk);
                 if (f) {
                     for (size_t k = 0; k < ids.size(); k++) s->queue.pop_front();
                     for (uint64_t id : ids) s->tickets[id].state = 1;
@@ -277,7 +288,7 @@ pac_status pac_serve_create(pac_ctx *ctx, const pac_serve_config *cfg, pac_serve
     if (!ctx || !cfg || !srv) return PAC_E_INVALID;
     *srv = nullptr;
     if (cfg->mem_budget == 0 || cfg->max_inflight < 1 || cfg->max_batch < 1 || cfg->n_streams < 1 ||
-        cfg->n_streams > 8 || cfg->reserved != 0)
+        cfg->n_streams > 32 || cfg->reserved != 0)
         return fail(ctx, PAC_E_INVALID, "bad server configuration");
     pac_server *s = new (std::nothrow) pac_server();
     if (!s) return fail(ctx, PAC_E_NOMEM, "server allocation");
@@ -296,6 +307,7 @@ pac_status pac_serve_create(pac_ctx *ctx, const pac_serve_config *cfg, pac_serve
         e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
         if (e == cudaSuccess) s->streams.push_back(q);
     }
+    s->stream_busy.assign(s->streams.size(), nullptr);
     if (e != cudaSuccess) {
         cudaGetLastError();
         for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
