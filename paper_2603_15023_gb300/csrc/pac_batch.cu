@@ -119,8 +119,27 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
     return x;
 }
 
+// Slot operations of a batch whose queries share one spec signature are
+// compile-time constants (no per-row dispatch on the operation); SIG 0 reads
+// them from the query at run time.
+//   SIG 1: {int64 SUM}                     (COUNT + SUM)
+//   SIG 2: {int64 SUM, float SUM}
+//   SIG 3: {int64 SUM, float SUM, float SUM}
+//   SIG 4: {float SUM}
+template <int SIG>
+__device__ __forceinline__ int op_of(const ItemShared &is, int s) {
+    if (SIG == 1) return OP_ISUM;
+    if (SIG == 2 || SIG == 3) return s == 0 ? OP_ISUM : OP_FSUM_COMP;
+    if (SIG == 4) return OP_FSUM_COMP;
+    return is.slot[s].op;
+}
+template <int SIG>
+__device__ __forceinline__ int nslots_of(const ItemShared &is) {
+    return SIG == 1 ? 1 : SIG == 2 ? 2 : SIG == 3 ? 3 : SIG == 4 ? 1 : is.n_slots;
+}
+
 // Loads row `row`'s group, mask and slot values; invalid rows get valid=false.
-template <int NS>
+template <int NS, int SIG>
 __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, bool &valid, uint32_t &gid,
                                          uint64_t &mask, uint64_t (&vals)[NS], uint64_t (&my_abs)[NS],
                                          uint32_t *status) {
@@ -135,9 +154,9 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
 #pragma unroll
         for (int s = 0; s < NS; s++) {
             vals[s] = 0;
-            if (s < is.n_slots && valid) {
+            if (s < nslots_of<SIG>(is) && valid) {
                 vals[s] = __ldg(reinterpret_cast<const unsigned long long *>(is.sval) + s * is.n + row);
-                if (is.slot[s].op == OP_ISUM) {
+                if (op_of<SIG>(is, s) == OP_ISUM) {
                     const long long v = static_cast<long long>(vals[s]);
                     const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
                     const uint64_t t = my_abs[s] + a;
@@ -160,9 +179,9 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         vals[s] = 0;
-        if (s < is.n_slots && valid) {
+        if (s < nslots_of<SIG>(is) && valid) {
             vals[s] = load_slot_value(is.slot[s], row);
-            if (is.slot[s].op == OP_ISUM) {
+            if (op_of<SIG>(is, s) == OP_ISUM) {
                 const long long v = static_cast<long long>(vals[s]);
                 const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
                 const uint64_t t = my_abs[s] + a;
@@ -196,7 +215,7 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float blk) {
 // Fills `ra` for run R of this batch.  T0/T1: transposed world sets of
 // worlds j and j+32 (T1 ignored with bal).  slice[s]: bit count when slot s
 // may be bit-sliced (0: loop).
-template <int NS>
+template <int NS, int SIG>
 __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint32_t T0, uint32_t T1, bool bal,
                                          const uint64_t (&vals)[NS], const int (&slice)[NS], int lane,
                                          RunAcc<NS> &ra) {
@@ -208,8 +227,8 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
     bool any_loop = false;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        if (s >= is.n_slots) continue;
-        const int op = is.slot[s].op;
+        if (s >= nslots_of<SIG>(is)) continue;
+        const int op = op_of<SIG>(is, s);
         ra.a0[s] = ra.a1[s] = op_identity(op);
         ra.tot[s] = 0;
         if (op == OP_ISUM && slice[s] > 0 && ra.n >= 8) {
@@ -238,8 +257,8 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
         const bool b0 = (M0 >> r) & 1u, b1 = (M1 >> r) & 1u;
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-            if (s >= is.n_slots) continue;
-            const int op = is.slot[s].op;
+            if (s >= nslots_of<SIG>(is)) continue;
+            const int op = op_of<SIG>(is, s);
             if (op == OP_ISUM) {
                 if (slice[s] > 0 && ra.n >= 8) continue;
                 const uint64_t x = __shfl_sync(kFull, vals[s], r);
@@ -268,8 +287,8 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
     }
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        if (s >= is.n_slots) continue;
-        const int op = is.slot[s].op;
+        if (s >= nslots_of<SIG>(is)) continue;
+        const int op = op_of<SIG>(is, s);
         if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
             comp_add(fs0[s], fc0[s], fb0[s]);
             comp_add(fs1[s], fc1[s], fb1[s]);
@@ -289,7 +308,7 @@ __device__ __forceinline__ bool by_complement(int op, bool bal) { return bal && 
 
 // Processes rows [base, base+32) of the item: transposes, finds the runs and
 // hands every run to `sink(g, ra)`.
-template <int NS, typename Sink>
+template <int NS, int SIG, typename Sink>
 __device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, uint64_t end, uint64_t (&my_abs)[NS],
                                          uint32_t *status, Sink &sink) {
     const int lane = threadIdx.x & 31;
@@ -297,7 +316,7 @@ __device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, ui
     bool valid = row < end;
     uint32_t gid;
     uint64_t mask, vals[NS];
-    load_row<NS>(is, row, valid, gid, mask, vals, my_abs, status);
+    load_row<NS, SIG>(is, row, valid, gid, mask, vals, my_abs, status);
     const bool bal = is.bal != 0;
     const uint32_t T0 = warp_transpose32(valid ? static_cast<uint32_t>(mask) : 0u, lane);
     const uint32_t T1 = bal ? 0u : warp_transpose32(valid ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
@@ -306,7 +325,7 @@ __device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, ui
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         slice[s] = 0;
-        if (s < is.n_slots && is.slot[s].op == OP_ISUM) {
+        if (s < nslots_of<SIG>(is) && op_of<SIG>(is, s) == OP_ISUM) {
             const uint32_t hi = __reduce_or_sync(kFull, static_cast<uint32_t>(vals[s] >> 32));
             const uint32_t lo = __reduce_or_sync(kFull, static_cast<uint32_t>(vals[s]));
             slice[s] = hi ? 0 : 32 - __clz(static_cast<int>(lo));
@@ -319,13 +338,13 @@ __device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, ui
         const uint32_t R = __ballot_sync(kFull, valid && gid == g);
         pending &= ~R;
         RunAcc<NS> ra;
-        run_fold<NS>(is, R, T0, T1, bal, vals, slice, lane, ra);
+        run_fold<NS, SIG>(is, R, T0, T1, bal, vals, slice, lane, ra);
         sink(g, ra, lane, bal);
     }
 }
 
 // Sink into the warp's private shared-memory state.
-template <int NS>
+template <int NS, int SIG>
 struct SmemSink {
     const ItemShared &is;
     uint64_t *st;    // this warp's [1+n_slots][G][64]
@@ -338,8 +357,8 @@ struct SmemSink {
         else if (lane == 0) cst[32] += ra.n;
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-            if (s >= is.n_slots) continue;
-            const int op = is.slot[s].op;
+            if (s >= nslots_of<SIG>(is)) continue;
+            const int op = op_of<SIG>(is, s);
             uint64_t *sst = st + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
             op_merge(op, sst[lane], ra.a0[s]);
             if (!by_complement(op, bal)) op_merge(op, sst[lane + 32], ra.a1[s]);
@@ -350,7 +369,7 @@ struct SmemSink {
 };
 
 // Sink into the query's global state with atomics.
-template <int NS>
+template <int NS, int SIG>
 struct AtomicSink {
     const ItemShared &is;
     uint32_t G;
@@ -364,8 +383,8 @@ struct AtomicSink {
         }
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-            if (s >= is.n_slots) continue;
-            const int op = is.slot[s].op;
+            if (s >= nslots_of<SIG>(is)) continue;
+            const int op = op_of<SIG>(is, s);
             uint64_t *sst = is.state + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
             if (ra.c0) atomic_fold(op, sst + lane, ra.a0[s]);
             if (!by_complement(op, bal)) {
@@ -379,15 +398,15 @@ struct AtomicSink {
 };
 
 // Adds run `b` into run accumulator `a` (same group).
-template <int NS>
+template <int NS, int SIG>
 __device__ __forceinline__ void run_merge(const ItemShared &is, RunAcc<NS> &a, const RunAcc<NS> &b) {
     a.c0 += b.c0;
     a.c1 += b.c1;
     a.n += b.n;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        if (s >= is.n_slots) continue;
-        const int op = is.slot[s].op;
+        if (s >= nslots_of<SIG>(is)) continue;
+        const int op = op_of<SIG>(is, s);
         if (op == OP_ISUM) {
             a.a0[s] += b.a0[s];
             a.a1[s] += b.a1[s];
@@ -402,15 +421,15 @@ __device__ __forceinline__ void run_merge(const ItemShared &is, RunAcc<NS> &a, c
 // Carries the current group's run across 32-row batches (rows in group
 // order) and flushes it to the global state with atomics when the group
 // changes and at the end of the item.
-template <int NS>
+template <int NS, int SIG>
 struct CarrySink {
-    AtomicSink<NS> out;
+    AtomicSink<NS, SIG> out;
     const ItemShared &is;
     RunAcc<NS> acc;
     uint32_t g_cur = 0xFFFFFFFFu;
     __device__ __forceinline__ void operator()(uint32_t g, const RunAcc<NS> &ra, int lane, bool bal) {
         if (g == g_cur) {
-            run_merge<NS>(is, acc, ra);
+            run_merge<NS, SIG>(is, acc, ra);
             return;
         }
         if (g_cur != 0xFFFFFFFFu) out(g_cur, acc, lane, bal);
@@ -424,7 +443,7 @@ struct CarrySink {
 };
 
 // One item of a query with warp-private shared-memory states.
-template <int NS>
+template <int NS, int SIG>
 __device__ void item_warp_private(const ItemShared &is, unsigned char *smem_raw, uint32_t *status) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     const uint32_t G = is.in.n_groups;
@@ -445,10 +464,10 @@ __device__ void item_warp_private(const ItemShared &is, unsigned char *smem_raw,
     uint64_t my_abs[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) my_abs[s] = 0;
-    SmemSink<NS> sink{is, st, ng, G};
+    SmemSink<NS, SIG> sink{is, st, ng, G};
     for (uint64_t base = is.row0 + static_cast<uint64_t>(warp) * 32; base < is.row_end;
          base += static_cast<uint64_t>(n_warps) * 32)
-        batch32w<NS>(is, base, is.row_end, my_abs, status, sink);
+        batch32w<NS, SIG>(is, base, is.row_end, my_abs, status, sink);
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         uint64_t m = my_abs[s];
@@ -493,14 +512,14 @@ __device__ void item_warp_private(const ItemShared &is, unsigned char *smem_raw,
 }
 
 // One item of a query with global-atomic states.
-template <int NS>
+template <int NS, int SIG>
 __device__ void item_atomic(const ItemShared &is, uint32_t *status) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     const uint32_t G = is.in.n_groups;
     uint64_t my_abs[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) my_abs[s] = 0;
-    CarrySink<NS> sink{AtomicSink<NS>{is, G}, is};
+    CarrySink<NS, SIG> sink{AtomicSink<NS, SIG>{is, G}, is};
     // each warp takes one contiguous stretch of the item, so group runs of
     // the group-ordered rows stay long within a warp
     const uint64_t span = is.row_end > is.row0 ? is.row_end - is.row0 : 0;
@@ -508,13 +527,13 @@ __device__ void item_atomic(const ItemShared &is, uint32_t *status) {
     const uint64_t w0 = is.row0 + static_cast<uint64_t>(warp) * per_warp;
     const uint64_t w1 = min(is.row_end, w0 + per_warp);
     ItemShared const &isr = is;
-    for (uint64_t base = w0; base < w1; base += 32) batch32w<NS>(isr, base, w1, my_abs, status, sink);
+    for (uint64_t base = w0; base < w1; base += 32) batch32w<NS, SIG>(isr, base, w1, my_abs, status, sink);
     sink.flush(lane, is.bal != 0);
     // int64 SUM guard: the wrapping atomics are exact while the query's total
     // of |v| stays below 2^63, which bounds every world's sum
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        if (s >= is.n_slots || is.slot[s].op != OP_ISUM) continue;
+        if (s >= nslots_of<SIG>(is) || op_of<SIG>(is, s) != OP_ISUM) continue;
         unsigned long long m = my_abs[s];
         for (int o = 16; o; o >>= 1) {
             const unsigned long long t = __shfl_xor_sync(kFull, m, o);
@@ -528,7 +547,7 @@ __device__ void item_atomic(const ItemShared &is, uint32_t *status) {
     }
 }
 
-template <int NS>
+template <int NS, int SIG>
 __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQueryDev *__restrict__ qs,
                                                                 const BatchItem *__restrict__ items,
                                                                 uint32_t n_items, unsigned int *counter,
@@ -567,8 +586,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQuery
         if (threadIdx.x < kMaxSpecs && static_cast<int>(threadIdx.x) < is.n_slots)
             is.slot[threadIdx.x] = qs[items[is.item].q].slot[threadIdx.x];
         __syncthreads();
-        if (is.mode == 0) item_warp_private<NS>(is, smem_raw, status);
-        else item_atomic<NS>(is, status);
+        if (is.mode == 0) item_warp_private<NS, SIG>(is, smem_raw, status);
+        else item_atomic<NS, SIG>(is, status);
         __syncthreads();  // every thread is done with `is` before thread 0 refills it
     }
 }
@@ -783,13 +802,16 @@ __global__ void __launch_bounds__(256) k_batch_merge(const BatchQueryDev *__rest
 // ===========================================================================
 namespace {
 
-template <int NS>
+template <int NS, int SIG>
 cudaError_t batch_kernel_setup(size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch_agg<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_batch_agg<NS, SIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_agg<NS>, kBatchWarps * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_agg<NS, SIG>, kBatchWarps * 32, smem);
 }
+
+// The kernel variant of a plan: (NS, SIG) pairs instantiated below.
+#define PAC_BATCH_VARIANTS(X) X(1, 0) X(2, 0) X(4, 0) X(kMaxSpecs, 0) X(1, 1) X(2, 2) X(4, 3) X(1, 4)
 
 template <typename T>
 T *img_at(pac_batch *b, size_t off) {
@@ -846,6 +868,21 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         max_slots = std::max(max_slots, static_cast<int>(d.n_slots));
     }
     b->ns = max_slots <= 1 ? 1 : max_slots <= 2 ? 2 : max_slots <= 4 ? 4 : kMaxSpecs;
+    // one shared slot signature -> a kernel with compile-time slot operations
+    auto sig_of = [](const BatchQueryDev &d) {
+        auto op = [&](int k) { return d.slot[k].op; };
+        if (d.n_slots == 1 && op(0) == OP_ISUM) return 1;
+        if (d.n_slots == 2 && op(0) == OP_ISUM && op(1) == OP_FSUM_COMP) return 2;
+        if (d.n_slots == 3 && op(0) == OP_ISUM && op(1) == OP_FSUM_COMP && op(2) == OP_FSUM_COMP) return 3;
+        if (d.n_slots == 1 && op(0) == OP_FSUM_COMP) return 4;
+        return 0;
+    };
+    b->sig = n_queries > 0 ? sig_of(hq[0]) : 0;
+    for (int i = 1; i < n_queries && b->sig; i++)
+        if (sig_of(hq[i]) != b->sig) b->sig = 0;
+    if (b->sig == 1 || b->sig == 4) b->ns = 1;
+    if (b->sig == 2) b->ns = 2;
+    if (b->sig == 3) b->ns = 4;
     // device block: [zeroed scratch | partials | image]; offsets relative to it
     size_t zero_off = 256;  // the item counter lives at offset 0
     size_t part_off = 0;    // relative to the start of the partials region
@@ -982,13 +1019,11 @@ void plan_bind(pac_batch *b, void *dbuf) {
 
 pac_status plan_setup_kernel(pac_ctx *ctx, pac_batch *b) {
     int per_sm = 0;
-    cudaError_t e;
-    switch (b->ns) {
-    case 1: e = batch_kernel_setup<1>(b->smem, &per_sm); break;
-    case 2: e = batch_kernel_setup<2>(b->smem, &per_sm); break;
-    case 4: e = batch_kernel_setup<4>(b->smem, &per_sm); break;
-    default: e = batch_kernel_setup<kMaxSpecs>(b->smem, &per_sm); break;
-    }
+    cudaError_t e = cudaErrorInvalidValue;
+#define PAC_SETUP(NS_, SIG_) \
+    if (b->ns == NS_ && b->sig == SIG_) e = batch_kernel_setup<NS_, SIG_>(b->smem, &per_sm);
+    PAC_BATCH_VARIANTS(PAC_SETUP)
+#undef PAC_SETUP
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch kernel setup");
     b->n_ctas = ctx->n_sms * std::max(per_sm, 1);
     return PAC_OK;
@@ -1013,14 +1048,12 @@ pac_status plan_enqueue(pac_ctx *ctx, pac_batch *b, cudaStream_t s, const void *
         k_part_scatter<<<pgrid, 256, 0, s>>>(d_q, d_items, b->n_items);
         PAC_CUDA(ctx, cudaGetLastError());
     }
-    switch (b->ns) {
-    case 1: k_batch_agg<1><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
-    case 2: k_batch_agg<2><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
-    case 4: k_batch_agg<4><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status); break;
-    default:
-        k_batch_agg<kMaxSpecs><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter, b->d_status);
-        break;
-    }
+#define PAC_LAUNCH(NS_, SIG_)                                                                              \
+    if (b->ns == NS_ && b->sig == SIG_)                                                                    \
+        k_batch_agg<NS_, SIG_><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter,  \
+                                                                       b->d_status);
+    PAC_BATCH_VARIANTS(PAC_LAUNCH)
+#undef PAC_LAUNCH
     PAC_CUDA(ctx, cudaGetLastError());
     if (b->total_cells > 0) {
         const uint64_t blocks = (b->total_cells + 255) / 256;

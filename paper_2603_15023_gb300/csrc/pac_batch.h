@@ -61,6 +61,7 @@ struct pac_batch {
     uint32_t n_items = 0;
     int n_rel = 0;
     int ns = 1;
+    int sig = 0;  // shared slot signature (0: operations read at run time)
     size_t smem = 0;
     int n_ctas = 0;
     int n_warp_private = 0, n_atomic = 0;
