@@ -212,9 +212,39 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float blk) {
     c += e;
 }
 
+// One row r of the broadcast loop: every loop-type slot takes row r's value.
+template <int NS, int SIG>
+__device__ __forceinline__ void loop_row(const ItemShared &is, int r, uint32_t M0, uint32_t M1,
+                                         const uint64_t (&vals)[NS], const int (&slice)[NS], uint32_t n,
+                                         RunAcc<NS> &ra, float (&fb0)[NS], float (&fb1)[NS]) {
+    const bool b0 = (M0 >> r) & 1u, b1 = (M1 >> r) & 1u;
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (s >= nslots_of<SIG>(is)) continue;
+        const int op = op_of<SIG>(is, s);
+        if (op == OP_ISUM) {
+            if (slice[s] > 0 && n >= 8) continue;
+            const uint64_t x = __shfl_sync(kFull, vals[s], r);
+            ra.a0[s] += b0 ? x : 0ull;
+            ra.a1[s] += b1 ? x : 0ull;
+            ra.tot[s] += x;
+        } else if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
+            const float x = __int_as_float(__shfl_sync(kFull, static_cast<int>(vals[s]), r));
+            fb0[s] += b0 ? x : 0.0f;
+            fb1[s] += b1 ? x : 0.0f;
+        } else {
+            const uint64_t x = __shfl_sync(kFull, vals[s], r);
+            op_update(op, ra.a0[s], x, b0 ? 1u : 0u);
+            op_update(op, ra.a1[s], x, b1 ? 1u : 0u);
+        }
+    }
+}
+
 // Fills `ra` for run R of this batch.  T0/T1: transposed world sets of
 // worlds j and j+32 (T1 ignored with bal).  slice[s]: bit count when slot s
-// may be bit-sliced (0: loop).
+// may be bit-sliced (0: loop).  With compile-time slot operations a run of
+// all 32 rows (the common case of group-ordered rows) takes a fully
+// unrolled loop.
 template <int NS, int SIG>
 __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint32_t T0, uint32_t T1, bool bal,
                                          const uint64_t (&vals)[NS], const int (&slice)[NS], int lane,
@@ -232,73 +262,71 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
         ra.a0[s] = ra.a1[s] = op_identity(op);
         ra.tot[s] = 0;
         if (op == OP_ISUM && slice[s] > 0 && ra.n >= 8) {
+            // bits below 26 add up in 32 bits (at most 32 rows * 2^26 < 2^31)
+            uint32_t p0 = 0, p1 = 0, pt = 0;
             uint64_t acc0 = 0, acc1 = 0, tot = 0;
             for (int b = 0; b < slice[s]; b++) {
                 const uint32_t vb = __ballot_sync(kFull, (vals[s] >> b) & 1ull) & R;
-                acc0 += static_cast<uint64_t>(__popc(M0 & vb)) << b;
-                acc1 += static_cast<uint64_t>(__popc(M1 & vb)) << b;
-                tot += static_cast<uint64_t>(__popc(vb)) << b;
+                const uint32_t c0 = __popc(M0 & vb), ct = __popc(vb);
+                const uint32_t c1 = bal ? 0u : __popc(M1 & vb);
+                if (b < 26) {
+                    p0 += c0 << b;
+                    p1 += c1 << b;
+                    pt += ct << b;
+                } else {
+                    acc0 += static_cast<uint64_t>(c0) << b;
+                    acc1 += static_cast<uint64_t>(c1) << b;
+                    tot += static_cast<uint64_t>(ct) << b;
+                }
             }
-            ra.a0[s] = acc0;
-            ra.a1[s] = acc1;
-            ra.tot[s] = tot;
+            ra.a0[s] = acc0 + p0;
+            ra.a1[s] = acc1 + p1;  // unused with bal (world j+32 = total - world j)
+            ra.tot[s] = tot + pt;
         } else {
             any_loop = true;
         }
     }
     if (!any_loop) return;
-    // broadcast loop over the rows of R for the remaining slots
+    // broadcast loop over the rows of R for the remaining slots; float sums
+    // fold 8-row blocks into a compensated pair
     float fs0[NS], fc0[NS], fb0[NS], fs1[NS], fc1[NS], fb1[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) fs0[s] = fc0[s] = fb0[s] = fs1[s] = fc1[s] = fb1[s] = 0.0f;
-    int blk = 0;
-    for (uint32_t rr = R; rr; rr &= rr - 1) {
-        const int r = __ffs(rr) - 1;
-        const bool b0 = (M0 >> r) & 1u, b1 = (M1 >> r) & 1u;
+    auto flush_blocks = [&]() {
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-            if (s >= nslots_of<SIG>(is)) continue;
-            const int op = op_of<SIG>(is, s);
-            if (op == OP_ISUM) {
-                if (slice[s] > 0 && ra.n >= 8) continue;
-                const uint64_t x = __shfl_sync(kFull, vals[s], r);
-                ra.a0[s] += b0 ? x : 0ull;
-                ra.a1[s] += b1 ? x : 0ull;
-                ra.tot[s] += x;
-            } else if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
-                const float x = __int_as_float(__shfl_sync(kFull, static_cast<int>(vals[s]), r));
-                fb0[s] += b0 ? x : 0.0f;
-                fb1[s] += b1 ? x : 0.0f;
-            } else {
-                const uint64_t x = __shfl_sync(kFull, vals[s], r);
-                op_update(op, ra.a0[s], x, b0 ? 1u : 0u);
-                op_update(op, ra.a1[s], x, b1 ? 1u : 0u);
-            }
+            comp_add(fs0[s], fc0[s], fb0[s]);
+            comp_add(fs1[s], fc1[s], fb1[s]);
+            fb0[s] = fb1[s] = 0.0f;
         }
-        if (++blk == 8) {
-            blk = 0;
+    };
+    if (SIG != 0 && R == kFull) {
 #pragma unroll
-            for (int s = 0; s < NS; s++) {
-                comp_add(fs0[s], fc0[s], fb0[s]);
-                comp_add(fs1[s], fc1[s], fb1[s]);
-                fb0[s] = fb1[s] = 0.0f;
+        for (int r = 0; r < 32; r++) {
+            loop_row<NS, SIG>(is, r, M0, M1, vals, slice, ra.n, ra, fb0, fb1);
+            if ((r & 7) == 7) flush_blocks();
+        }
+    } else {
+        int blk = 0;
+        for (uint32_t rr = R; rr; rr &= rr - 1) {
+            loop_row<NS, SIG>(is, __ffs(rr) - 1, M0, M1, vals, slice, ra.n, ra, fb0, fb1);
+            if (++blk == 8) {
+                blk = 0;
+                flush_blocks();
             }
         }
+        flush_blocks();
     }
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         if (s >= nslots_of<SIG>(is)) continue;
         const int op = op_of<SIG>(is, s);
-        if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
-            comp_add(fs0[s], fc0[s], fb0[s]);
-            comp_add(fs1[s], fc1[s], fb1[s]);
-            if (op == OP_FSUM_COMP) {
-                ra.a0[s] = pack_pair(fs0[s], fc0[s]);
-                ra.a1[s] = pack_pair(fs1[s], fc1[s]);
-            } else {
-                ra.a0[s] = pack_pair(fs0[s] + fc0[s], 0.0f);
-                ra.a1[s] = pack_pair(fs1[s] + fc1[s], 0.0f);
-            }
+        if (op == OP_FSUM_COMP) {
+            ra.a0[s] = pack_pair(fs0[s], fc0[s]);
+            ra.a1[s] = pack_pair(fs1[s], fc1[s]);
+        } else if (op == OP_FSUM_PLAIN) {
+            ra.a0[s] = pack_pair(fs0[s] + fc0[s], 0.0f);
+            ra.a1[s] = pack_pair(fs1[s] + fc1[s], 0.0f);
         }
     }
 }
