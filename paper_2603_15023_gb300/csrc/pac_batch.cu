@@ -626,15 +626,24 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQuery
 // slot values) into group order.  Warps aggregate their atomics per group
 // (match_any): one atomic per distinct group of a 32-row batch.
 // ---------------------------------------------------------------------------
+// Group ids below kPartSmem are counted per work item in shared memory
+// (warp-aggregated shared atomics) and flushed with one global atomic per
+// group and item; larger ids take a warp-aggregated global atomic per row.
+constexpr uint32_t kPartSmem = 2048;
+
 __global__ void __launch_bounds__(256) k_part_hist(const BatchQueryDev *__restrict__ qs,
                                                    const BatchItem *__restrict__ items, uint32_t n_items,
                                                    uint32_t *status) {
+    __shared__ uint32_t cnt_s[kPartSmem];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const BatchItem item = items[it];
         const BatchQueryDev &q = qs[item.q];
         if (q.mode != 1) continue;
         const uint32_t G = q.in.n_groups;
+        const uint32_t S = G < kPartSmem ? G : kPartSmem;
+        for (uint32_t g = threadIdx.x; g < S; g += blockDim.x) cnt_s[g] = 0;
+        __syncthreads();
         const uint64_t end = item.row0 + item.rows;
         for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; base < end;
              base += static_cast<uint64_t>(n_warps) * 32) {
@@ -647,13 +656,21 @@ __global__ void __launch_bounds__(256) k_part_hist(const BatchQueryDev *__restri
                 g = 0xFFFFFFFFu;
             }
             const uint32_t peers = __match_any_sync(kFull, g);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(q.pcnt + g, static_cast<uint32_t>(__popc(peers)));
+            if (valid && lane == __ffs(peers) - 1) {
+                if (g < S) atomicAdd(cnt_s + g, static_cast<uint32_t>(__popc(peers)));
+                else atomicAdd(q.pcnt + g, static_cast<uint32_t>(__popc(peers)));
+            }
         }
+        __syncthreads();
+        for (uint32_t g = threadIdx.x; g < S; g += blockDim.x)
+            if (cnt_s[g]) atomicAdd(q.pcnt + g, cnt_s[g]);
+        __syncthreads();
     }
 }
 
-// One CTA (1024 threads) per query: pcur = exclusive prefix of pcnt, and
-// pcnt[G] = the number of rows kept.
+// One CTA (1024 threads) per query: pcur = exclusive prefix of pcnt,
+// pcnt[G] = the number of rows kept, pcnt[G+1] = 1 when one group holds more
+// than 1/64 of them.
 __global__ void __launch_bounds__(1024) k_part_scan(const BatchQueryDev *__restrict__ qs) {
     __shared__ uint32_t wsum[32];
     const BatchQueryDev &q = qs[blockIdx.x];
@@ -662,8 +679,13 @@ __global__ void __launch_bounds__(1024) k_part_scan(const BatchQueryDev *__restr
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t chunk = (G + blockDim.x - 1) / blockDim.x;
     const uint32_t g0 = min(G, t * chunk), g1 = min(G, g0 + chunk);
-    uint32_t local = 0;
-    for (uint32_t g = g0; g < g1; g++) local += q.pcnt[g];
+    uint32_t local = 0, mx = 0;
+    for (uint32_t g = g0; g < g1; g++) {
+        local += q.pcnt[g];
+        mx = max(mx, q.pcnt[g]);
+    }
+    __shared__ uint32_t s_mx;
+    if (t == 0) s_mx = 0;
     uint32_t incl = local;
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t v = __shfl_up_sync(kFull, incl, o);
@@ -686,11 +708,25 @@ __global__ void __launch_bounds__(1024) k_part_scan(const BatchQueryDev *__restr
         q.pcur[g] = run;
         run += c;
     }
-    if (t == static_cast<int>(blockDim.x) - 1) q.pcnt[G] = wsum[(blockDim.x >> 5) - 1];
+    atomicMax(&s_mx, mx);
+    __syncthreads();
+    if (t == static_cast<int>(blockDim.x) - 1) {
+        const uint32_t kept = wsum[(blockDim.x >> 5) - 1];
+        q.pcnt[G] = kept;
+        // a group holding more than 1/64 of the rows makes the query "hot":
+        // its scatter then reserves ranges per item instead of per warp
+        q.pcnt[G + 1] = static_cast<uint64_t>(s_mx) * 64 > kept ? 1u : 0u;
+    }
 }
 
+// Scatter of one work item.  In a hot query (one group above 1/64 of the
+// rows) the item's rows of groups below kPartSmem are counted in shared
+// memory, each such group reserves one range of the query's cursor, and the
+// rows take consecutive places of that range through shared cursors; every
+// other row takes a warp-aggregated global cursor.
 __global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__restrict__ qs,
                                                       const BatchItem *__restrict__ items, uint32_t n_items) {
+    __shared__ uint32_t cur_s[kPartSmem];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -698,7 +734,27 @@ __global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__res
         const BatchQueryDev &q = qs[item.q];
         if (q.mode != 1) continue;
         const uint32_t G = q.in.n_groups;
+        const bool hot = q.pcnt[G + 1] != 0;
+        const uint32_t S = hot ? (G < kPartSmem ? G : kPartSmem) : 0u;  // no shared cursors for a cool query
         const uint64_t end = item.row0 + item.rows;
+        // (1) the item's rows per small group
+        for (uint32_t g = threadIdx.x; g < S; g += blockDim.x) cur_s[g] = 0;
+        __syncthreads();
+        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; hot && base < end;
+             base += static_cast<uint64_t>(n_warps) * 32) {
+            const uint64_t r = base + lane;
+            const uint32_t g = r < end ? row_gid(q.in, r) : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(kFull, g);
+            if (g < S && lane == __ffs(peers) - 1) atomicAdd(cur_s + g, static_cast<uint32_t>(__popc(peers)));
+        }
+        __syncthreads();
+        // (2) one range of the query's cursor per small group
+        for (uint32_t g = threadIdx.x; g < S; g += blockDim.x) {
+            const uint32_t c = cur_s[g];
+            if (c) cur_s[g] = atomicAdd(q.pcur + g, c);
+        }
+        __syncthreads();
+        // (3) rows into group order
         for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; base < end;
              base += static_cast<uint64_t>(n_warps) * 32) {
             const uint64_t r = base + lane;
@@ -711,14 +767,19 @@ __global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__res
             const uint32_t peers = __match_any_sync(kFull, g);
             const int leader = __ffs(peers) - 1;
             uint32_t at = 0;
-            if (valid && lane == leader) at = atomicAdd(q.pcur + g, static_cast<uint32_t>(__popc(peers)));
+            if (valid && lane == leader) {
+                at = g < S ? atomicAdd(cur_s + g, static_cast<uint32_t>(__popc(peers)))
+                           : atomicAdd(q.pcur + g, static_cast<uint32_t>(__popc(peers)));
+            }
             at = __shfl_sync(kFull, at, leader);
             if (!valid) continue;
             const uint64_t d = at + __popc(peers & lt);
             q.smask[d] = row_mask(q.in, r);
             q.sgid[d] = g;
-            for (int s = 0; s < q.n_slots; s++) q.sval[static_cast<uint64_t>(s) * q.in.n + d] = load_slot_value(q.slot[s], r);
+            for (int s2 = 0; s2 < q.n_slots; s2++)
+                q.sval[static_cast<uint64_t>(s2) * q.in.n + d] = load_slot_value(q.slot[s2], r);
         }
+        __syncthreads();
     }
 }
 
@@ -955,7 +1016,7 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             b->rel_abs[i] = align_up(zero_off, 256);
             zero_off = b->rel_abs[i] + kMaxSpecs * 8;
             b->rel_pcnt[i] = align_up(zero_off, 256);
-            zero_off = b->rel_pcnt[i] + (static_cast<size_t>(G) + 1) * 4;
+            zero_off = b->rel_pcnt[i] + (static_cast<size_t>(G) + 2) * 4;
             // group-ordered copies (fully overwritten by the scatter)
             p_pcur[i] = align_up(part_off, 256);
             part_off = p_pcur[i] + static_cast<size_t>(G) * 4;

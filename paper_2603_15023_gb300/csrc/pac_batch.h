@@ -29,7 +29,7 @@ struct BatchQueryDev {
     uint32_t first_item, n_items;
     // mode 1: the rows partitioned by group before aggregation, so that runs
     // of one group are long and atomics are paid once per run
-    uint32_t *pcnt;   // [G+1] rows per group (zeroed); [G] = rows kept after the scan
+    uint32_t *pcnt;   // [G+2] rows per group (zeroed); [G] = rows kept, [G+1] = hot flag (after the scan)
     uint32_t *pcur;   // [G] scatter cursors
     uint64_t *smask;  // [n] world masks in group order
     uint32_t *sgid;   // [n] group ids in group order
