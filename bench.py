@@ -59,7 +59,7 @@ WORKLOADS = {
                       "describe": "count + sum, exact; release of the 2M cells timed separately"},
     "serving": {"gid_bytes": 4, "n_cols": 3, "aggs": "count+sum+fsum+dsum", "finalize": "adaptive",
                 "in_bytes_per_row": 8 + 4 + 8 + 4 + 8, "flush_l2": False,
-                "describe": "Poisson arrivals at 2000 queries/s, shapes of batch_4096, count + exact int64 sum + exact "
+                "describe": "Poisson arrivals, shapes of batch_4096, count + exact int64 sum + exact "
                             "float32 sum + exact float64 lognormal(0,1.5) sum, adaptive release of every cell"},
     "batch_4096": {"gid_bytes": 4, "n_cols": 2, "aggs": "count+sum+fsum", "finalize": "none",
                    "in_bytes_per_row": 8 + 4 + 8 + 4, "flush_l2": False,

@@ -3,8 +3,8 @@
 // pac_noised_count, count[j*]*2; Sec. 3.2 "NULLs"; Sec. 5 "Diversity Check").
 //
 // In the adaptive mode every release depends on the posterior left by the
-// previous one, so one 64-thread chain walks all cells of the query in order
-// (group-major, then spec order), thread t holding world t; the independent
+// previous one, so one chain of threads walks all cells of the query in order
+// (group-major, then spec order), each thread holding some worlds; the independent
 // mode gives every cell its own warp (lane l: worlds l and l+32) under the
 // uniform prior.  FP64 is used only here.
 #include <cmath>
@@ -105,128 +105,341 @@ __device__ void release_cell(const FinParams &p, uint64_t c, int jstar, double &
 }
 
 // ---------------------------------------------------------------------------
-// The posterior chain of one query (adaptive mode, and every batched query):
-// 64 threads, thread t holds world t of the result vector and of the
-// log-posterior, so the FP64 work of a cell is split across two warps (two
-// SM sub-partitions).  Draws that do not depend on the posterior (the NULL
-// decision and the Box-Muller normal of a cell) are computed 32 cells at a
-// time, one cell per lane, and the next cell's world values are loaded while
-// the current cell's chain runs.  The arithmetic per cell is that of
-// release_cell above.
+// The posterior chain of one query (adaptive mode, and every batched query).
+// 64 threads, thread t holding world t.  The chain is bound by the latency of
+// dependent FP64 operations, so the state is kept in a form that needs one
+// exp and no log per update:
+//   L_t   log-weight of world t, shifted so that max_t L_t = 0 (all L_t <= 0),
+//   w_t   = exp(L_t), the weight left by the last update,
+//   se    = sum_t w_t,
+// which is the posterior of Sec. 4.1 step 4 up to normalisation:
+// p_t = w_t / se, log p_t = L_t - log(se).  The mean and variance of step 1
+// divide the weighted sums by se; the update adds -(e_t^2)/(2 delta) to L_t,
+// subtracts the new maximum (found as the least IEEE bit pattern, since every
+// L_t <= 0) and takes exp once.  In exact arithmetic every quantity is the
+// one of release_cell above; rounding differs by a few ulps.
+//
+// Step 1's test "all worlds of non-zero posterior agree" runs first, on the
+// raw 64-bit words, and skips both sums when it holds.  Once a single world
+// keeps non-zero weight (adaptive mode), every later release has variance 0
+// and the posterior no longer changes, so the remaining cells are released
+// in parallel, one per lane (collapsed_tail).  Draws that do not depend on
+// the posterior (the NULL decision and the Box-Muller normal of a cell) are
+// computed 32 cells at a time, one cell per lane, and world values are
+// loaded kAhead cells ahead of the chain.
 // ---------------------------------------------------------------------------
-constexpr int kChainThreads = 64;
+constexpr int kChainThreads = kWorlds;  // thread t holds world t
+constexpr int kChainWarps = kChainThreads / 32;
+constexpr int kAhead = 4;
 
 struct ChainShared {
-    double part[8][2];  // per-warp partials, rotating slots (one barrier per reduction)
+    double part[4][kChainWarps];  // per-warp partials, rotating slots (one barrier per reduction)
+    unsigned long long bits[4][kChainWarps];
 };
 
-__device__ __forceinline__ double chain_reduce(double v, bool is_max, ChainShared &sh, int &slot, int warp,
-                                               int lane) {
-    for (int o = 16; o; o >>= 1) {
-        const double t = __shfl_xor_sync(kFull, v, o);
-        v = is_max ? fmax(v, t) : v + t;
-    }
+__device__ __forceinline__ double chain_sum(double v, ChainShared &sh, int &slot, int warp, int lane) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     double *pp = sh.part[slot];
-    slot = (slot + 1) & 7;
+    slot = (slot + 1) & 3;
     if (lane == 0) pp[warp] = v;
     __syncthreads();
-    return is_max ? fmax(pp[0], pp[1]) : pp[0] + pp[1];
+    return pp[0] + pp[1];
 }
 
-struct CellLoad {
-    uint64_t orm, rows;
-    double y, yj;  // this thread's world value and the secret world's, scaled and masked
+// chain_sum, also counting the threads whose flag b is set.
+__device__ __forceinline__ double chain_sum_count(double v, bool b, int &cnt, ChainShared &sh, int &slot, int warp,
+                                                  int lane) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const unsigned bal = __ballot_sync(kFull, b);
+    double *pp = sh.part[slot];
+    unsigned long long *pb = sh.bits[slot];
+    slot = (slot + 1) & 3;
+    if (lane == 0) {
+        pp[warp] = v;
+        pb[warp] = bal;
+    }
+    __syncthreads();
+    cnt = __popc(static_cast<unsigned>(pb[0])) + __popc(static_cast<unsigned>(pb[1]));
+    return pp[0] + pp[1];
+}
+
+// Maximum of non-positive doubles: the least bit pattern (+0 < -0 < -tiny <
+// ... < -inf as unsigned integers).
+__device__ __forceinline__ double chain_max_nonpos(double x, ChainShared &sh, int &slot, int warp, int lane) {
+    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(kFull, b, o);
+        b = u < b ? u : b;
+    }
+    unsigned long long *pp = sh.bits[slot];
+    slot = (slot + 1) & 3;
+    if (lane == 0) pp[warp] = b;
+    __syncthreads();
+    b = pp[0] < pp[1] ? pp[0] : pp[1];
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
+__device__ __forceinline__ bool chain_all(bool x) { return __syncthreads_and(x) != 0; }
+
+__device__ __forceinline__ unsigned chain_or(unsigned m, ChainShared &sh, int &slot, int warp, int lane) {
+    m = __reduce_or_sync(kFull, m);
+    unsigned long long *pp = sh.bits[slot];
+    slot = (slot + 1) & 3;
+    if (lane == 0) pp[warp] = m;
+    __syncthreads();
+    return static_cast<unsigned>(pp[0] | pp[1]);
+}
+
+// How the 64-bit words of a spec's result array read as the release's value:
+// bits 0-1 conversion (0 unsigned count, 1 int64, 2 float64), bit 2 the
+// factor 2 of COUNT and SUM (Sec. 2: the secret world's result is doubled).
+__device__ __forceinline__ int cell_code(const FinSpec &sp) {
+    const int conv = sp.kind == PAC_COUNT ? 0 : ((sp.kind == PAC_AVG || sp.vtype != PAC_I64) ? 2 : 1);
+    return conv | ((sp.kind == PAC_COUNT || sp.kind == PAC_SUM) ? 4 : 0);
+}
+
+__device__ __forceinline__ double raw_to_double(unsigned long long b, int code) {
+    const int conv = code & 3;
+    const double v = conv == 0   ? static_cast<double>(b)
+                     : conv == 1 ? static_cast<double>(static_cast<long long>(b))
+                                 : __longlong_as_double(static_cast<long long>(b));
+    return (code & 4) ? 2.0 * v : v;
+}
+
+// raw_to_double(a) == raw_to_double(b), mostly decided on the integers.
+__device__ __forceinline__ bool same_value(unsigned long long a, unsigned long long b, int code) {
+    const int conv = code & 3;
+    bool exact;  // the integer comparison decides
+    if (conv == 2) {
+        const unsigned long long ma = a << 1, mb = b << 1;  // without the sign
+        if ((ma | mb) == 0) return true;                   // +0 and -0
+        if (a == b) return ma <= (0x7FF0000000000000ull << 1);  // NaN is unequal to itself
+        // distinct doubles stay distinct after doubling unless both overflow
+        exact = !((code & 4) && ma >= (0x7FE0000000000000ull << 1) && mb >= (0x7FE0000000000000ull << 1));
+    } else {
+        if (a == b) return true;
+        // distinct integers of magnitude <= 2^53 convert to distinct doubles
+        constexpr unsigned long long k53 = 1ull << 53;
+        exact = conv == 0 ? (a <= k53 && b <= k53) : (a + k53 <= 2 * k53 && b + k53 <= 2 * k53);
+    }
+    return exact ? false : raw_to_double(a, code) == raw_to_double(b, code);
+}
+
+// The release value is not finite (after the factor 2): the variance sums
+// would carry it into NaN even at zero weight.
+__device__ __forceinline__ bool raw_nonfinite(unsigned long long b, int code) {
+    if ((code & 3) != 2) return false;
+    const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
+    return e >= ((code & 4) ? 0x7FEu : 0x7FFu);
+}
+
+struct CellRaw {
+    unsigned long long y, yj;  // this thread's world and the secret world, as stored
+    int code;
 };
 
-__device__ __forceinline__ CellLoad load_cell(const FinParams &p, uint64_t c, int world, int jstar) {
-    CellLoad L;
-    const uint32_t g = static_cast<uint32_t>(c / p.n_specs);
-    const int s = static_cast<int>(c % p.n_specs);
+__device__ __forceinline__ CellRaw load_raw(const FinParams &p, uint32_t g, int s, int t, int jstar) {
     const FinSpec &sp = p.spec[s];
-    L.orm = p.meta[2 * g + 1];
-    L.rows = p.meta[2 * g];
-    const double scale = (sp.kind == PAC_COUNT || sp.kind == PAC_SUM) ? 2.0 : 1.0;
-    const size_t base = static_cast<size_t>(g) * kWorlds;
-    const double v = world_value(sp, base + world);
-    const double vj = world_value(sp, base + jstar);
-    L.y = ((L.orm >> world) & 1ull) ? scale * v : 0.0;
-    L.yj = ((L.orm >> jstar) & 1ull) ? scale * vj : 0.0;
-    return L;
+    const unsigned long long *o = static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * kWorlds;
+    CellRaw r;
+    r.y = o[t];
+    r.yj = o[jstar];
+    r.code = cell_code(sp);
+    return r;
+}
+
+// Per-lane facts of cell c that do not depend on the posterior.
+struct CellDraw {
+    unsigned long long orm;
+    bool null_, diversity;
+};
+
+__device__ __forceinline__ CellDraw draw_cell(const FinParams &p, uint64_t c) {
+    const uint32_t g = static_cast<uint32_t>(c / p.n_specs);
+    CellDraw d;
+    d.orm = p.meta[2 * g + 1];
+    const uint64_t rows = p.meta[2 * g];
+    const int pop = __popcll(d.orm);
+    d.null_ = pop < 64 && static_cast<int>(counter_draw(p.seed, kStreamNull, c) >> 58) < 64 - pop;
+    d.diversity = rows >= kDiversityMinRows && pop <= kDiversityMaxWorlds;
+    return d;
+}
+
+// Releases cells c0 .. n_cells-1 once world sw alone has non-zero weight
+// (w = 1, se = 1).  For each cell: if y_sw == y_j* the worlds agree and the
+// variance is 0; otherwise every other world has weight exactly 0, so the
+// mean is y_sw and the variance 0, unless some release value is not finite,
+// which makes the sums NaN.  No posterior update happens either way.
+__device__ void collapsed_tail(const FinParams &p, uint64_t c0, uint64_t n_cells, int jstar, int sw,
+                               ChainShared &sh, int &slot) {
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    bool any_float = false;
+    for (int s = 0; s < p.n_specs; s++) any_float = any_float || (cell_code(p.spec[s]) & 3) == 2;
+    for (; c0 < n_cells; c0 += 32) {
+        const uint64_t rem = n_cells - c0;
+        const int kend = rem < 32 ? static_cast<int>(rem) : 32;
+        unsigned bad = 0;
+        if (any_float) {
+            // bit k: this thread's world value of cell c0+k is not finite
+            uint32_t g = static_cast<uint32_t>(c0 / p.n_specs);
+            int s = static_cast<int>(c0 % p.n_specs);
+            for (int k = 0; k < kend; k++) {
+                const int code = cell_code(p.spec[s]);
+                if ((code & 3) == 2 && ((p.meta[2 * g + 1] >> t) & 1ull)) {
+                    const unsigned long long v =
+                        static_cast<const unsigned long long *>(p.spec[s].out)[static_cast<size_t>(g) * kWorlds + t];
+                    if (raw_nonfinite(v, code)) bad |= 1u << k;
+                }
+                if (++s == p.n_specs) s = 0, g++;
+            }
+            bad = chain_or(bad, sh, slot, warp, lane);
+        }
+        if (warp == 0 && lane < kend) {
+            const uint64_t c = c0 + lane;
+            const CellDraw d = draw_cell(p, c);
+            uint32_t f = d.diversity ? PAC_F_DIVERSITY : 0u;
+            if (d.null_) {
+                p.noised[c] = 0.0;
+                p.is_null[c] = 1;
+                p.flags[c] = f | PAC_F_NULL;
+            } else {
+                const uint32_t g = static_cast<uint32_t>(c / p.n_specs);
+                const FinSpec &sp = p.spec[c % p.n_specs];
+                const int code = cell_code(sp);
+                const unsigned long long *o =
+                    static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * kWorlds;
+                const double yj = raw_to_double(((d.orm >> jstar) & 1ull) ? o[jstar] : 0ull, code);
+                const double ys = raw_to_double(((d.orm >> sw) & 1ull) ? o[sw] : 0ull, code);
+                p.noised[c] = (ys == yj || !((bad >> lane) & 1u)) ? yj : __longlong_as_double(0x7FF8000000000000ll);
+                p.is_null[c] = 0;
+                p.flags[c] = f | PAC_F_ZEROVAR;
+            }
+        }
+    }
 }
 
 __device__ void finalize_chain(const FinParams &p) {
     __shared__ ChainShared sh;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> 58);
-    const double log_uniform = -log(64.0);
-    double logp = log_uniform;
+    const double inv2b = 1.0 / (2.0 * p.budget);
+    const bool adaptive = p.mode != PAC_FIN_INDEPENDENT;
+    double L = 0.0, w = 1.0, se = static_cast<double>(kWorlds), rse = 1.0 / se;
+    bool sup = true;     // posterior of world t is non-zero
+    bool single = false; // one world alone has non-zero weight
     int slot = 0;
     const uint64_t n_cells = static_cast<uint64_t>(p.n_groups) * p.n_specs;
-    CellLoad nxt{};
-    if (n_cells > 0) nxt = load_cell(p, 0, t, jstar);
-    for (uint64_t c0 = 0; c0 < n_cells; c0 += 32) {
+    // world values of cells pc - kAhead .. pc - 1, oldest first
+    CellRaw ring[kAhead];
+    uint32_t pg = 0;
+    int ps = 0;
+    uint64_t pc = 0;
+#pragma unroll
+    for (int i = 0; i < kAhead; i++) {
+        if (pc < n_cells) {
+            ring[i] = load_raw(p, pg, ps, t, jstar);
+            pc++;
+            if (++ps == p.n_specs) ps = 0, pg++;
+        }
+    }
+    uint64_t c0 = 0;
+    while (c0 < n_cells && !single) {
+        const uint64_t rem = n_cells - c0;
+        const int kend = rem < 32 ? static_cast<int>(rem) : 32;
         // posterior-free draws of cells c0 .. c0+31, one per lane
-        const uint64_t cl = c0 + lane;
+        CellDraw dl{0ull, true, false};
         double zc = 0.0;
-        bool nl = false;
-        if (cl < n_cells) {
-            const uint64_t orm = p.meta[2 * static_cast<uint32_t>(cl / p.n_specs) + 1];
-            const int pop = __popcll(orm);
-            nl = pop < 64 && static_cast<int>(counter_draw(p.seed, kStreamNull, cl) >> 58) < 64 - pop;
-            if (!nl) {
+        if (lane < kend) {
+            const uint64_t cl = c0 + lane;
+            dl = draw_cell(p, cl);
+            if (!dl.null_) {
                 const double u1 = uniform01_open0(counter_draw(p.seed, kStreamNoise, 2 * cl));
                 const double u2 = uniform01(counter_draw(p.seed, kStreamNoise, 2 * cl + 1));
                 zc = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
             }
         }
-        const uint32_t nulls = __ballot_sync(kFull, nl);
-        const uint64_t rem = n_cells - c0;
-        const int kend = rem < 32 ? static_cast<int>(rem) : 32;
-        for (int k = 0; k < kend; k++) {
-            const uint64_t c = c0 + k;
-            const CellLoad cur = nxt;
-            if (c + 1 < n_cells) nxt = load_cell(p, c + 1, t, jstar);
-            const int pop = __popcll(cur.orm);
-            uint32_t f = (cur.rows >= kDiversityMinRows && pop <= kDiversityMaxWorlds) ? PAC_F_DIVERSITY : 0u;
-            if (p.mode == PAC_FIN_INDEPENDENT) logp = log_uniform;
-            if ((nulls >> k) & 1u) {
-                if (t == 0) {
-                    p.noised[c] = 0.0;
-                    p.is_null[c] = 1;
-                    p.flags[c] = f | PAC_F_NULL;
-                }
-                continue;
+        const uint32_t nulls = __ballot_sync(kFull, dl.null_);
+        double my_yt = 0.0;
+        bool my_zv = false;
+        int kc = 0;
+        for (; kc < kend && !single; kc++) {
+            const CellRaw cur = ring[0];
+#pragma unroll
+            for (int i = 0; i + 1 < kAhead; i++) ring[i] = ring[i + 1];
+            if (pc < n_cells) {
+                ring[kAhead - 1] = load_raw(p, pg, ps, t, jstar);
+                pc++;
+                if (++ps == p.n_specs) ps = 0, pg++;
             }
-            const double z = __shfl_sync(kFull, zc, k);
-            // step 1: variance under the posterior (exactly 0 when all allowed worlds agree)
-            const double pw = exp(logp);
-            const bool same = !(pw > 0.0) || cur.y == cur.yj;
-            const bool all_equal = __syncthreads_and(same) != 0;
-            const double mu = chain_reduce(pw * cur.y, false, sh, slot, warp, lane);
-            const double d = cur.y - mu;
-            double var = chain_reduce(pw * d * d, false, sh, slot, warp, lane);
-            if (all_equal) var = 0.0;
+            if (!adaptive) {
+                L = 0.0, w = 1.0, se = static_cast<double>(kWorlds), rse = 1.0 / se;
+                sup = true;
+            }
+            if ((nulls >> kc) & 1u) continue;
+            const unsigned long long orm = __shfl_sync(kFull, dl.orm, kc);
+            const double z = __shfl_sync(kFull, zc, kc);
+            const unsigned long long yr = ((orm >> t) & 1ull) ? cur.y : 0ull;
+            const unsigned long long yjr = ((orm >> jstar) & 1ull) ? cur.yj : 0ull;
+            const double yj = raw_to_double(yjr, cur.code);
+            // step 1: variance under the posterior, exactly 0 when all worlds of
+            // non-zero posterior agree (then neither sum is needed)
+            double var = 0.0, y = 0.0;
+            if (!chain_all(!sup || same_value(yr, yjr, cur.code))) {
+                y = raw_to_double(yr, cur.code);
+                const double mu = chain_sum(w * y, sh, slot, warp, lane) * rse;
+                const double d = y - mu;
+                var = chain_sum(w * d * d, sh, slot, warp, lane) * rse;
+            }
             // step 2: noise variance; step 3: release
-            const double delta = var / (2.0 * p.budget);
-            const double yt = cur.yj + sqrt(delta) * z;
-            // step 4: Bayesian update in log space
-            if (delta > 0.0) {
-                const double e = yt - cur.y;
-                logp += -(e * e) / (2.0 * delta);
-                const double mx = chain_reduce(logp, true, sh, slot, warp, lane);
-                const double se = chain_reduce(exp(logp - mx), false, sh, slot, warp, lane);
-                logp -= mx + log(se);
-            } else {
-                f |= PAC_F_ZEROVAR;
+            const double delta = var * inv2b;
+            const double yt = delta == 0.0 ? yj : yj + sqrt(delta) * z;
+            // step 4: Bayesian update of the log-weights
+            const bool upd = delta > 0.0;
+            if (upd) {
+                const double e = yt - y;
+                L = fma(e * e, -0.5 / delta, L);
+                L -= chain_max_nonpos(L, sh, slot, warp, lane);
+                w = exp(L);
+                if (adaptive) {
+                    int cnt;
+                    se = chain_sum_count(w, w > 0.0, cnt, sh, slot, warp, lane);
+                    single = cnt == 1;
+                } else {
+                    se = chain_sum(w, sh, slot, warp, lane);
+                }
+                rse = 1.0 / se;
+                sup = w * rse > 0.0;
             }
-            if (t == 0) {
-                p.noised[c] = yt;
-                p.is_null[c] = 0;
-                p.flags[c] = f;
+            if (lane == kc) {
+                my_yt = yt;
+                my_zv = !upd;
             }
         }
+        // outputs of cells c0 .. c0+kc-1, one per lane of warp 0
+        if (warp == 0 && lane < kc) {
+            const uint64_t c = c0 + lane;
+            const bool nul = (nulls >> lane) & 1u;
+            const uint32_t f = dl.diversity ? PAC_F_DIVERSITY : 0u;
+            p.noised[c] = nul ? 0.0 : my_yt;
+            p.is_null[c] = nul ? 1 : 0;
+            p.flags[c] = f | (nul ? PAC_F_NULL : (my_zv ? PAC_F_ZEROVAR : 0u));
+        }
+        c0 += kc;
     }
-    if (p.posterior) p.posterior[t] = exp(logp);
+    if (single && c0 < n_cells) {
+        // the world left with weight 1
+        const unsigned bal = __ballot_sync(kFull, w > 0.0);
+        unsigned long long *pp = sh.bits[slot];
+        slot = (slot + 1) & 3;
+        if (lane == 0) pp[warp] = bal;
+        __syncthreads();
+        const int sw = pp[0] ? __ffs(static_cast<int>(pp[0])) - 1 : 32 + __ffs(static_cast<int>(pp[1])) - 1;
+        collapsed_tail(p, c0, n_cells, jstar, sw, sh, slot);
+    }
+    if (p.posterior) p.posterior[t] = w * rse;
 }
 
 __global__ void __launch_bounds__(kChainThreads) k_finalize_adaptive(const __grid_constant__ FinParams p) {
@@ -254,7 +467,7 @@ __global__ void __launch_bounds__(256) k_finalize_independent(const __grid_const
     }
 }
 
-// One posterior chain (64 threads) per query of a batch.
+// One posterior chain per query of a batch.
 __global__ void __launch_bounds__(kChainThreads) k_finalize_batch(const FinParams *__restrict__ ps, int n) {
     if (static_cast<int>(blockIdx.x) < n) finalize_chain(ps[blockIdx.x]);
 }

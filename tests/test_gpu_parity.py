@@ -194,6 +194,59 @@ def test_finalize_matches_oracle(ctx, mode, G):
     np.testing.assert_allclose(got["posterior"], ref["posterior"], rtol=1e-6, atol=1e-12)
 
 
+def _aggregate_like(G, seed):
+    """World results shaped like real aggregates: each world holds about half
+    of a group's rows, so the 64 results of a cell are close to one another
+    and the adaptive posterior narrows over the cells until one world is left."""
+    r = np.random.default_rng(seed)
+    n = np.maximum(1, r.lognormal(6, 2, G)).astype(np.int64)
+    cnt = r.binomial(n[:, None], 0.5, (G, 64)).astype(np.uint64)
+    c = cnt.astype(np.float64)
+    isum = (c * 500 + r.normal(0, 1, (G, 64)) * np.sqrt(c) * 290).astype(np.int64)
+    fsum = c * 3.7 + r.normal(0, 1, (G, 64)) * np.sqrt(c) * 2.0
+    avg = fsum / np.maximum(c, 1)
+    meta = np.zeros((G, 2), dtype=np.uint64)
+    meta[:, 0] = n
+    meta[:, 1] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    meta[n < 40, 1] = np.uint64(0x00FF00FF00FF00FF)
+    kv = [(B.PAC_COUNT, 0, B.PAC_I64), (B.PAC_SUM, 0, B.PAC_I64), (B.PAC_SUM, 0, B.PAC_F64),
+          (B.PAC_AVG, 0, B.PAC_I64)]
+    return [cnt, isum, fsum, avg], kv, meta
+
+
+@pytest.mark.parametrize("case", ["long", "nonfinite", "bigint", "independent"])
+def test_finalize_long_chain_matches_oracle(ctx, case):
+    """Thousands of chained releases on aggregate-like results: the posterior
+    collapses onto one world part-way, after which releases have variance 0.
+    'nonfinite' plants inf/NaN world values in float cells after the
+    collapse (the variance sums turn them into NaN releases); 'bigint' puts
+    int64 sums above 2^53, where distinct integers can meet as doubles."""
+    G = 2500
+    outs, kv, meta = _aggregate_like(G, 4242)
+    r = np.random.default_rng(7)
+    if case == "nonfinite":
+        for g in r.choice(np.arange(G // 2, G), 40, replace=False):
+            outs[2][g, r.integers(0, 64, 3)] = [np.inf, -np.inf, np.nan][int(r.integers(0, 3))]
+        outs[3][G - 5, :] = np.nan
+        outs[2][G - 7, :] = np.inf
+        outs[2][G - 9, :] = 2.0 ** 1023          # doubled by the release scale: inf
+    if case == "bigint":
+        outs[1] = (np.int64(1) << 60) + r.integers(0, 100, (G, 64)).astype(np.int64)
+        outs[1][::2] = r.integers(-2**62, 2**62, (G - G // 2, 64))
+    mode = B.PAC_FIN_INDEPENDENT if case == "independent" else B.PAC_FIN_ADAPTIVE
+    seed, budget = 99, 1.0 / 128
+    got = ctx.finalize(outs, kv, meta, seed, budget, mode)
+    y = np.stack([o.astype(np.float64) for o in outs], axis=1)
+    ref = orc.finalize(y, [orc.release_scale(k) for k, _, _ in kv], meta[:, 0], meta[:, 1], seed, budget, mode)
+    if case == "long":
+        assert ((ref["flags"] & orc.F_ZEROVAR) != 0).sum() > G      # the chain did collapse
+    np.testing.assert_array_equal(got["is_null"], ref["is_null"])
+    np.testing.assert_array_equal(got["flags"], ref["flags"])
+    live = ref["is_null"] == 0
+    np.testing.assert_allclose(got["noised"][live], ref["noised"][live], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(got["posterior"], ref["posterior"], rtol=1e-6, atol=1e-12)
+
+
 def test_lowcard_60m_full_size_sampled(ctx):
     """The 60M-row, 4-group, 4-column workload at full size, in the launch
     configuration the benchmark times: sampled worlds against the oracle,
