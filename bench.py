@@ -626,7 +626,9 @@ def run_ours(args):
     algo_bytes = n * wcfg["in_bytes_per_row"] + out_bytes
     achieved = algo_bytes / (agg_mean / 1e3) / 1e9
     kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
-              2: "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"}.get(path, str(path))
+              2: "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)",
+              3: "k_part_hist + k_part_scan + k_part_scatter + k_batch_agg + k_batch_merge "
+                 "(all launches of pac_aggregate_multi)"}.get(path, str(path))
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -645,7 +647,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": args.workload, "rows": n, "groups": G, "value_columns": C, "worlds": 64,
                        "aggregates": wcfg["describe"], "l2": l2,
-                       "agg_path": {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores"}.get(path, str(path))},
+                       "agg_path": {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
+                                    3: "group partition + per-bit engine"}.get(path, str(path))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(args.workload, n) if path == 2 else None,
                          "kernel": kernel, "algorithmic_bytes": algo_bytes, "peak_source": peak_src,

@@ -2,11 +2,21 @@
 // (Sec. 2 "PAC Privacy"; Sec. 4.1 noise function steps 1-4; Sec. 2 fused
 // pac_noised_count, count[j*]*2; Sec. 3.2 "NULLs"; Sec. 5 "Diversity Check").
 //
-// In the adaptive mode every release depends on the posterior left by the
-// previous one, so one chain of threads walks all cells of the query in order
-// (group-major, then spec order), each thread holding some worlds; the independent
-// mode gives every cell its own warp (lane l: worlds l and l+32) under the
-// uniform prior.  FP64 is used only here.
+// A cell (group g, spec s) has 64 world results y_t (scaled by 2 for COUNT
+// and SUM, 0 for worlds outside the group's OR mask).  Its release:
+//   step 1  mu = sum_t p_t y_t, var = sum_t p_t (y_t - mu)^2 under the
+//           posterior p, exactly 0 when every world of non-zero posterior
+//           has y_t == y_j* (j* the secret world);
+//   step 2  delta = var / (2 B);
+//   step 3  release y_j* + sqrt(delta) z, z standard normal (Box-Muller);
+//   step 4  if delta > 0: log p_t += -(release - y_t)^2 / (2 delta), then
+//           normalise.
+// A NULL draw (Sec. 3.2) replaces the release of a cell whose group misses
+// worlds.  In the adaptive mode every release depends on the posterior left
+// by the previous one, so one chain of threads walks all cells of the query
+// in order (group-major, then spec order); in the independent mode every
+// cell starts from the uniform prior and cells are released in parallel.
+// FP64 is used only here.
 #include <cmath>
 
 #include "pac_internal.cuh"
@@ -25,172 +35,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
-__device__ __forceinline__ double world_value(const FinSpec &s, size_t idx) {
-    if (s.kind == PAC_COUNT) return static_cast<double>(static_cast<const unsigned long long *>(s.out)[idx]);
-    if (s.kind == PAC_AVG || s.vtype != PAC_I64) return static_cast<const double *>(s.out)[idx];
-    return static_cast<double>(static_cast<const long long *>(s.out)[idx]);
-}
-
 __device__ __forceinline__ double uniform01(uint64_t u) { return static_cast<double>(u >> 11) * 0x1.0p-53; }
 __device__ __forceinline__ double uniform01_open0(uint64_t u) {
     return static_cast<double>((u >> 11) + 1) * 0x1.0p-53;
-}
-
-// Releases cell c; logp0/logp1 are this lane's log-posterior entries.
-__device__ void release_cell(const FinParams &p, uint64_t c, int jstar, double &logp0, double &logp1) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t g = static_cast<uint32_t>(c / p.n_specs);
-    const int s = static_cast<int>(c % p.n_specs);
-    const FinSpec &sp = p.spec[s];
-    const uint64_t orm = p.meta[2 * g + 1];
-    const uint64_t rows = p.meta[2 * g];
-    const int pop = __popcll(orm);
-    uint32_t f = (rows >= kDiversityMinRows && pop <= kDiversityMaxWorlds) ? PAC_F_DIVERSITY : 0u;
-
-    if (p.mode == PAC_FIN_INDEPENDENT) {
-        logp0 = -log(64.0);
-        logp1 = -log(64.0);
-    }
-    if (pop < 64 && static_cast<int>(counter_draw(p.seed, kStreamNull, c) >> 58) < 64 - pop) {
-        if (lane == 0) {
-            p.noised[c] = 0.0;
-            p.is_null[c] = 1;
-            p.flags[c] = f | PAC_F_NULL;
-        }
-        return;
-    }
-    const double scale = (sp.kind == PAC_COUNT || sp.kind == PAC_SUM) ? 2.0 : 1.0;
-    const size_t base = static_cast<size_t>(g) * kWorlds;
-    const double y0 = ((orm >> lane) & 1ull) ? scale * world_value(sp, base + lane) : 0.0;
-    const double y1 = ((orm >> (lane + 32)) & 1ull) ? scale * world_value(sp, base + lane + 32) : 0.0;
-    const double yj = __shfl_sync(kFull, jstar < 32 ? y0 : y1, jstar & 31);
-
-    // step 1: variance under the posterior (exactly 0 when all allowed worlds agree)
-    const double p0 = exp(logp0), p1 = exp(logp1);
-    const bool same = (!(p0 > 0.0) || y0 == yj) && (!(p1 > 0.0) || y1 == yj);
-    const bool all_equal = __all_sync(kFull, same);
-    const double mu = warp_sum(p0 * y0 + p1 * y1);
-    const double d0 = y0 - mu, d1 = y1 - mu;
-    double var = warp_sum(p0 * d0 * d0 + p1 * d1 * d1);
-    if (all_equal) var = 0.0;
-    // step 2: noise variance; step 3: release
-    const double delta = var / (2.0 * p.budget);
-    const double u1 = uniform01_open0(counter_draw(p.seed, kStreamNoise, 2 * c));
-    const double u2 = uniform01(counter_draw(p.seed, kStreamNoise, 2 * c + 1));
-    const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
-    const double yt = yj + sqrt(delta) * z;
-    // step 4: Bayesian update in log space
-    if (delta > 0.0) {
-        const double e0 = yt - y0, e1 = yt - y1;
-        logp0 += -(e0 * e0) / (2.0 * delta);
-        logp1 += -(e1 * e1) / (2.0 * delta);
-        const double mx = warp_max(fmax(logp0, logp1));
-        const double se = warp_sum(exp(logp0 - mx) + exp(logp1 - mx));
-        const double lse = mx + log(se);
-        logp0 -= lse;
-        logp1 -= lse;
-    } else {
-        f |= PAC_F_ZEROVAR;
-    }
-    if (lane == 0) {
-        p.noised[c] = yt;
-        p.is_null[c] = 0;
-        p.flags[c] = f;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The posterior chain of one query (adaptive mode, and every batched query).
-// 64 threads, thread t holding world t.  The chain is bound by the latency of
-// dependent FP64 operations, so the state is kept in a form that needs one
-// exp and no log per update:
-//   L_t   log-weight of world t, shifted so that max_t L_t = 0 (all L_t <= 0),
-//   w_t   = exp(L_t), the weight left by the last update,
-//   se    = sum_t w_t,
-// which is the posterior of Sec. 4.1 step 4 up to normalisation:
-// p_t = w_t / se, log p_t = L_t - log(se).  The mean and variance of step 1
-// divide the weighted sums by se; the update adds -(e_t^2)/(2 delta) to L_t,
-// subtracts the new maximum (found as the least IEEE bit pattern, since every
-// L_t <= 0) and takes exp once.  In exact arithmetic every quantity is the
-// one of release_cell above; rounding differs by a few ulps.
-//
-// Step 1's test "all worlds of non-zero posterior agree" runs first, on the
-// raw 64-bit words, and skips both sums when it holds.  Once a single world
-// keeps non-zero weight (adaptive mode), every later release has variance 0
-// and the posterior no longer changes, so the remaining cells are released
-// in parallel, one per lane (collapsed_tail).  Draws that do not depend on
-// the posterior (the NULL decision and the Box-Muller normal of a cell) are
-// computed 32 cells at a time, one cell per lane, and world values are
-// loaded kAhead cells ahead of the chain.
-// ---------------------------------------------------------------------------
-constexpr int kChainThreads = kWorlds;  // thread t holds world t
-constexpr int kChainWarps = kChainThreads / 32;
-constexpr int kAhead = 4;
-
-struct ChainShared {
-    double part[4][kChainWarps];  // per-warp partials, rotating slots (one barrier per reduction)
-    unsigned long long bits[4][kChainWarps];
-};
-
-__device__ __forceinline__ double chain_sum(double v, ChainShared &sh, int &slot, int warp, int lane) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    double *pp = sh.part[slot];
-    slot = (slot + 1) & 3;
-    if (lane == 0) pp[warp] = v;
-    __syncthreads();
-    return pp[0] + pp[1];
-}
-
-// chain_sum, also counting the threads whose flag b is set.
-__device__ __forceinline__ double chain_sum_count(double v, bool b, int &cnt, ChainShared &sh, int &slot, int warp,
-                                                  int lane) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    const unsigned bal = __ballot_sync(kFull, b);
-    double *pp = sh.part[slot];
-    unsigned long long *pb = sh.bits[slot];
-    slot = (slot + 1) & 3;
-    if (lane == 0) {
-        pp[warp] = v;
-        pb[warp] = bal;
-    }
-    __syncthreads();
-    cnt = __popc(static_cast<unsigned>(pb[0])) + __popc(static_cast<unsigned>(pb[1]));
-    return pp[0] + pp[1];
-}
-
-// Maximum of non-positive doubles: the least bit pattern (+0 < -0 < -tiny <
-// ... < -inf as unsigned integers).
-__device__ __forceinline__ double chain_max_nonpos(double x, ChainShared &sh, int &slot, int warp, int lane) {
-    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const unsigned long long u = __shfl_xor_sync(kFull, b, o);
-        b = u < b ? u : b;
-    }
-    unsigned long long *pp = sh.bits[slot];
-    slot = (slot + 1) & 3;
-    if (lane == 0) pp[warp] = b;
-    __syncthreads();
-    b = pp[0] < pp[1] ? pp[0] : pp[1];
-    return __longlong_as_double(static_cast<long long>(b));
-}
-
-__device__ __forceinline__ bool chain_all(bool x) { return __syncthreads_and(x) != 0; }
-
-__device__ __forceinline__ unsigned chain_or(unsigned m, ChainShared &sh, int &slot, int warp, int lane) {
-    m = __reduce_or_sync(kFull, m);
-    unsigned long long *pp = sh.bits[slot];
-    slot = (slot + 1) & 3;
-    if (lane == 0) pp[warp] = m;
-    __syncthreads();
-    return static_cast<unsigned>(pp[0] | pp[1]);
 }
 
 // How the 64-bit words of a spec's result array read as the release's value:
@@ -266,6 +113,199 @@ __device__ __forceinline__ CellDraw draw_cell(const FinParams &p, uint64_t c) {
     d.null_ = pop < 64 && static_cast<int>(counter_draw(p.seed, kStreamNull, c) >> 58) < 64 - pop;
     d.diversity = rows >= kDiversityMinRows && pop <= kDiversityMaxWorlds;
     return d;
+}
+
+// The standard normal of cell c (Box-Muller on two counter draws).
+__device__ __forceinline__ double normal_draw(uint64_t seed, uint64_t c) {
+    const double u1 = uniform01_open0(counter_draw(seed, kStreamNoise, 2 * c));
+    const double u2 = uniform01(counter_draw(seed, kStreamNoise, 2 * c + 1));
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+
+// ---------------------------------------------------------------------------
+// Independent mode: every cell starts from the uniform prior, so step 1 is
+// the plain mean and variance of the 64 worlds (p_t = 1/64) and the
+// posterior after a release is needed for the last cell only (the one the
+// caller can read back).  One warp takes 32 consecutive cells: lane k makes
+// cell k's NULL decision and normal draw, then the warp releases the cells
+// one by one, lane l holding worlds l and l+32, and lane k stores cell k.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_finalize_independent(const __grid_constant__ FinParams p) {
+    const int lane = threadIdx.x & 31;
+    const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> 58);
+    const double inv2b = 1.0 / (2.0 * p.budget);
+    const double log_uniform = -log(64.0);
+    const uint64_t n_cells = static_cast<uint64_t>(p.n_groups) * p.n_specs;
+    const uint64_t n_blk = (n_cells + 31) / 32;
+    const uint64_t wid = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_w = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t blk = wid; blk < n_blk; blk += n_w) {
+        const uint64_t c0 = blk * 32;
+        const uint64_t rem = n_cells - c0;
+        const int kend = rem < 32 ? static_cast<int>(rem) : 32;
+        CellDraw dl{0ull, true, false};
+        double zc = 0.0;
+        if (lane < kend) {
+            dl = draw_cell(p, c0 + lane);
+            if (!dl.null_) zc = normal_draw(p.seed, c0 + lane);
+        }
+        const uint32_t nulls = __ballot_sync(kFull, dl.null_);
+        double my_yt = 0.0;
+        bool my_zv = false;
+        uint32_t g = static_cast<uint32_t>(c0 / p.n_specs);
+        int s = static_cast<int>(c0 % p.n_specs);
+        for (int k = 0; k < kend; k++, s = (s + 1 == p.n_specs) ? (g++, 0) : s + 1) {
+            const uint64_t c = c0 + k;
+            const bool last = p.posterior && c == n_cells - 1;
+            if ((nulls >> k) & 1u) {
+                if (last) {
+                    p.posterior[lane] = exp(log_uniform);
+                    p.posterior[lane + 32] = exp(log_uniform);
+                }
+                continue;
+            }
+            const unsigned long long orm = __shfl_sync(kFull, dl.orm, k);
+            const double z = __shfl_sync(kFull, zc, k);
+            const FinSpec &sp = p.spec[s];
+            const int code = cell_code(sp);
+            const unsigned long long *o =
+                static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * kWorlds;
+            const unsigned long long r0 = ((orm >> lane) & 1ull) ? o[lane] : 0ull;
+            const unsigned long long r1 = ((orm >> (lane + 32)) & 1ull) ? o[lane + 32] : 0ull;
+            const unsigned long long rj = ((orm >> jstar) & 1ull) ? o[jstar] : 0ull;
+            const double yj = raw_to_double(rj, code);
+            double var = 0.0, y0 = 0.0, y1 = 0.0;
+            if (!__all_sync(kFull, same_value(r0, rj, code) && same_value(r1, rj, code))) {
+                y0 = raw_to_double(r0, code);
+                y1 = raw_to_double(r1, code);
+                const double mu = warp_sum(y0 + y1) * (1.0 / kWorlds);
+                const double d0 = y0 - mu, d1 = y1 - mu;
+                var = warp_sum(fma(d0, d0, d1 * d1)) * (1.0 / kWorlds);
+            }
+            const double delta = var * inv2b;
+            const double yt = delta == 0.0 ? yj : yj + sqrt(delta) * z;
+            if (last) {
+                double l0 = log_uniform, l1 = log_uniform;
+                if (delta > 0.0) {
+                    const double e0 = yt - y0, e1 = yt - y1;
+                    l0 += -(e0 * e0) / (2.0 * delta);
+                    l1 += -(e1 * e1) / (2.0 * delta);
+                    double mx = fmax(l0, l1);
+                    for (int o2 = 16; o2; o2 >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o2));
+                    const double lse = mx + log(warp_sum(exp(l0 - mx) + exp(l1 - mx)));
+                    l0 -= lse;
+                    l1 -= lse;
+                }
+                p.posterior[lane] = exp(l0);
+                p.posterior[lane + 32] = exp(l1);
+            }
+            if (lane == k) {
+                my_yt = yt;
+                my_zv = !(delta > 0.0);
+            }
+        }
+        if (lane < kend) {
+            const uint64_t c = c0 + lane;
+            const uint32_t f = dl.diversity ? PAC_F_DIVERSITY : 0u;
+            p.noised[c] = dl.null_ ? 0.0 : my_yt;
+            p.is_null[c] = dl.null_ ? 1 : 0;
+            p.flags[c] = f | (dl.null_ ? PAC_F_NULL : (my_zv ? PAC_F_ZEROVAR : 0u));
+        }
+    }
+    if (p.posterior && n_cells == 0 && blockIdx.x == 0 && threadIdx.x < 32) {
+        p.posterior[lane] = exp(log_uniform);
+        p.posterior[lane + 32] = exp(log_uniform);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The posterior chain of one query (adaptive mode, and every batched query).
+// 64 threads, thread t holding world t.  The chain is bound by the latency of
+// dependent FP64 operations, so the state is kept in a form that needs one
+// exp and no log per update:
+//   L_t   log-weight of world t, shifted so that max_t L_t = 0 (all L_t <= 0),
+//   w_t   = exp(L_t), the weight left by the last update,
+//   se    = sum_t w_t,
+// which is the posterior of Sec. 4.1 step 4 up to normalisation:
+// p_t = w_t / se, log p_t = L_t - log(se).  The mean and variance of step 1
+// divide the weighted sums by se; the update adds -(e_t^2)/(2 delta) to L_t,
+// subtracts the new maximum (found as the least IEEE bit pattern, since every
+// L_t <= 0) and takes exp once.  In exact arithmetic every quantity is the
+// one of steps 1-4 above; rounding differs by a few ulps.
+//
+// Step 1's test "all worlds of non-zero posterior agree" runs first, on the
+// raw 64-bit words, and skips both sums when it holds.  Once a single world
+// keeps non-zero weight (adaptive mode), every later release has variance 0
+// and the posterior no longer changes, so the remaining cells are released
+// in parallel, one per lane (collapsed_tail).  Draws that do not depend on
+// the posterior (the NULL decision and the Box-Muller normal of a cell) are
+// computed 32 cells at a time, one cell per lane, and world values are
+// loaded kAhead cells ahead of the chain.
+// ---------------------------------------------------------------------------
+constexpr int kChainThreads = kWorlds;  // thread t holds world t
+constexpr int kChainWarps = kChainThreads / 32;
+constexpr int kAhead = 4;
+
+struct ChainShared {
+    double part[4][kChainWarps];  // per-warp partials, rotating slots (one barrier per reduction)
+    unsigned long long bits[4][kChainWarps];
+};
+
+__device__ __forceinline__ double chain_sum(double v, ChainShared &sh, int &slot, int warp, int lane) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    double *pp = sh.part[slot];
+    slot = (slot + 1) & 3;
+    if (lane == 0) pp[warp] = v;
+    __syncthreads();
+    return pp[0] + pp[1];
+}
+
+// chain_sum, also counting the threads whose flag b is set.
+__device__ __forceinline__ double chain_sum_count(double v, bool b, int &cnt, ChainShared &sh, int &slot, int warp,
+                                                  int lane) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const unsigned bal = __ballot_sync(kFull, b);
+    double *pp = sh.part[slot];
+    unsigned long long *pb = sh.bits[slot];
+    slot = (slot + 1) & 3;
+    if (lane == 0) {
+        pp[warp] = v;
+        pb[warp] = bal;
+    }
+    __syncthreads();
+    cnt = __popc(static_cast<unsigned>(pb[0])) + __popc(static_cast<unsigned>(pb[1]));
+    return pp[0] + pp[1];
+}
+
+// Maximum of non-positive doubles: the least bit pattern (+0 < -0 < -tiny <
+// ... < -inf as unsigned integers).
+__device__ __forceinline__ double chain_max_nonpos(double x, ChainShared &sh, int &slot, int warp, int lane) {
+    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(kFull, b, o);
+        b = u < b ? u : b;
+    }
+    unsigned long long *pp = sh.bits[slot];
+    slot = (slot + 1) & 3;
+    if (lane == 0) pp[warp] = b;
+    __syncthreads();
+    b = pp[0] < pp[1] ? pp[0] : pp[1];
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
+__device__ __forceinline__ bool chain_all(bool x) { return __syncthreads_and(x) != 0; }
+
+__device__ __forceinline__ unsigned chain_or(unsigned m, ChainShared &sh, int &slot, int warp, int lane) {
+    m = __reduce_or_sync(kFull, m);
+    unsigned long long *pp = sh.bits[slot];
+    slot = (slot + 1) & 3;
+    if (lane == 0) pp[warp] = m;
+    __syncthreads();
+    return static_cast<unsigned>(pp[0] | pp[1]);
 }
 
 // Releases cells c0 .. n_cells-1 once world sw alone has non-zero weight
@@ -355,11 +395,7 @@ __device__ void finalize_chain(const FinParams &p) {
         if (lane < kend) {
             const uint64_t cl = c0 + lane;
             dl = draw_cell(p, cl);
-            if (!dl.null_) {
-                const double u1 = uniform01_open0(counter_draw(p.seed, kStreamNoise, 2 * cl));
-                const double u2 = uniform01(counter_draw(p.seed, kStreamNoise, 2 * cl + 1));
-                zc = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
-            }
+            if (!dl.null_) zc = normal_draw(p.seed, cl);
         }
         const uint32_t nulls = __ballot_sync(kFull, dl.null_);
         double my_yt = 0.0;
@@ -398,7 +434,9 @@ __device__ void finalize_chain(const FinParams &p) {
             const double yt = delta == 0.0 ? yj : yj + sqrt(delta) * z;
             // step 4: Bayesian update of the log-weights
             const bool upd = delta > 0.0;
-            if (upd) {
+            // independent mode: the next cell starts from the uniform prior, so
+            // only the last cell's update is ever read
+            if (upd && (adaptive || c0 + kc + 1 == n_cells)) {
                 const double e = yt - y;
                 L = fma(e * e, -0.5 / delta, L);
                 L -= chain_max_nonpos(L, sh, slot, warp, lane);
@@ -444,27 +482,6 @@ __device__ void finalize_chain(const FinParams &p) {
 
 __global__ void __launch_bounds__(kChainThreads) k_finalize_adaptive(const __grid_constant__ FinParams p) {
     finalize_chain(p);
-}
-
-__global__ void __launch_bounds__(256) k_finalize_independent(const __grid_constant__ FinParams p) {
-    const int lane = threadIdx.x & 31;
-    const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> 58);
-    const uint64_t n_cells = static_cast<uint64_t>(p.n_groups) * p.n_specs;
-    const uint64_t wid = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_w = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (uint64_t c = wid; c < n_cells; c += n_w) {
-        double logp0, logp1;
-        release_cell(p, c, jstar, logp0, logp1);
-        // the posterior left by the last release (uniform prior + one update)
-        if (p.posterior && c == n_cells - 1) {
-            p.posterior[lane] = exp(logp0);
-            p.posterior[lane + 32] = exp(logp1);
-        }
-    }
-    if (p.posterior && n_cells == 0 && blockIdx.x == 0 && threadIdx.x < 32) {
-        p.posterior[lane] = exp(-log(64.0));
-        p.posterior[lane + 32] = exp(-log(64.0));
-    }
 }
 
 // One posterior chain per query of a batch.

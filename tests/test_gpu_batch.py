@@ -147,6 +147,8 @@ def _mixed_batch():
         (90_000, 5000, np.int32, ALL, np.float32, {}),
         (12_345, 700, np.int32, [B.PAC_MIN, B.PAC_MAX], np.float64, {}),
         (65_536, 16, np.uint8, [B.PAC_COUNT, B.PAC_SUM], np.float32, {"fin_mode": B.PAC_FIN_ADAPTIVE}),
+        (40_000, 900, np.int32, [B.PAC_COUNT, B.PAC_SUM, B.PAC_AVG], np.int64,
+         {"fin_mode": B.PAC_FIN_INDEPENDENT}),
     ]
     for i, (n, G, gdt, kinds, vdt, kw) in enumerate(cases):
         qs.append(Q(500 + i, n, G, gdt, kinds, vdt, **kw))
