@@ -499,7 +499,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     ctx = B.pac_create(local)
     if args.path:
-        B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2}[args.path])
+        B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2, "engine": 3}[args.path])
 
     wcfg = WORKLOADS[args.workload]
     wl = _gen(args.workload, rank, args.rows)
@@ -676,7 +676,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lowcard_60m", choices=sorted(WORKLOADS))
     ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
-    ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma"])
+    ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma", "engine"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=4_000_000)
     ap.add_argument("--ref-rows", type=int, default=1_000_000)

@@ -214,8 +214,8 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float blk) {
 
 // One row r of the broadcast loop: every loop-type slot takes row r's value.
 template <int NS, int SIG>
-__device__ __forceinline__ void loop_row(const ItemShared &is, int r, uint32_t M0, uint32_t M1,
-                                         const uint64_t (&vals)[NS], const int (&slice)[NS], uint32_t n,
+__device__ __forceinline__ void loop_row(const ItemShared &is, int r, uint32_t M0, uint32_t M1, bool bal,
+                                         const uint64_t (&vals)[NS], const bool (&sliced)[NS],
                                          RunAcc<NS> &ra, float (&fb0)[NS], float (&fb1)[NS]) {
     const bool b0 = (M0 >> r) & 1u, b1 = (M1 >> r) & 1u;
 #pragma unroll
@@ -223,10 +223,10 @@ __device__ __forceinline__ void loop_row(const ItemShared &is, int r, uint32_t M
         if (s >= nslots_of<SIG>(is)) continue;
         const int op = op_of<SIG>(is, s);
         if (op == OP_ISUM) {
-            if (slice[s] > 0 && n >= 8) continue;
+            if (sliced[s]) continue;
             const uint64_t x = __shfl_sync(kFull, vals[s], r);
             ra.a0[s] += b0 ? x : 0ull;
-            ra.a1[s] += b1 ? x : 0ull;
+            if (!bal) ra.a1[s] += b1 ? x : 0ull;  // with bal world j+32 = total - world j
             ra.tot[s] += x;
         } else if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
             const float x = __int_as_float(__shfl_sync(kFull, static_cast<int>(vals[s]), r));
@@ -255,13 +255,18 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
     ra.c0 = __popc(M0);
     ra.c1 = __popc(M1);
     bool any_loop = false;
+    // bit-slicing costs a fixed amount per value bit, the broadcast loop a
+    // fixed amount per row: slice runs with at least as many rows as bits
+    bool sliced[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) {
+        sliced[s] = false;
         if (s >= nslots_of<SIG>(is)) continue;
         const int op = op_of<SIG>(is, s);
         ra.a0[s] = ra.a1[s] = op_identity(op);
         ra.tot[s] = 0;
-        if (op == OP_ISUM && slice[s] > 0 && ra.n >= 8) {
+        sliced[s] = op == OP_ISUM && slice[s] > 0 && ra.n >= static_cast<uint32_t>(slice[s]);
+        if (sliced[s]) {
             // bits below 26 add up in 32 bits (at most 32 rows * 2^26 < 2^31)
             uint32_t p0 = 0, p1 = 0, pt = 0;
             uint64_t acc0 = 0, acc1 = 0, tot = 0;
@@ -303,13 +308,13 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
     if (SIG != 0 && R == kFull) {
 #pragma unroll
         for (int r = 0; r < 32; r++) {
-            loop_row<NS, SIG>(is, r, M0, M1, vals, slice, ra.n, ra, fb0, fb1);
+            loop_row<NS, SIG>(is, r, M0, M1, bal, vals, sliced, ra, fb0, fb1);
             if ((r & 7) == 7) flush_blocks();
         }
     } else {
         int blk = 0;
         for (uint32_t rr = R; rr; rr &= rr - 1) {
-            loop_row<NS, SIG>(is, __ffs(rr) - 1, M0, M1, vals, slice, ra.n, ra, fb0, fb1);
+            loop_row<NS, SIG>(is, __ffs(rr) - 1, M0, M1, bal, vals, sliced, ra, fb0, fb1);
             if (++blk == 8) {
                 blk = 0;
                 flush_blocks();

@@ -301,19 +301,27 @@ def test_forced_per_bit_paths(ctx, path, mode, G, gdt, vdtype):
     np.testing.assert_array_equal(meta[:, 1], mo)
 
 
-@pytest.mark.parametrize("dist", ["narrow", "wide", "negative", "zeros"])
-def test_engine_int_sums_bit_sliced_and_looped(ctx, dist):
-    """Int64 SUM on the engine: narrow non-negative values take the bit-sliced
-    form, wide or negative ones the broadcast loop; both exact."""
+@pytest.mark.parametrize("only_sum", [False, True])
+@pytest.mark.parametrize("dist", ["narrow", "wide", "w45", "negative", "zeros", "short_runs"])
+def test_engine_int_sums_bit_sliced_and_looped(ctx, dist, only_sum):
+    """Int64 SUM on the engine: non-negative values in runs at least as long
+    as their bit length take the bit-sliced form (planes of the low and high
+    words), short runs and negative values the broadcast loop; all exact.
+    only_sum: COUNT + SUM alone (compile-time slot operations)."""
     n, G = 200_000, 3
     r = np.random.default_rng(len(dist))
     keys = r.integers(0, 50_000, n).astype(np.int64)
-    gids = np.sort(r.integers(0, G, n)).astype(np.uint8)   # long runs
+    gids = r.integers(0, G, n).astype(np.uint8)
+    if dist != "short_runs":
+        gids = np.sort(gids)                                # long runs
     vals = {"narrow": r.integers(0, 2**31, n), "wide": r.integers(0, 2**40, n),
-            "negative": r.integers(-10**9, 10**9, n), "zeros": np.zeros(n, dtype=np.int64)}[dist].astype(np.int64)
+            "w45": r.integers(2**44, 2**45, n), "negative": r.integers(-10**9, 10**9, n),
+            "zeros": np.zeros(n, dtype=np.int64), "short_runs": r.integers(0, 2**20, n)}[dist].astype(np.int64)
     qk = orc.query_key(99)
     masks = orc.hash_keys(keys, qk, orc.BALANCED)
-    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals), (B.PAC_AVG, 0, vals), (B.PAC_MIN, 0, vals)]
+    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals)]
+    if not only_sum:
+        specs += [(B.PAC_AVG, 0, vals), (B.PAC_MIN, 0, vals)]
     got, meta, st = ctx.aggregate(keys, gids, G, specs, qkey=qk, path=3)
     assert st == B.PAC_OK and ctx.last_path == 3
     for (kind, _, v), g_out in zip(specs, got):
