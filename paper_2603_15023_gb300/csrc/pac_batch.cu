@@ -650,20 +650,29 @@ __global__ void __launch_bounds__(256) k_part_hist(const BatchQueryDev *__restri
         for (uint32_t g = threadIdx.x; g < S; g += blockDim.x) cnt_s[g] = 0;
         __syncthreads();
         const uint64_t end = item.row0 + item.rows;
-        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; base < end;
-             base += static_cast<uint64_t>(n_warps) * 32) {
-            const uint64_t r = base + lane;
-            bool valid = r < end;
-            uint32_t g = valid ? row_gid(q.in, r) : 0xFFFFFFFFu;
-            if (valid && g >= G) {  // out-of-range group id: the row is dropped, and reported
-                raise_status(status, kStatusBadGroup);
-                valid = false;
-                g = 0xFFFFFFFFu;
+        constexpr int kC = 4;  // batches whose group ids are in flight together
+        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32 * kC; base < end;
+             base += static_cast<uint64_t>(n_warps) * 32 * kC) {
+            uint32_t gc[kC];
+#pragma unroll
+            for (int u = 0; u < kC; u++) {
+                const uint64_t r = base + 32 * u + lane;
+                gc[u] = r < end ? row_gid(q.in, r) : 0xFFFFFFFFu;
             }
-            const uint32_t peers = __match_any_sync(kFull, g);
-            if (valid && lane == __ffs(peers) - 1) {
-                if (g < S) atomicAdd(cnt_s + g, static_cast<uint32_t>(__popc(peers)));
-                else atomicAdd(q.pcnt + g, static_cast<uint32_t>(__popc(peers)));
+#pragma unroll
+            for (int u = 0; u < kC; u++) {
+                uint32_t g = gc[u];
+                bool valid = base + 32 * u + lane < end;
+                if (valid && g >= G) {  // out-of-range group id: the row is dropped, and reported
+                    raise_status(status, kStatusBadGroup);
+                    valid = false;
+                    g = 0xFFFFFFFFu;
+                }
+                const uint32_t peers = __match_any_sync(kFull, g);
+                if (valid && lane == __ffs(peers) - 1) {
+                    if (g < S) atomicAdd(cnt_s + g, static_cast<uint32_t>(__popc(peers)));
+                    else atomicAdd(q.pcnt + g, static_cast<uint32_t>(__popc(peers)));
+                }
             }
         }
         __syncthreads();
@@ -745,12 +754,20 @@ __global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__res
         // (1) the item's rows per small group
         for (uint32_t g = threadIdx.x; g < S; g += blockDim.x) cur_s[g] = 0;
         __syncthreads();
-        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; hot && base < end;
-             base += static_cast<uint64_t>(n_warps) * 32) {
-            const uint64_t r = base + lane;
-            const uint32_t g = r < end ? row_gid(q.in, r) : 0xFFFFFFFFu;
-            const uint32_t peers = __match_any_sync(kFull, g);
-            if (g < S && lane == __ffs(peers) - 1) atomicAdd(cur_s + g, static_cast<uint32_t>(__popc(peers)));
+        constexpr int kC = 4;  // batches whose group ids are in flight together
+        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32 * kC; hot && base < end;
+             base += static_cast<uint64_t>(n_warps) * 32 * kC) {
+            uint32_t gc[kC];
+#pragma unroll
+            for (int u = 0; u < kC; u++) {
+                const uint64_t r = base + 32 * u + lane;
+                gc[u] = r < end ? row_gid(q.in, r) : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int u = 0; u < kC; u++) {
+                const uint32_t peers = __match_any_sync(kFull, gc[u]);
+                if (gc[u] < S && lane == __ffs(peers) - 1) atomicAdd(cur_s + gc[u], static_cast<uint32_t>(__popc(peers)));
+            }
         }
         __syncthreads();
         // (2) one range of the query's cursor per small group
@@ -759,30 +776,54 @@ __global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__res
             if (c) cur_s[g] = atomicAdd(q.pcur + g, c);
         }
         __syncthreads();
-        // (3) rows into group order
-        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32; base < end;
-             base += static_cast<uint64_t>(n_warps) * 32) {
-            const uint64_t r = base + lane;
-            bool valid = r < end;
-            uint32_t g = valid ? row_gid(q.in, r) : 0xFFFFFFFFu;
-            if (valid && g >= G) {
-                valid = false;
-                g = 0xFFFFFFFFu;
+        // (3) rows into group order, two 32-row batches per warp at a time:
+        // the group ids, keys and first values of both are loaded before the
+        // cursor atomics and the hashing, so their latencies overlap
+        constexpr int kU = 2, kHoist = 2;
+        const uint64_t stride = static_cast<uint64_t>(n_warps) * 32 * kU;
+        const bool masks_in = (q.in.in_flags & PAC_IN_MASKS) != 0;
+        for (uint64_t base = item.row0 + static_cast<uint64_t>(warp) * 32 * kU; base < end; base += stride) {
+            uint64_t r[kU], raw[kU], v[kU][kHoist];
+            uint32_t g[kU];
+            bool valid[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                r[u] = base + 32 * u + lane;
+                valid[u] = r[u] < end;
+                g[u] = valid[u] ? row_gid(q.in, r[u]) : 0xFFFFFFFFu;
+                raw[u] = valid[u] ? static_cast<uint64_t>(__ldg(static_cast<const long long *>(q.in.km) + r[u])) : 0ull;
+#pragma unroll
+                for (int s2 = 0; s2 < kHoist; s2++)
+                    v[u][s2] = (valid[u] && s2 < q.n_slots) ? load_slot_value(q.slot[s2], r[u]) : 0ull;
             }
-            const uint32_t peers = __match_any_sync(kFull, g);
-            const int leader = __ffs(peers) - 1;
-            uint32_t at = 0;
-            if (valid && lane == leader) {
-                at = g < S ? atomicAdd(cur_s + g, static_cast<uint32_t>(__popc(peers)))
-                           : atomicAdd(q.pcur + g, static_cast<uint32_t>(__popc(peers)));
+            uint64_t d[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                if (valid[u] && g[u] >= G) {
+                    valid[u] = false;
+                    g[u] = 0xFFFFFFFFu;
+                }
+                const uint32_t peers = __match_any_sync(kFull, g[u]);
+                const int leader = __ffs(peers) - 1;
+                uint32_t at = 0;
+                if (valid[u] && lane == leader) {
+                    at = g[u] < S ? atomicAdd(cur_s + g[u], static_cast<uint32_t>(__popc(peers)))
+                                  : atomicAdd(q.pcur + g[u], static_cast<uint32_t>(__popc(peers)));
+                }
+                d[u] = __shfl_sync(kFull, at, leader) + __popc(peers & lt);
             }
-            at = __shfl_sync(kFull, at, leader);
-            if (!valid) continue;
-            const uint64_t d = at + __popc(peers & lt);
-            q.smask[d] = row_mask(q.in, r);
-            q.sgid[d] = g;
-            for (int s2 = 0; s2 < q.n_slots; s2++)
-                q.sval[static_cast<uint64_t>(s2) * q.in.n + d] = load_slot_value(q.slot[s2], r);
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                if (!valid[u]) continue;
+                q.smask[d[u]] = masks_in ? raw[u] : keyed_world_mask(static_cast<long long>(raw[u]), q.in.qkey,
+                                                                     q.in.hash_mode);
+                q.sgid[d[u]] = g[u];
+#pragma unroll
+                for (int s2 = 0; s2 < kHoist; s2++)
+                    if (s2 < q.n_slots) q.sval[static_cast<uint64_t>(s2) * q.in.n + d[u]] = v[u][s2];
+                for (int s2 = kHoist; s2 < q.n_slots; s2++)
+                    q.sval[static_cast<uint64_t>(s2) * q.in.n + d[u]] = load_slot_value(q.slot[s2], r[u]);
+            }
         }
         __syncthreads();
     }

@@ -253,7 +253,9 @@ __device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin,
     const uint64_t row = cta_begin + (ok ? off : n_rows - 1);
     r.km = __ldg(static_cast<const unsigned long long *>(p.in.km) + row);
     const uint32_t g = gid_load<GB>(p.in.gids, row);
-    r.gid = ok ? g : 0xFFFFFFFFu;
+    // all-ones marks a row past the end: a stored all-ones id (out of range
+    // too) becomes all-ones minus one, so it is still skipped and reported
+    r.gid = ok ? (g == 0xFFFFFFFFu ? 0xFFFFFFFEu : g) : 0xFFFFFFFFu;
     const long long x0 = __ldg(p.col[0] + row);
     r.v0 = p.n_cols > 0 ? x0 : 0;
     if (C4 == 4) {

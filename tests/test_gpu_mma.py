@@ -175,16 +175,20 @@ def test_mma_overflow_detected(ctx):
     assert st == B.PAC_E_OVERFLOW
 
 
-def test_mma_bad_group_id_is_reported(ctx):
+@pytest.mark.parametrize("gdt", [np.uint8, np.uint32])
+def test_mma_bad_group_id_is_reported(ctx, gdt):
     n = 1000
     keys = np.arange(n, dtype=np.int64)
-    gids = np.zeros(n, dtype=np.uint8)
+    gids = np.zeros(n, dtype=gdt)
     gids[17] = 9        # >= n_groups
+    if gdt == np.uint32:
+        gids[500] = 0xFFFFFFFF   # all ones: out of range too, not a padding row
     v = np.ones(n, dtype=np.int64)
-    for path in (1, 2):
-        got, meta, st = ctx.aggregate(keys, gids, 3, [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, v)], qkey=1, path=path)
-        assert st == B.PAC_E_INVALID
-        assert int(meta[0, 0]) == n - 1
+    for path in (1, 2, 3):
+        g_in = gids.view(np.int32) if gdt == np.uint32 else gids
+        got, meta, st = ctx.aggregate(keys, g_in, 3, [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, v)], qkey=1, path=path)
+        assert st == B.PAC_E_INVALID, path
+        assert int(meta[0, 0]) == n - (2 if gdt == np.uint32 else 1), path
 
 
 def test_auto_path_picks_tensor_cores(ctx):

@@ -342,6 +342,7 @@ def test_engine_bad_group_ids_skipped_and_reported(ctx, G):
     bad = r.random(n) < 0.01
     gids_bad = gids.copy()
     gids_bad[bad] = G + 5
+    gids_bad[np.flatnonzero(bad)[::2]] = -1     # 0xFFFFFFFF as an unsigned id
     vals = r.integers(-1000, 1000, n).astype(np.int64)
     qk = orc.query_key(5)
     specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals)]
