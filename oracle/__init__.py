@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             "orc_approx_sum_f32state": (i32, [vp, vp, i32, vp, i32, sz, u32, vp]),
             "orc_release_scale": (dbl, [i32, i32]),
             "orc_finalize": (None, [vp, vp, u32, u32, vp, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
+            "orc_select": (i32, [vp, vp, i32, i32, vp, u32, vp, i32, sz, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -102,6 +103,26 @@ def _out_dtype(kind: int, vtype: int):
     if kind == AVG:
         return np.float64
     return np.int64 if vtype == I64 else np.float64
+
+
+# -- PAC selection (Sec. 4.2 "PAC Selection"; Sec. 3.2 pac_select_<cmp>) ------
+LT, LE, EQ, NE, GT, GE = 0, 1, 2, 3, 4, 5
+
+
+def select(masks: np.ndarray, col: np.ndarray, cmp: int, thr: np.ndarray,
+           thr_ids: Optional[np.ndarray] = None):
+    """masks AND {world j : col[i] <cmp> thr[t_i][j]}.  thr: [n_thr, 64] of
+    col's dtype; thr_ids: [n] uint8/uint16/uint32 row -> t_i (None when
+    n_thr == 1).  Returns (selected masks uint64 [n], status)."""
+    masks = np.ascontiguousarray(masks, dtype=np.uint64)
+    col = np.ascontiguousarray(col)
+    thr = np.ascontiguousarray(thr, dtype=col.dtype).reshape(-1, 64)
+    tb = 0 if thr_ids is None else thr_ids.dtype.itemsize
+    t = None if thr_ids is None else np.ascontiguousarray(thr_ids)
+    out = np.zeros(masks.shape[0], dtype=np.uint64)
+    st = lib().orc_select(_p(masks), _p(col), _vtype(col), cmp, _p(thr), thr.shape[0], _p(t), tb,
+                          masks.shape[0], _p(out))
+    return out, st
 
 
 # -- hashing (Sec. 2 "SIMD-PAC-DB", Sec. 4.2 "PAC Hash") -----------------------

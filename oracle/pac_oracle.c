@@ -239,6 +239,56 @@ static void acc_emit(const acc_t *a, int vtype, int kind, void *out, size_t idx,
 }
 
 /* ====================================================================== */
+/* PAC selection (Sec. 4.2 "PAC Selection": the output bit j is set iff    */
+/* the row satisfies the predicate on world j's aggregate result and       */
+/* pu[j] = 1; Sec. 3.2: pac_select ANDs pu with 64 booleans, and the fused */
+/* pac_select_<cmp>(hash, col, list) compares col with each list entry).   */
+/* ====================================================================== */
+static int holds_i64(int64_t a, int64_t b, int cmp) {
+    switch (cmp) {
+    case ORC_CMP_LT: return a < b;
+    case ORC_CMP_LE: return a <= b;
+    case ORC_CMP_EQ: return a == b;
+    case ORC_CMP_NE: return a != b;
+    case ORC_CMP_GT: return a > b;
+    default: return a >= b;
+    }
+}
+
+static int holds_f64(double a, double b, int cmp) {
+    switch (cmp) {
+    case ORC_CMP_LT: return a < b;
+    case ORC_CMP_LE: return a <= b;
+    case ORC_CMP_EQ: return a == b;
+    case ORC_CMP_NE: return a != b;
+    case ORC_CMP_GT: return a > b;
+    default: return a >= b;
+    }
+}
+
+int orc_select(const uint64_t *masks, const void *col, int vtype, int cmp, const void *thr,
+               uint32_t n_thr, const void *thr_ids, int thr_id_bytes, size_t n, uint64_t *out) {
+    int status = 0;
+    for (size_t i = 0; i < n; i++) {
+        uint32_t t = n_thr == 1 ? 0 : gid_at(thr_ids, thr_id_bytes, i);
+        if (t >= n_thr) {
+            out[i] = 0;
+            status = 1;
+            continue;
+        }
+        uint64_t bits = 0;
+        for (int j = 0; j < 64; j++) {
+            size_t k = (size_t)t * 64 + (size_t)j;
+            int h = vtype == ORC_I64 ? holds_i64(((const int64_t *)col)[i], ((const int64_t *)thr)[k], cmp)
+                                     : holds_f64(fval_at(col, vtype, i), fval_at(thr, vtype, k), cmp);
+            if (h) bits |= 1ULL << j;
+        }
+        out[i] = masks[i] & bits;
+    }
+    return status;
+}
+
+/* ====================================================================== */
 /* Exact aggregation, row by row: r_j = agg{ e(t) : t in T, pu[j] = 1 }    */
 /* (Sec. 4.2 "PAC Aggregation"; the predicated 64-world update loop of     */
 /* PacCountUpdate in Sec. 1 and Sec. 5 "Naive"/predication).               */

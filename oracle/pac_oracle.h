@@ -52,6 +52,22 @@ void orc_hash_keys(const int64_t *keys, size_t n, uint64_t query_key, int mode,
 /* ---- counter-based generator used by the finalizer ----------------------- */
 uint64_t orc_rng_u64(uint64_t seed, uint64_t stream, uint64_t counter);
 
+/* ---- PAC selection (Sec. 4.2 "PAC Selection"; Sec. 3.2 pac_select and the
+ *      fused pac_select_<cmp>) ----------------------------------------------
+ * out[i] = masks[i] AND { bit j : col[i] <cmp> thr[t_i][j] }, the updated pu
+ * column of Sec. 4.2 compiler step (3).  col/thr: int64, float or double by
+ * vtype (int64 compares as integers, floats as doubles); cmp: ORC_CMP_*;
+ * thr: [n_thr][64]; t_i = thr_ids[i] (width thr_id_bytes) or 0 when n_thr is
+ * 1.  A row whose t_i >= n_thr selects no world and makes the status 1. */
+#define ORC_CMP_LT 0
+#define ORC_CMP_LE 1
+#define ORC_CMP_EQ 2
+#define ORC_CMP_NE 3
+#define ORC_CMP_GT 4
+#define ORC_CMP_GE 5
+int orc_select(const uint64_t *masks, const void *col, int vtype, int cmp, const void *thr,
+               uint32_t n_thr, const void *thr_ids, int thr_id_bytes, size_t n, uint64_t *out);
+
 /* ---- exact aggregation, row by row (Sec. 4.2 "PAC Aggregation") ---------- */
 /* values: int64 / float / double column selected by vtype (NULL for COUNT).
  * gids:   group id per row, width gid_bytes (1, 2, 4); NULL => one group.
