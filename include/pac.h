@@ -83,6 +83,11 @@ typedef enum { PAC_FIN_ADAPTIVE = 0, PAC_FIN_INDEPENDENT = 1 } pac_fin_mode;
  * computed world masks (uint64, e.g. from pac_hash_keys). */
 #define PAC_IN_KEYS 0u
 #define PAC_IN_MASKS 1u
+/* Or-ed into in_flags: a row whose world mask is 0 is a row of no group --
+ * it is skipped like a filtered row and not counted in meta's n_g (the
+ * paper's engine drops rows whose updated pu is 0 before the aggregate,
+ * Sec. 3.2 "Categorical Rewrites").  Not taken by pac_aggregate_noalloc. */
+#define PAC_IN_DROP_EMPTY 2u
 
 /* Per-cell flags written by pac_finalize. */
 #define PAC_F_NULL 1u      /* released NULL (Sec. 3.2 "NULLs") */
@@ -177,6 +182,58 @@ pac_status pac_aggregate(pac_ctx *ctx, const void *keys_or_masks, uint32_t in_fl
  * (n_specs <= PAC_MAX_SPECS; specs is a HOST array). */
 pac_status pac_aggregate_multi(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
                                int32_t n_specs, uint64_t *meta, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * 2b. pac_select  (Sec. 4.2 "PAC Selection" and compiler step (3); Sec. 3.2
+ *     "Categorical Rewrites": pac_select and the fused pac_select_<cmp>)
+ *
+ * A selection whose predicate depends on an aggregate computed per world
+ * (a correlated subquery, e.g. col < 0.2 * avg(col) of the row's part)
+ * updates the PU column: world j of row i is kept iff it was set and
+ *   col[i] <cmp> thr[t_i][j]
+ * holds.  thr is a [n_thr][64] table of per-world operands (typically a
+ * pac_aggregate result, one row per correlation key); t_i = thr_ids[i]
+ * picks the row's operand vector (thr_ids NULL and n_thr = 1: one vector
+ * for every row).
+ *   col, thr     [n] / [n_thr*64] of vtype (PAC_I64 compares as int64,
+ *                PAC_F32 / PAC_F64 as IEEE values: every comparison with a
+ *                NaN is false except PAC_CMP_NE)
+ *   thr_ids      [n] unsigned, width thr_id_bytes (1, 2 or 4), each < n_thr;
+ *                a row whose id is out of range keeps no world and the next
+ *                pac_sync_status returns PAC_E_INVALID
+ * ------------------------------------------------------------------------ */
+typedef enum {
+    PAC_CMP_LT = 0, /* col <  thr */
+    PAC_CMP_LE = 1, /* col <= thr */
+    PAC_CMP_EQ = 2, /* col == thr */
+    PAC_CMP_NE = 3, /* col != thr */
+    PAC_CMP_GT = 4, /* col >  thr */
+    PAC_CMP_GE = 5  /* col >= thr */
+} pac_cmp;
+
+typedef struct {
+    const void *col;      /* device [n], vtype */
+    int32_t vtype;        /* pac_dtype of col and thr */
+    int32_t cmp;          /* pac_cmp */
+    const void *thr;      /* device [n_thr*64], vtype, row-major [t][j] */
+    uint32_t n_thr;       /* >= 1 */
+    int32_t thr_id_bytes; /* 1, 2 or 4; ignored when thr_ids is NULL */
+    const void *thr_ids;  /* device [n] or NULL (then n_thr must be 1) */
+} pac_select_spec;
+
+/* masks_out[i] = mask_i AND {j : col[i] <cmp> thr[t_i][j]}, mask_i hashed
+ * from the keys (PAC_IN_KEYS) or read (PAC_IN_MASKS); in->group_ids and
+ * n_groups are not used.  masks_out: caller-owned device [n]. */
+pac_status pac_select(pac_ctx *ctx, const pac_input *in, const pac_select_spec *sel, uint64_t *masks_out,
+                      pac_stream stream);
+
+/* pac_aggregate_multi over the selected rows: the masks of pac_select, and
+ * rows whose selected mask is 0 dropped (PAC_IN_DROP_EMPTY).  The selected
+ * masks live in the context's workspace; nothing is written to the caller's
+ * columns. */
+pac_status pac_aggregate_select(pac_ctx *ctx, const pac_input *in, const pac_select_spec *sel,
+                                const pac_agg_spec *specs, int32_t n_specs, uint64_t *meta,
+                                pac_stream stream);
 
 /* ---------------------------------------------------------------------------
  * 3. pac_finalize  (Sec. 2 "PAC Privacy" and fused pac_noised_count;

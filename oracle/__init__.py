@@ -70,6 +70,8 @@ def lib() -> ctypes.CDLL:
             "orc_aggregate_brute": (i32, [vp, u64, i32, vp, i32, vp, i32, sz, u32, i32, vp]),
             "orc_approx_sum_i64": (i32, [vp, vp, vp, i32, sz, u32, vp]),
             "orc_approx_avg_i64": (i32, [vp, vp, vp, i32, sz, u32, vp]),
+            "orc_approx_sum_i64_ex": (i32, [vp, vp, vp, i32, sz, u32, vp, i32]),
+            "orc_approx_avg_i64_ex": (i32, [vp, vp, vp, i32, sz, u32, vp, i32]),
             "orc_approx_sum_f32state": (i32, [vp, vp, i32, vp, i32, sz, u32, vp]),
             "orc_release_scale": (dbl, [i32, i32]),
             "orc_finalize": (None, [vp, vp, u32, u32, vp, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
@@ -204,22 +206,25 @@ def aggregate_brute(keys: np.ndarray, qkey: int, mode: int, values: Optional[np.
     return out, st
 
 
-def approx_sum_i64(masks, values, gids, n_groups):
-    """Two-sided 25-level approximate integer SUM (Sec. 5 "Approximation")."""
+def approx_sum_i64(masks, values, gids, n_groups, drop_empty: bool = False):
+    """Two-sided 25-level approximate integer SUM (Sec. 5 "Approximation").
+    drop_empty: rows whose mask is 0 update nothing (filtered by a selection)."""
     masks = np.ascontiguousarray(masks, dtype=np.uint64)
     values = np.ascontiguousarray(values, dtype=np.int64)
     g, gb = _gid_args(gids)
     out = np.zeros((n_groups, 64), dtype=np.int64)
-    st = lib().orc_approx_sum_i64(_p(masks), _p(values), _p(g), gb, masks.shape[0], n_groups, _p(out))
+    st = lib().orc_approx_sum_i64_ex(_p(masks), _p(values), _p(g), gb, masks.shape[0], n_groups, _p(out),
+                                     int(drop_empty))
     return out, st
 
 
-def approx_avg_i64(masks, values, gids, n_groups):
+def approx_avg_i64(masks, values, gids, n_groups, drop_empty: bool = False):
     masks = np.ascontiguousarray(masks, dtype=np.uint64)
     values = np.ascontiguousarray(values, dtype=np.int64)
     g, gb = _gid_args(gids)
     out = np.zeros((n_groups, 64), dtype=np.float64)
-    st = lib().orc_approx_avg_i64(_p(masks), _p(values), _p(g), gb, masks.shape[0], n_groups, _p(out))
+    st = lib().orc_approx_avg_i64_ex(_p(masks), _p(values), _p(g), gb, masks.shape[0], n_groups, _p(out),
+                                     int(drop_empty))
     return out, st
 
 

@@ -471,9 +471,12 @@ static i128 apx_side_value(const apx_side *s, int j) {
 
 /* Runs the chunk schedule and leaves the combined per-group state in
  * `final_states` ([n_groups]).  Returns overflow as status 4. */
+/* drop_empty: a row whose mask is 0 is a row of no group (filtered out by a
+ * selection): it updates nothing, not even a level total, and the chunks
+ * stay over row positions. */
 static int apx_run(const uint64_t *masks, const int64_t *values,
                    const void *gids, int gid_bytes, size_t n, uint32_t n_groups,
-                   apx_state *final_states) {
+                   apx_state *final_states, int drop_empty) {
     int ovf = 0;
     size_t n_chunks = (n + ORC_APX_CHUNK - 1) / ORC_APX_CHUNK;
     if (n_chunks == 0) {
@@ -487,6 +490,7 @@ static int apx_run(const uint64_t *masks, const int64_t *values,
         size_t lo = c * ORC_APX_CHUNK, hi = lo + ORC_APX_CHUNK;
         if (hi > n) hi = n;
         for (size_t i = lo; i < hi; i++) {
+            if (drop_empty && masks[i] == 0) continue;
             uint32_t g = gid_at(gids, gid_bytes, i);
             apx_update(&states[c * n_groups + g], values[i], masks[i], &ovf);
         }
@@ -506,9 +510,15 @@ static int apx_run(const uint64_t *masks, const int64_t *values,
 int orc_approx_sum_i64(const uint64_t *masks, const int64_t *values,
                        const void *gids, int gid_bytes, size_t n,
                        uint32_t n_groups, int64_t *out) {
+    return orc_approx_sum_i64_ex(masks, values, gids, gid_bytes, n, n_groups, out, 0);
+}
+
+int orc_approx_sum_i64_ex(const uint64_t *masks, const int64_t *values,
+                          const void *gids, int gid_bytes, size_t n,
+                          uint32_t n_groups, int64_t *out, int drop_empty) {
     apx_state *fin = (apx_state *)calloc(n_groups ? n_groups : 1, sizeof(apx_state));
     if (!fin) return 2;
-    int status = apx_run(masks, values, gids, gid_bytes, n, n_groups, fin);
+    int status = apx_run(masks, values, gids, gid_bytes, n, n_groups, fin, drop_empty);
     for (uint32_t g = 0; g < n_groups; g++)
         for (int j = 0; j < 64; j++) {
             i128 v = apx_side_value(&fin[g].side[0], j) - apx_side_value(&fin[g].side[1], j);
@@ -521,11 +531,18 @@ int orc_approx_sum_i64(const uint64_t *masks, const int64_t *values,
 int orc_approx_avg_i64(const uint64_t *masks, const int64_t *values,
                        const void *gids, int gid_bytes, size_t n,
                        uint32_t n_groups, double *out) {
+    return orc_approx_avg_i64_ex(masks, values, gids, gid_bytes, n, n_groups, out, 0);
+}
+
+int orc_approx_avg_i64_ex(const uint64_t *masks, const int64_t *values,
+                          const void *gids, int gid_bytes, size_t n,
+                          uint32_t n_groups, double *out, int drop_empty) {
     apx_state *fin = (apx_state *)calloc(n_groups ? n_groups : 1, sizeof(apx_state));
     uint64_t *cnt = (uint64_t *)calloc(n_groups ? n_groups : 1, sizeof(uint64_t));
     if (!fin || !cnt) { free(fin); free(cnt); return 2; }
-    int status = apx_run(masks, values, gids, gid_bytes, n, n_groups, fin);
-    for (size_t i = 0; i < n; i++) cnt[gid_at(gids, gid_bytes, i)] += 1; /* exact update count */
+    int status = apx_run(masks, values, gids, gid_bytes, n, n_groups, fin, drop_empty);
+    for (size_t i = 0; i < n; i++) /* exact update count */
+        if (!(drop_empty && masks[i] == 0)) cnt[gid_at(gids, gid_bytes, i)] += 1;
     for (uint32_t g = 0; g < n_groups; g++)
         for (int j = 0; j < 64; j++) {
             i128 v = apx_side_value(&fin[g].side[0], j) - apx_side_value(&fin[g].side[1], j);

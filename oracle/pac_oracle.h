@@ -105,6 +105,15 @@ int orc_approx_avg_i64(const uint64_t *masks, const int64_t *values,
                        uint32_t n_groups, double *out);
 
 /* ---- approximate float SUM with FLOAT state (Sec. 5 "Approximation") ---- */
+/* The same two with drop_empty: rows whose mask is 0 (filtered out by a
+ * selection) update nothing and count in no group; chunks stay over row
+ * positions. */
+int orc_approx_sum_i64_ex(const uint64_t *masks, const int64_t *values,
+                          const void *gids, int gid_bytes, size_t n,
+                          uint32_t n_groups, int64_t *out, int drop_empty);
+int orc_approx_avg_i64_ex(const uint64_t *masks, const int64_t *values,
+                          const void *gids, int gid_bytes, size_t n,
+                          uint32_t n_groups, double *out, int drop_empty);
 int orc_approx_sum_f32state(const uint64_t *masks, const void *values,
                             int vtype, const void *gids, int gid_bytes,
                             size_t n, uint32_t n_groups, double *out);

@@ -21,14 +21,16 @@ PAC_I64, PAC_F32, PAC_F64 = range(3)
 PAC_EXACT, PAC_APPROX = 0, 1
 PAC_HASH_BALANCED, PAC_HASH_RAW = 0, 1
 PAC_FIN_ADAPTIVE, PAC_FIN_INDEPENDENT = 0, 1
-PAC_IN_KEYS, PAC_IN_MASKS = 0, 1
+PAC_IN_KEYS, PAC_IN_MASKS, PAC_IN_DROP_EMPTY = 0, 1, 2
+PAC_CMP_LT, PAC_CMP_LE, PAC_CMP_EQ, PAC_CMP_NE, PAC_CMP_GT, PAC_CMP_GE = range(6)
 PAC_F_NULL, PAC_F_DIVERSITY, PAC_F_ZEROVAR = 1, 2, 4
 PAC_MAX_SPECS = 16
 
 # every symbol the header declares
 EXPORTED = (
     "pac_create", "pac_destroy", "pac_last_error", "pac_status_string", "pac_sync_status",
-    "pac_query_key", "pac_hash_keys", "pac_aggregate", "pac_aggregate_multi", "pac_finalize",
+    "pac_query_key", "pac_hash_keys", "pac_aggregate", "pac_aggregate_multi", "pac_select",
+    "pac_aggregate_select", "pac_finalize",
     "pac_query_host", "pac_set_option", "pac_get_info", "pac_aggregate_noalloc",
     "pac_batch_plan", "pac_batch_launch", "pac_batch_free", "pac_batch_info", "pac_batch_run",
     "pac_serve_create", "pac_serve_submit", "pac_serve_poll", "pac_serve_wait", "pac_serve_stats",
@@ -47,6 +49,18 @@ class PacInput(ctypes.Structure):
         ("gid_bytes", ctypes.c_int32),
         ("n_groups", ctypes.c_uint32),
         ("n", ctypes.c_size_t),
+    ]
+
+
+class PacSelectSpec(ctypes.Structure):
+    _fields_ = [
+        ("col", ctypes.c_void_p),
+        ("vtype", ctypes.c_int32),
+        ("cmp", ctypes.c_int32),
+        ("thr", ctypes.c_void_p),
+        ("n_thr", ctypes.c_uint32),
+        ("thr_id_bytes", ctypes.c_int32),
+        ("thr_ids", ctypes.c_void_p),
     ]
 
 
@@ -115,6 +129,9 @@ def lib() -> ctypes.CDLL:
         "pac_hash_keys": (i32, [vp, vp, vp, sz, u64, i32, vp]),
         "pac_aggregate": (i32, [vp, vp, u32, u64, i32, vp, i32, vp, i32, sz, u32, i32, i32, vp, vp, vp]),
         "pac_aggregate_multi": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacAggSpec), i32, vp, vp]),
+        "pac_select": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacSelectSpec), vp, vp]),
+        "pac_aggregate_select": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacSelectSpec),
+                                       ctypes.POINTER(PacAggSpec), i32, vp, vp]),
         "pac_finalize": (i32, [vp, ctypes.POINTER(PacAggSpec), i32, u32, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
         "pac_query_host": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacAggSpec), i32, u64, dbl, i32,
                                  vp, vp, vp, vp]),
@@ -211,6 +228,21 @@ def make_specs(specs: Sequence[tuple]) -> ctypes.Array:
 def pac_aggregate_multi(ctx: int, inp: PacInput, specs: ctypes.Array, n_specs: int, meta: int,
                         stream: int = 0) -> None:
     _check(ctx, lib().pac_aggregate_multi(ctx, ctypes.byref(inp), specs, n_specs, meta or None, stream))
+
+
+def make_select(col: int, vtype: int, cmp: int, thr: int, n_thr: int = 1, thr_ids: int = 0,
+                thr_id_bytes: int = 0) -> PacSelectSpec:
+    return PacSelectSpec(col or None, vtype, cmp, thr or None, n_thr, thr_id_bytes, thr_ids or None)
+
+
+def pac_select(ctx: int, inp: PacInput, sel: PacSelectSpec, masks_out: int, stream: int = 0) -> None:
+    _check(ctx, lib().pac_select(ctx, ctypes.byref(inp), ctypes.byref(sel), masks_out or None, stream))
+
+
+def pac_aggregate_select(ctx: int, inp: PacInput, sel: PacSelectSpec, specs: ctypes.Array, n_specs: int,
+                         meta: int, stream: int = 0) -> None:
+    _check(ctx, lib().pac_aggregate_select(ctx, ctypes.byref(inp), ctypes.byref(sel), specs, n_specs,
+                                           meta or None, stream))
 
 
 def pac_finalize(ctx: int, specs: ctypes.Array, n_specs: int, n_groups: int, meta: int, seed: int,

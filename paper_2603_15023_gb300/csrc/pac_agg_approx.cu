@@ -124,7 +124,7 @@ __global__ void k_apx_chunks(const __grid_constant__ ApxParams p) {
         const uint64_t hi = min(p.in.n, lo + kApxChunk);
         for (uint64_t base = lo; base < hi; base += 32) {
             const uint64_t row = base + lane;
-            const bool valid = row < hi;
+            bool valid = row < hi;
             uint32_t gid = 0;
             long long v = 0;
             uint64_t mask = 0;
@@ -134,6 +134,7 @@ __global__ void k_apx_chunks(const __grid_constant__ ApxParams p) {
                 if (gid == g) {
                     v = row_i64(p.values, row);
                     mask = row_mask(p.in, row);
+                    if (drop_row(p.in, mask)) valid = false;
                 }
             }
             const uint32_t mine = __ballot_sync(kFull, valid && gid == g);

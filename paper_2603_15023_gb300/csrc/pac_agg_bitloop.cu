@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(256) k_bitloop_lowcard(const __grid_constant__
                 gid = 0;
             } else {
                 mask = row_mask(p.in, row);
+                if (drop_row(p.in, mask)) {
+                    valid = false;
+                    gid = 0;
+                }
             }
         }
 #pragma unroll
@@ -239,6 +243,10 @@ __global__ void __launch_bounds__(256) k_bitloop_atomic(const __grid_constant__ 
                 gid = 0;
             } else {
                 mask = row_mask(p.in, row);
+                if (drop_row(p.in, mask)) {
+                    valid = false;
+                    gid = 0;
+                }
             }
         }
         for (int s = 0; s < p.n_slots; s++) {

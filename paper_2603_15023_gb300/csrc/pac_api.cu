@@ -213,6 +213,43 @@ pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
     return PAC_OK;
 }
 
+pac_status check_select(pac_ctx *ctx, const pac_input *in, const pac_select_spec *sel) {
+    if (!sel) return fail(ctx, PAC_E_INVALID, "select spec is NULL");
+    if (in->n > 0 && !sel->col) return fail(ctx, PAC_E_INVALID, "select column is NULL");
+    if (sel->vtype != PAC_I64 && sel->vtype != PAC_F32 && sel->vtype != PAC_F64)
+        return fail(ctx, PAC_E_INVALID, "select vtype %d", sel->vtype);
+    if (sel->cmp < PAC_CMP_LT || sel->cmp > PAC_CMP_GE) return fail(ctx, PAC_E_INVALID, "select cmp %d", sel->cmp);
+    if (!sel->thr || sel->n_thr == 0) return fail(ctx, PAC_E_INVALID, "select operands missing");
+    if (!sel->thr_ids && sel->n_thr != 1)
+        return fail(ctx, PAC_E_INVALID, "n_thr %u operand vectors need thr_ids", sel->n_thr);
+    if (sel->thr_ids && sel->thr_id_bytes != 1 && sel->thr_id_bytes != 2 && sel->thr_id_bytes != 4)
+        return fail(ctx, PAC_E_INVALID, "thr_id_bytes %d", sel->thr_id_bytes);
+    return PAC_OK;
+}
+
+// Sorted operand tables, then the selected masks of every row into `out`
+// (two launches).  The tables go to the start of ctx->sws.
+pac_status run_select(pac_ctx *ctx, const pac_input *in, const pac_select_spec *sel, uint64_t *out,
+                      cudaStream_t stream) {
+    SelectDev d;
+    d.col = sel->col;
+    d.thr = sel->thr;
+    d.thr_ids = sel->thr_ids;
+    d.vtype = sel->vtype;
+    d.cmp = sel->cmp;
+    d.thr_id_bytes = sel->thr_ids ? sel->thr_id_bytes : 0;
+    d.n_thr = sel->n_thr;
+    SelTable *tabs = static_cast<SelTable *>(ctx->sws);
+    PAC_CUDA(ctx, launch_select_prep(d, tabs, stream));
+    const InputDev di = make_input(in);
+    PAC_CUDA(ctx, launch_select(di, d, tabs, out, ctx->d_status, ctx->n_sms, stream));
+    return PAC_OK;
+}
+
+size_t select_table_bytes(const pac_select_spec *sel) {
+    return align_up(static_cast<size_t>(sel->n_thr) * sizeof(SelTable), 256);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -251,6 +288,7 @@ void pac_destroy(pac_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->qws) cudaFree(ctx->qws);
+    if (ctx->sws) cudaFree(ctx->sws);
     if (ctx->pin_ev) {
         cudaEventSynchronize(ctx->pin_ev);
         cudaEventDestroy(ctx->pin_ev);
@@ -317,6 +355,56 @@ pac_status pac_aggregate_multi(pac_ctx *ctx, const pac_input *in, const pac_agg_
     st = bind_device(ctx);
     if (st != PAC_OK) return st;
     return aggregate_impl(ctx, in, specs, n_specs, meta, stream);
+}
+
+pac_status pac_select(pac_ctx *ctx, const pac_input *in, const pac_select_spec *sel, uint64_t *masks_out,
+                      pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    if (!in) return fail(ctx, PAC_E_INVALID, "input is NULL");
+    if (in->n > 0 && (!in->keys_or_masks || !masks_out)) return fail(ctx, PAC_E_INVALID, "keys/masks is NULL");
+    const uint32_t base_flags = in->in_flags & ~PAC_IN_DROP_EMPTY;
+    if (base_flags != PAC_IN_KEYS && base_flags != PAC_IN_MASKS)
+        return fail(ctx, PAC_E_INVALID, "in_flags %u", in->in_flags);
+    if (in->hash_mode != PAC_HASH_BALANCED && in->hash_mode != PAC_HASH_RAW)
+        return fail(ctx, PAC_E_INVALID, "hash_mode %d", in->hash_mode);
+    pac_status st = check_select(ctx, in, sel);
+    if (st != PAC_OK) return st;
+    st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    st = ensure_buffer(ctx, &ctx->sws, &ctx->sws_bytes, select_table_bytes(sel));
+    if (st != PAC_OK) return st;
+    st = run_select(ctx, in, sel, masks_out, stream);
+    if (st != PAC_OK) return st;
+    ctx->last_launches = in->n ? 2 : 1;
+    return PAC_OK;
+}
+
+pac_status pac_aggregate_select(pac_ctx *ctx, const pac_input *in, const pac_select_spec *sel,
+                                const pac_agg_spec *specs, int32_t n_specs, uint64_t *meta, pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    pac_status st = check_input(ctx, in);
+    if (st != PAC_OK) return st;
+    st = check_specs(ctx, in, specs, n_specs);
+    if (st != PAC_OK) return st;
+    if (n_specs == 0 && !meta) return fail(ctx, PAC_E_INVALID, "nothing to compute");
+    st = check_select(ctx, in, sel);
+    if (st != PAC_OK) return st;
+    st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    const size_t tb = select_table_bytes(sel);
+    st = ensure_buffer(ctx, &ctx->sws, &ctx->sws_bytes, tb + in->n * sizeof(uint64_t));
+    if (st != PAC_OK) return st;
+    uint64_t *masks = reinterpret_cast<uint64_t *>(static_cast<char *>(ctx->sws) + tb);
+    st = run_select(ctx, in, sel, masks, stream);
+    if (st != PAC_OK) return st;
+    // the selected rows: their masks, and rows left in no world dropped
+    pac_input ms = *in;
+    ms.keys_or_masks = masks;
+    ms.in_flags = PAC_IN_MASKS | PAC_IN_DROP_EMPTY;
+    st = aggregate_impl(ctx, &ms, specs, n_specs, meta, stream);
+    if (st != PAC_OK) return st;
+    ctx->last_launches += in->n ? 2 : 1;
+    return PAC_OK;
 }
 
 pac_status pac_aggregate(pac_ctx *ctx, const void *keys_or_masks, uint32_t in_flags, uint64_t query_key,

@@ -150,6 +150,10 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
         if (valid) {
             gid = __ldg(is.sgid + row);
             mask = __ldg(reinterpret_cast<const unsigned long long *>(is.smask) + row);
+            if (drop_row(is.in, mask)) {
+                valid = false;
+                gid = 0;
+            }
         }
 #pragma unroll
         for (int s = 0; s < NS; s++) {
@@ -174,6 +178,10 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
             gid = 0;
         } else {
             mask = row_mask(is.in, row);
+            if (drop_row(is.in, mask)) {
+                valid = false;
+                gid = 0;
+            }
         }
     }
 #pragma unroll
@@ -1029,7 +1037,7 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         BatchQueryDev &d = hq[i];
         d.in = make_input(&q.in);
         d.meta = q.meta;
-        d.bal = (q.in.in_flags == PAC_IN_KEYS && q.in.hash_mode == PAC_HASH_BALANCED) ? 1 : 0;
+        d.bal = ((q.in.in_flags & PAC_IN_MASKS) == 0 && q.in.hash_mode == PAC_HASH_BALANCED) ? 1 : 0;
         const uint32_t G = q.in.n_groups;
         const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
         const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);

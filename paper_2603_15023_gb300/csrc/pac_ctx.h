@@ -15,6 +15,8 @@ struct pac_ctx {
     size_t ws_bytes = 0;
     void *qws = nullptr;  // pac_query_host staging (inputs and outputs)
     size_t qws_bytes = 0;
+    void *sws = nullptr;  // selection: sorted operand tables, selected masks
+    size_t sws_bytes = 0;
     uint32_t *d_status = nullptr;
     void *pin = nullptr;  // pinned staging of per-bit engine descriptors
     size_t pin_bytes = 0;

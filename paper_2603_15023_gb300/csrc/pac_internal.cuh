@@ -90,6 +90,11 @@ __device__ __forceinline__ uint64_t row_mask(const InputDev &in, uint64_t i) {
     return keyed_world_mask(k, in.qkey, in.hash_mode);
 }
 
+// PAC_IN_DROP_EMPTY: a row whose world mask is 0 belongs to no group.
+__device__ __forceinline__ bool drop_row(const InputDev &in, uint64_t mask) {
+    return (in.in_flags & PAC_IN_DROP_EMPTY) != 0 && mask == 0;
+}
+
 __device__ __forceinline__ uint32_t row_gid(const InputDev &in, uint64_t i) {
     if (!in.gids) return 0;
     switch (in.gid_bytes) {

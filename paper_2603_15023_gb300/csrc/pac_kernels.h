@@ -49,6 +49,28 @@ cudaError_t launch_bitloop_merge(const BitloopParams &p, int n_parts, bool atomi
 cudaError_t launch_hash(const int64_t *keys, uint64_t *masks, size_t n, uint64_t qkey, int mode,
                         int n_sms, cudaStream_t s);
 
+// ---- PAC selection (Sec. 4.2 "PAC Selection") ---------------------------
+struct SelectDev {
+    const void *col;      // [n] of vtype
+    const void *thr;      // [n_thr][64] of vtype
+    const void *thr_ids;  // [n] or nullptr
+    int32_t vtype, cmp, thr_id_bytes;
+    uint32_t n_thr;
+};
+// One operand vector, sorted: key[0..n_valid) are the order-preserving keys
+// of its non-NaN operands, ascending; pm[k] = the worlds of the k smallest.
+struct SelTable {
+    unsigned long long key[64];
+    unsigned long long pm[65];
+    uint32_t n_valid;
+    uint32_t pad;
+};
+cudaError_t launch_select_prep(const SelectDev &sel, SelTable *tabs, cudaStream_t s);
+// out[i] = mask_i & {j : col[i] <cmp> thr[t_i][j]}; an out-of-range t_i keeps
+// no world and raises kStatusBadGroup.
+cudaError_t launch_select(const InputDev &in, const SelectDev &sel, const SelTable *tabs, uint64_t *out,
+                          uint32_t *status, int n_sms, cudaStream_t s);
+
 // ---- approximate integer SUM / AVG (Sec. 5 "Approximation") -------------
 constexpr int kApxLevels = 25;
 constexpr int kApxChunk = 4096;

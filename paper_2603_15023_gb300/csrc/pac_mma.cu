@@ -401,6 +401,10 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
             lo32[r] = keys_in ? hl : static_cast<uint32_t>(c.km);
             hi32[r] = keys_in ? hh : static_cast<uint32_t>(c.km >> 32);
         }
+        if (valid[r] && drop_row(p.in, (static_cast<uint64_t>(hi32[r]) << 32) | lo32[r])) {
+            gid[r] = 0xFFFFFFFFu;  // a row of no group: into the trash slot like a padding row
+            valid[r] = false;
+        }
         // OR of |v| in one's complement (v, or ~v for v < 0) bounds every
         // value's bit length; the sign bits say whether any is negative
         mag |= static_cast<unsigned long long>(c.v0 ^ (c.v0 >> 63));

@@ -32,7 +32,8 @@ inline bool spec_is_cascade(const pac_agg_spec &s) {
 inline pac_status check_input(pac_ctx *ctx, const pac_input *in) {
     if (!in) return fail(ctx, PAC_E_INVALID, "input is NULL");
     if (in->n > 0 && !in->keys_or_masks) return fail(ctx, PAC_E_INVALID, "keys_or_masks is NULL");
-    if (in->in_flags != PAC_IN_KEYS && in->in_flags != PAC_IN_MASKS)
+    const uint32_t base_flags = in->in_flags & ~PAC_IN_DROP_EMPTY;
+    if (base_flags != PAC_IN_KEYS && base_flags != PAC_IN_MASKS)
         return fail(ctx, PAC_E_INVALID, "in_flags %u", in->in_flags);
     if (in->hash_mode != PAC_HASH_BALANCED && in->hash_mode != PAC_HASH_RAW)
         return fail(ctx, PAC_E_INVALID, "hash_mode %d", in->hash_mode);

@@ -61,7 +61,7 @@ def test_create_without_gpu_fails_cleanly():
 
 
 def test_struct_layouts_match_the_header(tmp_path):
-    """The ctypes mirrors of pac_input / pac_agg_spec / pac_query have the C
+    """The ctypes mirrors of pac_input / pac_agg_spec / pac_query / pac_select_spec have the C
     header's sizes and field offsets (checked by compiling a probe with gcc)."""
     import ctypes
     import subprocess
@@ -74,6 +74,8 @@ def test_struct_layouts_match_the_header(tmp_path):
         '  printf("%zu %zu %zu\\n", sizeof(pac_agg_spec), offsetof(pac_agg_spec, values), offsetof(pac_agg_spec, out));\n'
         '  printf("%zu %zu %zu %zu\\n", sizeof(pac_query), offsetof(pac_query, specs), offsetof(pac_query, seed),'
         ' offsetof(pac_query, flags));\n'
+        '  printf("%zu %zu %zu %zu\\n", sizeof(pac_select_spec), offsetof(pac_select_spec, thr),'
+        ' offsetof(pac_select_spec, n_thr), offsetof(pac_select_spec, thr_ids));\n'
         '  return 0;\n}\n')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)])
@@ -82,3 +84,5 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert got[1] == [ctypes.sizeof(B.PacAggSpec), B.PacAggSpec.values.offset, B.PacAggSpec.out.offset]
     assert got[2] == [ctypes.sizeof(B.PacQuery), B.PacQuery.specs.offset, B.PacQuery.seed.offset,
                       B.PacQuery.flags.offset]
+    assert got[3] == [ctypes.sizeof(B.PacSelectSpec), B.PacSelectSpec.thr.offset, B.PacSelectSpec.n_thr.offset,
+                      B.PacSelectSpec.thr_ids.offset]
