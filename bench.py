@@ -57,6 +57,11 @@ WORKLOADS = {
     "highcard_100m": {"gid_bytes": 4, "n_cols": 1, "aggs": "count+sum", "finalize": "separate",
                       "in_bytes_per_row": 8 + 4 + 8, "flush_l2": False,
                       "describe": "count + sum, exact; release of the 2M cells timed separately"},
+    "select_60m": {"gid_bytes": 1, "n_cols": 4, "aggs": "count+sum+avg", "finalize": "adaptive",
+                   "in_bytes_per_row": 8 + 1 + 4 * 8, "flush_l2": False, "select": True,
+                   "describe": "lowcard_60m under a correlated PAC selection (Sec. 4.2): world j of a row kept "
+                               "iff value column 0 < world j's exact AVG of column 0 in the row's group; then "
+                               "count + 4 sum + 4 avg over the selected rows and adaptive release of 36 cells"},
     "serving": {"gid_bytes": 4, "n_cols": 3, "aggs": "count+sum+fsum+dsum", "finalize": "adaptive",
                 "in_bytes_per_row": 8 + 4 + 8 + 4 + 8, "flush_l2": False,
                 "describe": "Poisson arrivals, shapes of batch_4096, count + exact int64 sum + exact "
@@ -192,21 +197,36 @@ def cpu_oracle_sample(workload: str, rows: int, reps: int = 1, seed: int = 0):
     wl = _gen(workload, seed, rows)
     G = wl.n_groups
     qk = orc.query_key(seed)
+    thr = _select_operands(orc, wl, G, qk) if wcfg.get("select") else None
     t0 = time.perf_counter()
     for _ in range(reps):
-        _oracle_step(orc, wcfg, wl, G, qk)
+        _oracle_step(orc, wcfg, wl, G, qk, thr)
     dt = time.perf_counter() - t0
     return rows * reps / dt, dt
 
 
-def _oracle_step(orc, wcfg, wl, G, qk):
+def _select_operands(orc, wl, G, qk):
+    """Per-world operands of the select workloads: world j's exact AVG of
+    value column 0 in each group, truncated to int64 (computed once, outside
+    the timed step, like the subquery result a correlated selection reads)."""
     masks = orc.hash_keys(wl.keys, qk, orc.BALANCED)
-    res = [orc.aggregate(masks, None, wl.gids, G, orc.COUNT)]
-    for v in wl.values[:wcfg["n_cols"]]:
-        res.append(orc.aggregate(masks, v, wl.gids, G, orc.SUM))
+    avg, *_ = orc.aggregate(masks, wl.values[0], wl.gids, G, orc.AVG)
+    return np.trunc(avg).astype(np.int64)
+
+
+def _oracle_step(orc, wcfg, wl, G, qk, thr=None):
+    masks = orc.hash_keys(wl.keys, qk, orc.BALANCED)
+    gids, vals = wl.gids, wl.values[:wcfg["n_cols"]]
+    if thr is not None:
+        masks, _ = orc.select(masks, wl.values[0], orc.LT, thr, wl.gids)
+        keep = masks != 0
+        masks, gids, vals = masks[keep], gids[keep], [v[keep] for v in vals]
+    res = [orc.aggregate(masks, None, gids, G, orc.COUNT)]
+    for v in vals:
+        res.append(orc.aggregate(masks, v, gids, G, orc.SUM))
     if "avg" in wcfg["aggs"]:
-        for v in wl.values[:wcfg["n_cols"]]:
-            res.append(orc.aggregate(masks, v, wl.gids, G, orc.AVG))
+        for v in vals:
+            res.append(orc.aggregate(masks, v, gids, G, orc.AVG))
     if wcfg["finalize"] != "separate":
         y = np.stack([r[0].astype(np.float64) for r in res], axis=1)
         scales = [2.0] * (1 + wcfg["n_cols"]) + [1.0] * (len(res) - 1 - wcfg["n_cols"])
@@ -525,11 +545,27 @@ def run_ours(args):
     specs = B.make_specs(_spec_list(B, wcfg, [v.data_ptr() for v in d_vals], [o.data_ptr() for o in outs]))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda") if wcfg["flush_l2"] else None
     in_step_finalize = wcfg["finalize"] == "adaptive"
+    sel = None
+    if wcfg.get("select"):
+        # the correlated operands: world j's AVG of column 0 per group (a PAC
+        # aggregate, computed once outside the timed step), truncated to int64
+        d_avg = torch.empty((G, 64), dtype=torch.float64, device="cuda")
+        B.pac_aggregate_multi(ctx, inp, B.make_specs([(B.PAC_AVG, B.PAC_EXACT, B.PAC_I64, d_vals[0].data_ptr(),
+                                                         d_avg.data_ptr())]), 1, 0, sptr)
+        d_thr = torch.trunc(d_avg).to(torch.int64).contiguous()
+        sel = B.make_select(d_vals[0].data_ptr(), B.PAC_I64, B.PAC_CMP_LT, d_thr.data_ptr(), G,
+                            d_gids.data_ptr(), 1)
+
+    def aggregate(in_, sp):
+        if sel is not None:
+            B.pac_aggregate_select(ctx, in_, sel, sp, n_specs, meta.data_ptr(), sptr)
+        else:
+            B.pac_aggregate_multi(ctx, in_, sp, n_specs, meta.data_ptr(), sptr)
 
     def step(i, ev=None):
         if ev is not None:
             ev[0].record(stream)
-        B.pac_aggregate_multi(ctx, inp, specs, n_specs, meta.data_ptr(), sptr)
+        aggregate(inp, specs)
         k = B.pac_get_info(ctx, "last_launches")
         if ev is not None:
             ev[1].record(stream)
@@ -596,7 +632,38 @@ def run_ours(args):
 
     # end to end through the C ABI from pinned host memory
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and sel is not None:
+        # host columns -> device (pinned, on the step's stream), selection +
+        # aggregation + release through the C ABI, released cells -> host
+        h_keys = torch.from_numpy(wl.keys).pin_memory()
+        h_gids = torch.from_numpy(wl.gids).pin_memory()
+        h_vals = [torch.from_numpy(v).pin_memory() for v in wl.values[:C]]
+        h_noised = torch.empty(n_cells, dtype=torch.float64).pin_memory()
+        h_null = torch.empty(n_cells, dtype=torch.uint8).pin_memory()
+        h_flags = torch.empty(n_cells, dtype=torch.int32).pin_memory()
+
+        def e2e_step(i):
+            d_keys.copy_(h_keys, non_blocking=True)
+            d_gids.copy_(h_gids, non_blocking=True)
+            for d, h in zip(d_vals, h_vals):
+                d.copy_(h, non_blocking=True)
+            aggregate(inp, specs)
+            B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 100 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
+                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+            h_noised.copy_(noised, non_blocking=True)
+            h_null.copy_(is_null, non_blocking=True)
+            h_flags.copy_(flags, non_blocking=True)
+            torch.cuda.synchronize()
+
+        for i in range(2):
+            e2e_step(i)
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            e2e_step(2 + i)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": n * world / dt, "unit": "rows/s", "h2d_bytes_per_step": n * wcfg["in_bytes_per_row"],
+               "d2h_bytes_per_step": n_cells * (8 + 1 + 4), "ms_per_step": dt * 1e3}
+    elif args.e2e_steps > 0:
         h_keys = torch.from_numpy(wl.keys).pin_memory()
         h_gids = torch.from_numpy(wl.gids).pin_memory() if wl.gids is not None else None
         h_vals = [torch.from_numpy(v).pin_memory() for v in wl.values[:C]]
@@ -626,7 +693,8 @@ def run_ours(args):
     algo_bytes = n * wcfg["in_bytes_per_row"] + out_bytes
     achieved = algo_bytes / (agg_mean / 1e3) / 1e9
     kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
-              2: "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)",
+              2: ("k_select_prep + k_select + k_agg_mma + k_mma_finish (all launches of pac_aggregate_select)"
+                  if sel is not None else "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
               3: "k_part_hist + k_part_scan + k_part_scatter + k_batch_agg + k_batch_merge "
                  "(all launches of pac_aggregate_multi)"}.get(path, str(path))
     if rank == 0:

@@ -119,6 +119,7 @@ def small(seed: int, n: int, n_groups: int, n_keys: int, vdtype=np.int64,
 WORKLOADS = {
     "ungrouped_1m": ungrouped_1m,
     "lowcard_60m": lowcard_60m,
+    "select_60m": lowcard_60m,   # the same columns, read under a PAC selection
     "highcard_100m": highcard_100m,
 }
 

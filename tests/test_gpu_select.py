@@ -262,3 +262,45 @@ def test_drop_empty_on_caller_masks(ctx, path):
         np.testing.assert_array_equal(oc.cpu().numpy().view(np.uint64), rc)
         np.testing.assert_array_equal(osum.cpu().numpy(), rs)
         np.testing.assert_array_equal(meta.cpu().numpy().view(np.uint64)[:, 0], mn)
+
+
+def test_select_60m_full_size_sampled(ctx):
+    """The 60M-row select workload at full size, as the benchmark runs it:
+    operands = world j's exact AVG of column 0 per group (from the oracle, on
+    the first 1M rows, which keeps it to seconds), pac_aggregate_select on the
+    auto path (tensor cores); worlds 0, 21, 42 and 63 of COUNT and SUM
+    against the oracle's aggregate of the selected rows, meta n_g for every
+    group."""
+    from paper_2603_15023_gb300 import inputs
+    T = _t()
+    w = inputs.lowcard_60m(seed=0)
+    n, G = w.n, w.n_groups
+    qk = orc.query_key(0)
+    masks = orc.hash_keys(w.keys, qk, orc.BALANCED)
+    m1 = 1_000_000
+    avg, *_ = orc.aggregate(masks[:m1], w.values[0][:m1], w.gids[:m1], G, orc.AVG)
+    thr = np.trunc(avg).astype(np.int64)
+    sel_masks, st = orc.select(masks, w.values[0], orc.LT, thr, w.gids)
+    assert st == 0
+    keep = sel_masks != 0
+    dk, dg = dev(w.keys), dev(w.gids)
+    dv = [dev(v) for v in w.values]
+    dthr = dev(thr)
+    sel = B.make_select(dv[0].data_ptr(), B.PAC_I64, B.PAC_CMP_LT, dthr.data_ptr(), G, dg.data_ptr(), 1)
+    outs = [T.zeros((G, 64), dtype=T.int64, device="cuda") for _ in range(5)]
+    meta = T.zeros((G, 2), dtype=T.int64, device="cuda")
+    specs = [(B.PAC_COUNT, 0, B.PAC_I64, 0, outs[0].data_ptr())]
+    specs += [(B.PAC_SUM, 0, B.PAC_I64, dv[c].data_ptr(), outs[1 + c].data_ptr()) for c in range(4)]
+    inp = B.make_input(dk.data_ptr(), n, query_key=qk, group_ids=dg.data_ptr(), gid_bytes=1, n_groups=G)
+    B.pac_aggregate_select(ctx, inp, sel, B.make_specs(specs), 5, meta.data_ptr(), _stream())
+    assert B.pac_sync_status(ctx, _stream()) == B.PAC_OK
+    assert B.pac_get_info(ctx, "last_path") == 2
+    got = [o.cpu().numpy() for o in outs]
+    sm, sg = sel_masks[keep], w.gids[keep]
+    for j in (0, 21, 42, 63):
+        rc, st = orc.aggregate_world(sm, None, sg, G, orc.COUNT, j)
+        np.testing.assert_array_equal(got[0][:, j].view(np.uint64), rc)
+        for c in range(4):
+            rs, st = orc.aggregate_world(sm, w.values[c][keep], sg, G, orc.SUM, j)
+            np.testing.assert_array_equal(got[1 + c][:, j], rs)
+    np.testing.assert_array_equal(meta.cpu().numpy()[:, 0], np.bincount(sg, minlength=G))
