@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pac_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-COUNT, SUM, AVG, MIN, MAX = 0, 1, 2, 3, 4
+COUNT, SUM, AVG, MIN, MAX, LIFTED = 0, 1, 2, 3, 4, 5
 I64, F32, F64 = 0, 1, 2
 EXACT, APPROX = 0, 1
 BALANCED, RAW = 0, 1
@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
             "orc_release_scale": (dbl, [i32, i32]),
             "orc_finalize": (None, [vp, vp, u32, u32, vp, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
             "orc_select": (i32, [vp, vp, i32, i32, vp, u32, vp, i32, sz, vp]),
+            "orc_lift": (i32, [vp, vp, u32, u32, vp, i32, vp]),
+            "orc_filter": (None, [vp, u32, u64, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -125,6 +127,33 @@ def select(masks: np.ndarray, col: np.ndarray, cmp: int, thr: np.ndarray,
     st = lib().orc_select(_p(masks), _p(col), _vtype(col), cmp, _p(thr), thr.shape[0], _p(t), tb,
                           masks.shape[0], _p(out))
     return out, st
+
+
+# -- vector-lifted expressions and pac_filter (Sec. 4.2; Sec. 3.2) -------------
+(L_SPEC, L_CONST, L_ADD, L_SUB, L_MUL, L_DIV, L_NEG, L_ABS, L_MIN, L_MAX,
+ L_LT, L_LE, L_EQ, L_NE, L_GT, L_GE) = range(16)
+_LIFT_OP = np.dtype([("op", np.int32), ("arg", np.int32), ("c", np.float64)])
+
+
+def lift(y: np.ndarray, scales, prog):
+    """y: [n_groups, n_specs, 64] stored world results; scales: release scale
+    per spec; prog: (op, arg, c) tuples, postfix.  Returns (out [n_groups, 64],
+    status 0, or 1 for a malformed program)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    G, S = y.shape[0], y.shape[1]
+    sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float64))
+    p = np.array([tuple(t) for t in prog], dtype=_LIFT_OP)
+    out = np.zeros((G, 64), dtype=np.float64)
+    st = lib().orc_lift(_p(y), _p(sc), S, G, _p(p), len(prog), _p(out))
+    return out, st
+
+
+def pac_filter(b: np.ndarray, seed: int) -> np.ndarray:
+    """b: [n_groups, 64] lifted booleans (true = non-zero).  Returns keep uint8 [n_groups]."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    keep = np.zeros(b.shape[0], dtype=np.uint8)
+    lib().orc_filter(_p(b), b.shape[0], seed, _p(keep))
+    return keep
 
 
 # -- hashing (Sec. 2 "SIMD-PAC-DB", Sec. 4.2 "PAC Hash") -----------------------

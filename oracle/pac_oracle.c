@@ -289,6 +289,86 @@ int orc_select(const uint64_t *masks, const void *col, int vtype, int cmp, const
 }
 
 /* ====================================================================== */
+/* Vector-lifted expressions (Sec. 4.2 "Vector-lifted Expression, and      */
+/* Lambda Functions": the scalar expression applied world by world, scalar */
+/* operands broadcast to every world; Sec. 7 evaluates a ratio of two      */
+/* pac_sum vectors this way and noises it once).                           */
+/* ====================================================================== */
+static int lift_check(uint32_t n_specs, const orc_lift_op *prog, int n_ops) {
+    int depth = 0;
+    for (int k = 0; k < n_ops; k++) {
+        int op = prog[k].op;
+        if (op == ORC_LIFT_SPEC || op == ORC_LIFT_CONST) {
+            if (op == ORC_LIFT_SPEC && (prog[k].arg < 0 || (uint32_t)prog[k].arg >= n_specs)) return 1;
+            if (++depth > ORC_LIFT_DEPTH) return 1;
+        } else if (op == ORC_LIFT_NEG || op == ORC_LIFT_ABS) {
+            if (depth < 1) return 1;
+        } else if (op >= ORC_LIFT_ADD && op <= ORC_LIFT_GE) {
+            if (depth < 2) return 1;
+            depth--;
+        } else {
+            return 1;
+        }
+    }
+    return depth == 1 ? 0 : 1;
+}
+
+int orc_lift(const double *y, const double *scales, uint32_t n_specs, uint32_t n_groups,
+             const orc_lift_op *prog, int n_ops, double *out) {
+    if (lift_check(n_specs, prog, n_ops)) return 1;
+    for (uint32_t g = 0; g < n_groups; g++) {
+        for (int j = 0; j < 64; j++) {
+            double st[ORC_LIFT_DEPTH];
+            int sp = 0;
+            for (int k = 0; k < n_ops; k++) {
+                int op = prog[k].op;
+                if (op == ORC_LIFT_SPEC) {
+                    int s = prog[k].arg;
+                    st[sp++] = scales[s] * y[((size_t)g * n_specs + (size_t)s) * 64 + (size_t)j];
+                    continue;
+                }
+                if (op == ORC_LIFT_CONST) { st[sp++] = prog[k].c; continue; }
+                if (op == ORC_LIFT_NEG) { st[sp - 1] = -st[sp - 1]; continue; }
+                if (op == ORC_LIFT_ABS) { st[sp - 1] = fabs(st[sp - 1]); continue; }
+                double b = st[--sp], a = st[sp - 1], r;
+                switch (op) {
+                case ORC_LIFT_ADD: r = a + b; break;
+                case ORC_LIFT_SUB: r = a - b; break;
+                case ORC_LIFT_MUL: r = a * b; break;
+                case ORC_LIFT_DIV: r = a / b; break;
+                case ORC_LIFT_MIN: r = a < b ? a : b; break;
+                case ORC_LIFT_MAX: r = a > b ? a : b; break;
+                case ORC_LIFT_LT: r = a < b ? 1.0 : 0.0; break;
+                case ORC_LIFT_LE: r = a <= b ? 1.0 : 0.0; break;
+                case ORC_LIFT_EQ: r = a == b ? 1.0 : 0.0; break;
+                case ORC_LIFT_NE: r = a != b ? 1.0 : 0.0; break;
+                case ORC_LIFT_GT: r = a > b ? 1.0 : 0.0; break;
+                default: r = a >= b ? 1.0 : 0.0; break;
+                }
+                st[sp - 1] = r;
+            }
+            out[(size_t)g * 64 + (size_t)j] = st[0];
+        }
+    }
+    return 0;
+}
+
+/* ====================================================================== */
+/* pac_filter (Sec. 3.2 "Categorical Rewrites"): the fraction of the 64    */
+/* booleans that are true is the probability of a random yes/no choice.    */
+/* ====================================================================== */
+#define STREAM_FILTER 3
+
+void orc_filter(const double *b, uint32_t n_groups, uint64_t seed, uint8_t *keep) {
+    for (uint32_t g = 0; g < n_groups; g++) {
+        int t = 0;
+        for (int j = 0; j < 64; j++) t += b[(size_t)g * 64 + (size_t)j] != 0.0;
+        double u = orc_u01(orc_rng_u64(seed, STREAM_FILTER, g));
+        keep[g] = u < (double)t / 64.0 ? 1 : 0;
+    }
+}
+
+/* ====================================================================== */
 /* Exact aggregation, row by row: r_j = agg{ e(t) : t in T, pu[j] = 1 }    */
 /* (Sec. 4.2 "PAC Aggregation"; the predicated 64-world update loop of     */
 /* PacCountUpdate in Sec. 1 and Sec. 5 "Naive"/predication).               */

@@ -29,7 +29,7 @@ extern "C" {
 #endif
 
 /* ---- aggregate kinds / value types / variants (oracle-local numbering) --- */
-enum { ORC_COUNT = 0, ORC_SUM = 1, ORC_AVG = 2, ORC_MIN = 3, ORC_MAX = 4 };
+enum { ORC_COUNT = 0, ORC_SUM = 1, ORC_AVG = 2, ORC_MIN = 3, ORC_MAX = 4, ORC_LIFTED = 5 };
 enum { ORC_I64 = 0, ORC_F32 = 1, ORC_F64 = 2 };
 enum { ORC_EXACT = 0, ORC_APPROX = 1 };
 enum { ORC_BALANCED = 0, ORC_RAW = 1 };
@@ -67,6 +67,40 @@ uint64_t orc_rng_u64(uint64_t seed, uint64_t stream, uint64_t counter);
 #define ORC_CMP_GE 5
 int orc_select(const uint64_t *masks, const void *col, int vtype, int cmp, const void *thr,
                uint32_t n_thr, const void *thr_ids, int thr_id_bytes, size_t n, uint64_t *out);
+
+/* ---- vector-lifted expressions (Sec. 4.2 "Vector-lifted Expression, and
+ *      Lambda Functions": e applied world by world, scalars broadcast) -----
+ * y[n_groups][n_specs][64]: stored world results as doubles; scales: each
+ * spec's release scale; prog: postfix program over a stack of values:
+ *   SPEC k  push scales[k] * y[g][k][j]      CONST  push c
+ *   ADD SUB MUL DIV  pop b, pop a, push a op b (IEEE double)
+ *   MIN MAX  a < b ? a : b,  a > b ? a : b    NEG ABS  on the top value
+ *   LT LE EQ NE GT GE  push 1.0 if a <cmp> b else 0.0
+ * out[n_groups][64] = the program's single result per world.  Returns 1
+ * (out untouched) for a program that underflows, exceeds ORC_LIFT_DEPTH
+ * values, names a missing spec or does not end with one value. */
+enum {
+    ORC_LIFT_SPEC = 0, ORC_LIFT_CONST = 1, ORC_LIFT_ADD = 2, ORC_LIFT_SUB = 3, ORC_LIFT_MUL = 4,
+    ORC_LIFT_DIV = 5, ORC_LIFT_NEG = 6, ORC_LIFT_ABS = 7, ORC_LIFT_MIN = 8, ORC_LIFT_MAX = 9,
+    ORC_LIFT_LT = 10, ORC_LIFT_LE = 11, ORC_LIFT_EQ = 12, ORC_LIFT_NE = 13, ORC_LIFT_GT = 14,
+    ORC_LIFT_GE = 15
+};
+#define ORC_LIFT_DEPTH 8
+typedef struct {
+    int32_t op;
+    int32_t arg;
+    double c;
+} orc_lift_op;
+int orc_lift(const double *y, const double *scales, uint32_t n_specs, uint32_t n_groups,
+             const orc_lift_op *prog, int n_ops, double *out);
+
+/* ---- pac_filter (Sec. 3.2 "Categorical Rewrites": probabilistic filtering)
+ * b[n_groups][64]: a lifted boolean list per group (true = non-zero).  The
+ * fraction of true worlds is the probability of keeping the group's row:
+ * keep[g] = u_g < #true/64, u_g uniform in [0,1) from counter stream 3 of
+ * the seed at counter g.  It does not depend on the secret world and makes
+ * no posterior update. */
+void orc_filter(const double *b, uint32_t n_groups, uint64_t seed, uint8_t *keep);
 
 /* ---- exact aggregation, row by row (Sec. 4.2 "PAC Aggregation") ---------- */
 /* values: int64 / float / double column selected by vtype (NULL for COUNT).
