@@ -55,7 +55,9 @@ typedef enum {
 } pac_status;
 
 /* Aggregates of Sec. 4.2 "PAC Aggregation": agg in {sum,count,avg,min,max}. */
-typedef enum { PAC_COUNT = 0, PAC_SUM = 1, PAC_AVG = 2, PAC_MIN = 3, PAC_MAX = 4 } pac_kind;
+/* PAC_LIFTED (not an aggregate): a vector-lifted expression's [n_groups*64]
+ * double result from pac_lift, released by pac_finalize with scale 1. */
+typedef enum { PAC_COUNT = 0, PAC_SUM = 1, PAC_AVG = 2, PAC_MIN = 3, PAC_MAX = 4, PAC_LIFTED = 5 } pac_kind;
 
 /* Value column types. */
 typedef enum { PAC_I64 = 0, PAC_F32 = 1, PAC_F64 = 2 } pac_dtype;
@@ -262,6 +264,63 @@ pac_status pac_finalize(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs
                         uint32_t n_groups, const uint64_t *meta, uint64_t seed, double budget,
                         int32_t mode, double *noised, uint8_t *is_null, uint32_t *flags,
                         double *posterior, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * 3b. pac_lift  (Sec. 4.2 "Vector-lifted Expression, and Lambda Functions";
+ *     Sec. 7: a ratio of two pac_sum vectors evaluated world by world and
+ *     noised once)
+ *
+ * out[g][j] = e(x_1[g][j], ..., x_a[g][j]): a scalar expression applied to
+ * world j of every operand, scalar operands broadcast to all 64 worlds.  The
+ * expression is a postfix program over a stack of doubles (at most
+ * PAC_LIFT_DEPTH values, at most PAC_LIFT_MAX_OPS operations):
+ *   PAC_LIFT_SPEC k   push world j of specs[k] times its release scale
+ *                     (2 for COUNT and SUM, 1 otherwise: the estimate a
+ *                     pac_finalize release of that spec is centred on)
+ *   PAC_LIFT_CONST    push c
+ *   ADD SUB MUL DIV   pop b, pop a, push a op b (IEEE double: x/0 is +-inf
+ *                     or NaN)
+ *   MIN MAX           a < b ? a : b, a > b ? a : b
+ *   NEG ABS           on the top value
+ *   LT LE EQ NE GT GE push 1.0 if a <cmp> b else 0.0 (lifted booleans)
+ * specs: HOST array (kind, vtype, out) of the operand vectors (aggregate
+ * outputs, or earlier lifted vectors with kind PAC_LIFTED, vtype PAC_F64);
+ * out: device [n_groups*64] doubles.  A malformed program (underflow, more
+ * than one value left, a missing spec) is PAC_E_INVALID.  Release the result
+ * with pac_finalize and a spec {PAC_LIFTED, PAC_EXACT, PAC_F64, -, out},
+ * with the meta of the query it came from (its NULL accumulator).
+ * ------------------------------------------------------------------------ */
+typedef enum {
+    PAC_LIFT_SPEC = 0, PAC_LIFT_CONST = 1, PAC_LIFT_ADD = 2, PAC_LIFT_SUB = 3, PAC_LIFT_MUL = 4,
+    PAC_LIFT_DIV = 5, PAC_LIFT_NEG = 6, PAC_LIFT_ABS = 7, PAC_LIFT_MIN = 8, PAC_LIFT_MAX = 9,
+    PAC_LIFT_LT = 10, PAC_LIFT_LE = 11, PAC_LIFT_EQ = 12, PAC_LIFT_NE = 13, PAC_LIFT_GT = 14,
+    PAC_LIFT_GE = 15
+} pac_lift_opcode;
+
+typedef struct {
+    int32_t op;  /* pac_lift_opcode */
+    int32_t arg; /* spec index for PAC_LIFT_SPEC */
+    double c;    /* constant for PAC_LIFT_CONST */
+} pac_lift_op;
+
+#define PAC_LIFT_DEPTH 8
+#define PAC_LIFT_MAX_OPS 32
+
+pac_status pac_lift(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs, uint32_t n_groups,
+                    const pac_lift_op *prog, int32_t n_ops, double *out, pac_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * 3c. pac_filter  (Sec. 3.2 "Categorical Rewrites": probabilistic filtering
+ *     of a WHERE condition on aggregates)
+ *
+ * b: device [n_groups*64] lifted booleans (a world is true when non-zero).
+ * keep[g] = 1 with probability (#true worlds of g)/64: keep[g] = u_g <
+ * #true/64 with u_g uniform in [0,1) from the counter generator of `seed`
+ * (stream 3, counter g).  The choice does not depend on the secret world
+ * and updates no posterior.  keep: device [n_groups] bytes.
+ * ------------------------------------------------------------------------ */
+pac_status pac_filter(pac_ctx *ctx, const double *b, uint32_t n_groups, uint64_t seed, uint8_t *keep,
+                      pac_stream stream);
 
 /* ---------------------------------------------------------------------------
  * End-to-end query from HOST memory: copies the columns named by `in` and

@@ -16,7 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpac.so")
 
 PAC_OK, PAC_E_INVALID, PAC_E_NOMEM, PAC_E_CUDA, PAC_E_OVERFLOW, PAC_E_TIMEOUT, PAC_E_UNSUPPORTED = range(7)
-PAC_COUNT, PAC_SUM, PAC_AVG, PAC_MIN, PAC_MAX = range(5)
+PAC_COUNT, PAC_SUM, PAC_AVG, PAC_MIN, PAC_MAX, PAC_LIFTED = range(6)
+(PAC_LIFT_SPEC, PAC_LIFT_CONST, PAC_LIFT_ADD, PAC_LIFT_SUB, PAC_LIFT_MUL, PAC_LIFT_DIV, PAC_LIFT_NEG,
+ PAC_LIFT_ABS, PAC_LIFT_MIN, PAC_LIFT_MAX, PAC_LIFT_LT, PAC_LIFT_LE, PAC_LIFT_EQ, PAC_LIFT_NE, PAC_LIFT_GT,
+ PAC_LIFT_GE) = range(16)
 PAC_I64, PAC_F32, PAC_F64 = range(3)
 PAC_EXACT, PAC_APPROX = 0, 1
 PAC_HASH_BALANCED, PAC_HASH_RAW = 0, 1
@@ -30,7 +33,7 @@ PAC_MAX_SPECS = 16
 EXPORTED = (
     "pac_create", "pac_destroy", "pac_last_error", "pac_status_string", "pac_sync_status",
     "pac_query_key", "pac_hash_keys", "pac_aggregate", "pac_aggregate_multi", "pac_select",
-    "pac_aggregate_select", "pac_finalize",
+    "pac_aggregate_select", "pac_finalize", "pac_lift", "pac_filter",
     "pac_query_host", "pac_set_option", "pac_get_info", "pac_aggregate_noalloc",
     "pac_batch_plan", "pac_batch_launch", "pac_batch_free", "pac_batch_info", "pac_batch_run",
     "pac_serve_create", "pac_serve_submit", "pac_serve_poll", "pac_serve_wait", "pac_serve_stats",
@@ -62,6 +65,10 @@ class PacSelectSpec(ctypes.Structure):
         ("thr_id_bytes", ctypes.c_int32),
         ("thr_ids", ctypes.c_void_p),
     ]
+
+
+class PacLiftOp(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("arg", ctypes.c_int32), ("c", ctypes.c_double)]
 
 
 class PacAggSpec(ctypes.Structure):
@@ -130,6 +137,8 @@ def lib() -> ctypes.CDLL:
         "pac_aggregate": (i32, [vp, vp, u32, u64, i32, vp, i32, vp, i32, sz, u32, i32, i32, vp, vp, vp]),
         "pac_aggregate_multi": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacAggSpec), i32, vp, vp]),
         "pac_select": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacSelectSpec), vp, vp]),
+        "pac_lift": (i32, [vp, ctypes.POINTER(PacAggSpec), i32, u32, ctypes.POINTER(PacLiftOp), i32, vp, vp]),
+        "pac_filter": (i32, [vp, vp, u32, u64, vp, vp]),
         "pac_aggregate_select": (i32, [vp, ctypes.POINTER(PacInput), ctypes.POINTER(PacSelectSpec),
                                        ctypes.POINTER(PacAggSpec), i32, vp, vp]),
         "pac_finalize": (i32, [vp, ctypes.POINTER(PacAggSpec), i32, u32, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
@@ -243,6 +252,23 @@ def pac_aggregate_select(ctx: int, inp: PacInput, sel: PacSelectSpec, specs: cty
                          meta: int, stream: int = 0) -> None:
     _check(ctx, lib().pac_aggregate_select(ctx, ctypes.byref(inp), ctypes.byref(sel), specs, n_specs,
                                            meta or None, stream))
+
+
+def make_lift(prog: Sequence[tuple]) -> ctypes.Array:
+    """prog: (op, arg, c) tuples, postfix."""
+    arr = (PacLiftOp * max(len(prog), 1))()
+    for i, (op, arg, c) in enumerate(prog):
+        arr[i] = PacLiftOp(op, arg, c)
+    return arr
+
+
+def pac_lift(ctx: int, specs: ctypes.Array, n_specs: int, n_groups: int, prog: ctypes.Array, n_ops: int,
+             out: int, stream: int = 0) -> None:
+    _check(ctx, lib().pac_lift(ctx, specs, n_specs, n_groups, prog, n_ops, out or None, stream))
+
+
+def pac_filter(ctx: int, b: int, n_groups: int, seed: int, keep: int, stream: int = 0) -> None:
+    _check(ctx, lib().pac_filter(ctx, b or None, n_groups, seed, keep or None, stream))
 
 
 def pac_finalize(ctx: int, specs: ctypes.Array, n_specs: int, n_groups: int, meta: int, seed: int,

@@ -407,6 +407,68 @@ pac_status pac_aggregate_select(pac_ctx *ctx, const pac_input *in, const pac_sel
     return PAC_OK;
 }
 
+pac_status pac_lift(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs, uint32_t n_groups,
+                    const pac_lift_op *prog, int32_t n_ops, double *out, pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    if (n_specs < 0 || n_specs > PAC_MAX_SPECS || (n_specs > 0 && !specs))
+        return fail(ctx, PAC_E_INVALID, "n_specs %d", n_specs);
+    if (!prog || n_ops < 1 || n_ops > PAC_LIFT_MAX_OPS) return fail(ctx, PAC_E_INVALID, "n_ops %d", n_ops);
+    if (n_groups > 0 && !out) return fail(ctx, PAC_E_INVALID, "out is NULL");
+    LiftParams p{};
+    for (int i = 0; i < n_specs; i++) {
+        const pac_agg_spec &s = specs[i];
+        if (s.kind < PAC_COUNT || s.kind > PAC_LIFTED || (n_groups > 0 && !s.out))
+            return fail(ctx, PAC_E_INVALID, "spec %d", i);
+        if (s.kind == PAC_LIFTED && s.vtype != PAC_F64)
+            return fail(ctx, PAC_E_INVALID, "spec %d: a lifted vector is PAC_F64", i);
+        if (s.kind != PAC_COUNT && s.vtype != PAC_I64 && s.vtype != PAC_F32 && s.vtype != PAC_F64)
+            return fail(ctx, PAC_E_INVALID, "spec %d: vtype %d", i, s.vtype);
+        // stored as: COUNT uint64; AVG, lifted and float aggregates double; else int64
+        const int conv = s.kind == PAC_COUNT ? 0 : ((s.kind == PAC_AVG || s.vtype != PAC_I64) ? 2 : 1);
+        p.in[i] = s.out;
+        p.code[i] = conv | ((s.kind == PAC_COUNT || s.kind == PAC_SUM) ? 4 : 0);
+    }
+    int depth = 0;  // the program is checked on the host: the kernel trusts it
+    for (int k = 0; k < n_ops; k++) {
+        const int op = prog[k].op;
+        if (op == PAC_LIFT_SPEC || op == PAC_LIFT_CONST) {
+            if (op == PAC_LIFT_SPEC && (prog[k].arg < 0 || prog[k].arg >= n_specs))
+                return fail(ctx, PAC_E_INVALID, "op %d: no spec %d", k, prog[k].arg);
+            if (++depth > PAC_LIFT_DEPTH) return fail(ctx, PAC_E_INVALID, "op %d: deeper than %d", k, PAC_LIFT_DEPTH);
+        } else if (op == PAC_LIFT_NEG || op == PAC_LIFT_ABS) {
+            if (depth < 1) return fail(ctx, PAC_E_INVALID, "op %d: stack underflow", k);
+        } else if (op >= PAC_LIFT_ADD && op <= PAC_LIFT_GE) {
+            if (depth < 2) return fail(ctx, PAC_E_INVALID, "op %d: stack underflow", k);
+            depth--;
+        } else {
+            return fail(ctx, PAC_E_INVALID, "op %d: opcode %d", k, op);
+        }
+        p.prog[k].op = op;
+        p.prog[k].arg = prog[k].arg;
+        p.prog[k].c = prog[k].c;
+    }
+    if (depth != 1) return fail(ctx, PAC_E_INVALID, "the program leaves %d values", depth);
+    p.n_ops = n_ops;
+    p.n_groups = n_groups;
+    p.out = out;
+    pac_status st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    PAC_CUDA(ctx, launch_lift(p, ctx->n_sms, stream));
+    ctx->last_launches = n_groups ? 1 : 0;
+    return PAC_OK;
+}
+
+pac_status pac_filter(pac_ctx *ctx, const double *b, uint32_t n_groups, uint64_t seed, uint8_t *keep,
+                      pac_stream stream) {
+    if (!ctx) return PAC_E_INVALID;
+    if (n_groups > 0 && (!b || !keep)) return fail(ctx, PAC_E_INVALID, "b/keep is NULL");
+    pac_status st = bind_device(ctx);
+    if (st != PAC_OK) return st;
+    PAC_CUDA(ctx, launch_filter(b, n_groups, seed, keep, ctx->n_sms, stream));
+    ctx->last_launches = n_groups ? 1 : 0;
+    return PAC_OK;
+}
+
 pac_status pac_aggregate(pac_ctx *ctx, const void *keys_or_masks, uint32_t in_flags, uint64_t query_key,
                          int32_t hash_mode, const void *values, int32_t vtype, const void *group_ids,
                          int32_t gid_bytes, size_t n, uint32_t n_groups, int32_t kind, int32_t variant, void *out,
@@ -441,8 +503,10 @@ pac_status pac_finalize(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs
     if (mode != PAC_FIN_ADAPTIVE && mode != PAC_FIN_INDEPENDENT) return fail(ctx, PAC_E_INVALID, "mode %d", mode);
     FinParams p{};
     for (int i = 0; i < n_specs; i++) {
-        if (specs[i].kind < PAC_COUNT || specs[i].kind > PAC_MAX || !specs[i].out)
+        if (specs[i].kind < PAC_COUNT || specs[i].kind > PAC_LIFTED || !specs[i].out)
             return fail(ctx, PAC_E_INVALID, "spec %d", i);
+        if (specs[i].kind == PAC_LIFTED && specs[i].vtype != PAC_F64)
+            return fail(ctx, PAC_E_INVALID, "spec %d: a lifted vector is PAC_F64", i);
         p.spec[i].kind = specs[i].kind;
         p.spec[i].vtype = specs[i].kind == PAC_COUNT ? PAC_I64 : specs[i].vtype;
         p.spec[i].variant = specs[i].variant;

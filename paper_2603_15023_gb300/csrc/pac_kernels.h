@@ -119,6 +119,22 @@ struct FinParams {
     uint32_t *flags;
     double *posterior;
 };
+// ---- vector-lifted expressions and pac_filter (Sec. 4.2; Sec. 3.2) -------
+struct LiftOp {
+    int32_t op, arg;
+    double c;
+};
+struct LiftParams {
+    const void *in[kMaxSpecs];  // operand vectors [n_groups*64]
+    int32_t code[kMaxSpecs];    // bits 0-1: 0 uint64, 1 int64, 2 double; bit 2: scale 2
+    LiftOp prog[32];
+    int32_t n_ops;
+    uint32_t n_groups;
+    double *out;
+};
+cudaError_t launch_lift(const LiftParams &p, int n_sms, cudaStream_t s);
+cudaError_t launch_filter(const double *b, uint32_t n_groups, uint64_t seed, uint8_t *keep, int n_sms,
+                          cudaStream_t s);
 cudaError_t launch_finalize(const FinParams &p, cudaStream_t s);
 // One warp per query: d_params[n] device array of per-query parameters.
 cudaError_t launch_finalize_batch(const FinParams *d_params, int n, cudaStream_t s);
