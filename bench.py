@@ -62,6 +62,11 @@ WORKLOADS = {
                    "describe": "lowcard_60m under a correlated PAC selection (Sec. 4.2): world j of a row kept "
                                "iff value column 0 < world j's exact AVG of column 0 in the row's group; then "
                                "count + 4 sum + 4 avg over the selected rows and adaptive release of 36 cells"},
+    "ratio_100m": {"gid_bytes": 4, "n_cols": 2, "aggs": "count+sum", "finalize": "separate", "lift": True,
+                   "in_bytes_per_row": 8 + 4 + 2 * 8, "flush_l2": False,
+                   "describe": "highcard shape, count + exact sum of the chosen nation's sales and of all "
+                               "sales, market share lifted world by world (Sec. 4.2, Sec. 7: 100 * s1 / s2 over "
+                               "1M groups x 64 worlds); the single release of the 1M shares timed separately"},
     "serving": {"gid_bytes": 4, "n_cols": 3, "aggs": "count+sum+fsum+dsum", "finalize": "adaptive",
                 "in_bytes_per_row": 8 + 4 + 8 + 4 + 8, "flush_l2": False,
                 "describe": "Poisson arrivals, shapes of batch_4096, count + exact int64 sum + exact "
@@ -205,6 +210,11 @@ def cpu_oracle_sample(workload: str, rows: int, reps: int = 1, seed: int = 0):
     return rows * reps / dt, dt
 
 
+def RATIO_PROG_ORC(orc):
+    """100 * spec 0 / spec 1, the market share of the ratio workload."""
+    return [(orc.L_CONST, 0, 100.0), (orc.L_SPEC, 0, 0), (orc.L_MUL, 0, 0), (orc.L_SPEC, 1, 0), (orc.L_DIV, 0, 0)]
+
+
 def _select_operands(orc, wl, G, qk):
     """Per-world operands of the select workloads: world j's exact AVG of
     value column 0 in each group, truncated to int64 (computed once, outside
@@ -227,6 +237,9 @@ def _oracle_step(orc, wcfg, wl, G, qk, thr=None):
     if "avg" in wcfg["aggs"]:
         for v in vals:
             res.append(orc.aggregate(masks, v, gids, G, orc.AVG))
+    if wcfg.get("lift"):
+        y = np.stack([r[0].astype(np.float64) for r in res[1:3]], axis=1)
+        orc.lift(y, [2.0, 2.0], RATIO_PROG_ORC(orc))
     if wcfg["finalize"] != "separate":
         y = np.stack([r[0].astype(np.float64) for r in res], axis=1)
         scales = [2.0] * (1 + wcfg["n_cols"]) + [1.0] * (len(res) - 1 - wcfg["n_cols"])
@@ -556,6 +569,17 @@ def run_ours(args):
         sel = B.make_select(d_vals[0].data_ptr(), B.PAC_I64, B.PAC_CMP_LT, d_thr.data_ptr(), G,
                             d_gids.data_ptr(), 1)
 
+    lift = None
+    if wcfg.get("lift"):
+        # the market share 100 * s1 / s2, world by world, from the two SUM outputs
+        share = torch.empty((G, 64), dtype=torch.float64, device="cuda")
+        lift_specs = B.make_specs(_spec_list(B, wcfg, [v.data_ptr() for v in d_vals],
+                                             [o.data_ptr() for o in outs])[1:3])
+        prog = [(B.PAC_LIFT_CONST, 0, 100.0), (B.PAC_LIFT_SPEC, 0, 0), (B.PAC_LIFT_MUL, 0, 0),
+                (B.PAC_LIFT_SPEC, 1, 0), (B.PAC_LIFT_DIV, 0, 0)]
+        lift = (lift_specs, B.make_lift(prog), len(prog), share)
+        lift_ms = []
+
     def aggregate(in_, sp):
         if sel is not None:
             B.pac_aggregate_select(ctx, in_, sel, sp, n_specs, meta.data_ptr(), sptr)
@@ -569,6 +593,15 @@ def run_ours(args):
         k = B.pac_get_info(ctx, "last_launches")
         if ev is not None:
             ev[1].record(stream)
+        if lift is not None:
+            le = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) if ev else None
+            if le:
+                le[0].record(stream)
+            B.pac_lift(ctx, lift[0], 2, G, lift[1], lift[2], lift[3].data_ptr(), sptr)
+            if le:
+                le[1].record(stream)
+                lift_ms.append(le)
+            k += B.pac_get_info(ctx, "last_launches")
         if in_step_finalize:
             B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 1000 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
                            noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
@@ -624,23 +657,35 @@ def run_ours(args):
     if not in_step_finalize:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 5, 1.0 / 128, B.PAC_FIN_INDEPENDENT,
-                       noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+        if lift is not None:
+            rel = B.make_specs([(B.PAC_LIFTED, B.PAC_EXACT, B.PAC_F64, 0, lift[3].data_ptr())])
+            B.pac_finalize(ctx, rel, 1, G, meta.data_ptr(), 5, 1.0 / 128, B.PAC_FIN_INDEPENDENT,
+                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+        else:
+            B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 5, 1.0 / 128, B.PAC_FIN_INDEPENDENT,
+                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
         e1.record(stream)
         torch.cuda.synchronize()
         fin_ms = e0.elapsed_time(e1)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
-    if args.e2e_steps > 0 and sel is not None:
-        # host columns -> device (pinned, on the step's stream), selection +
-        # aggregation + release through the C ABI, released cells -> host
+    if args.e2e_steps > 0 and (sel is not None or lift is not None):
+        # host columns -> device (pinned, on the step's stream), selection /
+        # aggregation / lifting and the release through the C ABI, released
+        # cells -> host
         h_keys = torch.from_numpy(wl.keys).pin_memory()
         h_gids = torch.from_numpy(wl.gids).pin_memory()
         h_vals = [torch.from_numpy(v).pin_memory() for v in wl.values[:C]]
-        h_noised = torch.empty(n_cells, dtype=torch.float64).pin_memory()
-        h_null = torch.empty(n_cells, dtype=torch.uint8).pin_memory()
-        h_flags = torch.empty(n_cells, dtype=torch.int32).pin_memory()
+        rel_specs, rel_n = specs, n_specs
+        if lift is not None:
+            rel_specs = B.make_specs([(B.PAC_LIFTED, B.PAC_EXACT, B.PAC_F64, 0, lift[3].data_ptr())])
+            rel_n = 1
+        rel_cells = G * rel_n
+        h_noised = torch.empty(rel_cells, dtype=torch.float64).pin_memory()
+        h_null = torch.empty(rel_cells, dtype=torch.uint8).pin_memory()
+        h_flags = torch.empty(rel_cells, dtype=torch.int32).pin_memory()
+        rel_mode = B.PAC_FIN_ADAPTIVE if in_step_finalize else B.PAC_FIN_INDEPENDENT
 
         def e2e_step(i):
             d_keys.copy_(h_keys, non_blocking=True)
@@ -648,11 +693,13 @@ def run_ours(args):
             for d, h in zip(d_vals, h_vals):
                 d.copy_(h, non_blocking=True)
             aggregate(inp, specs)
-            B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 100 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
+            if lift is not None:
+                B.pac_lift(ctx, lift[0], 2, G, lift[1], lift[2], lift[3].data_ptr(), sptr)
+            B.pac_finalize(ctx, rel_specs, rel_n, G, meta.data_ptr(), 100 + i, 1.0 / 128, rel_mode,
                            noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
-            h_noised.copy_(noised, non_blocking=True)
-            h_null.copy_(is_null, non_blocking=True)
-            h_flags.copy_(flags, non_blocking=True)
+            h_noised.copy_(noised[:rel_cells], non_blocking=True)
+            h_null.copy_(is_null[:rel_cells], non_blocking=True)
+            h_flags.copy_(flags[:rel_cells], non_blocking=True)
             torch.cuda.synchronize()
 
         for i in range(2):
@@ -662,7 +709,7 @@ def run_ours(args):
             e2e_step(2 + i)
         dt = (time.perf_counter() - t0) / args.e2e_steps
         e2e = {"value": n * world / dt, "unit": "rows/s", "h2d_bytes_per_step": n * wcfg["in_bytes_per_row"],
-               "d2h_bytes_per_step": n_cells * (8 + 1 + 4), "ms_per_step": dt * 1e3}
+               "d2h_bytes_per_step": rel_cells * (8 + 1 + 4), "ms_per_step": dt * 1e3}
     elif args.e2e_steps > 0:
         h_keys = torch.from_numpy(wl.keys).pin_memory()
         h_gids = torch.from_numpy(wl.gids).pin_memory() if wl.gids is not None else None
@@ -728,6 +775,11 @@ def run_ours(args):
         }
         if fin_ms is not None:
             line["finalize_ms"] = fin_ms
+        if lift is not None and lift_ms:
+            lms = statistics.mean(a.elapsed_time(b) for a, b in lift_ms)
+            lb = G * 64 * (8 + 8 + 8)   # two operand vectors in, the lifted vector out
+            line["lift"] = {"kernel": "k_lift", "ms": lms, "bytes": lb, "achieved_gbs": lb / (lms / 1e3) / 1e9,
+                            "frac": lb / (lms / 1e3) / 1e9 / peak, "cells": G * 64}
         print(json.dumps(line))
     B.pac_destroy(ctx)
     if world > 1:

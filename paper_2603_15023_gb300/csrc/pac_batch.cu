@@ -126,16 +126,17 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 //   SIG 2: {int64 SUM, float SUM}
 //   SIG 3: {int64 SUM, float SUM, float SUM}
 //   SIG 4: {float SUM}
+//   SIG 5: {int64 SUM, int64 SUM}          (two sums, e.g. a lifted ratio)
 template <int SIG>
 __device__ __forceinline__ int op_of(const ItemShared &is, int s) {
-    if (SIG == 1) return OP_ISUM;
+    if (SIG == 1 || SIG == 5) return OP_ISUM;
     if (SIG == 2 || SIG == 3) return s == 0 ? OP_ISUM : OP_FSUM_COMP;
     if (SIG == 4) return OP_FSUM_COMP;
     return is.slot[s].op;
 }
 template <int SIG>
 __device__ __forceinline__ int nslots_of(const ItemShared &is) {
-    return SIG == 1 ? 1 : SIG == 2 ? 2 : SIG == 3 ? 3 : SIG == 4 ? 1 : is.n_slots;
+    return SIG == 1 ? 1 : SIG == 2 ? 2 : SIG == 3 ? 3 : SIG == 4 ? 1 : SIG == 5 ? 2 : is.n_slots;
 }
 
 // Loads row `row`'s group, mask and slot values; invalid rows get valid=false.
@@ -954,7 +955,7 @@ cudaError_t batch_kernel_setup(size_t smem, int *blocks_per_sm) {
 }
 
 // The kernel variant of a plan: (NS, SIG) pairs instantiated below.
-#define PAC_BATCH_VARIANTS(X) X(1, 0) X(2, 0) X(4, 0) X(kMaxSpecs, 0) X(1, 1) X(2, 2) X(4, 3) X(1, 4)
+#define PAC_BATCH_VARIANTS(X) X(1, 0) X(2, 0) X(4, 0) X(kMaxSpecs, 0) X(1, 1) X(2, 2) X(4, 3) X(1, 4) X(2, 5)
 
 template <typename T>
 T *img_at(pac_batch *b, size_t off) {
@@ -1018,13 +1019,14 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         if (d.n_slots == 2 && op(0) == OP_ISUM && op(1) == OP_FSUM_COMP) return 2;
         if (d.n_slots == 3 && op(0) == OP_ISUM && op(1) == OP_FSUM_COMP && op(2) == OP_FSUM_COMP) return 3;
         if (d.n_slots == 1 && op(0) == OP_FSUM_COMP) return 4;
+        if (d.n_slots == 2 && op(0) == OP_ISUM && op(1) == OP_ISUM) return 5;
         return 0;
     };
     b->sig = n_queries > 0 ? sig_of(hq[0]) : 0;
     for (int i = 1; i < n_queries && b->sig; i++)
         if (sig_of(hq[i]) != b->sig) b->sig = 0;
     if (b->sig == 1 || b->sig == 4) b->ns = 1;
-    if (b->sig == 2) b->ns = 2;
+    if (b->sig == 2 || b->sig == 5) b->ns = 2;
     if (b->sig == 3) b->ns = 4;
     // device block: [zeroed scratch | partials | image]; offsets relative to it
     size_t zero_off = 256;  // the item counter lives at offset 0

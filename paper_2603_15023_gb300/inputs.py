@@ -101,6 +101,19 @@ def highcard_100m(seed: int = 0, n: int = 100_000_000, n_groups: int = 1_000_000
                     {"n_keys": n_keys, "zipf_s": 1.1})
 
 
+def ratio_100m(seed: int = 0, n: int = 100_000_000, n_groups: int = 1_000_000,
+               n_keys: int = 10_000_000) -> Workload:
+    """The highcard shape with the two sums of a market-share ratio (the
+    Sec. 7 TPC-H Q08 form): v0 = sales where the row's nation is the chosen
+    one (a quarter of the rows) else 0, v1 = sales."""
+    w = highcard_100m(seed=seed, n=n, n_groups=n_groups, n_keys=n_keys)
+    sales = w.values[0]
+    chosen = _rng(seed, 3).random(n) < 0.25
+    share_num = np.where(chosen, sales, 0).astype(np.int64)
+    return Workload("ratio_100m", n, n_groups, w.keys, w.gids, [share_num, sales],
+                    {"n_keys": n_keys, "zipf_s": 1.1, "chosen_fraction": 0.25})
+
+
 def small(seed: int, n: int, n_groups: int, n_keys: int, vdtype=np.int64,
           vlo: int = -1000, vhi: int = 1000, gid_dtype=np.int32) -> Workload:
     """Generic small case for the tests: uniform keys, uniform groups, values
@@ -120,6 +133,7 @@ WORKLOADS = {
     "ungrouped_1m": ungrouped_1m,
     "lowcard_60m": lowcard_60m,
     "select_60m": lowcard_60m,   # the same columns, read under a PAC selection
+    "ratio_100m": ratio_100m,
     "highcard_100m": highcard_100m,
 }
 

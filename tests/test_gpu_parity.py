@@ -301,13 +301,14 @@ def test_forced_per_bit_paths(ctx, path, mode, G, gdt, vdtype):
     np.testing.assert_array_equal(meta[:, 1], mo)
 
 
-@pytest.mark.parametrize("only_sum", [False, True])
+@pytest.mark.parametrize("only_sum", [False, True, "two"])
 @pytest.mark.parametrize("dist", ["narrow", "wide", "w45", "negative", "zeros", "short_runs"])
 def test_engine_int_sums_bit_sliced_and_looped(ctx, dist, only_sum):
     """Int64 SUM on the engine: non-negative values in runs at least as long
     as their bit length take the bit-sliced form (planes of the low and high
     words), short runs and negative values the broadcast loop; all exact.
-    only_sum: COUNT + SUM alone (compile-time slot operations)."""
+    only_sum: COUNT + SUM alone, "two": COUNT + two SUMs (both with
+    compile-time slot operations)."""
     n, G = 200_000, 3
     r = np.random.default_rng(len(dist))
     keys = r.integers(0, 50_000, n).astype(np.int64)
@@ -320,7 +321,9 @@ def test_engine_int_sums_bit_sliced_and_looped(ctx, dist, only_sum):
     qk = orc.query_key(99)
     masks = orc.hash_keys(keys, qk, orc.BALANCED)
     specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals)]
-    if not only_sum:
+    if only_sum == "two":
+        specs.append((B.PAC_SUM, 0, (vals // 3).astype(np.int64)))
+    elif not only_sum:
         specs += [(B.PAC_AVG, 0, vals), (B.PAC_MIN, 0, vals)]
     got, meta, st = ctx.aggregate(keys, gids, G, specs, qkey=qk, path=3)
     assert st == B.PAC_OK and ctx.last_path == 3
