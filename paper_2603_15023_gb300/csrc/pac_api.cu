@@ -106,8 +106,15 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
     q.n_specs = k;
     q.fin_mode = -1;
     q.meta = meta;
+    // one query: work items small enough that every SM gets a few (a
+    // power of two from 4K rows up to the default size)
+    BatchConfig cfg = kBatchDefault;
+    const uint64_t per_slot = in->n / (static_cast<uint64_t>(ctx->n_sms) * 4);
+    uint32_t rows = 4096;
+    while (rows < per_slot && rows < cfg.item_rows) rows <<= 1;
+    cfg.item_rows = rows;
     pac_batch *b = nullptr;
-    pac_status st = plan_build(ctx, &q, 1, kBatchDefault, &b);
+    pac_status st = plan_build(ctx, &q, 1, cfg, &b);
     if (st != PAC_OK) return st;
     st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, b->device_bytes);
     if (st == PAC_OK && ctx->pin_bytes < b->image.size()) {
