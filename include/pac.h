@@ -108,7 +108,8 @@ const char *pac_status_string(pac_status s);
 
 /* Synchronises `stream`, returns (and clears) the device status word:
  * PAC_OK, PAC_E_OVERFLOW, PAC_E_TIMEOUT, or PAC_E_INVALID when a group id
- * was >= n_groups (such rows are skipped, never written out of bounds). */
+ * was >= n_groups or a selection's operand id was >= n_thr (such rows are
+ * skipped / keep no world, never read or written out of bounds). */
 pac_status pac_sync_status(pac_ctx *ctx, pac_stream stream);
 
 /* Host-only: the per-query hash key K (Sec. 4.2: drawn independently per
