@@ -561,18 +561,49 @@ pac_status pac_query_host(pac_ctx *ctx, const pac_input *in_h, const pac_agg_spe
     if (st != PAC_OK) return st;
     Carver cv(ctx->qws);
     pac_input in = *in_h;
+    // A query the tensor-core path serves alone reads each input byte once:
+    // when every column is pinned host memory, that kernel reads the columns
+    // where they are (the same bytes cross the host link, without a staging
+    // copy in front of the aggregation).
+    bool direct = n > 0 && (ctx->opt_agg_path == 0 || ctx->opt_agg_path == 2) && mma_supported(in_h, specs_h, n_specs);
+    for (int i = 0; i < n_specs && direct; i++) direct = !spec_is_cascade(specs_h[i]);
+    auto pinned = [](const void *p) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return static_cast<const void *>(nullptr);
+        }
+        return a.type == cudaMemoryTypeHost ? static_cast<const void *>(a.devicePointer) : nullptr;
+    };
+    pac_agg_spec direct_specs[PAC_MAX_SPECS];
+    if (direct) {
+        const void *k = pinned(in_h->keys_or_masks);
+        const void *g = in_h->group_ids ? pinned(in_h->group_ids) : nullptr;
+        direct = k && (!in_h->group_ids || g);
+        for (int i = 0; i < n_specs && direct; i++) {
+            direct_specs[i] = specs_h[i];
+            if (specs_h[i].kind != PAC_COUNT) {
+                direct_specs[i].values = pinned(specs_h[i].values);
+                direct = direct_specs[i].values != nullptr;
+            }
+        }
+        if (direct) {
+            in.keys_or_masks = k;
+            in.group_ids = g;
+        }
+    }
     void *d_keys = cv.take(n * 8);
-    if (n) PAC_CUDA(ctx, cudaMemcpyAsync(d_keys, in_h->keys_or_masks, n * 8, cudaMemcpyHostToDevice, stream));
-    in.keys_or_masks = d_keys;
-    if (in_h->group_ids) {
+    if (n && !direct) PAC_CUDA(ctx, cudaMemcpyAsync(d_keys, in_h->keys_or_masks, n * 8, cudaMemcpyHostToDevice, stream));
+    if (!direct) in.keys_or_masks = d_keys;
+    if (in_h->group_ids && !direct) {
         void *d_g = cv.take(gbytes);
         if (n) PAC_CUDA(ctx, cudaMemcpyAsync(d_g, in_h->group_ids, gbytes, cudaMemcpyHostToDevice, stream));
         in.group_ids = d_g;
     }
     pac_agg_spec specs[PAC_MAX_SPECS];
     for (int i = 0; i < n_specs; i++) {
-        specs[i] = specs_h[i];
-        if (specs[i].kind != PAC_COUNT) {
+        specs[i] = direct ? direct_specs[i] : specs_h[i];
+        if (specs[i].kind != PAC_COUNT && !direct) {
             const size_t vb = n * (specs[i].vtype == PAC_F32 ? 4 : 8);
             // a column shared by several specs is copied once
             const void *dv = nullptr;
