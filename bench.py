@@ -169,6 +169,25 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(vals, world: int):
+    """Each entry's maximum over the ranks: the job takes as long as its
+    slowest rank (NCCL on GPUs, gloo on CPU)."""
+    import torch
+    t = torch.tensor(list(vals), dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_throughput(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job units per second: every rank processes its own units (weak
+    scaling, no data-path collective) in at most `ms`."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def _gen(workload: str, seed: int, rows):
     from paper_2603_15023_gb300 import inputs
     fn = inputs.WORKLOADS[workload]
@@ -357,14 +376,8 @@ def run_batch(args):
         raise RuntimeError(B.status_name(st))
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms_step = start.elapsed_time(end) / args.steps
-    t = torch.tensor([ms_step], dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        t = t.cuda()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t = t.cpu()
-    ms_step = float(t[0])
-    value = db.total_rows * world / (ms_step / 1e3)
+    ms_step = max_over_ranks([ms_step], world)[0]
+    value = job_throughput(db.total_rows, world, ms_step)
     peak, peak_src = _peaks()
     algo = db.algorithmic_bytes()
     achieved = algo / (statistics.mean(step_ms) / 1e3) / 1e9
@@ -643,14 +656,8 @@ def run_ours(args):
     agg_ms = [a.elapsed_time(b) for a, b, _ in evs]
     step_ms = [a.elapsed_time(c) for a, _, c in evs]
     ms_step = start.elapsed_time(end) / args.steps if flush is None else statistics.mean(step_ms)
-    t = torch.tensor([ms_step, statistics.mean(agg_ms)], dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        t = t.cuda()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t = t.cpu()
-    ms_step, agg_mean = float(t[0]), float(t[1])
-    value = n * world / (ms_step / 1e3)
+    ms_step, agg_mean = max_over_ranks([ms_step, statistics.mean(agg_ms)], world)
+    value = job_throughput(n, world, ms_step)
 
     # the release of every cell, timed once beside the step when it is not in it
     fin_ms = None
