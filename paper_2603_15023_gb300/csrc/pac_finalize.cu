@@ -431,14 +431,19 @@ __device__ void finalize_chain(const FinParams &p) {
             }
             // step 2: noise variance; step 3: release
             const double delta = var * inv2b;
-            const double yt = delta == 0.0 ? yj : yj + sqrt(delta) * z;
+            // sqrt(delta) and -1/(2 delta) both from one reciprocal square root
+            // (the chain is bound by dependent FP64 instructions); delta = inf
+            // and deltas near the bottom of the range take the plain forms
+            const double rs = rsqrt(delta);
+            const bool plain = !(delta > 1e-300) || isinf(delta);
+            const double yt = delta == 0.0 ? yj : yj + (plain ? sqrt(delta) : delta * rs) * z;
             // step 4: Bayesian update of the log-weights
             const bool upd = delta > 0.0;
             // independent mode: the next cell starts from the uniform prior, so
             // only the last cell's update is ever read
             if (upd && (adaptive || c0 + kc + 1 == n_cells)) {
                 const double e = yt - y;
-                L = fma(e * e, -0.5 / delta, L);
+                L = fma(e * e, plain ? -0.5 / delta : -0.5 * rs * rs, L);
                 L -= chain_max_nonpos(L, sh, slot, warp, lane);
                 w = exp(L);
                 if (adaptive) {
