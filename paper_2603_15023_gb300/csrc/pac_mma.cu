@@ -510,12 +510,8 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
         const uint32_t w6 = spread4((x >> 24) & 0xF), w7 = spread4(x >> 28);
         sts128(a_row, w0, w1, w2, w3);
         sts128(a_row + 128, w4, w5, w6, w7);
-        if (balanced_keys) {
-            // worlds 32..63 are the complement of worlds 0..31
-            constexpr uint32_t k1 = 0x01010101u;
-            sts128(a_row + 256, w0 ^ k1, w1 ^ k1, w2 ^ k1, w3 ^ k1);
-            sts128(a_row + 384, w4 ^ k1, w5 ^ k1, w6 ^ k1, w7 ^ k1);
-        } else {
+        // balanced keys: the upper half of A is the constant written at launch
+        if (!balanced_keys) {
             write_bits16(a_row + 256, y & 0xFFFFu);
             write_bits16(a_row + 384, y >> 16);
         }
@@ -528,7 +524,7 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
         if (static_cast<uint32_t>(lane) < glen - gcnt) {
             const uint32_t ps = gl + gcnt + lane;
             const uint32_t a_row = a_stage + (ps >> 3) * 512 + (ps & 7) * 16;
-            for (int h = 0; h < 4; h++) sts128(a_row + h * 128, 0, 0, 0, 0);
+            for (int h = 0; h < (balanced_keys ? 2 : 4); h++) sts128(a_row + h * 128, 0, 0, 0, 0);
             const uint32_t b_row = b_stage + (ps >> 3) * ((N / 16) * 128) + (ps & 7) * 16;
             for (int h = 0; h < N / 16; h++) sts128(b_row + h * 128, 0, 0, 0, 0);
         }
@@ -581,6 +577,21 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
                 "r"(0u));
         }
         asm volatile("tcgen05.wait::st.sync.aligned;");
+    }
+    // Balanced keys: worlds 32..63 are the complements of worlds 0..31, so the
+    // upper half of A is one constant for every row -- world 32 set, 33..63
+    // clear -- and accumulator row 32 becomes the run's total (world 32 + j =
+    // total - world j, derived by the finish kernel).  Written once per stage;
+    // the producers then write only worlds 0..31.
+    if (!(p.in.in_flags & PAC_IN_MASKS) && p.in.hash_mode == PAC_HASH_BALANCED) {
+        const uint32_t slots = p.k_cap + 8;
+        for (uint32_t i = static_cast<uint32_t>(tid); i < kStages * slots; i += blockDim.x) {
+            const uint32_t stage = i / slots, sl = i % slots;
+            const uint32_t a_row = smem_u32(smem) + stage * (p.a_bytes + p.b_bytes) + (sl >> 3) * 512 + (sl & 7) * 16;
+            sts128(a_row + 256, 1u, 0u, 0u, 0u);
+            sts128(a_row + 384, 0u, 0u, 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -749,6 +760,7 @@ struct FinishParams {
     const unsigned long long *acc;
     const unsigned long long *ng;
     uint32_t G;
+    int32_t balanced;  // accumulator row 32 holds the run totals; worlds 32+j = total - world j
     int32_t n_cols, c4, n_alloc;
     int32_t n_out;
     int32_t out_kind[kMaxSpecs];
@@ -764,8 +776,16 @@ __global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
     const bool live = cell < static_cast<size_t>(f.G) * kWorlds;
     const uint32_t g = live ? static_cast<uint32_t>(cell / kWorlds) : 0;
     const int j = static_cast<int>(cell % kWorlds);
-    const long long *a = reinterpret_cast<const long long *>(f.acc) + cell * f.n_alloc;
-    const unsigned long long cnt = live ? static_cast<unsigned long long>(a[0]) : 0ull;
+    // digit total k of this cell; under balanced keys world 32 + j is the
+    // group total (row 32) minus world j, exactly (wrapping 64-bit integers)
+    const bool derive = f.balanced && j >= 32;
+    const unsigned long long *a = f.acc + cell * f.n_alloc;
+    const unsigned long long *tot_row = f.acc + (static_cast<size_t>(g) * kWorlds + 32) * f.n_alloc;
+    const unsigned long long *low_row = f.acc + (static_cast<size_t>(g) * kWorlds + (j & 31)) * f.n_alloc;
+    auto digit = [&](int k) -> long long {
+        return static_cast<long long>(derive ? tot_row[k] - low_row[k] : a[k]);
+    };
+    const unsigned long long cnt = live ? static_cast<unsigned long long>(digit(0)) : 0ull;
     const unsigned bal = __ballot_sync(kFull, live && cnt > 0);
     if (f.meta && live) {
         if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(f.meta + 2 * g + 1)[j >= 32 ? 1 : 0] = bal;
@@ -781,7 +801,7 @@ __global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
         __int128 tot = 0;
         for (int q = 15; q >= 0; q--) {
             const int feat = f.c4 == 1 ? 4 + q : 4 + q * f.c4 + c;
-            const long long dq = feat < f.n_alloc ? a[feat] : 0;
+            const long long dq = feat < f.n_alloc ? digit(feat) : 0;
             tot = tot * 16 + dq;
         }
         const bool fits = tot >= static_cast<__int128>(LLONG_MIN) && tot <= static_cast<__int128>(LLONG_MAX);
@@ -930,6 +950,7 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
     f.acc = p.acc;
     f.ng = p.ng;
     f.G = G;
+    f.balanced = !(in->in_flags & PAC_IN_MASKS) && in->hash_mode == PAC_HASH_BALANCED;
     f.n_cols = C;
     f.c4 = c4;
     f.n_alloc = p.n_alloc;
