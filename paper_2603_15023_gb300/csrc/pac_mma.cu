@@ -522,9 +522,9 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
         const uint32_t gcnt = __shfl_sync(kFull, cnt, warp), glen = __shfl_sync(kFull, len, warp);
         const uint32_t gl = __shfl_sync(kFull, glo, warp);
         if (static_cast<uint32_t>(lane) < glen - gcnt) {
+            // zero features make a padding row add nothing, whatever its world
+            // bytes (finite E4M3 0/1 values: the stage was cleared at launch)
             const uint32_t ps = gl + gcnt + lane;
-            const uint32_t a_row = a_stage + (ps >> 3) * 512 + (ps & 7) * 16;
-            for (int h = 0; h < (balanced_keys ? 2 : 4); h++) sts128(a_row + h * 128, 0, 0, 0, 0);
             const uint32_t b_row = b_stage + (ps >> 3) * ((N / 16) * 128) + (ps & 7) * 16;
             for (int h = 0; h < N / 16; h++) sts128(b_row + h * 128, 0, 0, 0, 0);
         }
@@ -583,12 +583,17 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
     // clear -- and accumulator row 32 becomes the run's total (world 32 + j =
     // total - world j, derived by the finish kernel).  Written once per stage;
     // the producers then write only worlds 0..31.
-    if (!(p.in.in_flags & PAC_IN_MASKS) && p.in.hash_mode == PAC_HASH_BALANCED) {
+    // The world bytes of every slot start at 0, so that the rows padding a
+    // group's run (their features zeroed per tile) multiply finite values.
+    {
+        const bool bal = !(p.in.in_flags & PAC_IN_MASKS) && p.in.hash_mode == PAC_HASH_BALANCED;
         const uint32_t slots = p.k_cap + 8;
         for (uint32_t i = static_cast<uint32_t>(tid); i < kStages * slots; i += blockDim.x) {
             const uint32_t stage = i / slots, sl = i % slots;
             const uint32_t a_row = smem_u32(smem) + stage * (p.a_bytes + p.b_bytes) + (sl >> 3) * 512 + (sl & 7) * 16;
-            sts128(a_row + 256, 1u, 0u, 0u, 0u);
+            sts128(a_row, 0u, 0u, 0u, 0u);
+            sts128(a_row + 128, 0u, 0u, 0u, 0u);
+            sts128(a_row + 256, bal ? 1u : 0u, 0u, 0u, 0u);
             sts128(a_row + 384, 0u, 0u, 0u, 0u);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
