@@ -57,6 +57,11 @@ WORKLOADS = {
     "highcard_100m": {"gid_bytes": 4, "n_cols": 1, "aggs": "count+sum", "finalize": "separate",
                       "in_bytes_per_row": 8 + 4 + 8, "flush_l2": False,
                       "describe": "count + sum, exact; release of the 2M cells timed separately"},
+    "lowcard_60m_approx": {"gid_bytes": 1, "n_cols": 4, "aggs": "count+sum+avg", "finalize": "adaptive",
+                           "in_bytes_per_row": 8 + 1 + 4 * 8, "flush_l2": False, "approx": True,
+                           "describe": "lowcard_60m with the paper's approximate SUM and AVG (Sec. 5: 25 levels "
+                                       "of 16-bit counters cascading every 4 bits, two-sided); count + 4 sum + 4 "
+                                       "avg, adaptive finalize of 36 cells"},
     "select_60m": {"gid_bytes": 1, "n_cols": 4, "aggs": "count+sum+avg", "finalize": "adaptive",
                    "in_bytes_per_row": 8 + 1 + 4 * 8, "flush_l2": False, "select": True,
                    "describe": "lowcard_60m under a correlated PAC selection (Sec. 4.2): world j of a row kept "
@@ -198,12 +203,13 @@ def _spec_list(B, wcfg, vals, outs):
     """(kind, variant, vtype, values, out) per spec: COUNT, SUM per column,
     AVG per column (lowcard only)."""
     C = wcfg["n_cols"]
+    var = B.PAC_APPROX if wcfg.get("approx") else B.PAC_EXACT
     specs = [(B.PAC_COUNT, B.PAC_EXACT, B.PAC_I64, 0, outs[0])]
     for k in range(C):
-        specs.append((B.PAC_SUM, B.PAC_EXACT, B.PAC_I64, vals[k], outs[1 + k]))
+        specs.append((B.PAC_SUM, var, B.PAC_I64, vals[k], outs[1 + k]))
     if "avg" in wcfg["aggs"]:
         for k in range(C):
-            specs.append((B.PAC_AVG, B.PAC_EXACT, B.PAC_I64, vals[k], outs[1 + C + k]))
+            specs.append((B.PAC_AVG, var, B.PAC_I64, vals[k], outs[1 + C + k]))
     return specs
 
 
@@ -251,11 +257,17 @@ def _oracle_step(orc, wcfg, wl, G, qk, thr=None):
         keep = masks != 0
         masks, gids, vals = masks[keep], gids[keep], [v[keep] for v in vals]
     res = [orc.aggregate(masks, None, gids, G, orc.COUNT)]
-    for v in vals:
-        res.append(orc.aggregate(masks, v, gids, G, orc.SUM))
-    if "avg" in wcfg["aggs"]:
+    if wcfg.get("approx"):
         for v in vals:
-            res.append(orc.aggregate(masks, v, gids, G, orc.AVG))
+            res.append(orc.approx_sum_i64(masks, v, gids, G))
+        for v in vals:
+            res.append(orc.approx_avg_i64(masks, v, gids, G))
+    else:
+        for v in vals:
+            res.append(orc.aggregate(masks, v, gids, G, orc.SUM))
+        if "avg" in wcfg["aggs"]:
+            for v in vals:
+                res.append(orc.aggregate(masks, v, gids, G, orc.AVG))
     if wcfg.get("lift"):
         y = np.stack([r[0].astype(np.float64) for r in res[1:3]], axis=1)
         orc.lift(y, [2.0, 2.0], RATIO_PROG_ORC(orc))
@@ -748,7 +760,10 @@ def run_ours(args):
     achieved = algo_bytes / (agg_mean / 1e3) / 1e9
     kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
               2: ("k_select_prep + k_select + k_agg_mma + k_mma_finish (all launches of pac_aggregate_select)"
-                  if sel is not None else "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
+                  if sel is not None else
+                  "k_agg_mma + k_mma_finish (COUNT) + k_apx_chunks / k_apx_merge / k_apx_emit per approximate "
+                  "spec (all launches of pac_aggregate_multi)" if wcfg.get("approx") else
+                  "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
               3: "k_part_hist + k_part_scan + k_part_scatter + k_batch_agg + k_batch_merge "
                  "(all launches of pac_aggregate_multi)"}.get(path, str(path))
     if rank == 0:

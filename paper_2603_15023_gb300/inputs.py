@@ -133,6 +133,7 @@ WORKLOADS = {
     "ungrouped_1m": ungrouped_1m,
     "lowcard_60m": lowcard_60m,
     "select_60m": lowcard_60m,   # the same columns, read under a PAC selection
+    "lowcard_60m_approx": lowcard_60m,  # the same columns, approximate SUM / AVG
     "ratio_100m": ratio_100m,
     "highcard_100m": highcard_100m,
 }
