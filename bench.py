@@ -758,14 +758,19 @@ def run_ours(args):
     out_bytes = G * 64 * 8 * n_specs + G * 16
     algo_bytes = n * wcfg["in_bytes_per_row"] + out_bytes
     achieved = algo_bytes / (agg_mean / 1e3) / 1e9
+    path_name = {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
+                 3: "group partition + per-bit engine"}.get(path, str(path))
     kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
               2: ("k_select_prep + k_select + k_agg_mma + k_mma_finish (all launches of pac_aggregate_select)"
-                  if sel is not None else
-                  "k_agg_mma + k_mma_finish (COUNT) + k_apx_chunks / k_apx_merge / k_apx_emit per approximate "
-                  "spec (all launches of pac_aggregate_multi)" if wcfg.get("approx") else
-                  "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
+                  if sel is not None else "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
               3: "k_part_hist + k_part_scan + k_part_scatter + k_batch_agg + k_batch_merge "
                  "(all launches of pac_aggregate_multi)"}.get(path, str(path))
+    if wcfg.get("approx"):
+        # the exact specs (COUNT and the row counts) take `path`; each distinct
+        # value column of an approximate spec runs one cascade
+        kernel = ("k_apx_chunks + k_apx_combine_level + k_apx_emit per approximate value column, plus "
+                  f"{path_name} for the exact specs (all launches of pac_aggregate_multi)")
+        path_name = f"approximate cascades + {path_name} (exact specs)"
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -784,8 +789,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": args.workload, "rows": n, "groups": G, "value_columns": C, "worlds": 64,
                        "aggregates": wcfg["describe"], "l2": l2,
-                       "agg_path": {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
-                                    3: "group partition + per-bit engine"}.get(path, str(path))},
+                       "agg_path": path_name},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(args.workload, n) if path == 2 else None,
                          "kernel": kernel, "algorithmic_bytes": algo_bytes, "peak_source": peak_src,
