@@ -54,6 +54,14 @@ WORKLOADS = {
     "ungrouped_1m": {"gid_bytes": 0, "n_cols": 1, "aggs": "count+sum", "finalize": "adaptive",
                      "in_bytes_per_row": 8 + 8, "flush_l2": True,
                      "describe": "count + sum, exact; adaptive finalize of 2 cells"},
+    "max_1g": {"gid_bytes": 0, "n_cols": 1, "aggs": "count+max", "finalize": "adaptive",
+               "in_bytes_per_row": 8 + 8, "flush_l2": False,
+               "describe": "ungrouped count + MAX of int64 values uniform in [0, 1e12] (Sec. 5 bound pruning "
+                           "applies); adaptive finalize of 2 cells"},
+    "max_1g_increasing": {"gid_bytes": 0, "n_cols": 1, "aggs": "count+max", "finalize": "adaptive",
+                          "in_bytes_per_row": 8 + 8, "flush_l2": False,
+                          "describe": "ungrouped count + MAX of value = row index, the adversarial order for "
+                                      "bound pruning (every row raises its worlds); adaptive finalize of 2 cells"},
     "highcard_100m": {"gid_bytes": 4, "n_cols": 1, "aggs": "count+sum", "finalize": "separate",
                       "in_bytes_per_row": 8 + 4 + 8, "flush_l2": False,
                       "describe": "count + sum, exact; release of the 2M cells timed separately"},
@@ -200,11 +208,13 @@ def _gen(workload: str, seed: int, rows):
 
 
 def _spec_list(B, wcfg, vals, outs):
-    """(kind, variant, vtype, values, out) per spec: COUNT, SUM per column,
-    AVG per column (lowcard only)."""
+    """(kind, variant, vtype, values, out) per spec: COUNT, then SUM (or MAX)
+    per column, then AVG per column where the workload has it."""
     C = wcfg["n_cols"]
     var = B.PAC_APPROX if wcfg.get("approx") else B.PAC_EXACT
     specs = [(B.PAC_COUNT, B.PAC_EXACT, B.PAC_I64, 0, outs[0])]
+    if "max" in wcfg["aggs"]:
+        return specs + [(B.PAC_MAX, B.PAC_EXACT, B.PAC_I64, vals[k], outs[1 + k]) for k in range(C)]
     for k in range(C):
         specs.append((B.PAC_SUM, var, B.PAC_I64, vals[k], outs[1 + k]))
     if "avg" in wcfg["aggs"]:
@@ -257,7 +267,10 @@ def _oracle_step(orc, wcfg, wl, G, qk, thr=None):
         keep = masks != 0
         masks, gids, vals = masks[keep], gids[keep], [v[keep] for v in vals]
     res = [orc.aggregate(masks, None, gids, G, orc.COUNT)]
-    if wcfg.get("approx"):
+    if "max" in wcfg["aggs"]:
+        for v in vals:
+            res.append(orc.aggregate(masks, v, gids, G, orc.MAX))
+    elif wcfg.get("approx"):
         for v in vals:
             res.append(orc.approx_sum_i64(masks, v, gids, G))
         for v in vals:
@@ -273,7 +286,8 @@ def _oracle_step(orc, wcfg, wl, G, qk, thr=None):
         orc.lift(y, [2.0, 2.0], RATIO_PROG_ORC(orc))
     if wcfg["finalize"] != "separate":
         y = np.stack([r[0].astype(np.float64) for r in res], axis=1)
-        scales = [2.0] * (1 + wcfg["n_cols"]) + [1.0] * (len(res) - 1 - wcfg["n_cols"])
+        per_col = 1.0 if "max" in wcfg["aggs"] else 2.0  # COUNT and SUM scale by 2, MAX and AVG by 1
+        scales = [2.0] + [per_col] * wcfg["n_cols"] + [1.0] * (len(res) - 1 - wcfg["n_cols"])
         orc.finalize(y, scales, res[0][1], res[0][2], 99, 1.0 / 128, orc.ADAPTIVE)
 
 
@@ -558,6 +572,7 @@ def run_ours(args):
     ctx = B.pac_create(local)
     if args.path:
         B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2, "engine": 3}[args.path])
+    B.pac_set_option(ctx, "minmax_prune", args.minmax_prune)
 
     wcfg = WORKLOADS[args.workload]
     wl = _gen(args.workload, rank, args.rows)
@@ -759,12 +774,13 @@ def run_ours(args):
     algo_bytes = n * wcfg["in_bytes_per_row"] + out_bytes
     achieved = algo_bytes / (agg_mean / 1e3) / 1e9
     path_name = {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
-                 3: "group partition + per-bit engine"}.get(path, str(path))
+                 3: "per-bit engine (rows partitioned by group first when the groups' states exceed "
+                    "shared memory)"}.get(path, str(path))
     kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
               2: ("k_select_prep + k_select + k_agg_mma + k_mma_finish (all launches of pac_aggregate_select)"
                   if sel is not None else "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
-              3: "k_part_hist + k_part_scan + k_part_scatter + k_batch_agg + k_batch_merge "
-                 "(all launches of pac_aggregate_multi)"}.get(path, str(path))
+              3: "k_batch_agg + k_batch_merge, after k_part_hist + k_part_scan + k_part_scatter when the "
+                 "rows are partitioned by group (all launches of pac_aggregate_multi)"}.get(path, str(path))
     if wcfg.get("approx"):
         # the exact specs (COUNT and the row counts) take `path`; each distinct
         # value column of an approximate spec runs one cascade
@@ -789,7 +805,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": args.workload, "rows": n, "groups": G, "value_columns": C, "worlds": 64,
                        "aggregates": wcfg["describe"], "l2": l2,
-                       "agg_path": path_name},
+                       "agg_path": path_name,
+                       **({"minmax_prune": bool(args.minmax_prune)} if "max" in wcfg["aggs"] else {})},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(args.workload, n) if path == 2 else None,
                          "kernel": kernel, "algorithmic_bytes": algo_bytes, "peak_source": peak_src,
@@ -824,6 +841,8 @@ def main():
     ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
     ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma", "engine"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--minmax-prune", type=int, default=1, choices=[0, 1],
+                    help="MIN/MAX bound pruning on the per-bit engine (results are identical either way)")
     ap.add_argument("--cpu-rows", type=int, default=4_000_000)
     ap.add_argument("--ref-rows", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

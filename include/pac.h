@@ -500,6 +500,10 @@ pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_spec *specs,
  *   per-bit CUDA-core kernels, 2 = force the tensor-core path
  *   (PAC_E_UNSUPPORTED where it cannot serve), 3 = force the per-bit engine
  *   (warp bit-transpose; the engine of the batched path).
+ *   "minmax_prune" 1 (default) = MIN/MAX bound pruning on the per-bit
+ *   engine (Sec. 5 "Pruning": rows whose value improves no world's current
+ *   extreme skip the update; results are identical), 0 = every row updated.
+ *   Plans built by pac_batch_plan take the setting current at plan time.
  *   pac_get_info(ctx, name, &value): "last_path" (1 plain per-bit, 2 tensor
  *   core, 3 per-bit engine), "last_launches" kernels launched by the last
  *   call.

@@ -18,9 +18,19 @@
 // packed as the low and high halves of one 32-bit word per level (a half can
 // never carry into the other: each half is bounded by the level total, which
 // stays <= 0xFFFF); lane k < 25 holds the level-k totals of both sides in
-// registers.  A CTA holds an aligned block of chunks and does the first tree
-// levels in shared memory; the remaining levels run one launch per level over
-// the block states in global memory.
+// registers.  A CTA holds an aligned block of 16 chunks of one group (grid
+// y = group, so a group with few rows frees its SM early) and does the first
+// tree levels in shared memory; the remaining levels run one launch per level
+// over the block states in global memory.
+//
+// Row loop: the lanes of a 32-row batch compute their rows' side, level and
+// level units in parallel; the warp then walks the group's rows in order.
+// Per side, the level of the latest update is "open": its counters since the
+// last commit sit in a register (acc) and its exact total in a uniform
+// register (ct).  A row of the open level whose units still fit under the cap
+// only adds to those registers; any other row commits them to the level state
+// and takes the full update with its flush chain.  Every flush decision reads
+// exact totals, so the state equals the row-by-row definition.
 #include "pac_internal.cuh"
 #include "pac_kernels.h"
 
@@ -60,17 +70,6 @@ __device__ __forceinline__ void apx_flush(ApxSide *s, uint32_t &t, int l, int la
     for (int k = h; k >= l; k--) apx_move(s, t, k, lane);
 }
 
-__device__ __forceinline__ void apx_add_value(ApxSide *s, uint32_t &t, uint64_t a, uint32_t b0,
-                                              uint32_t b1, int lane, bool &ovf) {
-    const int msb = 63 - __clzll(static_cast<long long>(a));
-    const int l = msb < 8 ? 0 : (msb - 8) >> 2;
-    const uint32_t x = static_cast<uint32_t>(a >> (4 * l));
-    if (lvl_total(t, l) + x > kCap) apx_flush(s, t, l, lane, ovf);
-    s->w[l][lane] += x * b0 + ((x * b1) << 16);
-    if (lane == l) t += x;
-    __syncwarp();
-}
-
 // dst (+)= src for one side; dst totals in registers, src totals in memory.
 __device__ __forceinline__ void apx_combine_side(ApxSide *dst, uint32_t &t, const ApxSide *src,
                                                  int lane, bool &ovf) {
@@ -106,30 +105,67 @@ __device__ __forceinline__ void apx_combine(ApxState *dst, const ApxState *src, 
     apx_store_totals(dst, t0, t1, lane);
 }
 
-__global__ void k_apx_chunks(const __grid_constant__ ApxParams p) {
+// The open level of one side (see the row loop above).
+struct ApxOpen {
+    uint32_t acc;  // this lane's packed counters added since the last commit
+    uint32_t ct;   // the open level's exact total (uniform)
+    int cl;        // the open level, -1 when none (uniform)
+};
+
+// Writes the open level back: counters into the level state, total into the
+// lane that holds it.
+__device__ __forceinline__ void apx_commit(ApxSide *s, uint32_t &t, ApxOpen &o, int lane) {
+    if (o.cl >= 0) {
+        s->w[o.cl][lane] += o.acc;
+        if (lane == o.cl) t = o.ct;
+        __syncwarp();
+    }
+    o.acc = 0;
+    o.cl = -1;
+}
+
+// One nonzero value of one side: x units at level l, this lane's world bits.
+__device__ __forceinline__ void apx_row(ApxSide *s, uint32_t &t, ApxOpen &o, int l, uint32_t x, uint32_t b0,
+                                        uint32_t b1, int lane, bool &ovf) {
+    const uint32_t add = x * b0 + ((x * b1) << 16);
+    if (l == o.cl && o.ct + x <= kCap) {  // no flush: the update stays in registers
+        o.acc += add;
+        o.ct += x;
+        return;
+    }
+    apx_commit(s, t, o, lane);
+    if (lvl_total(t, l) + x > kCap) apx_flush(s, t, l, lane, ovf);
+    o.cl = l;
+    o.ct = lvl_total(t, l) + x;
+    o.acc = add;
+}
+
+__global__ void __launch_bounds__(32 * kApxBlockChunks) k_apx_chunks(const __grid_constant__ ApxParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ApxState *sm = reinterpret_cast<ApxState *>(smem_raw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, ci = threadIdx.x >> 5;
     const uint32_t G = p.in.n_groups;
-    const int ci = warp / static_cast<int>(G);
-    const uint32_t g = warp % G;
-    const uint64_t chunk = static_cast<uint64_t>(blockIdx.x) * p.chunks_per_block + ci;
-    ApxState *st = sm + warp;
+    const uint32_t g = blockIdx.y;
+    const uint64_t chunk = static_cast<uint64_t>(blockIdx.x) * kApxBlockChunks + ci;
+    ApxState *st = sm + ci;
     apx_zero(st, lane);
     uint32_t t0 = 0, t1 = 0;
+    ApxOpen o0{0, 0, -1}, o1{0, 0, -1};
     bool ovf = false;
     uint64_t rows_g = 0;
     if (chunk < p.n_chunks) {
         const uint64_t lo = chunk * kApxChunk;
         const uint64_t hi = min(p.in.n, lo + kApxChunk);
+        // group ids one batch ahead, so that their load overlaps the row walk
+        uint32_t gid_next = lo + lane < hi ? row_gid(p.in, lo + lane) : 0u;
         for (uint64_t base = lo; base < hi; base += 32) {
             const uint64_t row = base + lane;
             bool valid = row < hi;
-            uint32_t gid = 0;
+            const uint32_t gid = gid_next;
+            if (base + 32 + lane < hi) gid_next = row_gid(p.in, base + 32 + lane);
             long long v = 0;
             uint64_t mask = 0;
             if (valid) {
-                gid = row_gid(p.in, row);
                 if (gid >= G && g == 0) raise_status(p.status, kStatusBadGroup);
                 if (gid == g) {
                     v = row_i64(p.values, row);
@@ -140,27 +176,35 @@ __global__ void k_apx_chunks(const __grid_constant__ ApxParams p) {
             const uint32_t mine = __ballot_sync(kFull, valid && gid == g);
             rows_g += __popc(mine);
             const uint32_t todo = __ballot_sync(kFull, valid && gid == g && v != 0);
+            // this lane's row as (side, level, units): a = |v| goes to level
+            // l = floor((msb(a) - 8) / 4) (0 below 2^8) as a >> 4l < 2^12
+            const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+            const int msb = a ? 63 - __clzll(static_cast<long long>(a)) : 0;
+            const int lv = msb < 8 ? 0 : (msb - 8) >> 2;
+            const uint32_t pk = static_cast<uint32_t>(a >> (4 * lv)) | (static_cast<uint32_t>(lv) << 12) |
+                                (v < 0 ? 1u << 17 : 0u);
             const uint32_t mlo = static_cast<uint32_t>(mask), mhi = static_cast<uint32_t>(mask >> 32);
             for (uint32_t rr = todo; rr; rr &= rr - 1) {
                 const int r = __ffs(rr) - 1;
-                const long long vr = __shfl_sync(kFull, v, r);
+                const uint32_t q = __shfl_sync(kFull, pk, r);
                 const uint32_t b0 = (__shfl_sync(kFull, mlo, r) >> lane) & 1u;
                 const uint32_t b1 = (__shfl_sync(kFull, mhi, r) >> lane) & 1u;
-                if (vr < 0) {
-                    apx_add_value(&st->side[1], t1, 0ull - static_cast<uint64_t>(vr), b0, b1, lane, ovf);
-                } else {
-                    apx_add_value(&st->side[0], t0, static_cast<uint64_t>(vr), b0, b1, lane, ovf);
-                }
+                const uint32_t x = q & 0xFFFu;
+                const int l = static_cast<int>((q >> 12) & 31u);
+                if (q >> 17) apx_row(&st->side[1], t1, o1, l, x, b0, b1, lane, ovf);
+                else apx_row(&st->side[0], t0, o0, l, x, b0, b1, lane, ovf);
             }
         }
     }
+    apx_commit(&st->side[0], t0, o0, lane);
+    apx_commit(&st->side[1], t1, o1, lane);
     apx_store_totals(st, t0, t1, lane);
     if (lane == 0 && rows_g) atomicAdd(reinterpret_cast<unsigned long long *>(p.ng + g), rows_g);
     __syncthreads();
     // first tree levels inside the block of chunks
-    for (uint32_t width = 1; width < p.chunks_per_block; width *= 2) {
-        if ((ci % (2 * width)) == 0 && ci + width < p.chunks_per_block && chunk + width < p.n_chunks)
-            apx_combine(st, sm + (ci + width) * G + g, lane, ovf);
+    for (uint32_t width = 1; width < kApxBlockChunks; width *= 2) {
+        if ((ci % (2 * width)) == 0 && ci + width < kApxBlockChunks && chunk + width < p.n_chunks)
+            apx_combine(st, sm + ci + width, lane, ovf);
         __syncthreads();
     }
     if (ci == 0) {
@@ -211,20 +255,13 @@ __global__ void k_apx_emit(const __grid_constant__ ApxParams p, long long *out_s
     }
 }
 
-uint32_t apx_chunks_per_block(uint32_t G) {
-    uint32_t b = 1;
-    while (b * 2 * G <= 32) b *= 2;
-    return b;
-}
-
 }  // namespace
 
 int apx_max_groups() { return 32; }
 
 size_t apx_scratch_bytes(uint64_t n, uint32_t G) {
     const uint64_t n_chunks = (n + kApxChunk - 1) / kApxChunk;
-    const uint32_t b = apx_chunks_per_block(G);
-    const uint64_t n_blocks = (n_chunks + b - 1) / b;
+    const uint64_t n_blocks = (n_chunks + kApxBlockChunks - 1) / kApxBlockChunks;
     return static_cast<size_t>(n_blocks ? n_blocks : 1) * G * sizeof(ApxState) + G * sizeof(uint64_t);
 }
 
@@ -233,8 +270,8 @@ cudaError_t launch_approx(const ApxParams &pin, void *out_sum, void *out_avg, cu
     ApxParams p = pin;
     const uint32_t G = p.in.n_groups;
     p.n_chunks = (p.in.n + kApxChunk - 1) / kApxChunk;
-    p.chunks_per_block = apx_chunks_per_block(G);
-    const uint64_t n_blocks = (p.n_chunks + p.chunks_per_block - 1) / p.chunks_per_block;
+    p.chunks_per_block = kApxBlockChunks;
+    const uint64_t n_blocks = (p.n_chunks + kApxBlockChunks - 1) / kApxBlockChunks;
     cudaError_t e = cudaMemsetAsync(p.ng, 0, G * sizeof(uint64_t), s);
     if (e != cudaSuccess) return e;
     if (n_blocks == 0) {
@@ -242,11 +279,10 @@ cudaError_t launch_approx(const ApxParams &pin, void *out_sum, void *out_avg, cu
         e = cudaMemsetAsync(p.states, 0, G * sizeof(ApxState), s);
         if (e != cudaSuccess) return e;
     } else {
-        const int threads = 32 * p.chunks_per_block * G;
-        const size_t smem = static_cast<size_t>(p.chunks_per_block) * G * sizeof(ApxState);
+        const size_t smem = static_cast<size_t>(kApxBlockChunks) * sizeof(ApxState);
         e = cudaFuncSetAttribute(k_apx_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        k_apx_chunks<<<static_cast<unsigned>(n_blocks), threads, smem, s>>>(p);
+        k_apx_chunks<<<dim3(static_cast<unsigned>(n_blocks), G), 32 * kApxBlockChunks, smem, s>>>(p);
         (*launches)++;
         for (uint64_t width = 1; width < n_blocks; width *= 2) {
             const uint64_t pairs = (n_blocks + 2 * width - 1) / (2 * width);

@@ -641,6 +641,11 @@ pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value) {
         ctx->opt_agg_path = value;
         return PAC_OK;
     }
+    if (strcmp(name, "minmax_prune") == 0) {
+        if (value < 0 || value > 1) return fail(ctx, PAC_E_INVALID, "minmax_prune %lld", static_cast<long long>(value));
+        ctx->opt_minmax_prune = value;
+        return PAC_OK;
+    }
     return fail(ctx, PAC_E_INVALID, "unknown option %s", name);
 }
 

@@ -75,7 +75,7 @@ __device__ __forceinline__ void atomic_fold(int op, uint64_t *cell, uint64_t acc
 struct ItemShared {
     InputDev in;
     SlotDev slot[kMaxSpecs];
-    int32_t n_slots, mode, bal;
+    int32_t n_slots, mode, bal, prune;
     uint64_t *state, *ng;
     unsigned long long *abs;
     uint64_t row0, row_end;
@@ -251,12 +251,13 @@ __device__ __forceinline__ void loop_row(const ItemShared &is, int r, uint32_t M
 
 // Fills `ra` for run R of this batch.  T0/T1: transposed world sets of
 // worlds j and j+32 (T1 ignored with bal).  slice[s]: bit count when slot s
-// may be bit-sliced (0: loop).  With compile-time slot operations a run of
-// all 32 rows (the common case of group-ordered rows) takes a fully
-// unrolled loop.
+// may be bit-sliced (0: loop).  L (a subset of R): the rows the broadcast
+// loop visits; rows of R outside L change no loop-type state (bound
+// pruning).  With compile-time slot operations a run of all 32 rows (the
+// common case of group-ordered rows) takes a fully unrolled loop.
 template <int NS, int SIG>
-__device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint32_t T0, uint32_t T1, bool bal,
-                                         const uint64_t (&vals)[NS], const int (&slice)[NS], int lane,
+__device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint32_t L, uint32_t T0, uint32_t T1,
+                                         bool bal, const uint64_t (&vals)[NS], const int (&slice)[NS], int lane,
                                          RunAcc<NS> &ra) {
     const uint32_t M0 = T0 & R;
     const uint32_t M1 = bal ? (R & ~T0) : (T1 & R);
@@ -300,8 +301,8 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
             any_loop = true;
         }
     }
-    if (!any_loop) return;
-    // broadcast loop over the rows of R for the remaining slots; float sums
+    if (!any_loop || L == 0) return;
+    // broadcast loop over the rows of L for the remaining slots; float sums
     // fold 8-row blocks into a compensated pair
     float fs0[NS], fc0[NS], fb0[NS], fs1[NS], fc1[NS], fb1[NS];
 #pragma unroll
@@ -322,7 +323,7 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
         }
     } else {
         int blk = 0;
-        for (uint32_t rr = R; rr; rr &= rr - 1) {
+        for (uint32_t rr = L; rr; rr &= rr - 1) {
             loop_row<NS, SIG>(is, __ffs(rr) - 1, M0, M1, bal, vals, sliced, ra, fb0, fb1);
             if (++blk == 8) {
                 blk = 0;
@@ -347,6 +348,60 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
 
 // States kept as worlds 0..31 + total with balanced masks (exact integers).
 __device__ __forceinline__ bool by_complement(int op, bool bal) { return bal && op == OP_ISUM; }
+
+// True when one row's value v would replace a MIN/MAX state st (the test of
+// op_update): MAX takes strictly greater values, MIN strictly smaller ones,
+// floats by IEEE comparison (a NaN value replaces nothing).
+__device__ __forceinline__ bool mm_improves(int op, uint64_t v, uint64_t st) {
+    switch (op) {
+    case OP_IMAX: return static_cast<long long>(v) > static_cast<long long>(st);
+    case OP_IMIN: return static_cast<long long>(v) < static_cast<long long>(st);
+    case OP_FMAX: return __longlong_as_double(static_cast<long long>(v)) > __longlong_as_double(static_cast<long long>(st));
+    default: return __longlong_as_double(static_cast<long long>(v)) < __longlong_as_double(static_cast<long long>(st));
+    }
+}
+
+constexpr uint32_t kPruneMinRun = 8;  // shorter runs visit every row
+
+// MIN/MAX bound pruning (Sec. 5 "Pruning"): the bound g is the weakest of
+// the 64 world states of the run's group (the smallest maximum for MAX, the
+// largest minimum for MIN).  A value that does not improve g improves no
+// world, so its row is left out of the broadcast loop.  The bound is read
+// from the sink's state at every run of at least kPruneMinRun rows (the
+// paper refreshes it every 2048 updates); a stale bound is weaker, never
+// wrong, because states only move towards the extreme.  Returns the rows
+// the loop must visit: R itself unless every loop-type slot is MIN/MAX.
+template <int NS, int SIG, typename Sink>
+__device__ __forceinline__ uint32_t prune_rows(const ItemShared &is, uint32_t R, uint32_t g,
+                                               const uint64_t (&vals)[NS], const int (&slice)[NS],
+                                               Sink &sink, int lane) {
+    if (SIG != 0 || !is.prune) return R;  // compile-time signatures hold no MIN/MAX slot
+    const uint32_t n = __popc(R);
+    if (n < kPruneMinRun) return R;
+    uint32_t keep = 0;
+    bool any_mm = false;
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (s >= is.n_slots) continue;
+        const int op = is.slot[s].op;
+        if (op == OP_ISUM) {
+            if (slice[s] > 0 && n >= static_cast<uint32_t>(slice[s])) continue;  // bit-sliced, not looped
+            return R;
+        }
+        if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) return R;
+        uint64_t b0, b1;
+        if (!sink.bound(g, s, lane, b0, b1)) return R;
+        uint64_t b = mm_improves(op, b0, b1) ? b1 : b0;  // the weaker of this lane's two worlds
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const uint64_t other = __shfl_xor_sync(kFull, b, o);
+            b = mm_improves(op, b, other) ? other : b;
+        }
+        keep |= __ballot_sync(kFull, ((R >> lane) & 1u) && mm_improves(op, vals[s], b));
+        any_mm = true;
+    }
+    return any_mm ? keep : R;
+}
 
 // Processes rows [base, base+32) of the item: transposes, finds the runs and
 // hands every run to `sink(g, ra)`.
@@ -380,7 +435,8 @@ __device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, ui
         const uint32_t R = __ballot_sync(kFull, valid && gid == g);
         pending &= ~R;
         RunAcc<NS> ra;
-        run_fold<NS, SIG>(is, R, T0, T1, bal, vals, slice, lane, ra);
+        const uint32_t L = prune_rows<NS, SIG>(is, R, g, vals, slice, sink, lane);
+        run_fold<NS, SIG>(is, R, L, T0, T1, bal, vals, slice, lane, ra);
         sink(g, ra, lane, bal);
     }
 }
@@ -407,6 +463,13 @@ struct SmemSink {
             else if (lane == 0) op_merge(op, sst[32], ra.tot[s]);
         }
         if (lane == 0) ng[g] += ra.n;
+    }
+    // this lane's current MIN/MAX states of worlds j and j+32 for slot s
+    __device__ __forceinline__ bool bound(uint32_t g, int s, int lane, uint64_t &b0, uint64_t &b1) const {
+        const uint64_t *sst = st + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
+        b0 = sst[lane];
+        b1 = sst[lane + 32];
+        return true;
     }
 };
 
@@ -481,6 +544,14 @@ struct CarrySink {
     __device__ __forceinline__ void flush(int lane, bool bal) {
         if (g_cur != 0xFFFFFFFFu) out(g_cur, acc, lane, bal);
         g_cur = 0xFFFFFFFFu;
+    }
+    // the carried run of group g is part of its final state: a bound for it
+    // (other groups' states live in global memory and are not read)
+    __device__ __forceinline__ bool bound(uint32_t g, int s, int lane, uint64_t &b0, uint64_t &b1) const {
+        if (g != g_cur) return false;
+        b0 = acc.a0[s];
+        b1 = acc.a1[s];
+        return true;
     }
 };
 
@@ -607,6 +678,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQuery
                 is.n_slots = q.n_slots;
                 is.mode = q.mode;
                 is.bal = q.bal;
+                is.prune = q.prune;
                 is.state = q.state;
                 is.ng = q.ng;
                 is.abs = q.abs;
@@ -1040,6 +1112,7 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         d.in = make_input(&q.in);
         d.meta = q.meta;
         d.bal = ((q.in.in_flags & PAC_IN_MASKS) == 0 && q.in.hash_mode == PAC_HASH_BALANCED) ? 1 : 0;
+        d.prune = ctx->opt_minmax_prune ? 1 : 0;
         const uint32_t G = q.in.n_groups;
         const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
         const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);

@@ -16,6 +16,7 @@ struct BatchQueryDev {
     int32_t n_slots, n_out;
     int32_t mode;  // 0: warp-private shared-memory states, 1: global atomics
     int32_t bal;   // balanced keyed masks: worlds 32..63 are the complements of 0..31
+    int32_t prune; // MIN/MAX bound pruning (rows that improve no world skip the update)
     SlotDev slot[kMaxSpecs];
     OutDev outs[kMaxSpecs];
     uint64_t *meta;

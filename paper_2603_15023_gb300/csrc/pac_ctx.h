@@ -22,6 +22,7 @@ struct pac_ctx {
     size_t pin_bytes = 0;
     cudaEvent_t pin_ev = nullptr;  // the last copy out of `pin`
     int64_t opt_agg_path = 0;
+    int64_t opt_minmax_prune = 1;
     int64_t last_path = 0;
     int64_t last_launches = 0;
     std::string last_error;

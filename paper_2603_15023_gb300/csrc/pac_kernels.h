@@ -74,6 +74,7 @@ cudaError_t launch_select(const InputDev &in, const SelectDev &sel, const SelTab
 // ---- approximate integer SUM / AVG (Sec. 5 "Approximation") -------------
 constexpr int kApxLevels = 25;
 constexpr int kApxChunk = 4096;
+constexpr int kApxBlockChunks = 16;  // chunks per CTA of the cascade kernel (first tree levels)
 // One (chunk-block, group) state: per side 25 levels x 32 packed words
 // (world l in the low 16 bits, world l+32 in the high 16 bits) and 25
 // level totals.

@@ -129,8 +129,29 @@ def small(seed: int, n: int, n_groups: int, n_keys: int, vdtype=np.int64,
     return Workload("small", n, n_groups, keys, gids, [vals], {"n_keys": n_keys})
 
 
+def max_1g(seed: int = 0, n: int = 1_000_000_000, n_keys: int = 10_000_000,
+           order: str = "random") -> Workload:
+    """Sec. 6 MAX experiment shape: 1G rows, ungrouped, one int64 value column.
+    order "random": values uniform in [0, 1e12]; "increasing": value = row
+    index, the adversarial input of bound pruning for MAX (every row raises
+    every world it belongs to)."""
+    keys = uniform_i64(seed, 0, n, 0, n_keys - 1)
+    if order == "increasing":
+        vals = np.arange(n, dtype=np.int64)
+    else:
+        vals = uniform_i64(seed, 1, n, 0, 10**12)
+    return Workload("max_1g" if order == "random" else "max_1g_" + order, n, 1, keys, None, [vals],
+                    {"n_keys": n_keys, "order": order})
+
+
+def max_1g_increasing(seed: int = 0, n: int = 1_000_000_000) -> Workload:
+    return max_1g(seed, n, order="increasing")
+
+
 WORKLOADS = {
     "ungrouped_1m": ungrouped_1m,
+    "max_1g": max_1g,
+    "max_1g_increasing": max_1g_increasing,
     "lowcard_60m": lowcard_60m,
     "select_60m": lowcard_60m,   # the same columns, read under a PAC selection
     "lowcard_60m_approx": lowcard_60m,  # the same columns, approximate SUM / AVG
