@@ -18,19 +18,20 @@
 // packed as the low and high halves of one 32-bit word per level (a half can
 // never carry into the other: each half is bounded by the level total, which
 // stays <= 0xFFFF); lane k < 25 holds the level-k totals of both sides in
-// registers.  A CTA holds an aligned block of 16 chunks of one group (grid
-// y = group, so a group with few rows frees its SM early) and does the first
-// tree levels in shared memory; the remaining levels run one launch per level
+// registers.  A CTA holds an aligned block of 16 chunks of one group (so a
+// group with few rows frees its SM early) and does the first tree levels in
+// shared memory; the remaining levels run one launch per level
 // over the block states in global memory.
 //
 // Row loop: the lanes of a 32-row batch compute their rows' side, level and
 // level units in parallel; the warp then walks the group's rows in order.
-// Per side, the level of the latest update is "open": its counters since the
-// last commit sit in a register (acc) and its exact total in a uniform
-// register (ct).  A row of the open level whose units still fit under the cap
-// only adds to those registers; any other row commits them to the level state
-// and takes the full update with its flush chain.  Every flush decision reads
-// exact totals, so the state equals the row-by-row definition.
+// Per side, the levels of the two latest slow updates are "open": their
+// counters since the last commit sit in registers (acc) and their exact
+// totals in uniform registers (ct).  A row of an open level whose units still
+// fit under the cap only adds to those registers; any other row commits both
+// to the level state and takes the full update with its flush chain.  Every
+// flush decision reads exact totals, so the state equals the row-by-row
+// definition.
 #include "pac_internal.cuh"
 #include "pac_kernels.h"
 
@@ -105,14 +106,14 @@ __device__ __forceinline__ void apx_combine(ApxState *dst, const ApxState *src, 
     apx_store_totals(dst, t0, t1, lane);
 }
 
-// The open level of one side (see the row loop above).
+// One open level of one side (see the row loop above).
 struct ApxOpen {
     uint32_t acc;  // this lane's packed counters added since the last commit
-    uint32_t ct;   // the open level's exact total (uniform)
-    int cl;        // the open level, -1 when none (uniform)
+    uint32_t ct;   // the level's exact total (uniform)
+    int cl;        // the level, -1 when none (uniform)
 };
 
-// Writes the open level back: counters into the level state, total into the
+// Writes an open level back: counters into the level state, total into the
 // lane that holds it.
 __device__ __forceinline__ void apx_commit(ApxSide *s, uint32_t &t, ApxOpen &o, int lane) {
     if (o.cl >= 0) {
@@ -125,54 +126,86 @@ __device__ __forceinline__ void apx_commit(ApxSide *s, uint32_t &t, ApxOpen &o, 
 }
 
 // One nonzero value of one side: x units at level l, this lane's world bits.
-__device__ __forceinline__ void apx_row(ApxSide *s, uint32_t &t, ApxOpen &o, int l, uint32_t x, uint32_t b0,
-                                        uint32_t b1, int lane, bool &ovf) {
+// oa holds the latest slow update's level, ob the one before.
+__device__ __forceinline__ void apx_row(ApxSide *s, uint32_t &t, ApxOpen &oa, ApxOpen &ob, int l, uint32_t x,
+                                        uint32_t b0, uint32_t b1, int lane, bool &ovf) {
     const uint32_t add = x * b0 + ((x * b1) << 16);
-    if (l == o.cl && o.ct + x <= kCap) {  // no flush: the update stays in registers
-        o.acc += add;
-        o.ct += x;
+    if (l == oa.cl && oa.ct + x <= kCap) {  // no flush: the update stays in registers
+        oa.acc += add;
+        oa.ct += x;
         return;
     }
-    apx_commit(s, t, o, lane);
+    if (l == ob.cl && ob.ct + x <= kCap) {
+        ob.acc += add;
+        ob.ct += x;
+        return;
+    }
+    const int keep = l == oa.cl ? ob.cl : oa.cl;  // the other recent level stays open
+    apx_commit(s, t, oa, lane);
+    apx_commit(s, t, ob, lane);
     if (lvl_total(t, l) + x > kCap) apx_flush(s, t, l, lane, ovf);
-    o.cl = l;
-    o.ct = lvl_total(t, l) + x;
-    o.acc = add;
+    oa.cl = l;
+    oa.ct = lvl_total(t, l) + x;
+    oa.acc = add;
+    const int kb = keep != l ? keep : -1;
+    const uint32_t tb = lvl_total(t, kb < 0 ? 0 : kb);
+    ob.cl = kb;
+    ob.ct = tb;
 }
 
-__global__ void __launch_bounds__(32 * kApxBlockChunks) k_apx_chunks(const __grid_constant__ ApxParams p) {
+__global__ void __launch_bounds__(32 * kApxBlockChunks, 2) k_apx_chunks(const __grid_constant__ ApxParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ApxState *sm = reinterpret_cast<ApxState *>(smem_raw);
     const int lane = threadIdx.x & 31, ci = threadIdx.x >> 5;
     const uint32_t G = p.in.n_groups;
-    const uint32_t g = blockIdx.y;
-    const uint64_t chunk = static_cast<uint64_t>(blockIdx.x) * kApxBlockChunks + ci;
+    // consecutive CTAs: the groups of one block of chunks (its group ids are
+    // read once from HBM, then from L2)
+    const uint32_t g = blockIdx.x % G;
+    const uint64_t blk = blockIdx.x / G;
+    const uint64_t chunk = blk * kApxBlockChunks + ci;
     ApxState *st = sm + ci;
     apx_zero(st, lane);
     uint32_t t0 = 0, t1 = 0;
-    ApxOpen o0{0, 0, -1}, o1{0, 0, -1};
+    ApxOpen o0{0, 0, -1}, p0{0, 0, -1}, o1{0, 0, -1}, p1{0, 0, -1};
     bool ovf = false;
     uint64_t rows_g = 0;
     if (chunk < p.n_chunks) {
         const uint64_t lo = chunk * kApxChunk;
         const uint64_t hi = min(p.in.n, lo + kApxChunk);
-        // group ids one batch ahead, so that their load overlaps the row walk
-        uint32_t gid_next = lo + lane < hi ? row_gid(p.in, lo + lane) : 0u;
+        // loads run ahead of the row walk: group ids two batches ahead, keys
+        // and values of this group's rows one batch ahead
+        const bool keys_in = (p.in.in_flags & PAC_IN_MASKS) == 0;
+        uint32_t gid_n1 = lo + lane < hi ? row_gid(p.in, lo + lane) : 0u;
+        uint32_t gid_n2 = lo + 32 + lane < hi ? row_gid(p.in, lo + 32 + lane) : 0u;
+        long long v_n1 = 0;
+        uint64_t km_n1 = 0;
+        if (lo + lane < hi && gid_n1 == g) {
+            v_n1 = row_i64(p.values, lo + lane);
+            km_n1 = __ldg(static_cast<const unsigned long long *>(p.in.km) + lo + lane);
+        }
         for (uint64_t base = lo; base < hi; base += 32) {
             const uint64_t row = base + lane;
             bool valid = row < hi;
-            const uint32_t gid = gid_next;
-            if (base + 32 + lane < hi) gid_next = row_gid(p.in, base + 32 + lane);
-            long long v = 0;
+            const uint32_t gid = gid_n1;
+            long long v = v_n1;
+            const uint64_t km = km_n1;
+            gid_n1 = gid_n2;
+            v_n1 = 0;
+            km_n1 = 0;
+            if (row + 32 < hi && gid_n1 == g) {
+                v_n1 = row_i64(p.values, row + 32);
+                km_n1 = __ldg(static_cast<const unsigned long long *>(p.in.km) + row + 32);
+            }
+            gid_n2 = row + 64 < hi ? row_gid(p.in, row + 64) : 0u;
             uint64_t mask = 0;
             if (valid) {
                 if (gid >= G && g == 0) raise_status(p.status, kStatusBadGroup);
                 if (gid == g) {
-                    v = row_i64(p.values, row);
-                    mask = row_mask(p.in, row);
+                    mask = keys_in ? keyed_world_mask(static_cast<long long>(km), p.in.qkey, p.in.hash_mode) : km;
                     if (drop_row(p.in, mask)) valid = false;
                 }
             }
+            if (!valid || gid != g) v = 0;
             const uint32_t mine = __ballot_sync(kFull, valid && gid == g);
             rows_g += __popc(mine);
             const uint32_t todo = __ballot_sync(kFull, valid && gid == g && v != 0);
@@ -191,13 +224,15 @@ __global__ void __launch_bounds__(32 * kApxBlockChunks) k_apx_chunks(const __gri
                 const uint32_t b1 = (__shfl_sync(kFull, mhi, r) >> lane) & 1u;
                 const uint32_t x = q & 0xFFFu;
                 const int l = static_cast<int>((q >> 12) & 31u);
-                if (q >> 17) apx_row(&st->side[1], t1, o1, l, x, b0, b1, lane, ovf);
-                else apx_row(&st->side[0], t0, o0, l, x, b0, b1, lane, ovf);
+                if (q >> 17) apx_row(&st->side[1], t1, o1, p1, l, x, b0, b1, lane, ovf);
+                else apx_row(&st->side[0], t0, o0, p0, l, x, b0, b1, lane, ovf);
             }
         }
     }
     apx_commit(&st->side[0], t0, o0, lane);
+    apx_commit(&st->side[0], t0, p0, lane);
     apx_commit(&st->side[1], t1, o1, lane);
+    apx_commit(&st->side[1], t1, p1, lane);
     apx_store_totals(st, t0, t1, lane);
     if (lane == 0 && rows_g) atomicAdd(reinterpret_cast<unsigned long long *>(p.ng + g), rows_g);
     __syncthreads();
@@ -209,7 +244,7 @@ __global__ void __launch_bounds__(32 * kApxBlockChunks) k_apx_chunks(const __gri
     }
     if (ci == 0) {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(st);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(p.states + static_cast<size_t>(blockIdx.x) * G + g);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(p.states + static_cast<size_t>(blk) * G + g);
         for (int k = lane; k < static_cast<int>(sizeof(ApxState) / 4); k += 32) dst[k] = src[k];
     }
     if (ovf && lane == 0) raise_status(p.status, kStatusOverflow);
@@ -282,7 +317,7 @@ cudaError_t launch_approx(const ApxParams &pin, void *out_sum, void *out_avg, cu
         const size_t smem = static_cast<size_t>(kApxBlockChunks) * sizeof(ApxState);
         e = cudaFuncSetAttribute(k_apx_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        k_apx_chunks<<<dim3(static_cast<unsigned>(n_blocks), G), 32 * kApxBlockChunks, smem, s>>>(p);
+        k_apx_chunks<<<static_cast<unsigned>(n_blocks * G), 32 * kApxBlockChunks, smem, s>>>(p);
         (*launches)++;
         for (uint64_t width = 1; width < n_blocks; width *= 2) {
             const uint64_t pairs = (n_blocks + 2 * width - 1) / (2 * width);

@@ -107,11 +107,13 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
     q.fin_mode = -1;
     q.meta = meta;
     // one query: work items small enough that every SM gets a few (a
-    // power of two from 4K rows up to the default size)
+    // power of two from 4K rows up to the default size), and no more than
+    // 2048 of them, since the merge reads one partial state per item
     BatchConfig cfg = kBatchDefault;
     const uint64_t per_slot = in->n / (static_cast<uint64_t>(ctx->n_sms) * 4);
     uint32_t rows = 4096;
     while (rows < per_slot && rows < cfg.item_rows) rows <<= 1;
+    while (in->n / rows > 2048 && rows < (1u << 30)) rows <<= 1;
     cfg.item_rows = rows;
     pac_batch *b = nullptr;
     pac_status st = plan_build(ctx, &q, 1, cfg, &b);

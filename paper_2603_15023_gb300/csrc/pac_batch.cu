@@ -200,11 +200,74 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
     }
 }
 
+// One lane's row as loaded from HBM, before the group check and the hash.
+// The warp-private item loop of the run-time signature fetches the next
+// 32-row batch into one of these while it folds the current one, so the
+// loads' latency overlaps the work (the compile-time signatures keep
+// load_row: their register budget has no room for a second batch).
+template <int NS>
+struct RawLane {
+    uint32_t gid;
+    uint64_t km;        // key, or world mask with PAC_IN_MASKS
+    uint64_t vals[NS];  // slot value patterns
+};
+
+template <int NS, int SIG>
+__device__ __forceinline__ void fetch_lane(const ItemShared &is, uint64_t row, uint64_t end, RawLane<NS> &r) {
+    r.gid = 0;
+    r.km = 0;
+#pragma unroll
+    for (int s = 0; s < NS; s++) r.vals[s] = 0;
+    if (row >= end) return;
+    r.gid = row_gid(is.in, row);
+    r.km = __ldg(static_cast<const unsigned long long *>(is.in.km) + row);
+#pragma unroll
+    for (int s = 0; s < NS; s++)
+        if (s < nslots_of<SIG>(is)) r.vals[s] = load_slot_value(is.slot[s], row);
+}
+
+// load_row's checks on a fetched lane: group range, world mask, dropped rows,
+// running sums of |v|.
+template <int NS, int SIG>
+__device__ __forceinline__ void finish_lane(const ItemShared &is, const RawLane<NS> &r, bool &valid, uint32_t &gid,
+                                            uint64_t &mask, uint64_t (&vals)[NS], uint64_t (&my_abs)[NS],
+                                            uint32_t *status) {
+    gid = 0;
+    mask = 0;
+    if (valid) {
+        if (r.gid >= is.in.n_groups) {
+            raise_status(status, kStatusBadGroup);
+            valid = false;
+        } else {
+            mask = (is.in.in_flags & PAC_IN_MASKS) ? r.km
+                                                    : keyed_world_mask(static_cast<long long>(r.km), is.in.qkey,
+                                                                       is.in.hash_mode);
+            if (drop_row(is.in, mask)) valid = false;
+            else gid = r.gid;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        vals[s] = 0;
+        if (s < nslots_of<SIG>(is) && valid) {
+            vals[s] = r.vals[s];
+            if (op_of<SIG>(is, s) == OP_ISUM) {
+                const long long v = static_cast<long long>(vals[s]);
+                const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
+                const uint64_t t = my_abs[s] + a;
+                my_abs[s] = t < a ? ~0ull : t;
+            }
+        }
+    }
+    if (!valid) mask = 0;
+}
+
 // One run's contributions for this lane: worlds j (index 0) and j+32 (1).
 template <int NS>
 struct RunAcc {
     uint32_t c0, c1;         // counts (c1 unused with bal)
     uint32_t n;              // rows in the run (uniform)
+    uint32_t loop;           // rows the broadcast loop visited (uniform; 0: MIN/MAX states are identities)
     uint64_t a0[NS], a1[NS]; // slot states of worlds j and j+32 (a1 unused for int64 SUM with bal)
     uint64_t tot[NS];        // int64 SUM totals over the run (uniform)
 };
@@ -262,6 +325,7 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
     const uint32_t M0 = T0 & R;
     const uint32_t M1 = bal ? (R & ~T0) : (T1 & R);
     ra.n = __popc(R);
+    ra.loop = L;
     ra.c0 = __popc(M0);
     ra.c1 = __popc(M1);
     bool any_loop = false;
@@ -301,7 +365,9 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
             any_loop = true;
         }
     }
-    if (!any_loop || L == 0) return;
+    // fixed signatures hold no MIN/MAX slot, so their loop covers R (kept
+    // literal: a separate mask there doubles the kernels' register count)
+    if (!any_loop || (SIG == 0 && L == 0)) return;
     // broadcast loop over the rows of L for the remaining slots; float sums
     // fold 8-row blocks into a compensated pair
     float fs0[NS], fc0[NS], fb0[NS], fs1[NS], fc1[NS], fb1[NS];
@@ -323,7 +389,7 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
         }
     } else {
         int blk = 0;
-        for (uint32_t rr = L; rr; rr &= rr - 1) {
+        for (uint32_t rr = SIG != 0 ? R : L; rr; rr &= rr - 1) {
             loop_row<NS, SIG>(is, __ffs(rr) - 1, M0, M1, bal, vals, sliced, ra, fb0, fb1);
             if (++blk == 8) {
                 blk = 0;
@@ -349,6 +415,10 @@ __device__ __forceinline__ void run_fold(const ItemShared &is, uint32_t R, uint3
 // States kept as worlds 0..31 + total with balanced masks (exact integers).
 __device__ __forceinline__ bool by_complement(int op, bool bal) { return bal && op == OP_ISUM; }
 
+__device__ __forceinline__ bool is_minmax(int op) {
+    return op == OP_IMIN || op == OP_IMAX || op == OP_FMIN || op == OP_FMAX;
+}
+
 // True when one row's value v would replace a MIN/MAX state st (the test of
 // op_update): MAX takes strictly greater values, MIN strictly smaller ones,
 // floats by IEEE comparison (a NaN value replaces nothing).
@@ -363,22 +433,30 @@ __device__ __forceinline__ bool mm_improves(int op, uint64_t v, uint64_t st) {
 
 constexpr uint32_t kPruneMinRun = 8;  // shorter runs visit every row
 
-// MIN/MAX bound pruning (Sec. 5 "Pruning"): the bound g is the weakest of
-// the 64 world states of the run's group (the smallest maximum for MAX, the
-// largest minimum for MIN).  A value that does not improve g improves no
-// world, so its row is left out of the broadcast loop.  The bound is read
-// from the sink's state at every run of at least kPruneMinRun rows (the
-// paper refreshes it every 2048 updates); a stale bound is weaker, never
-// wrong, because states only move towards the extreme.  Returns the rows
-// the loop must visit: R itself unless every loop-type slot is MIN/MAX.
+// The bounds of one group, kept by a warp across the runs of an item.
+template <int NS>
+struct PruneCache {
+    uint32_t g = 0xFFFFFFFFu;  // group the bounds belong to; none when all ones
+    uint64_t b[NS];            // per slot, this lane's copy of the bound
+};
+
+// MIN/MAX bound pruning (Sec. 5 "Pruning"): the bound is the weakest of the
+// 64 world states of the run's group (the smallest maximum for MAX, the
+// largest minimum for MIN).  A value that does not improve the bound
+// improves no world, so its row is left out of the broadcast loop.  The
+// bound is read from the sink's state (a warp reduction over the 64 worlds)
+// when the cache holds none for the group, and dropped after a run in which
+// some row survived, since the state may have moved (the paper refreshes it
+// every 2048 updates).  A stale bound is weaker, never wrong: states only
+// move towards the extreme.  Returns the rows the loop must visit: R itself
+// unless every loop-type slot is MIN/MAX.
 template <int NS, int SIG, typename Sink>
 __device__ __forceinline__ uint32_t prune_rows(const ItemShared &is, uint32_t R, uint32_t g,
                                                const uint64_t (&vals)[NS], const int (&slice)[NS],
-                                               Sink &sink, int lane) {
+                                               Sink &sink, PruneCache<NS> &pc, int lane) {
     if (SIG != 0 || !is.prune) return R;  // compile-time signatures hold no MIN/MAX slot
     const uint32_t n = __popc(R);
     if (n < kPruneMinRun) return R;
-    uint32_t keep = 0;
     bool any_mm = false;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
@@ -389,31 +467,52 @@ __device__ __forceinline__ uint32_t prune_rows(const ItemShared &is, uint32_t R,
             return R;
         }
         if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) return R;
-        uint64_t b0, b1;
-        if (!sink.bound(g, s, lane, b0, b1)) return R;
-        uint64_t b = mm_improves(op, b0, b1) ? b1 : b0;  // the weaker of this lane's two worlds
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const uint64_t other = __shfl_xor_sync(kFull, b, o);
-            b = mm_improves(op, b, other) ? other : b;
-        }
-        keep |= __ballot_sync(kFull, ((R >> lane) & 1u) && mm_improves(op, vals[s], b));
         any_mm = true;
     }
-    return any_mm ? keep : R;
+    if (!any_mm) return R;
+    if (pc.g != g) {
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            if (s >= is.n_slots) continue;
+            const int op = is.slot[s].op;
+            if (!is_minmax(op)) continue;
+            uint64_t b0, b1;
+            if (!sink.bound(g, s, lane, b0, b1)) return R;
+            uint64_t b = mm_improves(op, b0, b1) ? b1 : b0;  // the weaker of this lane's two worlds
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const uint64_t other = __shfl_xor_sync(kFull, b, o);
+                b = mm_improves(op, b, other) ? other : b;
+            }
+            pc.b[s] = b;
+        }
+        pc.g = g;
+    }
+    uint32_t keep = 0;
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (s >= is.n_slots) continue;
+        const int op = is.slot[s].op;
+        if (is_minmax(op)) keep |= __ballot_sync(kFull, ((R >> lane) & 1u) && mm_improves(op, vals[s], pc.b[s]));
+    }
+    if (keep) pc.g = 0xFFFFFFFFu;  // the state moves: read the bound again next time
+    return keep;
 }
 
 // Processes rows [base, base+32) of the item: transposes, finds the runs and
-// hands every run to `sink(g, ra)`.
+// hands every run to `sink(g, ra)`.  With `pre` the rows were fetched
+// already; otherwise they are loaded here.
 template <int NS, int SIG, typename Sink>
 __device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, uint64_t end, uint64_t (&my_abs)[NS],
-                                         uint32_t *status, Sink &sink) {
+                                         uint32_t *status, Sink &sink, PruneCache<NS> &pc,
+                                         const RawLane<NS> *pre = nullptr) {
     const int lane = threadIdx.x & 31;
     const uint64_t row = base + lane;
     bool valid = row < end;
     uint32_t gid;
     uint64_t mask, vals[NS];
-    load_row<NS, SIG>(is, row, valid, gid, mask, vals, my_abs, status);
+    if (pre) finish_lane<NS, SIG>(is, *pre, valid, gid, mask, vals, my_abs, status);
+    else load_row<NS, SIG>(is, row, valid, gid, mask, vals, my_abs, status);
     const bool bal = is.bal != 0;
     const uint32_t T0 = warp_transpose32(valid ? static_cast<uint32_t>(mask) : 0u, lane);
     const uint32_t T1 = bal ? 0u : warp_transpose32(valid ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
@@ -435,7 +534,7 @@ __device__ __forceinline__ void batch32w(const ItemShared &is, uint64_t base, ui
         const uint32_t R = __ballot_sync(kFull, valid && gid == g);
         pending &= ~R;
         RunAcc<NS> ra;
-        const uint32_t L = prune_rows<NS, SIG>(is, R, g, vals, slice, sink, lane);
+        const uint32_t L = prune_rows<NS, SIG>(is, R, g, vals, slice, sink, pc, lane);
         run_fold<NS, SIG>(is, R, L, T0, T1, bal, vals, slice, lane, ra);
         sink(g, ra, lane, bal);
     }
@@ -457,6 +556,7 @@ struct SmemSink {
         for (int s = 0; s < NS; s++) {
             if (s >= nslots_of<SIG>(is)) continue;
             const int op = op_of<SIG>(is, s);
+            if (is_minmax(op) && !ra.loop) continue;  // identities: nothing to merge
             uint64_t *sst = st + (static_cast<size_t>(s + 1) * G + g) * kWorlds;
             op_merge(op, sst[lane], ra.a0[s]);
             if (!by_complement(op, bal)) op_merge(op, sst[lane + 32], ra.a1[s]);
@@ -508,6 +608,7 @@ __device__ __forceinline__ void run_merge(const ItemShared &is, RunAcc<NS> &a, c
     a.c0 += b.c0;
     a.c1 += b.c1;
     a.n += b.n;
+    a.loop |= b.loop;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         if (s >= nslots_of<SIG>(is)) continue;
@@ -516,7 +617,7 @@ __device__ __forceinline__ void run_merge(const ItemShared &is, RunAcc<NS> &a, c
             a.a0[s] += b.a0[s];
             a.a1[s] += b.a1[s];
             a.tot[s] += b.tot[s];
-        } else {
+        } else if (!is_minmax(op) || b.loop) {
             op_merge(op, a.a0[s], b.a0[s]);
             op_merge(op, a.a1[s], b.a1[s]);
         }
@@ -578,9 +679,22 @@ __device__ void item_warp_private(const ItemShared &is, unsigned char *smem_raw,
 #pragma unroll
     for (int s = 0; s < NS; s++) my_abs[s] = 0;
     SmemSink<NS, SIG> sink{is, st, ng, G};
-    for (uint64_t base = is.row0 + static_cast<uint64_t>(warp) * 32; base < is.row_end;
-         base += static_cast<uint64_t>(n_warps) * 32)
-        batch32w<NS, SIG>(is, base, is.row_end, my_abs, status, sink);
+    PruneCache<NS> pc;
+    const uint64_t stride = static_cast<uint64_t>(n_warps) * 32;
+    uint64_t base = is.row0 + static_cast<uint64_t>(warp) * 32;
+    if (SIG == 0 && NS <= 4) {
+        // the next batch is fetched before the current one is folded
+        RawLane<NS> cur;
+        fetch_lane<NS, SIG>(is, base + lane, is.row_end, cur);
+        for (; base < is.row_end; base += stride) {
+            RawLane<NS> nxt;
+            fetch_lane<NS, SIG>(is, base + stride + lane, is.row_end, nxt);
+            batch32w<NS, SIG>(is, base, is.row_end, my_abs, status, sink, pc, &cur);
+            cur = nxt;
+        }
+    } else {
+        for (; base < is.row_end; base += stride) batch32w<NS, SIG>(is, base, is.row_end, my_abs, status, sink, pc);
+    }
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         uint64_t m = my_abs[s];
@@ -633,6 +747,7 @@ __device__ void item_atomic(const ItemShared &is, uint32_t *status) {
 #pragma unroll
     for (int s = 0; s < NS; s++) my_abs[s] = 0;
     CarrySink<NS, SIG> sink{AtomicSink<NS, SIG>{is, G}, is};
+    PruneCache<NS> pc;
     // each warp takes one contiguous stretch of the item, so group runs of
     // the group-ordered rows stay long within a warp
     const uint64_t span = is.row_end > is.row0 ? is.row_end - is.row0 : 0;
@@ -640,7 +755,7 @@ __device__ void item_atomic(const ItemShared &is, uint32_t *status) {
     const uint64_t w0 = is.row0 + static_cast<uint64_t>(warp) * per_warp;
     const uint64_t w1 = min(is.row_end, w0 + per_warp);
     ItemShared const &isr = is;
-    for (uint64_t base = w0; base < w1; base += 32) batch32w<NS, SIG>(isr, base, w1, my_abs, status, sink);
+    for (uint64_t base = w0; base < w1; base += 32) batch32w<NS, SIG>(isr, base, w1, my_abs, status, sink, pc);
     sink.flush(lane, is.bal != 0);
     // int64 SUM guard: the wrapping atomics are exact while the query's total
     // of |v| stays below 2^63, which bounds every world's sum
