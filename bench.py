@@ -571,7 +571,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     ctx = B.pac_create(local)
     if args.path:
-        B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2, "engine": 3}[args.path])
+        B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2, "engine": 3, "small": 4}[args.path])
     B.pac_set_option(ctx, "minmax_prune", args.minmax_prune)
 
     wcfg = WORKLOADS[args.workload]
@@ -775,12 +775,15 @@ def run_ours(args):
     achieved = algo_bytes / (agg_mean / 1e3) / 1e9
     path_name = {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
                  3: "per-bit engine (rows partitioned by group first when the groups' states exceed "
-                    "shared memory)"}.get(path, str(path))
+                    "shared memory)",
+                 4: "one launch on CUDA cores (warp bit-transpose, int128 sums, last CTA writes the outputs)"
+                 }.get(path, str(path))
     kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
               2: ("k_select_prep + k_select + k_agg_mma + k_mma_finish (all launches of pac_aggregate_select)"
                   if sel is not None else "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
               3: "k_batch_agg + k_batch_merge, after k_part_hist + k_part_scan + k_part_scatter when the "
-                 "rows are partitioned by group (all launches of pac_aggregate_multi)"}.get(path, str(path))
+                 "rows are partitioned by group (all launches of pac_aggregate_multi)",
+              4: "k_small_agg (the only launch of pac_aggregate_multi)"}.get(path, str(path))
     if wcfg.get("approx"):
         # the exact specs (COUNT and the row counts) take `path`; each distinct
         # value column of an approximate spec runs one cascade
@@ -839,7 +842,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lowcard_60m", choices=sorted(WORKLOADS))
     ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
-    ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma", "engine"])
+    ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma", "engine", "small"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--minmax-prune", type=int, default=1, choices=[0, 1],
                     help="MIN/MAX bound pruning on the per-bit engine (results are identical either way)")

@@ -109,7 +109,12 @@ const char *pac_status_string(pac_status s);
 /* Synchronises `stream`, returns (and clears) the device status word:
  * PAC_OK, PAC_E_OVERFLOW, PAC_E_TIMEOUT, or PAC_E_INVALID when a group id
  * was >= n_groups or a selection's operand id was >= n_thr (such rows are
- * skipped / keep no world, never read or written out of bounds). */
+ * skipped / keep no world, never read or written out of bounds).
+ * PAC_E_OVERFLOW: an exact int64 SUM did not fit.  The tensor-core and
+ * one-launch paths (agg_path 2 and 4) keep 128-bit totals: a SUM that does
+ * not fit is saturated to INT64_MIN / INT64_MAX, and AVG is still the exact
+ * total over the count.  The per-bit kernels keep 64-bit partial sums; after
+ * an overflow report their SUM and AVG outputs are unspecified. */
 pac_status pac_sync_status(pac_ctx *ctx, pac_stream stream);
 
 /* Host-only: the per-query hash key K (Sec. 4.2: drawn independently per
@@ -495,17 +500,22 @@ pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_spec *specs,
 
 /* ---------------------------------------------------------------------------
  * Path selection and introspection (for benchmarks and tests).
- *   pac_set_option(ctx, name, value): "agg_path" 0 = automatic (tensor-core
- *   path where it applies, else the per-bit engine), 1 = force the plain
- *   per-bit CUDA-core kernels, 2 = force the tensor-core path
- *   (PAC_E_UNSUPPORTED where it cannot serve), 3 = force the per-bit engine
- *   (warp bit-transpose; the engine of the batched path).
+ *   pac_set_option(ctx, name, value): "agg_path" 0 = automatic (the
+ *   one-launch path for ungrouped COUNT / exact int64 SUM / AVG queries of at
+ *   most 8M rows, the tensor-core path where it applies, else the per-bit
+ *   engine), 1 = force the plain per-bit CUDA-core kernels, 2 = force the
+ *   tensor-core path (PAC_E_UNSUPPORTED where it cannot serve), 3 = force the
+ *   per-bit engine (warp bit-transpose; the engine of the batched path),
+ *   4 = force the one-launch path (one group, COUNT / exact int64 SUM / AVG
+ *   over at most 4 value columns, any row count; PAC_E_UNSUPPORTED
+ *   otherwise).  The one-launch path keeps its accumulators in the context,
+ *   so calls on one context must not overlap.
  *   "minmax_prune" 1 (default) = MIN/MAX bound pruning on the per-bit
  *   engine (Sec. 5 "Pruning": rows whose value improves no world's current
  *   extreme skip the update; results are identical), 0 = every row updated.
  *   Plans built by pac_batch_plan take the setting current at plan time.
  *   pac_get_info(ctx, name, &value): "last_path" (1 plain per-bit, 2 tensor
- *   core, 3 per-bit engine), "last_launches" kernels launched by the last
+ *   core, 3 per-bit engine, 4 one-launch), "last_launches" kernels launched by the last
  *   call.
  * ------------------------------------------------------------------------ */
 pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value);

@@ -285,7 +285,7 @@ __global__ void k_apx_emit(const __grid_constant__ ApxParams p, long long *out_s
     if (out_sum) out_sum[cell] = fits ? static_cast<long long>(v) : (v < 0 ? (-0x7fffffffffffffffll - 1) : 0x7fffffffffffffffll);
     if (out_avg) {
         const uint64_t ng = p.ng[g];
-        const double dv = fits ? static_cast<double>(static_cast<long long>(v)) : static_cast<double>(v);
+        const double dv = i128_to_double(v);
         out_avg[cell] = ng ? 2.0 * dv / static_cast<double>(ng) : 0.0;
     }
 }

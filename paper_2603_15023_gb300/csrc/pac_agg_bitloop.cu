@@ -338,7 +338,7 @@ __global__ void k_bitloop_merge(const __grid_constant__ BitloopParams p, int n_p
             if (!fits) raise_status(p.status, kStatusOverflow);
             const long long v = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
             if (o.kind == PAC_SUM) static_cast<long long *>(o.out)[cell] = v;
-            else static_cast<double *>(o.out)[cell] = cnt ? static_cast<double>(v) / static_cast<double>(cnt) : 0.0;
+            else static_cast<double *>(o.out)[cell] = cnt ? i128_to_double(tot) / static_cast<double>(cnt) : 0.0;
         } else if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
             double total;
             if (atomic) {

@@ -10,6 +10,7 @@
 #include "pac_internal.cuh"
 #include "pac_kernels.h"
 #include "pac_mma.h"
+#include "pac_small.h"
 #include "pac_validate.h"
 #include "pac_batch.h"
 
@@ -200,12 +201,19 @@ pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
     pac_status st;
     ctx->last_launches = 0;
     // The tensor-core path serves COUNT and exact int64 SUM/AVG over few
-    // groups; the per-bit engine serves everything else; agg_path 1 forces the
-    // plain per-bit kernels (the baseline the other paths are measured against).
+    // groups, the one-launch path the same specs of small ungrouped queries;
+    // the per-bit engine serves everything else; agg_path 1 forces the plain
+    // per-bit kernels (the baseline the other paths are measured against).
     const int want = static_cast<int>(ctx->opt_agg_path);
-    bool mma_ok = (want == 0 || want == 2) && mma_supported(in, specs, n_specs);
+    const bool small_ok = (want == 0 || want == 4) && small_supported(in, specs, n_specs) &&
+                          (want == 4 || in->n <= kSmallAutoRows);
+    if (want == 4 && !small_ok) return fail(ctx, PAC_E_UNSUPPORTED, "one-launch path cannot serve this query");
+    bool mma_ok = !small_ok && (want == 0 || want == 2) && mma_supported(in, specs, n_specs);
     if (want == 2 && !mma_ok) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path cannot serve this query");
-    if (mma_ok) {
+    if (small_ok) {
+        st = run_small(ctx, in, specs, n_specs, meta, stream, &launches);
+        if (st != PAC_OK) return st;
+    } else if (mma_ok) {
         st = run_mma(ctx, in, specs, n_specs, meta, stream, &launches);
         if (st != PAC_OK) return st;
         ctx->last_path = 2;
@@ -298,6 +306,7 @@ void pac_destroy(pac_ctx *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->qws) cudaFree(ctx->qws);
     if (ctx->sws) cudaFree(ctx->sws);
+    if (ctx->small_acc) cudaFree(ctx->small_acc);
     if (ctx->pin_ev) {
         cudaEventSynchronize(ctx->pin_ev);
         cudaEventDestroy(ctx->pin_ev);
@@ -567,7 +576,10 @@ pac_status pac_query_host(pac_ctx *ctx, const pac_input *in_h, const pac_agg_spe
     // when every column is pinned host memory, that kernel reads the columns
     // where they are (the same bytes cross the host link, without a staging
     // copy in front of the aggregation).
-    bool direct = n > 0 && (ctx->opt_agg_path == 0 || ctx->opt_agg_path == 2) && mma_supported(in_h, specs_h, n_specs);
+    const int64_t want = ctx->opt_agg_path;
+    bool direct = n > 0 && (((want == 0 || want == 2) && mma_supported(in_h, specs_h, n_specs)) ||
+                            ((want == 0 || want == 4) && small_supported(in_h, specs_h, n_specs) &&
+                             (want == 4 || n <= kSmallAutoRows)));
     for (int i = 0; i < n_specs && direct; i++) direct = !spec_is_cascade(specs_h[i]);
     auto pinned = [](const void *p) {
         cudaPointerAttributes a{};
@@ -639,7 +651,7 @@ pac_status pac_query_host(pac_ctx *ctx, const pac_input *in_h, const pac_agg_spe
 pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value) {
     if (!ctx || !name) return PAC_E_INVALID;
     if (strcmp(name, "agg_path") == 0) {
-        if (value < 0 || value > 3) return fail(ctx, PAC_E_INVALID, "agg_path %lld", static_cast<long long>(value));
+        if (value < 0 || value > 4) return fail(ctx, PAC_E_INVALID, "agg_path %lld", static_cast<long long>(value));
         ctx->opt_agg_path = value;
         return PAC_OK;
     }

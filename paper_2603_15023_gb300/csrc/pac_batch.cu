@@ -1095,7 +1095,7 @@ __global__ void __launch_bounds__(256) k_batch_merge(const BatchQueryDev *__rest
             if (!fits) raise_status(status, kStatusOverflow);
             const long long v = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
             if (o.kind == PAC_SUM) static_cast<long long *>(o.out)[local] = v;
-            else static_cast<double *>(o.out)[local] = cnt ? static_cast<double>(v) / static_cast<double>(cnt) : 0.0;
+            else static_cast<double *>(o.out)[local] = cnt ? i128_to_double(tot) / static_cast<double>(cnt) : 0.0;
         } else if (op == OP_FSUM_COMP || op == OP_FSUM_PLAIN) {
             double total;
             if (atomic) {

@@ -17,6 +17,7 @@ struct pac_ctx {
     size_t qws_bytes = 0;
     void *sws = nullptr;  // selection: sorted operand tables, selected masks
     size_t sws_bytes = 0;
+    void *small_acc = nullptr;  // one-launch path: accumulators, zero between calls
     uint32_t *d_status = nullptr;
     void *pin = nullptr;  // pinned staging of per-bit engine descriptors
     size_t pin_bytes = 0;

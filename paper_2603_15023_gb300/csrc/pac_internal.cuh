@@ -36,6 +36,27 @@ __host__ __device__ __forceinline__ uint64_t mm3_fmix64(uint64_t x) {
     return x;
 }
 
+// An int128 integer as the nearest double (ties to even), as the IEEE
+// conversion defines it: within int64 the hardware conversion; beyond, the
+// top 53 bits of the magnitude rounded on the bits below them, then scaled
+// by a power of two (exact).
+__device__ __forceinline__ double i128_to_double(__int128 x) {
+    if (x >= -static_cast<__int128>(0x7fffffffffffffffll) - 1 && x <= static_cast<__int128>(0x7fffffffffffffffll))
+        return static_cast<double>(static_cast<long long>(x));
+    const bool neg = x < 0;
+    const unsigned __int128 m = neg ? static_cast<unsigned __int128>(0) - static_cast<unsigned __int128>(x)
+                                    : static_cast<unsigned __int128>(x);
+    const unsigned long long hi = static_cast<unsigned long long>(m >> 64), lo = static_cast<unsigned long long>(m);
+    const int msb = hi ? 127 - __clzll(static_cast<long long>(hi)) : 63 - __clzll(static_cast<long long>(lo));
+    const int sh = msb - 52;  // >= 11: |x| >= 2^63
+    unsigned long long mant = static_cast<unsigned long long>(m >> sh);
+    const unsigned __int128 rem = m - (static_cast<unsigned __int128>(mant) << sh);
+    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) mant++;  // mant <= 2^53: still exact
+    const double d = ldexp(static_cast<double>(mant), sh);
+    return neg ? -d : d;
+}
+
 __host__ __device__ __forceinline__ uint64_t keyed_world_mask(int64_t key, uint64_t qkey,
                                                               int mode) {
     const uint64_t h = mm3_fmix64(mm3_fmix64(static_cast<uint64_t>(key)) ^ qkey);

@@ -813,7 +813,7 @@ __global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
         if (!fits) raise_status(f.status, kStatusOverflow);
         const long long val = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
         if (f.out_kind[s] == PAC_SUM) static_cast<long long *>(f.out[s])[cell] = val;
-        else static_cast<double *>(f.out[s])[cell] = cnt ? static_cast<double>(val) / static_cast<double>(cnt) : 0.0;
+        else static_cast<double *>(f.out[s])[cell] = cnt ? i128_to_double(tot) / static_cast<double>(cnt) : 0.0;
     }
 }
 

@@ -357,3 +357,29 @@ def test_engine_bad_group_ids_skipped_and_reported(ctx, G):
         ref, mn, mo, _ = orc.aggregate(masks, None if v is None else v[keep], gids[keep], G, kind)
         np.testing.assert_array_equal(g_out, ref)
     np.testing.assert_array_equal(meta[:, 0], mn)
+
+
+@pytest.mark.parametrize("path", [1, 2, 3, 4])
+def test_avg_exact_when_the_sum_overflows(ctx, path):
+    """A world's int64 SUM that does not fit is reported (PAC_E_OVERFLOW) on
+    every path.  The tensor-core and one-launch paths keep 128-bit totals:
+    there the SUM is saturated and the AVG is still the exact sum over the
+    count (the int128 total rounded to the nearest double, then divided: the
+    oracle's reading).  The per-bit kernels keep 64-bit partial sums, so only
+    the report and the counts are defined there."""
+    n = 20_000
+    r = np.random.default_rng(path)
+    G = 1 if path == 4 else 3
+    keys = r.integers(0, 5000, n).astype(np.int64)
+    gids = None if G == 1 else r.integers(0, G, n).astype(np.uint8)
+    vals = (2**62 + r.integers(0, 2**40, n)).astype(np.int64)
+    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals), (B.PAC_AVG, 0, vals)]
+    qk = orc.query_key(path)
+    got, _, st = ctx.aggregate(keys, gids, G, specs, qkey=qk, path=path)
+    assert st == B.PAC_E_OVERFLOW
+    assert ctx.last_path == path
+    masks = orc.hash_keys(keys, qk, orc.BALANCED)
+    checked = specs if path in (2, 4) else specs[:1]
+    for (kind, _, v), g_out in zip(checked, got):
+        ref, *_ = orc.aggregate(masks, v, gids, G, kind)
+        np.testing.assert_array_equal(g_out, ref)
