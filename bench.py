@@ -106,22 +106,24 @@ def _source_sha(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:12]
 
 
-def _traffic(workload: str, n: int):
+def _traffic(workload: str, n: int, path: int):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summaries (a `bench-traffic:` line), scaled to n rows; None when no
-    capture exists or the kernel source changed since it was taken."""
-    pat = re.compile(r"bench-traffic:\s*workload=(\S+)\s+kernel_source=(\S+)\s+sha=(\S+)\s+bytes_per_row=([0-9.]+)")
+    summaries (a `bench-traffic:` line for the workload and aggregation path,
+    path 2 when the line names none), scaled to n rows; None when no capture
+    exists or the kernel source changed since it was taken."""
+    pat = re.compile(r"bench-traffic:\s*workload=(\S+)\s+(?:path=(\d+)\s+)?kernel_source=(\S+)\s+sha=(\S+)"
+                     r"\s+bytes_per_row=([0-9.]+)")
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(f) as fh:
             for line in fh:
                 m = pat.search(line)
-                if m and m.group(1) == workload:
+                if m and m.group(1) == workload and int(m.group(2) or 2) == path:
                     try:
-                        if _source_sha(m.group(2)) != m.group(3):
+                        if _source_sha(m.group(3)) != m.group(4):
                             return None
                     except OSError:
                         return None
-                    return float(m.group(4)) * n
+                    return float(m.group(5)) * n
     return None
 
 
@@ -811,7 +813,7 @@ def run_ours(args):
                        "agg_path": path_name,
                        **({"minmax_prune": bool(args.minmax_prune)} if "max" in wcfg["aggs"] else {})},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": _traffic(args.workload, n) if path == 2 else None,
+                         "frac": achieved / peak, "traffic": _traffic(args.workload, n, path),
                          "kernel": kernel, "algorithmic_bytes": algo_bytes, "peak_source": peak_src,
                          "agg_ms": agg_mean, "agg_ms_min": min(agg_ms)},
             "cpu_baseline": cpu,

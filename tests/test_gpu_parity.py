@@ -383,3 +383,59 @@ def test_avg_exact_when_the_sum_overflows(ctx, path):
     for (kind, _, v), g_out in zip(checked, got):
         ref, *_ = orc.aggregate(masks, v, gids, G, kind)
         np.testing.assert_array_equal(g_out, ref)
+
+
+def test_highcard_100m_full_size_sampled(ctx):
+    """The 100M-row, 1M-group Zipf workload at full size, in the launch
+    configuration the benchmark times (automatic path: rows partitioned by
+    group, then the per-bit engine).  Sampled groups (the largest, a middle
+    and a tail one) against the oracle on exactly their rows; every group
+    against the balanced invariants (worlds j and j+32 split the group's rows
+    and its value total)."""
+    w = inputs.highcard_100m(seed=0)
+    G = w.n_groups
+    qk = orc.query_key(0)
+    v = w.values[0]
+    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, v)]
+    got, meta, st = ctx.aggregate(w.keys, w.gids, G, specs, qkey=qk)
+    assert st == B.PAC_OK
+    assert ctx.last_path == 3
+    for g in (0, 4321, G - 1):
+        rows = np.flatnonzero(w.gids == g)
+        masks = orc.hash_keys(w.keys[rows], qk, orc.BALANCED)
+        c, mn, mo, _ = orc.aggregate(masks, None, None, 1, B.PAC_COUNT)
+        s, *_ = orc.aggregate(masks, v[rows], None, 1, B.PAC_SUM)
+        np.testing.assert_array_equal(got[0][g], c[0])
+        np.testing.assert_array_equal(got[1][g], s[0])
+        assert int(meta[g, 0]) == int(mn[0]) and int(meta[g, 1]) == int(mo[0])
+    ng = np.bincount(w.gids, minlength=G).astype(np.int64)
+    tot = np.bincount(w.gids, weights=v.astype(np.float64), minlength=G)  # per-group sums < 2^53: exact
+    np.testing.assert_array_equal(meta[:, 0].astype(np.int64), ng)
+    cnt = got[0].astype(np.int64)
+    assert np.all(cnt[:, :32] + cnt[:, 32:] == ng[:, None])
+    assert np.all(got[1][:, :32] + got[1][:, 32:] == tot.astype(np.int64)[:, None])
+
+
+def test_lowcard_60m_approx_full_size_bound(ctx):
+    """The paper's approximate SUM / AVG on the 60M-row headline columns at
+    full size, in the benchmark's launch configuration: for sampled worlds,
+    each approximate SUM lies under the exact one (from the oracle) by at most
+    the cascade's truncation bound, sum |v| (2^-8 + 25 * 2^-11.9) (values are
+    positive, so only the positive side is used), and AVG is 2 S / n_g of the
+    SUM the kernel wrote (bit-exact)."""
+    w = inputs.lowcard_60m(seed=0)
+    qk = orc.query_key(0)
+    specs = [(B.PAC_COUNT, 0, None)] + [(B.PAC_SUM, B.PAC_APPROX, v) for v in w.values] + \
+            [(B.PAC_AVG, B.PAC_APPROX, v) for v in w.values]
+    got, meta, st = ctx.aggregate(w.keys, w.gids, 4, specs, qkey=qk)
+    assert st == B.PAC_OK
+    masks = orc.hash_keys(w.keys, qk, orc.BALANCED)
+    ng = meta[:, 0].astype(np.float64)
+    for k, v in enumerate(w.values):
+        approx = got[1 + k]
+        np.testing.assert_array_equal(got[5 + k], np.where(ng[:, None] > 0, 2.0 * approx / ng[:, None], 0.0))
+        for j in (0, 17, 40, 63):
+            exact, _ = orc.aggregate_world(masks, v, w.gids, 4, B.PAC_SUM, j)
+            bound = exact.astype(np.float64) * (2.0**-8 + 25 * 2.0**-11.9)
+            diff = exact - approx[:, j]
+            assert np.all(diff >= 0) and np.all(diff <= bound), (k, j)
