@@ -161,21 +161,25 @@ __global__ void __launch_bounds__(kSmallWarps * 32) k_small_agg(const __grid_con
             const uint32_t vlo = static_cast<uint32_t>(v);
             if (!__any_sync(kFull, (static_cast<unsigned long long>(v) >> 32) != 0)) {
                 // non-negative values below 2^32: bit-sliced.  Horner from the
-                // top bit down, in 32 bits while the planes fit (32 rows x
-                // 2^26 < 2^31), the rest in 64
+                // top bit plane down (the plane's bit is the sign of x, which
+                // shifts left), in 32 bits while the planes fit (32 rows x
+                // 2^26 < 2^31), above that in 64
                 const uint32_t orv = __reduce_or_sync(kFull, vlo);
                 const int bits = orv ? 32 - __clz(static_cast<int>(orv)) : 0;
+                uint32_t x = bits ? vlo << (32 - bits) : 0u;
                 unsigned long long h0 = 0, h1 = 0;
-                int k = bits - 1;
-                for (; k >= 26; k--) {
-                    const uint32_t vb = __ballot_sync(kFull, (vlo >> k) & 1u);
+                int k = bits;
+                for (; k > 26; k--) {
+                    const uint32_t vb = __ballot_sync(kFull, static_cast<int>(x) < 0);
+                    x <<= 1;
                     h0 = 2 * h0 + __popc(T0 & vb);
                     h1 = 2 * h1 + __popc(T1 & vb);
                 }
                 uint32_t p0 = 0, p1 = 0;
 #pragma unroll 4
-                for (; k >= 0; k--) {
-                    const uint32_t vb = __ballot_sync(kFull, (vlo >> k) & 1u);
+                for (; k > 0; k--) {
+                    const uint32_t vb = __ballot_sync(kFull, static_cast<int>(x) < 0);
+                    x <<= 1;
                     p0 = 2 * p0 + __popc(T0 & vb);
                     p1 = 2 * p1 + __popc(T1 & vb);
                 }
