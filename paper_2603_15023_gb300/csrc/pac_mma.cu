@@ -776,10 +776,17 @@ struct FinishParams {
 };
 
 // Digit totals -> COUNT / SUM / AVG per (group, world), metadata per group.
+// One thread per (value column, cell), cells fastest: a column's 16 digit
+// totals are read once and serve its SUM and AVG specs; the column-0 threads
+// also write COUNT and the metadata.
 __global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
-    const size_t cell = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
-    const bool live = cell < static_cast<size_t>(f.G) * kWorlds;
-    const uint32_t g = live ? static_cast<uint32_t>(cell / kWorlds) : 0;
+    const size_t cells = static_cast<size_t>(f.G) * kWorlds;
+    const int cp = f.n_cols > 0 ? f.n_cols : 1;
+    const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    const bool live = t < cells * cp;
+    const int c = live ? static_cast<int>(t / cells) : 0;
+    const size_t cell = live ? t % cells : 0;
+    const uint32_t g = static_cast<uint32_t>(cell / kWorlds);
     const int j = static_cast<int>(cell % kWorlds);
     // digit total k of this cell; under balanced keys world 32 + j is the
     // group total (row 32) minus world j, exactly (wrapping 64-bit integers)
@@ -791,30 +798,37 @@ __global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
         return static_cast<long long>(derive ? tot_row[k] - low_row[k] : a[k]);
     };
     const unsigned long long cnt = live ? static_cast<unsigned long long>(digit(0)) : 0ull;
+    // a warp holds 32 consecutive cells of one column (cells is a multiple of 64)
     const unsigned bal = __ballot_sync(kFull, live && cnt > 0);
-    if (f.meta && live) {
-        if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(f.meta + 2 * g + 1)[j >= 32 ? 1 : 0] = bal;
-        if (j == 0) f.meta[2 * g] = f.ng[g];
-    }
     if (!live) return;
+    if (c == 0) {
+        if (f.meta) {
+            if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(f.meta + 2 * g + 1)[j >= 32 ? 1 : 0] = bal;
+            if (j == 0) f.meta[2 * g] = f.ng[g];
+        }
+        for (int s = 0; s < f.n_out; s++)
+            if (f.out_kind[s] == PAC_COUNT) static_cast<unsigned long long *>(f.out[s])[cell] = cnt;
+    }
+    if (f.n_cols == 0) return;
+    long long dq[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        const int feat = f.c4 == 1 ? 4 + q : 4 + q * f.c4 + c;
+        dq[q] = feat < f.n_alloc ? digit(feat) : 0;
+    }
+    __int128 tot = 0;
+#pragma unroll
+    for (int q = 15; q >= 0; q--) tot = tot * 16 + dq[q];
+    const bool fits = tot >= static_cast<__int128>(LLONG_MIN) && tot <= static_cast<__int128>(LLONG_MAX);
+    const long long val = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
+    bool used = false;
     for (int s = 0; s < f.n_out; s++) {
-        if (f.out_kind[s] == PAC_COUNT) {
-            static_cast<unsigned long long *>(f.out[s])[cell] = cnt;
-            continue;
-        }
-        const int c = f.out_col[s];
-        __int128 tot = 0;
-        for (int q = 15; q >= 0; q--) {
-            const int feat = f.c4 == 1 ? 4 + q : 4 + q * f.c4 + c;
-            const long long dq = feat < f.n_alloc ? digit(feat) : 0;
-            tot = tot * 16 + dq;
-        }
-        const bool fits = tot >= static_cast<__int128>(LLONG_MIN) && tot <= static_cast<__int128>(LLONG_MAX);
-        if (!fits) raise_status(f.status, kStatusOverflow);
-        const long long val = fits ? static_cast<long long>(tot) : (tot < 0 ? LLONG_MIN : LLONG_MAX);
+        if (f.out_kind[s] == PAC_COUNT || f.out_col[s] != c) continue;
+        used = true;
         if (f.out_kind[s] == PAC_SUM) static_cast<long long *>(f.out[s])[cell] = val;
         else static_cast<double *>(f.out[s])[cell] = cnt ? i128_to_double(tot) / static_cast<double>(cnt) : 0.0;
     }
+    if (used && !fits) raise_status(f.status, kStatusOverflow);
 }
 
 int mma_c4(int C) { return C == 1 ? 1 : 4; }
@@ -969,8 +983,8 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
         f.out[f.n_out] = specs[i].out;
         f.n_out++;
     }
-    const size_t cells = static_cast<size_t>(G) * kWorlds;
-    k_mma_finish<<<static_cast<unsigned>((cells + 255) / 256), 256, 0, stream>>>(f);
+    const size_t threads = static_cast<size_t>(G) * kWorlds * (C > 0 ? C : 1);
+    k_mma_finish<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, stream>>>(f);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         *why = cudaGetErrorString(e);
