@@ -159,6 +159,38 @@ def test_sum_overflow_is_reported(orc):
     assert st == 4 and s[0, 0] == np.iinfo(np.int64).max
 
 
+def test_avg_of_an_overflowing_sum_is_the_rounded_exact_quotient(orc):
+    """AVG = s_j / c_j on the exact sum even when s_j leaves int64 (reading
+    R3): the 128-bit sum rounded once to the nearest double (ties to even),
+    then one IEEE division.  Python's integers give the exact sum and its
+    int -> float conversion rounds to nearest, ties to even; a sum whose low
+    bits sit exactly on a tie and one just past it check the rounding."""
+    rng = np.random.default_rng(12)
+    n = 40
+    masks = rng.integers(0, 2**63, n, dtype=np.int64).astype(np.uint64) * np.uint64(2) + np.uint64(1)
+    v = (2**62 + rng.integers(0, 2**20, n)).astype(np.int64)
+    v[0] = 2**62 + 2**10          # with 2^62 x 39 others: sums whose 11 low bits decide the rounding
+    a, _, _, st = orc.aggregate(masks, v, None, 1, orc.AVG)
+    assert st == 0  # AVG itself fits; the SUM of the same worlds overflows
+    s, _, _, st_s = orc.aggregate(masks, v, None, 1, orc.SUM)
+    assert st_s == 4
+    for j in range(64):
+        rows = [i for i in range(n) if (int(masks[i]) >> j) & 1]
+        if not rows:
+            assert a[0, j] == 0.0
+            continue
+        exact = sum(int(v[i]) for i in rows)
+        assert a[0, j] == float(exact) / float(len(rows)), j
+    # the conversion itself: 2^63 + 1024 is a tie between 2^63 and 2^63 + 2048
+    # (ties to even: 2^63); 2^63 + 1025 rounds up
+    ties = np.array([2**62, 2**62 + 1024], dtype=np.int64)
+    up = np.array([2**62, 2**62 + 1025], dtype=np.int64)
+    one = np.array([np.uint64(1), np.uint64(1)])
+    at, *_ = orc.aggregate(one, ties, None, 1, orc.AVG)
+    au, *_ = orc.aggregate(one, up, None, 1, orc.AVG)
+    assert at[0, 0] == float(2**63) / 2.0 and au[0, 0] == float(2**63 + 2048) / 2.0
+
+
 def test_single_world_matches_all_worlds(orc):
     w = inputs.small(9, 30000, 4, 2000, vlo=-10**6, vhi=10**6)
     masks = orc.hash_keys(w.keys, orc.query_key(9), orc.RAW)
