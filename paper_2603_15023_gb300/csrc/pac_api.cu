@@ -290,7 +290,8 @@ pac_status pac_create(pac_ctx **out, int device) {
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
-        cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
+        cudaStreamSynchronize(0) != cudaSuccess) {  // cleared before any stream of the caller reads it
         cudaGetLastError();
         if (ctx->d_status) cudaFree(ctx->d_status);
         delete ctx;

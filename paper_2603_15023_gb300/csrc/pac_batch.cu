@@ -1426,6 +1426,10 @@ pac_status build_owned_plan(pac_ctx *ctx, const pac_query *qs, int n, const Batc
     plan_bind(b, dbuf);
     b->d_status = ctx->d_status;
     e = cudaMemcpy(static_cast<char *>(dbuf) + b->image_off, b->image.data(), b->image.size(), cudaMemcpyHostToDevice);
+    // a copy from pageable memory may still be in flight on the legacy
+    // stream when cudaMemcpy returns; the plan may be launched on a
+    // non-blocking stream, which is not ordered after it
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
         plan_destroy(b);
         return cuda_fail(ctx, e, "batch plan upload");

@@ -299,8 +299,14 @@ bool small_supported(const pac_input *in, const pac_agg_spec *specs, int n_specs
 pac_status run_small(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
                      cudaStream_t stream, int *launches) {
     if (!ctx->small_acc) {
-        PAC_CUDA(ctx, cudaMalloc(&ctx->small_acc, sizeof(SmallAcc)));
-        PAC_CUDA(ctx, cudaMemset(ctx->small_acc, 0, sizeof(SmallAcc)));  // the kernel leaves it zero
+        if (cudaMalloc(&ctx->small_acc, sizeof(SmallAcc)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->small_acc = nullptr;
+            return fail(ctx, PAC_E_NOMEM, "one-launch path: %zu bytes of accumulators", sizeof(SmallAcc));
+        }
+        // cleared on the caller's stream, ahead of the first kernel (every
+        // kernel leaves the accumulators zero again)
+        PAC_CUDA(ctx, cudaMemsetAsync(ctx->small_acc, 0, sizeof(SmallAcc), stream));
     }
     SmallParams p{};
     const void *cols[kSmallCols];
