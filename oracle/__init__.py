@@ -78,6 +78,11 @@ def lib() -> ctypes.CDLL:
             "orc_select": (i32, [vp, vp, i32, i32, vp, u32, vp, i32, sz, vp]),
             "orc_lift": (i32, [vp, vp, u32, u32, vp, i32, vp]),
             "orc_filter": (None, [vp, u32, u64, vp]),
+            "orc_query_key2": (u64, [u64]),
+            "orc_hash_keys128": (None, [vp, sz, u64, u64, i32, vp]),
+            "orc_aggregate128": (i32, [vp, vp, i32, vp, i32, sz, u32, i32, vp, vp, vp]),
+            "orc_aggregate_brute128": (i32, [vp, u64, u64, i32, vp, i32, vp, i32, sz, u32, i32, vp]),
+            "orc_finalize128": (None, [vp, vp, u32, u32, vp, vp, u64, dbl, i32, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -294,3 +299,67 @@ def finalize(y: np.ndarray, scales, meta_n: np.ndarray, meta_or: np.ndarray, see
                        ctypes.byref(js))
     return {"noised": noised, "is_null": is_null, "flags": flags, "posterior": post,
             "jstar": js.value}
+
+
+# -- m = 128 worlds (reading R7 of pac_oracle.c; Sec. 2 says m = 128 is possible) --
+
+def query_key2(seed: int) -> int:
+    """The second per-query key: the SplitMix64 output after K."""
+    return lib().orc_query_key2(seed)
+
+
+def hash_keys128(keys: np.ndarray, k1: int, k2: int, mode: int = BALANCED) -> np.ndarray:
+    """[n, 2] uint64 world masks over 128 worlds (world j: bit j % 64 of word j // 64)."""
+    keys = np.ascontiguousarray(keys, dtype=np.int64)
+    out = np.empty((keys.shape[0], 2), dtype=np.uint64)
+    lib().orc_hash_keys128(_p(keys), keys.shape[0], k1, k2, mode, _p(out))
+    return out
+
+
+def aggregate128(masks2: np.ndarray, values: Optional[np.ndarray], gids: Optional[np.ndarray],
+                 n_groups: int, kind: int):
+    """Exact definition over 128 worlds, row by row.  Returns (out[n_groups,128],
+    n_g, or_g[n_groups,2], status)."""
+    masks2 = np.ascontiguousarray(masks2, dtype=np.uint64).reshape(-1, 2)
+    values = None if values is None else np.ascontiguousarray(values)
+    vt = _vtype(values)
+    g, gb = _gid_args(gids)
+    out = np.zeros((n_groups, 128), dtype=_out_dtype(kind, vt))
+    mn = np.zeros(n_groups, dtype=np.uint64)
+    mo = np.zeros((n_groups, 2), dtype=np.uint64)
+    st = lib().orc_aggregate128(_p(masks2), _p(values), vt, _p(g), gb, masks2.shape[0], n_groups, kind,
+                                _p(out), _p(mn), _p(mo))
+    return out, mn, mo, st
+
+
+def aggregate_brute128(keys: np.ndarray, k1: int, k2: int, mode: int, values: Optional[np.ndarray],
+                       gids: Optional[np.ndarray], n_groups: int, kind: int):
+    """Same definition over 128 materialised subsamples.  Returns (out, status)."""
+    keys = np.ascontiguousarray(keys, dtype=np.int64)
+    values = None if values is None else np.ascontiguousarray(values)
+    vt = _vtype(values)
+    g, gb = _gid_args(gids)
+    out = np.zeros((n_groups, 128), dtype=_out_dtype(kind, vt))
+    st = lib().orc_aggregate_brute128(_p(keys), k1, k2, mode, _p(values), vt, _p(g), gb, keys.shape[0],
+                                      n_groups, kind, _p(out))
+    return out, st
+
+
+def finalize128(y: np.ndarray, scales, meta_n: np.ndarray, meta_or2: np.ndarray, seed: int,
+                budget: float, mode: int = ADAPTIVE):
+    """y: [n_groups, n_specs, 128] unscaled results; meta_or2 [n_groups, 2]."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n_groups, n_specs = y.shape[0], y.shape[1]
+    scales = np.ascontiguousarray(np.asarray(scales, dtype=np.float64))
+    assert scales.shape == (n_specs,) and y.shape[2] == 128
+    meta_n = np.ascontiguousarray(meta_n, dtype=np.uint64)
+    meta_or2 = np.ascontiguousarray(meta_or2, dtype=np.uint64).reshape(n_groups, 2)
+    nc = n_groups * n_specs
+    noised = np.zeros(nc, dtype=np.float64)
+    is_null = np.zeros(nc, dtype=np.uint8)
+    flags = np.zeros(nc, dtype=np.uint32)
+    post = np.zeros(128, dtype=np.float64)
+    js = ctypes.c_int32(0)
+    lib().orc_finalize128(_p(y), _p(scales), n_specs, n_groups, _p(meta_n), _p(meta_or2), seed, budget, mode,
+                          _p(noised), _p(is_null), _p(flags), _p(post), ctypes.byref(js))
+    return {"noised": noised, "is_null": is_null, "flags": flags, "posterior": post, "jstar": js.value}

@@ -39,6 +39,15 @@
  *       worlds ever received an update (Sec. 5 "Diversity Check").  The OR
  *       accumulator of Sec. 3.2 is used (the XOR of Sec. 5 cannot say which
  *       worlds were never updated).
+ *   R7  m = 128 worlds (Sec. 2 says m = 128 is possible; the paper runs 64):
+ *       two keyed re-hashes of the engine hash, h_a with K and h_b with K2,
+ *       the SplitMix64 output after K.  Balanced: worlds 0..31 are the low
+ *       word of h_a, 32..63 the low word of h_b, 64..127 the complement of
+ *       0..63 (every PU in exactly 64 worlds).  Raw: worlds 0..63 are h_a,
+ *       64..127 h_b.  The release is R5/R6 with 128 worlds: j* is the top 7
+ *       bits of the first draw, the prior is uniform over 128 worlds, a cell
+ *       is NULL with probability (128 - popcount(or_g))/128, and the
+ *       diversity flag needs at most 80 updated worlds (the same 5/8).
  */
 #include "pac_oracle.h"
 
@@ -745,4 +754,154 @@ void orc_finalize(const double *y, const double *scale, uint32_t n_specs,
     }
     if (posterior)
         for (int j = 0; j < 64; j++) posterior[j] = exp(logp[j]);
+}
+
+/* ====================================================================== */
+/* m = 128 worlds (reading R7).  The same definitions as above with a      */
+/* 128-bit world mask, one row at a time, one world at a time.             */
+/* ====================================================================== */
+
+uint64_t orc_query_key2(uint64_t seed) {
+    uint64_t s = seed ^ 0x5041435f4b455921ULL;
+    (void)orc_splitmix64_next(&s);      /* K */
+    return orc_splitmix64_next(&s);     /* K2 */
+}
+
+void orc_pac_hash128(int64_t key, uint64_t k1, uint64_t k2, int mode, uint64_t *out2) {
+    uint64_t inner = orc_fmix64((uint64_t)key);
+    uint64_t ha = orc_fmix64(inner ^ k1);
+    uint64_t hb = orc_fmix64(inner ^ k2);
+    if (mode == ORC_RAW) {
+        out2[0] = ha;
+        out2[1] = hb;
+        return;
+    }
+    uint64_t w0 = (ha & 0xffffffffULL) | ((hb & 0xffffffffULL) << 32);
+    out2[0] = w0;
+    out2[1] = ~w0;
+}
+
+void orc_hash_keys128(const int64_t *keys, size_t n, uint64_t k1, uint64_t k2, int mode,
+                      uint64_t *masks2) {
+    for (size_t i = 0; i < n; i++) orc_pac_hash128(keys[i], k1, k2, mode, masks2 + 2 * i);
+}
+
+static int world128(const uint64_t *m2, int j) { return (int)((m2[j >> 6] >> (j & 63)) & 1ULL); }
+
+int orc_aggregate128(const uint64_t *masks2, const void *values, int vtype, const void *gids,
+                     int gid_bytes, size_t n, uint32_t n_groups, int kind, void *out,
+                     uint64_t *meta_n, uint64_t *meta_or2) {
+    int status = 0;
+    acc_t *acc = (acc_t *)malloc(sizeof(acc_t) * (size_t)n_groups * 128);
+    if (!acc) return 2;
+    for (size_t k = 0; k < (size_t)n_groups * 128; k++) acc_init(&acc[k]);
+    if (meta_n) memset(meta_n, 0, sizeof(uint64_t) * n_groups);
+    if (meta_or2) memset(meta_or2, 0, sizeof(uint64_t) * 2 * n_groups);
+    for (size_t i = 0; i < n; i++) {
+        uint32_t g = gid_at(gids, gid_bytes, i);
+        const uint64_t *m2 = masks2 + 2 * i;
+        if (meta_n) meta_n[g] += 1;
+        if (meta_or2) {
+            meta_or2[2 * g] |= m2[0];
+            meta_or2[2 * g + 1] |= m2[1];
+        }
+        for (int j = 0; j < 128; j++)
+            if (world128(m2, j)) acc_update(&acc[(size_t)g * 128 + j], values, vtype, i);
+    }
+    for (size_t k = 0; k < (size_t)n_groups * 128; k++) acc_emit(&acc[k], vtype, kind, out, k, &status);
+    free(acc);
+    return status;
+}
+
+int orc_aggregate_brute128(const int64_t *keys, uint64_t k1, uint64_t k2, int mode, const void *values,
+                           int vtype, const void *gids, int gid_bytes, size_t n, uint32_t n_groups,
+                           int kind, void *out) {
+    int status = 0;
+    keyset universe;
+    if (!ks_init(&universe, n)) return 2;
+    for (size_t i = 0; i < n; i++) ks_insert(&universe, keys[i]);
+    acc_t *acc = (acc_t *)malloc(sizeof(acc_t) * n_groups);
+    if (!acc) { ks_free(&universe); return 2; }
+    for (int j = 0; j < 128; j++) {
+        /* step (1): the j-th sampled PU table */
+        keyset sample;
+        if (!ks_init(&sample, n)) { free(acc); ks_free(&universe); return 2; }
+        for (size_t p = 0; p < universe.cap; p++) {
+            if (!universe.used[p]) continue;
+            uint64_t h2[2];
+            orc_pac_hash128(universe.slot[p], k1, k2, mode, h2);
+            if (world128(h2, j)) ks_insert(&sample, universe.slot[p]);
+        }
+        /* step (2): the query on the j-th sampled instance */
+        for (uint32_t g = 0; g < n_groups; g++) acc_init(&acc[g]);
+        for (size_t i = 0; i < n; i++)
+            if (ks_contains(&sample, keys[i])) acc_update(&acc[gid_at(gids, gid_bytes, i)], values, vtype, i);
+        for (uint32_t g = 0; g < n_groups; g++) acc_emit(&acc[g], vtype, kind, out, (size_t)g * 128 + j, &status);
+        ks_free(&sample);
+    }
+    free(acc);
+    ks_free(&universe);
+    return status;
+}
+
+static void normalize_log128(double *logp) {
+    double mx = -INFINITY;
+    for (int j = 0; j < 128; j++) if (logp[j] > mx) mx = logp[j];
+    double s = 0.0;
+    for (int j = 0; j < 128; j++) s += exp(logp[j] - mx);
+    double lse = mx + log(s);
+    for (int j = 0; j < 128; j++) logp[j] -= lse;
+}
+
+void orc_finalize128(const double *y, const double *scale, uint32_t n_specs, uint32_t n_groups,
+                     const uint64_t *meta_n, const uint64_t *meta_or2, uint64_t seed, double budget,
+                     int mode, double *noised, uint8_t *is_null, uint32_t *flags, double *posterior,
+                     int32_t *jstar_out) {
+    int jstar = (int)(orc_rng_u64(seed, STREAM_JSTAR, 0) >> 57);   /* uniform on 0..127 */
+    if (jstar_out) *jstar_out = jstar;
+    double logp[128];
+    for (int j = 0; j < 128; j++) logp[j] = -log(128.0);
+    size_t n_cells = (size_t)n_groups * n_specs;
+    for (size_t c = 0; c < n_cells; c++) {
+        uint32_t g = (uint32_t)(c / n_specs);
+        uint32_t s = (uint32_t)(c % n_specs);
+        const uint64_t *orm = meta_or2 + 2 * g;
+        int pop = __builtin_popcountll(orm[0]) + __builtin_popcountll(orm[1]);
+        uint32_t f = 0;
+        if (meta_n[g] >= DIVERSITY_MIN_ROWS && pop <= 2 * DIVERSITY_MAX_WORLDS) f |= ORC_F_DIVERSITY;
+        if (mode == ORC_INDEPENDENT)
+            for (int j = 0; j < 128; j++) logp[j] = -log(128.0);
+        if (pop < 128 && (int)(orc_rng_u64(seed, STREAM_NULL, c) >> 57) < 128 - pop) {
+            noised[c] = 0.0; is_null[c] = 1; flags[c] = f | ORC_F_NULL;
+            continue;
+        }
+        is_null[c] = 0;
+        double yv[128];
+        for (int j = 0; j < 128; j++) yv[j] = world128(orm, j) ? scale[s] * y[c * 128 + j] : 0.0;
+        double p[128], mu = 0.0, var = 0.0;
+        int all_equal = 1;
+        for (int j = 0; j < 128; j++) p[j] = exp(logp[j]);
+        for (int j = 0; j < 128; j++)
+            if (p[j] > 0.0 && yv[j] != yv[jstar]) all_equal = 0;
+        for (int j = 0; j < 128; j++) mu += p[j] * yv[j];
+        for (int j = 0; j < 128; j++) var += p[j] * (yv[j] - mu) * (yv[j] - mu);
+        if (all_equal) var = 0.0;
+        double delta = var / (2.0 * budget);
+        double z = orc_box_muller(orc_rng_u64(seed, STREAM_NOISE, 2 * c),
+                                  orc_rng_u64(seed, STREAM_NOISE, 2 * c + 1));
+        double yt = yv[jstar] + sqrt(delta) * z;
+        noised[c] = yt;
+        if (delta > 0.0) {
+            for (int j = 0; j < 128; j++) {
+                double d = yt - yv[j];
+                logp[j] += -(d * d) / (2.0 * delta);
+            }
+            normalize_log128(logp);
+        } else {
+            f |= ORC_F_ZEROVAR;
+        }
+        flags[c] = f;
+    }
+    if (posterior)
+        for (int j = 0; j < 128; j++) posterior[j] = exp(logp[j]);
 }

@@ -173,7 +173,25 @@ double orc_u01_open0(uint64_t u);     /* (0,1] */
 double orc_u01(uint64_t u);           /* [0,1) */
 double orc_box_muller(uint64_t u1, uint64_t u2);
 
+/* m = 128 worlds (reading R7): masks are [n][2] words, world j in bit j % 64
+ * of word j / 64; outputs are [n_groups][128]; meta_or2 is [n_groups][2]. */
+uint64_t orc_query_key2(uint64_t seed);
+void orc_pac_hash128(int64_t key, uint64_t k1, uint64_t k2, int mode, uint64_t *out2);
+void orc_hash_keys128(const int64_t *keys, size_t n, uint64_t k1, uint64_t k2, int mode,
+                      uint64_t *masks2);
+int orc_aggregate128(const uint64_t *masks2, const void *values, int vtype, const void *gids,
+                     int gid_bytes, size_t n, uint32_t n_groups, int kind, void *out,
+                     uint64_t *meta_n, uint64_t *meta_or2);
+int orc_aggregate_brute128(const int64_t *keys, uint64_t k1, uint64_t k2, int mode, const void *values,
+                           int vtype, const void *gids, int gid_bytes, size_t n, uint32_t n_groups,
+                           int kind, void *out);
+void orc_finalize128(const double *y, const double *scale, uint32_t n_specs, uint32_t n_groups,
+                     const uint64_t *meta_n, const uint64_t *meta_or2, uint64_t seed, double budget,
+                     int mode, double *noised, uint8_t *is_null, uint32_t *flags, double *posterior,
+                     int32_t *jstar_out);
+
 #ifdef __cplusplus
 }
 #endif
+
 #endif
