@@ -161,7 +161,7 @@ def test_sum_overflow_is_reported(orc):
 
 def test_avg_of_an_overflowing_sum_is_the_rounded_exact_quotient(orc):
     """AVG = s_j / c_j on the exact sum even when s_j leaves int64 (reading
-    R3): the 128-bit sum rounded once to the nearest double (ties to even),
+    R4): the 128-bit sum rounded once to the nearest double (ties to even),
     then one IEEE division.  Python's integers give the exact sum and its
     int -> float conversion rounds to nearest, ties to even; a sum whose low
     bits sit exactly on a tie and one just past it check the rounding."""
