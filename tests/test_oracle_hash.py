@@ -5,7 +5,9 @@ pac_hash (Sec. 2 "SIMD-PAC-DB", Sec. 4.2 "PAC Hash") turns a PU key into a
 paper prints no hash value, so the pins are properties the paper fixes (each
 PU in exactly m/2 worlds under the balanced construction of Sec. 4.1, each
 world a 50% sample) plus properties of the published building blocks
-(fmix64 is a bijection with fmix64(0) = 0; SplitMix64's published outputs).
+(fmix64 is a bijection with fmix64(0) = 0; SplitMix64's published outputs;
+MurmurHash3_x64_128's published verification value, which runs through
+fmix64).
 """
 import os
 
@@ -48,6 +50,66 @@ def test_rng_is_splitmix64_by_stream_and_counter(orc):
             seq = _py_splitmix64(stream_state, 40)
             got = [orc.rng_u64(seed, stream, c) for c in range(40)]
             assert got == seq
+
+
+def _murmur3_x64_128(data, seed, fmix):
+    """MurmurHash3_x64_128 (Appleby) written from its published definition:
+    16-byte blocks mixed into two 64-bit lanes, the tail, the length, then
+    fmix64 on both lanes.  fmix is the finalizer under test."""
+    def rotl(x, r):
+        return ((x << r) | (x >> (64 - r))) & M64
+    c1, c2 = 0x87C37B91114253D5, 0x4CF5AD432745937F
+    n = len(data)
+    h1 = h2 = seed & 0xFFFFFFFF
+    nblocks = n // 16
+    for b in range(nblocks):
+        k1 = int.from_bytes(data[16 * b:16 * b + 8], "little")
+        k2 = int.from_bytes(data[16 * b + 8:16 * b + 16], "little")
+        h1 ^= (rotl((k1 * c1) & M64, 31) * c2) & M64
+        h1 = ((rotl(h1, 27) + h2) * 5 + 0x52DCE729) & M64
+        h2 ^= (rotl((k2 * c2) & M64, 33) * c1) & M64
+        h2 = ((rotl(h2, 31) + h1) * 5 + 0x38495AB5) & M64
+    tail = data[16 * nblocks:]
+    if len(tail) > 8:
+        k2 = int.from_bytes(tail[8:], "little")
+        h2 ^= (rotl((k2 * c2) & M64, 33) * c1) & M64
+    if len(tail) > 0:
+        k1 = int.from_bytes(tail[:8], "little")
+        h1 ^= (rotl((k1 * c1) & M64, 31) * c2) & M64
+    h1 ^= n
+    h2 ^= n
+    h1 = (h1 + h2) & M64
+    h2 = (h2 + h1) & M64
+    h1, h2 = fmix(h1), fmix(h2)
+    h1 = (h1 + h2) & M64
+    h2 = (h2 + h1) & M64
+    return h1.to_bytes(8, "little") + h2.to_bytes(8, "little")
+
+
+def _smhasher_verification(fmix):
+    """SMHasher's verification value: keys {0..i-1} with seed 256 - i, their
+    hashes concatenated and hashed with seed 0, first 4 bytes as uint32."""
+    key = bytes(range(256))
+    hashes = b"".join(_murmur3_x64_128(key[:i], 256 - i, fmix) for i in range(256))
+    return int.from_bytes(_murmur3_x64_128(hashes, 0, fmix)[:4], "little")
+
+
+def test_fmix64_known_answer_through_murmur3(orc):
+    """The oracle's fmix64 inside MurmurHash3_x64_128 reproduces the
+    verification value SMHasher publishes for that hash, so a mistyped
+    multiplier or shift in fmix64 cannot pass (the inverse-based pin below
+    cannot see one, since the inverse is built from the same constants)."""
+    expected = _golden_u64_hex("murmur3_x64_128_verification.txt")
+    assert _smhasher_verification(orc.fmix64) == expected
+    # the pin is sensitive: one flipped bit of fmix64's output changes it
+    assert _smhasher_verification(lambda k: orc.fmix64(k) ^ (1 << 17)) != expected
+
+
+def _golden_u64_hex(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        vals = [int(l, 16) for l in f if l.strip() and not l.startswith("#")]
+    assert len(vals) == 1
+    return vals[0]
 
 
 def test_fmix64_zero_and_inverse(orc):
