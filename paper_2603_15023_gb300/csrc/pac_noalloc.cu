@@ -23,6 +23,8 @@
 // (n_groups x features per group) x 64 worlds x 8-byte totals, the per-group
 // row counts and alignment: 263,168 bytes.
 static constexpr size_t kNoallocScratchBytes = 512 * 64 * 8 + 1024;
+static_assert(kNoallocScratchBytes >= pacgpu::kMmaMaxScratchBytes,
+              "the static scratch must hold the largest query the tensor-core path serves");
 
 // The scratch and the status word every call shares (one copy per GPU).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -50,7 +52,10 @@ void put_err(char *err, size_t err_len, const char *fmt, ...) {
 
 // Device addresses of the static arrays on the current device.  In host code
 // the arrays' names are host-side stand-ins, so the addresses come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// addresses are kept for the life of the process: after cudaDeviceReset the
+// module is loaded again and the arrays may move, so the entry point must not
+// be used across a device reset.
 pac_status device_setup(int dev, DeviceSlots &out, char *err, size_t err_len) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSlots &d = g_dev[dev];
@@ -70,6 +75,11 @@ pac_status device_setup(int dev, DeviceSlots &out, char *err, size_t err_len) {
     }
     out = d;
     return PAC_OK;
+}
+
+pac_status cuda_fail(char *err, size_t err_len) {
+    put_err(err, err_len, "%s", cudaGetErrorString(cudaGetLastError()));
+    return PAC_E_CUDA;
 }
 
 }  // namespace
@@ -99,20 +109,23 @@ extern "C" pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_s
             return PAC_E_INVALID;
         }
     }
-    const cudaStream_t st = stream;
-    if (in->n == 0) {  // every output is zero
-        for (int i = 0; i < n_specs; i++)
-            if (cudaMemsetAsync(specs[i].out, 0, static_cast<size_t>(in->n_groups) * 64 * 8, st) != cudaSuccess)
-                return PAC_E_CUDA;
-        if (meta && cudaMemsetAsync(meta, 0, static_cast<size_t>(in->n_groups) * 16, st) != cudaSuccess)
-            return PAC_E_CUDA;
-        return cudaStreamSynchronize(st) == cudaSuccess ? PAC_OK : PAC_E_CUDA;
-    }
-    if (!pacgpu::mma_supported(in, specs, n_specs)) {
+    // the same specs and group counts are served whatever the row count
+    if (!pacgpu::mma_specs_served(in->n_groups, specs, n_specs)) {
         put_err(err, err_len,
                 "only COUNT and exact int64 SUM/AVG over at most 4 value columns and 8 groups are served here");
         return PAC_E_UNSUPPORTED;
     }
+    const cudaStream_t st = stream;
+    if (in->n == 0) {  // every output is zero
+        for (int i = 0; i < n_specs; i++)
+            if (cudaMemsetAsync(specs[i].out, 0, static_cast<size_t>(in->n_groups) * 64 * 8, st) != cudaSuccess)
+                return cuda_fail(err, err_len);
+        if (meta && cudaMemsetAsync(meta, 0, static_cast<size_t>(in->n_groups) * 16, st) != cudaSuccess)
+            return cuda_fail(err, err_len);
+        return cudaStreamSynchronize(st) == cudaSuccess ? PAC_OK : cuda_fail(err, err_len);
+    }
+    // cannot trigger with the limits above (see the static_assert); kept so
+    // that a later change of those limits cannot overrun the array
     const size_t need = pacgpu::mma_scratch_bytes(in, specs, n_specs);
     if (need > kNoallocScratchBytes) {
         put_err(err, err_len, "query needs %zu bytes of scratch; the static limit is %zu", need,
@@ -127,7 +140,7 @@ extern "C" pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_s
     DeviceSlots d;
     pac_status ps = device_setup(dev, d, err, err_len);
     if (ps != PAC_OK) return ps;
-    if (cudaMemsetAsync(d.status, 0, sizeof(uint32_t), st) != cudaSuccess) return PAC_E_CUDA;
+    if (cudaMemsetAsync(d.status, 0, sizeof(uint32_t), st) != cudaSuccess) return cuda_fail(err, err_len);
     int launches = 0;
     const char *why = "";
     ps = pacgpu::mma_launch(in, specs, n_specs, meta, st, d.scratch, d.status, d.n_sms, &launches, &why);
@@ -141,11 +154,17 @@ extern "C" pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_s
         put_err(err, err_len, "%s", cudaGetErrorString(cudaGetLastError()));
         return PAC_E_CUDA;
     }
-    if (h & pacgpu::kStatusTimeout) return PAC_E_TIMEOUT;
+    if (h & pacgpu::kStatusTimeout) {
+        put_err(err, err_len, "a bounded device wait gave up; the outputs are incomplete");
+        return PAC_E_TIMEOUT;
+    }
     if (h & pacgpu::kStatusBadGroup) {
         put_err(err, err_len, "a group id was >= n_groups (rows skipped)");
         return PAC_E_INVALID;
     }
-    if (h & pacgpu::kStatusOverflow) return PAC_E_OVERFLOW;
+    if (h & pacgpu::kStatusOverflow) {
+        put_err(err, err_len, "an int64 SUM did not fit and was saturated (AVG is still exact)");
+        return PAC_E_OVERFLOW;
+    }
     return PAC_OK;
 }
