@@ -661,6 +661,11 @@ pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value) {
         ctx->opt_minmax_prune = value;
         return PAC_OK;
     }
+    if (strcmp(name, "wait_limit_ns") == 0) {
+        if (value < 0) return fail(ctx, PAC_E_INVALID, "wait_limit_ns %lld", static_cast<long long>(value));
+        ctx->opt_wait_ns = value;
+        return PAC_OK;
+    }
     return fail(ctx, PAC_E_INVALID, "unknown option %s", name);
 }
 

@@ -24,6 +24,7 @@ struct pac_ctx {
     cudaEvent_t pin_ev = nullptr;  // the last copy out of `pin`
     int64_t opt_agg_path = 0;
     int64_t opt_minmax_prune = 1;
+    int64_t opt_wait_ns = 0;  // tensor-core pipeline wait limit (0: default 2 s)
     int64_t last_path = 0;
     int64_t last_launches = 0;
     std::string last_error;

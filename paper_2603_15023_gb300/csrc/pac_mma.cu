@@ -53,7 +53,7 @@ constexpr int kMaxGroups = 8;
 constexpr int kMaxCols = 4;
 constexpr uint32_t kMaxRowsPerCta = 1u << 20;  // keeps FP32 digit totals below 2^24
 constexpr uint32_t kTmemCols = 512;
-constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s of wall time
+constexpr uint64_t kWaitNs = 2000000000ull;  // default: a wait gives up after 2 s of wall time
 constexpr uint32_t kSuspendHintNs = 20000;    // longest park of one try_wait
 
 // Accumulator / feature columns per group for C value columns.
@@ -72,6 +72,7 @@ struct MmaParams {
     unsigned long long *acc; // [G][64][n_alloc] int64 digit totals (zeroed)
     unsigned long long *ng;  // [G] rows per group (zeroed)
     uint32_t *status;
+    uint64_t wait_ns;        // limit of the pipeline waits (the final drain keeps kWaitNs)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -88,22 +89,24 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Bounded wait on an mbarrier phase; false once kWaitNs of wall time have
+// Bounded wait on an mbarrier phase; false once limit_ns of wall time have
 // passed.  Each try_wait may park the warp until the phase completes
-// (suspend-time hint) and polls back off with __nanosleep, so a waiting warp
-// takes few issue slots from the warps it is waiting for.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// (suspend-time hint, never longer than the limit) and polls back off with
+// __nanosleep, so a waiting warp takes few issue slots from the warps it is
+// waiting for.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     uint32_t done = 0;
     uint32_t ns = 16;
+    const uint32_t hint = limit_ns < kSuspendHintNs ? static_cast<uint32_t>(limit_ns) : kSuspendHintNs;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(hint)
             : "memory");
         if (done) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
         if (it >= 8) {
             __nanosleep(ns);
             if (ns < 128) ns <<= 1;
@@ -305,6 +308,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 struct MmaShared {
     uint64_t full_bar[kStages];   // producers -> MMA warps: the stage holds a tile
     uint64_t empty_bar[kStages];  // MMA warps (tcgen05.commit) -> producers: the stage is free
+    uint64_t drain_bar;           // one tcgen05.commit per MMA warp at the end: every MMA done
     uint32_t tmem_slot;
     int abort_flag;
     uint32_t st_cnt[kStages][2][kGroupThreads / 32][kMaxGroups];  // per group, tile parity, warp
@@ -480,9 +484,12 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
         const uint32_t sv = __shfl_sync(kFull, base, valid[r] ? static_cast<int>(gid[r]) : 0) + rank[r];
         slot[r] = valid[r] ? sv : p.k_cap;
     }
-    // (4) the stage must be free: the MMAs of the group's previous tile are done
+    // (4) the stage must be free: the MMAs of the group's previous tile are done.
+    // After a give-up the MMA warps issue nothing more, so nothing is awaited.
     if (it >= kStages) {
-        if (lane == 0 && !mbar_wait(&sh.empty_bar[pg], ((it >> 1) - 1) & 1)) sh.abort_flag = 1;
+        if (lane == 0 && !*reinterpret_cast<volatile int *>(&sh.abort_flag) &&
+            !mbar_wait(&sh.empty_bar[pg], ((it >> 1) - 1) & 1, p.wait_ns))
+            sh.abort_flag = 1;
         __syncwarp();
     }
     if (warp == 0) {
@@ -553,6 +560,7 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
             mbar_init(&sh.full_bar[s], kGroupThreads / 32);
             mbar_init(&sh.empty_bar[s], kMmaWarps);
         }
+        mbar_init(&sh.drain_bar, kMmaWarps);
         asm volatile("fence.mbarrier_init.release.cluster;");
         sh.abort_flag = 0;
     }
@@ -615,12 +623,21 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
         int my_n = 0;
         uint32_t my_sl[kMaxSlots / kMmaWarps], my_g[kMaxSlots / kMmaWarps], my_idx[kMaxSlots / kMmaWarps],
             my_share[kMaxSlots / kMmaWarps];
+        // Once a wait has given up, this warp reads no stage and issues no MMA
+        // (a stage's layout may not be written yet) and commits nothing more;
+        // the results are then discarded with PAC_E_TIMEOUT.
+        bool gave_up = false;
         for (uint32_t it = 0; it < n_tiles; it++) {
-            if (lane == 0) {
+            if (lane == 0 && !gave_up) {
+                if (!mbar_wait(&sh.full_bar[it & 1], (it >> 1) & 1, p.wait_ns)) {
+                    sh.abort_flag = 1;
+                    gave_up = true;
+                }
+            }
+            if (lane == 0 && !gave_up) {
                 const int s = static_cast<int>(it & 1);
                 const uint32_t a_stage = smem_base + s * (p.a_bytes + p.b_bytes);
                 const uint32_t b_stage = a_stage + p.a_bytes;
-                if (!mbar_wait(&sh.full_bar[s], (it >> 1) & 1)) sh.abort_flag = 1;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 if (it == 0) {
                     // the k-th slot dealt to this warp goes to register set k
@@ -680,10 +697,13 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
             }
             __syncwarp();
         }
-        // drain: the last commit of each MMA warp covers every MMA it issued
-        if (lane == 0 && n_tiles > 0) {
-            const uint32_t last = n_tiles - 1;
-            if (!mbar_wait(&sh.empty_bar[last & 1], (last >> 1) & 1)) sh.abort_flag = 1;
+        // drain: a last commit of each MMA warp covers every MMA it issued; the
+        // wait keeps the default limit even when the pipeline waits are short,
+        // so no MMA is still in flight when TMEM is read and freed
+        if (lane == 0) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&sh.drain_bar)));
+            if (!mbar_wait(&sh.drain_bar, 0, kWaitNs)) sh.abort_flag = 1;
         }
         __syncwarp();
     } else {
@@ -852,13 +872,20 @@ int mma_columns(const pac_agg_spec *specs, int n_specs, const void **cols) {
 
 }  // namespace
 
-bool mma_supported(const pac_input *in, const pac_agg_spec *specs, int n_specs) {
+static_assert(kMmaMaxScratchBytes == static_cast<size_t>(kTmemCols) * kWorlds * 8 + 256 + kMaxGroups * 8,
+              "kMmaMaxScratchBytes must follow the tensor-memory and group limits");
+
+bool mma_specs_served(uint32_t n_groups, const pac_agg_spec *specs, int n_specs) {
     const void *cols[kMaxCols];
     const int C = mma_columns(specs, n_specs, cols);
-    if (C < 0 || in->n == 0) return false;
-    if (in->n_groups > static_cast<uint32_t>(kMaxGroups)) return false;
+    if (C < 0) return false;
+    if (n_groups > static_cast<uint32_t>(kMaxGroups)) return false;
     const int n_alloc = feat_alloc(C == 0 ? 1 : C);
-    return in->n_groups * static_cast<uint32_t>(n_alloc) <= kTmemCols;
+    return n_groups * static_cast<uint32_t>(n_alloc) <= kTmemCols;
+}
+
+bool mma_supported(const pac_input *in, const pac_agg_spec *specs, int n_specs) {
+    return in->n > 0 && mma_specs_served(in->n_groups, specs, n_specs);
 }
 
 // Builds the launch of the tensor-core path.  scratch: the accumulators
@@ -918,7 +945,7 @@ size_t mma_scratch_bytes(const pac_input *in, const pac_agg_spec *specs, int n_s
 
 pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
                       cudaStream_t stream, void *scratch, uint32_t *status, int n_sms, int *launches,
-                      const char **why) {
+                      const char **why, uint64_t wait_ns) {
     MmaParams p;
     size_t smem;
     int c4, C;
@@ -931,6 +958,7 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
     p.acc = static_cast<unsigned long long *>(scratch);
     p.ng = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + ((acc_bytes + 255) / 256) * 256);
     p.status = status;
+    p.wait_ns = wait_ns ? wait_ns : kWaitNs;
     cudaError_t e = cudaMemsetAsync(scratch, 0, ((acc_bytes + 255) / 256) * 256 + G * 8, stream);
     if (e != cudaSuccess) {
         *why = cudaGetErrorString(e);
@@ -999,7 +1027,8 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
     pac_status st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, mma_scratch_bytes(in, specs, n_specs) + 1024);
     if (st != PAC_OK) return st;
     const char *why = "";
-    st = mma_launch(in, specs, n_specs, meta, stream, ctx->ws, ctx->d_status, ctx->n_sms, launches, &why);
+    st = mma_launch(in, specs, n_specs, meta, stream, ctx->ws, ctx->d_status, ctx->n_sms, launches, &why,
+                    static_cast<uint64_t>(ctx->opt_wait_ns));
     if (st != PAC_OK) return fail(ctx, st, "%s", why);
     return PAC_OK;
 }

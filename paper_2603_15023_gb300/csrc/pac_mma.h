@@ -9,6 +9,15 @@ namespace pacgpu {
 // count fits the tensor-memory accumulators.
 bool mma_supported(const pac_input *in, const pac_agg_spec *specs, int n_specs);
 
+// The same test on the specs and the group count alone, whatever the row
+// count (mma_supported also needs n > 0).
+bool mma_specs_served(uint32_t n_groups, const pac_agg_spec *specs, int n_specs);
+
+// Largest scratch mma_scratch_bytes returns for a query the path serves:
+// 512 tensor-memory columns x 64 worlds of 8-byte digit totals, 256 bytes of
+// alignment and the row counts of at most 8 groups.
+constexpr size_t kMmaMaxScratchBytes = 512 * 64 * 8 + 256 + 8 * 8;
+
 pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int n_specs,
                    uint64_t *meta, cudaStream_t stream, int *launches);
 
@@ -16,8 +25,9 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
 size_t mma_scratch_bytes(const pac_input *in, const pac_agg_spec *specs, int n_specs);
 
 // Enqueues the tensor-core path with caller-provided scratch and status word.
+// wait_ns: limit of the kernel's pipeline waits (0: the default of 2 s).
 pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
                       cudaStream_t stream, void *scratch, uint32_t *status, int n_sms, int *launches,
-                      const char **why);
+                      const char **why, uint64_t wait_ns = 0);
 
 }  // namespace pacgpu

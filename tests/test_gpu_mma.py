@@ -197,3 +197,24 @@ def test_auto_path_picks_tensor_cores(ctx):
     assert ctx.last_path == 2
     ctx.aggregate(w.keys, w.gids.astype(np.uint8), 4, [(B.PAC_MAX, 0, w.values[0])])
     assert ctx.last_path == 3   # MAX: the per-bit engine
+
+
+def test_wait_give_up_reports_timeout_then_recovers(ctx):
+    """The bounded-wait give-up path of the tensor-core kernel, on an ordinary
+    launch: with the pipeline waits limited to 1 ns they run out while the
+    producers are still filling the first tiles (nothing is left out; the
+    producers are simply slower than that).  The kernel then stops its
+    tensor-core work, drains, frees tensor memory and reports PAC_E_TIMEOUT.
+    The next call on the same context, with the default limit, is bit-exact."""
+    n, G = 4_000_003, 4
+    w = inputs.small(4242, n, G, 200_000, vlo=-(10**6), vhi=10**6, gid_dtype=np.uint8)
+    qk = orc.query_key(4242)
+    specs = _specs(w.values)
+    B.pac_set_option(ctx.h, "wait_limit_ns", 1)
+    try:
+        _, _, st = ctx.aggregate(w.keys, w.gids, G, specs, path=2, qkey=qk)
+    finally:
+        B.pac_set_option(ctx.h, "wait_limit_ns", 0)
+    assert st == B.PAC_E_TIMEOUT, B.status_name(st)
+    masks = orc.hash_keys(w.keys, qk, orc.BALANCED)
+    _check(ctx, w.keys, w.gids, G, specs, masks, qkey=qk)
