@@ -775,13 +775,24 @@ __device__ void item_atomic(const ItemShared &is, uint32_t *status) {
     }
 }
 
+// span[0] = ~(earliest block start), span[1] = latest block end, in
+// %globaltimer nanoseconds (both zeroed before the launch): the device-time
+// interval the kernel ran in, read back by the server to show that batches
+// overlap on the device.
+__device__ __forceinline__ unsigned long long device_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <int NS, int SIG>
 __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQueryDev *__restrict__ qs,
                                                                 const BatchItem *__restrict__ items,
                                                                 uint32_t n_items, unsigned int *counter,
-                                                                uint32_t *status) {
+                                                                uint32_t *status, unsigned long long *span) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ ItemShared is;
+    if (threadIdx.x == 0) atomicMax(span, ~device_ns());
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t it = atomicAdd(counter, 1u);
@@ -819,6 +830,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQuery
         else item_atomic<NS, SIG>(is, status);
         __syncthreads();  // every thread is done with `is` before thread 0 refills it
     }
+    if (threadIdx.x == 0) atomicMax(span + 1, device_ns());
 }
 
 // ---------------------------------------------------------------------------
@@ -1372,6 +1384,7 @@ pac_status plan_enqueue(pac_ctx *ctx, pac_batch *b, cudaStream_t s, const void *
     const uint64_t *d_prefix = reinterpret_cast<const uint64_t *>(base + b->image_off + b->img_prefix);
     const FinParams *d_fin = reinterpret_cast<const FinParams *>(base + b->image_off + b->img_fin);
     unsigned int *counter = reinterpret_cast<unsigned int *>(base);
+    unsigned long long *span = reinterpret_cast<unsigned long long *>(base + kPlanSpanOffset);
     const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(b->n_ctas, std::max<uint32_t>(b->n_items, 1)));
     if (b->n_atomic > 0) {
         const unsigned pgrid = static_cast<unsigned>(std::min<uint64_t>(static_cast<uint64_t>(ctx->n_sms) * 8,
@@ -1384,7 +1397,7 @@ pac_status plan_enqueue(pac_ctx *ctx, pac_batch *b, cudaStream_t s, const void *
 #define PAC_LAUNCH(NS_, SIG_)                                                                              \
     if (b->ns == NS_ && b->sig == SIG_)                                                                    \
         k_batch_agg<NS_, SIG_><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter,  \
-                                                                       b->d_status);
+                                                                       b->d_status, span);
     PAC_BATCH_VARIANTS(PAC_LAUNCH)
 #undef PAC_LAUNCH
     PAC_CUDA(ctx, cudaGetLastError());

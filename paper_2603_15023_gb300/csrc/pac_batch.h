@@ -49,6 +49,12 @@ struct BatchConfig {
 };
 constexpr BatchConfig kBatchDefault = {1u << 16, 100 * 1024};
 
+// The zeroed head of a plan's device block (256 bytes): the work-item
+// counter at 0, the server's status word at 8, and at kPlanSpanOffset two
+// uint64 words that the aggregation kernel fills with the device-time span
+// it ran in (~earliest block start, latest block end; %globaltimer ns).
+constexpr size_t kPlanSpanOffset = 16;
+
 }  // namespace pacgpu
 
 // A plan: host image of the device descriptors plus the device layout.

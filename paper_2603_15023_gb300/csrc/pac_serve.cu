@@ -7,7 +7,8 @@
 // the arena (pac_batch.h: host layout, bind, image staged in pinned memory),
 // and enqueues the batch on the next of n_streams streams: image copy,
 // scratch memset, aggregation, merge and release kernels, a copy of the
-// batch's status word, and a host callback that stamps the completion time.
+// batch's status word and of the device-time span its aggregation kernel ran
+// in, and a host callback that stamps the completion time.
 // The worker never holds its lock across a CUDA call, and callbacks take no
 // lock, so a callback can never wait on the worker.
 #include <algorithm>
@@ -84,8 +85,9 @@ struct Flight {
     size_t arena_off = 0, arena_bytes = 0;
     size_t stage_off = 0, stage_bytes = 0;
     std::vector<uint64_t> tickets;
-    uint32_t *h_status = nullptr;  // pinned word written by the stream
+    unsigned char *h_head = nullptr;  // pinned copy of the status word and the kernel's span
     uint32_t status_seen = 0;
+    uint64_t span_lo = 0, span_hi = 0;  // device ns the aggregation kernel ran in (0, 0: none)
     std::atomic<bool> done{false};
     Clock::time_point t_done;
     struct pac_server *srv = nullptr;
@@ -122,6 +124,7 @@ struct pac_server {
     std::thread worker;
     // statistics
     std::vector<double> lat;
+    std::vector<std::pair<uint64_t, uint64_t>> spans;  // device-time spans of the batches' aggregation kernels
     uint64_t batches = 0, batched_queries = 0;
     int inflight_q = 0, max_inflight_seen = 0;
     size_t arena_used = 0, arena_hw = 0;
@@ -129,10 +132,20 @@ struct pac_server {
 
 namespace {
 
+// Bytes copied back from the plan's head: the status word (offset 8) up to
+// the end of the two span words.
+constexpr size_t kHeadCopy = pacgpu::kPlanSpanOffset + 16 - 8;
+
 void CUDART_CB on_done(void *p) {
     Flight *f = static_cast<Flight *>(p);
     f->t_done = Clock::now();
-    f->status_seen = *f->h_status;
+    uint64_t span[2];
+    std::memcpy(&f->status_seen, f->h_head, 4);
+    std::memcpy(span, f->h_head + (pacgpu::kPlanSpanOffset - 8), 16);
+    if (span[0] && span[1]) {
+        f->span_lo = ~span[0];
+        f->span_hi = span[1];
+    }
     f->done.store(true, std::memory_order_release);
     f->srv->cv_work.notify_one();
 }
@@ -153,6 +166,7 @@ void retire(pac_server *s) {
             t.latency_ms = std::chrono::duration<double, std::milli>(f->t_done - t.t_submit).count();
             s->lat.push_back(t.latency_ms);
         }
+        if (f->span_hi) s->spans.emplace_back(f->span_lo, f->span_hi);
         s->inflight_q -= static_cast<int>(f->tickets.size());
         if (f->stream_idx >= 0 && s->stream_busy[f->stream_idx] == f) s->stream_busy[f->stream_idx] = nullptr;
         if (f->arena_bytes) s->arena_alloc->release(f->arena_off, f->arena_bytes);
@@ -187,7 +201,7 @@ Flight *launch_batch(pac_server *s, const std::vector<uint64_t> &ids, int si, st
         return f;
     }
     size_t aoff = 0, poff = 0;
-    const size_t stage = b->image.size() + 256;
+    const size_t stage = (b->image.size() + 15) / 16 * 16 + 256;
     if (!s->arena_alloc->alloc(b->device_bytes, 256, &aoff)) {
         pacgpu::plan_destroy(b);
         return nullptr;
@@ -215,12 +229,12 @@ Flight *launch_batch(pac_server *s, const std::vector<uint64_t> &ids, int si, st
     char *pin = s->pinned + poff;
     pacgpu::plan_bind(b, dev);
     b->d_status = reinterpret_cast<uint32_t *>(dev + 8);  // inside the zeroed head of the block
-    f->h_status = reinterpret_cast<uint32_t *>(pin + b->image.size());
+    f->h_head = reinterpret_cast<unsigned char *>(pin + (b->image.size() + 15) / 16 * 16);
     std::memcpy(pin, b->image.data(), b->image.size());
     st = pacgpu::plan_setup_kernel(s->ctx, b);
     if (st == PAC_OK) st = pacgpu::plan_enqueue(s->ctx, b, stream, pin);
     cudaError_t e = cudaSuccess;
-    if (st == PAC_OK) e = cudaMemcpyAsync(f->h_status, b->d_status, 4, cudaMemcpyDeviceToHost, stream);
+    if (st == PAC_OK) e = cudaMemcpyAsync(f->h_head, b->d_status, kHeadCopy, cudaMemcpyDeviceToHost, stream);
     if (st == PAC_OK && e == cudaSuccess) e = cudaLaunchHostFunc(stream, on_done, f);
     lk.lock();
     if (st != PAC_OK || e != cudaSuccess) {
@@ -338,7 +352,7 @@ pac_status pac_serve_submit(pac_server *s, const pac_query *q, uint64_t *ticket)
     st = pacgpu::plan_build(&tmp, q, 1, s->bcfg, &b);
     if (st != PAC_OK) return st;
     t.need = b->device_bytes;
-    const size_t stage = b->image.size() + 256;
+    const size_t stage = (b->image.size() + 15) / 16 * 16 + 256;
     pacgpu::plan_destroy(b);
     if (t.need > s->cfg.mem_budget || stage > s->pinned_bytes) return PAC_E_NOMEM;
     t.t_submit = Clock::now();
@@ -396,7 +410,20 @@ pac_status pac_serve_stats(pac_server *s, const char *name, double *value) {
     else if (!strcmp(name, "max_ms")) *value = pct(1.0);
     else if (!strcmp(name, "max_inflight_seen")) *value = s->max_inflight_seen;
     else if (!strcmp(name, "arena_high_water")) *value = static_cast<double>(s->arena_hw);
-    else return PAC_E_INVALID;
+    else if (!strcmp(name, "max_device_overlap")) {
+        // most batches whose aggregation kernels were running at one instant
+        std::vector<std::pair<uint64_t, int>> ev;
+        for (const auto &iv : s->spans) {
+            ev.emplace_back(iv.first, 1);
+            ev.emplace_back(iv.second, -1);
+        }
+        std::sort(ev.begin(), ev.end(), [](const auto &a, const auto &b) {
+            return a.first != b.first ? a.first < b.first : a.second < b.second;  // ends before starts
+        });
+        int cur = 0, best = 0;
+        for (const auto &e : ev) best = std::max(best, cur += e.second);
+        *value = best;
+    } else return PAC_E_INVALID;
     return PAC_OK;
 }
 

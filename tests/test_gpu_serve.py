@@ -6,8 +6,10 @@ from several host threads while other batches run, admitted as memory and
 slots free up) as when it runs alone: integer aggregates, MIN/MAX, meta and
 the released cells of integer queries bit-exact; float sums within 1e-6
 relative to the world's sum of |v| (global float atomics do not fix the
-order of additions).  A tight memory budget forces admission in several
-rounds; an oversized query is refused.
+order of additions).  Batches admitted while others run execute at the same
+time on the GPU (their aggregation kernels' device-timer spans intersect).
+A tight memory budget forces admission in several rounds; an oversized query
+is refused.
 """
 import threading
 import time
@@ -112,6 +114,31 @@ def test_served_results_equal_alone(ctx):
         B.pac_serve_destroy(srv)
     for q, a in zip(qs, alone):
         _same(q, a, _snapshot(q))
+        q.check()
+
+
+def test_batches_overlap_on_the_device(ctx):
+    """Continuous batching overlaps work on the device: one query per batch,
+    four streams, queries of 2M rows (about 31 work items, so one batch's
+    kernel holds a fraction of the SMs for about a millisecond).  The server
+    stamps each batch's aggregation kernel with the GPU's global timer (the
+    earliest block start and the latest block end) and reports the most
+    batches whose kernels were running at one instant; with batches launched
+    every few tens of microseconds, at least two must coincide.  Every result
+    is still checked against the oracle."""
+    from test_gpu_batch import Q
+    qs = [Q(50_000 + i, 2_000_000, 8, np.uint8, [B.PAC_COUNT, B.PAC_SUM], np.int64) for i in range(12)]
+    srv = B.pac_serve_create(ctx, mem_budget=1 << 30, max_inflight=12, max_batch=1, n_streams=4)
+    try:
+        tickets = [B.pac_serve_submit(srv, q.query) for q in qs]
+        for tk in tickets:
+            _, st = B.pac_serve_wait(srv, tk)
+            assert st == B.PAC_OK
+        assert B.pac_serve_stats(srv, "batches") == len(qs)
+        assert B.pac_serve_stats(srv, "max_device_overlap") >= 2
+    finally:
+        B.pac_serve_destroy(srv)
+    for q in qs:
         q.check()
 
 
