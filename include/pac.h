@@ -459,7 +459,9 @@ pac_status pac_serve_wait(pac_server *srv, uint64_t ticket, double *latency_ms);
 
 /* Server statistics over completed tickets: "completed", "batches",
  * "mean_batch" (queries per launch), "p50_ms", "p99_ms", "max_ms",
- * "max_inflight_seen", "arena_high_water" (bytes). */
+ * "max_inflight_seen", "arena_high_water" (bytes), "max_device_overlap"
+ * (the most batches whose aggregation kernels were running on the GPU at one
+ * instant, from device-timer stamps the kernels record). */
 pac_status pac_serve_stats(pac_server *srv, const char *name, double *value);
 
 /* Finishes every queued and running query, then frees the server. */
@@ -487,13 +489,18 @@ void pac_serve_destroy(pac_server *srv);
  *       int64 overflow, PAC_E_INVALID for a group id >= n_groups).
  *   err, err_len: optional HOST buffer for a message (may be NULL).
  * Returns PAC_E_UNSUPPORTED for specs the tensor-core path does not serve
- * and PAC_E_INVALID when a query would need more than the static scratch.
+ * (whatever n, so n = 0 is refused for them too).  A query that would need
+ * more scratch than the array holds is refused with PAC_E_INVALID; within
+ * the limits above none does (the array is sized for the largest).  Every
+ * failure writes a message into err.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and its contents persist between
- * calls (each call clears what must start at zero): calls whose work
- * overlaps on the same GPU (other host threads, other streams) race and must
- * be serialised by the caller.
+ * device, with that device current) and keeps it for the process: make that
+ * first call before any stream capture, and do not use this entry point
+ * across cudaDeviceReset.  The call synchronises `stream` before returning.
+ * Every call shares the one array and its contents persist between calls
+ * (each call clears what must start at zero): calls whose work overlaps on
+ * the same GPU (other host threads, other streams) race and must be
+ * serialised by the caller.
  * ------------------------------------------------------------------------ */
 pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
                                  uint64_t *meta, pac_stream stream, char *err, size_t err_len);
@@ -514,6 +521,12 @@ pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_spec *specs,
  *   engine (Sec. 5 "Pruning": rows whose value improves no world's current
  *   extreme skip the update; results are identical), 0 = every row updated.
  *   Plans built by pac_batch_plan take the setting current at plan time.
+ *   "wait_limit_ns" (for tests of the give-up path): the wall-time limit of
+ *   the tensor-core kernel's pipeline waits, 0 (default) = 2 s.  A wait that
+ *   runs out stops the kernel's tensor-core work, its results are discarded
+ *   and the next pac_sync_status returns PAC_E_TIMEOUT; a very short limit
+ *   makes ordinary launches run out.  The kernel's final wait for its own
+ *   tensor-core operations keeps the 2 s limit.
  *   pac_get_info(ctx, name, &value): "last_path" (1 plain per-bit, 2 tensor
  *   core, 3 per-bit engine, 4 one-launch), "last_launches" kernels launched by the last
  *   call.

@@ -5,7 +5,7 @@ Below 16M rows the columns are copied and then aggregated; from 16M rows on
 a query the tensor-core path serves alone is pipelined (row chunks copied on
 a second stream, each aggregated once it has arrived).  Both forms must
 release exactly what the oracle releases: NULL decisions and flags
-bit-exact, values within 1e-9 relative.
+bit-exact, values within 1e-12 relative.
 """
 import numpy as np
 import pytest
@@ -70,4 +70,4 @@ def test_query_host_matches_oracle(ctx, n, with_avg, pinned):
     np.testing.assert_array_equal(is_null, ref["is_null"])
     np.testing.assert_array_equal(flags, ref["flags"])
     live = ref["is_null"] == 0
-    np.testing.assert_allclose(noised[live], ref["noised"][live], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(noised[live], ref["noised"][live], rtol=1e-12, atol=0)

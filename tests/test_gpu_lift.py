@@ -142,8 +142,8 @@ def test_lifted_release_matches_oracle(ctx, mode):
     np.testing.assert_array_equal(is_null.cpu().numpy(), ref["is_null"])
     np.testing.assert_array_equal(flags.cpu().numpy().view(np.uint32), ref["flags"])
     live = ref["is_null"] == 0
-    np.testing.assert_allclose(noised.cpu().numpy()[live], ref["noised"][live], rtol=1e-9, atol=0)
-    np.testing.assert_allclose(post.cpu().numpy(), ref["posterior"], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(noised.cpu().numpy()[live], ref["noised"][live], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(post.cpu().numpy(), ref["posterior"], rtol=1e-10, atol=1e-15)
 
 
 @pytest.mark.parametrize("G", [1, 1000, 100_003])
@@ -200,4 +200,4 @@ def test_ratio_query_end_to_end(ctx):
     np.testing.assert_array_equal(is_null.cpu().numpy(), ref["is_null"])
     np.testing.assert_array_equal(flags.cpu().numpy().view(np.uint32), ref["flags"])
     live = ref["is_null"] == 0
-    np.testing.assert_allclose(noised.cpu().numpy()[live], ref["noised"][live], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(noised.cpu().numpy()[live], ref["noised"][live], rtol=1e-12, atol=0)
