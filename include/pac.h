@@ -506,6 +506,55 @@ pac_status pac_aggregate_noalloc(const pac_input *in, const pac_agg_spec *specs,
                                  uint64_t *meta, pac_stream stream, char *err, size_t err_len);
 
 /* ---------------------------------------------------------------------------
+ * 6. m = 128 worlds  (Sec. 2 "SIMD-PAC-DB": m = 64 is the paper's choice,
+ *    m = 128 is possible with twice the state; the cost at most doubles)
+ *
+ * A PU's membership in 128 worlds comes from two keyed re-hashes of the same
+ * engine hash, h_a = fmix64(fmix64(key) ^ K) and h_b = fmix64(fmix64(key) ^
+ * K2), K2 being the SplitMix64 output after K (pac_query_key2).  Mask word 0
+ * holds worlds 0..63, word 1 worlds 64..127:
+ *   PAC_HASH_BALANCED: word 0 = low 32 bits of h_a | (low 32 bits of h_b)
+ *                      << 32, word 1 = ~word 0 (every PU in exactly 64
+ *                      worlds; world 64 + j is the complement of world j);
+ *   PAC_HASH_RAW:      word 0 = h_a, word 1 = h_b.
+ * Everything else is the m = 64 definition with 128 worlds: results are
+ * row-major [n_groups][128]; meta is [n_groups][3] {n_g, OR of mask word 0,
+ * OR of mask word 1}.
+ * ------------------------------------------------------------------------ */
+
+/* Host-only: K2 for a query seed (the SplitMix64 output after K). */
+uint64_t pac_query_key2(uint64_t seed);
+
+/* masks: device [n][2] uint64 (word 0, word 1 of each row); keys: device
+ * [n] int64.  n = 0 is a no-op.  keys and masks must not overlap. */
+pac_status pac_hash_keys128(pac_ctx *ctx, const int64_t *keys, uint64_t *masks, size_t n,
+                            uint64_t query_key, uint64_t query_key2, int32_t hash_mode,
+                            pac_stream stream);
+
+/* pac_aggregate_multi over 128 worlds.  in->keys_or_masks: [n] int64 keys
+ * (PAC_IN_KEYS, hashed with in->query_key and query_key2) or [n][2] uint64
+ * masks (PAC_IN_MASKS).  Every exact kind and vtype is served
+ * (PAC_E_UNSUPPORTED for PAC_APPROX and PAC_IN_DROP_EMPTY).  specs[i].out:
+ * device [n_groups*128] of the kind's output type; meta: device
+ * [n_groups*3] or NULL.  COUNT and exact int64 SUM/AVG over at most 8 groups
+ * and 4 value columns run on the tensor cores with 128-row accumulator
+ * tiles; the other queries run the per-bit engine on each 64-world half. */
+pac_status pac_aggregate128(pac_ctx *ctx, const pac_input *in, uint64_t query_key2,
+                            const pac_agg_spec *specs, int32_t n_specs, uint64_t *meta,
+                            pac_stream stream);
+
+/* pac_finalize over 128 worlds: the release of every cell (Sec. 4.1 steps
+ * 1-4, Sec. 3.2 NULLs) with j* the top 7 bits of the first draw of stream 0,
+ * a uniform prior over 128 worlds, a cell NULL with probability
+ * (128 - popcount(or_g))/128, the diversity flag at >= 64 rows and <= 80
+ * updated worlds.  meta: device [n_groups*3] from pac_aggregate128;
+ * posterior: device [128] or NULL. */
+pac_status pac_finalize128(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs, uint32_t n_groups,
+                           const uint64_t *meta, uint64_t seed, double budget, int32_t mode,
+                           double *noised, uint8_t *is_null, uint32_t *flags, double *posterior,
+                           pac_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Path selection and introspection (for benchmarks and tests).
  *   pac_set_option(ctx, name, value): "agg_path" 0 = automatic (the
  *   one-launch path for ungrouped COUNT / exact int64 SUM / AVG queries of at

@@ -37,7 +37,7 @@ EXPORTED = (
     "pac_query_host", "pac_set_option", "pac_get_info", "pac_aggregate_noalloc",
     "pac_batch_plan", "pac_batch_launch", "pac_batch_free", "pac_batch_info", "pac_batch_run",
     "pac_serve_create", "pac_serve_submit", "pac_serve_poll", "pac_serve_wait", "pac_serve_stats",
-    "pac_serve_destroy",
+    "pac_serve_destroy", "pac_query_key2", "pac_hash_keys128", "pac_aggregate128", "pac_finalize128",
 )
 PAC_BATCH_AUTOTUNE = 1
 
@@ -159,6 +159,11 @@ def lib() -> ctypes.CDLL:
         "pac_serve_wait": (i32, [vp, u64, ctypes.POINTER(dbl)]),
         "pac_serve_stats": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(dbl)]),
         "pac_serve_destroy": (None, [vp]),
+        "pac_query_key2": (u64, [u64]),
+        "pac_hash_keys128": (i32, [vp, vp, vp, sz, u64, u64, i32, vp]),
+        "pac_aggregate128": (i32, [vp, ctypes.POINTER(PacInput), u64, ctypes.POINTER(PacAggSpec), i32, vp, vp]),
+        "pac_finalize128": (i32, [vp, ctypes.POINTER(PacAggSpec), i32, u32, vp, u64, dbl, i32, vp, vp, vp, vp,
+                                  vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -276,6 +281,27 @@ def pac_finalize(ctx: int, specs: ctypes.Array, n_specs: int, n_groups: int, met
                  stream: int = 0) -> None:
     _check(ctx, lib().pac_finalize(ctx, specs, n_specs, n_groups, meta, seed, budget, mode, noised, is_null,
                                    flags, posterior or None, stream))
+
+
+def pac_query_key2(seed: int) -> int:
+    return lib().pac_query_key2(seed)
+
+
+def pac_hash_keys128(ctx: int, keys: int, masks: int, n: int, query_key: int, query_key2: int, hash_mode: int,
+                     stream: int = 0) -> None:
+    _check(ctx, lib().pac_hash_keys128(ctx, keys, masks, n, query_key, query_key2, hash_mode, stream))
+
+
+def pac_aggregate128(ctx: int, inp: PacInput, query_key2: int, specs: ctypes.Array, n_specs: int, meta: int,
+                     stream: int = 0) -> None:
+    _check(ctx, lib().pac_aggregate128(ctx, ctypes.byref(inp), query_key2, specs, n_specs, meta or None, stream))
+
+
+def pac_finalize128(ctx: int, specs: ctypes.Array, n_specs: int, n_groups: int, meta: int, seed: int,
+                    budget: float, mode: int, noised: int, is_null: int, flags: int, posterior: int,
+                    stream: int = 0) -> None:
+    _check(ctx, lib().pac_finalize128(ctx, specs, n_specs, n_groups, meta, seed, budget, mode, noised, is_null,
+                                      flags, posterior or None, stream))
 
 
 def pac_query_host(ctx: int, inp: PacInput, specs: ctypes.Array, n_specs: int, seed: int, budget: float,

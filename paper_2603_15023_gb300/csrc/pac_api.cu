@@ -269,6 +269,13 @@ size_t select_table_bytes(const pac_select_spec *sel) {
 
 }  // namespace
 
+namespace pacgpu {
+pac_status aggregate_dispatch(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                              uint64_t *meta, cudaStream_t stream) {
+    return aggregate_impl(ctx, in, specs, n_specs, meta, stream);
+}
+}  // namespace pacgpu
+
 // ===========================================================================
 // exported entry points
 // ===========================================================================
@@ -308,6 +315,7 @@ void pac_destroy(pac_ctx *ctx) {
     if (ctx->qws) cudaFree(ctx->qws);
     if (ctx->sws) cudaFree(ctx->sws);
     if (ctx->small_acc) cudaFree(ctx->small_acc);
+    if (ctx->m128) cudaFree(ctx->m128);
     if (ctx->pin_ev) {
         cudaEventSynchronize(ctx->pin_ev);
         cudaEventDestroy(ctx->pin_ev);
@@ -515,33 +523,11 @@ pac_status pac_finalize(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs
                         const uint64_t *meta, uint64_t seed, double budget, int32_t mode, double *noised,
                         uint8_t *is_null, uint32_t *flags, double *posterior, pac_stream stream) {
     if (!ctx) return PAC_E_INVALID;
-    if (n_specs < 1 || n_specs > PAC_MAX_SPECS || !specs) return fail(ctx, PAC_E_INVALID, "n_specs %d", n_specs);
-    if (n_groups < 1) return fail(ctx, PAC_E_INVALID, "n_groups must be >= 1");
-    if (!meta || !noised || !is_null || !flags) return fail(ctx, PAC_E_INVALID, "NULL output or meta");
-    if (!(budget > 0.0)) return fail(ctx, PAC_E_INVALID, "budget must be > 0");
-    if (mode != PAC_FIN_ADAPTIVE && mode != PAC_FIN_INDEPENDENT) return fail(ctx, PAC_E_INVALID, "mode %d", mode);
     FinParams p{};
-    for (int i = 0; i < n_specs; i++) {
-        if (specs[i].kind < PAC_COUNT || specs[i].kind > PAC_LIFTED || !specs[i].out)
-            return fail(ctx, PAC_E_INVALID, "spec %d", i);
-        if (specs[i].kind == PAC_LIFTED && specs[i].vtype != PAC_F64)
-            return fail(ctx, PAC_E_INVALID, "spec %d: a lifted vector is PAC_F64", i);
-        p.spec[i].kind = specs[i].kind;
-        p.spec[i].vtype = specs[i].kind == PAC_COUNT ? PAC_I64 : specs[i].vtype;
-        p.spec[i].variant = specs[i].variant;
-        p.spec[i].out = specs[i].out;
-    }
-    p.n_specs = n_specs;
-    p.n_groups = n_groups;
-    p.meta = meta;
-    p.seed = seed;
-    p.budget = budget;
-    p.mode = mode;
-    p.noised = noised;
-    p.is_null = is_null;
-    p.flags = flags;
-    p.posterior = posterior;
-    pac_status st = bind_device(ctx);
+    pac_status st = build_fin_params(ctx, specs, n_specs, n_groups, meta, seed, budget, mode, noised, is_null,
+                                     flags, posterior, p);
+    if (st != PAC_OK) return st;
+    st = bind_device(ctx);
     if (st != PAC_OK) return st;
     PAC_CUDA(ctx, launch_finalize(p, stream));
     ctx->last_launches = 1;

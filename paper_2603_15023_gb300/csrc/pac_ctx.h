@@ -18,6 +18,8 @@ struct pac_ctx {
     void *sws = nullptr;  // selection: sorted operand tables, selected masks
     size_t sws_bytes = 0;
     void *small_acc = nullptr;  // one-launch path: accumulators, zero between calls
+    void *m128 = nullptr;  // m = 128: mask words and the two 64-world halves
+    size_t m128_bytes = 0;
     uint32_t *d_status = nullptr;
     void *pin = nullptr;  // pinned staging of per-bit engine descriptors
     size_t pin_bytes = 0;

@@ -29,7 +29,44 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint64_t kStreamJstar = 0, kStreamNull = 1, kStreamNoise = 2;
 constexpr uint64_t kDiversityMinRows = 64;
-constexpr int kDiversityMaxWorlds = 40;
+
+// W = 64 or 128 worlds.  meta per group: {n_g, OR word 0[, OR word 1]}; j*
+// is the top log2(W) bits of the first draw; the diversity flag needs at most
+// 5/8 of the worlds updated (40 of 64, 80 of 128).
+template <int W>
+struct Worlds {
+    static constexpr int kWords = W / 64;
+    static constexpr int kMetaStride = 1 + kWords;
+    static constexpr int kJShift = W == 64 ? 58 : 57;
+    static constexpr int kDiversityMaxWorlds = W * 5 / 8;
+};
+
+// The OR of a group's mask words: world t was updated by some row.
+template <int W>
+struct OrMask {
+    unsigned long long w[W / 64];
+    __device__ __forceinline__ bool bit(int t) const { return (w[t >> 6] >> (t & 63)) & 1ull; }
+    __device__ __forceinline__ int popc() const {
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < W / 64; k++) c += __popcll(w[k]);
+        return c;
+    }
+    __device__ __forceinline__ OrMask shfl(int src) const {
+        OrMask o;
+#pragma unroll
+        for (int k = 0; k < W / 64; k++) o.w[k] = __shfl_sync(0xffffffffu, w[k], src);
+        return o;
+    }
+};
+
+template <int W>
+__device__ __forceinline__ OrMask<W> group_or(const FinParams &p, uint32_t g) {
+    OrMask<W> o;
+#pragma unroll
+    for (int k = 0; k < W / 64; k++) o.w[k] = p.meta[static_cast<size_t>(Worlds<W>::kMetaStride) * g + 1 + k];
+    return o;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -88,9 +125,10 @@ struct CellRaw {
     int code;
 };
 
+template <int W>
 __device__ __forceinline__ CellRaw load_raw(const FinParams &p, uint32_t g, int s, int t, int jstar) {
     const FinSpec &sp = p.spec[s];
-    const unsigned long long *o = static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * kWorlds;
+    const unsigned long long *o = static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * W;
     CellRaw r;
     r.y = o[t];
     r.yj = o[jstar];
@@ -99,19 +137,31 @@ __device__ __forceinline__ CellRaw load_raw(const FinParams &p, uint32_t g, int 
 }
 
 // Per-lane facts of cell c that do not depend on the posterior.
+template <int W>
 struct CellDraw {
-    unsigned long long orm;
+    OrMask<W> orm;
     bool null_, diversity;
 };
 
-__device__ __forceinline__ CellDraw draw_cell(const FinParams &p, uint64_t c) {
+template <int W>
+__device__ __forceinline__ CellDraw<W> draw_cell(const FinParams &p, uint64_t c) {
     const uint32_t g = static_cast<uint32_t>(c / p.n_specs);
-    CellDraw d;
-    d.orm = p.meta[2 * g + 1];
-    const uint64_t rows = p.meta[2 * g];
-    const int pop = __popcll(d.orm);
-    d.null_ = pop < 64 && static_cast<int>(counter_draw(p.seed, kStreamNull, c) >> 58) < 64 - pop;
-    d.diversity = rows >= kDiversityMinRows && pop <= kDiversityMaxWorlds;
+    CellDraw<W> d;
+    d.orm = group_or<W>(p, g);
+    const uint64_t rows = p.meta[static_cast<size_t>(Worlds<W>::kMetaStride) * g];
+    const int pop = d.orm.popc();
+    d.null_ = pop < W && static_cast<int>(counter_draw(p.seed, kStreamNull, c) >> Worlds<W>::kJShift) < W - pop;
+    d.diversity = rows >= kDiversityMinRows && pop <= Worlds<W>::kDiversityMaxWorlds;
+    return d;
+}
+
+template <int W>
+__device__ __forceinline__ CellDraw<W> no_cell() {
+    CellDraw<W> d;
+#pragma unroll
+    for (int k = 0; k < W / 64; k++) d.orm.w[k] = 0ull;
+    d.null_ = true;
+    d.diversity = false;
     return d;
 }
 
@@ -125,17 +175,20 @@ __device__ __forceinline__ double normal_draw(uint64_t seed, uint64_t c) {
 
 // ---------------------------------------------------------------------------
 // Independent mode: every cell starts from the uniform prior, so step 1 is
-// the plain mean and variance of the 64 worlds (p_t = 1/64) and the
-// posterior after a release is needed for the last cell only (the one the
-// caller can read back).  One warp takes 32 consecutive cells: lane k makes
-// cell k's NULL decision and normal draw, then the warp releases the cells
-// one by one, lane l holding worlds l and l+32, and lane k stores cell k.
+// the plain mean and variance of the W worlds (p_t = 1/W) and the posterior
+// after a release is needed for the last cell only (the one the caller can
+// read back).  One warp takes 32 consecutive cells: lane k makes cell k's
+// NULL decision and normal draw, then the warp releases the cells one by
+// one, lane l holding worlds l, l+32, ... (W/32 of them), and lane k stores
+// cell k.
 // ---------------------------------------------------------------------------
+template <int W>
 __global__ void __launch_bounds__(256) k_finalize_independent(const __grid_constant__ FinParams p) {
+    constexpr int V = W / 32;
     const int lane = threadIdx.x & 31;
-    const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> 58);
+    const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> Worlds<W>::kJShift);
     const double inv2b = 1.0 / (2.0 * p.budget);
-    const double log_uniform = -log(64.0);
+    const double log_uniform = -log(static_cast<double>(W));
     const uint64_t n_cells = static_cast<uint64_t>(p.n_groups) * p.n_specs;
     const uint64_t n_blk = (n_cells + 31) / 32;
     const uint64_t wid = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -144,10 +197,10 @@ __global__ void __launch_bounds__(256) k_finalize_independent(const __grid_const
         const uint64_t c0 = blk * 32;
         const uint64_t rem = n_cells - c0;
         const int kend = rem < 32 ? static_cast<int>(rem) : 32;
-        CellDraw dl{0ull, true, false};
+        CellDraw<W> dl = no_cell<W>();
         double zc = 0.0;
         if (lane < kend) {
-            dl = draw_cell(p, c0 + lane);
+            dl = draw_cell<W>(p, c0 + lane);
             if (!dl.null_) zc = normal_draw(p.seed, c0 + lane);
         }
         const uint32_t nulls = __ballot_sync(kFull, dl.null_);
@@ -159,46 +212,69 @@ __global__ void __launch_bounds__(256) k_finalize_independent(const __grid_const
             const uint64_t c = c0 + k;
             const bool last = p.posterior && c == n_cells - 1;
             if ((nulls >> k) & 1u) {
-                if (last) {
-                    p.posterior[lane] = exp(log_uniform);
-                    p.posterior[lane + 32] = exp(log_uniform);
-                }
+                if (last)
+#pragma unroll
+                    for (int v = 0; v < V; v++) p.posterior[lane + 32 * v] = exp(log_uniform);
                 continue;
             }
-            const unsigned long long orm = __shfl_sync(kFull, dl.orm, k);
+            const OrMask<W> orm = dl.orm.shfl(k);
             const double z = __shfl_sync(kFull, zc, k);
             const FinSpec &sp = p.spec[s];
             const int code = cell_code(sp);
             const unsigned long long *o =
-                static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * kWorlds;
-            const unsigned long long r0 = ((orm >> lane) & 1ull) ? o[lane] : 0ull;
-            const unsigned long long r1 = ((orm >> (lane + 32)) & 1ull) ? o[lane + 32] : 0ull;
-            const unsigned long long rj = ((orm >> jstar) & 1ull) ? o[jstar] : 0ull;
+                static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * W;
+            unsigned long long r[V];
+            bool agree = true;
+            const unsigned long long rj = orm.bit(jstar) ? o[jstar] : 0ull;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                r[v] = orm.bit(lane + 32 * v) ? o[lane + 32 * v] : 0ull;
+                agree = agree && same_value(r[v], rj, code);
+            }
             const double yj = raw_to_double(rj, code);
-            double var = 0.0, y0 = 0.0, y1 = 0.0;
-            if (!__all_sync(kFull, same_value(r0, rj, code) && same_value(r1, rj, code))) {
-                y0 = raw_to_double(r0, code);
-                y1 = raw_to_double(r1, code);
-                const double mu = warp_sum(y0 + y1) * (1.0 / kWorlds);
-                const double d0 = y0 - mu, d1 = y1 - mu;
-                var = warp_sum(fma(d0, d0, d1 * d1)) * (1.0 / kWorlds);
+            double var = 0.0, y[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) y[v] = 0.0;
+            if (!__all_sync(kFull, agree)) {
+                double sum = 0.0;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    y[v] = raw_to_double(r[v], code);
+                    sum += y[v];
+                }
+                const double mu = warp_sum(sum) * (1.0 / W);
+                double sq = 0.0;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const double d = y[v] - mu;
+                    sq = fma(d, d, sq);
+                }
+                var = warp_sum(sq) * (1.0 / W);
             }
             const double delta = var * inv2b;
             const double yt = delta == 0.0 ? yj : yj + sqrt(delta) * z;
             if (last) {
-                double l0 = log_uniform, l1 = log_uniform;
+                double l[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) l[v] = log_uniform;
                 if (delta > 0.0) {
-                    const double e0 = yt - y0, e1 = yt - y1;
-                    l0 += -(e0 * e0) / (2.0 * delta);
-                    l1 += -(e1 * e1) / (2.0 * delta);
-                    double mx = fmax(l0, l1);
+                    double mx = -INFINITY;
+#pragma unroll
+                    for (int v = 0; v < V; v++) {
+                        const double e = yt - y[v];
+                        l[v] += -(e * e) / (2.0 * delta);
+                        mx = fmax(mx, l[v]);
+                    }
                     for (int o2 = 16; o2; o2 >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, o2));
-                    const double lse = mx + log(warp_sum(exp(l0 - mx) + exp(l1 - mx)));
-                    l0 -= lse;
-                    l1 -= lse;
+                    double se = 0.0;
+#pragma unroll
+                    for (int v = 0; v < V; v++) se += exp(l[v] - mx);
+                    const double lse = mx + log(warp_sum(se));
+#pragma unroll
+                    for (int v = 0; v < V; v++) l[v] -= lse;
                 }
-                p.posterior[lane] = exp(l0);
-                p.posterior[lane + 32] = exp(l1);
+#pragma unroll
+                for (int v = 0; v < V; v++) p.posterior[lane + 32 * v] = exp(l[v]);
             }
             if (lane == k) {
                 my_yt = yt;
@@ -213,10 +289,9 @@ __global__ void __launch_bounds__(256) k_finalize_independent(const __grid_const
             p.flags[c] = f | (dl.null_ ? PAC_F_NULL : (my_zv ? PAC_F_ZEROVAR : 0u));
         }
     }
-    if (p.posterior && n_cells == 0 && blockIdx.x == 0 && threadIdx.x < 32) {
-        p.posterior[lane] = exp(log_uniform);
-        p.posterior[lane + 32] = exp(log_uniform);
-    }
+    if (p.posterior && n_cells == 0 && blockIdx.x == 0 && threadIdx.x < 32)
+#pragma unroll
+        for (int v = 0; v < V; v++) p.posterior[lane + 32 * v] = exp(log_uniform);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,15 +318,16 @@ __global__ void __launch_bounds__(256) k_finalize_independent(const __grid_const
 // computed 32 cells at a time, one cell per lane, and world values are
 // loaded kAhead cells ahead of the chain.
 // ---------------------------------------------------------------------------
-constexpr int kChainThreads = kWorlds;  // thread t holds world t
-constexpr int kChainWarps = kChainThreads / 32;
 constexpr int kAhead = 4;
+constexpr int kMaxChainWarps = kWorlds128 / 32;
 
+// W threads (thread t holds world t), W/32 warps.
 struct ChainShared {
-    double part[4][kChainWarps];  // per-warp partials, rotating slots (one barrier per reduction)
-    unsigned long long bits[4][kChainWarps];
+    double part[4][kMaxChainWarps];  // per-warp partials, rotating slots (one barrier per reduction)
+    unsigned long long bits[4][kMaxChainWarps];
 };
 
+template <int NW>
 __device__ __forceinline__ double chain_sum(double v, ChainShared &sh, int &slot, int warp, int lane) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -259,10 +335,14 @@ __device__ __forceinline__ double chain_sum(double v, ChainShared &sh, int &slot
     slot = (slot + 1) & 3;
     if (lane == 0) pp[warp] = v;
     __syncthreads();
-    return pp[0] + pp[1];
+    double t = pp[0] + pp[1];
+#pragma unroll
+    for (int w = 2; w < NW; w++) t += pp[w];
+    return t;
 }
 
 // chain_sum, also counting the threads whose flag b is set.
+template <int NW>
 __device__ __forceinline__ double chain_sum_count(double v, bool b, int &cnt, ChainShared &sh, int &slot, int warp,
                                                   int lane) {
 #pragma unroll
@@ -276,12 +356,18 @@ __device__ __forceinline__ double chain_sum_count(double v, bool b, int &cnt, Ch
         pb[warp] = bal;
     }
     __syncthreads();
-    cnt = __popc(static_cast<unsigned>(pb[0])) + __popc(static_cast<unsigned>(pb[1]));
-    return pp[0] + pp[1];
+    cnt = 0;
+    double t = pp[0] + pp[1];
+#pragma unroll
+    for (int w = 0; w < NW; w++) cnt += __popc(static_cast<unsigned>(pb[w]));
+#pragma unroll
+    for (int w = 2; w < NW; w++) t += pp[w];
+    return t;
 }
 
 // Maximum of non-positive doubles: the least bit pattern (+0 < -0 < -tiny <
 // ... < -inf as unsigned integers).
+template <int NW>
 __device__ __forceinline__ double chain_max_nonpos(double x, ChainShared &sh, int &slot, int warp, int lane) {
     unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
 #pragma unroll
@@ -293,19 +379,25 @@ __device__ __forceinline__ double chain_max_nonpos(double x, ChainShared &sh, in
     slot = (slot + 1) & 3;
     if (lane == 0) pp[warp] = b;
     __syncthreads();
-    b = pp[0] < pp[1] ? pp[0] : pp[1];
+    b = pp[0];
+#pragma unroll
+    for (int w = 1; w < NW; w++) b = pp[w] < b ? pp[w] : b;
     return __longlong_as_double(static_cast<long long>(b));
 }
 
 __device__ __forceinline__ bool chain_all(bool x) { return __syncthreads_and(x) != 0; }
 
+template <int NW>
 __device__ __forceinline__ unsigned chain_or(unsigned m, ChainShared &sh, int &slot, int warp, int lane) {
     m = __reduce_or_sync(kFull, m);
     unsigned long long *pp = sh.bits[slot];
     slot = (slot + 1) & 3;
     if (lane == 0) pp[warp] = m;
     __syncthreads();
-    return static_cast<unsigned>(pp[0] | pp[1]);
+    unsigned long long o = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) o |= pp[w];
+    return static_cast<unsigned>(o);
 }
 
 // Releases cells c0 .. n_cells-1 once world sw alone has non-zero weight
@@ -313,6 +405,7 @@ __device__ __forceinline__ unsigned chain_or(unsigned m, ChainShared &sh, int &s
 // variance is 0; otherwise every other world has weight exactly 0, so the
 // mean is y_sw and the variance 0, unless some release value is not finite,
 // which makes the sums NaN.  No posterior update happens either way.
+template <int W>
 __device__ void collapsed_tail(const FinParams &p, uint64_t c0, uint64_t n_cells, int jstar, int sw,
                                ChainShared &sh, int &slot) {
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -328,18 +421,18 @@ __device__ void collapsed_tail(const FinParams &p, uint64_t c0, uint64_t n_cells
             int s = static_cast<int>(c0 % p.n_specs);
             for (int k = 0; k < kend; k++) {
                 const int code = cell_code(p.spec[s]);
-                if ((code & 3) == 2 && ((p.meta[2 * g + 1] >> t) & 1ull)) {
+                if ((code & 3) == 2 && group_or<W>(p, g).bit(t)) {
                     const unsigned long long v =
-                        static_cast<const unsigned long long *>(p.spec[s].out)[static_cast<size_t>(g) * kWorlds + t];
+                        static_cast<const unsigned long long *>(p.spec[s].out)[static_cast<size_t>(g) * W + t];
                     if (raw_nonfinite(v, code)) bad |= 1u << k;
                 }
                 if (++s == p.n_specs) s = 0, g++;
             }
-            bad = chain_or(bad, sh, slot, warp, lane);
+            bad = chain_or<W / 32>(bad, sh, slot, warp, lane);
         }
         if (warp == 0 && lane < kend) {
             const uint64_t c = c0 + lane;
-            const CellDraw d = draw_cell(p, c);
+            const CellDraw<W> d = draw_cell<W>(p, c);
             uint32_t f = d.diversity ? PAC_F_DIVERSITY : 0u;
             if (d.null_) {
                 p.noised[c] = 0.0;
@@ -350,9 +443,9 @@ __device__ void collapsed_tail(const FinParams &p, uint64_t c0, uint64_t n_cells
                 const FinSpec &sp = p.spec[c % p.n_specs];
                 const int code = cell_code(sp);
                 const unsigned long long *o =
-                    static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * kWorlds;
-                const double yj = raw_to_double(((d.orm >> jstar) & 1ull) ? o[jstar] : 0ull, code);
-                const double ys = raw_to_double(((d.orm >> sw) & 1ull) ? o[sw] : 0ull, code);
+                    static_cast<const unsigned long long *>(sp.out) + static_cast<size_t>(g) * W;
+                const double yj = raw_to_double(d.orm.bit(jstar) ? o[jstar] : 0ull, code);
+                const double ys = raw_to_double(d.orm.bit(sw) ? o[sw] : 0ull, code);
                 p.noised[c] = (ys == yj || !((bad >> lane) & 1u)) ? yj : __longlong_as_double(0x7FF8000000000000ll);
                 p.is_null[c] = 0;
                 p.flags[c] = f | PAC_F_ZEROVAR;
@@ -361,13 +454,15 @@ __device__ void collapsed_tail(const FinParams &p, uint64_t c0, uint64_t n_cells
     }
 }
 
+template <int W>
 __device__ void finalize_chain(const FinParams &p) {
+    constexpr int NW = W / 32;
     __shared__ ChainShared sh;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> 58);
+    const int jstar = static_cast<int>(counter_draw(p.seed, kStreamJstar, 0) >> Worlds<W>::kJShift);
     const double inv2b = 1.0 / (2.0 * p.budget);
     const bool adaptive = p.mode != PAC_FIN_INDEPENDENT;
-    double L = 0.0, w = 1.0, se = static_cast<double>(kWorlds), rse = 1.0 / se;
+    double L = 0.0, w = 1.0, se = static_cast<double>(W), rse = 1.0 / se;
     bool sup = true;     // posterior of world t is non-zero
     bool single = false; // one world alone has non-zero weight
     int slot = 0;
@@ -380,7 +475,7 @@ __device__ void finalize_chain(const FinParams &p) {
 #pragma unroll
     for (int i = 0; i < kAhead; i++) {
         if (pc < n_cells) {
-            ring[i] = load_raw(p, pg, ps, t, jstar);
+            ring[i] = load_raw<W>(p, pg, ps, t, jstar);
             pc++;
             if (++ps == p.n_specs) ps = 0, pg++;
         }
@@ -390,11 +485,11 @@ __device__ void finalize_chain(const FinParams &p) {
         const uint64_t rem = n_cells - c0;
         const int kend = rem < 32 ? static_cast<int>(rem) : 32;
         // posterior-free draws of cells c0 .. c0+31, one per lane
-        CellDraw dl{0ull, true, false};
+        CellDraw<W> dl = no_cell<W>();
         double zc = 0.0;
         if (lane < kend) {
             const uint64_t cl = c0 + lane;
-            dl = draw_cell(p, cl);
+            dl = draw_cell<W>(p, cl);
             if (!dl.null_) zc = normal_draw(p.seed, cl);
         }
         const uint32_t nulls = __ballot_sync(kFull, dl.null_);
@@ -406,28 +501,28 @@ __device__ void finalize_chain(const FinParams &p) {
 #pragma unroll
             for (int i = 0; i + 1 < kAhead; i++) ring[i] = ring[i + 1];
             if (pc < n_cells) {
-                ring[kAhead - 1] = load_raw(p, pg, ps, t, jstar);
+                ring[kAhead - 1] = load_raw<W>(p, pg, ps, t, jstar);
                 pc++;
                 if (++ps == p.n_specs) ps = 0, pg++;
             }
             if (!adaptive) {
-                L = 0.0, w = 1.0, se = static_cast<double>(kWorlds), rse = 1.0 / se;
+                L = 0.0, w = 1.0, se = static_cast<double>(W), rse = 1.0 / se;
                 sup = true;
             }
             if ((nulls >> kc) & 1u) continue;
-            const unsigned long long orm = __shfl_sync(kFull, dl.orm, kc);
+            const OrMask<W> orm = dl.orm.shfl(kc);
             const double z = __shfl_sync(kFull, zc, kc);
-            const unsigned long long yr = ((orm >> t) & 1ull) ? cur.y : 0ull;
-            const unsigned long long yjr = ((orm >> jstar) & 1ull) ? cur.yj : 0ull;
+            const unsigned long long yr = orm.bit(t) ? cur.y : 0ull;
+            const unsigned long long yjr = orm.bit(jstar) ? cur.yj : 0ull;
             const double yj = raw_to_double(yjr, cur.code);
             // step 1: variance under the posterior, exactly 0 when all worlds of
             // non-zero posterior agree (then neither sum is needed)
             double var = 0.0, y = 0.0;
             if (!chain_all(!sup || same_value(yr, yjr, cur.code))) {
                 y = raw_to_double(yr, cur.code);
-                const double mu = chain_sum(w * y, sh, slot, warp, lane) * rse;
+                const double mu = chain_sum<NW>(w * y, sh, slot, warp, lane) * rse;
                 const double d = y - mu;
-                var = chain_sum(w * d * d, sh, slot, warp, lane) * rse;
+                var = chain_sum<NW>(w * d * d, sh, slot, warp, lane) * rse;
             }
             // step 2: noise variance; step 3: release
             const double delta = var * inv2b;
@@ -444,14 +539,14 @@ __device__ void finalize_chain(const FinParams &p) {
             if (upd && (adaptive || c0 + kc + 1 == n_cells)) {
                 const double e = yt - y;
                 L = fma(e * e, plain ? -0.5 / delta : -0.5 * rs * rs, L);
-                L -= chain_max_nonpos(L, sh, slot, warp, lane);
+                L -= chain_max_nonpos<NW>(L, sh, slot, warp, lane);
                 w = exp(L);
                 if (adaptive) {
                     int cnt;
-                    se = chain_sum_count(w, w > 0.0, cnt, sh, slot, warp, lane);
+                    se = chain_sum_count<NW>(w, w > 0.0, cnt, sh, slot, warp, lane);
                     single = cnt == 1;
                 } else {
-                    se = chain_sum(w, sh, slot, warp, lane);
+                    se = chain_sum<NW>(w, sh, slot, warp, lane);
                 }
                 rse = 1.0 / se;
                 sup = w * rse > 0.0;
@@ -479,39 +574,48 @@ __device__ void finalize_chain(const FinParams &p) {
         slot = (slot + 1) & 3;
         if (lane == 0) pp[warp] = bal;
         __syncthreads();
-        const int sw = pp[0] ? __ffs(static_cast<int>(pp[0])) - 1 : 32 + __ffs(static_cast<int>(pp[1])) - 1;
-        collapsed_tail(p, c0, n_cells, jstar, sw, sh, slot);
+        int sw = 0;
+#pragma unroll
+        for (int k = NW - 1; k >= 0; k--)
+            if (pp[k]) sw = 32 * k + __ffs(static_cast<int>(pp[k])) - 1;
+        collapsed_tail<W>(p, c0, n_cells, jstar, sw, sh, slot);
     }
     if (p.posterior) p.posterior[t] = w * rse;
 }
 
-__global__ void __launch_bounds__(kChainThreads) k_finalize_adaptive(const __grid_constant__ FinParams p) {
-    finalize_chain(p);
+template <int W>
+__global__ void __launch_bounds__(W) k_finalize_adaptive(const __grid_constant__ FinParams p) {
+    finalize_chain<W>(p);
 }
 
 // One posterior chain per query of a batch.
-__global__ void __launch_bounds__(kChainThreads) k_finalize_batch(const FinParams *__restrict__ ps, int n) {
-    if (static_cast<int>(blockIdx.x) < n) finalize_chain(ps[blockIdx.x]);
+__global__ void __launch_bounds__(kWorlds) k_finalize_batch(const FinParams *__restrict__ ps, int n) {
+    if (static_cast<int>(blockIdx.x) < n) finalize_chain<kWorlds>(ps[blockIdx.x]);
 }
 
-}  // namespace
-
-cudaError_t launch_finalize(const FinParams &p, cudaStream_t s) {
+template <int W>
+cudaError_t launch_finalize_w(const FinParams &p, cudaStream_t s) {
     const uint64_t n_cells = static_cast<uint64_t>(p.n_groups) * p.n_specs;
     if (p.mode == PAC_FIN_ADAPTIVE) {
-        k_finalize_adaptive<<<1, kChainThreads, 0, s>>>(p);
+        k_finalize_adaptive<W><<<1, W, 0, s>>>(p);
     } else {
         uint64_t blocks = (n_cells * 32 + 255) / 256;
         if (blocks > 152 * 16) blocks = 152 * 16;
         if (blocks == 0) blocks = 1;
-        k_finalize_independent<<<static_cast<unsigned>(blocks), 256, 0, s>>>(p);
+        k_finalize_independent<W><<<static_cast<unsigned>(blocks), 256, 0, s>>>(p);
     }
     return cudaGetLastError();
 }
 
+}  // namespace
+
+cudaError_t launch_finalize(const FinParams &p, cudaStream_t s) { return launch_finalize_w<kWorlds>(p, s); }
+
+cudaError_t launch_finalize128(const FinParams &p, cudaStream_t s) { return launch_finalize_w<kWorlds128>(p, s); }
+
 cudaError_t launch_finalize_batch(const FinParams *d_params, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_finalize_batch<<<static_cast<unsigned>(n), kChainThreads, 0, s>>>(d_params, n);
+    k_finalize_batch<<<static_cast<unsigned>(n), kWorlds, 0, s>>>(d_params, n);
     return cudaGetLastError();
 }
 

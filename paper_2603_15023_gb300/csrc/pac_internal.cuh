@@ -65,6 +65,26 @@ __host__ __device__ __forceinline__ uint64_t keyed_world_mask(int64_t key, uint6
     return lo | ((lo ^ 0xffffffffull) << 32);
 }
 
+// m = 128 worlds (Sec. 2: m = 128 is possible with twice the state): two
+// keyed re-hashes of one engine hash, h_a with K and h_b with K2.  Word 0
+// holds worlds 0..63, word 1 worlds 64..127.  Balanced: word 0 = low 32 bits
+// of h_a | low 32 bits of h_b << 32, word 1 its complement (every PU in
+// exactly 64 worlds); raw: h_a and h_b.
+constexpr int kWorlds128 = 128;
+
+__host__ __device__ __forceinline__ void keyed_world_mask128(int64_t key, uint64_t k1, uint64_t k2, int mode,
+                                                             uint64_t &w0, uint64_t &w1) {
+    const uint64_t inner = mm3_fmix64(static_cast<uint64_t>(key));
+    const uint64_t ha = mm3_fmix64(inner ^ k1), hb = mm3_fmix64(inner ^ k2);
+    if (mode == PAC_HASH_RAW) {
+        w0 = ha;
+        w1 = hb;
+        return;
+    }
+    w0 = (ha & 0xffffffffull) | (hb << 32);
+    w1 = ~w0;
+}
+
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea & Flood 2014) used as a counter-based generator:
 // output i of the sequence started at state s is mix(s + (i+1) * gamma).

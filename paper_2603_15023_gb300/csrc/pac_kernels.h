@@ -49,6 +49,10 @@ cudaError_t launch_bitloop_merge(const BitloopParams &p, int n_parts, bool atomi
 cudaError_t launch_hash(const int64_t *keys, uint64_t *masks, size_t n, uint64_t qkey, int mode,
                         int n_sms, cudaStream_t s);
 
+// ---- path dispatch of pac_aggregate_multi (checked arguments) -----------
+pac_status aggregate_dispatch(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
+                              uint64_t *meta, cudaStream_t stream);
+
 // ---- PAC selection (Sec. 4.2 "PAC Selection") ---------------------------
 struct SelectDev {
     const void *col;      // [n] of vtype
@@ -137,6 +141,8 @@ cudaError_t launch_lift(const LiftParams &p, int n_sms, cudaStream_t s);
 cudaError_t launch_filter(const double *b, uint32_t n_groups, uint64_t seed, uint8_t *keep, int n_sms,
                           cudaStream_t s);
 cudaError_t launch_finalize(const FinParams &p, cudaStream_t s);
+// The same release over 128 worlds (meta [G][3], results [G][128]).
+cudaError_t launch_finalize128(const FinParams &p, cudaStream_t s);
 // One warp per query: d_params[n] device array of per-query parameters.
 cudaError_t launch_finalize_batch(const FinParams *d_params, int n, cudaStream_t s);
 

@@ -45,8 +45,12 @@ constexpr int kThreads = 512;        // producer threads: two groups of 8 warps
 constexpr int kGroupThreads = 256;   // one producer group
 constexpr int kMmaWarps = 4;         // warps issuing tcgen05.mma
 constexpr int kMaxSlots = 16;        // accumulator slots (one group each)
-constexpr int kRows = 2;             // rows per producer thread per tile
-constexpr int kTileRows = kGroupThreads * kRows;  // a producer group fills one stage per tile
+// M = accumulator rows = worlds (64, or 128 for m = 128).  An M = 128
+// operand row is twice as wide, so its tiles hold half the rows.
+template <int M>
+__host__ __device__ constexpr int rows_per_thread() { return M == 64 ? 2 : 1; }
+template <int M>
+__host__ __device__ constexpr int tile_rows() { return kGroupThreads * rows_per_thread<M>(); }
 constexpr int kStages = 2;                        // one per producer group
 constexpr int kMmaK = 32;               // rows per tcgen05.mma of 8-bit operands
 constexpr int kMaxGroups = 8;
@@ -62,6 +66,7 @@ __host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
 
 struct MmaParams {
     InputDev in;
+    uint64_t qkey2;          // K2 of the second mask word (m = 128 from keys)
     const long long *col[kMaxCols];
     int32_t n_cols;
     int32_t n_alloc;
@@ -119,9 +124,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// kind::f8f6f4, A = B = E4M3, D = F32, A and B MN-major, M = 64.
+// kind::f8f6f4, A = B = E4M3, D = F32, A and B MN-major, M = 64 or 128.
+template <int M>
 __device__ __forceinline__ uint32_t instr_desc(int n) {
-    return (1u << 4) | (1u << 15) | (1u << 16) | (static_cast<uint32_t>(n >> 3) << 17) | (4u << 24);
+    return (1u << 4) | (1u << 15) | (1u << 16) | (static_cast<uint32_t>(n >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
@@ -137,11 +144,6 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
 
 // 4 mask bits -> 4 bytes 0x00/0x01
 __device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
-
-// 16 bits -> 16 bytes of 0x00/0x01 (one 16-world column block of A)
-__device__ __forceinline__ void write_bits16(uint32_t addr, uint32_t x) {
-    sts128(addr, spread4(x & 0xF), spread4((x >> 4) & 0xF), spread4((x >> 8) & 0xF), spread4((x >> 12) & 0xF));
-}
 
 // Digit bytes of one row.  C4 = 1: one column, feature 4+q = digit q.
 // C4 = 4: up to four columns, feature 4 + 4q + c = digit q of column c.
@@ -231,9 +233,10 @@ __device__ __forceinline__ int digit_class(int need) {
     return 16;
 }
 
-// Raw columns of one row, loaded two tiles ahead of their use.
+// Raw columns of one row, loaded two tiles ahead of their use.  km2: the
+// second mask word of an m = 128 mask input.
 struct RawRow {
-    unsigned long long km;
+    unsigned long long km, km2;
     uint32_t gid;
     long long v0, v1, v2, v3;
 };
@@ -249,12 +252,18 @@ __device__ __forceinline__ uint32_t gid_load(const void *gids, uint64_t row) {
 // Loads row `off` of the CTA's range.  Rows past the end load the last row
 // instead (always in bounds) and come back with the invalid group id; value
 // columns beyond n_cols load column 0 and are zeroed.  No branches.
-template <int C4, int GB>
+template <int C4, int GB, int M>
 __device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin, uint32_t off, uint32_t n_rows,
                                          RawRow &r) {
     const bool ok = off < n_rows;
     const uint64_t row = cta_begin + (ok ? off : n_rows - 1);
-    r.km = __ldg(static_cast<const unsigned long long *>(p.in.km) + row);
+    if (M == 128 && (p.in.in_flags & PAC_IN_MASKS)) {  // [n][2] mask words
+        r.km = __ldg(static_cast<const unsigned long long *>(p.in.km) + 2 * row);
+        r.km2 = __ldg(static_cast<const unsigned long long *>(p.in.km) + 2 * row + 1);
+    } else {
+        r.km = __ldg(static_cast<const unsigned long long *>(p.in.km) + row);
+        r.km2 = 0;
+    }
     const uint32_t g = gid_load<GB>(p.in.gids, row);
     // all-ones marks a row past the end: a stored all-ones id (out of range
     // too) becomes all-ones minus one, so it is still skipped and reported
@@ -273,25 +282,25 @@ __device__ __forceinline__ void load_raw(const MmaParams &p, uint64_t cta_begin,
     }
 }
 
-// Both rows of a thread under one dispatch on the tile's digit class.
-template <int C4>
-__device__ __forceinline__ void write_features_2rows(int L, uint32_t b_stage, uint32_t s0, uint32_t s1,
-                                                     const RawRow &r0, const RawRow &r1, bool sgn) {
-#define PAC_FEAT2(LL)                                                                        \
-    do {                                                                                     \
-        write_features<C4, LL>(b_stage, s0, r0.v0, r0.v1, r0.v2, r0.v3, sgn);                 \
-        write_features<C4, LL>(b_stage, s1, r1.v0, r1.v1, r1.v2, r1.v3, sgn);                 \
+// The rows of a thread under one dispatch on the tile's digit class.
+template <int C4, int R>
+__device__ __forceinline__ void write_features_rows(int L, uint32_t b_stage, const uint32_t (&sl)[R],
+                                                    const RawRow (&rr)[R], bool sgn) {
+#define PAC_FEATR(LL)                                                                         \
+    do {                                                                                      \
+        _Pragma("unroll") for (int r = 0; r < R; r++)                                         \
+            write_features<C4, LL>(b_stage, sl[r], rr[r].v0, rr[r].v1, rr[r].v2, rr[r].v3, sgn); \
     } while (0)
     if (C4 == 1) {
-        if (L <= 12) PAC_FEAT2(12);
-        else PAC_FEAT2(16);
+        if (L <= 12) PAC_FEATR(12);
+        else PAC_FEATR(16);
     } else {
-        if (L <= 4) PAC_FEAT2(4);
-        else if (L <= 6) PAC_FEAT2(6);
-        else if (L <= 8) PAC_FEAT2(8);
-        else PAC_FEAT2(16);
+        if (L <= 4) PAC_FEATR(4);
+        else if (L <= 6) PAC_FEATR(6);
+        else if (L <= 8) PAC_FEATR(8);
+        else PAC_FEATR(16);
     }
-#undef PAC_FEAT2
+#undef PAC_FEATR
 }
 
 // Named barrier among the warps of one producer group (ids 1 and 2).
@@ -371,11 +380,15 @@ __device__ void plan_slots(MmaShared &sh, uint32_t G, uint32_t max_slots, const 
     }
 }
 
-// One tile of the producer warps: statistics, layout, operands.
-template <int C4>
+// One tile of the producer warps: statistics, layout, operands.  Each
+// thread holds R = rows_per_thread<M>() rows; a row's M world bits are kept
+// as M/32 words (word k: worlds 32k .. 32k+31).
+template <int C4, int M>
 __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, uint32_t it, uint32_t max_slots,
-                                             const RawRow &r0, const RawRow &r1, uint32_t a_stage, uint32_t b_stage,
-                                             bool keys_in, bool balanced_keys) {
+                                             const RawRow (&rr)[rows_per_thread<M>()], uint32_t a_stage,
+                                             uint32_t b_stage, bool keys_in, bool balanced_keys) {
+    constexpr int R = rows_per_thread<M>();
+    constexpr int kWords = M / 32;
     const int lane = threadIdx.x & 31;
     constexpr int kWarps = kGroupThreads / 32;
     const int pg = static_cast<int>(it & 1);                 // producer group = stage
@@ -385,29 +398,36 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
     const int pb = (it >> 1) & 1;                            // the group's tile parity
 
     // (1) group, world mask, magnitude and sign statistics of the rows
-    uint32_t gid[kRows], lo32[kRows], hi32[kRows];
-    bool valid[kRows];
+    uint32_t gid[R], wd[R][kWords];
+    bool valid[R];
     bool any_bad = false;
     const bool raw_hash = p.in.hash_mode == PAC_HASH_RAW;
     unsigned long long mag = 0, sgnbits = 0;
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
-        const RawRow &c = r == 0 ? r0 : r1;
+    for (int r = 0; r < R; r++) {
+        const RawRow &c = rr[r];
         gid[r] = c.gid;
         const bool bad = gid[r] != 0xFFFFFFFFu && gid[r] >= G;  // out-of-range group id: skip, report
         any_bad |= bad;
         gid[r] = bad ? 0xFFFFFFFFu : gid[r];
         valid[r] = gid[r] != 0xFFFFFFFFu;
-        {
+        if (M == 64) {
             const uint64_t h = mm3_fmix64(mm3_fmix64(c.km) ^ p.in.qkey);
             const uint32_t hl = static_cast<uint32_t>(h);
             const uint32_t hh = raw_hash ? static_cast<uint32_t>(h >> 32) : ~hl;  // balanced: complement
-            lo32[r] = keys_in ? hl : static_cast<uint32_t>(c.km);
-            hi32[r] = keys_in ? hh : static_cast<uint32_t>(c.km >> 32);
-        }
-        if (valid[r] && drop_row(p.in, (static_cast<uint64_t>(hi32[r]) << 32) | lo32[r])) {
-            gid[r] = 0xFFFFFFFFu;  // a row of no group: into the trash slot like a padding row
-            valid[r] = false;
+            wd[r][0] = keys_in ? hl : static_cast<uint32_t>(c.km);
+            wd[r][1] = keys_in ? hh : static_cast<uint32_t>(c.km >> 32);
+            if (valid[r] && drop_row(p.in, (static_cast<uint64_t>(wd[r][1]) << 32) | wd[r][0])) {
+                gid[r] = 0xFFFFFFFFu;  // a row of no group: into the trash slot like a padding row
+                valid[r] = false;
+            }
+        } else {
+            uint64_t w0 = c.km, w1 = c.km2;
+            if (keys_in) keyed_world_mask128(static_cast<int64_t>(c.km), p.in.qkey, p.qkey2, p.in.hash_mode, w0, w1);
+            wd[r][0] = static_cast<uint32_t>(w0);
+            wd[r][1] = static_cast<uint32_t>(w0 >> 32);
+            wd[r][kWords > 2 ? 2 : 0] = static_cast<uint32_t>(w1);
+            wd[r][kWords > 3 ? 3 : 0] = static_cast<uint32_t>(w1 >> 32);
         }
         // OR of |v| in one's complement (v, or ~v for v < 0) bounds every
         // value's bit length; the sign bits say whether any is negative
@@ -421,23 +441,23 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
         }
     }
     // (2) ranks inside the warp: rows of one group get consecutive ranks,
-    // pass-0 rows first; leaders publish the warp's count per group
+    // row 0 of every thread first; leaders publish the warp's count per group
     if (__any_sync(kFull, any_bad) && lane == 0) raise_status(p.status, kStatusBadGroup);
-    uint32_t rank[kRows];
+    uint32_t rank[R];
     {
         uint32_t *cnt_row = sh.st_cnt[pg][pb][warp];
         if (lane < kMaxGroups) cnt_row[lane] = 0;
         __syncwarp();
-        const uint32_t peers0 = __match_any_sync(kFull, gid[0]);
-        rank[0] = __popc(peers0 & lt);
-        if (valid[0] && rank[0] == 0) cnt_row[gid[0]] = __popc(peers0);
-        __syncwarp();
-        const uint32_t peers1 = __match_any_sync(kFull, gid[1]);
-        const uint32_t r1 = __popc(peers1 & lt);
-        const uint32_t before1 = valid[1] ? cnt_row[gid[1]] : 0u;
-        rank[1] = before1 + r1;
-        __syncwarp();
-        if (valid[1] && r1 == 0) cnt_row[gid[1]] = before1 + __popc(peers1);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const uint32_t peers = __match_any_sync(kFull, gid[r]);
+            const uint32_t rk = __popc(peers & lt);
+            const uint32_t before = (r > 0 && valid[r]) ? cnt_row[gid[r]] : 0u;
+            rank[r] = before + rk;
+            if (r > 0) __syncwarp();
+            if (valid[r] && rk == 0) cnt_row[gid[r]] = before + __popc(peers);
+            __syncwarp();
+        }
     }
     const uint32_t mag_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(mag >> 32));
     const uint32_t mag_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(mag));
@@ -478,9 +498,9 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
     const int N = C4 == 1 ? round16(4 + L) : round16(4 + L * 4);
     const uint32_t base = glo + before;  // lane g: this warp's first slot in group g
     // invalid rows (past the end of the range) go to a trash slot past k_cap
-    uint32_t slot[kRows];
+    uint32_t slot[R];
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
+    for (int r = 0; r < R; r++) {
         const uint32_t sv = __shfl_sync(kFull, base, valid[r] ? static_cast<int>(gid[r]) : 0) + rank[r];
         slot[r] = valid[r] ? sv : p.k_cap;
     }
@@ -506,24 +526,23 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
             if (lane == 0) plan_slots(sh, G, max_slots, cg);
         }
     }
-    // (5) operands into the stage, rows sorted by group
+    // (5) operands into the stage, rows sorted by group.  An A row is M world
+    // bytes in M/16 column blocks of 16 (one core matrix row each); under
+    // balanced keys the upper half is the constant written at launch.
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
-        const uint32_t x = lo32[r], y = hi32[r];
-        const uint32_t a_row = a_stage + (slot[r] >> 3) * 512 + (slot[r] & 7) * 16;
-        const uint32_t w0 = spread4(x & 0xF), w1 = spread4((x >> 4) & 0xF);
-        const uint32_t w2 = spread4((x >> 8) & 0xF), w3 = spread4((x >> 12) & 0xF);
-        const uint32_t w4 = spread4((x >> 16) & 0xF), w5 = spread4((x >> 20) & 0xF);
-        const uint32_t w6 = spread4((x >> 24) & 0xF), w7 = spread4(x >> 28);
-        sts128(a_row, w0, w1, w2, w3);
-        sts128(a_row + 128, w4, w5, w6, w7);
-        // balanced keys: the upper half of A is the constant written at launch
-        if (!balanced_keys) {
-            write_bits16(a_row + 256, y & 0xFFFFu);
-            write_bits16(a_row + 384, y >> 16);
+    for (int r = 0; r < R; r++) {
+        const uint32_t a_row = a_stage + (slot[r] >> 3) * (M * 8) + (slot[r] & 7) * 16;
+#pragma unroll
+        for (int k = 0; k < kWords; k++) {
+            if (k >= kWords / 2 && balanced_keys) continue;
+            const uint32_t x = wd[r][k];
+            sts128(a_row + 256 * k, spread4(x & 0xF), spread4((x >> 4) & 0xF), spread4((x >> 8) & 0xF),
+                   spread4((x >> 12) & 0xF));
+            sts128(a_row + 256 * k + 128, spread4((x >> 16) & 0xF), spread4((x >> 20) & 0xF),
+                   spread4((x >> 24) & 0xF), spread4(x >> 28));
         }
     }
-    write_features_2rows<C4>(L, b_stage, slot[0], slot[1], r0, r1, neg);
+    write_features_rows<C4, R>(L, b_stage, slot, rr, neg);
     // zero the rows that pad each group's run to the MMA step (warp g: group g)
     if (warp < static_cast<int>(G)) {
         const uint32_t gcnt = __shfl_sync(kFull, cnt, warp), glen = __shfl_sync(kFull, len, warp);
@@ -541,14 +560,16 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
     if (lane == 0) mbar_arrive(&sh.full_bar[pg]);
 }
 
-// Warp-specialised CTA: warps 0..15 produce operands (two rows per thread per
-// tile), warps 16..19 issue the tensor-core MMAs, each into its own
-// accumulator slots.  Producers agree on a tile's layout through a
-// producer-only named barrier; the single operand stage is handed over with
+// Warp-specialised CTA: warps 0..15 produce operands (rows_per_thread<M>()
+// rows per thread per tile), warps 16..19 issue the tensor-core MMAs, each
+// into its own accumulator slots.  Producers agree on a tile's layout through
+// a producer-only named barrier; the single operand stage is handed over with
 // two mbarriers (full: 16 producer-warp arrivals; empty: one tcgen05.commit
-// per MMA warp).
-template <int C4, int GB>
+// per MMA warp).  M = 64 or 128 accumulator rows (worlds).
+template <int C4, int GB, int M>
 __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const __grid_constant__ MmaParams p) {
+    constexpr int R = rows_per_thread<M>();
+    constexpr int kTile = tile_rows<M>();
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ MmaShared sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -586,11 +607,11 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
         }
         asm volatile("tcgen05.wait::st.sync.aligned;");
     }
-    // Balanced keys: worlds 32..63 are the complements of worlds 0..31, so the
-    // upper half of A is one constant for every row -- world 32 set, 33..63
-    // clear -- and accumulator row 32 becomes the run's total (world 32 + j =
-    // total - world j, derived by the finish kernel).  Written once per stage;
-    // the producers then write only worlds 0..31.
+    // Balanced keys: worlds M/2..M-1 are the complements of worlds 0..M/2-1,
+    // so the upper half of A is one constant for every row -- world M/2 set,
+    // the rest clear -- and accumulator row M/2 becomes the run's total (world
+    // M/2 + j = total - world j, derived by the finish kernel).  Written once
+    // per stage; the producers then write only the lower half.
     // The world bytes of every slot start at 0, so that the rows padding a
     // group's run (their features zeroed per tile) multiply finite values.
     {
@@ -598,11 +619,10 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
         const uint32_t slots = p.k_cap + 8;
         for (uint32_t i = static_cast<uint32_t>(tid); i < kStages * slots; i += blockDim.x) {
             const uint32_t stage = i / slots, sl = i % slots;
-            const uint32_t a_row = smem_u32(smem) + stage * (p.a_bytes + p.b_bytes) + (sl >> 3) * 512 + (sl & 7) * 16;
-            sts128(a_row, 0u, 0u, 0u, 0u);
-            sts128(a_row + 128, 0u, 0u, 0u, 0u);
-            sts128(a_row + 256, bal ? 1u : 0u, 0u, 0u, 0u);
-            sts128(a_row + 384, 0u, 0u, 0u, 0u);
+            const uint32_t a_row =
+                smem_u32(smem) + stage * (p.a_bytes + p.b_bytes) + (sl >> 3) * (M * 8) + (sl & 7) * 16;
+#pragma unroll
+            for (int k = 0; k < M / 16; k++) sts128(a_row + 128 * k, (bal && k == M / 32) ? 1u : 0u, 0u, 0u, 0u);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -613,7 +633,7 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
     const uint64_t begin = static_cast<uint64_t>(blockIdx.x) * p.rows_per_cta;
     const uint64_t end = min(p.in.n, begin + p.rows_per_cta);
     const uint32_t n_rows = static_cast<uint32_t>(end - begin);
-    const uint32_t n_tiles = (n_rows + kTileRows - 1) / kTileRows;
+    const uint32_t n_tiles = (n_rows + kTile - 1) / kTile;
     const uint32_t smem_base = smem_u32(smem);
 
     if (warp >= kWarps) {
@@ -662,11 +682,11 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
                     my_n = found < kMaxSlots / kMmaWarps ? found : kMaxSlots / kMmaWarps;
                 }
                 const int N = sh.meta_n[s];
-                const uint32_t idesc = instr_desc(N);
+                const uint32_t idesc = instr_desc<M>(N);
                 const uint32_t lbo_b = (N / 16) * 128;
                 // descriptors of slot 0; one 32-row block moves the start address
-                // (in 16-byte units) by 4*512/16 for A and 4*lbo_b/16 for B
-                const uint64_t da0 = smem_desc(a_stage, 512, 128);
+                // (in 16-byte units) by 4*(8M)/16 for A and 4*lbo_b/16 for B
+                const uint64_t da0 = smem_desc(a_stage, M * 8, 128);
                 const uint64_t db0 = smem_desc(b_stage, lbo_b, 128);
                 const uint32_t step_b = lbo_b >> 2;
                 uint32_t lo[kMaxSlots / kMmaWarps], nb[kMaxSlots / kMmaWarps];
@@ -683,9 +703,9 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
                     const uint32_t d = tmem + my_sl[k] * static_cast<uint32_t>(p.n_alloc);
                     const uint32_t blk0 = (lo[k] >> 5) + my_idx[k];
                     const uint32_t blk_end = (lo[k] >> 5) + nb[k];
-                    uint64_t da = da0 + blk0 * 128u;
+                    uint64_t da = da0 + blk0 * (2u * M);
                     uint64_t db = db0 + blk0 * step_b;
-                    const uint64_t sa = 128ull * my_share[k], sb = static_cast<uint64_t>(step_b) * my_share[k];
+                    const uint64_t sa = 2ull * M * my_share[k], sb = static_cast<uint64_t>(step_b) * my_share[k];
                     for (uint32_t blk = blk0; blk < blk_end; blk += my_share[k]) {
                         mma_f8(d, da, db, idesc);
                         da += sa;
@@ -717,26 +737,22 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
         const uint32_t b_stage = a_stage + p.a_bytes;
         const bool keys_in = !(p.in.in_flags & PAC_IN_MASKS);
         const bool balanced_keys = keys_in && p.in.hash_mode == PAC_HASH_BALANCED;
-        RawRow a0, a1, b0, b1;
-        {
-            const uint32_t o0 = pg * kTileRows + gt, o1 = (pg + 2) * kTileRows + gt;
-            load_raw<C4, GB>(p, begin, o0, n_rows, a0);
-            load_raw<C4, GB>(p, begin, o0 + kGroupThreads, n_rows, a1);
-            load_raw<C4, GB>(p, begin, o1, n_rows, b0);
-            load_raw<C4, GB>(p, begin, o1 + kGroupThreads, n_rows, b1);
+        // thread gt holds rows gt + r * kGroupThreads (r < R) of a tile
+        RawRow ra[R], rb[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            load_raw<C4, GB, M>(p, begin, pg * kTile + gt + r * kGroupThreads, n_rows, ra[r]);
+            load_raw<C4, GB, M>(p, begin, (pg + 2) * kTile + gt + r * kGroupThreads, n_rows, rb[r]);
         }
         for (uint32_t it = pg; it < n_tiles; it += 4) {
-            produce_tile<C4>(p, sh, it, max_slots, a0, a1, a_stage, b_stage, keys_in, balanced_keys);
-            {
-                const uint32_t off = (it + 4) * kTileRows + gt;
-                load_raw<C4, GB>(p, begin, off, n_rows, a0);
-                load_raw<C4, GB>(p, begin, off + kGroupThreads, n_rows, a1);
-            }
+            produce_tile<C4, M>(p, sh, it, max_slots, ra, a_stage, b_stage, keys_in, balanced_keys);
+#pragma unroll
+            for (int r = 0; r < R; r++) load_raw<C4, GB, M>(p, begin, (it + 4) * kTile + gt + r * kGroupThreads, n_rows, ra[r]);
             if (it + 2 < n_tiles) {
-                produce_tile<C4>(p, sh, it + 2, max_slots, b0, b1, a_stage, b_stage, keys_in, balanced_keys);
-                const uint32_t off = (it + 6) * kTileRows + gt;
-                load_raw<C4, GB>(p, begin, off, n_rows, b0);
-                load_raw<C4, GB>(p, begin, off + kGroupThreads, n_rows, b1);
+                produce_tile<C4, M>(p, sh, it + 2, max_slots, rb, a_stage, b_stage, keys_in, balanced_keys);
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    load_raw<C4, GB, M>(p, begin, (it + 6) * kTile + gt + r * kGroupThreads, n_rows, rb[r]);
             }
         }
     }
@@ -746,10 +762,11 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
     if (sh.abort_flag) {
         if (tid == 0) raise_status(p.status, kStatusTimeout);
     } else if (warp < 4) {
-        // read back: TMEM lane 32w + l (l < 16) holds world 16w + l; the slots
-        // of a group add into the same totals
+        // read back: for M = 64, TMEM lane 32w + l (l < 16) holds world
+        // 16w + l; for M = 128, lane 32w + l holds world 32w + l.  The slots of
+        // a group add into the same totals.
         const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
-        const int world = 16 * warp + lane;
+        const int world = (M / 4) * warp + lane;
         for (int sl = 0; sl < sh.n_slots; sl++) {
             const uint32_t g = sh.sl_group[sl];
             for (int c0 = 0; c0 < p.n_alloc; c0 += 16) {
@@ -761,8 +778,8 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
                       "=r"(r[15])
                     : "r"(tmem + lane_base + static_cast<uint32_t>(sl) * static_cast<uint32_t>(p.n_alloc) + c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (lane < 16) {
-                    unsigned long long *dst = p.acc + (static_cast<size_t>(g) * kWorlds + world) * p.n_alloc + c0;
+                if (lane < M / 4) {
+                    unsigned long long *dst = p.acc + (static_cast<size_t>(g) * M + world) * p.n_alloc + c0;
 #pragma unroll
                     for (int k = 0; k < 16; k++) {
                         const int x = __float2int_rn(__uint_as_float(r[k]) * 262144.0f);  // units of 2^-18
@@ -785,7 +802,8 @@ struct FinishParams {
     const unsigned long long *acc;
     const unsigned long long *ng;
     uint32_t G;
-    int32_t balanced;  // accumulator row 32 holds the run totals; worlds 32+j = total - world j
+    int32_t worlds;    // M: 64 (meta {n_g, or}) or 128 (meta {n_g, or word 0, or word 1})
+    int32_t balanced;  // accumulator row M/2 holds the run totals; worlds M/2+j = total - world j
     int32_t n_cols, c4, n_alloc;
     int32_t n_out;
     int32_t out_kind[kMaxSpecs];
@@ -800,20 +818,21 @@ struct FinishParams {
 // totals are read once and serve its SUM and AVG specs; the column-0 threads
 // also write COUNT and the metadata.
 __global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
-    const size_t cells = static_cast<size_t>(f.G) * kWorlds;
+    const int W = f.worlds, half = W / 2;
+    const size_t cells = static_cast<size_t>(f.G) * W;
     const int cp = f.n_cols > 0 ? f.n_cols : 1;
     const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
     const bool live = t < cells * cp;
     const int c = live ? static_cast<int>(t / cells) : 0;
     const size_t cell = live ? t % cells : 0;
-    const uint32_t g = static_cast<uint32_t>(cell / kWorlds);
-    const int j = static_cast<int>(cell % kWorlds);
-    // digit total k of this cell; under balanced keys world 32 + j is the
-    // group total (row 32) minus world j, exactly (wrapping 64-bit integers)
-    const bool derive = f.balanced && j >= 32;
+    const uint32_t g = static_cast<uint32_t>(cell / W);
+    const int j = static_cast<int>(cell % W);
+    // digit total k of this cell; under balanced keys world W/2 + j is the
+    // group total (row W/2) minus world j, exactly (wrapping 64-bit integers)
+    const bool derive = f.balanced && j >= half;
     const unsigned long long *a = f.acc + cell * f.n_alloc;
-    const unsigned long long *tot_row = f.acc + (static_cast<size_t>(g) * kWorlds + 32) * f.n_alloc;
-    const unsigned long long *low_row = f.acc + (static_cast<size_t>(g) * kWorlds + (j & 31)) * f.n_alloc;
+    const unsigned long long *tot_row = f.acc + (static_cast<size_t>(g) * W + half) * f.n_alloc;
+    const unsigned long long *low_row = f.acc + (static_cast<size_t>(g) * W + (j & (half - 1))) * f.n_alloc;
     auto digit = [&](int k) -> long long {
         return static_cast<long long>(derive ? tot_row[k] - low_row[k] : a[k]);
     };
@@ -823,8 +842,12 @@ __global__ void k_mma_finish(const __grid_constant__ FinishParams f) {
     if (!live) return;
     if (c == 0) {
         if (f.meta) {
-            if ((threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(f.meta + 2 * g + 1)[j >= 32 ? 1 : 0] = bal;
-            if (j == 0) f.meta[2 * g] = f.ng[g];
+            // meta per group: {n_g, OR word 0[, OR word 1]}; a warp's 32 cells
+            // are one 32-bit half of an OR word
+            const size_t stride = W == 64 ? 2 : 3;
+            if ((threadIdx.x & 31) == 0)
+                reinterpret_cast<uint32_t *>(f.meta + stride * g + 1 + (j >> 6))[(j >> 5) & 1] = bal;
+            if (j == 0) f.meta[stride * g] = f.ng[g];
         }
         for (int s = 0; s < f.n_out; s++)
             if (f.out_kind[s] == PAC_COUNT) static_cast<unsigned long long *>(f.out[s])[cell] = cnt;
@@ -890,8 +913,8 @@ bool mma_supported(const pac_input *in, const pac_agg_spec *specs, int n_specs) 
 
 // Builds the launch of the tensor-core path.  scratch: the accumulators
 // (mma_scratch_bytes bytes, cleared here); status: the device status word.
-static pac_status mma_plan(const pac_input *in, const pac_agg_spec *specs, int n_specs, int n_sms, MmaParams &p,
-                           size_t &smem, int &c4, const void **cols, int &C, const char **why) {
+static pac_status mma_plan(const pac_input *in, const pac_agg_spec *specs, int n_specs, int n_sms, int worlds,
+                           MmaParams &p, size_t &smem, int &c4, const void **cols, int &C, const char **why) {
     p = MmaParams{};
     C = mma_columns(specs, n_specs, cols);
     if (C < 0) {
@@ -917,14 +940,15 @@ static pac_status mma_plan(const pac_input *in, const pac_agg_spec *specs, int n
     p.n_cols = C;
     p.n_alloc = feat_alloc(Ceff);
     const uint32_t G = in->n_groups;
+    const uint32_t tile = worlds == 64 ? tile_rows<64>() : tile_rows<128>();
     uint64_t per = (in->n + n_sms - 1) / n_sms;
-    per = (per + kTileRows - 1) / kTileRows * kTileRows;
+    per = (per + tile - 1) / tile * tile;
     if (per > kMaxRowsPerCta) per = kMaxRowsPerCta;
-    if (per == 0) per = kTileRows;
+    if (per == 0) per = tile;
     p.rows_per_cta = static_cast<uint32_t>(per);
-    p.k_cap = (kTileRows + (kMmaK - 1) * G + kMmaK - 1) / kMmaK * kMmaK;
+    p.k_cap = (tile + (kMmaK - 1) * G + kMmaK - 1) / kMmaK * kMmaK;
     // one more 8-row block past k_cap takes the writes of invalid rows
-    p.a_bytes = (p.k_cap + 8) * 64;
+    p.a_bytes = (p.k_cap + 8) * static_cast<uint32_t>(worlds);
     p.b_bytes = (p.k_cap + 8) * p.n_alloc;
     smem = static_cast<size_t>(kStages) * (p.a_bytes + p.b_bytes);
     if (smem > 220 * 1024) {
@@ -936,25 +960,30 @@ static pac_status mma_plan(const pac_input *in, const pac_agg_spec *specs, int n
     return PAC_OK;
 }
 
-size_t mma_scratch_bytes(const pac_input *in, const pac_agg_spec *specs, int n_specs) {
+size_t mma_scratch_bytes(const pac_input *in, const pac_agg_spec *specs, int n_specs, int worlds) {
     const void *cols[kMaxCols];
     const int C = mma_columns(specs, n_specs, cols);
     const int Ceff = C <= 0 ? 1 : C;
-    return static_cast<size_t>(in->n_groups) * kWorlds * feat_alloc(Ceff) * 8 + 256 + in->n_groups * 8;
+    return static_cast<size_t>(in->n_groups) * worlds * feat_alloc(Ceff) * 8 + 256 + in->n_groups * 8;
 }
 
 pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
                       cudaStream_t stream, void *scratch, uint32_t *status, int n_sms, int *launches,
-                      const char **why, uint64_t wait_ns) {
+                      const char **why, uint64_t wait_ns, int worlds, uint64_t qkey2) {
     MmaParams p;
     size_t smem;
     int c4, C;
     const void *cols[kMaxCols];
-    pac_status st = mma_plan(in, specs, n_specs, n_sms, p, smem, c4, cols, C, why);
+    if (worlds != 64 && worlds != 128) {
+        *why = "tensor-core path: 64 or 128 worlds";
+        return PAC_E_INVALID;
+    }
+    pac_status st = mma_plan(in, specs, n_specs, n_sms, worlds, p, smem, c4, cols, C, why);
     if (st != PAC_OK) return st;
+    p.qkey2 = qkey2;
     const uint32_t G = in->n_groups;
     const uint64_t n_ctas = (in->n + p.rows_per_cta - 1) / p.rows_per_cta;
-    const size_t acc_bytes = static_cast<size_t>(G) * kWorlds * p.n_alloc * 8;
+    const size_t acc_bytes = static_cast<size_t>(G) * worlds * p.n_alloc * 8;
     p.acc = static_cast<unsigned long long *>(scratch);
     p.ng = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + ((acc_bytes + 255) / 256) * 256);
     p.status = status;
@@ -965,12 +994,17 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
         return PAC_E_CUDA;
     }
     const int gb = in->group_ids ? in->gid_bytes : 0;
-#define PAC_MMA_LAUNCH(C4_, GB_)                                                                              \
-    do {                                                                                                      \
-        e = cudaFuncSetAttribute(k_agg_mma<C4_, GB_>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                                 static_cast<int>(smem));                                                    \
-        if (e == cudaSuccess)                                                                                 \
-            k_agg_mma<C4_, GB_><<<static_cast<unsigned>(n_ctas), kThreads + 32 * kMmaWarps, smem, stream>>>(p); \
+#define PAC_MMA_LAUNCH1(C4_, GB_, M_)                                                                           \
+    do {                                                                                                        \
+        e = cudaFuncSetAttribute(k_agg_mma<C4_, GB_, M_>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                 static_cast<int>(smem));                                                      \
+        if (e == cudaSuccess)                                                                                   \
+            k_agg_mma<C4_, GB_, M_><<<static_cast<unsigned>(n_ctas), kThreads + 32 * kMmaWarps, smem, stream>>>(p); \
+    } while (0)
+#define PAC_MMA_LAUNCH(C4_, GB_)                              \
+    do {                                                      \
+        if (worlds == 64) PAC_MMA_LAUNCH1(C4_, GB_, 64);      \
+        else PAC_MMA_LAUNCH1(C4_, GB_, 128);                  \
     } while (0)
     if (c4 == 1) {
         switch (gb) {
@@ -988,6 +1022,7 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
         }
     }
 #undef PAC_MMA_LAUNCH
+#undef PAC_MMA_LAUNCH1
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         *why = cudaGetErrorString(e);
@@ -997,6 +1032,7 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
     f.acc = p.acc;
     f.ng = p.ng;
     f.G = G;
+    f.worlds = worlds;
     f.balanced = !(in->in_flags & PAC_IN_MASKS) && in->hash_mode == PAC_HASH_BALANCED;
     f.n_cols = C;
     f.c4 = c4;
@@ -1011,7 +1047,7 @@ pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_spec
         f.out[f.n_out] = specs[i].out;
         f.n_out++;
     }
-    const size_t threads = static_cast<size_t>(G) * kWorlds * (C > 0 ? C : 1);
+    const size_t threads = static_cast<size_t>(G) * worlds * (C > 0 ? C : 1);
     k_mma_finish<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, stream>>>(f);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -22,12 +22,15 @@ pac_status run_mma(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs,
                    uint64_t *meta, cudaStream_t stream, int *launches);
 
 // Scratch (accumulators and row counts) the tensor-core path needs.
-size_t mma_scratch_bytes(const pac_input *in, const pac_agg_spec *specs, int n_specs);
+size_t mma_scratch_bytes(const pac_input *in, const pac_agg_spec *specs, int n_specs, int worlds = 64);
 
 // Enqueues the tensor-core path with caller-provided scratch and status word.
 // wait_ns: limit of the kernel's pipeline waits (0: the default of 2 s).
+// worlds: 64, or 128 (masks [n][2], or keys hashed with query_key and
+// qkey2; meta [G][3]).  PAC_E_UNSUPPORTED when the tile does not fit shared
+// memory.
 pac_status mma_launch(const pac_input *in, const pac_agg_spec *specs, int n_specs, uint64_t *meta,
                       cudaStream_t stream, void *scratch, uint32_t *status, int n_sms, int *launches,
-                      const char **why, uint64_t wait_ns = 0);
+                      const char **why, uint64_t wait_ns = 0, int worlds = 64, uint64_t qkey2 = 0);
 
 }  // namespace pacgpu

@@ -70,6 +70,41 @@ inline pac_status check_specs(pac_ctx *ctx, const pac_input *in, const pac_agg_s
     return PAC_OK;
 }
 
+// Argument checks of a release (pac_finalize, pac_finalize128) and its
+// launch parameters.
+inline pac_status build_fin_params(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_specs, uint32_t n_groups,
+                                   const uint64_t *meta, uint64_t seed, double budget, int32_t mode,
+                                   double *noised, uint8_t *is_null, uint32_t *flags, double *posterior,
+                                   FinParams &p) {
+    if (n_specs < 1 || n_specs > PAC_MAX_SPECS || !specs) return fail(ctx, PAC_E_INVALID, "n_specs %d", n_specs);
+    if (n_groups < 1) return fail(ctx, PAC_E_INVALID, "n_groups must be >= 1");
+    if (!meta || !noised || !is_null || !flags) return fail(ctx, PAC_E_INVALID, "NULL output or meta");
+    if (!(budget > 0.0)) return fail(ctx, PAC_E_INVALID, "budget must be > 0");
+    if (mode != PAC_FIN_ADAPTIVE && mode != PAC_FIN_INDEPENDENT) return fail(ctx, PAC_E_INVALID, "mode %d", mode);
+    p = FinParams{};
+    for (int i = 0; i < n_specs; i++) {
+        if (specs[i].kind < PAC_COUNT || specs[i].kind > PAC_LIFTED || !specs[i].out)
+            return fail(ctx, PAC_E_INVALID, "spec %d", i);
+        if (specs[i].kind == PAC_LIFTED && specs[i].vtype != PAC_F64)
+            return fail(ctx, PAC_E_INVALID, "spec %d: a lifted vector is PAC_F64", i);
+        p.spec[i].kind = specs[i].kind;
+        p.spec[i].vtype = specs[i].kind == PAC_COUNT ? PAC_I64 : specs[i].vtype;
+        p.spec[i].variant = specs[i].variant;
+        p.spec[i].out = specs[i].out;
+    }
+    p.n_specs = n_specs;
+    p.n_groups = n_groups;
+    p.meta = meta;
+    p.seed = seed;
+    p.budget = budget;
+    p.mode = mode;
+    p.noised = noised;
+    p.is_null = is_null;
+    p.flags = flags;
+    p.posterior = posterior;
+    return PAC_OK;
+}
+
 inline InputDev make_input(const pac_input *in) {
     InputDev d;
     d.km = in->keys_or_masks;
