@@ -293,7 +293,172 @@ def _oracle_step(orc, wcfg, wl, G, qk, thr=None):
         orc.finalize(y, scales, res[0][1], res[0][2], 99, 1.0 / 128, orc.ADAPTIVE)
 
 
-def cpu_oracle_batch_sample(rows_budget: int, seed: int = 0):
+def host_cpu():
+    """Host cores this process may use and the CPU model (lscpu's model
+    name, else /proc/cpuinfo), recorded beside every CPU baseline."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": cores, "cpu_model": model or "unknown", "machine": os.uname().machine}
+
+
+def _gen_groups(workload: str) -> int:
+    """Group count of a workload's generator (its default size)."""
+    from paper_2603_15023_gb300 import inputs
+    import inspect
+    sig = inspect.signature(inputs.WORKLOADS[workload])
+    p = sig.parameters.get("n_groups")
+    if p is not None:
+        return int(p.default)
+    return 4 if WORKLOADS[workload]["gid_bytes"] == 1 else 1
+
+
+def _chunked_ok(wcfg) -> bool:
+    """Workloads whose per-thread states merge by addition: COUNT, exact SUM
+    (and AVG, derived from the merged COUNT and SUM states)."""
+    return not (wcfg.get("approx") or wcfg.get("select") or wcfg.get("lift") or "max" in wcfg["aggs"])
+
+
+def cpu_oracle_chunked(workload: str, rows: int, threads: int, chunk: int = 1 << 18, seed: int = 0, wl=None):
+    """The oracle on all host cores: rows cut into consecutive chunks, each
+    thread hashing its chunks and aggregating them with the oracle's COUNT and
+    SUM (per-thread chunk states), the states merged in chunk order
+    (COUNT, SUM, n_g by addition, or_g by OR), AVG = SUM / COUNT of the merged
+    states, then the release of every cell.  The oracle's C functions release
+    the GIL, so the threads run in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle as orc
+    wcfg = WORKLOADS[workload]
+    wl = _gen(workload, seed, rows) if wl is None else wl
+    G, C = wl.n_groups, wcfg["n_cols"]
+    qk = orc.query_key(seed)
+    bounds = [(a, min(a + chunk, rows)) for a in range(0, rows, chunk)]
+
+    def one(b):
+        a, e = b
+        masks = orc.hash_keys(wl.keys[a:e], qk, orc.BALANCED)
+        gids = None if wl.gids is None else wl.gids[a:e]
+        cnt, n_g, or_g, _ = orc.aggregate(masks, None, gids, G, orc.COUNT)
+        sums = [orc.aggregate(masks, v[a:e], gids, G, orc.SUM)[0] for v in wl.values[:C]]
+        return cnt, sums, n_g, or_g
+
+    if G > 4096:
+        # many groups: a row chunk's state would hold every group, so each
+        # thread takes a range of groups instead (all of their rows, in row
+        # order) and the disjoint states are placed side by side
+        return _cpu_oracle_group_ranges(orc, wcfg, wl, rows, threads, qk)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(one, bounds))
+    cnt = np.zeros((G, 64), np.uint64)
+    sums = [np.zeros((G, 64), np.int64) for _ in range(C)]
+    n_g = np.zeros(G, np.uint64)
+    or_g = np.zeros(G, np.uint64)
+    for c, sm, ng, og in parts:              # chunk order
+        cnt += c
+        for k in range(C):
+            sums[k] += sm[k]
+        n_g += ng
+        or_g |= og
+    res = [cnt.astype(np.float64)] + [x.astype(np.float64) for x in sums]
+    scales = [2.0] * (1 + C)
+    if "avg" in wcfg["aggs"]:
+        cf = cnt.astype(np.float64)
+        res += [np.where(cnt > 0, x / np.maximum(cf, 1.0), 0.0) for x in res[1:1 + C]]
+        scales += [1.0] * C
+    if wcfg["finalize"] != "separate":
+        orc.finalize(np.stack(res, axis=1), scales, n_g, or_g, 99, 1.0 / 128, orc.ADAPTIVE)
+    dt = time.perf_counter() - t0
+    return rows / dt, dt
+
+
+def _cpu_oracle_group_ranges(orc, wcfg, wl, rows, threads, qk):
+    """All-cores leg for many groups: thread t aggregates the rows of groups
+    [t*G/T, (t+1)*G/T) with the oracle (hash, COUNT, SUM per column), then
+    the release.  Timed from the row selection on."""
+    from concurrent.futures import ThreadPoolExecutor
+    G, C = wl.n_groups, wcfg["n_cols"]
+    gids = wl.gids[:rows]
+    edges = [G * t // threads for t in range(threads + 1)]
+
+    def one(t):
+        lo, hi = edges[t], edges[t + 1]
+        sel = np.flatnonzero((gids >= lo) & (gids < hi))
+        masks = orc.hash_keys(wl.keys[sel], qk, orc.BALANCED)
+        g = (gids[sel] - lo).astype(np.uint32)
+        Gt = max(hi - lo, 1)
+        cnt, n_g, or_g, _ = orc.aggregate(masks, None, g, Gt, orc.COUNT)
+        sums = [orc.aggregate(masks, v[sel], g, Gt, orc.SUM)[0] for v in wl.values[:C]]
+        return cnt, sums, n_g, or_g
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(one, range(threads)))
+    cnt = np.concatenate([p[0] for p in parts])
+    sums = [np.concatenate([p[1][k] for p in parts]) for k in range(C)]
+    n_g = np.concatenate([p[2] for p in parts])
+    or_g = np.concatenate([p[3] for p in parts])
+    if wcfg["finalize"] != "separate":
+        res = [cnt.astype(np.float64)] + [x.astype(np.float64) for x in sums]
+        orc.finalize(np.stack(res, axis=1), [2.0] * (1 + C), n_g, or_g, 99, 1.0 / 128, orc.ADAPTIVE)
+    dt = time.perf_counter() - t0
+    return rows / dt, dt
+
+
+def cpu_baseline(workload: str, n: int, one_rows: int, all_rows: int):
+    """Both legs of the CPU baseline: (i) the oracle's step as it stands on
+    one thread, (ii) all host cores with per-thread chunk states merged in
+    order.  The line's value is the all-cores leg where the workload's states
+    merge by addition, else the one-thread leg."""
+    host = host_cpu()
+    wcfg = WORKLOADS[workload]
+    srows = min(one_rows, n)
+    reps = max(1, one_rows // srows)
+    v1, dt1 = cpu_oracle_sample(workload, srows, reps)
+    what = f"first {srows} rows of {workload}" if srows < n else f"the whole {workload} workload ({n} rows), {reps}x"
+    legs = {"one_thread": {"value": v1, "cores": 1, "seconds": dt1,
+                           "sample": f"{what} ({wcfg['describe']}), the oracle's step as it stands"}}
+    out = {"value": v1, "unit": "rows/s", "cores": 1, "kind": "oracle",
+           "sample": f"{what} ({wcfg['describe']}), one thread, {dt1:.1f} s", **host, "legs": legs}
+    if _chunked_ok(wcfg) and host["nproc"] > 1:
+        arows = min(all_rows, n)
+        areps = max(1, all_rows // arows)
+        vals = [cpu_oracle_chunked(workload, arows, host["nproc"]) for _ in range(areps)]
+        va = arows * areps / sum(dt for _, dt in vals)
+        dta = sum(dt for _, dt in vals)
+        awhat = f"first {arows} rows of {workload}" if arows < n else f"the whole {workload} workload, {areps}x"
+        how = ("one range of groups per thread (all of its rows, in row order), the disjoint states side by side"
+               if _gen_groups(workload) > 4096 else
+               "256K-row chunks over the threads, chunk states (COUNT, SUM, n_g, or_g) merged in order, AVG from "
+               "the merged states")
+        legs["all_cores"] = {"value": va, "cores": host["nproc"], "seconds": dta,
+                             "sample": f"{awhat}, {host['nproc']} threads: {how}, then the release"}
+        out.update({"value": va, "cores": host["nproc"],
+                    "sample": f"{awhat}, {host['nproc']} threads ({how}), {dta:.1f} s; one-thread leg "
+                              f"{v1 / 1e6:.2f} M rows/s"})
+    return out
+
+
+def cpu_oracle_batch_sample(rows_budget: int, seed: int = 0, threads: int = 1):
     """Times the oracle on the first queries of the batched workload (whole
     queries, in order, until `rows_budget` rows): hash, COUNT, SUM, float SUM."""
     import oracle as orc
@@ -305,62 +470,115 @@ def cpu_oracle_batch_sample(rows_budget: int, seed: int = 0):
             break
         cols.append((q, spec.columns(q)))
         rows += int(spec.rows[q])
-    t0 = time.perf_counter()
-    for q, (keys, gids, v, f) in cols:
+
+    def one(item):
+        q, (keys, gids, v, f) = item
         G = int(spec.groups[q])
         masks = orc.hash_keys(keys, orc.query_key(1_000_000 + q), orc.BALANCED)
         orc.aggregate(masks, None, gids, G, orc.COUNT)
         orc.aggregate(masks, v, gids, G, orc.SUM)
         orc.aggregate(masks, f, gids, G, orc.SUM)
+
+    t0 = time.perf_counter()
+    if threads <= 1:
+        for item in cols:
+            one(item)
+    else:  # independent queries: whole queries per thread
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(one, cols))
     dt = time.perf_counter() - t0
     return rows / dt, dt, len(cols), rows
 
 
+def cpu_baseline_batch(one_rows: int, all_rows: int, what: str = "batch_4096"):
+    """Both legs on the batched workload's queries: one thread, then all host
+    cores with whole queries per thread."""
+    host = host_cpu()
+    v1, dt1, nq1, r1 = cpu_oracle_batch_sample(one_rows)
+    legs = {"one_thread": {"value": v1, "cores": 1, "seconds": dt1,
+                           "sample": f"the first {nq1} queries of batch_4096 ({r1} rows; hash, count, sum, "
+                                     f"float sum)"}}
+    out = {"value": v1, "unit": "rows/s", "cores": 1, "kind": "oracle",
+           "sample": f"the first {nq1} queries of batch_4096 ({r1} rows), one thread, {dt1:.1f} s", **host,
+           "legs": legs}
+    if host["nproc"] > 1:
+        va, dta, nqa, ra = cpu_oracle_batch_sample(all_rows, threads=host["nproc"])
+        legs["all_cores"] = {"value": va, "cores": host["nproc"], "seconds": dta,
+                             "sample": f"the first {nqa} queries of batch_4096 ({ra} rows), whole queries per "
+                                       f"thread over {host['nproc']} threads"}
+        out.update({"value": va, "cores": host["nproc"],
+                    "sample": f"the first {nqa} queries of batch_4096 ({ra} rows), {host['nproc']} threads "
+                              f"(whole queries per thread), {dta:.1f} s; one-thread leg {v1 / 1e6:.2f} M rows/s"
+                              + ("" if what == "batch_4096" else f"; {what} draws its queries from these shapes")})
+    return out
+
+
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on the host cores (rank 0
+    only).  Workloads whose states merge by addition run on every core with
+    per-thread chunk states merged in order, a bounded sample of --ref-rows
+    rows per step; the others on one thread."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
+    workload = args.workload or "lowcard_60m"
+    wcfg = WORKLOADS[workload]
+    host = host_cpu()
     rows = args.ref_rows
     vals = []
-    for i in range(args.warmup + args.steps):
-        if args.workload in ("batch_4096", "serving"):
-            # serving draws its queries from the batched workload's shapes
-            v, dt, _, _ = cpu_oracle_batch_sample(rows)
-        else:
-            v, dt = cpu_oracle_sample(args.workload, rows)
-        if i >= args.warmup:
-            vals.append((v, dt))
+    if workload in ("batch_4096", "serving"):
+        # serving draws its queries from the batched workload's shapes
+        for i in range(args.warmup + args.steps):
+            v, dt, _, rows = cpu_oracle_batch_sample(args.ref_rows, threads=host["nproc"])
+            if i >= args.warmup:
+                vals.append((v, dt))
+        cores = host["nproc"]
+        sample = f"the first queries of batch_4096 ({rows} rows) per step, whole queries per thread"
+    elif _chunked_ok(wcfg):
+        wl = _gen(workload, 0, rows)
+        rows = wl.n
+        for i in range(args.warmup + args.steps):
+            v, dt = cpu_oracle_chunked(workload, rows, host["nproc"], wl=wl)
+            if i >= args.warmup:
+                vals.append((v, dt))
+        cores = host["nproc"]
+        sample = (f"first {rows} rows of {workload} per step, 256K-row chunks over {cores} threads, chunk states "
+                  "merged in order, then the release")
+    else:
+        rows = min(rows, 1_000_000)
+        for i in range(args.warmup + args.steps):
+            v, dt = cpu_oracle_sample(workload, rows)
+            if i >= args.warmup:
+                vals.append((v, dt))
+        cores = 1
+        sample = f"first {rows} rows of {workload} per step, one thread"
     value = statistics.median(v for v, _ in vals)
     ms = statistics.median(dt for _, dt in vals) * 1e3
-    wcfg = WORKLOADS[args.workload]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "rows": rows, "aggregates": wcfg["describe"], "worlds": 64},
-        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {rows} rows of {args.workload}, one thread"},
+        "config": {"workload": workload, "rows": rows, "aggregates": wcfg["describe"], "worlds": 64},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         **host},
         "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def run_batch(args):
+def measure_batch(args, suite=False):
     """The batched workload: every query's columns generated in HBM, one
     autotuned plan, its launch captured in a CUDA graph; a step is one replay
-    (the aggregation of all queries)."""
+    (the aggregation of all queries).  Returns the JSON dict (rank 0)."""
     import torch
     from paper_2603_15023_gb300 import batch_inputs, inputs
     from paper_2603_15023_gb300 import binding as B
 
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     ctx = B.pac_create(local)
-    spec = inputs.batch_4096(seed=rank, n_queries=args.queries)
+    spec = inputs.batch_4096(seed=rank, n_queries=4096 if suite else args.queries)
     s = torch.cuda.Stream()
     db = batch_inputs.DeviceBatch(spec, stream=s.cuda_stream)
     s.synchronize()
@@ -403,19 +621,16 @@ def run_batch(args):
     if st != B.PAC_OK:
         raise RuntimeError(B.status_name(st))
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms_step = start.elapsed_time(end) / args.steps
-    ms_step = max_over_ranks([ms_step], world)[0]
+    ms_step = max_over_ranks([statistics.median(step_ms)], world)[0]
     value = job_throughput(db.total_rows, world, ms_step)
     peak, peak_src = _peaks()
     algo = db.algorithmic_bytes()
-    achieved = algo / (statistics.mean(step_ms) / 1e3) / 1e9
+    achieved = algo / (ms_step / 1e3) / 1e9
+    line = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, dt, nq, rows = cpu_oracle_batch_sample(args.cpu_rows)
-            cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                   "sample": f"the first {nq} queries of batch_4096 ({rows} rows; hash, count, sum, float sum), "
-                             f"one thread, {dt:.1f} s"}
+            cpu = cpu_baseline_batch(args.cpu_rows, args.cpu_rows_all)
         wcfg = WORKLOADS["batch_4096"]
         line = {
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
@@ -424,25 +639,28 @@ def run_batch(args):
             "config": {"workload": "batch_4096", "queries": db.n_queries, "rows": db.total_rows,
                        "groups_total": db.total_groups, "worlds": 64, "aggregates": wcfg["describe"],
                        "l2": f"inputs {db.total_rows * wcfg['in_bytes_per_row'] / 1e9:.1f} GB > 129 MB L2",
-                       "plan": info, "plan_seconds_incl_autotune": plan_s},
+                       "plan": info, "plan_seconds_incl_autotune": plan_s,
+                       "timing": f"median of {args.steps} CUDA-graph replays, CUDA events on the launching stream"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_batch_agg + k_batch_merge (one graph replay)",
+                         "traffic": _traffic("batch_4096", db.total_rows, 3),
+                         "kernel": "k_batch_agg + k_batch_merge (one graph replay)",
                          "algorithmic_bytes": algo, "peak_source": peak_src},
             "cpu_baseline": cpu,
             "e2e": None,
+            "e2e_note": "the 102 GB of columns are generated in HBM (larger than the host memory of the build "
+                        "machine); no host-to-device leg is timed for this workload",
             "gpu_launches": info["kernels"] * args.steps,
             "clocks": clocks.summary(),
         }
-        print(json.dumps(line))
     B.pac_batch_free(plan)
     B.pac_destroy(ctx)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
+    del db, graph
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line
 
 
-def run_serving(args):
+def measure_serving(args):
     """Continuous batching under Poisson arrivals: a pool of query shapes drawn
     from the batched workload's distribution lives in HBM (columns generated
     on the device, plus a float64 lognormal(0, 1.5) column); every arrival
@@ -454,7 +672,6 @@ def run_serving(args):
     from paper_2603_15023_gb300 import gen, inputs
 
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
     ctx = B.pac_create(local)
     spec = inputs.batch_4096(seed=100 + rank, n_queries=args.pool)
     P = spec.n_queries
@@ -536,7 +753,7 @@ def run_serving(args):
     lat_ms = np.array(tickets, dtype=np.float64) * 1e3
     rows = int(sum(cols[int(q)][0] for q in shapes))
     stats = {k: B.pac_serve_stats(srv, k) for k in ("batches", "mean_batch", "max_inflight_seen",
-                                                     "arena_high_water")}
+                                                     "arena_high_water", "max_device_overlap")}
     B.pac_serve_destroy(srv)
     value = rows / wall
     line = {
@@ -549,39 +766,42 @@ def run_serving(args):
                    "output_ring_slots": R},
         "latency": {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                     "max_ms": float(lat_ms.max()), "definition": "completion stamp - scheduled Poisson arrival"},
-        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "roofline": None,
+        "roofline_note": "latency-bound by design: the offered load is about 1% of HBM bandwidth",
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_batch(args.cpu_rows, args.cpu_rows_all,
+                                                                              "serving"),
+        "e2e": None,
+        "e2e_note": "queries are submitted through the public serving API (pac_serve_submit / pac_serve_wait) "
+                    "with their columns resident in HBM; latency is measured from the scheduled arrival",
         "gpu_launches": int(stats["batches"]) * 3,
         "clocks": clocks.summary(),
     }
-    print(json.dumps(line))
     B.pac_destroy(ctx)
-    return 0
+    del cols, ring
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line if rank == 0 else None
 
 
-def run_ours(args):
+def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suite=False):
+    """One workload of single queries: returns its JSON dict (rank 0) or None."""
     import torch
     from paper_2603_15023_gb300 import binding as B
 
-    if args.workload == "batch_4096":
-        return run_batch(args)
-    if args.workload == "serving":
-        return run_serving(args)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     ctx = B.pac_create(local)
-    if args.path:
+    if args.path and not suite:
         B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2, "engine": 3, "small": 4}[args.path])
     B.pac_set_option(ctx, "minmax_prune", args.minmax_prune)
 
-    wcfg = WORKLOADS[args.workload]
-    wl = _gen(args.workload, rank, args.rows)
+    wcfg = WORKLOADS[workload]
+    wl = _gen(workload, rank, rows)
     n, G = wl.n, wl.n_groups
     C = wcfg["n_cols"]
     n_specs = _n_specs(wcfg)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
     d_keys = torch.from_numpy(wl.keys).cuda()
     d_gids = torch.from_numpy(wl.gids).cuda() if wl.gids is not None else None
@@ -593,6 +813,7 @@ def run_ours(args):
     noised = torch.empty(n_cells, dtype=torch.float64, device="cuda")
     is_null = torch.empty(n_cells, dtype=torch.uint8, device="cuda")
     flags = torch.empty(n_cells, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
     qk = B.pac_query_key(rank)
     inp = B.make_input(d_keys.data_ptr(), n, query_key=qk,
                        group_ids=d_gids.data_ptr() if d_gids is not None else 0,
@@ -607,11 +828,13 @@ def run_ours(args):
         d_avg = torch.empty((G, 64), dtype=torch.float64, device="cuda")
         B.pac_aggregate_multi(ctx, inp, B.make_specs([(B.PAC_AVG, B.PAC_EXACT, B.PAC_I64, d_vals[0].data_ptr(),
                                                          d_avg.data_ptr())]), 1, 0, sptr)
+        stream.synchronize()
         d_thr = torch.trunc(d_avg).to(torch.int64).contiguous()
         sel = B.make_select(d_vals[0].data_ptr(), B.PAC_I64, B.PAC_CMP_LT, d_thr.data_ptr(), G,
                             d_gids.data_ptr(), 1)
 
     lift = None
+    lift_ms = []
     if wcfg.get("lift"):
         # the market share 100 * s1 / s2, world by world, from the two SUM outputs
         share = torch.empty((G, 64), dtype=torch.float64, device="cuda")
@@ -620,63 +843,94 @@ def run_ours(args):
         prog = [(B.PAC_LIFT_CONST, 0, 100.0), (B.PAC_LIFT_SPEC, 0, 0), (B.PAC_LIFT_MUL, 0, 0),
                 (B.PAC_LIFT_SPEC, 1, 0), (B.PAC_LIFT_DIV, 0, 0)]
         lift = (lift_specs, B.make_lift(prog), len(prog), share)
-        lift_ms = []
 
-    def aggregate(in_, sp):
+    def aggregate(sp_ptr):
         if sel is not None:
-            B.pac_aggregate_select(ctx, in_, sel, sp, n_specs, meta.data_ptr(), sptr)
+            B.pac_aggregate_select(ctx, inp, sel, specs, n_specs, meta.data_ptr(), sp_ptr)
         else:
-            B.pac_aggregate_multi(ctx, in_, sp, n_specs, meta.data_ptr(), sptr)
+            B.pac_aggregate_multi(ctx, inp, specs, n_specs, meta.data_ptr(), sp_ptr)
+        return B.pac_get_info(ctx, "last_launches")
 
-    def step(i, ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        aggregate(inp, specs)
-        k = B.pac_get_info(ctx, "last_launches")
-        if ev is not None:
-            ev[1].record(stream)
+    def release(i, sp_ptr, lift_ev=None):
+        k = 0
         if lift is not None:
-            le = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) if ev else None
-            if le:
-                le[0].record(stream)
-            B.pac_lift(ctx, lift[0], 2, G, lift[1], lift[2], lift[3].data_ptr(), sptr)
-            if le:
-                le[1].record(stream)
-                lift_ms.append(le)
+            le = None
+            if lift_ev is not None:
+                le = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                le[0].record(torch.cuda.current_stream())
+            B.pac_lift(ctx, lift[0], 2, G, lift[1], lift[2], lift[3].data_ptr(), sp_ptr)
+            if le is not None:
+                le[1].record(torch.cuda.current_stream())
+                lift_ev.append(le)
             k += B.pac_get_info(ctx, "last_launches")
         if in_step_finalize:
             B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 1000 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
-                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sp_ptr)
             k += B.pac_get_info(ctx, "last_launches")
-        if ev is not None:
-            ev[2].record(stream)
         return k
 
-    for i in range(args.warmup):
-        if flush is not None:
-            flush.fill_(i)
-        step(i)
+    with torch.cuda.stream(stream):
+        for i in range(warmup):
+            if flush is not None:
+                flush.fill_(i)
+            aggregate(sptr)
+            release(i, sptr)
     torch.cuda.synchronize()
     st = B.pac_sync_status(ctx, sptr)
     if st != B.PAC_OK:
         raise RuntimeError(B.status_name(st))
     path = B.pac_get_info(ctx, "last_path")
 
+    # The tensor-core and one-launch paths enqueue only kernels and memsets
+    # once warm, so a step is captured as CUDA graphs (aggregation; release)
+    # and replayed; the other paths plan on the host per call and are timed
+    # as stream work.  Either way the reported time is the median step.
+    graphs = None
+    if path in (2, 4) and sel is None and lift is None and not wcfg.get("approx"):
+        try:
+            g_agg, g_rel = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            launches_agg = launches_rel = 0
+            with torch.cuda.graph(g_agg, stream=stream):
+                launches_agg = aggregate(stream.cuda_stream)
+            with torch.cuda.graph(g_rel, stream=stream):
+                launches_rel = release(warmup, stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    g_agg.replay()
+                    g_rel.replay()
+            torch.cuda.synchronize()
+            graphs = (g_agg, g_rel, launches_agg, launches_rel)
+        except Exception as e:  # fall back to stream-timed steps
+            print(f"graph capture unavailable ({e}); timing stream steps", file=sys.stderr)
+            torch.cuda.synchronize()
+            graphs = None
+
     clocks = ClockSampler(local)
-    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    start.record(stream)
     launches = 0
-    for i in range(args.steps):
-        if flush is not None:
-            flush.fill_(i)  # L2 flush between steps, outside the step's events
-        launches += step(args.warmup + i, evs[i])
-    end.record(stream)
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            if flush is not None:
+                flush.fill_(i)  # L2 flush between steps, outside the step's events
+            ev = evs[i]
+            ev[0].record(stream)
+            if graphs is not None:
+                graphs[0].replay()
+                launches += graphs[2]
+            else:
+                launches += aggregate(sptr)
+            ev[1].record(stream)
+            if graphs is not None:
+                graphs[1].replay()
+                launches += graphs[3]
+            else:
+                launches += release(warmup + i, sptr, lift_ms)
+            ev[2].record(stream)
     torch.cuda.synchronize()
     clocks.stop()
     st = B.pac_sync_status(ctx, sptr)
@@ -684,9 +938,11 @@ def run_ours(args):
         raise RuntimeError(B.status_name(st))
     agg_ms = [a.elapsed_time(b) for a, b, _ in evs]
     step_ms = [a.elapsed_time(c) for a, _, c in evs]
-    ms_step = start.elapsed_time(end) / args.steps if flush is None else statistics.mean(step_ms)
-    ms_step, agg_mean = max_over_ranks([ms_step, statistics.mean(agg_ms)], world)
+    ms_step, agg_med = max_over_ranks([statistics.median(step_ms), statistics.median(agg_ms)], world)
     value = job_throughput(n, world, ms_step)
+    timing = (f"median of {steps} CUDA-graph replays (aggregation graph + release graph), CUDA events on the "
+              "launching stream" if graphs is not None else
+              f"median of {steps} steps enqueued on one stream, CUDA events on that stream")
 
     # the release of every cell, timed once beside the step when it is not in it
     fin_ms = None
@@ -724,18 +980,19 @@ def run_ours(args):
         rel_mode = B.PAC_FIN_ADAPTIVE if in_step_finalize else B.PAC_FIN_INDEPENDENT
 
         def e2e_step(i):
-            d_keys.copy_(h_keys, non_blocking=True)
-            d_gids.copy_(h_gids, non_blocking=True)
-            for d, h in zip(d_vals, h_vals):
-                d.copy_(h, non_blocking=True)
-            aggregate(inp, specs)
-            if lift is not None:
-                B.pac_lift(ctx, lift[0], 2, G, lift[1], lift[2], lift[3].data_ptr(), sptr)
-            B.pac_finalize(ctx, rel_specs, rel_n, G, meta.data_ptr(), 100 + i, 1.0 / 128, rel_mode,
-                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
-            h_noised.copy_(noised[:rel_cells], non_blocking=True)
-            h_null.copy_(is_null[:rel_cells], non_blocking=True)
-            h_flags.copy_(flags[:rel_cells], non_blocking=True)
+            with torch.cuda.stream(stream):
+                d_keys.copy_(h_keys, non_blocking=True)
+                d_gids.copy_(h_gids, non_blocking=True)
+                for d, h in zip(d_vals, h_vals):
+                    d.copy_(h, non_blocking=True)
+                aggregate(sptr)
+                if lift is not None:
+                    B.pac_lift(ctx, lift[0], 2, G, lift[1], lift[2], lift[3].data_ptr(), sptr)
+                B.pac_finalize(ctx, rel_specs, rel_n, G, meta.data_ptr(), 100 + i, 1.0 / 128, rel_mode,
+                               noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+                h_noised.copy_(noised[:rel_cells], non_blocking=True)
+                h_null.copy_(is_null[:rel_cells], non_blocking=True)
+                h_flags.copy_(flags[:rel_cells], non_blocking=True)
             torch.cuda.synchronize()
 
         for i in range(2):
@@ -774,7 +1031,7 @@ def run_ours(args):
     peak, peak_src = _peaks()
     out_bytes = G * 64 * 8 * n_specs + G * 16
     algo_bytes = n * wcfg["in_bytes_per_row"] + out_bytes
-    achieved = algo_bytes / (agg_mean / 1e3) / 1e9
+    achieved = algo_bytes / (agg_med / 1e3) / 1e9
     path_name = {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
                  3: "per-bit engine (rows partitioned by group first when the groups' states exceed "
                     "shared memory)",
@@ -792,30 +1049,24 @@ def run_ours(args):
         kernel = ("k_apx_chunks + k_apx_combine_level + k_apx_emit per approximate value column, plus "
                   f"{path_name} for the exact specs (all launches of pac_aggregate_multi)")
         path_name = f"approximate cascades + {path_name} (exact specs)"
+    line = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            srows = min(args.cpu_rows, n)
-            reps = max(1, args.cpu_rows // srows)
-            v, dt = cpu_oracle_sample(args.workload, srows, reps)
-            what = (f"first {srows} rows of {args.workload}" if srows < n else
-                    f"the whole {args.workload} workload ({n} rows), {reps} times")
-            cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{what} ({wcfg['describe']}), one thread, {dt:.1f} s"}
+            cpu = cpu_baseline(workload, n, args.cpu_rows, args.cpu_rows_all)
         l2 = ("L2 flushed before every step (512 MB write), inputs 16 MB" if flush is not None else
               f"inputs {n * wcfg['in_bytes_per_row'] / 1e9:.2f} GB > 129 MB L2 (no flush needed)")
         line = {
-            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": args.workload, "rows": n, "groups": G, "value_columns": C, "worlds": 64,
-                       "aggregates": wcfg["describe"], "l2": l2,
-                       "agg_path": path_name,
+            "config": {"workload": workload, "rows": n, "groups": G, "value_columns": C, "worlds": 64,
+                       "aggregates": wcfg["describe"], "l2": l2, "agg_path": path_name, "timing": timing,
                        **({"minmax_prune": bool(args.minmax_prune)} if "max" in wcfg["aggs"] else {})},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": _traffic(args.workload, n, path),
+                         "frac": achieved / peak, "traffic": _traffic(workload, n, path),
                          "kernel": kernel, "algorithmic_bytes": algo_bytes, "peak_source": peak_src,
-                         "agg_ms": agg_mean, "agg_ms_min": min(agg_ms)},
+                         "agg_ms": agg_med, "agg_ms_min": min(agg_ms)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -824,16 +1075,46 @@ def run_ours(args):
         if fin_ms is not None:
             line["finalize_ms"] = fin_ms
         if lift is not None and lift_ms:
-            lms = statistics.mean(a.elapsed_time(b) for a, b in lift_ms)
+            lms = statistics.median(a.elapsed_time(b) for a, b in lift_ms)
             lb = G * 64 * (8 + 8 + 8)   # two operand vectors in, the lifted vector out
             line["lift"] = {"kernel": "k_lift", "ms": lms, "bytes": lb, "achieved_gbs": lb / (lms / 1e3) / 1e9,
                             "frac": lb / (lms / 1e3) / 1e9 / peak, "cells": G * 64}
-        print(json.dumps(line))
     B.pac_destroy(ctx)
+    del d_keys, d_gids, d_vals, outs, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line
+
+
+# The default run: the headline workload, then (one GPU) one entry per other
+# configuration of the benchmark suite inside the same JSON line.
+SUITE = ("ungrouped_1m", "highcard_100m", "batch_4096", "serving")
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    line = measure(args, args.workload or "lowcard_60m")
+    if args.workload is None and world == 1 and not args.no_suite:
+        line["workloads"] = {w: measure(args, w, suite=True) for w in SUITE}
+    if rank == 0:
+        print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def measure(args, workload: str, suite: bool = False):
+    if workload == "batch_4096":
+        return measure_batch(args, suite=suite)
+    if workload == "serving":
+        return measure_serving(args)
+    return measure_single(args, workload, rows=None if suite else args.rows, suite=suite)
 
 
 def main():
@@ -842,14 +1123,20 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lowcard_60m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="one workload; default: lowcard_60m as the headline plus (one GPU) an entry per "
+                         "configuration of the suite in `workloads`")
+    ap.add_argument("--no-suite", action="store_true", help="default run: the headline workload only")
     ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
     ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma", "engine", "small"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--minmax-prune", type=int, default=1, choices=[0, 1],
                     help="MIN/MAX bound pruning on the per-bit engine (results are identical either way)")
-    ap.add_argument("--cpu-rows", type=int, default=4_000_000)
-    ap.add_argument("--ref-rows", type=int, default=1_000_000)
+    ap.add_argument("--cpu-rows", type=int, default=4_000_000, help="CPU baseline: rows of the one-thread leg")
+    ap.add_argument("--cpu-rows-all", type=int, default=16_000_000,
+                    help="CPU baseline: rows of the all-cores leg")
+    ap.add_argument("--ref-rows", type=int, default=8_000_000,
+                    help="--impl reference: rows per step (all host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=4096, help="batch_4096: number of queries")
     ap.add_argument("--no-autotune", action="store_true", help="batch_4096: default plan configuration")
