@@ -23,15 +23,17 @@
 // shared memory; the remaining levels run one launch per level
 // over the block states in global memory.
 //
-// Row loop: the lanes of a 32-row batch compute their rows' side, level and
-// level units in parallel; the warp then walks the group's rows in order.
-// Per side, the levels of the two latest slow updates are "open": their
-// counters since the last commit sit in registers (acc) and their exact
-// totals in uniform registers (ct).  A row of an open level whose units still
-// fit under the cap only adds to those registers; any other row commits both
-// to the level state and takes the full update with its flush chain.  Every
-// flush decision reads exact totals, so the state equals the row-by-row
-// definition.
+// Row loop: between two flushes of a level, its 64 counters only grow by
+// sum_i x_i * bit_j(mask_i); the sequential part of the cascade is the scalar
+// level totals alone.  The warp queues its group's rows of the chunk (in row
+// order) and takes them 32 at a time: lane r computes row r's side, level and
+// units x_r, the 32 masks are bit-transposed (lane j: world j's bits of the
+// batch), and the batch is cut at the first row whose update would overflow
+// its level's total (found from per-level prefix sums of x against the
+// totals).  The rows before the cut are added level by level as bit-plane
+// popcount sums (12 planes of x); the cut row's level is flushed with its
+// cascade and the walk resumes at that row.  Every flush decision reads exact
+// totals, so the state equals the row-by-row definition.
 #include "pac_internal.cuh"
 #include "pac_kernels.h"
 
@@ -106,55 +108,87 @@ __device__ __forceinline__ void apx_combine(ApxState *dst, const ApxState *src, 
     apx_store_totals(dst, t0, t1, lane);
 }
 
-// One open level of one side (see the row loop above).
-struct ApxOpen {
-    uint32_t acc;  // this lane's packed counters added since the last commit
-    uint32_t ct;   // the level's exact total (uniform)
-    int cl;        // the level, -1 when none (uniform)
-};
+// 32 x 32 bit transpose across a warp: lane r holds row r's 32 world bits;
+// afterwards lane j holds world j's bits of the 32 rows (bit r = row r).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                                  : s == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+    }
+    return x;
+}
 
-// Writes an open level back: counters into the level state, total into the
-// lane that holds it.
-__device__ __forceinline__ void apx_commit(ApxSide *s, uint32_t &t, ApxOpen &o, int lane) {
-    if (o.cl >= 0) {
-        s->w[o.cl][lane] += o.acc;
-        if (lane == o.cl) t = o.ct;
+// sum over rows r in the set TS (a lane's world bits of the batch, already
+// restricted to the rows that count) of x_r, from the bit planes V[b] of the
+// rows' units (x < 2^12): a Horner sum of popcounts.
+__device__ __forceinline__ uint32_t plane_sum(uint32_t TS, const uint32_t (&V)[12]) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int b = 11; b >= 0; b--) acc = 2 * acc + __popc(TS & V[b]);
+    return acc;
+}
+
+// One side of a dense batch (rows R of the warp's batch, lane r = row r in
+// row order; lane r's level lv and units x).  Between two flushes a level's
+// 64 counters only grow by sum x_r * bit_j(mask_r), so the batch is cut at
+// the first row whose update would overflow its level total: the rows before
+// it are added level by level as plane sums, the level of that row is
+// flushed (with its cascade), and the walk resumes at that row.  The flush
+// decisions read exact totals, so the state equals the row-by-row
+// definition.  bal: world j + 32 is the complement of world j, so its sum is
+// the segment total minus world j's.
+__device__ __forceinline__ void apx_side_batch(ApxSide *s, uint32_t &t, uint32_t R, int lv, uint32_t x,
+                                               uint32_t Tlo, uint32_t Thi, bool bal, const uint32_t (&V)[12],
+                                               int lane, bool &ovf) {
+    const uint32_t me = 1u << lane;
+    while (R) {
+        // inclusive prefix of x over this lane's level's rows in R
+        uint32_t P = 0;
+        for (uint32_t todo = R; todo;) {
+            const int l = __shfl_sync(kFull, lv, __ffs(todo) - 1);
+            const uint32_t Ml = __ballot_sync(kFull, lv == l) & R;
+            uint32_t xv = (Ml & me) ? x : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, xv, o);
+                if (lane >= o) xv += y;
+            }
+            if (Ml & me) P = xv;
+            todo &= ~Ml;
+        }
+        const uint32_t tl = __shfl_sync(kFull, t, lv & 31);
+        const uint32_t over = __ballot_sync(kFull, (R & me) && tl + P > kCap);
+        const uint32_t pre = over ? (R & ((1u << (__ffs(over) - 1)) - 1u)) : R;
+        for (uint32_t todo = pre; todo;) {
+            const int l = __shfl_sync(kFull, lv, __ffs(todo) - 1);
+            const uint32_t S = __ballot_sync(kFull, lv == l) & todo;
+            const uint32_t tot = __shfl_sync(kFull, P, 31 - __clz(static_cast<int>(S)));
+            const uint32_t lo = plane_sum(Tlo & S, V);
+            const uint32_t hi = bal ? tot - lo : plane_sum(Thi & S, V);
+            s->w[l][lane] += lo | (hi << 16);
+            if (lane == l) t += tot;
+            todo &= ~S;
+        }
         __syncwarp();
+        if (!over) break;
+        apx_flush(s, t, __shfl_sync(kFull, lv, __ffs(over) - 1), lane, ovf);
+        R &= ~pre;  // the overflowing row stays: its level is empty now
     }
-    o.acc = 0;
-    o.cl = -1;
 }
 
-// One nonzero value of one side: x units at level l, this lane's world bits.
-// oa holds the latest slow update's level, ob the one before.
-__device__ __forceinline__ void apx_row(ApxSide *s, uint32_t &t, ApxOpen &oa, ApxOpen &ob, int l, uint32_t x,
-                                        uint32_t b0, uint32_t b1, int lane, bool &ovf) {
-    const uint32_t add = x * b0 + ((x * b1) << 16);
-    if (l == oa.cl && oa.ct + x <= kCap) {  // no flush: the update stays in registers
-        oa.acc += add;
-        oa.ct += x;
-        return;
-    }
-    if (l == ob.cl && ob.ct + x <= kCap) {
-        ob.acc += add;
-        ob.ct += x;
-        return;
-    }
-    const int keep = l == oa.cl ? ob.cl : oa.cl;  // the other recent level stays open
-    apx_commit(s, t, oa, lane);
-    apx_commit(s, t, ob, lane);
-    if (lvl_total(t, l) + x > kCap) apx_flush(s, t, l, lane, ovf);
-    oa.cl = l;
-    oa.ct = lvl_total(t, l) + x;
-    oa.acc = add;
-    const int kb = keep != l ? keep : -1;
-    const uint32_t tb = lvl_total(t, kb < 0 ? 0 : kb);
-    ob.cl = kb;
-    ob.ct = tb;
-}
+// Rows of the warp's group waiting in its ring (offsets in the chunk).
+constexpr int kRing = 64;
 
+// One warp per (chunk, group).  The warp scans the chunk's group ids 32 rows
+// at a time and queues the offsets of its group's rows in a ring, in row
+// order; every 32 queued rows form a dense batch: lane r hashes row r, the
+// masks are bit-transposed, and each side is walked with apx_side_batch.
 __global__ void __launch_bounds__(32 * kApxBlockChunks, 2) k_apx_chunks(const __grid_constant__ ApxParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint16_t ring_all[kApxBlockChunks][kRing];
     ApxState *sm = reinterpret_cast<ApxState *>(smem_raw);
     const int lane = threadIdx.x & 31, ci = threadIdx.x >> 5;
     const uint32_t G = p.in.n_groups;
@@ -164,75 +198,62 @@ __global__ void __launch_bounds__(32 * kApxBlockChunks, 2) k_apx_chunks(const __
     const uint64_t blk = blockIdx.x / G;
     const uint64_t chunk = blk * kApxBlockChunks + ci;
     ApxState *st = sm + ci;
+    uint16_t *ring = ring_all[ci];
     apx_zero(st, lane);
     uint32_t t0 = 0, t1 = 0;
-    ApxOpen o0{0, 0, -1}, p0{0, 0, -1}, o1{0, 0, -1}, p1{0, 0, -1};
     bool ovf = false;
     uint64_t rows_g = 0;
+    const bool keys_in = (p.in.in_flags & PAC_IN_MASKS) == 0;
+    const bool bal = keys_in && p.in.hash_mode == PAC_HASH_BALANCED;
+    const uint32_t lt = (1u << lane) - 1u;
     if (chunk < p.n_chunks) {
         const uint64_t lo = chunk * kApxChunk;
         const uint64_t hi = min(p.in.n, lo + kApxChunk);
-        // loads run ahead of the row walk: group ids two batches ahead, keys
-        // and values of this group's rows one batch ahead
-        const bool keys_in = (p.in.in_flags & PAC_IN_MASKS) == 0;
-        uint32_t gid_n1 = lo + lane < hi ? row_gid(p.in, lo + lane) : 0u;
-        uint32_t gid_n2 = lo + 32 + lane < hi ? row_gid(p.in, lo + 32 + lane) : 0u;
-        long long v_n1 = 0;
-        uint64_t km_n1 = 0;
-        if (lo + lane < hi && gid_n1 == g) {
-            v_n1 = row_i64(p.values, lo + lane);
-            km_n1 = __ldg(static_cast<const unsigned long long *>(p.in.km) + lo + lane);
-        }
-        for (uint64_t base = lo; base < hi; base += 32) {
-            const uint64_t row = base + lane;
-            bool valid = row < hi;
-            const uint32_t gid = gid_n1;
-            long long v = v_n1;
-            const uint64_t km = km_n1;
-            gid_n1 = gid_n2;
-            v_n1 = 0;
-            km_n1 = 0;
-            if (row + 32 < hi && gid_n1 == g) {
-                v_n1 = row_i64(p.values, row + 32);
-                km_n1 = __ldg(static_cast<const unsigned long long *>(p.in.km) + row + 32);
-            }
-            gid_n2 = row + 64 < hi ? row_gid(p.in, row + 64) : 0u;
-            uint64_t mask = 0;
-            if (valid) {
-                if (gid >= G && g == 0) raise_status(p.status, kStatusBadGroup);
-                if (gid == g) {
-                    mask = keys_in ? keyed_world_mask(static_cast<long long>(km), p.in.qkey, p.in.hash_mode) : km;
-                    if (drop_row(p.in, mask)) valid = false;
-                }
-            }
-            if (!valid || gid != g) v = 0;
-            const uint32_t mine = __ballot_sync(kFull, valid && gid == g);
-            rows_g += __popc(mine);
-            const uint32_t todo = __ballot_sync(kFull, valid && gid == g && v != 0);
-            // this lane's row as (side, level, units): a = |v| goes to level
-            // l = floor((msb(a) - 8) / 4) (0 below 2^8) as a >> 4l < 2^12
+        uint32_t head = 0, qn = 0;  // ring: rows queued at head .. head+qn-1 (mod kRing)
+        // a dense batch of k queued rows (k <= 32), lane r = the r-th
+        auto batch = [&](uint32_t k) {
+            const bool act = static_cast<uint32_t>(lane) < k;
+            const uint64_t row = lo + (act ? ring[(head + lane) & (kRing - 1)] : 0u);
+            long long v = act ? row_i64(p.values, row) : 0;
+            const uint64_t km = act ? __ldg(static_cast<const unsigned long long *>(p.in.km) + row) : 0ull;
+            const uint64_t mask =
+                keys_in ? keyed_world_mask(static_cast<long long>(km), p.in.qkey, p.in.hash_mode) : km;
+            const bool valid = act && !drop_row(p.in, mask);
+            rows_g += __popc(__ballot_sync(kFull, valid));
+            if (!valid) v = 0;
+            // (side, level, units): a = |v| goes to level l = floor((msb(a) - 8) / 4)
+            // (0 below 2^8) as x = a >> 4l < 2^12
             const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
             const int msb = a ? 63 - __clzll(static_cast<long long>(a)) : 0;
             const int lv = msb < 8 ? 0 : (msb - 8) >> 2;
-            const uint32_t pk = static_cast<uint32_t>(a >> (4 * lv)) | (static_cast<uint32_t>(lv) << 12) |
-                                (v < 0 ? 1u << 17 : 0u);
-            const uint32_t mlo = static_cast<uint32_t>(mask), mhi = static_cast<uint32_t>(mask >> 32);
-            for (uint32_t rr = todo; rr; rr &= rr - 1) {
-                const int r = __ffs(rr) - 1;
-                const uint32_t q = __shfl_sync(kFull, pk, r);
-                const uint32_t b0 = (__shfl_sync(kFull, mlo, r) >> lane) & 1u;
-                const uint32_t b1 = (__shfl_sync(kFull, mhi, r) >> lane) & 1u;
-                const uint32_t x = q & 0xFFFu;
-                const int l = static_cast<int>((q >> 12) & 31u);
-                if (q >> 17) apx_row(&st->side[1], t1, o1, p1, l, x, b0, b1, lane, ovf);
-                else apx_row(&st->side[0], t0, o0, p0, l, x, b0, b1, lane, ovf);
-            }
+            const uint32_t x = static_cast<uint32_t>(a >> (4 * lv));
+            uint32_t V[12];
+#pragma unroll
+            for (int b = 0; b < 12; b++) V[b] = __ballot_sync(kFull, (x >> b) & 1u);
+            const uint32_t Tlo = transpose32(valid ? static_cast<uint32_t>(mask) : 0u, lane);
+            const uint32_t Thi = bal ? 0u : transpose32(valid ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
+            const uint32_t Rp = __ballot_sync(kFull, v > 0), Rn = __ballot_sync(kFull, v < 0);
+            if (Rp) apx_side_batch(&st->side[0], t0, Rp, lv, x, Tlo, Thi, bal, V, lane, ovf);
+            if (Rn) apx_side_batch(&st->side[1], t1, Rn, lv, x, Tlo, Thi, bal, V, lane, ovf);
+            head = (head + k) & (kRing - 1);
+            qn -= k;
+            __syncwarp();  // every lane has read its ring slot before the next writes
+        };
+        uint32_t gid_n = lo + lane < hi ? row_gid(p.in, lo + lane) : 0xFFFFFFFFu;
+        for (uint64_t base = lo; base < hi; base += 32) {
+            const uint32_t gid = gid_n;
+            gid_n = base + 32 + lane < hi ? row_gid(p.in, base + 32 + lane) : 0xFFFFFFFFu;
+            const bool in_range = base + lane < hi;
+            if (in_range && gid >= G && g == 0) raise_status(p.status, kStatusBadGroup);
+            const uint32_t mine = __ballot_sync(kFull, in_range && gid == g);
+            if (mine & (1u << lane))
+                ring[(head + qn + __popc(mine & lt)) & (kRing - 1)] = static_cast<uint16_t>(base + lane - lo);
+            qn += __popc(mine);
+            __syncwarp();
+            if (qn >= 32) batch(32);
         }
+        if (qn) batch(qn);
     }
-    apx_commit(&st->side[0], t0, o0, lane);
-    apx_commit(&st->side[0], t0, p0, lane);
-    apx_commit(&st->side[1], t1, o1, lane);
-    apx_commit(&st->side[1], t1, p1, lane);
     apx_store_totals(st, t0, t1, lane);
     if (lane == 0 && rows_g) atomicAdd(reinterpret_cast<unsigned long long *>(p.ng + g), rows_g);
     __syncthreads();

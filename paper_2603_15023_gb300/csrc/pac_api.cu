@@ -204,24 +204,36 @@ pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
     // groups, the one-launch path the same specs of small ungrouped queries;
     // the per-bit engine serves everything else; agg_path 1 forces the plain
     // per-bit kernels (the baseline the other paths are measured against).
+    // The approximate integer SUM/AVG specs run their own cascades (below);
+    // the path is chosen on the other specs, which also write meta.
+    pac_agg_spec ex[PAC_MAX_SPECS];
+    int32_t n_ex = 0;
+    for (int i = 0; i < n_specs; i++)
+        if (!spec_is_cascade(specs[i])) ex[n_ex++] = specs[i];
+    if (n_ex < n_specs && n_ex == 0 && !meta) {
+        st = run_cascades(ctx, in, specs, n_specs, stream, &launches);
+        if (st != PAC_OK) return st;
+        ctx->last_launches = launches;
+        return PAC_OK;
+    }
     const int want = static_cast<int>(ctx->opt_agg_path);
-    const bool small_ok = (want == 0 || want == 4) && small_supported(in, specs, n_specs) &&
+    const bool small_ok = (want == 0 || want == 4) && n_ex > 0 && small_supported(in, ex, n_ex) &&
                           (want == 4 || in->n <= kSmallAutoRows);
     if (want == 4 && !small_ok) return fail(ctx, PAC_E_UNSUPPORTED, "one-launch path cannot serve this query");
-    bool mma_ok = !small_ok && (want == 0 || want == 2) && mma_supported(in, specs, n_specs);
+    bool mma_ok = !small_ok && (want == 0 || want == 2) && mma_supported(in, ex, n_ex);
     if (want == 2 && !mma_ok) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path cannot serve this query");
     if (small_ok) {
-        st = run_small(ctx, in, specs, n_specs, meta, stream, &launches);
+        st = run_small(ctx, in, ex, n_ex, meta, stream, &launches);
         if (st != PAC_OK) return st;
     } else if (mma_ok) {
-        st = run_mma(ctx, in, specs, n_specs, meta, stream, &launches);
+        st = run_mma(ctx, in, ex, n_ex, meta, stream, &launches);
         if (st != PAC_OK) return st;
         ctx->last_path = 2;
     } else if (want == 1) {
-        st = run_bitloop(ctx, in, specs, n_specs, meta, stream, &launches);
+        st = run_bitloop(ctx, in, ex, n_ex, meta, stream, &launches);
         if (st != PAC_OK) return st;
     } else {
-        st = run_engine(ctx, in, specs, n_specs, meta, stream, &launches);
+        st = run_engine(ctx, in, ex, n_ex, meta, stream, &launches);
         if (st != PAC_OK) return st;
     }
     st = run_cascades(ctx, in, specs, n_specs, stream, &launches);

@@ -121,6 +121,31 @@ def test_approx_cascade_many_flushes(ctx):
     np.testing.assert_array_equal(got[0], ref)
 
 
+@pytest.mark.parametrize("in_flags", [B.PAC_IN_KEYS, B.PAC_IN_MASKS])
+@pytest.mark.parametrize("mode", [B.PAC_HASH_BALANCED, B.PAC_HASH_RAW])
+def test_approx_cascade_headline_shape_bit_exact(ctx, in_flags, mode):
+    """The headline's column shape (4 groups with probabilities .25/.25/.49/
+    .01, cents uniform in [100, 10^7], so most rows land on level 3 and every
+    level total flushes every few dozen rows) on 2M rows, keys or masks, both
+    hash modes, with COUNT on its own path beside the cascades: bit-exact
+    against the oracle's row-by-row cascade."""
+    w = inputs.lowcard_60m(seed=5, n=2_000_000)
+    qk = orc.query_key(5)
+    masks = orc.hash_keys(w.keys, qk, mode)
+    first = masks if in_flags == B.PAC_IN_MASKS else w.keys
+    specs = [(B.PAC_COUNT, B.PAC_EXACT, None), (B.PAC_SUM, B.PAC_APPROX, w.values[0]),
+             (B.PAC_AVG, B.PAC_APPROX, w.values[0]), (B.PAC_SUM, B.PAC_APPROX, w.values[1])]
+    got, meta, st = ctx.aggregate(first, w.gids, 4, specs, in_flags=in_flags, hash_mode=mode, qkey=qk)
+    assert st == B.PAC_OK
+    cnt, mn, mo, _ = orc.aggregate(masks, None, w.gids, 4, orc.COUNT)
+    np.testing.assert_array_equal(got[0], cnt)
+    np.testing.assert_array_equal(meta[:, 0], mn)
+    np.testing.assert_array_equal(meta[:, 1], mo)
+    np.testing.assert_array_equal(got[1], orc.approx_sum_i64(masks, w.values[0], w.gids, 4)[0])
+    np.testing.assert_array_equal(got[2], orc.approx_avg_i64(masks, w.values[0], w.gids, 4)[0])
+    np.testing.assert_array_equal(got[3], orc.approx_sum_i64(masks, w.values[1], w.gids, 4)[0])
+
+
 @pytest.mark.parametrize("vdtype", [np.float32, np.float64])
 def test_approx_float_state_bound(ctx, vdtype):
     n = 300_000
