@@ -125,10 +125,16 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 // restricted to the rows that count) of x_r, from the bit planes V[b] of the
 // rows' units (x < 2^12): a Horner sum of popcounts.
 __device__ __forceinline__ uint32_t plane_sum(uint32_t TS, const uint32_t (&V)[12]) {
-    uint32_t acc = 0;
+    // three independent 4-plane Horner chains (more instruction-level
+    // parallelism than one 12-long chain), joined at the end
+    uint32_t a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
-    for (int b = 11; b >= 0; b--) acc = 2 * acc + __popc(TS & V[b]);
-    return acc;
+    for (int b = 3; b >= 0; b--) {
+        a0 = 2 * a0 + __popc(TS & V[b]);
+        a1 = 2 * a1 + __popc(TS & V[b + 4]);
+        a2 = 2 * a2 + __popc(TS & V[b + 8]);
+    }
+    return a0 + (a1 << 4) + (a2 << 8);
 }
 
 // One side of a dense batch (rows R of the warp's batch, lane r = row r in
@@ -144,21 +150,23 @@ __device__ __forceinline__ void apx_side_batch(ApxSide *s, uint32_t &t, uint32_t
                                                uint32_t Tlo, uint32_t Thi, bool bal, const uint32_t (&V)[12],
                                                int lane, bool &ovf) {
     const uint32_t me = 1u << lane;
-    while (R) {
-        // inclusive prefix of x over this lane's level's rows in R
-        uint32_t P = 0;
-        for (uint32_t todo = R; todo;) {
-            const int l = __shfl_sync(kFull, lv, __ffs(todo) - 1);
-            const uint32_t Ml = __ballot_sync(kFull, lv == l) & R;
-            uint32_t xv = (Ml & me) ? x : 0u;
+    // inclusive prefix of x over this lane's level's rows in R; after each cut
+    // the rows already added are taken out of it (so it counts from the
+    // first row not yet added)
+    uint32_t P = 0;
+    for (uint32_t todo = R; todo;) {
+        const int l = __shfl_sync(kFull, lv, __ffs(todo) - 1);
+        const uint32_t Ml = __ballot_sync(kFull, lv == l) & R;
+        uint32_t xv = (Ml & me) ? x : 0u;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, xv, o);
-                if (lane >= o) xv += y;
-            }
-            if (Ml & me) P = xv;
-            todo &= ~Ml;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, xv, o);
+            if (lane >= o) xv += y;
         }
+        if (Ml & me) P = xv;
+        todo &= ~Ml;
+    }
+    for (;;) {
         const uint32_t tl = __shfl_sync(kFull, t, lv & 31);
         const uint32_t over = __ballot_sync(kFull, (R & me) && tl + P > kCap);
         const uint32_t pre = over ? (R & ((1u << (__ffs(over) - 1)) - 1u)) : R;
@@ -166,10 +174,24 @@ __device__ __forceinline__ void apx_side_batch(ApxSide *s, uint32_t &t, uint32_t
             const int l = __shfl_sync(kFull, lv, __ffs(todo) - 1);
             const uint32_t S = __ballot_sync(kFull, lv == l) & todo;
             const uint32_t tot = __shfl_sync(kFull, P, 31 - __clz(static_cast<int>(S)));
-            const uint32_t lo = plane_sum(Tlo & S, V);
-            const uint32_t hi = bal ? tot - lo : plane_sum(Thi & S, V);
+            uint32_t lo, hi;
+            if (__popc(S) <= 4) {  // a few rows: broadcast them
+                lo = 0;
+                hi = 0;
+                for (uint32_t rr = S; rr; rr &= rr - 1) {
+                    const int r = __ffs(rr) - 1;
+                    const uint32_t xr = __shfl_sync(kFull, x, r);
+                    lo += ((Tlo >> r) & 1u) * xr;
+                    hi += ((Thi >> r) & 1u) * xr;
+                }
+                if (bal) hi = tot - lo;
+            } else {
+                lo = plane_sum(Tlo & S, V);
+                hi = bal ? tot - lo : plane_sum(Thi & S, V);
+            }
             s->w[l][lane] += lo | (hi << 16);
             if (lane == l) t += tot;
+            if (lv == l && !(pre & me)) P -= tot;  // later rows of level l count from here
             todo &= ~S;
         }
         __syncwarp();
@@ -203,6 +225,7 @@ __global__ void __launch_bounds__(32 * kApxBlockChunks, 2) k_apx_chunks(const __
     uint32_t t0 = 0, t1 = 0;
     bool ovf = false;
     uint64_t rows_g = 0;
+    uint32_t c_lo = 0, c_hi = 0;  // this lane's COUNT of worlds lane and lane + 32 (when p.cnt)
     const bool keys_in = (p.in.in_flags & PAC_IN_MASKS) == 0;
     const bool bal = keys_in && p.in.hash_mode == PAC_HASH_BALANCED;
     const uint32_t lt = (1u << lane) - 1u;
@@ -232,6 +255,8 @@ __global__ void __launch_bounds__(32 * kApxBlockChunks, 2) k_apx_chunks(const __
             for (int b = 0; b < 12; b++) V[b] = __ballot_sync(kFull, (x >> b) & 1u);
             const uint32_t Tlo = transpose32(valid ? static_cast<uint32_t>(mask) : 0u, lane);
             const uint32_t Thi = bal ? 0u : transpose32(valid ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
+            c_lo += __popc(Tlo);
+            c_hi += __popc(Thi);
             const uint32_t Rp = __ballot_sync(kFull, v > 0), Rn = __ballot_sync(kFull, v < 0);
             if (Rp) apx_side_batch(&st->side[0], t0, Rp, lv, x, Tlo, Thi, bal, V, lane, ovf);
             if (Rn) apx_side_batch(&st->side[1], t1, Rn, lv, x, Tlo, Thi, bal, V, lane, ovf);
@@ -256,6 +281,10 @@ __global__ void __launch_bounds__(32 * kApxBlockChunks, 2) k_apx_chunks(const __
     }
     apx_store_totals(st, t0, t1, lane);
     if (lane == 0 && rows_g) atomicAdd(reinterpret_cast<unsigned long long *>(p.ng + g), rows_g);
+    if (p.cnt) {
+        if (c_lo) atomicAdd(p.cnt + static_cast<size_t>(g) * kWorlds + lane, static_cast<unsigned long long>(c_lo));
+        if (c_hi) atomicAdd(p.cnt + static_cast<size_t>(g) * kWorlds + 32 + lane, static_cast<unsigned long long>(c_hi));
+    }
     __syncthreads();
     // first tree levels inside the block of chunks
     for (uint32_t width = 1; width < kApxBlockChunks; width *= 2) {
@@ -289,9 +318,23 @@ __global__ void k_apx_combine_level(const __grid_constant__ ApxParams p, uint64_
 __global__ void k_apx_emit(const __grid_constant__ ApxParams p, long long *out_sum, double *out_avg) {
     const size_t cell = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
     const uint32_t G = p.in.n_groups;
-    if (cell >= static_cast<size_t>(G) * kWorlds) return;
-    const uint32_t g = cell / kWorlds;
-    const int j = cell % kWorlds;
+    const bool live = cell < static_cast<size_t>(G) * kWorlds;
+    const uint32_t g = live ? static_cast<uint32_t>(cell / kWorlds) : 0u;
+    const int j = static_cast<int>(cell % kWorlds);
+    if (p.cnt) {
+        // COUNT of the cascade's pass; under balanced keys world 32 + j is the
+        // group's rows minus world j
+        const bool bal = (p.in.in_flags & PAC_IN_MASKS) == 0 && p.in.hash_mode == PAC_HASH_BALANCED;
+        const unsigned long long c =
+            !live ? 0ull : (bal && j >= 32 ? p.ng[g] - p.cnt[static_cast<size_t>(g) * kWorlds + j - 32] : p.cnt[cell]);
+        const unsigned orm = __ballot_sync(0xffffffffu, live && c > 0);  // 32 cells of one group per warp
+        if (live) {
+            if (p.count_out) p.count_out[cell] = c;
+            if (p.meta && (threadIdx.x & 31) == 0) reinterpret_cast<uint32_t *>(p.meta + 2 * g + 1)[j >= 32 ? 1 : 0] = orm;
+            if (p.meta && j == 0) p.meta[2 * g] = p.ng[g];
+        }
+    }
+    if (!live) return;
     const ApxState *st = p.states + g;  // block 0 holds the tree root
     __int128 side[2] = {0, 0};
     for (int s = 0; s < 2; s++)
@@ -318,7 +361,8 @@ int apx_max_groups() { return 32; }
 size_t apx_scratch_bytes(uint64_t n, uint32_t G) {
     const uint64_t n_chunks = (n + kApxChunk - 1) / kApxChunk;
     const uint64_t n_blocks = (n_chunks + kApxBlockChunks - 1) / kApxBlockChunks;
-    return static_cast<size_t>(n_blocks ? n_blocks : 1) * G * sizeof(ApxState) + G * sizeof(uint64_t);
+    return static_cast<size_t>(n_blocks ? n_blocks : 1) * G * sizeof(ApxState) + G * sizeof(uint64_t) +
+           static_cast<size_t>(G) * kWorlds * 8 + 512;
 }
 
 cudaError_t launch_approx(const ApxParams &pin, void *out_sum, void *out_avg, cudaStream_t s,
@@ -329,6 +373,7 @@ cudaError_t launch_approx(const ApxParams &pin, void *out_sum, void *out_avg, cu
     p.chunks_per_block = kApxBlockChunks;
     const uint64_t n_blocks = (p.n_chunks + kApxBlockChunks - 1) / kApxBlockChunks;
     cudaError_t e = cudaMemsetAsync(p.ng, 0, G * sizeof(uint64_t), s);
+    if (e == cudaSuccess && p.cnt) e = cudaMemsetAsync(p.cnt, 0, static_cast<size_t>(G) * kWorlds * 8, s);
     if (e != cudaSuccess) return e;
     if (n_blocks == 0) {
         // no rows: one zero state so that the emit kernel writes zeros

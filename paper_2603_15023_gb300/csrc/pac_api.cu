@@ -149,15 +149,20 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
     if (st == PAC_OK) st = plan_enqueue(ctx, b, stream, ctx->pin);
     if (st == PAC_OK && cudaEventRecord(ctx->pin_ev, stream) != cudaSuccess) st = fail(ctx, PAC_E_CUDA, "event record");
     const bool b_atomic = b->n_atomic > 0;
+    const int n_wide = b->n_wide;
     plan_destroy(b);
     if (st != PAC_OK) return st;
-    *launches += 2 + (b_atomic ? 3 : 0);
+    *launches += 2 + (b_atomic ? 3 : 0) + 2 * n_wide;
     ctx->last_path = 3;
     return PAC_OK;
 }
 
+// counts / n_counts / meta: COUNT specs and the metadata, produced by the
+// first cascade's pass (n_counts = 0 and meta = NULL: none).
 pac_status run_cascades(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
-                        cudaStream_t stream, int *launches) {
+                        cudaStream_t stream, int *launches, const pac_agg_spec *counts = nullptr,
+                        int n_counts = 0, uint64_t *meta = nullptr) {
+    bool first = true;
     for (int i = 0; i < n_specs; i++) {
         if (!spec_is_cascade(specs[i])) continue;
         // one cascade per distinct column serves its SUM and AVG specs
@@ -180,6 +185,11 @@ pac_status run_cascades(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *s
         if (st != PAC_OK) return st;
         Carver cv(ctx->ws);
         p.ng = static_cast<uint64_t *>(cv.take(in->n_groups * sizeof(uint64_t)));
+        if (first && (n_counts > 0 || meta)) {
+            p.cnt = static_cast<unsigned long long *>(cv.take(static_cast<size_t>(in->n_groups) * kWorlds * 8));
+            p.count_out = n_counts > 0 ? static_cast<unsigned long long *>(counts[0].out) : nullptr;
+            p.meta = meta;
+        }
         p.states = static_cast<ApxState *>(cv.take(states));
         PAC_CUDA(ctx, launch_approx(p, first_sum >= 0 ? specs[first_sum].out : nullptr,
                                     first_avg >= 0 ? specs[first_avg].out : nullptr, stream, launches));
@@ -191,6 +201,11 @@ pac_status run_cascades(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *s
             PAC_CUDA(ctx, cudaMemcpyAsync(specs[k].out, src, static_cast<size_t>(in->n_groups) * kWorlds * 8,
                                           cudaMemcpyDeviceToDevice, stream));
         }
+        if (first)
+            for (int k = 1; k < n_counts; k++)
+                PAC_CUDA(ctx, cudaMemcpyAsync(counts[k].out, counts[0].out, static_cast<size_t>(in->n_groups) * kWorlds * 8,
+                                              cudaMemcpyDeviceToDevice, stream));
+        first = false;
     }
     return PAC_OK;
 }
@@ -210,8 +225,11 @@ pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
     int32_t n_ex = 0;
     for (int i = 0; i < n_specs; i++)
         if (!spec_is_cascade(specs[i])) ex[n_ex++] = specs[i];
-    if (n_ex < n_specs && n_ex == 0 && !meta) {
-        st = run_cascades(ctx, in, specs, n_specs, stream, &launches);
+    bool only_counts = true;
+    for (int i = 0; i < n_ex; i++) only_counts = only_counts && ex[i].kind == PAC_COUNT;
+    if (n_ex < n_specs && only_counts && ctx->opt_agg_path == 0) {
+        // COUNT and meta come out of the first cascade's pass over the rows
+        st = run_cascades(ctx, in, specs, n_specs, stream, &launches, ex, n_ex, meta);
         if (st != PAC_OK) return st;
         ctx->last_launches = launches;
         return PAC_OK;

@@ -98,6 +98,12 @@ struct ApxParams {
     uint32_t *status;
     uint64_t n_chunks;
     uint32_t chunks_per_block;
+    // COUNT and meta of the query from the same pass (or nullptr): cnt [G][64]
+    // accumulators (zeroed by the launcher), count_out [G][64] uint64, meta
+    // [G][2] {n_g, or_g}
+    unsigned long long *cnt;
+    unsigned long long *count_out;
+    uint64_t *meta;
 };
 
 int apx_max_groups();
