@@ -892,11 +892,12 @@ __global__ void __launch_bounds__(256) k_part_hist(const BatchQueryDev *__restri
 
 // One CTA (1024 threads) per query: pcur = exclusive prefix of pcnt,
 // pcnt[G] = the number of rows kept, pcnt[G+1] = 1 when one group holds more
-// than 1/64 of them.
+// than 1/64 of them.  Queries above kWideScanGroups take the multi-block scan
+// below instead.
 __global__ void __launch_bounds__(1024) k_part_scan(const BatchQueryDev *__restrict__ qs) {
     __shared__ uint32_t wsum[32];
     const BatchQueryDev &q = qs[blockIdx.x];
-    if (q.mode != 1) return;
+    if (q.mode != 1 || q.in.n_groups > kWideScanGroups) return;
     const uint32_t G = q.in.n_groups;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t chunk = (G + blockDim.x - 1) / blockDim.x;
@@ -938,6 +939,91 @@ __global__ void __launch_bounds__(1024) k_part_scan(const BatchQueryDev *__restr
         // a group holding more than 1/64 of the rows makes the query "hot":
         // its scatter then reserves ranges per item instead of per warp
         q.pcnt[G + 1] = static_cast<uint64_t>(s_mx) * 64 > kept ? 1u : 0u;
+    }
+}
+
+// Multi-block scan of one query with many groups: block b of nb takes the
+// groups [G b / nb, G (b+1) / nb).  Pass 1 writes each range's sum and
+// maximum to part[b] and part[nb + b]; pass 2 scans each range in 1024-group
+// tiles (coalesced) from the sum of the ranges before it, and the last block
+// writes pcnt[G] (rows kept) and pcnt[G+1] (the hot flag).
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    total = wsum[nw - 1];
+    const uint32_t r = v + (warp > 0 ? wsum[warp - 1] : 0u);
+    __syncthreads();  // wsum is reused by the next call
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_wide_sum(const uint32_t *__restrict__ pcnt, uint32_t G, uint32_t nb,
+                                                        uint32_t *__restrict__ part) {
+    __shared__ uint32_t red[2][32];
+    const uint32_t b = blockIdx.x;
+    const uint32_t g0 = static_cast<uint32_t>(static_cast<uint64_t>(G) * b / nb);
+    const uint32_t g1 = static_cast<uint32_t>(static_cast<uint64_t>(G) * (b + 1) / nb);
+    uint32_t sum = 0, mx = 0;
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        const uint32_t c = pcnt[g];
+        sum += c;
+        mx = max(mx, c);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    sum = __reduce_add_sync(kFull, sum);
+    mx = __reduce_max_sync(kFull, mx);
+    if (lane == 0) {
+        red[0][warp] = sum;
+        red[1][warp] = mx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        sum = __reduce_add_sync(kFull, lane < nw ? red[0][lane] : 0u);
+        mx = __reduce_max_sync(kFull, lane < nw ? red[1][lane] : 0u);
+        if (lane == 0) {
+            part[b] = sum;
+            part[nb + b] = mx;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_wide_apply(uint32_t *__restrict__ pcnt, uint32_t *__restrict__ pcur,
+                                                          uint32_t G, uint32_t nb, const uint32_t *__restrict__ part) {
+    __shared__ uint32_t wsum[32];
+    const uint32_t b = blockIdx.x;
+    const uint32_t g0 = static_cast<uint32_t>(static_cast<uint64_t>(G) * b / nb);
+    const uint32_t g1 = static_cast<uint32_t>(static_cast<uint64_t>(G) * (b + 1) / nb);
+    uint32_t run = 0;
+    for (uint32_t k = 0; k < b; k++) run += part[k];
+    for (uint32_t base = g0; base < g1; base += blockDim.x) {
+        const uint32_t g = base + threadIdx.x;
+        const uint32_t c = g < g1 ? pcnt[g] : 0u;
+        uint32_t total;
+        const uint32_t incl = block_incl_scan(c, wsum, total);
+        if (g < g1) pcur[g] = run + incl - c;
+        run += total;
+    }
+    if (b == nb - 1 && threadIdx.x == 0) {
+        uint32_t mx = 0;
+        for (uint32_t k = 0; k < nb; k++) mx = max(mx, part[nb + k]);
+        pcnt[G] = run;  // every range's rows: the rows kept
+        pcnt[G + 1] = static_cast<uint64_t>(mx) * 64 > run ? 1u : 0u;
     }
 }
 
@@ -1272,7 +1358,8 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             b->rel_abs[i] = align_up(zero_off, 256);
             zero_off = b->rel_abs[i] + kMaxSpecs * 8;
             b->rel_pcnt[i] = align_up(zero_off, 256);
-            zero_off = b->rel_pcnt[i] + (static_cast<size_t>(G) + 2) * 4;
+            zero_off = b->rel_pcnt[i] + (static_cast<size_t>(G) + 2 + 2 * kWideScanBlocks) * 4;
+            if (G > kWideScanGroups) b->n_wide++;
             // group-ordered copies (fully overwritten by the scatter)
             p_pcur[i] = align_up(part_off, 256);
             part_off = p_pcur[i] + static_cast<size_t>(G) * 4;
@@ -1391,6 +1478,18 @@ pac_status plan_enqueue(pac_ctx *ctx, pac_batch *b, cudaStream_t s, const void *
                                                                         std::max<uint32_t>(b->n_items, 1)));
         k_part_hist<<<pgrid, 256, 0, s>>>(d_q, d_items, b->n_items, b->d_status);
         k_part_scan<<<static_cast<unsigned>(b->n_queries), 1024, 0, s>>>(d_q);
+        if (b->n_wide > 0) {
+            const BatchQueryDev *hq = reinterpret_cast<const BatchQueryDev *>(b->image.data() + b->img_q);
+            for (int i = 0; i < b->n_queries; i++) {
+                const uint32_t G = hq[i].in.n_groups;
+                if (hq[i].mode != 1 || G <= kWideScanGroups) continue;
+                uint32_t *pcnt = reinterpret_cast<uint32_t *>(base + b->rel_pcnt[i]);
+                uint32_t *pcur = reinterpret_cast<uint32_t *>(base + b->rel_pcur[i]);
+                const uint32_t nb = wide_scan_blocks(G);
+                k_scan_wide_sum<<<nb, 1024, 0, s>>>(pcnt, G, nb, pcnt + G + 2);
+                k_scan_wide_apply<<<nb, 1024, 0, s>>>(pcnt, pcur, G, nb, pcnt + G + 2);
+            }
+        }
         k_part_scatter<<<pgrid, 256, 0, s>>>(d_q, d_items, b->n_items);
         PAC_CUDA(ctx, cudaGetLastError());
     }
@@ -1586,7 +1685,8 @@ pac_status pac_batch_info(const pac_batch *plan, const char *name, int64_t *valu
     if (!strcmp(name, "n_items")) *value = plan->n_items;
     else if (!strcmp(name, "item_rows")) *value = plan->cfg.item_rows;
     else if (!strcmp(name, "smem_cap")) *value = static_cast<int64_t>(plan->cfg.smem_cap);
-    else if (!strcmp(name, "kernels")) *value = 2 + (plan->n_rel > 0 ? 1 : 0) + (plan->n_atomic > 0 ? 3 : 0);
+    else if (!strcmp(name, "kernels"))
+        *value = 2 + (plan->n_rel > 0 ? 1 : 0) + (plan->n_atomic > 0 ? 3 : 0) + 2 * plan->n_wide;
     else if (!strcmp(name, "n_warp_private")) *value = plan->n_warp_private;
     else if (!strcmp(name, "n_atomic")) *value = plan->n_atomic;
     else if (!strcmp(name, "device_bytes")) *value = static_cast<int64_t>(plan->device_bytes);

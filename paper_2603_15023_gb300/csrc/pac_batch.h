@@ -55,6 +55,17 @@ constexpr BatchConfig kBatchDefault = {1u << 16, 100 * 1024};
 // it ran in (~earliest block start, latest block end; %globaltimer ns).
 constexpr size_t kPlanSpanOffset = 16;
 
+// A partitioned query with more groups than this scans its group counts with
+// a multi-block scan of up to kWideScanBlocks blocks (16K groups or more per
+// block) instead of one block per query.  Its block sums and maxima follow
+// the query's pcnt[G+2] counters (2 * kWideScanBlocks more words, zeroed).
+constexpr uint32_t kWideScanGroups = 32768;
+constexpr uint32_t kWideScanBlocks = 64;
+inline uint32_t wide_scan_blocks(uint32_t G) {
+    const uint32_t nb = (G + 16383) / 16384;
+    return nb < kWideScanBlocks ? nb : kWideScanBlocks;
+}
+
 }  // namespace pacgpu
 
 // A plan: host image of the device descriptors plus the device layout.
@@ -72,6 +83,7 @@ struct pac_batch {
     size_t smem = 0;
     int n_ctas = 0;
     int n_warp_private = 0, n_atomic = 0;
+    int n_wide = 0;  // partitioned queries with the multi-block scan
     pacgpu::BatchConfig cfg{};
     uint64_t total_cells = 0;
     std::vector<unsigned char> image;

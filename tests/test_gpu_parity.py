@@ -464,3 +464,27 @@ def test_lowcard_60m_approx_full_size_bound(ctx):
             bound = exact.astype(np.float64) * (2.0**-8 + 25 * 2.0**-11.9)
             diff = exact - approx[:, j]
             assert np.all(diff >= 0) and np.all(diff <= bound), (k, j)
+
+
+@pytest.mark.parametrize("G", [40_000, 150_001])
+def test_many_groups_multi_block_scan(ctx, G):
+    """Queries above 32K groups scan their group counts with several blocks:
+    the partitioned engine path with Zipf-like skew (one hot group) and a
+    uniform tail, every world against the oracle."""
+    n = 400_003
+    r = np.random.default_rng(G)
+    gids = np.where(r.random(n) < 0.2, 0, r.integers(0, G, n)).astype(np.int32)
+    keys = r.integers(0, 60_000, n).astype(np.int64)
+    vals = r.integers(-(10**6), 10**6, n).astype(np.int64)
+    qk = orc.query_key(G)
+    masks = orc.hash_keys(keys, qk, orc.BALANCED)
+    specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, vals), (B.PAC_MAX, 0, vals)]
+    got, meta, st = ctx.aggregate(keys, gids, G, specs, qkey=qk)
+    assert st == B.PAC_OK
+    assert ctx.last_path == 3
+    for (kind, _, v), g_out in zip(specs, got):
+        ref, mn, mo, rst = orc.aggregate(masks, v, gids, G, kind)
+        assert rst == 0
+        np.testing.assert_array_equal(g_out, ref)
+    np.testing.assert_array_equal(meta[:, 0], mn)
+    np.testing.assert_array_equal(meta[:, 1], mo)
