@@ -70,6 +70,14 @@ WORKLOADS = {
                            "describe": "lowcard_60m with the paper's approximate SUM and AVG (Sec. 5: 25 levels "
                                        "of 16-bit counters cascading every 4 bits, two-sided); count + 4 sum + 4 "
                                        "avg, adaptive finalize of 36 cells"},
+    "hash_100m": {"gid_bytes": 0, "n_cols": 0, "aggs": "hash", "finalize": "none", "hash_only": True,
+                  "in_bytes_per_row": 8 + 8, "flush_l2": False,
+                  "describe": "pac_hash_keys alone: 100M int64 PU keys (uniform over 10M) to balanced 64-bit "
+                              "world masks (Sec. 2, Sec. 4.2), 8 bytes in and 8 out per row"},
+    "lowcard_60m_m128": {"gid_bytes": 1, "n_cols": 4, "aggs": "count+sum+avg", "finalize": "adaptive",
+                         "in_bytes_per_row": 8 + 1 + 4 * 8, "flush_l2": False, "worlds": 128,
+                         "describe": "lowcard_60m over m = 128 worlds (two keyed re-hashes, Sec. 2): count + 4 "
+                                     "sum + 4 avg, exact; adaptive finalize of 36 cells over 128 worlds"},
     "select_60m": {"gid_bytes": 1, "n_cols": 4, "aggs": "count+sum+avg", "finalize": "adaptive",
                    "in_bytes_per_row": 8 + 1 + 4 * 8, "flush_l2": False, "select": True,
                    "describe": "lowcard_60m under a correlated PAC selection (Sec. 4.2): world j of a row kept "
@@ -263,6 +271,8 @@ def _select_operands(orc, wl, G, qk):
 
 def _oracle_step(orc, wcfg, wl, G, qk, thr=None):
     masks = orc.hash_keys(wl.keys, qk, orc.BALANCED)
+    if wcfg.get("hash_only"):
+        return
     gids, vals = wl.gids, wl.values[:wcfg["n_cols"]]
     if thr is not None:
         masks, _ = orc.select(masks, wl.values[0], orc.LT, thr, wl.gids)
@@ -356,6 +366,8 @@ def cpu_oracle_chunked(workload: str, rows: int, threads: int, chunk: int = 1 <<
     def one(b):
         a, e = b
         masks = orc.hash_keys(wl.keys[a:e], qk, orc.BALANCED)
+        if wcfg.get("hash_only"):
+            return None
         gids = None if wl.gids is None else wl.gids[a:e]
         cnt, n_g, or_g, _ = orc.aggregate(masks, None, gids, G, orc.COUNT)
         sums = [orc.aggregate(masks, v[a:e], gids, G, orc.SUM)[0] for v in wl.values[:C]]
@@ -369,6 +381,9 @@ def cpu_oracle_chunked(workload: str, rows: int, threads: int, chunk: int = 1 <<
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
         parts = list(ex.map(one, bounds))
+    if wcfg.get("hash_only"):
+        dt = time.perf_counter() - t0
+        return rows / dt, dt
     cnt = np.zeros((G, 64), np.uint64)
     sums = [np.zeros((G, 64), np.int64) for _ in range(C)]
     n_g = np.zeros(G, np.uint64)
@@ -806,9 +821,10 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
     d_keys = torch.from_numpy(wl.keys).cuda()
     d_gids = torch.from_numpy(wl.gids).cuda() if wl.gids is not None else None
     d_vals = [torch.from_numpy(v).cuda() for v in wl.values[:C]]
-    outs = [torch.empty((G, 64), dtype=torch.int64 if i < 1 + C else torch.float64, device="cuda")
+    W = wcfg.get("worlds", 64)
+    outs = [torch.empty((G, W), dtype=torch.int64 if i < 1 + C else torch.float64, device="cuda")
             for i in range(n_specs)]
-    meta = torch.empty((G, 2), dtype=torch.int64, device="cuda")
+    meta = torch.empty((G, 2 if W == 64 else 3), dtype=torch.int64, device="cuda")
     n_cells = G * n_specs
     noised = torch.empty(n_cells, dtype=torch.float64, device="cuda")
     is_null = torch.empty(n_cells, dtype=torch.uint8, device="cuda")
@@ -844,8 +860,16 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                 (B.PAC_LIFT_SPEC, 1, 0), (B.PAC_LIFT_DIV, 0, 0)]
         lift = (lift_specs, B.make_lift(prog), len(prog), share)
 
+    qk2 = B.pac_query_key2(rank)
+
+    d_masks = torch.empty(n if wcfg.get("hash_only") else 0, dtype=torch.int64, device="cuda")
+
     def aggregate(sp_ptr):
-        if sel is not None:
+        if wcfg.get("hash_only"):
+            B.pac_hash_keys(ctx, d_keys.data_ptr(), d_masks.data_ptr(), n, qk, B.PAC_HASH_BALANCED, sp_ptr)
+        elif W == 128:
+            B.pac_aggregate128(ctx, inp, qk2, specs, n_specs, meta.data_ptr(), sp_ptr)
+        elif sel is not None:
             B.pac_aggregate_select(ctx, inp, sel, specs, n_specs, meta.data_ptr(), sp_ptr)
         else:
             B.pac_aggregate_multi(ctx, inp, specs, n_specs, meta.data_ptr(), sp_ptr)
@@ -864,8 +888,9 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                 lift_ev.append(le)
             k += B.pac_get_info(ctx, "last_launches")
         if in_step_finalize:
-            B.pac_finalize(ctx, specs, n_specs, G, meta.data_ptr(), 1000 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
-                           noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sp_ptr)
+            fin = B.pac_finalize128 if W == 128 else B.pac_finalize
+            fin(ctx, specs, n_specs, G, meta.data_ptr(), 1000 + i, 1.0 / 128, B.PAC_FIN_ADAPTIVE,
+                noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sp_ptr)
             k += B.pac_get_info(ctx, "last_launches")
         return k
 
@@ -886,7 +911,7 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
     # and replayed; the other paths plan on the host per call and are timed
     # as stream work.  Either way the reported time is the median step.
     graphs = None
-    if path in (2, 4) and sel is None and lift is None and not wcfg.get("approx"):
+    if (path in (2, 4) or wcfg.get("hash_only")) and sel is None and lift is None and not wcfg.get("approx"):
         try:
             g_agg, g_rel = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
             launches_agg = launches_rel = 0
@@ -944,6 +969,32 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
               "launching stream" if graphs is not None else
               f"median of {steps} steps enqueued on one stream, CUDA events on that stream")
 
+    # m = 128: the same columns aggregated over 64 worlds, timed the same way,
+    # for the cost ratio of the second mask word
+    m128 = None
+    if W == 128:
+        o64 = [torch.empty((G, 64), dtype=torch.int64 if i < 1 + C else torch.float64, device="cuda")
+               for i in range(n_specs)]
+        meta64 = torch.empty((G, 2), dtype=torch.int64, device="cuda")
+        specs64 = B.make_specs(_spec_list(B, wcfg, [v.data_ptr() for v in d_vals], [o.data_ptr() for o in o64]))
+        g64 = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                B.pac_aggregate_multi(ctx, inp, specs64, n_specs, meta64.data_ptr(), sptr)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g64, stream=stream):
+            B.pac_aggregate_multi(ctx, inp, specs64, n_specs, meta64.data_ptr(), stream.cuda_stream)
+        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for a, b in ev64:
+                a.record(stream)
+                g64.replay()
+                b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = statistics.median(a.elapsed_time(b) for a, b in ev64)
+        m128 = {"agg_ms_m128": agg_med, "agg_ms_m64": ms64, "cost_ratio": agg_med / ms64,
+                "note": "the paper expects at most twice the cost for m = 128 (Sec. 2)"}
+
     # the release of every cell, timed once beside the step when it is not in it
     fin_ms = None
     if not in_step_finalize:
@@ -962,7 +1013,27 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
 
     # end to end through the C ABI from pinned host memory
     e2e = None
-    if args.e2e_steps > 0 and (sel is not None or lift is not None):
+    if args.e2e_steps > 0 and wcfg.get("hash_only"):
+        # keys from pinned host memory, the hash, the masks back to pinned host memory
+        h_keys = torch.from_numpy(wl.keys).pin_memory()
+        h_masks = torch.empty(n, dtype=torch.int64).pin_memory()
+
+        def e2e_hash():
+            with torch.cuda.stream(stream):
+                d_keys.copy_(h_keys, non_blocking=True)
+                B.pac_hash_keys(ctx, d_keys.data_ptr(), d_masks.data_ptr(), n, qk, B.PAC_HASH_BALANCED, sptr)
+                h_masks.copy_(d_masks, non_blocking=True)
+            torch.cuda.synchronize()
+
+        for _ in range(2):
+            e2e_hash()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_hash()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": n * world / dt, "unit": "rows/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+               "ms_per_step": dt * 1e3}
+    elif args.e2e_steps > 0 and (sel is not None or lift is not None or W == 128):
         # host columns -> device (pinned, on the step's stream), selection /
         # aggregation / lifting and the release through the C ABI, released
         # cells -> host
@@ -988,8 +1059,9 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                 aggregate(sptr)
                 if lift is not None:
                     B.pac_lift(ctx, lift[0], 2, G, lift[1], lift[2], lift[3].data_ptr(), sptr)
-                B.pac_finalize(ctx, rel_specs, rel_n, G, meta.data_ptr(), 100 + i, 1.0 / 128, rel_mode,
-                               noised.data_ptr(), is_null.data_ptr(), flags.data_ptr(), 0, sptr)
+                (B.pac_finalize128 if W == 128 else B.pac_finalize)(
+                    ctx, rel_specs, rel_n, G, meta.data_ptr(), 100 + i, 1.0 / 128, rel_mode, noised.data_ptr(),
+                    is_null.data_ptr(), flags.data_ptr(), 0, sptr)
                 h_noised.copy_(noised[:rel_cells], non_blocking=True)
                 h_null.copy_(is_null[:rel_cells], non_blocking=True)
                 h_flags.copy_(flags[:rel_cells], non_blocking=True)
@@ -1029,7 +1101,7 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                "ms_per_step": dt * 1e3}
 
     peak, peak_src = _peaks()
-    out_bytes = G * 64 * 8 * n_specs + G * 16
+    out_bytes = 0 if wcfg.get("hash_only") else G * W * 8 * n_specs + G * (16 if W == 64 else 24)
     algo_bytes = n * wcfg["in_bytes_per_row"] + out_bytes
     achieved = algo_bytes / (agg_med / 1e3) / 1e9
     path_name = {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
@@ -1037,12 +1109,16 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                     "shared memory)",
                  4: "one launch on CUDA cores (warp bit-transpose, int128 sums, last CTA writes the outputs)"
                  }.get(path, str(path))
+    if wcfg.get("hash_only"):
+        path_name = "k_hash_keys (16-byte vector loads and stores, grid = SMs x 8)"
     kernel = {1: "per-bit CUDA-core aggregation (all launches of pac_aggregate_multi)",
               2: ("k_select_prep + k_select + k_agg_mma + k_mma_finish (all launches of pac_aggregate_select)"
                   if sel is not None else "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
               3: "k_batch_agg + k_batch_merge, after k_part_hist + k_part_scan + k_part_scatter when the "
                  "rows are partitioned by group (all launches of pac_aggregate_multi)",
               4: "k_small_agg (the only launch of pac_aggregate_multi)"}.get(path, str(path))
+    if wcfg.get("hash_only"):
+        kernel = "k_hash_keys (the only launch of pac_hash_keys)"
     if wcfg.get("approx"):
         # the exact specs (COUNT and the row counts) take `path`; each distinct
         # value column of an approximate spec runs one cascade
@@ -1074,6 +1150,8 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
         }
         if fin_ms is not None:
             line["finalize_ms"] = fin_ms
+        if m128 is not None:
+            line["m128"] = m128
         if lift is not None and lift_ms:
             lms = statistics.median(a.elapsed_time(b) for a, b in lift_ms)
             lb = G * 64 * (8 + 8 + 8)   # two operand vectors in, the lifted vector out

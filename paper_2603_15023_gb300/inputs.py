@@ -148,7 +148,16 @@ def max_1g_increasing(seed: int = 0, n: int = 1_000_000_000) -> Workload:
     return max_1g(seed, n, order="increasing")
 
 
+def hash_100m(seed: int = 0, n: int = 100_000_000, n_keys: int = 10_000_000) -> Workload:
+    """The key column of the high-cardinality shape alone: PU keys uniform over
+    10M keys, for the standalone key-to-mask hash."""
+    keys = uniform_i64(seed, 0, n, 0, n_keys - 1)
+    return Workload("hash_100m", n, 1, keys, None, [], {"n_keys": n_keys})
+
+
 WORKLOADS = {
+    "hash_100m": hash_100m,
+    "lowcard_60m_m128": lowcard_60m,  # the same columns over 128 worlds
     "ungrouped_1m": ungrouped_1m,
     "max_1g": max_1g,
     "max_1g_increasing": max_1g_increasing,
