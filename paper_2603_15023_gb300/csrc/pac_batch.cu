@@ -148,9 +148,13 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
     gid = 0;
     mask = 0;
     if (is.smask) {  // group-ordered copy: ids already checked, masks already hashed
+        // records of 16 bytes: {mask, first slot value}; further slots in sval
+        unsigned long long v0 = 0;
         if (valid) {
             gid = __ldg(is.sgid + row);
-            mask = __ldg(reinterpret_cast<const unsigned long long *>(is.smask) + row);
+            const ulonglong2 rec = __ldg(reinterpret_cast<const ulonglong2 *>(is.smask) + row);
+            mask = rec.x;
+            v0 = rec.y;
             if (drop_row(is.in, mask)) {
                 valid = false;
                 gid = 0;
@@ -160,7 +164,7 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
         for (int s = 0; s < NS; s++) {
             vals[s] = 0;
             if (s < nslots_of<SIG>(is) && valid) {
-                vals[s] = __ldg(reinterpret_cast<const unsigned long long *>(is.sval) + s * is.n + row);
+                vals[s] = s == 0 ? v0 : __ldg(reinterpret_cast<const unsigned long long *>(is.sval) + (s - 1) * is.n + row);
                 if (op_of<SIG>(is, s) == OP_ISUM) {
                     const long long v = static_cast<long long>(vals[s]);
                     const uint64_t a = v < 0 ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
@@ -1109,14 +1113,20 @@ __global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__res
 #pragma unroll
             for (int u = 0; u < kU; u++) {
                 if (!valid[u]) continue;
-                q.smask[d[u]] = masks_in ? raw[u] : keyed_world_mask(static_cast<long long>(raw[u]), q.in.qkey,
-                                                                     q.in.hash_mode);
+                const uint64_t m = masks_in ? raw[u] : keyed_world_mask(static_cast<long long>(raw[u]), q.in.qkey,
+                                                                        q.in.hash_mode);
+                // one 16-byte record per row: the mask and the first slot value
+                // (a scattered row then touches two sectors, not three)
+                if (q.n_slots > 0)
+                    reinterpret_cast<ulonglong2 *>(q.smask)[d[u]] = make_ulonglong2(m, v[u][0]);
+                else
+                    q.smask[2 * static_cast<uint64_t>(d[u])] = m;
                 q.sgid[d[u]] = g[u];
 #pragma unroll
-                for (int s2 = 0; s2 < kHoist; s2++)
-                    if (s2 < q.n_slots) q.sval[static_cast<uint64_t>(s2) * q.in.n + d[u]] = v[u][s2];
+                for (int s2 = 1; s2 < kHoist; s2++)
+                    if (s2 < q.n_slots) q.sval[static_cast<uint64_t>(s2 - 1) * q.in.n + d[u]] = v[u][s2];
                 for (int s2 = kHoist; s2 < q.n_slots; s2++)
-                    q.sval[static_cast<uint64_t>(s2) * q.in.n + d[u]] = load_slot_value(q.slot[s2], r[u]);
+                    q.sval[static_cast<uint64_t>(s2 - 1) * q.in.n + d[u]] = load_slot_value(q.slot[s2], r[u]);
             }
         }
         __syncthreads();
@@ -1363,12 +1373,12 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             // group-ordered copies (fully overwritten by the scatter)
             p_pcur[i] = align_up(part_off, 256);
             part_off = p_pcur[i] + static_cast<size_t>(G) * 4;
-            p_smask[i] = align_up(part_off, 256);
-            part_off = p_smask[i] + n * 8;
+            p_smask[i] = align_up(part_off, 256);  // 16-byte records {mask, slot 0}
+            part_off = p_smask[i] + n * 16;
             p_sgid[i] = align_up(part_off, 256);
             part_off = p_sgid[i] + n * 4;
-            p_sval[i] = align_up(part_off, 256);
-            part_off = p_sval[i] + n * 8 * static_cast<size_t>(d.n_slots);
+            p_sval[i] = align_up(part_off, 256);  // slots 1 .. n_slots-1
+            part_off = p_sval[i] + n * 8 * static_cast<size_t>(d.n_slots > 0 ? d.n_slots - 1 : 0);
             b->n_atomic++;
         }
         prefix[i + 1] = prefix[i] + static_cast<uint64_t>(G) * kWorlds;

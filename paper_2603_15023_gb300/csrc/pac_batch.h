@@ -32,9 +32,9 @@ struct BatchQueryDev {
     // of one group are long and atomics are paid once per run
     uint32_t *pcnt;   // [G+2] rows per group (zeroed); [G] = rows kept, [G+1] = hot flag (after the scan)
     uint32_t *pcur;   // [G] scatter cursors
-    uint64_t *smask;  // [n] world masks in group order
+    uint64_t *smask;  // [n] 16-byte records {world mask, slot 0 value} in group order
     uint32_t *sgid;   // [n] group ids in group order
-    uint64_t *sval;   // [n_slots][n] slot values (64-bit patterns) in group order
+    uint64_t *sval;   // [n_slots-1][n] values of slots 1.. (64-bit patterns) in group order
 };
 
 struct BatchItem {
