@@ -119,20 +119,26 @@ def _traffic(workload: str, n: int, path: int):
     summaries (a `bench-traffic:` line for the workload and aggregation path,
     path 2 when the line names none), scaled to n rows; None when no capture
     exists or the kernel source changed since it was taken."""
-    pat = re.compile(r"bench-traffic:\s*workload=(\S+)\s+(?:path=(\d+)\s+)?kernel_source=(\S+)\s+sha=(\S+)"
-                     r"\s+bytes_per_row=([0-9.]+)")
+    return _traffic_kernel(workload, n, path)[0]
+
+
+def _traffic_kernel(workload: str, n: int, path: int):
+    """(bytes, kernel) of the `bench-traffic:` line (kernel: the line's
+    `kernel=` field, None when it names none); (None, None) when none applies."""
+    pat = re.compile(r"bench-traffic:\s*workload=(\S+)\s+(?:path=(\d+)\s+)?(?:kernel=(\S+)\s+)?kernel_source=(\S+)"
+                     r"\s+sha=(\S+)\s+bytes_per_row=([0-9.]+)")
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(f) as fh:
             for line in fh:
                 m = pat.search(line)
                 if m and m.group(1) == workload and int(m.group(2) or 2) == path:
                     try:
-                        if _source_sha(m.group(3)) != m.group(4):
-                            return None
+                        if _source_sha(m.group(4)) != m.group(5):
+                            return None, None
                     except OSError:
-                        return None
-                    return float(m.group(5)) * n
-    return None
+                        return None, None
+                    return float(m.group(6)) * n, m.group(3)
+    return None, None
 
 
 class ClockSampler:
@@ -658,6 +664,7 @@ def measure_batch(args, suite=False):
                        "timing": f"median of {args.steps} CUDA-graph replays, CUDA events on the launching stream"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": _traffic("batch_4096", db.total_rows, 3),
+                         "traffic_kernel": _traffic_kernel("batch_4096", db.total_rows, 3)[1],
                          "kernel": "k_batch_agg + k_batch_merge (one graph replay)",
                          "algorithmic_bytes": algo, "peak_source": peak_src},
             "cpu_baseline": cpu,
@@ -1141,6 +1148,7 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                        **({"minmax_prune": bool(args.minmax_prune)} if "max" in wcfg["aggs"] else {})},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(workload, n, path),
+                         "traffic_kernel": _traffic_kernel(workload, n, path)[1] or kernel.split(" ")[0],
                          "kernel": kernel, "algorithmic_bytes": algo_bytes, "peak_source": peak_src,
                          "agg_ms": agg_med, "agg_ms_min": min(agg_ms)},
             "cpu_baseline": cpu,
