@@ -815,7 +815,7 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
     world, rank, local = _dist()
     ctx = B.pac_create(local)
     if args.path and not suite:
-        B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2, "engine": 3, "small": 4}[args.path])
+        B.pac_set_option(ctx, "agg_path", {"auto": 0, "bitloop": 1, "mma": 2, "engine": 3, "small": 4, "part": 5}[args.path])
     B.pac_set_option(ctx, "minmax_prune", args.minmax_prune)
 
     wcfg = WORKLOADS[workload]
@@ -1114,7 +1114,9 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
     path_name = {1: "per-bit CUDA cores", 2: "tcgen05 tensor cores",
                  3: "per-bit engine (rows partitioned by group first when the groups' states exceed "
                     "shared memory)",
-                 4: "one launch on CUDA cores (warp bit-transpose, int128 sums, last CTA writes the outputs)"
+                 4: "one launch on CUDA cores (warp bit-transpose, int128 sums, last CTA writes the outputs)",
+                 5: "rows partitioned by group, then tcgen05 tensor cores over the group-ordered rows "
+                    "(bulk-copy staged; groups inside a 32-row block summed by their warp)"
                  }.get(path, str(path))
     if wcfg.get("hash_only"):
         path_name = "k_hash_keys (16-byte vector loads and stores, grid = SMs x 8)"
@@ -1123,7 +1125,9 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                   if sel is not None else "k_agg_mma + k_mma_finish (all launches of pac_aggregate_multi)"),
               3: "k_batch_agg + k_batch_merge, after k_part_hist + k_part_scan + k_part_scatter when the "
                  "rows are partitioned by group (all launches of pac_aggregate_multi)",
-              4: "k_small_agg (the only launch of pac_aggregate_multi)"}.get(path, str(path))
+              4: "k_small_agg (the only launch of pac_aggregate_multi)",
+              5: "k_part_hist + k_part_scan + k_part_scatter + k_part_mma + k_part_merge + k_part_empty "
+                 "(all launches of pac_aggregate_multi)"}.get(path, str(path))
     if wcfg.get("hash_only"):
         kernel = "k_hash_keys (the only launch of pac_hash_keys)"
     if wcfg.get("approx"):
@@ -1214,7 +1218,7 @@ def main():
                          "configuration of the suite in `workloads`")
     ap.add_argument("--no-suite", action="store_true", help="default run: the headline workload only")
     ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
-    ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma", "engine", "small"])
+    ap.add_argument("--path", default=None, choices=[None, "auto", "bitloop", "mma", "engine", "small", "part"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--minmax-prune", type=int, default=1, choices=[0, 1],
                     help="MIN/MAX bound pruning on the per-bit engine (results are identical either way)")

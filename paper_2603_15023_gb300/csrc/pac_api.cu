@@ -10,6 +10,7 @@
 #include "pac_internal.cuh"
 #include "pac_kernels.h"
 #include "pac_mma.h"
+#include "pac_part_mma.h"
 #include "pac_small.h"
 #include "pac_validate.h"
 #include "pac_batch.h"
@@ -94,8 +95,11 @@ pac_status run_bitloop(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *sp
 // The per-bit engine of the batched path (warp bit-transpose, warp-private
 // or atomic states) on one query: a one-query plan placed in the context's
 // workspace, its descriptors staged in pinned memory.
+// tensor: the many-group tensor-core path instead -- the same plan, ending
+// with the partition, then the tensor-core kernel over the group-ordered
+// copies (its partial records placed after the plan in the workspace).
 pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *specs, int32_t n_specs,
-                      uint64_t *meta, cudaStream_t stream, int *launches) {
+                      uint64_t *meta, cudaStream_t stream, int *launches, bool tensor = false) {
     pac_agg_spec kept[PAC_MAX_SPECS];
     int k = 0;
     for (int i = 0; i < n_specs; i++)
@@ -116,10 +120,13 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
     while (rows < per_slot && rows < cfg.item_rows) rows <<= 1;
     while (in->n / rows > 2048 && rows < (1u << 30)) rows <<= 1;
     cfg.item_rows = rows;
+    cfg.partition_only = tensor;
     pac_batch *b = nullptr;
     pac_status st = plan_build(ctx, &q, 1, cfg, &b);
     if (st != PAC_OK) return st;
-    st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes, b->device_bytes);
+    const size_t part_off = align_up(b->device_bytes, 256);
+    st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes,
+                       tensor ? part_off + part_mma_scratch_bytes(in->n, ctx->n_sms) : b->device_bytes);
     if (st == PAC_OK && ctx->pin_bytes < b->image.size()) {
         if (ctx->pin) {
             cudaEventSynchronize(ctx->pin_ev);
@@ -150,10 +157,33 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
     if (st == PAC_OK && cudaEventRecord(ctx->pin_ev, stream) != cudaSuccess) st = fail(ctx, PAC_E_CUDA, "event record");
     const bool b_atomic = b->n_atomic > 0;
     const int n_wide = b->n_wide;
+    if (st == PAC_OK && tensor) {
+        char *base = static_cast<char *>(ctx->ws);
+        PartMmaArgs a{};
+        a.in = make_input(in);
+        a.rec = base + b->rel_smask[0];
+        a.sgid = reinterpret_cast<const uint32_t *>(base + b->rel_sgid[0]);
+        a.pcnt = reinterpret_cast<const uint32_t *>(base + b->rel_pcnt[0]);
+        a.specs = kept;
+        a.n_specs = k;
+        a.meta = meta;
+        a.scratch = base + part_off;
+        a.status = ctx->d_status;
+        a.n_sms = ctx->n_sms;
+        a.wait_ns = static_cast<uint64_t>(ctx->opt_wait_ns);
+        const char *why = "";
+        st = part_mma_launch(a, stream, launches, &why);
+        if (st != PAC_OK) st = fail(ctx, st, "many-group tensor-core path: %s", why);
+    }
     plan_destroy(b);
     if (st != PAC_OK) return st;
-    *launches += 2 + (b_atomic ? 3 : 0) + 2 * n_wide;
-    ctx->last_path = 3;
+    if (tensor) {
+        *launches += 3 + 2 * n_wide;  // histogram, scan, scatter (+ the wide scan)
+        ctx->last_path = 5;
+    } else {
+        *launches += 2 + (b_atomic ? 3 : 0) + 2 * n_wide;
+        ctx->last_path = 3;
+    }
     return PAC_OK;
 }
 
@@ -240,6 +270,11 @@ pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
     if (want == 4 && !small_ok) return fail(ctx, PAC_E_UNSUPPORTED, "one-launch path cannot serve this query");
     bool mma_ok = !small_ok && (want == 0 || want == 2) && mma_supported(in, ex, n_ex);
     if (want == 2 && !mma_ok) return fail(ctx, PAC_E_UNSUPPORTED, "tensor-core path cannot serve this query");
+    // many groups: the partition and the tensor cores over the group-ordered rows
+    const bool part_ok = !small_ok && !mma_ok && (want == 0 || want == 5) && in->n > 0 && n_ex > 0 &&
+                         (want == 5 || in->n_groups > kPartMmaAutoGroups) && part_mma_specs_served(ex, n_ex);
+    if (want == 5 && !part_ok)
+        return fail(ctx, PAC_E_UNSUPPORTED, "many-group tensor-core path cannot serve this query");
     if (small_ok) {
         st = run_small(ctx, in, ex, n_ex, meta, stream, &launches);
         if (st != PAC_OK) return st;
@@ -247,6 +282,9 @@ pac_status aggregate_impl(pac_ctx *ctx, const pac_input *in, const pac_agg_spec 
         st = run_mma(ctx, in, ex, n_ex, meta, stream, &launches);
         if (st != PAC_OK) return st;
         ctx->last_path = 2;
+    } else if (part_ok) {
+        st = run_engine(ctx, in, ex, n_ex, meta, stream, &launches, true);
+        if (st != PAC_OK) return st;
     } else if (want == 1) {
         st = run_bitloop(ctx, in, ex, n_ex, meta, stream, &launches);
         if (st != PAC_OK) return st;
@@ -668,7 +706,7 @@ pac_status pac_query_host(pac_ctx *ctx, const pac_input *in_h, const pac_agg_spe
 pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value) {
     if (!ctx || !name) return PAC_E_INVALID;
     if (strcmp(name, "agg_path") == 0) {
-        if (value < 0 || value > 4) return fail(ctx, PAC_E_INVALID, "agg_path %lld", static_cast<long long>(value));
+        if (value < 0 || value > 5) return fail(ctx, PAC_E_INVALID, "agg_path %lld", static_cast<long long>(value));
         ctx->opt_agg_path = value;
         return PAC_OK;
     }

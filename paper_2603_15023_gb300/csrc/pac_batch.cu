@@ -1339,7 +1339,7 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         const uint32_t G = q.in.n_groups;
         const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
         const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);
-        d.mode = smem_need <= cfg.smem_cap ? 0 : 1;
+        d.mode = (smem_need <= cfg.smem_cap && !cfg.partition_only) ? 0 : 1;
         const uint64_t n = q.in.n;
         const uint32_t n_items = n == 0 ? 1u : static_cast<uint32_t>((n + cfg.item_rows - 1) / cfg.item_rows);
         d.first_item = static_cast<uint32_t>(hitems.size());
@@ -1361,12 +1361,14 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             part_off = p_ng[i] + static_cast<size_t>(G) * 8 * n_items;
             b->n_warp_private++;
         } else {
-            b->rel_state[i] = align_up(zero_off, 256);
-            zero_off = b->rel_state[i] + per_part;
-            b->rel_ng[i] = align_up(zero_off, 256);
-            zero_off = b->rel_ng[i] + static_cast<size_t>(G) * 8;
-            b->rel_abs[i] = align_up(zero_off, 256);
-            zero_off = b->rel_abs[i] + kMaxSpecs * 8;
+            if (!cfg.partition_only) {
+                b->rel_state[i] = align_up(zero_off, 256);
+                zero_off = b->rel_state[i] + per_part;
+                b->rel_ng[i] = align_up(zero_off, 256);
+                zero_off = b->rel_ng[i] + static_cast<size_t>(G) * 8;
+                b->rel_abs[i] = align_up(zero_off, 256);
+                zero_off = b->rel_abs[i] + kMaxSpecs * 8;
+            }
             b->rel_pcnt[i] = align_up(zero_off, 256);
             zero_off = b->rel_pcnt[i] + (static_cast<size_t>(G) + 2 + 2 * kWideScanBlocks) * 4;
             if (G > kWideScanGroups) b->n_wide++;
@@ -1376,7 +1378,7 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             p_smask[i] = align_up(part_off, 256);  // 16-byte records {mask, slot 0}
             part_off = p_smask[i] + n * 16;
             p_sgid[i] = align_up(part_off, 256);
-            part_off = p_sgid[i] + n * 4;
+            part_off = p_sgid[i] + n * 4 + 16;  // 16 bytes readable past the end (bulk copies of whole 16-byte units)
             p_sval[i] = align_up(part_off, 256);  // slots 1 .. n_slots-1
             part_off = p_sval[i] + n * 8 * static_cast<size_t>(d.n_slots > 0 ? d.n_slots - 1 : 0);
             b->n_atomic++;
@@ -1503,6 +1505,7 @@ pac_status plan_enqueue(pac_ctx *ctx, pac_batch *b, cudaStream_t s, const void *
         k_part_scatter<<<pgrid, 256, 0, s>>>(d_q, d_items, b->n_items);
         PAC_CUDA(ctx, cudaGetLastError());
     }
+    if (b->cfg.partition_only) return PAC_OK;
 #define PAC_LAUNCH(NS_, SIG_)                                                                              \
     if (b->ns == NS_ && b->sig == SIG_)                                                                    \
         k_batch_agg<NS_, SIG_><<<grid, kBatchWarps * 32, b->smem, s>>>(d_q, d_items, b->n_items, counter,  \

@@ -46,6 +46,10 @@ struct BatchItem {
 struct BatchConfig {
     uint32_t item_rows;  // rows per work item
     size_t smem_cap;     // warp-private states only when they fit this many bytes
+    // every query partitioned, no aggregation states and no aggregation
+    // launches: the plan ends with the group-ordered copies (read by the
+    // many-group tensor-core kernel)
+    bool partition_only = false;
 };
 constexpr BatchConfig kBatchDefault = {1u << 16, 100 * 1024};
 

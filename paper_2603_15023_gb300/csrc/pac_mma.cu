@@ -7,7 +7,8 @@
 // state is the small matrix product  D_g = Bits_g^T * Digits_g  (64 worlds x
 // features) accumulated on the tensor cores:
 //   A operand  (M = 64 worlds x K rows): bit j of row i as an E4M3 byte,
-//              0x00 or 0x01;
+//              0x00 or 0x01 (worlds in an interleaved row order that takes
+//              two operations per four bytes to lay out);
 //   B operand  (N features x K rows): a constant 1 (COUNT) and the digits of
 //              each value column as E4M3 bytes 0x00..0x0F;
 //   D          FP32 in tensor memory.
@@ -35,12 +36,14 @@
 #include "pac_internal.cuh"
 #include "pac_kernels.h"
 #include "pac_mma.h"
+#include "pac_tc.cuh"
 
 namespace pacgpu {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using namespace tc;
+
 constexpr int kThreads = 512;        // producer threads: two groups of 8 warps
 constexpr int kGroupThreads = 256;   // one producer group
 constexpr int kMmaWarps = 4;         // warps issuing tcgen05.mma
@@ -57,12 +60,9 @@ constexpr int kMaxGroups = 8;
 constexpr int kMaxCols = 4;
 constexpr uint32_t kMaxRowsPerCta = 1u << 20;  // keeps FP32 digit totals below 2^24
 constexpr uint32_t kTmemCols = 512;
-constexpr uint64_t kWaitNs = 2000000000ull;  // default: a wait gives up after 2 s of wall time
-constexpr uint32_t kSuspendHintNs = 20000;    // longest park of one try_wait
 
 // Accumulator / feature columns per group for C value columns.
 __host__ __device__ constexpr int feat_alloc(int C) { return C == 1 ? 32 : 80; }
-__host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
 
 struct MmaParams {
     InputDev in;
@@ -78,123 +78,6 @@ struct MmaParams {
     unsigned long long *ng;  // [G] rows per group (zeroed)
     uint32_t *status;
     uint64_t wait_ns;        // limit of the pipeline waits (the final drain keeps kWaitNs)
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait on an mbarrier phase; false once limit_ns of wall time have
-// passed.  Each try_wait may park the warp until the phase completes
-// (suspend-time hint, never longer than the limit) and polls back off with
-// __nanosleep, so a waiting warp takes few issue slots from the warps it is
-// waiting for.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
-    uint32_t done = 0;
-    uint32_t ns = 16;
-    const uint32_t hint = limit_ns < kSuspendHintNs ? static_cast<uint32_t>(limit_ns) : kSuspendHintNs;
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 0;; ++it) {
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity), "r"(hint)
-            : "memory");
-        if (done) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-        if (it >= 8) {
-            __nanosleep(ns);
-            if (ns < 128) ns <<= 1;
-        }
-    }
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
-           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// kind::f8f6f4, A = B = E4M3, D = F32, A and B MN-major, M = 64 or 128.
-template <int M>
-__device__ __forceinline__ uint32_t instr_desc(int n) {
-    return (1u << 4) | (1u << 15) | (1u << 16) | (static_cast<uint32_t>(n >> 3) << 17) |
-           (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc));
-}
-
-__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-
-// 4 mask bits -> 4 bytes 0x00/0x01
-__device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
-
-// Digit bytes of one row.  C4 = 1: one column, feature 4+q = digit q.
-// C4 = 4: up to four columns, feature 4 + 4q + c = digit q of column c.
-// Word 0 holds the COUNT feature (byte 1) and three zero pad features.
-template <int C4, int L>
-struct Features {
-    static constexpr int kN = round16(4 + L * C4);
-    static constexpr int kWords = kN / 4;
-    __device__ __forceinline__ static uint32_t sm_byte(long long d) {
-        return d < 0 ? (0x80u | static_cast<uint32_t>(-d)) : static_cast<uint32_t>(d);
-    }
-    __device__ __forceinline__ static void build(long long v0, long long v1, long long v2, long long v3, bool sgn,
-                                                 uint32_t *w) {
-        w[0] = 1u;
-#pragma unroll
-        for (int k = 1; k < kWords; k++) w[k] = 0u;
-        if (C4 == 1) {
-            const unsigned long long u = static_cast<unsigned long long>(v0);
-#pragma unroll
-            for (int k = 0; k < (L + 3) / 4; k++) {
-                uint32_t x = static_cast<uint32_t>(u >> (16 * k)) & 0xFFFFu;
-                x = (x | (x << 8)) & 0x00FF00FFu;
-                x = (x | (x << 4)) & 0x0F0F0F0Fu;
-                w[1 + k] = x;
-            }
-            if (L % 4) w[1 + (L - 1) / 4] &= (1u << (8 * (L % 4))) - 1u;  // digits < L only
-            if (sgn) {
-                const int wi = 1 + (L - 1) / 4, sh = 8 * ((L - 1) % 4);
-                w[wi] = (w[wi] & ~(0xFFu << sh)) | (sm_byte(v0 >> (4 * (L - 1))) << sh);
-            }
-        } else {
-            // byte p of the four values holds digits 2p and 2p+1
-#pragma unroll
-            for (int p = 0; p < L / 2; p++) {
-                const int h = p / 4, b = p % 4;
-                const uint32_t a0 = static_cast<uint32_t>(static_cast<unsigned long long>(v0) >> (32 * h));
-                const uint32_t a1 = static_cast<uint32_t>(static_cast<unsigned long long>(v1) >> (32 * h));
-                const uint32_t a2 = static_cast<uint32_t>(static_cast<unsigned long long>(v2) >> (32 * h));
-                const uint32_t a3 = static_cast<uint32_t>(static_cast<unsigned long long>(v3) >> (32 * h));
-                const uint32_t sel = static_cast<uint32_t>(b | ((4 + b) << 4));
-                const uint32_t word = __byte_perm(__byte_perm(a0, a1, sel), __byte_perm(a2, a3, sel), 0x5410);
-                w[1 + 2 * p] = word & 0x0F0F0F0Fu;
-                w[2 + 2 * p] = (word >> 4) & 0x0F0F0F0Fu;
-            }
-            if (sgn) {
-                const int sh = 4 * (L - 1);
-                w[L] = sm_byte(v0 >> sh) | (sm_byte(v1 >> sh) << 8) | (sm_byte(v2 >> sh) << 16) |
-                       (sm_byte(v3 >> sh) << 24);
-            }
-        }
-    }
 };
 
 template <int C4, int L>
@@ -308,9 +191,6 @@ __device__ __forceinline__ void producers_sync(int pg) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + pg), "n"(kGroupThreads) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Shared state of one CTA of the tensor-core aggregation.  Producer group g
 // (warps 8g..8g+7) fills stage g with the tiles it = g, g+2, g+4, ...
@@ -536,10 +416,9 @@ __device__ __forceinline__ void produce_tile(const MmaParams &p, MmaShared &sh, 
         for (int k = 0; k < kWords; k++) {
             if (k >= kWords / 2 && balanced_keys) continue;
             const uint32_t x = wd[r][k];
-            sts128(a_row + 256 * k, spread4(x & 0xF), spread4((x >> 4) & 0xF), spread4((x >> 8) & 0xF),
-                   spread4((x >> 12) & 0xF));
-            sts128(a_row + 256 * k + 128, spread4((x >> 16) & 0xF), spread4((x >> 20) & 0xF),
-                   spread4((x >> 24) & 0xF), spread4(x >> 28));
+            sts128(a_row + 256 * k, world_bytes(x, 0), world_bytes(x, 1), world_bytes(x, 2), world_bytes(x, 3));
+            sts128(a_row + 256 * k + 128, world_bytes(x, 4), world_bytes(x, 5), world_bytes(x, 6),
+                   world_bytes(x, 7));
         }
     }
     write_features_rows<C4, R>(L, b_stage, slot, rr, neg);
@@ -762,11 +641,12 @@ __global__ void __launch_bounds__(kThreads + 32 * kMmaWarps, 1) k_agg_mma(const 
     if (sh.abort_flag) {
         if (tid == 0) raise_status(p.status, kStatusTimeout);
     } else if (warp < 4) {
-        // read back: for M = 64, TMEM lane 32w + l (l < 16) holds world
-        // 16w + l; for M = 128, lane 32w + l holds world 32w + l.  The slots of
-        // a group add into the same totals.
+        // read back: for M = 64, TMEM lane 32w + l (l < 16) holds accumulator
+        // row 16w + l; for M = 128, lane 32w + l holds row 32w + l.  Row r
+        // holds world world_of_row(r) (under balanced keys row M/2, the run
+        // total, maps to itself).  The slots of a group add into the same totals.
         const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
-        const int world = (M / 4) * warp + lane;
+        const int world = world_of_row((M / 4) * warp + lane);
         for (int sl = 0; sl < sh.n_slots; sl++) {
             const uint32_t g = sh.sl_group[sl];
             for (int c0 = 0; c0 < p.n_alloc; c0 += 16) {
@@ -895,6 +775,9 @@ int mma_columns(const pac_agg_spec *specs, int n_specs, const void **cols) {
 
 }  // namespace
 
+static_assert(world_of_row(kWorlds / 2) == kWorlds / 2 && world_of_row(1) == 8 && world_of_row(4) == 1 &&
+                  world_of_row(127) == 127,
+              "accumulator rows must map onto the worlds as the operand words lay them out");
 static_assert(kMmaMaxScratchBytes == static_cast<size_t>(kTmemCols) * kWorlds * 8 + 256 + kMaxGroups * 8,
               "kMmaMaxScratchBytes must follow the tensor-memory and group limits");
 

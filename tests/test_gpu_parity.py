@@ -413,10 +413,11 @@ def test_avg_exact_when_the_sum_overflows(ctx, path):
 def test_highcard_100m_full_size_sampled(ctx):
     """The 100M-row, 1M-group Zipf workload at full size, in the launch
     configuration the benchmark times (automatic path: rows partitioned by
-    group, then the per-bit engine).  Sampled groups (the largest, a middle
-    and a tail one) against the oracle on exactly their rows; every group
-    against the balanced invariants (worlds j and j+32 split the group's rows
-    and its value total)."""
+    group, then the many-group tensor-core kernel).  Sampled groups (the
+    largest, a middle and a tail one) against the oracle on exactly their
+    rows; every group against the balanced invariants (worlds j and j+32
+    split the group's rows and its value total) and against the per-bit
+    engine, bit for bit."""
     w = inputs.highcard_100m(seed=0)
     G = w.n_groups
     qk = orc.query_key(0)
@@ -424,7 +425,12 @@ def test_highcard_100m_full_size_sampled(ctx):
     specs = [(B.PAC_COUNT, 0, None), (B.PAC_SUM, 0, v)]
     got, meta, st = ctx.aggregate(w.keys, w.gids, G, specs, qkey=qk)
     assert st == B.PAC_OK
-    assert ctx.last_path == 3
+    assert ctx.last_path == 5
+    got3, meta3, st3 = ctx.aggregate(w.keys, w.gids, G, specs, qkey=qk, path=3)
+    assert st3 == B.PAC_OK
+    for a, b in zip(got, got3):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(meta, meta3)
     for g in (0, 4321, G - 1):
         rows = np.flatnonzero(w.gids == g)
         masks = orc.hash_keys(w.keys[rows], qk, orc.BALANCED)
