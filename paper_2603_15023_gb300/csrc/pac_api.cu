@@ -164,6 +164,7 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
         a.rec = base + b->rel_smask[0];
         a.sgid = reinterpret_cast<const uint32_t *>(base + b->rel_sgid[0]);
         a.pcnt = reinterpret_cast<const uint32_t *>(base + b->rel_pcnt[0]);
+        a.pend = reinterpret_cast<const uint32_t *>(base + b->rel_pcur[0]);
         a.specs = kept;
         a.n_specs = k;
         a.meta = meta;

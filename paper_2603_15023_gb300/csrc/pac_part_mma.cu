@@ -25,8 +25,8 @@
 //     block's world bytes as A and a B copy that holds the group's digits
 //     and zeros in the block's other rows (at most two per block: such a
 //     group always holds the block's first or last row).
-// The MMAs of one group accumulate into one of 16 tensor-memory slots, a ring
-// over the CTA's tensor-core groups in order; the slot of a new group is
+// The MMAs of one group accumulate into one of sixteen tensor-memory slots (a
+// ring over the CTA's tensor-core groups in order); the slot of a new group is
 // taken once the epilogue has emptied it.  When a group's last MMA is done,
 // the epilogue warps read its slot, zero it, and write the group's
 // COUNT/SUM/AVG and metadata.  A group that crosses an edge of the CTA's
@@ -34,8 +34,10 @@
 // adds the partials of each such group in CTA order.  No result is written
 // with an atomic operation.
 //
-// Warps: 0-7 producers (blocks w and w + 8 of every chunk), 8-11 epilogue
-// (tensor-memory lane quadrants 0-3), 12 bulk-copy loader, 13 MMA issuer.
+// Warps: 0-15 producers (block w of every chunk), 16-19 epilogue
+// (tensor-memory lane quadrants 0-3), 20 bulk-copy loader, 21 MMA issuer,
+// 22 classifier (each chunk's group starts and edge classes, ahead of the
+// producers, which then share no barrier).
 // Every wait is bounded (%globaltimer); a wait that gives up stops its warp's
 // work, the CTA drains what it has in flight and reports PAC_E_TIMEOUT.
 #include <climits>
@@ -56,13 +58,19 @@ constexpr int kBlocks = kChunk / 32;       // 32-row blocks per chunk
 constexpr int kPairs = 2 * kBlocks;        // MMAs per chunk at most (two runs per block)
 constexpr int kRawStages = 4;              // chunks in flight
 constexpr int kOpStages = 2;               // operand stages
-constexpr int kProdWarps = 8;
-constexpr int kEpiWarp0 = 8;               // warps 8..11: epilogue, quadrant = warp % 4
-constexpr int kLoadWarp = 12;
-constexpr int kMmaWarp = 13;
-constexpr int kThreadsP = 14 * 32;
-constexpr int kAlloc = 32;                 // tensor-memory columns per slot
-constexpr int kSlots = 512 / kAlloc;       // accumulator slots
+constexpr int kProdWarps = 16;             // one 32-row block each per chunk
+constexpr int kBlocksPerWarp = kBlocks / kProdWarps;
+constexpr int kEpiWarp0 = kProdWarps;      // epilogue warps, lane quadrant = warp % 4
+constexpr int kLoadWarp = kEpiWarp0 + 4;
+constexpr int kIssuers = 1;                // MMA-issuing warps (more did not pay: see the issue loop)
+constexpr int kMmaWarp0 = kLoadWarp + 1;
+constexpr int kClsWarp = kMmaWarp0 + kIssuers;  // classifies each chunk's groups ahead of the producers
+constexpr int kThreadsP = (kClsWarp + 1) * 32;
+constexpr int kAlloc = 32;                 // tensor-memory columns per accumulator
+// A group's MMAs rotate over kSub accumulators, one per issuing warp; a
+// slot = kSub accumulators.
+constexpr int kSub = kIssuers;
+constexpr int kSlots = 512 / (kAlloc * kSub);  // slots in the ring
 constexpr int kFeat = 20;                  // COUNT, three pad features, 16 digits
 constexpr int kInfo = 256;                 // per-group records of the ring (see the MMA warp)
 constexpr int kNMax = 32;                  // B bytes per row: N for 16 digits
@@ -84,6 +92,9 @@ constexpr uint32_t kOpBytes = kABytes + kBBytes;
 constexpr size_t kSmemP = static_cast<size_t>(kRawStages) * kRawBytes + kOpStages * kOpBytes;
 
 static_assert(kSlots >= 2, "the slot ring needs two slots");
+static_assert(kBlocks % kProdWarps == 0 && kProdWarps <= 32, "producer warps split the chunk's blocks evenly");
+static_assert(kPairs == 32, "the MMA warp holds one pair per lane");
+static_assert(kEpiWarp0 % 4 == 0, "epilogue warp q must own tensor-memory lane quadrant q");
 static_assert(kInfo >= kSlots + 3 * kPairs, "the group records must outlive the ring");
 
 // One MMA of a chunk: a run of group `gid` in block (pair index / 2).
@@ -107,7 +118,7 @@ struct PartShared {
     uint64_t raw_empty[kRawStages];
     uint64_t full[kOpStages];
     uint64_t empty[kOpStages];
-    uint64_t done[kSlots];   // MMA warp (commit + arrive) -> epilogue: the slot's group is complete
+    uint64_t done[kSlots];   // MMA warps (a commit each + an arrive) -> epilogue: the slot's group is complete
     uint64_t freeb[kSlots];  // epilogue (4 warps) -> MMA warp: the slot is zero and free
     uint64_t drain;
     uint32_t tmem_slot;
@@ -116,10 +127,11 @@ struct PartShared {
     uint32_t split_lo;       // group crossing the CTA's left edge, or kNone
     uint32_t split_hi;       // group crossing its right edge, or kNone
     int epi_go;
-    int prod_go;             // producers: the chunk (and the next one, when needed) has landed
-    uint32_t sbits[2][kBlocks];      // per chunk parity: group start bits of the chunk's rows
-    uint32_t prev_gid[2];            // per chunk parity: the chunk's last group ...
-    int prev_cls[2];                 // ... and its class as the next chunk sees it
+    uint64_t cls_full[kRawStages];   // classifier -> producers: the chunk in raw slot r is classified
+    uint8_t ccls[kRawStages][kBlocks];  // per raw slot and block: first-row class | last-row class << 2
+    uint8_t pvalid[kOpStages][kProdWarps];  // valid pairs of warp w: bits 2bb, 2bb + 1 = block w + 16 bb
+    uint32_t prev_gid0;              // chunk 0: the group crossing the left edge (or kNone) ...
+    int prev_cls0;                   // ... and its class
     PairRec pairs[kOpStages][kPairs];
     OrdInfo info[kInfo];
     long long tot[kFeat];            // balanced keys: the total row of the group being emitted
@@ -141,6 +153,7 @@ struct PartMmaParams {
     const ulonglong2 *rec;     // [n] group-ordered {mask, value}
     const uint32_t *sgid;      // [n] group-ordered group ids
     const uint32_t *pcnt;      // [G + 2]: rows per group, [G] = rows kept
+    const uint32_t *pend;      // [G]: end of each group's rows in the group order
     uint32_t rows_per_cta;
     int32_t bal;               // balanced keys: accumulator row 32 is the run total
     int32_t has_col;           // 0: COUNT only (the records carry no value)
@@ -165,10 +178,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                      smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
-}
-
-__device__ __forceinline__ void producers_sync() {
-    asm volatile("bar.sync 1, 256;" ::: "memory");
 }
 
 __device__ __forceinline__ void epi_sync() {
@@ -201,8 +210,23 @@ __device__ __forceinline__ void emit_world(const PartMmaParams &p, uint32_t g, i
     if (used && !fits) raise_status(p.status, kStatusOverflow);
 }
 
-// A group's SUM from its digit totals d[4 + q] (digit q, weight 16^q).
+// A group's SUM from its digit totals d[4 + q] (digit q, weight 16^q).  A
+// digit total is below 2^24 in magnitude (at most 2^20 rows of digits below
+// 16), so each half, sum_{q<8} d_q 16^q and sum_{q>=8} d_q 16^(q-8), stays
+// below 2^53: two 64-bit Horner chains, joined once in 128 bits.
 __device__ __forceinline__ __int128 digits_to_sum(const long long (&d)[kFeat]) {
+    long long lo = 0, hi = 0;
+#pragma unroll
+    for (int q = 7; q >= 0; q--) {
+        lo = lo * 16 + d[4 + q];
+        hi = hi * 16 + d[12 + q];
+    }
+    return static_cast<__int128>(lo) + (static_cast<__int128>(hi) << 32);
+}
+
+// The same for digit totals added over several CTAs (no bound on their size
+// beyond int64): one 128-bit Horner chain.
+__device__ __forceinline__ __int128 digits_to_sum_wide(const long long (&d)[kFeat]) {
     __int128 t = 0;
 #pragma unroll
     for (int q = 15; q >= 0; q--) t = t * 16 + d[4 + q];
@@ -233,8 +257,8 @@ __device__ __forceinline__ void pair_features(uint32_t b_pair, int lane, bool me
     const uint32_t base = b_pair + (lane >> 3) * ((F::kN / 16) * 128) + (lane & 7) * 16;
 #pragma unroll
     for (int h = 0; h < F::kN / 16; h++) {
-        if (member) sts128(base + h * 128, w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3]);
-        else sts128(base + h * 128, 0u, 0u, 0u, 0u);
+        if (member) sts128_unordered(base + h * 128, w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3]);
+        else sts128_unordered(base + h * 128, 0u, 0u, 0u, 0u);
     }
 }
 
@@ -247,12 +271,29 @@ __device__ __forceinline__ void group_results(const PartMmaParams &p, uint32_t g
     const uint32_t c_lo = __popc(T & Rl);
     const uint32_t c_hi = p.bal ? __popc(Rl) - c_lo : __popc(T2 & Rl);
     __int128 s_lo = 0, s_hi = 0, tot = 0;
-    for (uint32_t rr = Rl; rr; rr &= rr - 1) {
-        const int i = __ffs(rr) - 1;
-        const long long vi = __shfl_sync(kFull, v, i);
-        tot += vi;
-        if ((T >> i) & 1u) s_lo += vi;
-        if ((T2 >> i) & 1u) s_hi += vi;
+    // at most 32 values below 2^58 in magnitude: every sum fits int64
+    const bool wide = __any_sync(kFull, ((Rl >> lane) & 1u) &&
+                                            (static_cast<unsigned long long>(v ^ (v >> 63)) >> 58) != 0);
+    if (!wide) {
+        long long a_lo = 0, a_hi = 0, at = 0;
+        for (uint32_t rr = Rl; rr; rr &= rr - 1) {
+            const int i = __ffs(rr) - 1;
+            const long long vi = __shfl_sync(kFull, v, i);
+            at += vi;
+            a_lo += ((T >> i) & 1u) ? vi : 0ll;
+            a_hi += ((T2 >> i) & 1u) ? vi : 0ll;
+        }
+        s_lo = a_lo;
+        s_hi = a_hi;
+        tot = at;
+    } else {
+        for (uint32_t rr = Rl; rr; rr &= rr - 1) {
+            const int i = __ffs(rr) - 1;
+            const long long vi = __shfl_sync(kFull, v, i);
+            tot += vi;
+            if ((T >> i) & 1u) s_lo += vi;
+            if ((T2 >> i) & 1u) s_hi += vi;
+        }
     }
     if (p.bal) s_hi = tot - s_lo;
     emit_world(p, g, lane, c_lo, s_lo);
@@ -266,201 +307,144 @@ __device__ __forceinline__ void group_results(const PartMmaParams &p, uint32_t g
     }
 }
 
-// How a group is aggregated.  MMA: tensor cores (more than 32 rows, or the
-// group crosses an edge of the CTA's range); DIRECT: by one warp, all its
-// rows at once (at most 32 rows); SKIP: a group that began in the previous
-// chunk and was finished there.
-enum : int { kClsMma = 0, kClsDirect = 1, kClsSkip = 2 };
+// How the tensor-core kernel treats a group of its range.  MMA: more than 32
+// rows (tensor cores); SMALL: at most 32 rows, left to k_part_small; SKIP: a
+// SMALL group that began in the previous chunk (or range).
+enum : int { kClsMma = 0, kClsSmall = 1, kClsSkip = 2 };
 
-// Start-bit searches over a chunk (lane k < 16 holds word k; bit i of word k:
-// row 32k + i is the first row of a group in the chunk).  Warp-uniform.
-__device__ __forceinline__ int prev_start(uint32_t Sk, int lane, int r) {
-    const int w = r >> 5;
-    const uint32_t upto = (r & 31) == 31 ? 0xFFFFFFFFu : ((2u << (r & 31)) - 1u);
-    const uint32_t m = lane < w ? Sk : (lane == w ? (Sk & upto) : 0u);
-    const uint32_t bl = __ballot_sync(kFull, m != 0);
-    if (!bl) return -1;
-    const int k = 31 - __clz(static_cast<int>(bl));
-    const uint32_t mk = __shfl_sync(kFull, m, k);
-    return 32 * k + 31 - __clz(static_cast<int>(mk));
+// Inclusive prefix maximum over lanes (up) and suffix minimum (down).
+__device__ __forceinline__ int scan_max_up(int x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x = max(x, y);
+    }
+    return x;
 }
 
-__device__ __forceinline__ int next_start(uint32_t Sk, int lane, int r, int nv) {
-    const int w = r >> 5;
-    const uint32_t above = (r & 31) == 31 ? 0u : ~((2u << (r & 31)) - 1u);
-    const uint32_t m = (lane > w && lane < kBlocks) ? Sk : (lane == w ? (Sk & above) : 0u);
-    const uint32_t bl = __ballot_sync(kFull, m != 0);
-    if (!bl) return nv;
-    const int k = __ffs(bl) - 1;
-    const uint32_t mk = __shfl_sync(kFull, m, k);
-    return 32 * k + __ffs(mk) - 1;
+__device__ __forceinline__ int scan_min_down(int x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_down_sync(kFull, x, o);
+        if (lane + o < 32) x = min(x, y);
+    }
+    return x;
 }
 
-// What every producer warp knows of the chunk after its start bits are in.
-struct ChunkView {
-    const ulonglong2 *rec_s;   // this chunk's records
-    const ulonglong2 *rec_n;   // the next chunk's (when the last group was looked up in it)
-    const uint32_t *gid_s;
-    uint32_t Sk;               // this lane's start-bit word (lanes < 16)
-    int nv;                    // valid rows of the chunk
-    int last_s, last_tot, last_cls;  // the chunk's last group: first row (-1: began earlier), rows, class
-    int prev_cls;              // class of a group that began in an earlier chunk
+// The classes of every block's edge groups in one pass over the chunk's
+// start bits (lane b < 16 = block b; bit i of word b: row 32b + i is the first
+// row of a group): the group holding the block's first row and the one
+// holding its last valid row (distinct when the block holds a start after
+// its first row).  chunk_scans: per lane the last start before word b and
+// the first start after it, and (uniform) the first row of the chunk's last
+// group (-1: it began in an earlier chunk).
+struct ChunkScan {
+    int pmax_ex, smin_ex, ls, last_s;
 };
 
-// Extent and class of the group that holds chunk row r.
-__device__ __forceinline__ void group_at(const ChunkView &cv, int lane, int r, int &s, int &tot, int &cls) {
-    s = prev_start(cv.Sk, lane, r);
-    const int e = next_start(cv.Sk, lane, r, cv.nv);
-    if (e >= cv.nv) {
-        s = cv.last_s;
-        tot = cv.last_tot;
-        cls = cv.last_cls;
-        return;
-    }
-    if (s < 0) {  // began in an earlier chunk, ends in this one
-        tot = 0;
-        cls = cv.prev_cls;
-        return;
-    }
-    tot = e - s;
-    cls = tot <= 32 ? kClsDirect : kClsMma;
+__device__ __forceinline__ ChunkScan chunk_scans(uint32_t Sk, int lane) {
+    ChunkScan c;
+    c.ls = Sk ? 32 * lane + 31 - __clz(static_cast<int>(Sk)) : -1;
+    const int fs = Sk ? 32 * lane + __ffs(static_cast<int>(Sk)) - 1 : INT_MAX;
+    const int pmax = scan_max_up(c.ls, lane);
+    const int smin = scan_min_down(fs, lane);
+    c.pmax_ex = __shfl_up_sync(kFull, pmax, 1);
+    if (lane == 0) c.pmax_ex = -1;
+    c.smin_ex = __shfl_down_sync(kFull, smin, 1);
+    if (lane == 31) c.smin_ex = INT_MAX;
+    c.last_s = __shfl_sync(kFull, pmax, 31);
+    return c;
 }
 
-// A DIRECT group that reaches past its first block: its rows [s, s + tot)
-// of the chunk (rows from 512 on are the next chunk's first rows).
-__device__ __forceinline__ void direct_group(const PartMmaParams &p, const ChunkView &cv, uint32_t g, int s,
-                                             int tot) {
-    const int lane = threadIdx.x & 31;
-    const int r = s + lane;
-    const bool in = lane < tot;
-    ulonglong2 rc = make_ulonglong2(0ull, 0ull);
-    if (in) rc = r < kChunk ? cv.rec_s[r] : cv.rec_n[r - kChunk];
-    const uint64_t mask = rc.x;
-    const long long v = (in && p.has_col) ? static_cast<long long>(rc.y) : 0ll;
-    const bool live = in && !drop_row(p.in, mask);
-    const uint32_t T = warp_transpose(live ? static_cast<uint32_t>(mask) : 0u, lane);
-    const uint32_t T2 = p.bal ? 0u : warp_transpose(live ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
-    group_results(p, g, T, T2, __ballot_sync(kFull, live), v);
+__device__ __forceinline__ void block_classes(uint32_t Sk, int lane, int nv, const ChunkScan &c, int last_cls,
+                                              int prev_cls, int &cls_f, int &cls_l) {
+    const uint32_t after0 = Sk & ~1u;
+    const int sF = (Sk & 1u) ? 32 * lane : c.pmax_ex;
+    const int eF = after0 ? 32 * lane + __ffs(static_cast<int>(after0)) - 1 : min(c.smin_ex, nv);
+    const int sL = after0 ? c.ls : sF;
+    const int eL = min(c.smin_ex, nv);
+    auto cls = [&](int s0, int e0) {
+        if (e0 >= nv) return last_cls;
+        if (s0 < 0) return prev_cls;
+        return e0 - s0 <= 32 ? static_cast<int>(kClsSmall) : static_cast<int>(kClsMma);
+    };
+    cls_f = cls(sF, eF);
+    cls_l = cls(sL, eL);
 }
 
 // One 32-row block of a chunk on its producer warp: operands and pair records
 // of its MMA runs (the block's first and last run, when their groups are
-// MMA-class), the DIRECT groups that begin in it.
-__device__ __forceinline__ void produce_block(const PartMmaParams &p, const ChunkView &cv, int b, uint32_t a_stage,
-                                              uint32_t b_stage, PairRec *pairs) {
+// MMA-class; a group of more than 32 rows always holds one of them).
+// Returns the valid pairs: bit 0 = pair 2b, bit 1 = pair 2b + 1.
+__device__ __forceinline__ uint32_t produce_block(const PartMmaParams &p, const ulonglong2 *rec_s,
+                                                  const uint32_t *gid_s, int nv, int b, int cls_f, int cls_l,
+                                                  uint32_t a_stage, uint32_t b_stage, PairRec *pairs) {
     const int lane = threadIdx.x & 31;
     const int ri = 32 * b + lane;  // row within the chunk
-    const bool valid = ri < cv.nv;
-    const uint32_t gid = valid ? cv.gid_s[ri] : kNone;
-    const ulonglong2 rc = cv.rec_s[ri];
+    const bool valid = ri < nv;
+    const uint32_t VB = __ballot_sync(kFull, valid);
+    if (VB == 0) return 0u;
+    const uint32_t gid = valid ? gid_s[ri] : kNone;
+    const int last = 31 - __clz(static_cast<int>(VB));
+    const uint32_t g_first = __shfl_sync(kFull, gid, 0), g_lastb = __shfl_sync(kFull, gid, last);
+    const bool two = g_first != g_lastb;
+    const uint32_t mmaF = cls_f == kClsMma ? __ballot_sync(kFull, valid && gid == g_first) : 0u;
+    const uint32_t mmaL = (two && cls_l == kClsMma) ? __ballot_sync(kFull, valid && gid == g_lastb) : 0u;
+    if (!(mmaF | mmaL)) return 0u;
+    const uint32_t me = 1u << lane;
+    const ulonglong2 rc = rec_s[ri];
     const uint64_t mask = valid ? rc.x : 0ull;
     const long long v = (valid && p.has_col) ? static_cast<long long>(rc.y) : 0ll;
     const bool live = valid && !drop_row(p.in, mask);
-    const uint32_t VB = __ballot_sync(kFull, valid);
-    PairRec &p0 = pairs[2 * b], &p1 = pairs[2 * b + 1];
-    if (VB == 0) {
-        if (lane == 0) {
-            p0.valid = 0;
-            p1.valid = 0;
-        }
-        return;
-    }
-    const int last = 31 - __clz(static_cast<int>(VB));
-    const uint32_t g_first = __shfl_sync(kFull, gid, 0), g_lastb = __shfl_sync(kFull, gid, last);
-    const uint32_t F = __ballot_sync(kFull, valid && gid == g_first);
-    const uint32_t Lr = __ballot_sync(kFull, valid && gid == g_lastb);
     const uint32_t LB = __ballot_sync(kFull, live);
-    const uint32_t me = 1u << lane;
-    int sF, tF, cF, sL, tL, cL;
-    group_at(cv, lane, 32 * b, sF, tF, cF);
-    if (Lr == F) {
-        sL = sF;
-        tL = tF;
-        cL = cF;
-    } else {
-        group_at(cv, lane, 32 * b + last, sL, tL, cL);
-    }
-    const int b0 = 32 * b, b1 = b0 + 32;
-    const bool two = Lr != F;
-    // DIRECT groups wholly inside the block share one transpose
-    const bool f_inside = cF == kClsDirect && sF >= b0 && sF + tF <= b1;
-    const bool l_inside = two && cL == kClsDirect && sL >= b0 && sL + tL <= b1;
-    uint32_t I = VB & ~(F | Lr);
-    if (f_inside) I |= F;
-    if (l_inside) I |= Lr;
-    // MMA runs: A world bytes of their rows, one B copy each
-    const uint32_t mmaF = cF == kClsMma ? F : 0u;
-    const uint32_t mmaL = (two && cL == kClsMma) ? Lr : 0u;
+    // A: world bytes of the MMA rows
     if ((mmaF | mmaL) & me) {
         const uint32_t a_row = a_stage + (static_cast<uint32_t>(ri) >> 3) * 512 + (ri & 7) * 16;
         const uint32_t x = static_cast<uint32_t>(mask);
-        sts128(a_row, world_bytes(x, 0), world_bytes(x, 1), world_bytes(x, 2), world_bytes(x, 3));
-        sts128(a_row + 128, world_bytes(x, 4), world_bytes(x, 5), world_bytes(x, 6), world_bytes(x, 7));
+        sts128_unordered(a_row, world_bytes(x, 0), world_bytes(x, 1), world_bytes(x, 2), world_bytes(x, 3));
+        sts128_unordered(a_row + 128, world_bytes(x, 4), world_bytes(x, 5), world_bytes(x, 6), world_bytes(x, 7));
         if (!p.bal) {
             const uint32_t y = static_cast<uint32_t>(mask >> 32);
-            sts128(a_row + 256, world_bytes(y, 0), world_bytes(y, 1), world_bytes(y, 2), world_bytes(y, 3));
-            sts128(a_row + 384, world_bytes(y, 4), world_bytes(y, 5), world_bytes(y, 6), world_bytes(y, 7));
+            sts128_unordered(a_row + 256, world_bytes(y, 0), world_bytes(y, 1), world_bytes(y, 2), world_bytes(y, 3));
+            sts128_unordered(a_row + 384, world_bytes(y, 4), world_bytes(y, 5), world_bytes(y, 6), world_bytes(y, 7));
         }
     }
+    // B: one copy per MMA run, digits chosen per run
+    uint32_t out = 0;
 #pragma unroll
     for (int e = 0; e < 2; e++) {
         const uint32_t R = e == 0 ? mmaF : mmaL;
-        PairRec &pr = e == 0 ? p0 : p1;
-        if (!R) {
-            if (lane == 0) pr.valid = 0;
-            continue;
-        }
+        if (!R) continue;
         const bool member = (R & me) && live;
-        const unsigned long long mg = member ? static_cast<unsigned long long>(v ^ (v >> 63)) : 0ull;
-        const uint32_t mh = __reduce_or_sync(kFull, static_cast<uint32_t>(mg >> 32));
-        const uint32_t ml = __reduce_or_sync(kFull, static_cast<uint32_t>(mg));
-        const bool neg = __any_sync(kFull, member && v < 0);
-        const int bits = mh ? 64 - __clz(static_cast<int>(mh)) : (ml ? 32 - __clz(static_cast<int>(ml)) : 0);
-        const int need = neg ? (bits + 4) / 4 : (bits + 3) / 4;
+        // 16 digits, the top one signed: every int64 value, no per-run digit count
         const uint32_t b_pair = b_stage + static_cast<uint32_t>(2 * b + e) * kPairBytes;
-        int nfeat;
-        if (need <= 12) {
-            pair_features<12>(b_pair, lane, member, v, neg);
-            nfeat = Features<1, 12>::kN;
-        } else {
-            pair_features<16>(b_pair, lane, member, v, neg);
-            nfeat = Features<1, 16>::kN;
-        }
+        pair_features<16>(b_pair, lane, member, v, true);
+        constexpr int nfeat = Features<1, 16>::kN;
         if (lane == 0) {
+            PairRec &pr = pairs[2 * b + e];
             pr.gid = e == 0 ? g_first : g_lastb;
             pr.n = static_cast<uint16_t>(__popc(R & LB));
             pr.valid = 1;
             pr.nfeat = static_cast<uint8_t>(nfeat);
         }
+        out |= 1u << e;
     }
-    // DIRECT groups that begin in this block and reach past it
-    if (cF == kClsDirect && sF >= b0 && !f_inside) direct_group(p, cv, g_first, sF, tF);
-    if (two && cL == kClsDirect && sL >= b0 && !l_inside) direct_group(p, cv, g_lastb, sL, tL);
-    // DIRECT groups inside the block: lane j = world j (and j + 32)
-    if (!I) return;
-    const uint32_t T = warp_transpose(live ? static_cast<uint32_t>(mask) : 0u, lane);
-    const uint32_t T2 = p.bal ? 0u : warp_transpose(live ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
-    while (I) {
-        const uint32_t g = __shfl_sync(kFull, gid, __ffs(I) - 1);
-        const uint32_t R = __ballot_sync(kFull, gid == g) & I;
-        I &= ~R;
-        group_results(p, g, T, T2, R & LB, v);
-    }
+    return out;
 }
 
 // One tensor-memory slot's accumulator rows of this warp's lane quadrant as
 // integer digit totals (units of 2^-18: exact below 2^24).
 __device__ __forceinline__ void read_slot(uint32_t taddr, long long (&d)[kFeat]) {
-    uint32_t r[32];
+    static_assert(kFeat == 20, "columns 0-15 and 16-19");
+    uint32_t r[kFeat];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19])
+                 : "r"(taddr + 16));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int f = 0; f < kFeat; f++) d[f] = __float2ll_rn(__uint_as_float(r[f]) * 262144.0f);
@@ -488,17 +472,18 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
     if (tid == 0) {
         for (int r = 0; r < kRawStages; r++) {
             mbar_init(&sh.raw_full[r], 1);
-            mbar_init(&sh.raw_empty[r], kProdWarps);
+            mbar_init(&sh.raw_empty[r], kProdWarps + 1);  // the producers and the classifier
+            mbar_init(&sh.cls_full[r], 1);
         }
         for (int s = 0; s < kOpStages; s++) {
             mbar_init(&sh.full[s], kProdWarps);
-            mbar_init(&sh.empty[s], 1);
+            mbar_init(&sh.empty[s], kIssuers);
         }
         for (int k = 0; k < kSlots; k++) {
-            mbar_init(&sh.done[k], 2);
+            mbar_init(&sh.done[k], kIssuers + 1);
             mbar_init(&sh.freeb[k], 4);
         }
-        mbar_init(&sh.drain, 1);
+        mbar_init(&sh.drain, kIssuers);
         asm volatile("fence.mbarrier_init.release.cluster;");
         sh.abort_flag = 0;
         const uint32_t G = p.in.n_groups;
@@ -507,11 +492,18 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         const uint64_t hi = min(lo + p.rows_per_cta, kept);
         sh.lo = static_cast<uint32_t>(lo);
         sh.hi = static_cast<uint32_t>(hi);
-        sh.split_lo = (lo < hi && lo > 0 && p.sgid[lo - 1] == p.sgid[lo]) ? p.sgid[lo] : kNone;
-        sh.split_hi = (lo < hi && hi < kept && p.sgid[hi - 1] == p.sgid[hi]) ? p.sgid[hi - 1] : kNone;
-        // chunk 0 sees the group crossing the left edge as an MMA group begun earlier
-        sh.prev_gid[1] = sh.split_lo;
-        sh.prev_cls[1] = kClsMma;
+        // groups crossing the range's edges: partial records when they are
+        // tensor-core groups (more than 32 rows in all); chunk 0 sees the one
+        // crossing the left edge as a group begun earlier
+        const uint32_t g_lo = lo < hi ? p.sgid[lo] : kNone;
+        const bool cont_lo = lo < hi && lo > 0 && p.sgid[lo - 1] == g_lo;
+        const bool big_lo = cont_lo && p.pcnt[g_lo] > 32;
+        sh.split_lo = big_lo ? g_lo : kNone;
+        sh.prev_gid0 = cont_lo ? g_lo : kNone;
+        sh.prev_cls0 = (cont_lo && !big_lo) ? kClsSkip : kClsMma;
+        const uint32_t g_hi = lo < hi ? p.sgid[hi - 1] : kNone;
+        const bool cont_hi = lo < hi && hi < kept && p.sgid[hi] == g_hi;
+        sh.split_hi = (cont_hi && p.pcnt[g_hi] > 32) ? g_hi : kNone;
     }
     if (warp == kEpiWarp0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_slot)),
@@ -545,91 +537,120 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
     volatile int *abort_v = &sh.abort_flag;
 
     if (warp < kProdWarps) {
-        // ---------------- producers: blocks warp and warp + 8 ----------------
-        // Per chunk: one thread waits for the chunk (and the operand stage),
-        // every warp writes its blocks' start bits, one thread waits for the
-        // next chunk when more rows follow (the chunk's last group may end
-        // there), then every warp lays out its blocks.  Both go/no-go
-        // decisions are read by all producer warps after a barrier.
+        // ---------------- producers: block warp (+ 16 bb) of every chunk ----------------
+        // Per chunk: wait for its classes and the operand stage, lay out the
+        // block's tensor-core runs, arrive.  No barrier among the producers.
         for (uint32_t i = 0; i < n_chunks; i++) {
-            const int r = static_cast<int>(i % kRawStages), s = static_cast<int>(i & 1), par = s;
+            const int r = static_cast<int>(i % kRawStages), s = static_cast<int>(i % kOpStages);
             const uint32_t c0 = lo + i * kChunk;
             const int nv = static_cast<int>(min(static_cast<uint32_t>(kChunk), hi - c0));
-            const bool more = c0 + kChunk < hi;
-            if (tid == 0) {
-                bool ok = !*abort_v && mbar_wait(&sh.raw_full[r], (i / kRawStages) & 1, p.wait_ns);
-                if (ok && i >= kOpStages) ok = !*abort_v && mbar_wait(&sh.empty[s], ((i >> 1) - 1) & 1, p.wait_ns);
+            int ok = 1;
+            if (lane == 0) {
+                ok = !*abort_v && mbar_wait(&sh.cls_full[r], (i / kRawStages) & 1, p.wait_ns);
+                // the bulk copy's own completion as well (already complete: one try)
+                if (ok) ok = !*abort_v && mbar_wait(&sh.raw_full[r], (i / kRawStages) & 1, p.wait_ns);
+                if (ok && i >= kOpStages)
+                    ok = !*abort_v && mbar_wait(&sh.empty[s], ((i / kOpStages) - 1) & 1, p.wait_ns);
                 if (!ok) *abort_v = 1;
-                sh.prod_go = ok;
             }
-            producers_sync();
-            if (!*reinterpret_cast<volatile int *>(&sh.prod_go)) break;
+            ok = __shfl_sync(kFull, ok, 0);
+            if (!ok) break;
             const unsigned char *raw = smem + r * kRawBytes;
+            const ulonglong2 *rec_s = reinterpret_cast<const ulonglong2 *>(raw);
             const uint32_t *gid_s = reinterpret_cast<const uint32_t *>(raw + kRawRecBytes);
-#pragma unroll
-            for (int bb = 0; bb < 2; bb++) {
-                const int b = warp + kProdWarps * bb;
-                const int ri = 32 * b + lane;
-                const bool valid = ri < nv;
-                const bool st = valid && (ri == 0 || gid_s[ri] != gid_s[ri - 1]);
-                const uint32_t bits = __ballot_sync(kFull, st);
-                if (lane == 0) sh.sbits[par][b] = bits;
-            }
-            if (tid == 0) {
-                const uint32_t rn = (i + 1) % kRawStages;
-                bool ok = !more || (!*abort_v && mbar_wait(&sh.raw_full[rn], ((i + 1) / kRawStages) & 1, p.wait_ns));
-                if (!ok) *abort_v = 1;
-                sh.prod_go = ok;
-            }
-            producers_sync();
-            if (!*reinterpret_cast<volatile int *>(&sh.prod_go)) break;
-            ChunkView cv;
-            cv.rec_s = reinterpret_cast<const ulonglong2 *>(raw);
-            const unsigned char *raw_n = smem + ((i + 1) % kRawStages) * kRawBytes;
-            cv.rec_n = reinterpret_cast<const ulonglong2 *>(raw_n);
-            cv.gid_s = gid_s;
-            cv.nv = nv;
-            const uint32_t pg = sh.prev_gid[par ^ 1];
-            cv.prev_cls = sh.prev_cls[par ^ 1];
-            // row 0 begins a group unless it continues the previous chunk's last one
-            uint32_t Sk = lane < kBlocks ? sh.sbits[par][lane] : 0u;
-            if (lane == 0 && gid_s[0] == pg) Sk &= ~1u;
-            cv.Sk = Sk;
-            // the chunk's last group, looked up in the next chunk when it reaches the end
-            const uint32_t g_last = gid_s[nv - 1];
-            cv.last_s = prev_start(Sk, lane, nv - 1);
-            if (cv.last_s < 0) {
-                cv.last_tot = 0;
-                cv.last_cls = cv.prev_cls;
-            } else {
-                cv.last_tot = nv - cv.last_s;
-                if (!more) {
-                    cv.last_cls = (g_last == sh.split_hi || cv.last_tot > 32) ? kClsMma : kClsDirect;
-                } else if (cv.last_tot > 32) {
-                    cv.last_cls = kClsMma;
-                } else {
-                    const uint32_t *gid_n = reinterpret_cast<const uint32_t *>(raw_n + kRawRecBytes);
-                    const uint32_t rows_n = min(static_cast<uint32_t>(kChunk), hi - (c0 + kChunk));
-                    const uint32_t gn = static_cast<uint32_t>(lane) < rows_n ? gid_n[lane] : kNone;
-                    const uint32_t eq = __ballot_sync(kFull, gn == g_last);
-                    const int ext = ~eq ? __ffs(~eq) - 1 : 32;
-                    cv.last_tot += ext;
-                    cv.last_cls = (cv.last_tot > 32 || (g_last == sh.split_hi && c0 + kChunk + ext == hi))
-                                      ? kClsMma
-                                      : kClsDirect;
-                }
-            }
-            if (tid == 0) {
-                sh.prev_gid[par] = g_last;
-                sh.prev_cls[par] = cv.last_cls == kClsDirect ? kClsSkip : cv.last_cls;
-            }
             const uint32_t a_stage = op_base + s * kOpBytes, b_stage = a_stage + kABytes;
-            produce_block(p, cv, warp, a_stage, b_stage, sh.pairs[s]);
-            produce_block(p, cv, warp + kProdWarps, a_stage, b_stage, sh.pairs[s]);
+            uint32_t pv = 0;
+#pragma unroll
+            for (int bb = 0; bb < kBlocksPerWarp; bb++) {
+                const int b = warp + kProdWarps * bb;
+                const uint32_t cc = sh.ccls[r][b];
+                pv |= produce_block(p, rec_s, gid_s, nv, b, static_cast<int>(cc & 3u), static_cast<int>(cc >> 2),
+                                    a_stage, b_stage, sh.pairs[s])
+                      << (2 * bb);
+            }
+            if (lane == 0) sh.pvalid[s][warp] = static_cast<uint8_t>(pv);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&sh.full[s]);
+                mbar_arrive(&sh.raw_empty[r]);
+            }
+        }
+    } else if (warp == kClsWarp) {
+        // ---------------- classifier: the chunk's groups, one chunk ahead ----------------
+        // Group start bits of the chunk's rows (lane b ends with block b's
+        // word), then every block's edge classes in one pass; the chunk's last
+        // group is measured into the next chunk (already landed) when more
+        // rows follow.  The previous chunk's last group and its class stay in
+        // registers.
+        uint32_t prev_gid = sh.prev_gid0;
+        int prev_cls = sh.prev_cls0;
+        for (uint32_t i = 0; i < n_chunks; i++) {
+            const int r = static_cast<int>(i % kRawStages);
+            const uint32_t rn = (i + 1) % kRawStages;
+            const uint32_t c0 = lo + i * kChunk;
+            const int nv = static_cast<int>(min(static_cast<uint32_t>(kChunk), hi - c0));
+            const bool more = c0 + kChunk < hi;
+            int ok = 1;
+            if (lane == 0) {
+                ok = !*abort_v && mbar_wait(&sh.raw_full[r], (i / kRawStages) & 1, p.wait_ns);
+                if (ok && more) ok = !*abort_v && mbar_wait(&sh.raw_full[rn], ((i + 1) / kRawStages) & 1, p.wait_ns);
+                if (!ok) *abort_v = 1;
+            }
+            ok = __shfl_sync(kFull, ok, 0);
+            if (!ok) break;
+            const uint32_t *gid_s = reinterpret_cast<const uint32_t *>(smem + r * kRawBytes + kRawRecBytes);
+            const uint32_t g_last = gid_s[nv - 1];
+            if (gid_s[0] == prev_gid && g_last == prev_gid) {
+                // the whole chunk continues the previous chunk's group (rows are
+                // in group order): every block's class is that group's
+                if (lane < kBlocks) sh.ccls[r][lane] = static_cast<uint8_t>(prev_cls | (prev_cls << 2));
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&sh.cls_full[r]);
+                    mbar_arrive(&sh.raw_empty[r]);
+                }
+                continue;
+            }
+            uint32_t Sk = 0;
+#pragma unroll 4
+            for (int b = 0; b < kBlocks; b++) {
+                const int ri = 32 * b + lane;
+                const bool valid = ri < nv;
+                const uint32_t g = valid ? gid_s[ri] : kNone;
+                const uint32_t gp = ri == 0 ? prev_gid : (valid ? gid_s[ri - 1] : kNone);
+                const uint32_t w = __ballot_sync(kFull, valid && g != gp);
+                if (lane == b) Sk = w;
+            }
+            const ChunkScan cs = chunk_scans(Sk, lane);
+            int last_cls;
+            if (cs.last_s < 0) {
+                last_cls = prev_cls;
+            } else {
+                int tot = nv - cs.last_s;
+                if (!more) {
+                    last_cls = (g_last == sh.split_hi || tot > 32) ? kClsMma : kClsSmall;
+                } else if (tot > 32) {
+                    last_cls = kClsMma;
+                } else {
+                    const uint32_t *gid_n =
+                        reinterpret_cast<const uint32_t *>(smem + rn * kRawBytes + kRawRecBytes);
+                    const uint32_t rows_n = min(static_cast<uint32_t>(kChunk), hi - (c0 + kChunk));
+                    const uint32_t gn = static_cast<uint32_t>(lane) < rows_n ? gid_n[lane] : kNone;
+                    const uint32_t eq = __ballot_sync(kFull, gn == g_last);
+                    const int ext = ~eq ? __ffs(static_cast<int>(~eq)) - 1 : 32;
+                    tot += ext;
+                    last_cls = (tot > 32 || (g_last == sh.split_hi && c0 + kChunk + ext == hi)) ? kClsMma : kClsSmall;
+                }
+            }
+            int cls_f, cls_l;
+            block_classes(Sk, lane, nv, cs, last_cls, prev_cls, cls_f, cls_l);
+            if (lane < kBlocks) sh.ccls[r][lane] = static_cast<uint8_t>(cls_f | (cls_l << 2));
+            prev_gid = g_last;
+            prev_cls = last_cls == kClsSmall ? kClsSkip : last_cls;
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&sh.cls_full[r]);
                 mbar_arrive(&sh.raw_empty[r]);
             }
         }
@@ -657,80 +678,139 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 if (!mbar_wait(&sh.raw_full[i % kRawStages], (i / kRawStages) & 1, kWaitNs)) *abort_v = 1;
         }
         __syncwarp();
-    } else if (warp == kMmaWarp) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
+    } else if (warp >= kMmaWarp0 && warp < kMmaWarp0 + kIssuers) {
+        // ---------------- MMA issuers ----------------
+        // Every issuer walks the same pairs and numbers the groups alike;
+        // issuer w issues a group's MMAs w, w + kIssuers, ... into accumulator
+        // w of its slot.  Completion: a commit from every issuer (the chunk's
+        // stage, a group's slot, the final drain); issuer 0 also records the
+        // group and arrives once more on its slot.
+        const int iw = warp - kMmaWarp0;
+        // The chunk's pair records are read lane-parallel (lane p: pair p)
+        // and reach the issuing lane by shuffles: no shared-memory load sits
+        // between two MMAs (a tcgen05.mma from one thread costs about 100
+        // cycles of issue; a dependent load per MMA more than doubled that).
+        {
             int k = -1;  // ordinal of the current group
-            uint32_t cur = kNone, n_acc = 0;
-            bool gave_up = false;
+            uint32_t cur = kNone, n_acc = 0, n_mma = 0;
+            int gave_up = 0;
             auto close = [&](int kk) {
-                OrdInfo &oi = sh.info[kk % kInfo];
-                oi.gid = cur;
-                oi.n = n_acc;
-                oi.end = 0;
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&sh.done[kk % kSlots])));
-                mbar_arrive(&sh.done[kk % kSlots]);
+                if (lane == 0) {
+                    if (iw == 0) {
+                        OrdInfo &oi = sh.info[kk % kInfo];
+                        oi.gid = cur;
+                        oi.n = n_acc;
+                        oi.end = 0;
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&sh.done[kk % kSlots])));
+                    if (iw == 0) mbar_arrive(&sh.done[kk % kSlots]);
+                }
             };
             // the slot of ordinal kk is free once the epilogue has emptied ordinal kk - kSlots
             auto take_slot = [&](int kk) -> bool {
                 if (kk < kSlots) return true;
-                if (*abort_v || !mbar_wait(&sh.freeb[kk % kSlots], ((kk / kSlots) - 1) & 1, p.wait_ns)) return false;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                return true;
+                int ok = 1;
+                if (lane == 0) {
+                    ok = !*abort_v && mbar_wait(&sh.freeb[kk % kSlots], ((kk / kSlots) - 1) & 1, p.wait_ns);
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                }
+                return __shfl_sync(kFull, ok, 0) != 0;
             };
             for (uint32_t i = 0; i < n_chunks && !gave_up; i++) {
-                const int s = static_cast<int>(i & 1);
-                if (*abort_v || !mbar_wait(&sh.full[s], (i >> 1) & 1, p.wait_ns)) {
-                    gave_up = true;
+                const int s = static_cast<int>(i % kOpStages);
+                int ok = 1;
+                if (lane == 0) ok = !*abort_v && mbar_wait(&sh.full[s], (i / kOpStages) & 1, p.wait_ns);
+                if (!__shfl_sync(kFull, ok, 0)) {
+                    gave_up = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t a_stage = op_base + s * kOpBytes, b_stage = a_stage + kABytes;
-                for (int pi = 0; pi < kPairs; pi++) {
-                    const PairRec pr = sh.pairs[s][pi];
-                    if (!pr.valid) continue;
-                    if (pr.gid != cur) {
+                // lane p: pair p's validity, record and operand descriptors
+                const int wq = lane >> 1, bq = wq % kProdWarps, bbq = wq / kProdWarps;
+                const uint32_t nib = sh.pvalid[s][bq];
+                const bool pvld = (nib >> (2 * bbq + (lane & 1))) & 1u;
+                const PairRec prl = sh.pairs[s][lane];
+                const uint32_t pm = __ballot_sync(kFull, pvld);
+                const uint32_t gid_l = pvld ? prl.gid : kNone;
+                const uint32_t n_l = pvld ? prl.n : 0u;
+                const uint64_t da_l = smem_desc(a_stage + static_cast<uint32_t>(lane >> 1) * 2048, 512, 128);
+                const uint64_t db_l = smem_desc(b_stage + static_cast<uint32_t>(lane) * kPairBytes,
+                                                (static_cast<uint32_t>(prl.nfeat) / 16) * 128, 128);
+                const uint32_t id_l = instr_desc<64>(prl.nfeat);
+                // group starts: a valid pair whose group differs from the previous valid pair's
+                int pv_idx = pvld ? lane : -1;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, pv_idx, o);
+                    if (lane >= o) pv_idx = max(pv_idx, y);
+                }
+                int prev_valid = __shfl_up_sync(kFull, pv_idx, 1);
+                if (lane == 0) prev_valid = -1;
+                const uint32_t gprev = __shfl_sync(kFull, gid_l, prev_valid < 0 ? 0 : prev_valid);
+                const uint32_t ng = __ballot_sync(kFull, pvld && gid_l != (prev_valid < 0 ? cur : gprev));
+                // segments of one group, issued back to back (shuffles and one MMA each)
+                for (uint32_t rest = pm; rest;) {
+                    const int p0 = __ffs(static_cast<int>(rest)) - 1;
+                    if ((ng >> p0) & 1u) {
                         if (k >= 0) close(k);
                         k++;
                         if (!take_slot(k)) {
-                            gave_up = true;
+                            gave_up = 1;
                             break;
                         }
-                        cur = pr.gid;
+                        cur = __shfl_sync(kFull, gid_l, p0);
                         n_acc = 0;
+                        n_mma = 0;
                     }
-                    n_acc += pr.n;
-                    const uint64_t da = smem_desc(a_stage + static_cast<uint32_t>(pi >> 1) * 2048, 512, 128);
-                    const uint64_t db = smem_desc(b_stage + static_cast<uint32_t>(pi) * kPairBytes,
-                                                  (static_cast<uint32_t>(pr.nfeat) / 16) * 128, 128);
-                    mma_f8(tmem + static_cast<uint32_t>(k % kSlots) * kAlloc, da, db, instr_desc<64>(pr.nfeat));
+                    // the segment: valid pairs from p0 up to the next group start
+                    const uint32_t after = ng & ~((2u << p0) - 1u) & ~(p0 == 31 ? 0xFFFFFFFFu : 0u);
+                    const uint32_t seg = after ? (rest & ((1u << (__ffs(static_cast<int>(after)) - 1)) - 1u)) : rest;
+                    rest &= ~seg;
+                    n_acc += __reduce_add_sync(kFull, ((seg >> lane) & 1u) ? n_l : 0u);
+                    const uint32_t dacc = tmem + static_cast<uint32_t>(k % kSlots) * (kAlloc * kSub) + iw * kAlloc;
+                    for (uint32_t q = seg; q; q &= q - 1) {
+                        const int pi = __ffs(static_cast<int>(q)) - 1;
+                        const uint64_t da = __shfl_sync(kFull, da_l, pi);
+                        const uint64_t db = __shfl_sync(kFull, db_l, pi);
+                        const uint32_t id = __shfl_sync(kFull, id_l, pi);
+                        if (lane == 0 && n_mma % kIssuers == static_cast<uint32_t>(iw)) mma_f8(dacc, da, db, id);
+                        n_mma++;
+                    }
                 }
                 if (gave_up) break;
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&sh.empty[s])));
+                if (lane == 0)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&sh.empty[s])));
             }
             if (gave_up) {
-                *abort_v = 1;
+                if (lane == 0) *abort_v = 1;
             } else {
                 if (k >= 0) close(k);
                 // end marker: ordinal k + 1 (its slot's previous group emptied first)
                 const int ke = k + 1;
                 if (take_slot(ke)) {
-                    OrdInfo &oi = sh.info[ke % kInfo];
-                    oi.gid = kNone;
-                    oi.n = 0;
-                    oi.end = 1;
-                    mbar_arrive(&sh.done[ke % kSlots]);
-                    mbar_arrive(&sh.done[ke % kSlots]);
-                } else {
+                    if (lane == 0) {
+                        if (iw == 0) {
+                            OrdInfo &oi = sh.info[ke % kInfo];
+                            oi.gid = kNone;
+                            oi.n = 0;
+                            oi.end = 1;
+                            mbar_arrive(&sh.done[ke % kSlots]);
+                        }
+                        mbar_arrive(&sh.done[ke % kSlots]);
+                    }
+                } else if (lane == 0) {
                     *abort_v = 1;
                 }
             }
             // every MMA issued is complete before tensor memory is read or freed
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&sh.drain)));
-            if (!mbar_wait(&sh.drain, 0, kWaitNs)) *abort_v = 1;
+            if (lane == 0) {
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&sh.drain)));
+                if (!mbar_wait(&sh.drain, 0, kWaitNs)) *abort_v = 1;
+            }
         }
         __syncwarp();
     } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
@@ -750,10 +830,20 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             if (go != 1) break;
             const OrdInfo oi = sh.info[k % kInfo];
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // the slot's kSub accumulators, added (each below 2^24: their sum
+            // is a per-CTA total, below 2^24 as well)
             long long d[kFeat];
-            const uint32_t taddr = tmem + lane_base + static_cast<uint32_t>(slot) * kAlloc;
+            const uint32_t taddr = tmem + lane_base + static_cast<uint32_t>(slot) * (kAlloc * kSub);
             read_slot(taddr, d);
             zero_slot(taddr);
+#pragma unroll
+            for (int u = 1; u < kSub; u++) {
+                long long du[kFeat];
+                read_slot(taddr + u * kAlloc, du);
+                zero_slot(taddr + u * kAlloc);
+#pragma unroll
+                for (int f = 0; f < kFeat; f++) d[f] += du[f];
+            }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.freeb[slot]);
@@ -763,6 +853,13 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 for (int f = 0; f < kFeat; f++) sh.tot[f] = d[f];
             }
             epi_sync();
+            __int128 tot_sum = 0;
+            if (p.bal && !split) {
+                long long td[kFeat];
+#pragma unroll
+                for (int f = 0; f < kFeat; f++) td[f] = sh.tot[f];
+                tot_sum = digits_to_sum(td);
+            }
             unsigned long long bits = 0;
             if (split) {
                 const int side = (k == 0 && oi.gid == sh.split_lo) ? 0 : 1;
@@ -778,14 +875,14 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 }
             } else if (lane < 16 && (!p.bal || q < 2)) {
                 const int w = world_of_row(m);
-                emit_world(p, oi.gid, w, static_cast<unsigned long long>(d[0]), digits_to_sum(d));
+                const __int128 sw = digits_to_sum(d);
+                emit_world(p, oi.gid, w, static_cast<unsigned long long>(d[0]), sw);
                 bits = (d[0] > 0 ? 1ull : 0ull) << w;
                 if (p.bal) {
-                    long long dc[kFeat];
-#pragma unroll
-                    for (int f = 0; f < kFeat; f++) dc[f] = sh.tot[f] - d[f];
-                    emit_world(p, oi.gid, w + 32, static_cast<unsigned long long>(dc[0]), digits_to_sum(dc));
-                    bits |= (dc[0] > 0 ? 1ull : 0ull) << (w + 32);
+                    // world w + 32 = the group total minus world w (the sum is linear in the digits)
+                    const long long c2 = sh.tot[0] - d[0];
+                    emit_world(p, oi.gid, w + 32, static_cast<unsigned long long>(c2), tot_sum - sw);
+                    bits |= (c2 > 0 ? 1ull : 0ull) << (w + 32);
                 }
             }
             const uint32_t o_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(bits));
@@ -841,13 +938,13 @@ __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartM
     unsigned long long bits = 0;
     if (!p.bal || m < 32) {
         const int w = world_of_row(m);
-        emit_world(p, g, w, static_cast<unsigned long long>(d[0]), digits_to_sum(d));
+        emit_world(p, g, w, static_cast<unsigned long long>(d[0]), digits_to_sum_wide(d));
         bits = (d[0] > 0 ? 1ull : 0ull) << w;
         if (p.bal) {
             long long dc[kFeat];
 #pragma unroll
             for (int f = 0; f < kFeat; f++) dc[f] = tot[f] - d[f];
-            emit_world(p, g, w + 32, static_cast<unsigned long long>(dc[0]), digits_to_sum(dc));
+            emit_world(p, g, w + 32, static_cast<unsigned long long>(dc[0]), digits_to_sum_wide(dc));
             bits |= (dc[0] > 0 ? 1ull : 0ull) << (w + 32);
         }
     }
@@ -861,14 +958,52 @@ __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartM
     }
 }
 
-// Groups without rows: zero results and metadata.
-__global__ void k_part_empty(const __grid_constant__ PartMmaParams p) {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= p.in.n_groups || p.pcnt[g] != 0) return;
-    for (int w = 0; w < kWorlds; w++) emit_world(p, g, w, 0ull, 0);
-    if (p.meta) {
-        p.meta[2 * static_cast<size_t>(g)] = 0;
-        p.meta[2 * static_cast<size_t>(g) + 1] = 0;
+// Groups of at most 32 rows (and groups without rows): warp w takes the 32
+// groups [32w, 32w + 32).  Lane l loads group 32w + l's row count and end in
+// the group order (one coalesced load each); the warp then walks its small
+// groups in order, the rows [end - n, end) of the next one loaded while the
+// current one is summed.  Lane j = world j (and j + 32).
+__global__ void __launch_bounds__(256) k_part_small(const __grid_constant__ PartMmaParams p) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t g0 = ((static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
+    const uint32_t G = p.in.n_groups;
+    if (g0 >= G) return;
+    const uint64_t gl = g0 + lane;
+    const bool in_g = gl < G;
+    const uint32_t cnt = in_g ? p.pcnt[gl] : 0xFFFFFFFFu;
+    const uint32_t end = in_g ? p.pend[gl] : 0u;
+    uint32_t todo = __ballot_sync(kFull, in_g && cnt <= 32);
+    auto fetch = [&](int j, ulonglong2 &rc, uint32_t &n) {
+        n = __shfl_sync(kFull, cnt, j);
+        const uint32_t e = __shfl_sync(kFull, end, j);
+        rc = make_ulonglong2(0ull, 0ull);
+        if (static_cast<uint32_t>(lane) < n) rc = p.rec[static_cast<uint64_t>(e) - n + lane];
+    };
+    if (!todo) return;
+    int j = __ffs(static_cast<int>(todo)) - 1;
+    todo &= todo - 1;
+    ulonglong2 rc;
+    uint32_t n;
+    fetch(j, rc, n);
+    for (;;) {
+        ulonglong2 rc_next = make_ulonglong2(0ull, 0ull);
+        uint32_t n_next = 0;
+        const int j_next = todo ? __ffs(static_cast<int>(todo)) - 1 : -1;
+        if (j_next >= 0) {
+            todo &= todo - 1;
+            fetch(j_next, rc_next, n_next);
+        }
+        const bool in = static_cast<uint32_t>(lane) < n;
+        const uint64_t mask = rc.x;
+        const long long v = (in && p.has_col) ? static_cast<long long>(rc.y) : 0ll;
+        const bool live = in && !drop_row(p.in, mask);
+        const uint32_t T = warp_transpose(live ? static_cast<uint32_t>(mask) : 0u, lane);
+        const uint32_t T2 = p.bal ? 0u : warp_transpose(live ? static_cast<uint32_t>(mask >> 32) : 0u, lane);
+        group_results(p, static_cast<uint32_t>(g0) + j, T, T2, __ballot_sync(kFull, live), v);
+        if (j_next < 0) break;
+        j = j_next;
+        rc = rc_next;
+        n = n_next;
     }
 }
 
@@ -909,6 +1044,7 @@ pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launc
     p.rec = static_cast<const ulonglong2 *>(a.rec);
     p.sgid = a.sgid;
     p.pcnt = a.pcnt;
+    p.pend = a.pend;
     p.rows_per_cta = part_rows_per_cta(a.in.n, a.n_sms);
     p.bal = !(a.in.in_flags & PAC_IN_MASKS) && a.in.hash_mode == PAC_HASH_BALANCED;
     p.has_col = 0;
@@ -930,7 +1066,9 @@ pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launc
     if (e == cudaSuccess) {
         k_part_mma<<<static_cast<unsigned>(grid), kThreadsP, kSmemP, stream>>>(p);
         k_part_merge<<<static_cast<unsigned>(2 * grid), 64, 0, stream>>>(p, static_cast<uint32_t>(2 * grid));
-        k_part_empty<<<(a.in.n_groups + 255) / 256, 256, 0, stream>>>(p);
+        // one warp per 32 groups, 8 warps per block
+        k_part_small<<<static_cast<unsigned>((static_cast<uint64_t>(a.in.n_groups) + 255) / 256), 256, 0,
+                       stream>>>(p);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

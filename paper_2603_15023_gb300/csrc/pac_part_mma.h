@@ -20,6 +20,7 @@ struct PartMmaArgs {
     const void *rec;             // [n] group-ordered 16-byte records {mask, value}
     const uint32_t *sgid;        // [n] group-ordered group ids, 16 bytes readable past the end
     const uint32_t *pcnt;        // [G + 2]: rows per group, [G] = rows kept
+    const uint32_t *pend;        // [G]: end of each group's rows (the scatter's cursors)
     const pac_agg_spec *specs;   // COUNT and exact int64 SUM/AVG of one column
     int n_specs;
     uint64_t *meta;              // [G][2] or null

@@ -84,6 +84,14 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
+// The same store with no compiler memory barrier: ordinary loads may be
+// scheduled across it.  For operand stores to shared memory that nothing in
+// the thread reads back; they keep their order relative to every other asm
+// volatile statement (the proxy fence that publishes them among them).
+__device__ __forceinline__ void sts128_unordered(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d));
+}
+
 // Operand word q (q < 8) of a 32-world block: bytes b = 0..3 are world bits
 // q + 8b, each 0x00 or 0x01.  So accumulator row 4q + b of the block holds
 // world q + 8b (world_of_row undoes this at read-back); two operations per
