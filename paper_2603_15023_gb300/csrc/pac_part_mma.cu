@@ -103,6 +103,8 @@ struct PairRec {
     uint16_t n;      // rows of the run that count (dropped rows excluded)
     uint8_t valid;
     uint8_t nfeat;   // N of the run's B copy (16 or 32)
+    unsigned long long sum_lo;  // balanced keys: the run's value total, 128-bit two's complement
+    long long sum_hi;
 };
 
 // A group of the CTA in MMA order (ordinal k at k % kInfo).
@@ -111,6 +113,8 @@ struct OrdInfo {
     uint32_t n;
     uint32_t end;    // 1: no more groups (the epilogue stops)
     uint32_t pad;
+    unsigned long long sum_lo;  // balanced keys: the group's value total in this CTA
+    long long sum_hi;
 };
 
 struct PartShared {
@@ -126,7 +130,6 @@ struct PartShared {
     uint32_t lo, hi;         // the CTA's rows [lo, hi)
     uint32_t split_lo;       // group crossing the CTA's left edge, or kNone
     uint32_t split_hi;       // group crossing its right edge, or kNone
-    int epi_go;
     uint64_t cls_full[kRawStages];   // classifier -> producers: the chunk in raw slot r is classified
     uint8_t ccls[kRawStages][kBlocks];  // per raw slot and block: first-row class | last-row class << 2
     uint8_t pvalid[kOpStages][kProdWarps];  // valid pairs of warp w: bits 2bb, 2bb + 1 = block w + 16 bb
@@ -134,8 +137,8 @@ struct PartShared {
     int prev_cls0;                   // ... and its class
     PairRec pairs[kOpStages][kPairs];
     OrdInfo info[kInfo];
-    long long tot[kFeat];            // balanced keys: the total row of the group being emitted
-    unsigned long long orw[4];       // per quadrant: worlds with a nonzero count
+    unsigned long long meta_or[kInfo];  // per group record: worlds with a nonzero count, ...
+    uint32_t meta_cnt[kInfo];           // ... and the epilogue warps that have added theirs
 };
 
 }  // namespace
@@ -143,6 +146,8 @@ struct PartShared {
 struct PartRec {
     uint32_t gid, used;
     unsigned long long n;
+    unsigned long long sum_lo;     // balanced keys: value total (128-bit two's complement)
+    long long sum_hi;
     long long d[kWorlds][kFeat];   // digit totals per accumulator row (units of 2^-18 folded out)
 };
 
@@ -178,10 +183,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                      smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
-}
-
-__device__ __forceinline__ void epi_sync() {
-    asm volatile("bar.sync 3, 128;" ::: "memory");
 }
 
 __device__ __forceinline__ bool fits_i64(__int128 v) {
@@ -245,6 +246,30 @@ __device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
         x = (lane & s) ? ((x & ~m) | ((o >> s) & m)) : ((x & m) | ((o << s) & ~m));
     }
     return x;
+}
+
+// Exact warp sum of one int64 per lane, by 16-bit pieces (each piece's sum
+// over 32 lanes stays below 2^21; the top piece is signed).
+__device__ __forceinline__ __int128 warp_sum_i64(long long x) {
+    const unsigned long long u = static_cast<unsigned long long>(x);
+    const uint32_t c0 = __reduce_add_sync(kFull, static_cast<uint32_t>(u & 0xFFFFull));
+    const uint32_t c1 = __reduce_add_sync(kFull, static_cast<uint32_t>((u >> 16) & 0xFFFFull));
+    const uint32_t c2 = __reduce_add_sync(kFull, static_cast<uint32_t>((u >> 32) & 0xFFFFull));
+    const int c3 = __reduce_add_sync(kFull, static_cast<int>(x >> 48));
+    return static_cast<__int128>(c0) + (static_cast<__int128>(c1) << 16) + (static_cast<__int128>(c2) << 32) +
+           (static_cast<__int128>(c3) << 48);
+}
+
+// The same for one int128 per lane (eight pieces, the top one signed).
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 x) {
+    const unsigned __int128 u = static_cast<unsigned __int128>(x);
+    __int128 t = 0;
+#pragma unroll
+    for (int c = 0; c < 7; c++)
+        t += static_cast<__int128>(__reduce_add_sync(kFull, static_cast<uint32_t>((u >> (16 * c)) & 0xFFFFu)))
+             << (16 * c);
+    t += static_cast<__int128>(__reduce_add_sync(kFull, static_cast<int>(x >> 112))) << 112;
+    return t;
 }
 
 // The features of one row in B copy `pair` (a 32-row region, rows by lane):
@@ -420,12 +445,20 @@ __device__ __forceinline__ uint32_t produce_block(const PartMmaParams &p, const 
         const uint32_t b_pair = b_stage + static_cast<uint32_t>(2 * b + e) * kPairBytes;
         pair_features<16>(b_pair, lane, member, v, true);
         constexpr int nfeat = Features<1, 16>::kN;
+        // balanced keys: the run's value total (the epilogue derives worlds
+        // j + 32 from it)
+        __int128 tr = 0;
+        if (p.bal) tr = warp_sum_i64(member ? v : 0ll);
+        const unsigned long long t_lo = static_cast<unsigned long long>(tr);
+        const long long t_hi = static_cast<long long>(tr >> 64);
         if (lane == 0) {
             PairRec &pr = pairs[2 * b + e];
             pr.gid = e == 0 ? g_first : g_lastb;
             pr.n = static_cast<uint16_t>(__popc(R & LB));
             pr.valid = 1;
             pr.nfeat = static_cast<uint8_t>(nfeat);
+            pr.sum_lo = t_lo;
+            pr.sum_hi = t_hi;
         }
         out |= 1u << e;
     }
@@ -481,7 +514,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         }
         for (int k = 0; k < kSlots; k++) {
             mbar_init(&sh.done[k], kIssuers + 1);
-            mbar_init(&sh.freeb[k], 4);
+            mbar_init(&sh.freeb[k], p.bal ? 2 : 4);  // the epilogue warps whose quadrants hold worlds
         }
         mbar_init(&sh.drain, kIssuers);
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -518,14 +551,17 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
         for (uint32_t c0 = 0; c0 < 512; c0 += 32) zero_slot(tmem + lane_base + c0);
     }
-    // A rows start as zeros, with the constant world byte of balanced keys:
-    // accumulator row 32 (upper half, first byte) counts every row, so it
-    // becomes the run's total
+    // A rows start as zeros (under balanced keys the upper half stays zero:
+    // worlds 32..63 come from the group totals)
     for (uint32_t i = static_cast<uint32_t>(tid); i < kOpStages * kChunk; i += blockDim.x) {
         const uint32_t st = i / kChunk, r = i % kChunk;
         const uint32_t a_row = op_base + st * kOpBytes + (r >> 3) * 512 + (r & 7) * 16;
 #pragma unroll
-        for (int k = 0; k < 4; k++) sts128(a_row + 128 * k, (p.bal && k == 2) ? 1u : 0u, 0u, 0u, 0u);
+        for (int k = 0; k < 4; k++) sts128(a_row + 128 * k, 0u, 0u, 0u, 0u);
+    }
+    for (int i = tid; i < kInfo; i += blockDim.x) {
+        sh.meta_or[i] = 0;
+        sh.meta_cnt[i] = 0;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -693,14 +729,18 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         {
             int k = -1;  // ordinal of the current group
             uint32_t cur = kNone, n_acc = 0, n_mma = 0;
+            __int128 s_part = 0;  // this lane's share of the group's value total (balanced keys)
             int gave_up = 0;
             auto close = [&](int kk) {
+                const __int128 st = p.bal ? warp_sum_i128(s_part) : static_cast<__int128>(0);
                 if (lane == 0) {
                     if (iw == 0) {
                         OrdInfo &oi = sh.info[kk % kInfo];
                         oi.gid = cur;
                         oi.n = n_acc;
                         oi.end = 0;
+                        oi.sum_lo = static_cast<unsigned long long>(st);
+                        oi.sum_hi = static_cast<long long>(st >> 64);
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&sh.done[kk % kSlots])));
@@ -735,6 +775,8 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 const uint32_t pm = __ballot_sync(kFull, pvld);
                 const uint32_t gid_l = pvld ? prl.gid : kNone;
                 const uint32_t n_l = pvld ? prl.n : 0u;
+                const unsigned long long slo_l = pvld ? prl.sum_lo : 0ull;
+                const long long shi_l = pvld ? prl.sum_hi : 0ll;
                 const uint64_t da_l = smem_desc(a_stage + static_cast<uint32_t>(lane >> 1) * 2048, 512, 128);
                 const uint64_t db_l = smem_desc(b_stage + static_cast<uint32_t>(lane) * kPairBytes,
                                                 (static_cast<uint32_t>(prl.nfeat) / 16) * 128, 128);
@@ -763,12 +805,15 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                         cur = __shfl_sync(kFull, gid_l, p0);
                         n_acc = 0;
                         n_mma = 0;
+                        s_part = 0;
                     }
                     // the segment: valid pairs from p0 up to the next group start
                     const uint32_t after = ng & ~((2u << p0) - 1u) & ~(p0 == 31 ? 0xFFFFFFFFu : 0u);
                     const uint32_t seg = after ? (rest & ((1u << (__ffs(static_cast<int>(after)) - 1)) - 1u)) : rest;
                     rest &= ~seg;
                     n_acc += __reduce_add_sync(kFull, ((seg >> lane) & 1u) ? n_l : 0u);
+                    if (p.bal && ((seg >> lane) & 1u))
+                        s_part += (static_cast<__int128>(shi_l) << 64) | static_cast<__int128>(slo_l);
                     const uint32_t dacc = tmem + static_cast<uint32_t>(k % kSlots) * (kAlloc * kSub) + iw * kAlloc;
                     for (uint32_t q = seg; q; q &= q - 1) {
                         const int pi = __ffs(static_cast<int>(q)) - 1;
@@ -813,25 +858,29 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             }
         }
         __syncwarp();
-    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
+    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + (p.bal ? 2 : 4)) {
         // ---------------- epilogue: lane quadrant q holds accumulator rows 16q .. 16q + 15 ----------------
+        // Each warp drains the groups in order on its own (no barrier among
+        // them): wait for the group's slot, read and zero its quadrant, free
+        // it, write its worlds.  Under balanced keys only quadrants 0 and 1
+        // hold worlds (0..31); world j + 32 = the group's total (count and
+        // value total from the producers) minus world j.  The metadata's
+        // world bits meet in shared memory; the last warp writes them.
         const int q = warp & 3;
+        const int n_epi = p.bal ? 2 : 4;
         const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
         const int m = 16 * q + lane;  // accumulator row of this lane (lane < 16)
         for (int k = 0;; k++) {
             const int slot = k % kSlots;
-            if (warp == kEpiWarp0 && lane == 0) {
-                const bool ok = !*abort_v && mbar_wait(&sh.done[slot], (k / kSlots) & 1, p.wait_ns);
+            int ok = 1;
+            if (lane == 0) {
+                ok = !*abort_v && mbar_wait(&sh.done[slot], (k / kSlots) & 1, p.wait_ns);
                 if (!ok) *abort_v = 1;
-                sh.epi_go = ok ? (sh.info[k % kInfo].end ? 2 : 1) : 0;
             }
-            epi_sync();
-            const int go = *reinterpret_cast<volatile int *>(&sh.epi_go);
-            if (go != 1) break;
+            if (!__shfl_sync(kFull, ok, 0)) break;
             const OrdInfo oi = sh.info[k % kInfo];
+            if (oi.end) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // the slot's kSub accumulators, added (each below 2^24: their sum
-            // is a per-CTA total, below 2^24 as well)
             long long d[kFeat];
             const uint32_t taddr = tmem + lane_base + static_cast<uint32_t>(slot) * (kAlloc * kSub);
             read_slot(taddr, d);
@@ -848,19 +897,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.freeb[slot]);
             const bool split = (k == 0 && oi.gid == sh.split_lo) || oi.gid == sh.split_hi;
-            if (p.bal && q == 2 && lane == 0) {
-#pragma unroll
-                for (int f = 0; f < kFeat; f++) sh.tot[f] = d[f];
-            }
-            epi_sync();
-            __int128 tot_sum = 0;
-            if (p.bal && !split) {
-                long long td[kFeat];
-#pragma unroll
-                for (int f = 0; f < kFeat; f++) td[f] = sh.tot[f];
-                tot_sum = digits_to_sum(td);
-            }
-            unsigned long long bits = 0;
+            const __int128 tot_sum = (static_cast<__int128>(oi.sum_hi) << 64) | static_cast<__int128>(oi.sum_lo);
             if (split) {
                 const int side = (k == 0 && oi.gid == sh.split_lo) ? 0 : 1;
                 PartRec &pr = p.part[2 * static_cast<size_t>(cta) + side];
@@ -871,27 +908,38 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 if (q == 0 && lane == 0) {
                     pr.gid = oi.gid;
                     pr.n = oi.n;
+                    pr.sum_lo = oi.sum_lo;
+                    pr.sum_hi = oi.sum_hi;
                     pr.used = 1;
                 }
-            } else if (lane < 16 && (!p.bal || q < 2)) {
+                continue;
+            }
+            unsigned long long bits = 0;
+            if (lane < 16) {
                 const int w = world_of_row(m);
                 const __int128 sw = digits_to_sum(d);
                 emit_world(p, oi.gid, w, static_cast<unsigned long long>(d[0]), sw);
                 bits = (d[0] > 0 ? 1ull : 0ull) << w;
                 if (p.bal) {
-                    // world w + 32 = the group total minus world w (the sum is linear in the digits)
-                    const long long c2 = sh.tot[0] - d[0];
+                    const long long c2 = static_cast<long long>(oi.n) - d[0];
                     emit_world(p, oi.gid, w + 32, static_cast<unsigned long long>(c2), tot_sum - sw);
                     bits |= (c2 > 0 ? 1ull : 0ull) << (w + 32);
                 }
             }
             const uint32_t o_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(bits));
             const uint32_t o_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(bits >> 32));
-            if (lane == 0) sh.orw[q] = o_lo | (static_cast<unsigned long long>(o_hi) << 32);
-            epi_sync();
-            if (!split && p.meta && warp == kEpiWarp0 && lane == 0) {
-                p.meta[2 * static_cast<size_t>(oi.gid)] = oi.n;
-                p.meta[2 * static_cast<size_t>(oi.gid) + 1] = sh.orw[0] | sh.orw[1] | sh.orw[2] | sh.orw[3];
+            if (lane == 0 && p.meta) {
+                const int ix = k % kInfo;
+                atomicOr(&sh.meta_or[ix], o_lo | (static_cast<unsigned long long>(o_hi) << 32));
+                __threadfence_block();
+                if (atomicAdd(&sh.meta_cnt[ix], 1u) == static_cast<uint32_t>(n_epi - 1)) {
+                    __threadfence_block();
+                    const unsigned long long orw = atomicOr(&sh.meta_or[ix], 0ull);
+                    p.meta[2 * static_cast<size_t>(oi.gid)] = oi.n;
+                    p.meta[2 * static_cast<size_t>(oi.gid) + 1] = orw;
+                    sh.meta_or[ix] = 0;
+                    sh.meta_cnt[ix] = 0;
+                }
             }
         }
     }
@@ -906,7 +954,6 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
 // of a group (in CTA order) adds up its group's records and writes the
 // results.  Thread m (of 64) = accumulator row m.
 __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartMmaParams p, uint32_t n_recs) {
-    __shared__ long long tot[kFeat];
     __shared__ unsigned long long orw[2];
     const uint32_t r0 = blockIdx.x;
     const PartRec &first = p.part[r0];
@@ -922,6 +969,7 @@ __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartM
 #pragma unroll
     for (int f = 0; f < kFeat; f++) d[f] = 0;
     unsigned long long n = 0;
+    __int128 tsum = 0;
     for (uint32_t j = r0; j < n_recs; j++) {
         const PartRec &pr = p.part[j];
         if (!pr.used) continue;
@@ -929,23 +977,18 @@ __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartM
 #pragma unroll
         for (int f = 0; f < kFeat; f++) d[f] += pr.d[m][f];
         n += pr.n;
+        tsum += (static_cast<__int128>(pr.sum_hi) << 64) | static_cast<__int128>(pr.sum_lo);
     }
-    if (m == 32) {
-#pragma unroll
-        for (int f = 0; f < kFeat; f++) tot[f] = d[f];
-    }
-    __syncthreads();
     unsigned long long bits = 0;
     if (!p.bal || m < 32) {
         const int w = world_of_row(m);
-        emit_world(p, g, w, static_cast<unsigned long long>(d[0]), digits_to_sum_wide(d));
+        const __int128 sw = digits_to_sum_wide(d);
+        emit_world(p, g, w, static_cast<unsigned long long>(d[0]), sw);
         bits = (d[0] > 0 ? 1ull : 0ull) << w;
         if (p.bal) {
-            long long dc[kFeat];
-#pragma unroll
-            for (int f = 0; f < kFeat; f++) dc[f] = tot[f] - d[f];
-            emit_world(p, g, w + 32, static_cast<unsigned long long>(dc[0]), digits_to_sum_wide(dc));
-            bits |= (dc[0] > 0 ? 1ull : 0ull) << (w + 32);
+            const long long c2 = static_cast<long long>(n) - d[0];
+            emit_world(p, g, w + 32, static_cast<unsigned long long>(c2), tsum - sw);
+            bits |= (c2 > 0 ? 1ull : 0ull) << (w + 32);
         }
     }
     const uint32_t o_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(bits));
