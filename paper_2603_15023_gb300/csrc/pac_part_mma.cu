@@ -103,8 +103,6 @@ struct PairRec {
     uint16_t n;      // rows of the run that count (dropped rows excluded)
     uint8_t valid;
     uint8_t nfeat;   // N of the run's B copy (16 or 32)
-    unsigned long long sum_lo;  // balanced keys: the run's value total, 128-bit two's complement
-    long long sum_hi;
 };
 
 // A group of the CTA in MMA order (ordinal k at k % kInfo).
@@ -113,8 +111,6 @@ struct OrdInfo {
     uint32_t n;
     uint32_t end;    // 1: no more groups (the epilogue stops)
     uint32_t pad;
-    unsigned long long sum_lo;  // balanced keys: the group's value total in this CTA
-    long long sum_hi;
 };
 
 struct PartShared {
@@ -137,6 +133,8 @@ struct PartShared {
     int prev_cls0;                   // ... and its class
     PairRec pairs[kOpStages][kPairs];
     OrdInfo info[kInfo];
+    uint64_t tot_ready[kSlots];         // quadrant-2 epilogue warp -> quadrants 0, 1: the slot's total row
+    long long tot[kSlots][kFeat];       // balanced keys: accumulator row 32 (the group total) per slot
     unsigned long long meta_or[kInfo];  // per group record: worlds with a nonzero count, ...
     uint32_t meta_cnt[kInfo];           // ... and the epilogue warps that have added theirs
 };
@@ -146,8 +144,6 @@ struct PartShared {
 struct PartRec {
     uint32_t gid, used;
     unsigned long long n;
-    unsigned long long sum_lo;     // balanced keys: value total (128-bit two's complement)
-    long long sum_hi;
     long long d[kWorlds][kFeat];   // digit totals per accumulator row (units of 2^-18 folded out)
 };
 
@@ -246,30 +242,6 @@ __device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
         x = (lane & s) ? ((x & ~m) | ((o >> s) & m)) : ((x & m) | ((o << s) & ~m));
     }
     return x;
-}
-
-// Exact warp sum of one int64 per lane, by 16-bit pieces (each piece's sum
-// over 32 lanes stays below 2^21; the top piece is signed).
-__device__ __forceinline__ __int128 warp_sum_i64(long long x) {
-    const unsigned long long u = static_cast<unsigned long long>(x);
-    const uint32_t c0 = __reduce_add_sync(kFull, static_cast<uint32_t>(u & 0xFFFFull));
-    const uint32_t c1 = __reduce_add_sync(kFull, static_cast<uint32_t>((u >> 16) & 0xFFFFull));
-    const uint32_t c2 = __reduce_add_sync(kFull, static_cast<uint32_t>((u >> 32) & 0xFFFFull));
-    const int c3 = __reduce_add_sync(kFull, static_cast<int>(x >> 48));
-    return static_cast<__int128>(c0) + (static_cast<__int128>(c1) << 16) + (static_cast<__int128>(c2) << 32) +
-           (static_cast<__int128>(c3) << 48);
-}
-
-// The same for one int128 per lane (eight pieces, the top one signed).
-__device__ __forceinline__ __int128 warp_sum_i128(__int128 x) {
-    const unsigned __int128 u = static_cast<unsigned __int128>(x);
-    __int128 t = 0;
-#pragma unroll
-    for (int c = 0; c < 7; c++)
-        t += static_cast<__int128>(__reduce_add_sync(kFull, static_cast<uint32_t>((u >> (16 * c)) & 0xFFFFu)))
-             << (16 * c);
-    t += static_cast<__int128>(__reduce_add_sync(kFull, static_cast<int>(x >> 112))) << 112;
-    return t;
 }
 
 // The features of one row in B copy `pair` (a 32-row region, rows by lane):
@@ -445,20 +417,12 @@ __device__ __forceinline__ uint32_t produce_block(const PartMmaParams &p, const 
         const uint32_t b_pair = b_stage + static_cast<uint32_t>(2 * b + e) * kPairBytes;
         pair_features<16>(b_pair, lane, member, v, true);
         constexpr int nfeat = Features<1, 16>::kN;
-        // balanced keys: the run's value total (the epilogue derives worlds
-        // j + 32 from it)
-        __int128 tr = 0;
-        if (p.bal) tr = warp_sum_i64(member ? v : 0ll);
-        const unsigned long long t_lo = static_cast<unsigned long long>(tr);
-        const long long t_hi = static_cast<long long>(tr >> 64);
         if (lane == 0) {
             PairRec &pr = pairs[2 * b + e];
             pr.gid = e == 0 ? g_first : g_lastb;
             pr.n = static_cast<uint16_t>(__popc(R & LB));
             pr.valid = 1;
             pr.nfeat = static_cast<uint8_t>(nfeat);
-            pr.sum_lo = t_lo;
-            pr.sum_hi = t_hi;
         }
         out |= 1u << e;
     }
@@ -514,7 +478,8 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         }
         for (int k = 0; k < kSlots; k++) {
             mbar_init(&sh.done[k], kIssuers + 1);
-            mbar_init(&sh.freeb[k], p.bal ? 2 : 4);  // the epilogue warps whose quadrants hold worlds
+            mbar_init(&sh.freeb[k], p.bal ? 3 : 4);  // the epilogue warps that read the slot
+            mbar_init(&sh.tot_ready[k], 1);
         }
         mbar_init(&sh.drain, kIssuers);
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -551,13 +516,14 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
         for (uint32_t c0 = 0; c0 < 512; c0 += 32) zero_slot(tmem + lane_base + c0);
     }
-    // A rows start as zeros (under balanced keys the upper half stays zero:
-    // worlds 32..63 come from the group totals)
+    // A rows start as zeros, with the constant world byte of balanced keys:
+    // accumulator row 32 (upper half, first byte) counts every row, so it
+    // becomes the group's total (worlds 32..63 are total - worlds 0..31)
     for (uint32_t i = static_cast<uint32_t>(tid); i < kOpStages * kChunk; i += blockDim.x) {
         const uint32_t st = i / kChunk, r = i % kChunk;
         const uint32_t a_row = op_base + st * kOpBytes + (r >> 3) * 512 + (r & 7) * 16;
 #pragma unroll
-        for (int k = 0; k < 4; k++) sts128(a_row + 128 * k, 0u, 0u, 0u, 0u);
+        for (int k = 0; k < 4; k++) sts128(a_row + 128 * k, (p.bal && k == 2) ? 1u : 0u, 0u, 0u, 0u);
     }
     for (int i = tid; i < kInfo; i += blockDim.x) {
         sh.meta_or[i] = 0;
@@ -729,18 +695,14 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         {
             int k = -1;  // ordinal of the current group
             uint32_t cur = kNone, n_acc = 0, n_mma = 0;
-            __int128 s_part = 0;  // this lane's share of the group's value total (balanced keys)
             int gave_up = 0;
             auto close = [&](int kk) {
-                const __int128 st = p.bal ? warp_sum_i128(s_part) : static_cast<__int128>(0);
                 if (lane == 0) {
                     if (iw == 0) {
                         OrdInfo &oi = sh.info[kk % kInfo];
                         oi.gid = cur;
                         oi.n = n_acc;
                         oi.end = 0;
-                        oi.sum_lo = static_cast<unsigned long long>(st);
-                        oi.sum_hi = static_cast<long long>(st >> 64);
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&sh.done[kk % kSlots])));
@@ -775,8 +737,6 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 const uint32_t pm = __ballot_sync(kFull, pvld);
                 const uint32_t gid_l = pvld ? prl.gid : kNone;
                 const uint32_t n_l = pvld ? prl.n : 0u;
-                const unsigned long long slo_l = pvld ? prl.sum_lo : 0ull;
-                const long long shi_l = pvld ? prl.sum_hi : 0ll;
                 const uint64_t da_l = smem_desc(a_stage + static_cast<uint32_t>(lane >> 1) * 2048, 512, 128);
                 const uint64_t db_l = smem_desc(b_stage + static_cast<uint32_t>(lane) * kPairBytes,
                                                 (static_cast<uint32_t>(prl.nfeat) / 16) * 128, 128);
@@ -805,15 +765,12 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                         cur = __shfl_sync(kFull, gid_l, p0);
                         n_acc = 0;
                         n_mma = 0;
-                        s_part = 0;
                     }
                     // the segment: valid pairs from p0 up to the next group start
                     const uint32_t after = ng & ~((2u << p0) - 1u) & ~(p0 == 31 ? 0xFFFFFFFFu : 0u);
                     const uint32_t seg = after ? (rest & ((1u << (__ffs(static_cast<int>(after)) - 1)) - 1u)) : rest;
                     rest &= ~seg;
                     n_acc += __reduce_add_sync(kFull, ((seg >> lane) & 1u) ? n_l : 0u);
-                    if (p.bal && ((seg >> lane) & 1u))
-                        s_part += (static_cast<__int128>(shi_l) << 64) | static_cast<__int128>(slo_l);
                     const uint32_t dacc = tmem + static_cast<uint32_t>(k % kSlots) * (kAlloc * kSub) + iw * kAlloc;
                     for (uint32_t q = seg; q; q &= q - 1) {
                         const int pi = __ffs(static_cast<int>(q)) - 1;
@@ -858,23 +815,26 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             }
         }
         __syncwarp();
-    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + (p.bal ? 2 : 4)) {
+    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + (p.bal ? 3 : 4)) {
         // ---------------- epilogue: lane quadrant q holds accumulator rows 16q .. 16q + 15 ----------------
-        // Each warp drains the groups in order on its own (no barrier among
-        // them): wait for the group's slot, read and zero its quadrant, free
-        // it, write its worlds.  Under balanced keys only quadrants 0 and 1
-        // hold worlds (0..31); world j + 32 = the group's total (count and
-        // value total from the producers) minus world j.  The metadata's
-        // world bits meet in shared memory; the last warp writes them.
+        // Each warp drains the groups in order on its own (no named barrier):
+        // wait for the group's slot, read and zero its quadrant, free it,
+        // write its worlds.  Under balanced keys quadrants 0 and 1 hold worlds
+        // 0..31 and quadrant 2 the group's total (row 32), which it hands to
+        // them through the slot's total buffer and an mbarrier; worlds j + 32
+        // are total - world j.  Quadrants 0 and 1 free the slot only after
+        // reading the total, so the buffer is not written again before.  The
+        // metadata's world bits meet in shared memory; the last warp writes them.
         const int q = warp & 3;
-        const int n_epi = p.bal ? 2 : 4;
+        const int n_meta = p.bal ? 2 : 4;  // warps that hold worlds
         const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
         const int m = 16 * q + lane;  // accumulator row of this lane (lane < 16)
         for (int k = 0;; k++) {
             const int slot = k % kSlots;
+            const uint32_t ph = (k / kSlots) & 1;
             int ok = 1;
             if (lane == 0) {
-                ok = !*abort_v && mbar_wait(&sh.done[slot], (k / kSlots) & 1, p.wait_ns);
+                ok = !*abort_v && mbar_wait(&sh.done[slot], ph, p.wait_ns);
                 if (!ok) *abort_v = 1;
             }
             if (!__shfl_sync(kFull, ok, 0)) break;
@@ -894,10 +854,39 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 for (int f = 0; f < kFeat; f++) d[f] += du[f];
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.freeb[slot]);
             const bool split = (k == 0 && oi.gid == sh.split_lo) || oi.gid == sh.split_hi;
-            const __int128 tot_sum = (static_cast<__int128>(oi.sum_hi) << 64) | static_cast<__int128>(oi.sum_lo);
+            long long tot_cnt = 0;
+            __int128 tot_sum = 0;
+            if (p.bal && q == 2) {
+                if (lane == 0) {
+#pragma unroll
+                    for (int f = 0; f < kFeat; f++) sh.tot[slot][f] = d[f];
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&sh.tot_ready[slot]);
+                    mbar_arrive(&sh.freeb[slot]);
+                }
+            } else if (p.bal) {
+                int tok = 1;
+                if (lane == 0) {
+                    tok = !*abort_v && mbar_wait(&sh.tot_ready[slot], ph, p.wait_ns);
+                    if (!tok) *abort_v = 1;
+                }
+                if (!__shfl_sync(kFull, tok, 0)) break;
+                {
+                    long long td[kFeat];
+#pragma unroll
+                    for (int f = 0; f < kFeat; f++) td[f] = sh.tot[slot][f];
+                    tot_cnt = td[0];
+                    tot_sum = digits_to_sum(td);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.freeb[slot]);
+            } else {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.freeb[slot]);
+            }
             if (split) {
                 const int side = (k == 0 && oi.gid == sh.split_lo) ? 0 : 1;
                 PartRec &pr = p.part[2 * static_cast<size_t>(cta) + side];
@@ -908,12 +897,11 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 if (q == 0 && lane == 0) {
                     pr.gid = oi.gid;
                     pr.n = oi.n;
-                    pr.sum_lo = oi.sum_lo;
-                    pr.sum_hi = oi.sum_hi;
                     pr.used = 1;
                 }
                 continue;
             }
+            if (p.bal && q == 2) continue;
             unsigned long long bits = 0;
             if (lane < 16) {
                 const int w = world_of_row(m);
@@ -921,7 +909,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 emit_world(p, oi.gid, w, static_cast<unsigned long long>(d[0]), sw);
                 bits = (d[0] > 0 ? 1ull : 0ull) << w;
                 if (p.bal) {
-                    const long long c2 = static_cast<long long>(oi.n) - d[0];
+                    const long long c2 = tot_cnt - d[0];
                     emit_world(p, oi.gid, w + 32, static_cast<unsigned long long>(c2), tot_sum - sw);
                     bits |= (c2 > 0 ? 1ull : 0ull) << (w + 32);
                 }
@@ -932,7 +920,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 const int ix = k % kInfo;
                 atomicOr(&sh.meta_or[ix], o_lo | (static_cast<unsigned long long>(o_hi) << 32));
                 __threadfence_block();
-                if (atomicAdd(&sh.meta_cnt[ix], 1u) == static_cast<uint32_t>(n_epi - 1)) {
+                if (atomicAdd(&sh.meta_cnt[ix], 1u) == static_cast<uint32_t>(n_meta - 1)) {
                     __threadfence_block();
                     const unsigned long long orw = atomicOr(&sh.meta_or[ix], 0ull);
                     p.meta[2 * static_cast<size_t>(oi.gid)] = oi.n;
@@ -954,6 +942,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
 // of a group (in CTA order) adds up its group's records and writes the
 // results.  Thread m (of 64) = accumulator row m.
 __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartMmaParams p, uint32_t n_recs) {
+    __shared__ long long tot[kFeat];
     __shared__ unsigned long long orw[2];
     const uint32_t r0 = blockIdx.x;
     const PartRec &first = p.part[r0];
@@ -969,7 +958,6 @@ __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartM
 #pragma unroll
     for (int f = 0; f < kFeat; f++) d[f] = 0;
     unsigned long long n = 0;
-    __int128 tsum = 0;
     for (uint32_t j = r0; j < n_recs; j++) {
         const PartRec &pr = p.part[j];
         if (!pr.used) continue;
@@ -977,8 +965,13 @@ __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartM
 #pragma unroll
         for (int f = 0; f < kFeat; f++) d[f] += pr.d[m][f];
         n += pr.n;
-        tsum += (static_cast<__int128>(pr.sum_hi) << 64) | static_cast<__int128>(pr.sum_lo);
     }
+    // balanced keys: row 32 is the group total
+    if (m == 32) {
+#pragma unroll
+        for (int f = 0; f < kFeat; f++) tot[f] = d[f];
+    }
+    __syncthreads();
     unsigned long long bits = 0;
     if (!p.bal || m < 32) {
         const int w = world_of_row(m);
@@ -986,9 +979,11 @@ __global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartM
         emit_world(p, g, w, static_cast<unsigned long long>(d[0]), sw);
         bits = (d[0] > 0 ? 1ull : 0ull) << w;
         if (p.bal) {
-            const long long c2 = static_cast<long long>(n) - d[0];
-            emit_world(p, g, w + 32, static_cast<unsigned long long>(c2), tsum - sw);
-            bits |= (c2 > 0 ? 1ull : 0ull) << (w + 32);
+            long long dc[kFeat];
+#pragma unroll
+            for (int f = 0; f < kFeat; f++) dc[f] = tot[f] - d[f];
+            emit_world(p, g, w + 32, static_cast<unsigned long long>(dc[0]), digits_to_sum_wide(dc));
+            bits |= (dc[0] > 0 ? 1ull : 0ull) << (w + 32);
         }
     }
     const uint32_t o_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(bits));
