@@ -1116,7 +1116,7 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
                     "shared memory)",
                  4: "one launch on CUDA cores (warp bit-transpose, int128 sums, last CTA writes the outputs)",
                  5: "rows partitioned by group, then tcgen05 tensor cores over the group-ordered rows "
-                    "(bulk-copy staged; groups inside a 32-row block summed by their warp)"
+                    "(bulk-copy staged; groups of at most 32 rows summed by one warp each)"
                  }.get(path, str(path))
     if wcfg.get("hash_only"):
         path_name = "k_hash_keys (16-byte vector loads and stores, grid = SMs x 8)"
@@ -1126,7 +1126,7 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
               3: "k_batch_agg + k_batch_merge, after k_part_hist + k_part_scan + k_part_scatter when the "
                  "rows are partitioned by group (all launches of pac_aggregate_multi)",
               4: "k_small_agg (the only launch of pac_aggregate_multi)",
-              5: "k_part_hist + k_part_scan + k_part_scatter + k_part_mma + k_part_merge + k_part_empty "
+              5: "k_part_hist + k_part_scan + k_part_scatter + k_part_mma + k_part_merge + k_part_small "
                  "(all launches of pac_aggregate_multi)"}.get(path, str(path))
     if wcfg.get("hash_only"):
         kernel = "k_hash_keys (the only launch of pac_hash_keys)"
