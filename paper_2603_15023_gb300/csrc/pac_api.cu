@@ -165,6 +165,8 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
         a.sgid = reinterpret_cast<const uint32_t *>(base + b->rel_sgid[0]);
         a.pcnt = reinterpret_cast<const uint32_t *>(base + b->rel_pcnt[0]);
         a.pend = reinterpret_cast<const uint32_t *>(base + b->rel_pcur[0]);
+        // the plan packs the group id into the records under balanced keys
+        a.packed = ((in->in_flags & PAC_IN_MASKS) == 0 && in->hash_mode == PAC_HASH_BALANCED) ? 1 : 0;
         a.specs = kept;
         a.n_specs = k;
         a.meta = meta;

@@ -1116,12 +1116,20 @@ __global__ void __launch_bounds__(256) k_part_scatter(const BatchQueryDev *__res
                 const uint64_t m = masks_in ? raw[u] : keyed_world_mask(static_cast<long long>(raw[u]), q.in.qkey,
                                                                         q.in.hash_mode);
                 // one 16-byte record per row: the mask and the first slot value
-                // (a scattered row then touches two sectors, not three)
-                if (q.n_slots > 0)
-                    reinterpret_cast<ulonglong2 *>(q.smask)[d[u]] = make_ulonglong2(m, v[u][0]);
-                else
-                    q.smask[2 * static_cast<uint64_t>(d[u])] = m;
-                q.sgid[d[u]] = g[u];
+                // (a scattered row then touches two sectors, not three); packed:
+                // the low mask word and the group id share the first 8 bytes
+                // (one sector per row)
+                if (q.pack) {
+                    reinterpret_cast<ulonglong2 *>(q.smask)[d[u]] =
+                        make_ulonglong2((m & 0xFFFFFFFFull) | (static_cast<uint64_t>(g[u]) << 32),
+                                        q.n_slots > 0 ? v[u][0] : 0ull);
+                } else {
+                    if (q.n_slots > 0)
+                        reinterpret_cast<ulonglong2 *>(q.smask)[d[u]] = make_ulonglong2(m, v[u][0]);
+                    else
+                        q.smask[2 * static_cast<uint64_t>(d[u])] = m;
+                    q.sgid[d[u]] = g[u];
+                }
 #pragma unroll
                 for (int s2 = 1; s2 < kHoist; s2++)
                     if (s2 < q.n_slots) q.sval[static_cast<uint64_t>(s2 - 1) * q.in.n + d[u]] = v[u][s2];
@@ -1336,6 +1344,7 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         d.meta = q.meta;
         d.bal = ((q.in.in_flags & PAC_IN_MASKS) == 0 && q.in.hash_mode == PAC_HASH_BALANCED) ? 1 : 0;
         d.prune = ctx->opt_minmax_prune ? 1 : 0;
+        d.pack = (cfg.partition_only && d.bal) ? 1 : 0;
         const uint32_t G = q.in.n_groups;
         const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
         const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);
@@ -1378,7 +1387,9 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
             p_smask[i] = align_up(part_off, 256);  // 16-byte records {mask, slot 0}
             part_off = p_smask[i] + n * 16;
             p_sgid[i] = align_up(part_off, 256);
-            part_off = p_sgid[i] + n * 4 + 16;  // 16 bytes readable past the end (bulk copies of whole 16-byte units)
+            // 16 bytes readable past the end (bulk copies of whole 16-byte units);
+            // packed records carry the group ids themselves
+            part_off = p_sgid[i] + (d.pack ? 0 : n * 4) + 16;
             p_sval[i] = align_up(part_off, 256);  // slots 1 .. n_slots-1
             part_off = p_sval[i] + n * 8 * static_cast<size_t>(d.n_slots > 0 ? d.n_slots - 1 : 0);
             b->n_atomic++;

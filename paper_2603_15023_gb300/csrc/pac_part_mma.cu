@@ -152,7 +152,8 @@ namespace {
 struct PartMmaParams {
     InputDev in;
     const ulonglong2 *rec;     // [n] group-ordered {mask, value}
-    const uint32_t *sgid;      // [n] group-ordered group ids
+    const uint32_t *sgid;      // [n] group-ordered group ids (unpacked records)
+    int32_t packed;            // records {low mask word | group id << 32, value} (balanced keys)
     const uint32_t *pcnt;      // [G + 2]: rows per group, [G] = rows kept
     const uint32_t *pend;      // [G]: end of each group's rows in the group order
     uint32_t rows_per_cta;
@@ -180,6 +181,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
+
+// A record's world mask and group id.  Packed records (balanced keys) hold
+// the low mask word and the group id in their first 8 bytes; the high mask
+// word is the complement of the low one.
+__device__ __forceinline__ uint64_t rec_mask(uint64_t x, bool packed) {
+    if (!packed) return x;
+    const uint64_t lo = x & 0xFFFFFFFFull;
+    return lo | ((lo ^ 0xFFFFFFFFull) << 32);
+}
+
+struct GidView {
+    const ulonglong2 *rec;
+    const uint32_t *gid;
+    bool packed;
+    __device__ __forceinline__ uint32_t operator[](int i) const {
+        return packed ? static_cast<uint32_t>(rec[i].x >> 32) : gid[i];
+    }
+};
 
 __device__ __forceinline__ bool fits_i64(__int128 v) {
     return v >= static_cast<__int128>(LLONG_MIN) && v <= static_cast<__int128>(LLONG_MAX);
@@ -374,7 +393,7 @@ __device__ __forceinline__ void block_classes(uint32_t Sk, int lane, int nv, con
 // MMA-class; a group of more than 32 rows always holds one of them).
 // Returns the valid pairs: bit 0 = pair 2b, bit 1 = pair 2b + 1.
 __device__ __forceinline__ uint32_t produce_block(const PartMmaParams &p, const ulonglong2 *rec_s,
-                                                  const uint32_t *gid_s, int nv, int b, int cls_f, int cls_l,
+                                                  const GidView gid_s, int nv, int b, int cls_f, int cls_l,
                                                   uint32_t a_stage, uint32_t b_stage, PairRec *pairs) {
     const int lane = threadIdx.x & 31;
     const int ri = 32 * b + lane;  // row within the chunk
@@ -390,7 +409,7 @@ __device__ __forceinline__ uint32_t produce_block(const PartMmaParams &p, const 
     if (!(mmaF | mmaL)) return 0u;
     const uint32_t me = 1u << lane;
     const ulonglong2 rc = rec_s[ri];
-    const uint64_t mask = valid ? rc.x : 0ull;
+    const uint64_t mask = valid ? rec_mask(rc.x, p.packed) : 0ull;
     const long long v = (valid && p.has_col) ? static_cast<long long>(rc.y) : 0ll;
     const bool live = valid && !drop_row(p.in, mask);
     const uint32_t LB = __ballot_sync(kFull, live);
@@ -493,14 +512,15 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         // groups crossing the range's edges: partial records when they are
         // tensor-core groups (more than 32 rows in all); chunk 0 sees the one
         // crossing the left edge as a group begun earlier
-        const uint32_t g_lo = lo < hi ? p.sgid[lo] : kNone;
-        const bool cont_lo = lo < hi && lo > 0 && p.sgid[lo - 1] == g_lo;
+        const GidView pg{p.rec, p.sgid, p.packed != 0};
+        const uint32_t g_lo = lo < hi ? pg[lo] : kNone;
+        const bool cont_lo = lo < hi && lo > 0 && pg[lo - 1] == g_lo;
         const bool big_lo = cont_lo && p.pcnt[g_lo] > 32;
         sh.split_lo = big_lo ? g_lo : kNone;
         sh.prev_gid0 = cont_lo ? g_lo : kNone;
         sh.prev_cls0 = (cont_lo && !big_lo) ? kClsSkip : kClsMma;
-        const uint32_t g_hi = lo < hi ? p.sgid[hi - 1] : kNone;
-        const bool cont_hi = lo < hi && hi < kept && p.sgid[hi] == g_hi;
+        const uint32_t g_hi = lo < hi ? pg[hi - 1] : kNone;
+        const bool cont_hi = lo < hi && hi < kept && pg[hi] == g_hi;
         sh.split_hi = (cont_hi && p.pcnt[g_hi] > 32) ? g_hi : kNone;
     }
     if (warp == kEpiWarp0) {
@@ -559,7 +579,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             if (!ok) break;
             const unsigned char *raw = smem + r * kRawBytes;
             const ulonglong2 *rec_s = reinterpret_cast<const ulonglong2 *>(raw);
-            const uint32_t *gid_s = reinterpret_cast<const uint32_t *>(raw + kRawRecBytes);
+            const GidView gid_s{rec_s, reinterpret_cast<const uint32_t *>(raw + kRawRecBytes), p.packed != 0};
             const uint32_t a_stage = op_base + s * kOpBytes, b_stage = a_stage + kABytes;
             uint32_t pv = 0;
 #pragma unroll
@@ -601,7 +621,8 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             }
             ok = __shfl_sync(kFull, ok, 0);
             if (!ok) break;
-            const uint32_t *gid_s = reinterpret_cast<const uint32_t *>(smem + r * kRawBytes + kRawRecBytes);
+            const GidView gid_s{reinterpret_cast<const ulonglong2 *>(smem + r * kRawBytes),
+                                reinterpret_cast<const uint32_t *>(smem + r * kRawBytes + kRawRecBytes), p.packed != 0};
             const uint32_t g_last = gid_s[nv - 1];
             if (gid_s[0] == prev_gid && g_last == prev_gid) {
                 // the whole chunk continues the previous chunk's group (rows are
@@ -635,8 +656,9 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 } else if (tot > 32) {
                     last_cls = kClsMma;
                 } else {
-                    const uint32_t *gid_n =
-                        reinterpret_cast<const uint32_t *>(smem + rn * kRawBytes + kRawRecBytes);
+                    const GidView gid_n{reinterpret_cast<const ulonglong2 *>(smem + rn * kRawBytes),
+                                        reinterpret_cast<const uint32_t *>(smem + rn * kRawBytes + kRawRecBytes),
+                                        p.packed != 0};
                     const uint32_t rows_n = min(static_cast<uint32_t>(kChunk), hi - (c0 + kChunk));
                     const uint32_t gn = static_cast<uint32_t>(lane) < rows_n ? gid_n[lane] : kNone;
                     const uint32_t eq = __ballot_sync(kFull, gn == g_last);
@@ -670,9 +692,10 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 const uint32_t c0 = lo + i * kChunk;
                 const uint32_t rows = min(static_cast<uint32_t>(kChunk), hi - c0);
                 const uint32_t rows4 = (rows + 3) & ~3u;  // the group-id array has 16 bytes of slack
-                mbar_expect_tx(&sh.raw_full[r], rows * 16 + rows4 * 4);
+                mbar_expect_tx(&sh.raw_full[r], rows * 16 + (p.packed ? 0u : rows4 * 4));
                 bulk_g2s(raw_base + r * kRawBytes, p.rec + c0, rows * 16, &sh.raw_full[r]);
-                bulk_g2s(raw_base + r * kRawBytes + kRawRecBytes, p.sgid + c0, rows4 * 4, &sh.raw_full[r]);
+                if (!p.packed)
+                    bulk_g2s(raw_base + r * kRawBytes + kRawRecBytes, p.sgid + c0, rows4 * 4, &sh.raw_full[r]);
                 issued = i + 1;
             }
             // every issued copy has landed before the CTA ends
@@ -1032,7 +1055,7 @@ __global__ void __launch_bounds__(256) k_part_small(const __grid_constant__ Part
             fetch(j_next, rc_next, n_next);
         }
         const bool in = static_cast<uint32_t>(lane) < n;
-        const uint64_t mask = rc.x;
+        const uint64_t mask = rec_mask(rc.x, p.packed);
         const long long v = (in && p.has_col) ? static_cast<long long>(rc.y) : 0ll;
         const bool live = in && !drop_row(p.in, mask);
         const uint32_t T = warp_transpose(live ? static_cast<uint32_t>(mask) : 0u, lane);
@@ -1081,6 +1104,7 @@ pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launc
     p.in = a.in;
     p.rec = static_cast<const ulonglong2 *>(a.rec);
     p.sgid = a.sgid;
+    p.packed = a.packed;
     p.pcnt = a.pcnt;
     p.pend = a.pend;
     p.rows_per_cta = part_rows_per_cta(a.in.n, a.n_sms);

@@ -18,7 +18,8 @@ constexpr uint32_t kPartMmaAutoGroups = 64;
 struct PartMmaArgs {
     InputDev in;                 // the query (n, n_groups, flags, hash mode)
     const void *rec;             // [n] group-ordered 16-byte records {mask, value}
-    const uint32_t *sgid;        // [n] group-ordered group ids, 16 bytes readable past the end
+    const uint32_t *sgid;        // [n] group-ordered group ids, 16 bytes readable past the end (unpacked)
+    int packed;                  // records {low mask word | group id << 32, value}: balanced keys, no sgid
     const uint32_t *pcnt;        // [G + 2]: rows per group, [G] = rows kept
     const uint32_t *pend;        // [G]: end of each group's rows (the scatter's cursors)
     const pac_agg_spec *specs;   // COUNT and exact int64 SUM/AVG of one column
