@@ -75,7 +75,7 @@ __device__ __forceinline__ void atomic_fold(int op, uint64_t *cell, uint64_t acc
 struct ItemShared {
     InputDev in;
     SlotDev slot[kMaxSpecs];
-    int32_t n_slots, mode, bal, prune;
+    int32_t n_slots, mode, bal, prune, pack;
     uint64_t *state, *ng;
     unsigned long long *abs;
     uint64_t row0, row_end;
@@ -151,9 +151,15 @@ __device__ __forceinline__ void load_row(const ItemShared &is, uint64_t row, boo
         // records of 16 bytes: {mask, first slot value}; further slots in sval
         unsigned long long v0 = 0;
         if (valid) {
-            gid = __ldg(is.sgid + row);
             const ulonglong2 rec = __ldg(reinterpret_cast<const ulonglong2 *>(is.smask) + row);
-            mask = rec.x;
+            if (is.pack) {  // {low mask word | group id << 32, value}: the high word is the complement
+                gid = static_cast<uint32_t>(rec.x >> 32);
+                const uint64_t lo = rec.x & 0xFFFFFFFFull;
+                mask = lo | ((lo ^ 0xFFFFFFFFull) << 32);
+            } else {
+                gid = __ldg(is.sgid + row);
+                mask = rec.x;
+            }
             v0 = rec.y;
             if (drop_row(is.in, mask)) {
                 valid = false;
@@ -817,6 +823,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch_agg(const BatchQuery
                 is.k = item.k;
                 is.smask = q.mode == 1 ? q.smask : nullptr;
                 is.sgid = q.sgid;
+                is.pack = q.pack;
                 is.sval = q.sval;
                 is.n = q.in.n;
                 if (q.mode == 1) {
@@ -1344,7 +1351,7 @@ pac_status plan_build(pac_ctx *ctx, const pac_query *qs, int n_queries, const Ba
         d.meta = q.meta;
         d.bal = ((q.in.in_flags & PAC_IN_MASKS) == 0 && q.in.hash_mode == PAC_HASH_BALANCED) ? 1 : 0;
         d.prune = ctx->opt_minmax_prune ? 1 : 0;
-        d.pack = (cfg.partition_only && d.bal) ? 1 : 0;
+        d.pack = d.bal;  // partitioned queries with balanced keys write packed records
         const uint32_t G = q.in.n_groups;
         const size_t per_part = static_cast<size_t>(1 + d.n_slots) * G * kWorlds * 8;
         const size_t smem_need = bitloop_smem_bytes(kBatchWarps, d.n_slots, G, b->ns);

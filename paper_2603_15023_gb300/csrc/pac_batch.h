@@ -17,8 +17,8 @@ struct BatchQueryDev {
     int32_t mode;  // 0: warp-private shared-memory states, 1: global atomics
     int32_t bal;   // balanced keyed masks: worlds 32..63 are the complements of 0..31
     int32_t prune; // MIN/MAX bound pruning (rows that improve no world skip the update)
-    int32_t pack;  // partition-only plan, balanced keys: records {low mask word | group id << 32,
-                   // slot 0 value} (the high word is the complement of the low one), no sgid
+    int32_t pack;  // balanced keys: partition records {low mask word | group id << 32, slot 0
+                   // value} (the high word is the complement of the low one), no sgid
     SlotDev slot[kMaxSpecs];
     OutDev outs[kMaxSpecs];
     uint64_t *meta;
