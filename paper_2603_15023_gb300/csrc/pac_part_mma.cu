@@ -26,18 +26,21 @@
 //     and zeros in the block's other rows (at most two per block: such a
 //     group always holds the block's first or last row).
 // The MMAs of one group accumulate into one of sixteen tensor-memory slots (a
-// ring over the CTA's tensor-core groups in order); the slot of a new group is
-// taken once the epilogue has emptied it.  When a group's last MMA is done,
-// the epilogue warps read its slot, zero it, and write the group's
-// COUNT/SUM/AVG and metadata.  A group that crosses an edge of the CTA's
-// range writes its digit totals as a partial record instead; k_part_merge
-// adds the partials of each such group in CTA order.  No result is written
-// with an atomic operation.
+// ring over the CTA's tensor-core groups in order; the group's first MMA
+// overwrites the slot, so a slot is never zeroed); the slot of a new group is
+// taken once the epilogue has read it out.  When a group's last MMA is done,
+// an epilogue warp set reads its slot and writes the group's COUNT/SUM/AVG
+// and metadata; two sets drain alternate groups, since one group's drain is a
+// chain of dependent latencies (tensor-memory load, conversion, the total's
+// hand-over, stores) far longer than its issue time.  A group that crosses an
+// edge of the CTA's range writes its digit totals as a partial record
+// instead; k_part_merge adds the partials of each such group in CTA order.
+// No result is written with an atomic operation.
 //
-// Warps: 0-15 producers (block w of every chunk), 16-19 epilogue
-// (tensor-memory lane quadrants 0-3), 20 bulk-copy loader, 21 MMA issuer,
-// 22 classifier (each chunk's group starts and edge classes, ahead of the
-// producers, which then share no barrier).
+// Warps: 0-15 producers (block w of every chunk), 16-19 and 20-23 the two
+// epilogue sets (tensor-memory lane quadrant = warp % 4), 24 bulk-copy
+// loader, 25 MMA issuer, 26 classifier (each chunk's group starts and edge
+// classes, ahead of the producers, which then share no barrier).
 // Every wait is bounded (%globaltimer); a wait that gives up stops its warp's
 // work, the CTA drains what it has in flight and reports PAC_E_TIMEOUT.
 #include <climits>
@@ -60,17 +63,14 @@ constexpr int kRawStages = 4;              // chunks in flight
 constexpr int kOpStages = 2;               // operand stages
 constexpr int kProdWarps = 16;             // one 32-row block each per chunk
 constexpr int kBlocksPerWarp = kBlocks / kProdWarps;
-constexpr int kEpiWarp0 = kProdWarps;      // epilogue warps, lane quadrant = warp % 4
-constexpr int kLoadWarp = kEpiWarp0 + 4;
-constexpr int kIssuers = 1;                // MMA-issuing warps (more did not pay: see the issue loop)
-constexpr int kMmaWarp0 = kLoadWarp + 1;
-constexpr int kClsWarp = kMmaWarp0 + kIssuers;  // classifies each chunk's groups ahead of the producers
+constexpr int kEpiSets = 2;                // epilogue warp sets (set e drains the groups k = e mod kEpiSets)
+constexpr int kEpiWarp0 = kProdWarps;      // set e: warps kEpiWarp0 + 4 e + q, lane quadrant q
+constexpr int kLoadWarp = kEpiWarp0 + 4 * kEpiSets;
+constexpr int kMmaWarp = kLoadWarp + 1;    // one issuing thread (more issuing warps did not pay)
+constexpr int kClsWarp = kMmaWarp + 1;     // classifies each chunk's groups ahead of the producers
 constexpr int kThreadsP = (kClsWarp + 1) * 32;
-constexpr int kAlloc = 32;                 // tensor-memory columns per accumulator
-// A group's MMAs rotate over kSub accumulators, one per issuing warp; a
-// slot = kSub accumulators.
-constexpr int kSub = kIssuers;
-constexpr int kSlots = 512 / (kAlloc * kSub);  // slots in the ring
+constexpr int kAlloc = 32;                 // tensor-memory columns per accumulator (a slot)
+constexpr int kSlots = 512 / kAlloc;       // slots in the ring
 constexpr int kFeat = 20;                  // COUNT, three pad features, 16 digits
 constexpr int kInfo = 256;                 // per-group records of the ring (see the MMA warp)
 constexpr int kNMax = 32;                  // B bytes per row: N for 16 digits
@@ -95,6 +95,8 @@ static_assert(kSlots >= 2, "the slot ring needs two slots");
 static_assert(kBlocks % kProdWarps == 0 && kProdWarps <= 32, "producer warps split the chunk's blocks evenly");
 static_assert(kPairs == 32, "the MMA warp holds one pair per lane");
 static_assert(kEpiWarp0 % 4 == 0, "epilogue warp q must own tensor-memory lane quadrant q");
+static_assert(kSlots % kEpiSets == 0, "a slot's groups must all fall to one epilogue set");
+static_assert(kAlloc >= kNMax, "a slot holds one accumulator of N = kNMax columns");
 static_assert(kInfo >= kSlots + 3 * kPairs, "the group records must outlive the ring");
 
 // One MMA of a chunk: a run of group `gid` in block (pair index / 2).
@@ -102,7 +104,7 @@ struct PairRec {
     uint32_t gid;
     uint16_t n;      // rows of the run that count (dropped rows excluded)
     uint8_t valid;
-    uint8_t nfeat;   // N of the run's B copy (16 or 32)
+    uint8_t pad;
 };
 
 // A group of the CTA in MMA order (ordinal k at k % kInfo).
@@ -118,8 +120,8 @@ struct PartShared {
     uint64_t raw_empty[kRawStages];
     uint64_t full[kOpStages];
     uint64_t empty[kOpStages];
-    uint64_t done[kSlots];   // MMA warps (a commit each + an arrive) -> epilogue: the slot's group is complete
-    uint64_t freeb[kSlots];  // epilogue (4 warps) -> MMA warp: the slot is zero and free
+    uint64_t done[kSlots];   // MMA warp (a commit + an arrive) -> epilogue: the slot's group is complete
+    uint64_t freeb[kSlots];  // epilogue (the set's 3 or 4 warps) -> MMA warp: the slot has been read out
     uint64_t drain;
     uint32_t tmem_slot;
     int abort_flag;
@@ -435,13 +437,12 @@ __device__ __forceinline__ uint32_t produce_block(const PartMmaParams &p, const 
         // 16 digits, the top one signed: every int64 value, no per-run digit count
         const uint32_t b_pair = b_stage + static_cast<uint32_t>(2 * b + e) * kPairBytes;
         pair_features<16>(b_pair, lane, member, v, true);
-        constexpr int nfeat = Features<1, 16>::kN;
+        static_assert(Features<1, 16>::kN == kNMax, "every B copy has N = kNMax columns");
         if (lane == 0) {
             PairRec &pr = pairs[2 * b + e];
             pr.gid = e == 0 ? g_first : g_lastb;
             pr.n = static_cast<uint16_t>(__popc(R & LB));
             pr.valid = 1;
-            pr.nfeat = static_cast<uint8_t>(nfeat);
         }
         out |= 1u << e;
     }
@@ -466,14 +467,6 @@ __device__ __forceinline__ void read_slot(uint32_t taddr, long long (&d)[kFeat])
     for (int f = 0; f < kFeat; f++) d[f] = __float2ll_rn(__uint_as_float(r[f]) * 262144.0f);
 }
 
-__device__ __forceinline__ void zero_slot(uint32_t taddr) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
-        "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
-        "r"(0u));
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
 __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant__ PartMmaParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PartShared sh;
@@ -493,14 +486,14 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         }
         for (int s = 0; s < kOpStages; s++) {
             mbar_init(&sh.full[s], kProdWarps);
-            mbar_init(&sh.empty[s], kIssuers);
+            mbar_init(&sh.empty[s], 1);
         }
         for (int k = 0; k < kSlots; k++) {
-            mbar_init(&sh.done[k], kIssuers + 1);
-            mbar_init(&sh.freeb[k], p.bal ? 3 : 4);  // the epilogue warps that read the slot
+            mbar_init(&sh.done[k], 2);  // the issuer's commit and its arrive with the group's record
+            mbar_init(&sh.freeb[k], p.bal ? 3 : 4);  // the epilogue set's warps that read the slot
             mbar_init(&sh.tot_ready[k], 1);
         }
-        mbar_init(&sh.drain, kIssuers);
+        mbar_init(&sh.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         sh.abort_flag = 0;
         const uint32_t G = p.in.n_groups;
@@ -532,10 +525,6 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = sh.tmem_slot;
-    if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {  // zero every slot (lane quadrant warp % 4)
-        const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
-        for (uint32_t c0 = 0; c0 < 512; c0 += 32) zero_slot(tmem + lane_base + c0);
-    }
     // A rows start as zeros, with the constant world byte of balanced keys:
     // accumulator row 32 (upper half, first byte) counts every row, so it
     // becomes the group's total (worlds 32..63 are total - worlds 0..31)
@@ -703,36 +692,32 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 if (!mbar_wait(&sh.raw_full[i % kRawStages], (i / kRawStages) & 1, kWaitNs)) *abort_v = 1;
         }
         __syncwarp();
-    } else if (warp >= kMmaWarp0 && warp < kMmaWarp0 + kIssuers) {
-        // ---------------- MMA issuers ----------------
-        // Every issuer walks the same pairs and numbers the groups alike;
-        // issuer w issues a group's MMAs w, w + kIssuers, ... into accumulator
-        // w of its slot.  Completion: a commit from every issuer (the chunk's
-        // stage, a group's slot, the final drain); issuer 0 also records the
-        // group and arrives once more on its slot.
-        const int iw = warp - kMmaWarp0;
-        // The chunk's pair records are read lane-parallel (lane p: pair p)
-        // and reach the issuing lane by shuffles: no shared-memory load sits
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer ----------------
+        // Completion: a commit per chunk (its operand stage), per group (its
+        // slot; with an arrive that publishes the group's record) and a final
+        // drain.  The chunk's pair records are read lane-parallel (lane p:
+        // pair p); lane 0 alone issues, each MMA's operand descriptors
+        // computed from its pair index: no shuffle or shared-memory load sits
         // between two MMAs (a tcgen05.mma from one thread costs about 100
-        // cycles of issue; a dependent load per MMA more than doubled that).
+        // cycles of issue; a dependent load or shuffle per MMA more than
+        // doubled that).
         {
             int k = -1;  // ordinal of the current group
             uint32_t cur = kNone, n_acc = 0, n_mma = 0;
             int gave_up = 0;
             auto close = [&](int kk) {
                 if (lane == 0) {
-                    if (iw == 0) {
-                        OrdInfo &oi = sh.info[kk % kInfo];
-                        oi.gid = cur;
-                        oi.n = n_acc;
-                        oi.end = 0;
-                    }
+                    OrdInfo &oi = sh.info[kk % kInfo];
+                    oi.gid = cur;
+                    oi.n = n_acc;
+                    oi.end = 0;
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&sh.done[kk % kSlots])));
-                    if (iw == 0) mbar_arrive(&sh.done[kk % kSlots]);
+                    mbar_arrive(&sh.done[kk % kSlots]);
                 }
             };
-            // the slot of ordinal kk is free once the epilogue has emptied ordinal kk - kSlots
+            // the slot of ordinal kk is free once the epilogue has read out ordinal kk - kSlots
             auto take_slot = [&](int kk) -> bool {
                 if (kk < kSlots) return true;
                 int ok = 1;
@@ -742,6 +727,12 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 }
                 return __shfl_sync(kFull, ok, 0) != 0;
             };
+            // pair p's A block is p / 2 (2048 bytes each) and its B copy p
+            // (kPairBytes each): the descriptors' address fields (16-byte
+            // units, below 2^14 for any shared-memory address) advance by
+            // 128 and kPairBytes / 16 per step
+            static_assert((32 * 64) / 16 == (1 << 7) && kPairBytes / 16 == (1 << 6), "descriptor steps");
+            const uint32_t idesc = instr_desc<64>(kNMax);
             for (uint32_t i = 0; i < n_chunks && !gave_up; i++) {
                 const int s = static_cast<int>(i % kOpStages);
                 int ok = 1;
@@ -752,7 +743,9 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t a_stage = op_base + s * kOpBytes, b_stage = a_stage + kABytes;
-                // lane p: pair p's validity, record and operand descriptors
+                const uint64_t da0 = smem_desc(a_stage, 512, 128);
+                const uint64_t db0 = smem_desc(b_stage, (kNMax / 16) * 128, 128);
+                // lane p: pair p's validity and record
                 const int wq = lane >> 1, bq = wq % kProdWarps, bbq = wq / kProdWarps;
                 const uint32_t nib = sh.pvalid[s][bq];
                 const bool pvld = (nib >> (2 * bbq + (lane & 1))) & 1u;
@@ -760,10 +753,6 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 const uint32_t pm = __ballot_sync(kFull, pvld);
                 const uint32_t gid_l = pvld ? prl.gid : kNone;
                 const uint32_t n_l = pvld ? prl.n : 0u;
-                const uint64_t da_l = smem_desc(a_stage + static_cast<uint32_t>(lane >> 1) * 2048, 512, 128);
-                const uint64_t db_l = smem_desc(b_stage + static_cast<uint32_t>(lane) * kPairBytes,
-                                                (static_cast<uint32_t>(prl.nfeat) / 16) * 128, 128);
-                const uint32_t id_l = instr_desc<64>(prl.nfeat);
                 // group starts: a valid pair whose group differs from the previous valid pair's
                 int pv_idx = pvld ? lane : -1;
 #pragma unroll
@@ -775,7 +764,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 if (lane == 0) prev_valid = -1;
                 const uint32_t gprev = __shfl_sync(kFull, gid_l, prev_valid < 0 ? 0 : prev_valid);
                 const uint32_t ng = __ballot_sync(kFull, pvld && gid_l != (prev_valid < 0 ? cur : gprev));
-                // segments of one group, issued back to back (shuffles and one MMA each)
+                // segments of one group, issued back to back
                 for (uint32_t rest = pm; rest;) {
                     const int p0 = __ffs(static_cast<int>(rest)) - 1;
                     if ((ng >> p0) & 1u) {
@@ -794,15 +783,16 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                     const uint32_t seg = after ? (rest & ((1u << (__ffs(static_cast<int>(after)) - 1)) - 1u)) : rest;
                     rest &= ~seg;
                     n_acc += __reduce_add_sync(kFull, ((seg >> lane) & 1u) ? n_l : 0u);
-                    const uint32_t dacc = tmem + static_cast<uint32_t>(k % kSlots) * (kAlloc * kSub) + iw * kAlloc;
-                    for (uint32_t q = seg; q; q &= q - 1) {
-                        const int pi = __ffs(static_cast<int>(q)) - 1;
-                        const uint64_t da = __shfl_sync(kFull, da_l, pi);
-                        const uint64_t db = __shfl_sync(kFull, db_l, pi);
-                        const uint32_t id = __shfl_sync(kFull, id_l, pi);
-                        if (lane == 0 && n_mma % kIssuers == static_cast<uint32_t>(iw)) mma_f8(dacc, da, db, id);
-                        n_mma++;
+                    const uint32_t dacc = tmem + static_cast<uint32_t>(k % kSlots) * kAlloc;
+                    if (lane == 0) {
+                        uint32_t acc = n_mma != 0 ? 1u : 0u;  // the group's first MMA overwrites its slot
+                        for (uint32_t q = seg; q; q &= q - 1) {
+                            const uint32_t pi = static_cast<uint32_t>(__ffs(static_cast<int>(q)) - 1);
+                            mma_f8_acc(dacc, da0 + ((pi >> 1) << 7), db0 + (pi << 6), idesc, acc);
+                            acc = 1u;
+                        }
                     }
+                    n_mma += static_cast<uint32_t>(__popc(seg));
                 }
                 if (gave_up) break;
                 if (lane == 0)
@@ -813,21 +803,21 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 if (lane == 0) *abort_v = 1;
             } else {
                 if (k >= 0) close(k);
-                // end marker: ordinal k + 1 (its slot's previous group emptied first)
-                const int ke = k + 1;
-                if (take_slot(ke)) {
+                // end markers: ordinals k + 1 .. k + kEpiSets, one for each
+                // epilogue set (each slot's previous group read out first)
+                for (int ke = k + 1; ke <= k + kEpiSets; ke++) {
+                    if (!take_slot(ke)) {
+                        if (lane == 0) *abort_v = 1;
+                        break;
+                    }
                     if (lane == 0) {
-                        if (iw == 0) {
-                            OrdInfo &oi = sh.info[ke % kInfo];
-                            oi.gid = kNone;
-                            oi.n = 0;
-                            oi.end = 1;
-                            mbar_arrive(&sh.done[ke % kSlots]);
-                        }
+                        OrdInfo &oi = sh.info[ke % kInfo];
+                        oi.gid = kNone;
+                        oi.n = 0;
+                        oi.end = 1;
+                        mbar_arrive(&sh.done[ke % kSlots]);
                         mbar_arrive(&sh.done[ke % kSlots]);
                     }
-                } else if (lane == 0) {
-                    *abort_v = 1;
                 }
             }
             // every MMA issued is complete before tensor memory is read or freed
@@ -838,21 +828,23 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             }
         }
         __syncwarp();
-    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + (p.bal ? 3 : 4)) {
-        // ---------------- epilogue: lane quadrant q holds accumulator rows 16q .. 16q + 15 ----------------
-        // Each warp drains the groups in order on its own (no named barrier):
-        // wait for the group's slot, read and zero its quadrant, free it,
-        // write its worlds.  Under balanced keys quadrants 0 and 1 hold worlds
-        // 0..31 and quadrant 2 the group's total (row 32), which it hands to
-        // them through the slot's total buffer and an mbarrier; worlds j + 32
-        // are total - world j.  Quadrants 0 and 1 free the slot only after
-        // reading the total, so the buffer is not written again before.  The
-        // metadata's world bits meet in shared memory; the last warp writes them.
+    } else if (warp >= kEpiWarp0 && warp < kLoadWarp && (warp & 3) < (p.bal ? 3 : 4)) {
+        // ------- epilogue set (warp - kEpiWarp0) / 4: lane quadrant q holds accumulator rows 16q .. 16q + 15 -------
+        // Each warp drains its set's groups (ordinals e, e + kEpiSets, ...) in
+        // order on its own (no named barrier): wait for the group's slot, read
+        // its quadrant, free it, write its worlds.  Under balanced keys
+        // quadrants 0 and 1 hold worlds 0..31 and quadrant 2 the group's total
+        // (row 32), which it hands to them through the slot's total buffer and
+        // an mbarrier; worlds j + 32 are total - world j.  Quadrants 0 and 1
+        // free the slot only after reading the total, so the buffer is not
+        // written again before.  The metadata's world bits meet in shared
+        // memory; the last warp writes them.
         const int q = warp & 3;
+        const int eset = (warp - kEpiWarp0) >> 2;
         const int n_meta = p.bal ? 2 : 4;  // warps that hold worlds
         const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
         const int m = 16 * q + lane;  // accumulator row of this lane (lane < 16)
-        for (int k = 0;; k++) {
+        for (int k = eset;; k += kEpiSets) {
             const int slot = k % kSlots;
             const uint32_t ph = (k / kSlots) & 1;
             int ok = 1;
@@ -865,17 +857,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             if (oi.end) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             long long d[kFeat];
-            const uint32_t taddr = tmem + lane_base + static_cast<uint32_t>(slot) * (kAlloc * kSub);
-            read_slot(taddr, d);
-            zero_slot(taddr);
-#pragma unroll
-            for (int u = 1; u < kSub; u++) {
-                long long du[kFeat];
-                read_slot(taddr + u * kAlloc, du);
-                zero_slot(taddr + u * kAlloc);
-#pragma unroll
-                for (int f = 0; f < kFeat; f++) d[f] += du[f];
-            }
+            read_slot(tmem + lane_base + static_cast<uint32_t>(slot) * kAlloc, d);
             asm volatile("tcgen05.fence::before_thread_sync;");
             const bool split = (k == 0 && oi.gid == sh.split_lo) || oi.gid == sh.split_hi;
             long long tot_cnt = 0;
