@@ -1135,8 +1135,8 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
               3: "k_batch_agg + k_batch_merge, after k_part_hist + k_part_scan + k_part_scatter when the "
                  "rows are partitioned by group (all launches of pac_aggregate_multi)",
               4: "k_small_agg (the only launch of pac_aggregate_multi)",
-              5: "k_part_hist + k_part_scan + k_part_scatter + k_part_mma + k_part_merge + k_part_small "
-                 "(all launches of pac_aggregate_multi)"}.get(path, str(path))
+              5: "k_part_hist + k_part_scan + k_part_scatter + k_range_tiles + k_range_plan + k_range_cuts + "
+                 "k_part_mma + k_part_merge + k_part_small (all launches of pac_aggregate_multi)"}.get(path, str(path))
     if wcfg.get("hash_only"):
         kernel = "k_hash_keys (the only launch of pac_hash_keys)"
     if wcfg.get("approx"):

@@ -126,7 +126,7 @@ pac_status run_engine(pac_ctx *ctx, const pac_input *in, const pac_agg_spec *spe
     if (st != PAC_OK) return st;
     const size_t part_off = align_up(b->device_bytes, 256);
     st = ensure_buffer(ctx, &ctx->ws, &ctx->ws_bytes,
-                       tensor ? part_off + part_mma_scratch_bytes(in->n, ctx->n_sms) : b->device_bytes);
+                       tensor ? part_off + part_mma_scratch_bytes(in->n, in->n_groups, ctx->n_sms) : b->device_bytes);
     if (st == PAC_OK && ctx->pin_bytes < b->image.size()) {
         if (ctx->pin) {
             cudaEventSynchronize(ctx->pin_ev);

@@ -43,6 +43,7 @@
 // classes, ahead of the producers, which then share no barrier).
 // Every wait is bounded (%globaltimer); a wait that gives up stops its warp's
 // work, the CTA drains what it has in flight and reports PAC_E_TIMEOUT.
+#include <algorithm>
 #include <climits>
 
 #include "pac_internal.cuh"
@@ -74,10 +75,19 @@ constexpr int kSlots = 512 / kAlloc;       // slots in the ring
 constexpr int kFeat = 20;                  // COUNT, three pad features, 16 digits
 constexpr int kInfo = 256;                 // per-group records of the ring (see the MMA warp)
 constexpr int kNMax = 32;                  // B bytes per row: N for 16 digits
-// rows per CTA at most: many more CTAs than SMs, so that ranges of many small
-// groups (more output per row) spread over the SMs (below 2^20: FP32 digit
-// totals stay exact)
-constexpr uint32_t kMaxRowsPerCtaP = 1u << 16;
+// rows per range at most (digit totals below 2^20: FP32 accumulation stays exact)
+constexpr uint32_t kMaxRowsPerRange = 1u << 16;
+// Range planning.  A range's time on one SM is close to (its rows) +
+// kGroupCost x (its groups of more than 32 rows) row times: each such group
+// is drained once by the epilogue, about 300 rows' worth (1.3 us against
+// 4.2 ns a row, measured).  The rows are cut into ranges of equal cost, at
+// most kRangeCost each (every row costs at least 1, so no range exceeds
+// kMaxRowsPerRange rows once its ends are rounded down to chunk boundaries).
+constexpr uint32_t kGroupCost = 300;
+constexpr uint32_t kRangeCost = kMaxRowsPerRange - kChunk;
+constexpr uint32_t kMinRangeCost = 8 * kChunk;  // fewer ranges than SMs rather than ranges below this
+constexpr uint32_t kTileGroups = 4096;           // groups per planning tile
+constexpr int kPlanThreads = 256;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 // one raw chunk: records, then group ids
@@ -125,7 +135,8 @@ struct PartShared {
     uint64_t drain;
     uint32_t tmem_slot;
     int abort_flag;
-    uint32_t lo, hi;         // the CTA's rows [lo, hi)
+    uint32_t range;          // the range in work (kNone: none left)
+    uint32_t lo, hi;         // its rows [lo, hi)
     uint32_t split_lo;       // group crossing the CTA's left edge, or kNone
     uint32_t split_hi;       // group crossing its right edge, or kNone
     uint64_t cls_full[kRawStages];   // classifier -> producers: the chunk in raw slot r is classified
@@ -151,6 +162,14 @@ struct PartRec {
 
 namespace {
 
+// The ranges of k_part_mma (written by k_range_plan).
+struct RangePlan {
+    unsigned long long total;  // the kept rows' cost
+    unsigned long long share;  // cost per range (at most kRangeCost)
+    uint32_t n_ranges;         // R
+    uint32_t next;             // ranges handed out so far (k_part_mma's counter)
+};
+
 struct PartMmaParams {
     InputDev in;
     const ulonglong2 *rec;     // [n] group-ordered {mask, value}
@@ -158,14 +177,17 @@ struct PartMmaParams {
     int32_t packed;            // records {low mask word | group id << 32, value} (balanced keys)
     const uint32_t *pcnt;      // [G + 2]: rows per group, [G] = rows kept
     const uint32_t *pend;      // [G]: end of each group's rows in the group order
-    uint32_t rows_per_cta;
+    RangePlan *plan;
+    uint32_t *range_lo;        // [R + 1]: range r = rows [range_lo[r], range_lo[r + 1])
+    unsigned long long *tile;  // [ceil(G / kTileGroups)]: tile costs, then their exclusive sums
+    uint32_t r_max;            // R at most (the partial records' capacity)
     int32_t bal;               // balanced keys: accumulator row 32 is the run total
     int32_t has_col;           // 0: COUNT only (the records carry no value)
     int32_t n_out;
     int32_t out_kind[kMaxSpecs];
     void *out[kMaxSpecs];
     uint64_t *meta;            // [G][2] {n_g, worlds with a nonzero count} or null
-    PartRec *part;             // [grid][2] (zeroed)
+    PartRec *part;             // [R][2]: range r's records (used = 0 unless written)
     uint32_t *status;
     uint64_t wait_ns;
 };
@@ -467,82 +489,187 @@ __device__ __forceinline__ void read_slot(uint32_t taddr, long long (&d)[kFeat])
     for (int f = 0; f < kFeat; f++) d[f] = __float2ll_rn(__uint_as_float(r[f]) * 262144.0f);
 }
 
-__global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant__ PartMmaParams p) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ PartShared sh;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // row ranges in reverse launch order: the last ranges of the group order
-    // (many small groups, the most output per row) start first
-    const uint32_t cta = gridDim.x - 1 - blockIdx.x;
-    const uint32_t smem_base = smem_u32(smem);
-    const uint32_t raw_base = smem_base;
-    const uint32_t op_base = smem_base + kRawStages * kRawBytes;
+// ---------------- range planning ----------------
+// k_part_mma's ranges cut the kept rows at equal shares of their cost: a row
+// costs 1 and a group of more than 32 rows kGroupCost more, at its first row,
+// so that a range of many mid-size groups holds fewer rows than one inside a
+// heavy group.  Three launches: the cost of every tile of kTileGroups groups;
+// their exclusive sums, the total and the plan (one block); the cuts.
 
-    if (tid == 0) {
-        for (int r = 0; r < kRawStages; r++) {
-            mbar_init(&sh.raw_full[r], 1);
-            mbar_init(&sh.raw_empty[r], kProdWarps + 1);  // the producers and the classifier
-            mbar_init(&sh.cls_full[r], 1);
-        }
-        for (int s = 0; s < kOpStages; s++) {
-            mbar_init(&sh.full[s], kProdWarps);
-            mbar_init(&sh.empty[s], 1);
-        }
-        for (int k = 0; k < kSlots; k++) {
-            mbar_init(&sh.done[k], 2);  // the issuer's commit and its arrive with the group's record
-            mbar_init(&sh.freeb[k], p.bal ? 3 : 4);  // the epilogue set's warps that read the slot
-            mbar_init(&sh.tot_ready[k], 1);
-        }
-        mbar_init(&sh.drain, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        sh.abort_flag = 0;
-        const uint32_t G = p.in.n_groups;
-        const uint64_t kept = p.pcnt[G];
-        const uint64_t lo = min(static_cast<uint64_t>(cta) * p.rows_per_cta, kept);
-        const uint64_t hi = min(lo + p.rows_per_cta, kept);
-        sh.lo = static_cast<uint32_t>(lo);
-        sh.hi = static_cast<uint32_t>(hi);
-        // groups crossing the range's edges: partial records when they are
-        // tensor-core groups (more than 32 rows in all); chunk 0 sees the one
-        // crossing the left edge as a group begun earlier
-        const GidView pg{p.rec, p.sgid, p.packed != 0};
-        const uint32_t g_lo = lo < hi ? pg[lo] : kNone;
-        const bool cont_lo = lo < hi && lo > 0 && pg[lo - 1] == g_lo;
-        const bool big_lo = cont_lo && p.pcnt[g_lo] > 32;
-        sh.split_lo = big_lo ? g_lo : kNone;
-        sh.prev_gid0 = cont_lo ? g_lo : kNone;
-        sh.prev_cls0 = (cont_lo && !big_lo) ? kClsSkip : kClsMma;
-        const uint32_t g_hi = lo < hi ? pg[hi - 1] : kNone;
-        const bool cont_hi = lo < hi && hi < kept && pg[hi] == g_hi;
-        sh.split_hi = (cont_hi && p.pcnt[g_hi] > 32) ? g_hi : kNone;
-    }
-    if (warp == kEpiWarp0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_slot)),
-                     "r"(512));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = sh.tmem_slot;
-    // A rows start as zeros, with the constant world byte of balanced keys:
-    // accumulator row 32 (upper half, first byte) counts every row, so it
-    // becomes the group's total (worlds 32..63 are total - worlds 0..31)
-    for (uint32_t i = static_cast<uint32_t>(tid); i < kOpStages * kChunk; i += blockDim.x) {
-        const uint32_t st = i / kChunk, r = i % kChunk;
-        const uint32_t a_row = op_base + st * kOpBytes + (r >> 3) * 512 + (r & 7) * 16;
+__device__ __forceinline__ unsigned long long group_cost(uint32_t n) {
+    return static_cast<unsigned long long>(n) + (n > 32 ? kGroupCost : 0u);
+}
+
+// Exclusive sum over the block of one value per thread (kPlanThreads or
+// 1024 threads); *total = the block's sum.  Every thread of the block calls it.
+template <int T>
+__device__ __forceinline__ unsigned long long block_exclusive(unsigned long long v, unsigned long long *total) {
+    __shared__ unsigned long long wsum[T / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
 #pragma unroll
-        for (int k = 0; k < 4; k++) sts128(a_row + 128 * k, (p.bal && k == 2) ? 1u : 0u, 0u, 0u, 0u);
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
     }
-    for (int i = tid; i < kInfo; i += blockDim.x) {
-        sh.meta_or[i] = 0;
-        sh.meta_cnt[i] = 0;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (w == 0) {
+        unsigned long long s = lane < T / 32 ? wsum[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < T / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long before = (w ? wsum[w - 1] : 0ull) + x - v;
+    *total = wsum[T / 32 - 1];
+    __syncthreads();  // wsum is reused by the next call
+    return before;
+}
 
+// block b: the cost of groups [b kTileGroups, (b + 1) kTileGroups)
+__global__ void __launch_bounds__(kPlanThreads) k_range_tiles(const __grid_constant__ PartMmaParams p) {
+    const uint64_t G = p.in.n_groups;
+    const uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * kTileGroups, g1 = min(g0 + kTileGroups, G);
+    unsigned long long c = 0;
+    for (uint64_t g = g0 + threadIdx.x; g < g1; g += kPlanThreads) c += group_cost(p.pcnt[g]);
+    unsigned long long tot;
+    block_exclusive<kPlanThreads>(c, &tot);
+    if (threadIdx.x == 0) p.tile[blockIdx.x] = tot;
+}
+
+// One block: the tiles' exclusive sums (in place), the total cost, the plan:
+// R = a multiple of the SM count with shares of at most kRangeCost (fewer
+// when the rows are few), share = ceil(total / R); cuts at or past the total
+// are the end of the kept rows.
+__global__ void __launch_bounds__(1024) k_range_plan(const __grid_constant__ PartMmaParams p, uint32_t n_tiles,
+                                                     uint32_t n_sms) {
+    __shared__ unsigned long long s_total, s_share;
+    __shared__ uint32_t s_r;
+    unsigned long long running = 0;
+    for (uint32_t base = 0; base < n_tiles; base += 1024) {
+        const uint32_t t = base + threadIdx.x;
+        const unsigned long long v = t < n_tiles ? p.tile[t] : 0ull;
+        unsigned long long tot;
+        const unsigned long long before = block_exclusive<1024>(v, &tot);
+        if (t < n_tiles) p.tile[t] = running + before;
+        running += tot;
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = running;
+        const unsigned long long per_wave = static_cast<unsigned long long>(n_sms) * kRangeCost;
+        unsigned long long r = static_cast<unsigned long long>(n_sms) * max(1ull, (total + per_wave - 1) / per_wave);
+        r = min(r, max(1ull, (total + kMinRangeCost - 1) / kMinRangeCost));
+        r = min(r, static_cast<unsigned long long>(p.r_max));
+        const unsigned long long share = max(1ull, (total + r - 1) / r);
+        p.plan->total = total;
+        p.plan->share = share;
+        p.plan->n_ranges = static_cast<uint32_t>(r);
+        p.plan->next = 0;
+        p.range_lo[0] = 0;
+        s_total = total;
+        s_share = share;
+        s_r = static_cast<uint32_t>(r);
+    }
+    __syncthreads();
+    const uint32_t kept = p.pcnt[p.in.n_groups];
+    for (uint32_t j = 1 + threadIdx.x; j <= s_r; j += 1024)
+        if (static_cast<unsigned long long>(j) * s_share >= s_total) p.range_lo[j] = kept;
+}
+
+// block b: the cuts that fall in tile b's groups.  Cut j (0 < j < R) sits at
+// cost j share; inside group g (cost interval [c0, c1)) it is the group's
+// first row while in the group's extra cost, else the row that many units
+// further, rounded down to a chunk boundary.
+__global__ void __launch_bounds__(kPlanThreads) k_range_cuts(const __grid_constant__ PartMmaParams p) {
+    constexpr int kPer = kTileGroups / kPlanThreads;
+    __shared__ uint32_t cnt_s[kTileGroups];
+    const uint64_t G = p.in.n_groups;
+    const uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * kTileGroups;
+    for (uint32_t i = threadIdx.x; i < kTileGroups; i += kPlanThreads)
+        cnt_s[i] = g0 + i < G ? p.pcnt[g0 + i] : 0u;
+    __syncthreads();
+    unsigned long long c = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) c += group_cost(cnt_s[kPer * threadIdx.x + k]);
+    unsigned long long tot;
+    unsigned long long c0 = p.tile[blockIdx.x] + block_exclusive<kPlanThreads>(c, &tot);
+    const unsigned long long share = p.plan->share;
+    const uint32_t R = p.plan->n_ranges;
+    for (int k = 0; k < kPer; k++) {
+        const uint64_t g = g0 + kPer * threadIdx.x + k;
+        if (g >= G) break;
+        const uint32_t n = cnt_s[kPer * threadIdx.x + k];
+        const unsigned long long c1 = c0 + group_cost(n);
+        if (n) {
+            const uint32_t extra = n > 32 ? kGroupCost : 0u;
+            const uint32_t start = p.pend[g] - n;
+            for (unsigned long long j = max(1ull, (c0 + share - 1) / share); j < R && j * share < c1; j++) {
+                const unsigned long long o = j * share - c0;
+                const uint32_t r = o < extra ? 0u : static_cast<uint32_t>(o - extra);
+                p.range_lo[j] = (start + r) / kChunk * kChunk;
+            }
+        }
+        c0 = c1;
+    }
+}
+
+// Re-arms the barriers and reads range sh.range's ends and edge groups (one
+// thread).  Every barrier is idle here: each wait of the previous range has
+// returned, and every copy and MMA that range issued is complete (the loader
+// and the issuer wait for their last completions before the range ends).
+__device__ __forceinline__ void begin_range(const PartMmaParams &p, PartShared &sh, bool rearm) {
+    auto arm = [&](uint64_t *bar, uint32_t count) {
+        if (rearm) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+        mbar_init(bar, count);
+    };
+    for (int r = 0; r < kRawStages; r++) {
+        arm(&sh.raw_full[r], 1);
+        arm(&sh.raw_empty[r], kProdWarps + 1);  // the producers and the classifier
+        arm(&sh.cls_full[r], 1);
+    }
+    for (int s = 0; s < kOpStages; s++) {
+        arm(&sh.full[s], kProdWarps);
+        arm(&sh.empty[s], 1);
+    }
+    for (int k = 0; k < kSlots; k++) {
+        arm(&sh.done[k], 2);                // the issuer's commit and its arrive with the group's record
+        arm(&sh.freeb[k], p.bal ? 3 : 4);   // the epilogue set's warps that read the slot
+        arm(&sh.tot_ready[k], 1);
+    }
+    arm(&sh.drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    const uint32_t rng = sh.range;
+    const uint32_t G = p.in.n_groups;
+    const uint32_t kept = p.pcnt[G];
+    const uint32_t lo = min(p.range_lo[rng], kept);
+    const uint32_t hi = max(lo, min(p.range_lo[rng + 1], kept));
+    sh.lo = lo;
+    sh.hi = hi;
+    // groups crossing the range's edges: partial records when they are
+    // tensor-core groups (more than 32 rows in all); chunk 0 sees the one
+    // crossing the left edge as a group begun earlier
+    const GidView pg{p.rec, p.sgid, p.packed != 0};
+    const uint32_t g_lo = lo < hi ? pg[lo] : kNone;
+    const bool cont_lo = lo < hi && lo > 0 && pg[lo - 1] == g_lo;
+    const bool big_lo = cont_lo && p.pcnt[g_lo] > 32;
+    sh.split_lo = big_lo ? g_lo : kNone;
+    sh.prev_gid0 = cont_lo ? g_lo : kNone;
+    sh.prev_cls0 = (cont_lo && !big_lo) ? kClsSkip : kClsMma;
+    const uint32_t g_hi = lo < hi ? pg[hi - 1] : kNone;
+    const bool cont_hi = lo < hi && hi < kept && pg[hi] == g_hi;
+    sh.split_hi = (cont_hi && p.pcnt[g_hi] > 32) ? g_hi : kNone;
+    p.part[2 * static_cast<size_t>(rng)].used = 0;
+    p.part[2 * static_cast<size_t>(rng) + 1].used = 0;
+}
+
+// One range [sh.lo, sh.hi) of the group order on the whole CTA: the warp roles.
+__device__ __forceinline__ void part_range(const PartMmaParams &p, PartShared &sh, unsigned char *smem,
+                                           uint32_t raw_base, uint32_t op_base, uint32_t tmem, uint32_t rng) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lo = sh.lo, hi = sh.hi;
     const uint32_t n_chunks = (hi - lo + kChunk - 1) / kChunk;
     volatile int *abort_v = &sh.abort_flag;
@@ -705,6 +832,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
         {
             int k = -1;  // ordinal of the current group
             uint32_t cur = kNone, n_acc = 0, n_mma = 0;
+            uint32_t n_committed = 0;  // chunks whose stage commit is issued
             int gave_up = 0;
             auto close = [&](int kk) {
                 if (lane == 0) {
@@ -798,6 +926,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                 if (lane == 0)
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         smem_u32(&sh.empty[s])));
+                n_committed = i + 1;
             }
             if (gave_up) {
                 if (lane == 0) *abort_v = 1;
@@ -820,11 +949,15 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
                     }
                 }
             }
-            // every MMA issued is complete before tensor memory is read or freed
+            // every MMA issued is complete before tensor memory is read or
+            // freed, and the last stage commits have arrived before the
+            // barriers are re-armed for the next range
             if (lane == 0) {
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&sh.drain)));
                 if (!mbar_wait(&sh.drain, 0, kWaitNs)) *abort_v = 1;
+                for (uint32_t i = n_committed > kOpStages ? n_committed - kOpStages : 0; i < n_committed; i++)
+                    if (!mbar_wait(&sh.empty[i % kOpStages], (i / kOpStages) & 1, kWaitNs)) *abort_v = 1;
             }
         }
         __syncwarp();
@@ -894,7 +1027,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             }
             if (split) {
                 const int side = (k == 0 && oi.gid == sh.split_lo) ? 0 : 1;
-                PartRec &pr = p.part[2 * static_cast<size_t>(cta) + side];
+                PartRec &pr = p.part[2 * static_cast<size_t>(rng) + side];
                 if (lane < 16) {
 #pragma unroll
                     for (int f = 0; f < kFeat; f++) pr.d[m][f] = d[f];
@@ -936,20 +1069,72 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
             }
         }
     }
+}
+
+// One CTA per SM, persistent: the CTAs take the ranges one at a time, the
+// last range of the group order first (many small groups, the most output
+// per row), until none is left.
+__global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant__ PartMmaParams p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ PartShared sh;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t smem_base = smem_u32(smem);
+    const uint32_t raw_base = smem_base;
+    const uint32_t op_base = smem_base + kRawStages * kRawBytes;
+    if (tid == 0) sh.abort_flag = 0;
+    if (warp == kEpiWarp0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // A rows start as zeros, with the constant world byte of balanced keys:
+    // accumulator row 32 (upper half, first byte) counts every row, so it
+    // becomes the group's total (worlds 32..63 are total - worlds 0..31)
+    for (uint32_t i = static_cast<uint32_t>(tid); i < kOpStages * kChunk; i += blockDim.x) {
+        const uint32_t st = i / kChunk, r = i % kChunk;
+        const uint32_t a_row = op_base + st * kOpBytes + (r >> 3) * 512 + (r & 7) * 16;
+#pragma unroll
+        for (int k = 0; k < 4; k++) sts128(a_row + 128 * k, (p.bal && k == 2) ? 1u : 0u, 0u, 0u, 0u);
+    }
+    for (int i = tid; i < kInfo; i += blockDim.x) {
+        sh.meta_or[i] = 0;
+        sh.meta_cnt[i] = 0;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = sh.tmem_slot;
+    for (bool rearm = false;; rearm = true) {
+        if (tid == 0) {
+            const uint32_t n_r = p.plan->n_ranges;
+            const uint32_t j = sh.abort_flag ? n_r : atomicAdd(&p.plan->next, 1u);
+            sh.range = j < n_r ? n_r - 1 - j : kNone;
+            if (sh.range != kNone) begin_range(p, sh, rearm);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t rng = sh.range;
+        if (rng == kNone) break;
+        part_range(p, sh, smem, raw_base, op_base, tmem, rng);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
     if (tid == 0 && sh.abort_flag) raise_status(p.status, kStatusTimeout);
     if (warp == kEpiWarp0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// Groups that cross a CTA edge: one CTA per partial record; the first record
-// of a group (in CTA order) adds up its group's records and writes the
-// results.  Thread m (of 64) = accumulator row m.
-__global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartMmaParams p, uint32_t n_recs) {
+// Groups that cross a range edge: one CTA per partial record; the first
+// record of a group (in range order) adds up its group's records and writes
+// the results.  Thread m (of 64) = accumulator row m.
+__global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartMmaParams p) {
     __shared__ long long tot[kFeat];
     __shared__ unsigned long long orw[2];
+    const uint32_t n_recs = 2 * p.plan->n_ranges;
     const uint32_t r0 = blockIdx.x;
+    if (r0 >= n_recs) return;
     const PartRec &first = p.part[r0];
     if (!first.used) return;
     const uint32_t g = first.gid;
@@ -1050,12 +1235,33 @@ __global__ void __launch_bounds__(256) k_part_small(const __grid_constant__ Part
     }
 }
 
-uint32_t part_rows_per_cta(uint64_t n, int n_sms) {
-    uint64_t per = (n + n_sms - 1) / n_sms;
-    per = (per + kChunk - 1) / kChunk * kChunk;
-    if (per > kMaxRowsPerCtaP) per = kMaxRowsPerCtaP;
-    if (per == 0) per = kChunk;
-    return static_cast<uint32_t>(per);
+// R at most: the kept rows' cost is at most n + kGroupCost x min(G, n / 33)
+// (a group of more than 32 rows holds at least 33 of them), and the plan
+// takes the fewest whole waves of SM-count ranges with shares of at most
+// kRangeCost.
+uint32_t part_r_max(uint64_t n, uint64_t G, int n_sms) {
+    const uint64_t cmax = n + kGroupCost * std::min<uint64_t>(G, n / 33);
+    const uint64_t per_wave = static_cast<uint64_t>(n_sms) * kRangeCost;
+    return static_cast<uint32_t>(static_cast<uint64_t>(n_sms) * std::max<uint64_t>(1, (cmax + per_wave - 1) / per_wave));
+}
+
+uint32_t part_n_tiles(uint64_t G) { return static_cast<uint32_t>(std::max<uint64_t>(1, (G + kTileGroups - 1) / kTileGroups)); }
+
+// The scratch: partial records [r_max][2], the plan, the cuts [r_max + 1],
+// the tile sums.
+struct PartScratch {
+    size_t plan, cuts, tiles, bytes;
+};
+
+PartScratch part_scratch_layout(uint64_t n, uint64_t G, int n_sms) {
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const uint64_t r_max = part_r_max(n, G, n_sms);
+    PartScratch l;
+    l.plan = up(static_cast<size_t>(2 * r_max) * sizeof(PartRec));
+    l.cuts = up(l.plan + sizeof(RangePlan));
+    l.tiles = up(l.cuts + static_cast<size_t>(r_max + 1) * sizeof(uint32_t));
+    l.bytes = l.tiles + static_cast<size_t>(part_n_tiles(G)) * sizeof(unsigned long long);
+    return l;
 }
 
 }  // namespace
@@ -1075,10 +1281,8 @@ bool part_mma_specs_served(const pac_agg_spec *specs, int n_specs) {
     return true;
 }
 
-size_t part_mma_scratch_bytes(uint64_t n, int n_sms) {
-    const uint64_t per = part_rows_per_cta(n, n_sms);
-    const uint64_t grid = n == 0 ? 1 : (n + per - 1) / per;
-    return static_cast<size_t>(grid) * 2 * sizeof(PartRec);
+size_t part_mma_scratch_bytes(uint64_t n, uint32_t n_groups, int n_sms) {
+    return part_scratch_layout(n, n_groups, n_sms).bytes;
 }
 
 pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launches, const char **why) {
@@ -1089,7 +1293,6 @@ pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launc
     p.packed = a.packed;
     p.pcnt = a.pcnt;
     p.pend = a.pend;
-    p.rows_per_cta = part_rows_per_cta(a.in.n, a.n_sms);
     p.bal = !(a.in.in_flags & PAC_IN_MASKS) && a.in.hash_mode == PAC_HASH_BALANCED;
     p.has_col = 0;
     for (int i = 0; i < a.n_specs; i++) {
@@ -1099,17 +1302,25 @@ pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launc
     }
     p.n_out = a.n_specs;
     p.meta = a.meta;
-    p.part = static_cast<PartRec *>(a.scratch);
+    const PartScratch l = part_scratch_layout(a.in.n, a.in.n_groups, a.n_sms);
+    char *scratch = static_cast<char *>(a.scratch);
+    p.part = reinterpret_cast<PartRec *>(scratch);
+    p.plan = reinterpret_cast<RangePlan *>(scratch + l.plan);
+    p.range_lo = reinterpret_cast<uint32_t *>(scratch + l.cuts);
+    p.tile = reinterpret_cast<unsigned long long *>(scratch + l.tiles);
+    p.r_max = part_r_max(a.in.n, a.in.n_groups, a.n_sms);
     p.status = a.status;
     p.wait_ns = a.wait_ns ? a.wait_ns : kWaitNs;
-    const uint64_t grid = a.in.n == 0 ? 1 : (a.in.n + p.rows_per_cta - 1) / p.rows_per_cta;
-    const size_t part_bytes = static_cast<size_t>(grid) * 2 * sizeof(PartRec);
-    cudaError_t e = cudaMemsetAsync(a.scratch, 0, part_bytes, stream);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_part_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemP));
+    const uint32_t n_tiles = part_n_tiles(a.in.n_groups);
+    cudaError_t e = cudaFuncSetAttribute(k_part_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemP));
     if (e == cudaSuccess) {
-        k_part_mma<<<static_cast<unsigned>(grid), kThreadsP, kSmemP, stream>>>(p);
-        k_part_merge<<<static_cast<unsigned>(2 * grid), 64, 0, stream>>>(p, static_cast<uint32_t>(2 * grid));
+        k_range_tiles<<<n_tiles, kPlanThreads, 0, stream>>>(p);
+        k_range_plan<<<1, 1024, 0, stream>>>(p, n_tiles, static_cast<uint32_t>(a.n_sms));
+        k_range_cuts<<<n_tiles, kPlanThreads, 0, stream>>>(p);
+        // one persistent CTA per SM (tensor memory and shared memory admit one)
+        k_part_mma<<<static_cast<unsigned>(std::min<uint32_t>(static_cast<uint32_t>(a.n_sms), p.r_max)), kThreadsP,
+                     kSmemP, stream>>>(p);
+        k_part_merge<<<2 * p.r_max, 64, 0, stream>>>(p);
         // one warp per 32 groups, 8 warps per block
         k_part_small<<<static_cast<unsigned>((static_cast<uint64_t>(a.in.n_groups) + 255) / 256), 256, 0,
                        stream>>>(p);
@@ -1119,7 +1330,7 @@ pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launc
         *why = cudaGetErrorString(e);
         return PAC_E_CUDA;
     }
-    *launches += 3;
+    *launches += 6;
     return PAC_OK;
 }
 

@@ -32,7 +32,7 @@ struct PartMmaArgs {
 };
 
 bool part_mma_specs_served(const pac_agg_spec *specs, int n_specs);
-size_t part_mma_scratch_bytes(uint64_t n, int n_sms);
+size_t part_mma_scratch_bytes(uint64_t n, uint32_t n_groups, int n_sms);
 pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launches, const char **why);
 
 }  // namespace pacgpu

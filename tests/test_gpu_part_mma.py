@@ -2,13 +2,15 @@
 partitioned into group order, then aggregated over the group-ordered rows --
 groups of more than 32 rows by tcgen05 MMAs, groups of at most 32 rows by one
 warp each (also across 32-row block and 512-row chunk edges), groups crossing
-a CTA edge merged from partial records.
+a range edge merged from partial records.  The ranges are cut at equal
+shares of the rows' cost (a row costs 1, a group of more than 32 rows a fixed
+amount more), inside heavy groups and at the starts of mid-size ones.
 
 Bar: bit-exact against the oracle (COUNT, exact int64 SUM, AVG and the
 metadata) and against the per-bit engine (agg_path 3), over group-size mixes
-(one heavy group across many CTAs, Zipf, groups of one to three rows, empty
+(one heavy group across many ranges, Zipf, groups of one to three rows, empty
 groups), value magnitudes and signs, key or mask input, both hash modes,
-dropped rows, ragged row counts and CTA edges.
+dropped rows, ragged row counts and range edges.
 """
 import numpy as np
 import pytest
@@ -71,9 +73,10 @@ def test_part_shapes(ctx, G, n):
     _check(ctx, keys, gids, G, _specs(v), masks, qkey=qk)
 
 
-def test_part_zipf_heavy_groups_across_ctas(ctx):
-    # 3M rows on every SM: ~20K rows per CTA, the top group (~12 % of the
-    # rows) spans many CTAs, the next ones cross CTA edges, the tail is tiny
+def test_part_zipf_heavy_groups_across_ranges(ctx):
+    # 3M rows: one range per SM (~20K rows' cost each), the top group (~12 %
+    # of the rows) spans many ranges, the next ones cross range edges, the
+    # tail is tiny
     n = 3_000_017
     G = 100_000
     gids = inputs.zipf_groups(5, 0, n, G)
@@ -81,6 +84,24 @@ def test_part_zipf_heavy_groups_across_ctas(ctx):
     keys = r.integers(0, 1_000_000, n).astype(np.int64)
     v = inputs.lognormal_i64(5, 2, n, 8.0, 2.0, 1 << 40)
     qk = orc.query_key(5)
+    masks = orc.hash_keys(keys, qk, orc.BALANCED)
+    _check(ctx, keys, gids, G, _specs(v), masks, qkey=qk)
+
+
+@pytest.mark.parametrize("mid", [33, 64, 200])
+def test_part_cost_balanced_ranges(ctx, mid):
+    # one group of 1.5M rows (cut into several ranges inside it), then groups
+    # of `mid` rows (each adds a fixed cost: the ranges there hold fewer rows,
+    # cut at group starts and inside groups), then 20K groups of 1 to 32 rows
+    r = np.random.default_rng(mid)
+    sizes = np.concatenate([[1_500_000], np.full(1_200_000 // mid, mid), r.integers(1, 33, 20_000)])
+    G = sizes.size
+    gids = np.repeat(np.arange(G, dtype=np.int32), sizes)
+    r.shuffle(gids)  # the partition restores the group order
+    n = gids.size
+    keys = r.integers(0, n // 3, n).astype(np.int64)
+    v = r.integers(-10**9, 10**9, n).astype(np.int64)
+    qk = orc.query_key(mid)
     masks = orc.hash_keys(keys, qk, orc.BALANCED)
     _check(ctx, keys, gids, G, _specs(v), masks, qkey=qk)
 
@@ -187,7 +208,7 @@ def test_part_count_only(ctx):
 def test_part_overflow_reported_avg_exact(ctx):
     """A world SUM beyond int64 is reported; the SUM is saturated and the AVG
     is the exact 128-bit total over the count (the oracle's reading), in
-    groups summed by the tensor cores, by the warp and across CTAs."""
+    groups summed by the tensor cores, by the warp and across ranges."""
     n = 200_000
     G = 800
     r = np.random.default_rng(12)
