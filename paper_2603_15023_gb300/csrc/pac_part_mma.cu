@@ -881,46 +881,73 @@ __device__ __forceinline__ void part_range(const PartMmaParams &p, PartShared &s
                 const uint32_t pm = __ballot_sync(kFull, pvld);
                 const uint32_t gid_l = pvld ? prl.gid : kNone;
                 const uint32_t n_l = pvld ? prl.n : 0u;
-                // group starts: a valid pair whose group differs from the previous valid pair's
-                int pv_idx = pvld ? lane : -1;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, pv_idx, o);
-                    if (lane >= o) pv_idx = max(pv_idx, y);
-                }
-                int prev_valid = __shfl_up_sync(kFull, pv_idx, 1);
-                if (lane == 0) prev_valid = -1;
-                const uint32_t gprev = __shfl_sync(kFull, gid_l, prev_valid < 0 ? 0 : prev_valid);
-                const uint32_t ng = __ballot_sync(kFull, pvld && gid_l != (prev_valid < 0 ? cur : gprev));
-                // segments of one group, issued back to back
-                for (uint32_t rest = pm; rest;) {
-                    const int p0 = __ffs(static_cast<int>(rest)) - 1;
-                    if ((ng >> p0) & 1u) {
-                        if (k >= 0) close(k);
-                        k++;
-                        if (!take_slot(k)) {
-                            gave_up = 1;
-                            break;
-                        }
-                        cur = __shfl_sync(kFull, gid_l, p0);
-                        n_acc = 0;
-                        n_mma = 0;
-                    }
-                    // the segment: valid pairs from p0 up to the next group start
-                    const uint32_t after = ng & ~((2u << p0) - 1u) & ~(p0 == 31 ? 0xFFFFFFFFu : 0u);
-                    const uint32_t seg = after ? (rest & ((1u << (__ffs(static_cast<int>(after)) - 1)) - 1u)) : rest;
-                    rest &= ~seg;
-                    n_acc += __reduce_add_sync(kFull, ((seg >> lane) & 1u) ? n_l : 0u);
+                // Inside a heavy group every valid pair continues the current
+                // group: one vote, then the pairs' MMAs, with no group-start
+                // scan or segment walk (a chunk of single-run blocks, pairs 0,
+                // 2, .., 30, fully unrolled)
+                const bool cont = k >= 0 && __all_sync(kFull, !pvld || gid_l == cur);
+                if (cont) {
+                    n_acc += __reduce_add_sync(kFull, n_l);
                     const uint32_t dacc = tmem + static_cast<uint32_t>(k % kSlots) * kAlloc;
-                    if (lane == 0) {
-                        uint32_t acc = n_mma != 0 ? 1u : 0u;  // the group's first MMA overwrites its slot
-                        for (uint32_t q = seg; q; q &= q - 1) {
-                            const uint32_t pi = static_cast<uint32_t>(__ffs(static_cast<int>(q)) - 1);
-                            mma_f8_acc(dacc, da0 + ((pi >> 1) << 7), db0 + (pi << 6), idesc, acc);
-                            acc = 1u;
+                    if (lane == 0 && pm) {
+                        uint32_t acc = n_mma != 0 ? 1u : 0u;
+                        if (pm == 0x55555555u) {
+#pragma unroll
+                            for (uint32_t b = 0; b < kBlocks; b++) {  // pair 2b: A block b, B copy 2b
+                                mma_f8_acc(dacc, da0 + (b << 7), db0 + (b << 7), idesc, acc);
+                                acc = 1u;
+                            }
+                        } else {
+                            for (uint32_t q = pm; q; q &= q - 1) {
+                                const uint32_t pi = static_cast<uint32_t>(__ffs(static_cast<int>(q)) - 1);
+                                mma_f8_acc(dacc, da0 + ((pi >> 1) << 7), db0 + (pi << 6), idesc, acc);
+                                acc = 1u;
+                            }
                         }
                     }
-                    n_mma += static_cast<uint32_t>(__popc(seg));
+                    n_mma += static_cast<uint32_t>(__popc(pm));
+                } else {
+                    // group starts: a valid pair whose group differs from the previous valid pair's
+                    int pv_idx = pvld ? lane : -1;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(kFull, pv_idx, o);
+                        if (lane >= o) pv_idx = max(pv_idx, y);
+                    }
+                    int prev_valid = __shfl_up_sync(kFull, pv_idx, 1);
+                    if (lane == 0) prev_valid = -1;
+                    const uint32_t gprev = __shfl_sync(kFull, gid_l, prev_valid < 0 ? 0 : prev_valid);
+                    const uint32_t ng = __ballot_sync(kFull, pvld && gid_l != (prev_valid < 0 ? cur : gprev));
+                    // segments of one group, issued back to back
+                    for (uint32_t rest = pm; rest;) {
+                        const int p0 = __ffs(static_cast<int>(rest)) - 1;
+                        if ((ng >> p0) & 1u) {
+                            if (k >= 0) close(k);
+                            k++;
+                            if (!take_slot(k)) {
+                                gave_up = 1;
+                                break;
+                            }
+                            cur = __shfl_sync(kFull, gid_l, p0);
+                            n_acc = 0;
+                            n_mma = 0;
+                        }
+                        // the segment: valid pairs from p0 up to the next group start
+                        const uint32_t after = ng & ~((2u << p0) - 1u) & ~(p0 == 31 ? 0xFFFFFFFFu : 0u);
+                        const uint32_t seg = after ? (rest & ((1u << (__ffs(static_cast<int>(after)) - 1)) - 1u)) : rest;
+                        rest &= ~seg;
+                        n_acc += __reduce_add_sync(kFull, ((seg >> lane) & 1u) ? n_l : 0u);
+                        const uint32_t dacc = tmem + static_cast<uint32_t>(k % kSlots) * kAlloc;
+                        if (lane == 0) {
+                            uint32_t acc = n_mma != 0 ? 1u : 0u;  // the group's first MMA overwrites its slot
+                            for (uint32_t q = seg; q; q &= q - 1) {
+                                const uint32_t pi = static_cast<uint32_t>(__ffs(static_cast<int>(q)) - 1);
+                                mma_f8_acc(dacc, da0 + ((pi >> 1) << 7), db0 + (pi << 6), idesc, acc);
+                                acc = 1u;
+                            }
+                        }
+                        n_mma += static_cast<uint32_t>(__popc(seg));
+                    }
                 }
                 if (gave_up) break;
                 if (lane == 0)
