@@ -1153,63 +1153,101 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_part_mma(const __grid_constant
     if (warp == kEpiWarp0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// Groups that cross a range edge: one CTA per partial record; the first
-// record of a group (in range order) adds up its group's records and writes
-// the results.  Thread m (of 64) = accumulator row m.
-__global__ void __launch_bounds__(64) k_part_merge(const __grid_constant__ PartMmaParams p) {
+// Groups that cross a range edge: the first record of a group (in range
+// order) adds up the group's records and writes the results.  A block takes
+// the records blockIdx.x, blockIdx.x + gridDim.x, ...; thread t is accumulator
+// row t % 64 of slice t / 64, and the slices sum every kMergeSlices-th record
+// of the group (a heavy group spans hundreds of ranges: one thread walking
+// them in turn would wait out one memory latency per record).
+constexpr int kMergeSlices = 4;
+
+__global__ void __launch_bounds__(64 * kMergeSlices) k_part_merge(const __grid_constant__ PartMmaParams p) {
+    __shared__ long long part_s[kMergeSlices - 1][64][kFeat];
+    __shared__ unsigned long long n_s[kMergeSlices - 1];
     __shared__ long long tot[kFeat];
     __shared__ unsigned long long orw[2];
+    __shared__ uint32_t end_s;
     const uint32_t n_recs = 2 * p.plan->n_ranges;
-    const uint32_t r0 = blockIdx.x;
-    if (r0 >= n_recs) return;
-    const PartRec &first = p.part[r0];
-    if (!first.used) return;
-    const uint32_t g = first.gid;
-    for (uint32_t j = r0; j-- > 0;) {
-        if (!p.part[j].used) continue;
-        if (p.part[j].gid == g) return;  // not the group's first record
-        break;
-    }
-    const int m = threadIdx.x;
-    long long d[kFeat];
-#pragma unroll
-    for (int f = 0; f < kFeat; f++) d[f] = 0;
-    unsigned long long n = 0;
-    for (uint32_t j = r0; j < n_recs; j++) {
-        const PartRec &pr = p.part[j];
-        if (!pr.used) continue;
-        if (pr.gid != g) break;
-#pragma unroll
-        for (int f = 0; f < kFeat; f++) d[f] += pr.d[m][f];
-        n += pr.n;
-    }
-    // balanced keys: row 32 is the group total
-    if (m == 32) {
-#pragma unroll
-        for (int f = 0; f < kFeat; f++) tot[f] = d[f];
-    }
-    __syncthreads();
-    unsigned long long bits = 0;
-    if (!p.bal || m < 32) {
-        const int w = world_of_row(m);
-        const __int128 sw = digits_to_sum_wide(d);
-        emit_world(p, g, w, static_cast<unsigned long long>(d[0]), sw);
-        bits = (d[0] > 0 ? 1ull : 0ull) << w;
-        if (p.bal) {
-            long long dc[kFeat];
-#pragma unroll
-            for (int f = 0; f < kFeat; f++) dc[f] = tot[f] - d[f];
-            emit_world(p, g, w + 32, static_cast<unsigned long long>(dc[0]), digits_to_sum_wide(dc));
-            bits |= (dc[0] > 0 ? 1ull : 0ull) << (w + 32);
+    const int m = threadIdx.x & 63, sl = threadIdx.x >> 6;
+    for (uint32_t r0 = blockIdx.x; r0 < n_recs; r0 += gridDim.x) {
+        const PartRec &first = p.part[r0];
+        if (!first.used) continue;
+        const uint32_t g = first.gid;
+        bool is_first = true;
+        for (uint32_t j = r0; j-- > 0;) {
+            if (!p.part[j].used) continue;
+            is_first = p.part[j].gid != g;
+            break;
         }
-    }
-    const uint32_t o_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(bits));
-    const uint32_t o_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(bits >> 32));
-    if ((m & 31) == 0) orw[m >> 5] = o_lo | (static_cast<unsigned long long>(o_hi) << 32);
-    __syncthreads();
-    if (m == 0 && p.meta) {
-        p.meta[2 * static_cast<size_t>(g)] = n;
-        p.meta[2 * static_cast<size_t>(g) + 1] = orw[0] | orw[1];
+        if (!is_first) continue;
+        // the group's records end at the first used record of another group
+        if (threadIdx.x == 0) end_s = n_recs;
+        __syncthreads();
+        for (uint32_t base = r0 + 1; base < n_recs; base += blockDim.x) {
+            const uint32_t j = base + threadIdx.x;
+            if (j < n_recs && p.part[j].used && p.part[j].gid != g) atomicMin(&end_s, j);
+            __syncthreads();
+            const uint32_t e = end_s;
+            __syncthreads();
+            if (e < base + blockDim.x) break;
+        }
+        const uint32_t end = end_s;
+        long long d[kFeat];
+#pragma unroll
+        for (int f = 0; f < kFeat; f++) d[f] = 0;
+        unsigned long long n = 0;
+        for (uint32_t j = r0 + sl; j < end; j += kMergeSlices) {
+            const PartRec &pr = p.part[j];
+            if (!pr.used) continue;  // a used record before `end` is of group g
+#pragma unroll
+            for (int f = 0; f < kFeat; f++) d[f] += pr.d[m][f];
+            n += pr.n;
+        }
+        if (sl > 0) {
+#pragma unroll
+            for (int f = 0; f < kFeat; f++) part_s[sl - 1][m][f] = d[f];
+            if (m == 0) n_s[sl - 1] = n;
+        }
+        __syncthreads();
+        if (sl == 0) {
+#pragma unroll
+            for (int t = 0; t < kMergeSlices - 1; t++) {
+#pragma unroll
+                for (int f = 0; f < kFeat; f++) d[f] += part_s[t][m][f];
+                n += n_s[t];
+            }
+            // balanced keys: row 32 is the group total
+            if (m == 32) {
+#pragma unroll
+                for (int f = 0; f < kFeat; f++) tot[f] = d[f];
+            }
+        }
+        __syncthreads();
+        if (sl == 0) {  // warps 0 and 1
+            unsigned long long bits = 0;
+            if (!p.bal || m < 32) {
+                const int w = world_of_row(m);
+                const __int128 sw = digits_to_sum_wide(d);
+                emit_world(p, g, w, static_cast<unsigned long long>(d[0]), sw);
+                bits = (d[0] > 0 ? 1ull : 0ull) << w;
+                if (p.bal) {
+                    long long dc[kFeat];
+#pragma unroll
+                    for (int f = 0; f < kFeat; f++) dc[f] = tot[f] - d[f];
+                    emit_world(p, g, w + 32, static_cast<unsigned long long>(dc[0]), digits_to_sum_wide(dc));
+                    bits |= (dc[0] > 0 ? 1ull : 0ull) << (w + 32);
+                }
+            }
+            const uint32_t o_lo = __reduce_or_sync(kFull, static_cast<uint32_t>(bits));
+            const uint32_t o_hi = __reduce_or_sync(kFull, static_cast<uint32_t>(bits >> 32));
+            if ((m & 31) == 0) orw[m >> 5] = o_lo | (static_cast<unsigned long long>(o_hi) << 32);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && p.meta) {
+            p.meta[2 * static_cast<size_t>(g)] = n;
+            p.meta[2 * static_cast<size_t>(g) + 1] = orw[0] | orw[1];
+        }
+        __syncthreads();  // the shared buffers are reused for the next record
     }
 }
 
@@ -1347,7 +1385,8 @@ pac_status part_mma_launch(const PartMmaArgs &a, cudaStream_t stream, int *launc
         // one persistent CTA per SM (tensor memory and shared memory admit one)
         k_part_mma<<<static_cast<unsigned>(std::min<uint32_t>(static_cast<uint32_t>(a.n_sms), p.r_max)), kThreadsP,
                      kSmemP, stream>>>(p);
-        k_part_merge<<<2 * p.r_max, 64, 0, stream>>>(p);
+        k_part_merge<<<std::min<uint32_t>(2 * p.r_max, 4u * static_cast<uint32_t>(a.n_sms)), 64 * kMergeSlices, 0,
+                       stream>>>(p);
         // one warp per 32 groups, 8 warps per block
         k_part_small<<<static_cast<unsigned>((static_cast<uint64_t>(a.in.n_groups) + 255) / 256), 256, 0,
                        stream>>>(p);
