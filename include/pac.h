@@ -568,8 +568,8 @@ pac_status pac_finalize128(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_sp
  *   into group order, then tensor-core sums over the group-ordered rows;
  *   COUNT and exact int64 SUM / AVG of one value column, any group count;
  *   PAC_E_UNSUPPORTED otherwise).  The automatic choice takes path 5 above
- *   64 groups when it can serve the query.  The one-launch path keeps its accumulators in the context,
- *   so calls on one context must not overlap.
+ *   64 groups when it can serve the query.  The one-launch path keeps its
+ *   accumulators in the context, so calls on one context must not overlap.
  *   "minmax_prune" 1 (default) = MIN/MAX bound pruning on the per-bit
  *   engine (Sec. 5 "Pruning": rows whose value improves no world's current
  *   extreme skip the update; results are identical), 0 = every row updated.
@@ -581,8 +581,8 @@ pac_status pac_finalize128(pac_ctx *ctx, const pac_agg_spec *specs, int32_t n_sp
  *   makes ordinary launches run out.  The kernel's final wait for its own
  *   tensor-core operations keeps the 2 s limit.
  *   pac_get_info(ctx, name, &value): "last_path" (1 plain per-bit, 2 tensor
- *   core, 3 per-bit engine, 4 one-launch, 5 many-group tensor core), "last_launches" kernels launched by the last
- *   call.
+ *   core, 3 per-bit engine, 4 one-launch, 5 many-group tensor core),
+ *   "last_launches" kernels launched by the last call.
  * ------------------------------------------------------------------------ */
 pac_status pac_set_option(pac_ctx *ctx, const char *name, int64_t value);
 pac_status pac_get_info(pac_ctx *ctx, const char *name, int64_t *value);
