@@ -2,39 +2,39 @@
 // groups (Sec. 4.2 "PAC Aggregation" on a high-cardinality GROUP BY).
 //
 // Input: the query's rows in group order, as the partition (histogram, scan,
-// scatter of pac_batch.cu) writes them: one 16-byte record {world mask,
-// value} and the group id of every row.  A group's rows are consecutive, so
-// the per-group contraction D_g = Bits_g^T * Digits_g of the tensor-core path
+// scatter of pac_batch.cu) writes them: one 16-byte record per row, packed
+// {low mask word | group id << 32, value} under balanced keys (the high mask
+// word is the complement of the low one), else {world mask, value} with the
+// group ids beside the records.  A group's rows are consecutive, so the
+// per-group contraction D_g = Bits_g^T * Digits_g of the tensor-core path
 // (E4M3 world bytes times E4M3 value digits, FP32 in tensor memory, exact:
 // see pac_mma.cu) needs no sort.
 //
-// Work split: CTA c takes the group-ordered rows [c R, (c+1) R), R a multiple
-// of 512 and at most 2^16 (many more CTAs than SMs, launched last range
-// first, so that ranges of many small groups -- the most output per row --
-// spread over the SMs).  Its rows arrive in 512-row chunks through bulk
-// asynchronous copies (cp.async.bulk, one elected thread) into a ring in
-// shared memory.  Each group is aggregated one of two ways:
-//   - a group of at most 32 rows (inside the CTA's range) by one warp:
-//     lane j holds world j's bits of the group's rows after a warp bit
-//     transpose; counts by popcount, sums exact in 128 bits.  Groups wholly
-//     inside a 32-row block share the block's transpose; a group that
-//     crosses a block or chunk edge is gathered into one warp (the chunk's
-//     last group is looked up in the next chunk, already in the ring);
-//   - a larger group, or one that crosses an edge of the CTA's range, by the
-//     tensor cores: one 32-row MMA per 32-row block it touches, with the
-//     block's world bytes as A and a B copy that holds the group's digits
+// Work split: three small kernels cut the kept rows into R ranges of equal
+// cost (a row costs 1, a group of more than 32 rows kGroupCost more), at most
+// 2^16 rows each; k_part_mma runs one persistent CTA per SM, which takes the
+// ranges one at a time from an atomic counter, the last range of the group
+// order first (many small groups, the most output per row).  A range's rows
+// arrive in 512-row chunks through bulk asynchronous copies (cp.async.bulk,
+// one elected thread) into a ring in shared memory.  Each group is
+// aggregated one of two ways:
+//   - a group of at most 32 rows by k_part_small (one warp per 32 groups;
+//     k_part_mma's classifier marks its rows to be skipped);
+//   - a larger group, or one of more than 32 rows that crosses a range edge,
+//     by the tensor cores: one 32-row MMA per 32-row block it touches, with
+//     the block's world bytes as A and a B copy that holds the group's digits
 //     and zeros in the block's other rows (at most two per block: such a
 //     group always holds the block's first or last row).
 // The MMAs of one group accumulate into one of sixteen tensor-memory slots (a
-// ring over the CTA's tensor-core groups in order; the group's first MMA
+// ring over the range's tensor-core groups in order; the group's first MMA
 // overwrites the slot, so a slot is never zeroed); the slot of a new group is
 // taken once the epilogue has read it out.  When a group's last MMA is done,
 // an epilogue warp set reads its slot and writes the group's COUNT/SUM/AVG
 // and metadata; two sets drain alternate groups, since one group's drain is a
 // chain of dependent latencies (tensor-memory load, conversion, the total's
-// hand-over, stores) far longer than its issue time.  A group that crosses an
-// edge of the CTA's range writes its digit totals as a partial record
-// instead; k_part_merge adds the partials of each such group in CTA order.
+// hand-over, stores) far longer than its issue time.  A group that crosses a
+// range edge writes its digit totals as a partial record instead;
+// k_part_merge adds the partials of each such group in range order.
 // No result is written with an atomic operation.
 //
 // Warps: 0-15 producers (block w of every chunk), 16-19 and 20-23 the two
@@ -42,7 +42,8 @@
 // loader, 25 MMA issuer, 26 classifier (each chunk's group starts and edge
 // classes, ahead of the producers, which then share no barrier).
 // Every wait is bounded (%globaltimer); a wait that gives up stops its warp's
-// work, the CTA drains what it has in flight and reports PAC_E_TIMEOUT.
+// work, the CTA drains what it has in flight, takes no further range and
+// reports PAC_E_TIMEOUT.
 #include <algorithm>
 #include <climits>
 
@@ -117,7 +118,7 @@ struct PairRec {
     uint8_t pad;
 };
 
-// A group of the CTA in MMA order (ordinal k at k % kInfo).
+// A tensor-core group of the range in MMA order (ordinal k at k % kInfo).
 struct OrdInfo {
     uint32_t gid;
     uint32_t n;
@@ -137,7 +138,7 @@ struct PartShared {
     int abort_flag;
     uint32_t range;          // the range in work (kNone: none left)
     uint32_t lo, hi;         // its rows [lo, hi)
-    uint32_t split_lo;       // group crossing the CTA's left edge, or kNone
+    uint32_t split_lo;       // group crossing the range's left edge, or kNone
     uint32_t split_hi;       // group crossing its right edge, or kNone
     uint64_t cls_full[kRawStages];   // classifier -> producers: the chunk in raw slot r is classified
     uint8_t ccls[kRawStages][kBlocks];  // per raw slot and block: first-row class | last-row class << 2
@@ -264,7 +265,7 @@ __device__ __forceinline__ __int128 digits_to_sum(const long long (&d)[kFeat]) {
     return static_cast<__int128>(lo) + (static_cast<__int128>(hi) << 32);
 }
 
-// The same for digit totals added over several CTAs (no bound on their size
+// The same for digit totals added over several ranges (no bound on their size
 // beyond int64): one 128-bit Horner chain.
 __device__ __forceinline__ __int128 digits_to_sum_wide(const long long (&d)[kFeat]) {
     __int128 t = 0;
@@ -814,7 +815,7 @@ __device__ __forceinline__ void part_range(const PartMmaParams &p, PartShared &s
                     bulk_g2s(raw_base + r * kRawBytes + kRawRecBytes, p.sgid + c0, rows4 * 4, &sh.raw_full[r]);
                 issued = i + 1;
             }
-            // every issued copy has landed before the CTA ends
+            // every issued copy has landed before the range ends
             for (uint32_t i = issued > kRawStages ? issued - kRawStages : 0; i < issued; i++)
                 if (!mbar_wait(&sh.raw_full[i % kRawStages], (i / kRawStages) & 1, kWaitNs)) *abort_v = 1;
         }
