@@ -109,6 +109,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+E2E_TIMING = ("median of the timed steps, each timed on the host around one synchronous step "
+              "(host-to-device copies of its inputs, the GPU work, device-to-host copies of its results)")
+
+
+def _median(xs):
+    ys = sorted(xs)
+    k = len(ys)
+    return ys[k // 2] if k % 2 else 0.5 * (ys[k // 2 - 1] + ys[k // 2])
+
+
 def _source_sha(path: str) -> str:
     with open(os.path.join(ROOT, path), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:12]
@@ -1043,12 +1053,14 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
 
         for _ in range(2):
             e2e_hash()
-        t0 = time.perf_counter()
+        dts = []
         for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
             e2e_hash()
-        dt = (time.perf_counter() - t0) / args.e2e_steps
+            dts.append(time.perf_counter() - t0)
+        dt = _median(dts)
         e2e = {"value": n * world / dt, "unit": "rows/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
-               "ms_per_step": dt * 1e3}
+               "ms_per_step": dt * 1e3, "timing": E2E_TIMING}
     elif args.e2e_steps > 0 and (sel is not None or lift is not None or W == 128):
         # host columns -> device (pinned, on the step's stream), selection /
         # aggregation / lifting and the release through the C ABI, released
@@ -1085,12 +1097,14 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
 
         for i in range(2):
             e2e_step(i)
-        t0 = time.perf_counter()
+        dts = []
         for i in range(args.e2e_steps):
+            t0 = time.perf_counter()
             e2e_step(2 + i)
-        dt = (time.perf_counter() - t0) / args.e2e_steps
+            dts.append(time.perf_counter() - t0)
+        dt = _median(dts)
         e2e = {"value": n * world / dt, "unit": "rows/s", "h2d_bytes_per_step": n * wcfg["in_bytes_per_row"],
-               "d2h_bytes_per_step": rel_cells * (8 + 1 + 4), "ms_per_step": dt * 1e3}
+               "d2h_bytes_per_step": rel_cells * (8 + 1 + 4), "ms_per_step": dt * 1e3, "timing": E2E_TIMING}
     elif args.e2e_steps > 0:
         h_keys = torch.from_numpy(wl.keys).pin_memory()
         h_gids = torch.from_numpy(wl.gids).pin_memory() if wl.gids is not None else None
@@ -1106,15 +1120,17 @@ def measure_single(args, workload: str, rows=None, steps=None, warmup=None, suit
         for i in range(2):
             B.pac_query_host(ctx, hin, hspecs, n_specs, 7 + i, 1.0 / 128, mode, h_noised.data_ptr(),
                              h_null.data_ptr(), h_flags.data_ptr(), sptr)
-        t0 = time.perf_counter()
+        dts = []
         for i in range(args.e2e_steps):
+            t0 = time.perf_counter()
             B.pac_query_host(ctx, hin, hspecs, n_specs, 100 + i, 1.0 / 128, mode, h_noised.data_ptr(),
                              h_null.data_ptr(), h_flags.data_ptr(), sptr)
-        dt = (time.perf_counter() - t0) / args.e2e_steps
+            dts.append(time.perf_counter() - t0)
+        dt = _median(dts)
         h2d = n * wcfg["in_bytes_per_row"]
         d2h = n_cells * (8 + 1 + 4)
         e2e = {"value": n * world / dt, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": dt * 1e3}
+               "ms_per_step": dt * 1e3, "timing": E2E_TIMING}
 
     peak, peak_src = _peaks()
     out_bytes = 0 if wcfg.get("hash_only") else G * W * 8 * n_specs + G * (16 if W == 64 else 24)
