@@ -1,6 +1,11 @@
-"""Host logic of the benchmark (no GPU): the DRAM-traffic lookup in the ncu
-summaries and the spec list each workload times."""
+"""Host logic of bench.py, without a GPU: the `bench-traffic:` lines of the
+ncu summaries (traffic per row of the dominant kernel, valid only while the
+kernel's source has the hash the line records), the spec list each workload
+times, and the median of the end-to-end step timings."""
+import hashlib
 import os
+
+import pytest
 
 import bench
 
@@ -11,46 +16,78 @@ class _B:
     PAC_I64 = 0
 
 
-def _write_profile(root, line):
-    os.makedirs(os.path.join(root, "profiles"), exist_ok=True)
-    with open(os.path.join(root, "profiles", "k_test.md"), "w") as f:
-        f.write("# a summary\n\n" + line + "\n")
+def _write(root, name, text):
+    path = os.path.join(root, name)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        f.write(text)
+    return path
 
 
-def test_traffic_follows_source_hash_and_path(tmp_path, monkeypatch):
+@pytest.fixture()
+def fake_root(tmp_path, monkeypatch):
     root = str(tmp_path)
-    src = os.path.join(root, "k.cu")
-    with open(src, "w") as f:
-        f.write("__global__ void k() {}\n")
+    src = _write(root, "csrc/k.cu", "__global__ void k() {}\n")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
     monkeypatch.setattr(bench, "ROOT", root)
-    sha = bench._source_sha("k.cu")
-    _write_profile(root, f"bench-traffic: workload=w1 path=4 kernel_source=k.cu sha={sha} bytes_per_row=16.5")
-    assert bench._traffic("w1", 1000, 4) == 16500.0
-    assert bench._traffic("w1", 1000, 2) is None        # another aggregation path
-    assert bench._traffic("w2", 1000, 4) is None        # another workload
-    # a line without a path is the tensor-core path's
-    _write_profile(root, f"bench-traffic: workload=w1 kernel_source=k.cu sha={sha} bytes_per_row=41.0")
-    assert bench._traffic("w1", 10, 2) == 410.0
-    # the kernel source changed since the counters were taken: no traffic
-    with open(src, "a") as f:
-        f.write("// edited\n")
-    assert bench._traffic("w1", 10, 2) is None
+    return root, sha
+
+
+def test_traffic_line_scales_to_the_rows_and_names_the_kernel(fake_root):
+    root, sha = fake_root
+    _write(root, "profiles/a.md",
+           f"text\nbench-traffic: workload=w1 path=5 kernel=k_x kernel_source=csrc/k.cu sha={sha} bytes_per_row=17.5\n")
+    assert bench._traffic_kernel("w1", 1000, 5) == (17500.0, "k_x")
+    assert bench._traffic("w1", 2000, 5) == 35000.0
+
+
+def test_traffic_line_without_a_path_is_the_tensor_core_path(fake_root):
+    root, sha = fake_root
+    _write(root, "profiles/a.md", f"bench-traffic: workload=w2 kernel_source=csrc/k.cu sha={sha} bytes_per_row=4\n")
+    assert bench._traffic_kernel("w2", 10, 2) == (40.0, None)
+    assert bench._traffic_kernel("w2", 10, 3) == (None, None)
+
+
+def test_traffic_is_null_once_the_kernel_source_changes(fake_root):
+    root, sha = fake_root
+    _write(root, "profiles/a.md",
+           f"bench-traffic: workload=w3 path=3 kernel=k_y kernel_source=csrc/k.cu sha={sha} bytes_per_row=8\n")
+    assert bench._traffic("w3", 10, 3) == 80.0
+    _write(root, "csrc/k.cu", "__global__ void k() { /* changed */ }\n")
+    assert bench._traffic_kernel("w3", 10, 3) == (None, None)
+
+
+def test_traffic_is_null_for_a_missing_source_or_workload(fake_root):
+    root, sha = fake_root
+    _write(root, "profiles/a.md",
+           f"bench-traffic: workload=w4 path=3 kernel=k_z kernel_source=csrc/gone.cu sha={sha} bytes_per_row=8\n")
+    assert bench._traffic_kernel("w4", 10, 3) == (None, None)
+    assert bench._traffic_kernel("other", 10, 3) == (None, None)
 
 
 def test_committed_traffic_lines_parse():
-    """Every committed bench-traffic line names an existing source file."""
+    # every line in profiles/ names a workload, a source and a positive figure
     import glob
     import re
-    pat = re.compile(r"bench-traffic:\s*workload=(\S+)\s+(?:path=(\d+)\s+)?kernel_source=(\S+)\s+sha=(\S+)")
-    found = 0
-    for f in glob.glob(os.path.join(bench.ROOT, "profiles", "*.md")):
+    pat = re.compile(r"bench-traffic:\s*workload=(\S+)\s+(?:path=(\d+)\s+)?(?:kernel=(\S+)\s+)?kernel_source=(\S+)"
+                     r"\s+sha=([0-9a-f]{12})\s+bytes_per_row=([0-9.]+)")
+    n = 0
+    for f in glob.glob(os.path.join(os.path.dirname(bench.__file__), "profiles", "*.md")):
         for line in open(f):
-            m = pat.search(line)
-            if m:
-                found += 1
+            if "bench-traffic:" in line:
+                m = pat.search(line)
+                assert m, line
                 assert m.group(1) in bench.WORKLOADS, f
-                assert os.path.exists(os.path.join(bench.ROOT, m.group(3))), f
-    assert found >= 2
+                assert float(m.group(6)) > 0
+                assert os.path.exists(os.path.join(os.path.dirname(bench.__file__), m.group(4)))
+                n += 1
+    assert n >= 1
+
+
+@pytest.mark.parametrize("xs,want", [([3.0], 3.0), ([5.0, 1.0, 3.0], 3.0), ([4.0, 1.0, 3.0, 2.0], 2.5),
+                                     ([21.4, 35.1, 21.3, 21.5], 21.45)])
+def test_median_of_step_timings(xs, want):
+    assert bench._median(xs) == pytest.approx(want)
 
 
 def test_spec_lists_of_the_workloads():
